@@ -1,0 +1,478 @@
+/*
+ * FP64 CPU oracle for the RKHS registration of "A New Framework for Registration
+ * of Semantic Point Clouds from Stereo and RGB-D Cameras" (arXiv:2012.03683).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain, obviously correct
+ * reference that the CUDA library is compared against.  Only the tests, the
+ * package smoke check and the benchmark's CPU-baseline leg may load it.  It
+ * shares no code, header or constant with the CUDA library.
+ *
+ * Every quantity is computed by brute force over all N x M point pairs in
+ * double precision, in the order the definitions state them:
+ *
+ *   y_j   = R z_j + t                      the pose T = (R, t) maps Z into X's
+ *                                          frame; T is the inverse of the h of
+ *                                          Problem 1 (Sec. III, Eq. max)
+ *   k     = sigma^2 exp(-|x_i - y_j|^2 / (2 l^2))           Eq. (k)
+ *   c_ij  = prod_k k_Vk(u_ki, v_kj)        Eq. (tensor_product) / (double_sum)
+ *           k_Vk = sigma_k^2 exp(-|u-v|^2/(2 l_k^2))        Eq. (newscalar)
+ *                  or <u, v>                                Eq. (scalar)
+ *   F     = sum_{pairs} k * c_ij                            Eq. (double_sum)
+ *   i_th  = F / sqrt(N M)                                   Eq. (indicator_actual)
+ *
+ * A pair enters the sum when the cutoff is off (cutoff_mult <= 0) or when
+ * |x_i - y_j|^2 <= (cutoff_mult * l)^2 (inclusive, in double precision).  The
+ * paper says the sum is sparse (Sec. III-B) but fixes no threshold.
+ *
+ * The gradient, the second derivative, the step rule and the stopping rules
+ * are not printed in the paper (it cites gradient ascent on the Lie group,
+ * Sec. I).  They are derived here from Eq. (double_sum) for the left
+ * perturbation T(xi) = exp(xi^) T, xi = (omega, v):
+ *
+ *   dF/dv     = (1/l^2) sum w (x_i - y_j)
+ *   dF/domega = (1/l^2) sum w (y_j x x_i)
+ *   d^2/dt^2 F(exp(t xi^) T) at t=0, with d = omega x y_j + v, e = y_j - x_i:
+ *             = sum w [ (e.d)^2 / l^4 - (|d|^2 + e.(omega x d)) / l^2 ]
+ *
+ * The gradient and the second derivative are pinned by central finite
+ * differences of F (tests).  The step rule, the annealing trigger and the
+ * convergence test are readings of the paper (Sec. IV for annealing) and are
+ * PARITY UNPINNED beyond their fixed point: the registration's end point is
+ * pinned by recovery of a known transform, its trajectory is not.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_MAX_BLOCKS 4
+
+typedef struct {
+    double ell;          /* geometric lengthscale l, Eq. (k) */
+    double sigma;        /* sigma of Eq. (k) */
+    double cutoff_mult;  /* pairs with |x-y| <= cutoff_mult*l enter; <= 0: all pairs */
+    int n_blocks;        /* feature blocks, concatenated per point */
+    int dim[ORC_MAX_BLOCKS];
+    int kind[ORC_MAX_BLOCKS];     /* 0: squared exponential, Eq. (newscalar); 1: inner product, Eq. (scalar) */
+    double scale[ORC_MAX_BLOCKS]; /* l_k of a squared-exponential block */
+    double sigk[ORC_MAX_BLOCKS];  /* sigma_k of a squared-exponential block */
+} orc_kernel;
+
+typedef struct {
+    int n;               /* points */
+    const double* xyz;   /* n x 3, row major */
+    const double* feat;  /* n x D, row major, blocks concatenated (NULL if D == 0) */
+} orc_cloud;
+
+static int feat_dim(const orc_kernel* k)
+{
+    int d = 0;
+    for (int b = 0; b < k->n_blocks; ++b) d += k->dim[b];
+    return d;
+}
+
+/* c_ij of Eq. (double_sum): the product over blocks of each block's kernel. */
+static double feature_kernel(const orc_kernel* k, const double* u, const double* v)
+{
+    double c = 1.0;
+    int off = 0;
+    for (int b = 0; b < k->n_blocks; ++b) {
+        const int d = k->dim[b];
+        if (k->kind[b] == 0) {
+            double s = 0.0;
+            for (int a = 0; a < d; ++a) {
+                const double diff = u[off + a] - v[off + a];
+                s += diff * diff;
+            }
+            c *= k->sigk[b] * k->sigk[b] * exp(-s / (2.0 * k->scale[b] * k->scale[b]));
+        } else {
+            double s = 0.0;
+            for (int a = 0; a < d; ++a) s += u[off + a] * v[off + a];
+            c *= s;
+        }
+        off += d;
+    }
+    return c;
+}
+
+static void cross3(const double a[3], const double b[3], double out[3])
+{
+    out[0] = a[1] * b[2] - a[2] * b[1];
+    out[1] = a[2] * b[0] - a[0] * b[2];
+    out[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double dot3(const double a[3], const double b[3])
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+/*
+ * Brute-force evaluation at pose T (row-major 4x4).
+ *   out[0]   F                      Eq. (double_sum)
+ *   out[1:4] dF/domega              left perturbation
+ *   out[4:7] dF/dv
+ *   out[7]   d^2F along dir (0 if dir == NULL)
+ * npairs receives the number of pairs inside the cutoff.
+ * Returns 0, or -1 on an invalid argument.
+ */
+int orc_eval(const orc_kernel* k, const orc_cloud* X, const orc_cloud* Z, const double T[16],
+             const double* dir, double out[8], long long* npairs, int nthreads)
+{
+    if (!k || !X || !Z || !T || !out || k->ell <= 0.0 || k->n_blocks < 0 || k->n_blocks > ORC_MAX_BLOCKS)
+        return -1;
+    const int D = feat_dim(k);
+    const double l2 = k->ell * k->ell;
+    const double l4 = l2 * l2;
+    const double rc2 = k->cutoff_mult > 0.0 ? (k->cutoff_mult * k->ell) * (k->cutoff_mult * k->ell) : -1.0;
+    const double s2 = k->sigma * k->sigma;
+    double F = 0.0, gw[3] = {0, 0, 0}, gv[3] = {0, 0, 0}, Fpp = 0.0;
+    long long cnt = 0;
+    double om[3] = {0, 0, 0}, vv[3] = {0, 0, 0};
+    if (dir) {
+        om[0] = dir[0]; om[1] = dir[1]; om[2] = dir[2];
+        vv[0] = dir[3]; vv[1] = dir[4]; vv[2] = dir[5];
+    }
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    /* Per-point partial sums, then one ordered sum: the result does not depend
+       on the thread count or schedule. */
+    double* part = (double*)calloc((size_t)(X->n > 0 ? X->n : 1) * 8, sizeof(double));
+    long long* pcnt = (long long*)calloc((size_t)(X->n > 0 ? X->n : 1), sizeof(long long));
+    if (!part || !pcnt) {
+        free(part);
+        free(pcnt);
+        return -1;
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int i = 0; i < X->n; ++i) {
+        const double* x = X->xyz + 3 * (size_t)i;
+        double Fi = 0.0, gwi[3] = {0, 0, 0}, gvi[3] = {0, 0, 0}, Fppi = 0.0;
+        long long ci = 0;
+        for (int j = 0; j < Z->n; ++j) {
+            const double* z = Z->xyz + 3 * (size_t)j;
+            double y[3];
+            for (int r = 0; r < 3; ++r) y[r] = T[4 * r + 0] * z[0] + T[4 * r + 1] * z[1] + T[4 * r + 2] * z[2] + T[4 * r + 3];
+            const double e[3] = {y[0] - x[0], y[1] - x[1], y[2] - x[2]};
+            const double d2 = dot3(e, e);
+            if (rc2 >= 0.0 && !(d2 <= rc2)) continue;
+            double c = 1.0;
+            if (D > 0) c = feature_kernel(k, X->feat + (size_t)D * i, Z->feat + (size_t)D * j);
+            const double w = s2 * exp(-d2 / (2.0 * l2)) * c;
+            ci += 1;
+            Fi += w;
+            double yx[3];
+            cross3(y, x, yx);
+            for (int r = 0; r < 3; ++r) {
+                gwi[r] += w * yx[r] / l2;
+                gvi[r] += -w * e[r] / l2;
+            }
+            if (dir) {
+                double d[3], od[3];
+                cross3(om, y, d);
+                d[0] += vv[0]; d[1] += vv[1]; d[2] += vv[2];
+                cross3(om, d, od);
+                const double ed = dot3(e, d);
+                Fppi += w * (ed * ed / l4 - (dot3(d, d) + dot3(e, od)) / l2);
+            }
+        }
+        double* p = part + 8 * (size_t)i;
+        p[0] = Fi;
+        p[1] = gwi[0]; p[2] = gwi[1]; p[3] = gwi[2];
+        p[4] = gvi[0]; p[5] = gvi[1]; p[6] = gvi[2];
+        p[7] = Fppi;
+        pcnt[i] = ci;
+    }
+    for (int i = 0; i < X->n; ++i) {
+        const double* p = part + 8 * (size_t)i;
+        F += p[0];
+        gw[0] += p[1]; gw[1] += p[2]; gw[2] += p[3];
+        gv[0] += p[4]; gv[1] += p[5]; gv[2] += p[6];
+        Fpp += p[7];
+        cnt += pcnt[i];
+    }
+    free(part);
+    free(pcnt);
+    out[0] = F;
+    out[1] = gw[0]; out[2] = gw[1]; out[3] = gw[2];
+    out[4] = gv[0]; out[5] = gv[1]; out[6] = gv[2];
+    out[7] = Fpp;
+    if (npairs) *npairs = cnt;
+    return 0;
+}
+
+/* Number of pairs whose squared distance lies within [lo, hi] (cutoff-boundary census). */
+long long orc_count_band(const orc_cloud* X, const orc_cloud* Z, const double T[16], double lo, double hi)
+{
+    long long cnt = 0;
+#pragma omp parallel for schedule(static) reduction(+ : cnt)
+    for (int i = 0; i < X->n; ++i) {
+        const double* x = X->xyz + 3 * (size_t)i;
+        for (int j = 0; j < Z->n; ++j) {
+            const double* z = Z->xyz + 3 * (size_t)j;
+            double d2 = 0.0;
+            for (int r = 0; r < 3; ++r) {
+                const double y = T[4 * r + 0] * z[0] + T[4 * r + 1] * z[1] + T[4 * r + 2] * z[2] + T[4 * r + 3];
+                d2 += (y - x[r]) * (y - x[r]);
+            }
+            if (d2 >= lo && d2 <= hi) cnt += 1;
+        }
+    }
+    return cnt;
+}
+
+/* ------------------------------------------------------------------------ */
+/* SE(3): closed-form exponential and logarithm (textbook, e.g. Murray, Li  */
+/* and Sastry), xi = (omega, v), hat(xi) = [[omega]x, v; 0, 0].             */
+/* ------------------------------------------------------------------------ */
+
+/* A = sin(th)/th, B = (1-cos th)/th^2, C = (th - sin th)/th^3 with series for small th. */
+static void se3_coeffs(double th, double* A, double* B, double* C)
+{
+    const double t2 = th * th;
+    if (th < 1e-3) {
+        *A = 1.0 - t2 / 6.0 + t2 * t2 / 120.0;
+        *B = 0.5 - t2 / 24.0 + t2 * t2 / 720.0;
+        *C = 1.0 / 6.0 - t2 / 120.0 + t2 * t2 / 5040.0;
+    } else {
+        *A = sin(th) / th;
+        *B = (1.0 - cos(th)) / t2;
+        *C = (th - sin(th)) / (t2 * th);
+    }
+}
+
+void orc_se3_exp(const double xi[6], double T[16])
+{
+    const double* w = xi;
+    const double* v = xi + 3;
+    const double th = sqrt(dot3(w, w));
+    double A, B, C;
+    se3_coeffs(th, &A, &B, &C);
+    const double W[9] = {0, -w[2], w[1], w[2], 0, -w[0], -w[1], w[0], 0};
+    double W2[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int q = 0; q < 3; ++q) s += W[3 * r + q] * W[3 * q + c];
+            W2[3 * r + c] = s;
+        }
+    for (int r = 0; r < 3; ++r) {
+        double tr = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            const double I = (r == c) ? 1.0 : 0.0;
+            T[4 * r + c] = I + A * W[3 * r + c] + B * W2[3 * r + c];
+            tr += (I + B * W[3 * r + c] + C * W2[3 * r + c]) * v[c];
+        }
+        T[4 * r + 3] = tr;
+    }
+    T[12] = 0.0; T[13] = 0.0; T[14] = 0.0; T[15] = 1.0;
+}
+
+/* Logarithm for rotation angles below pi.  Returns 0, or -1 near pi. */
+int orc_se3_log(const double T[16], double xi[6])
+{
+    const double tr = T[0] + T[5] + T[10];
+    double c = 0.5 * (tr - 1.0);
+    if (c > 1.0) c = 1.0;
+    if (c < -1.0) c = -1.0;
+    const double th = acos(c);
+    if (th > M_PI - 1e-6) return -1;
+    const double vee[3] = {T[9] - T[6], T[2] - T[8], T[4] - T[1]};
+    double f; /* omega = f * vee, f = th / (2 sin th) */
+    if (th < 1e-4) f = 0.5 + th * th / 12.0;
+    else f = th / (2.0 * sin(th));
+    const double w[3] = {f * vee[0], f * vee[1], f * vee[2]};
+    double A, B, C;
+    se3_coeffs(th, &A, &B, &C);
+    /* V^{-1} = I - W/2 + (1/th^2)(1 - A/(2B)) W^2 */
+    double k2;
+    if (th < 1e-3) k2 = 1.0 / 12.0 + th * th / 720.0;
+    else k2 = (1.0 - A / (2.0 * B)) / (th * th);
+    const double W[9] = {0, -w[2], w[1], w[2], 0, -w[0], -w[1], w[0], 0};
+    const double t[3] = {T[3], T[7], T[11]};
+    for (int r = 0; r < 3; ++r) {
+        double s = 0.0;
+        for (int q = 0; q < 3; ++q) {
+            double W2rq = 0.0;
+            for (int p = 0; p < 3; ++p) W2rq += W[3 * r + p] * W[3 * p + q];
+            const double I = (r == q) ? 1.0 : 0.0;
+            s += (I - 0.5 * W[3 * r + q] + k2 * W2rq) * t[q];
+        }
+        xi[3 + r] = s;
+    }
+    xi[0] = w[0]; xi[1] = w[1]; xi[2] = w[2];
+    return 0;
+}
+
+static void mat4_mul(const double A[16], const double B[16], double C[16])
+{
+    double tmp[16];
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            double s = 0.0;
+            for (int q = 0; q < 4; ++q) s += A[4 * r + q] * B[4 * q + c];
+            tmp[4 * r + c] = s;
+        }
+    memcpy(C, tmp, sizeof(tmp));
+}
+
+/* Gram-Schmidt on the columns of R (keeps det R = +1). */
+static void reorthonormalize(double T[16])
+{
+    double c0[3] = {T[0], T[4], T[8]}, c1[3] = {T[1], T[5], T[9]}, c2[3];
+    double n0 = sqrt(dot3(c0, c0));
+    for (int r = 0; r < 3; ++r) c0[r] /= n0;
+    const double p = dot3(c0, c1);
+    for (int r = 0; r < 3; ++r) c1[r] -= p * c0[r];
+    double n1 = sqrt(dot3(c1, c1));
+    for (int r = 0; r < 3; ++r) c1[r] /= n1;
+    cross3(c0, c1, c2);
+    for (int r = 0; r < 3; ++r) {
+        T[4 * r + 0] = c0[r];
+        T[4 * r + 1] = c1[r];
+        T[4 * r + 2] = c2[r];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Registration loop                                                        */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double ell_init, ell_min;     /* lengthscale schedule */
+    double decay;                 /* l <- max(decay*l, ell_min) when the indicator stabilises (Sec. IV: 2 %) */
+    double indicator_tol;         /* |i_k - i_ref| < tol * |i_ref| counts as "stabilised" */
+    int max_iters;
+    int anneal;
+    double step_tol_rot, step_tol_trans;   /* convergence: |t omega| and |t v| below these */
+    double max_step_rot;                   /* clamp |t omega| (rad) */
+    double max_step_trans;                 /* clamp |t v| (m); <= 0: 0.5 * current l */
+} orc_reg;
+
+typedef struct {
+    int iters;
+    int status;          /* 0 converged, 1 iteration cap */
+    double ell_final, F, i_theta, last_step_rot, last_step_trans;
+    long long pairs_total;
+} orc_info;
+
+#define ORC_TRACE_STRIDE 10 /* ell, F, i_theta, |g|, Fpp, t, |t omega|, |t v|, decayed, pairs */
+
+/*
+ * Gradient ascent on SE(3), one line-Newton step along the gradient per
+ * iteration, with the lengthscale annealing of Sec. IV.
+ *
+ * Iteration k at pose T_k and lengthscale l_k:
+ *   1. F, g, and the second derivative F'' along xi = g (brute force).
+ *   2. i_k = F / sqrt(N M), Eq. (indicator_actual).
+ *   3. Step: t = |g|^2 / (-F'') if F'' < 0, else 1e-3 / |g|; then clamp so that
+ *      |t omega| <= max_step_rot and |t v| <= max_step_trans.
+ *   4. T_{k+1} = exp(t xi^) T_k; Gram-Schmidt on R every 16 iterations.
+ *   5. Stop (converged) if annealing is off or l_k == ell_min, and
+ *      |t omega| < step_tol_rot and |t v| < step_tol_trans.
+ *   6. Annealing: if a reference indicator i_ref at l_k exists and
+ *      |i_k - i_ref| < tol |i_ref|, then l_{k+1} = max(decay l_k, ell_min) and
+ *      the reference is cleared; otherwise i_ref = i_k.
+ * replay (optional, max_iters entries): when given, replay[k] in {0,1} forces
+ * the decay decision of step 6 instead of the indicator test.
+ * trace (optional, max_iters x ORC_TRACE_STRIDE doubles) records each iteration.
+ */
+int orc_register(const orc_kernel* kin, const orc_reg* r, const orc_cloud* X, const orc_cloud* Z,
+                 const double T_init[16], double T_out[16], orc_info* info, double* trace,
+                 const int* replay, int nthreads)
+{
+    if (!kin || !r || !X || !Z || !T_init || !T_out || r->max_iters < 0) return -1;
+    orc_kernel k = *kin;
+    double T[16];
+    memcpy(T, T_init, sizeof(T));
+    double ell = r->ell_init;
+    int have_ref = 0;
+    double i_ref = 0.0;
+    const double norm = (X->n > 0 && Z->n > 0) ? 1.0 / sqrt((double)X->n * (double)Z->n) : 0.0;
+    orc_info inf;
+    memset(&inf, 0, sizeof(inf));
+    inf.status = 1;
+    int it;
+    for (it = 0; it < r->max_iters; ++it) {
+        k.ell = ell;
+        double out[8];
+        long long np = 0;
+        orc_eval(&k, X, Z, T, NULL, out, &np, nthreads);
+        double g[6];
+        memcpy(g, out + 1, sizeof(g));
+        /* second derivative along the gradient */
+        orc_eval(&k, X, Z, T, g, out, NULL, nthreads);
+        const double F = out[0], Fpp = out[7];
+        const double ith = F * norm;
+        double gn2 = 0.0;
+        for (int q = 0; q < 6; ++q) gn2 += g[q] * g[q];
+        double t = 0.0;
+        if (gn2 > 0.0) {
+            t = (Fpp < 0.0) ? gn2 / (-Fpp) : 1e-3 / sqrt(gn2);
+            const double wn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+            const double vn = sqrt(g[3] * g[3] + g[4] * g[4] + g[5] * g[5]);
+            const double max_tr = r->max_step_trans > 0.0 ? r->max_step_trans : 0.5 * ell;
+            if (t * wn > r->max_step_rot) t = r->max_step_rot / wn;
+            if (t * vn > max_tr) t = max_tr / vn;
+        }
+        double xi[6], E[16];
+        for (int q = 0; q < 6; ++q) xi[q] = t * g[q];
+        orc_se3_exp(xi, E);
+        mat4_mul(E, T, T);
+        if ((it + 1) % 16 == 0) reorthonormalize(T);
+        const double srot = sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
+        const double strans = sqrt(xi[3] * xi[3] + xi[4] * xi[4] + xi[5] * xi[5]);
+        inf.pairs_total += np;
+        inf.F = F;
+        inf.i_theta = ith;
+        inf.last_step_rot = srot;
+        inf.last_step_trans = strans;
+        inf.ell_final = ell;
+        int decayed = 0;
+        const int at_floor = !r->anneal || ell <= r->ell_min;
+        const int converged = at_floor && srot < r->step_tol_rot && strans < r->step_tol_trans;
+        if (!converged && r->anneal && ell > r->ell_min) {
+            int fire;
+            if (replay) fire = replay[it] != 0;
+            else fire = have_ref && fabs(ith - i_ref) < r->indicator_tol * fabs(i_ref);
+            if (fire) {
+                ell = r->decay * ell;
+                if (ell < r->ell_min) ell = r->ell_min;
+                have_ref = 0;
+                decayed = 1;
+            } else {
+                i_ref = ith;
+                have_ref = 1;
+            }
+        }
+        if (trace) {
+            double* tr = trace + (size_t)ORC_TRACE_STRIDE * it;
+            tr[0] = k.ell; tr[1] = F; tr[2] = ith; tr[3] = sqrt(gn2); tr[4] = Fpp;
+            tr[5] = t; tr[6] = srot; tr[7] = strans; tr[8] = decayed; tr[9] = (double)np;
+        }
+        if (converged) {
+            inf.status = 0;
+            ++it;
+            break;
+        }
+    }
+    inf.iters = it;
+    memcpy(T_out, T, sizeof(T));
+    if (info) *info = inf;
+    return 0;
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

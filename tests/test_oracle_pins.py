@@ -1,0 +1,404 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these tests re-types the oracle's formula.  Each checks the oracle
+against an independent route:
+  * quadrature of the Gaussian convolution identity (the SE kernel of Eq. (k)
+    is, up to a constant, the L2 inner product of two narrower Gaussians), so
+    F = <f_X, f_{h^-1 Z}> becomes an integral of two smoothed fields;
+  * the explicit tensor product (numpy.kron) of Eq. (tensor_product);
+  * scipy's k-d tree for the set of pairs inside the cutoff;
+  * scipy.linalg.expm for the SE(3) exponential;
+  * central finite differences of F on se(3) for the gradient and the second
+    derivative;
+  * invariants: symmetry of the inner product, invariance under a common rigid
+    motion, Cauchy-Schwarz, the Remark of Sec. III-C, the behaviour of Fig. 3,
+    and recovery of a known transform.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+from scipy.spatial import cKDTree
+
+import oracle
+import scenes
+
+
+def rng(seed=0):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def hat(xi):
+    w, v = xi[:3], xi[3:]
+    M = np.zeros((4, 4))
+    M[:3, :3] = [[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]]
+    M[:3, 3] = v
+    return M
+
+
+def expm_se3(xi):
+    return scipy.linalg.expm(hat(np.asarray(xi, dtype=np.float64)))
+
+
+def rand_T(r, ang=0.6, tr=0.5):
+    xi = np.concatenate([r.normal(size=3) * ang / math.sqrt(3), r.normal(size=3) * tr / math.sqrt(3)])
+    return expm_se3(xi)
+
+
+def transform(T, P):
+    return P @ T[:3, :3].T + T[:3, 3]
+
+
+# ---------------------------------------------------------------------------
+# 1. the inner product by quadrature (Eq. k, newscalar, scalar, double_sum)
+# ---------------------------------------------------------------------------
+
+def _grid(lo, hi, h):
+    n = int(math.ceil((hi - lo) / h)) + 1
+    return lo + h * np.arange(n)
+
+
+def _gauss_fields(P, axes, ell):
+    """exp(-|p - u|^2 / l^2) on a 3-D tensor grid, one flattened field per point."""
+    gx, gy, gz = axes
+    out = []
+    for p in P:
+        fx = np.exp(-((gx - p[0]) ** 2) / ell ** 2)
+        fy = np.exp(-((gy - p[1]) ** 2) / ell ** 2)
+        fz = np.exp(-((gz - p[2]) ** 2) / ell ** 2)
+        out.append(np.einsum("a,b,c->abc", fx, fy, fz).ravel())
+    return np.array(out)
+
+
+def quad_F(X, Y, ell, sigma, fx=None, fy=None, feat=None):
+    """sigma^2 (pi l^2/2)^(-3/2) * integral of sum_i a_i(u) * sum_j b_j(u) du,
+    with the feature part either a 1-D squared exponential (feat=("se", l_c,
+    sigma_c)) integrated on its own axis, or an inner product (feat=("dot",))."""
+    lo = np.minimum(X.min(0), Y.min(0)) - 6 * ell
+    hi = np.maximum(X.max(0), Y.max(0)) + 6 * ell
+    h = ell / 3.0
+    axes = [_grid(lo[d], hi[d], h) for d in range(3)]
+    GX = _gauss_fields(X, axes, ell)
+    GY = _gauss_fields(Y, axes, ell)
+    c = sigma ** 2 * (math.pi * ell ** 2 / 2) ** -1.5 * h ** 3
+    if feat is None:
+        return c * np.sum(GX.sum(0) * GY.sum(0))
+    if feat[0] == "dot":
+        A = fx.T @ GX  # (D, grid)
+        B = fy.T @ GY
+        return c * np.sum(A * B)
+    _, lc, sc = feat
+    flo = min(fx.min(), fy.min()) - 6 * lc
+    fhi = max(fx.max(), fy.max()) + 6 * lc
+    hr = lc / 3.0
+    r = _grid(flo, fhi, hr)
+    HX = np.exp(-((r[None, :] - fx[:, :1]) ** 2) / lc ** 2)  # (n, R)
+    HY = np.exp(-((r[None, :] - fy[:, :1]) ** 2) / lc ** 2)
+    A = np.einsum("iu,ir->ur", GX, HX)
+    B = np.einsum("ju,jr->ur", GY, HY)
+    cc = sc ** 2 * (math.pi * lc ** 2 / 2) ** -0.5 * hr
+    return c * cc * np.sum(A * B)
+
+
+def test_inner_product_geometric_by_quadrature():
+    r = rng(1)
+    X = r.uniform(-0.5, 0.5, size=(3, 3))
+    Z = r.uniform(-0.5, 0.5, size=(4, 3))
+    T = rand_T(r, 0.3, 0.2)
+    ell, sigma = 0.3, 1.3
+    ref = quad_F(X, transform(T, Z), ell, sigma)
+    got = oracle.evaluate(X, Z, T, ell=ell, sigma=sigma)["F"]
+    assert got == pytest.approx(ref, rel=1e-10)
+
+
+def test_inner_product_se_feature_by_quadrature():
+    r = rng(2)
+    X = r.uniform(-0.4, 0.4, size=(3, 3))
+    Z = r.uniform(-0.4, 0.4, size=(3, 3))
+    fx = r.uniform(0, 1, size=(3, 1))
+    fz = r.uniform(0, 1, size=(3, 1))
+    T = rand_T(r, 0.2, 0.1)
+    ell, sigma, lc, sc = 0.3, 0.9, 0.25, 1.7
+    ref = quad_F(X, transform(T, Z), ell, sigma, fx, fz, feat=("se", lc, sc))
+    got = oracle.evaluate(X, Z, T, FX=fx, FZ=fz, blocks=[("se", 1, lc, sc)], ell=ell, sigma=sigma)["F"]
+    assert got == pytest.approx(ref, rel=1e-9)
+
+
+def test_inner_product_dot_feature_by_quadrature():
+    r = rng(3)
+    X = r.uniform(-0.4, 0.4, size=(4, 3))
+    Z = r.uniform(-0.4, 0.4, size=(3, 3))
+    fx = r.dirichlet(np.ones(5), size=4)
+    fz = r.dirichlet(np.ones(5), size=3)
+    T = rand_T(r, 0.2, 0.1)
+    ell, sigma = 0.25, 1.0
+    ref = quad_F(X, transform(T, Z), ell, sigma, fx, fz, feat=("dot",))
+    got = oracle.evaluate(X, Z, T, FX=fx, FZ=fz, blocks=[("dot", 5, 1.0, 1.0)], ell=ell, sigma=sigma)["F"]
+    assert got == pytest.approx(ref, rel=1e-10)
+
+
+def test_tensor_product_blocks_equal_kron():
+    """Eq. (tensor_product): <u1 (x) u2, v1 (x) v2> = <u1,v1><u2,v2>."""
+    r = rng(4)
+    X = r.uniform(-1, 1, size=(6, 3))
+    Z = r.uniform(-1, 1, size=(5, 3))
+    a1, a2 = r.uniform(0, 1, size=(6, 2)), r.uniform(0, 1, size=(6, 3))
+    b1, b2 = r.uniform(0, 1, size=(5, 2)), r.uniform(0, 1, size=(5, 3))
+    T = rand_T(r)
+    two = oracle.evaluate(X, Z, T, FX=np.hstack([a1, a2]), FZ=np.hstack([b1, b2]),
+                          blocks=[("dot", 2, 1, 1), ("dot", 3, 1, 1)], ell=0.7)
+    kx = np.array([np.kron(a1[i], a2[i]) for i in range(6)])
+    kz = np.array([np.kron(b1[j], b2[j]) for j in range(5)])
+    one = oracle.evaluate(X, Z, T, FX=kx, FZ=kz, blocks=[("dot", 6, 1, 1)], ell=0.7)
+    assert two["F"] == pytest.approx(one["F"], rel=1e-13)
+    np.testing.assert_allclose(two["g"], one["g"], rtol=1e-12, atol=1e-14)
+
+
+def test_geometric_only_equals_unit_labels():
+    """Eq. (geometric_only): labels identically 1 reduce to the plain kernel sum."""
+    r = rng(5)
+    X = r.uniform(-1, 1, size=(7, 3))
+    Z = r.uniform(-1, 1, size=(9, 3))
+    T = rand_T(r)
+    a = oracle.evaluate(X, Z, T, ell=0.5)
+    b = oracle.evaluate(X, Z, T, FX=np.ones((7, 1)), FZ=np.ones((9, 1)), blocks=[("dot", 1, 1, 1)], ell=0.5)
+    assert a["F"] == pytest.approx(b["F"], rel=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# 2. the cutoff: the pair set is the k-d tree's ball query
+# ---------------------------------------------------------------------------
+
+def test_cutoff_pair_set_matches_kdtree():
+    r = rng(6)
+    X = r.uniform(-2, 2, size=(400, 3))
+    Z = r.uniform(-2, 2, size=(500, 3))
+    T = rand_T(r, 0.3, 0.3)
+    ell, cm = 0.2, 3.0
+    res = oracle.evaluate(X, Z, T, ell=ell, cutoff_mult=cm)
+    Y = transform(T, Z)
+    n_tree = sum(len(v) for v in cKDTree(Y).query_ball_point(X, cm * ell))
+    assert res["npairs"] == n_tree
+    # the pairs left out are exactly the ones beyond the radius: their kernel
+    # values make up the difference to the dense sum
+    dense = oracle.evaluate(X, Z, T, ell=ell)
+    d2 = ((X[:, None, :] - Y[None, :, :]) ** 2).sum(-1)
+    far = np.exp(-d2[d2 > (cm * ell) ** 2] / (2 * ell ** 2)).sum()
+    assert dense["F"] - res["F"] == pytest.approx(far, rel=1e-9, abs=1e-12)
+
+
+def test_empty_clouds_give_zero():
+    X = np.zeros((0, 3))
+    Z = np.ones((5, 3))
+    res = oracle.evaluate(X, Z, np.eye(4), ell=0.3)
+    assert res["F"] == 0 and res["npairs"] == 0 and not np.any(res["g"])
+    assert oracle.indicator(X, Z, np.eye(4), ell=0.3) == 0.0
+
+
+# ---------------------------------------------------------------------------
+# 3. invariants
+# ---------------------------------------------------------------------------
+
+BLOCKS = [("se", 3, 0.4, 1.1), ("dot", 4, 1.0, 1.0)]
+
+
+def _cloud_pair(seed, n=30, m=25):
+    r = rng(seed)
+    X = r.uniform(-1, 1, size=(n, 3))
+    Z = r.uniform(-1, 1, size=(m, 3))
+    FX = np.hstack([r.uniform(0, 1, size=(n, 3)), r.dirichlet(np.ones(4), size=n)])
+    FZ = np.hstack([r.uniform(0, 1, size=(m, 3)), r.dirichlet(np.ones(4), size=m)])
+    return r, X, Z, FX, FZ
+
+
+@pytest.mark.parametrize("cm", [0.0, 2.5])
+def test_symmetry(cm):
+    """<f_X, T f_Z> = <f_Z, T^-1 f_X> (the inner product and c_ij are symmetric)."""
+    r, X, Z, FX, FZ = _cloud_pair(7)
+    T = rand_T(r)
+    a = oracle.evaluate(X, Z, T, FX=FX, FZ=FZ, blocks=BLOCKS, ell=0.4, cutoff_mult=cm, sigma=1.2)
+    b = oracle.evaluate(Z, X, np.linalg.inv(T), FX=FZ, FZ=FX, blocks=BLOCKS, ell=0.4, cutoff_mult=cm, sigma=1.2)
+    assert a["F"] == pytest.approx(b["F"], rel=1e-12)
+    assert a["npairs"] == b["npairs"]
+
+
+def test_rigid_invariance():
+    """F(GX, GZ, G T G^-1) = F(X, Z, T) for any rigid G."""
+    r, X, Z, FX, FZ = _cloud_pair(8)
+    T = rand_T(r)
+    G = rand_T(r, 2.0, 5.0)
+    a = oracle.evaluate(X, Z, T, FX=FX, FZ=FZ, blocks=BLOCKS, ell=0.4)
+    b = oracle.evaluate(transform(G, X), transform(G, Z), G @ T @ np.linalg.inv(G), FX=FX, FZ=FZ,
+                        blocks=BLOCKS, ell=0.4)
+    assert a["F"] == pytest.approx(b["F"], rel=1e-11)
+    assert oracle.indicator(X, Z, T, FX=FX, FZ=FZ, blocks=BLOCKS, ell=0.4) == pytest.approx(
+        oracle.indicator(transform(G, X), transform(G, Z), G @ T @ np.linalg.inv(G), FX=FX, FZ=FZ,
+                         blocks=BLOCKS, ell=0.4), rel=1e-11)
+
+
+@pytest.mark.parametrize("cm", [0.0, 3.0])
+def test_zero_gradient_identical_clouds(cm):
+    """Z = X, T = I: every pair (i, j) has its mirror (j, i), so g = 0."""
+    r, X, _, FX, _ = _cloud_pair(9)
+    res = oracle.evaluate(X, X, np.eye(4), FX=FX, FZ=FX, blocks=BLOCKS, ell=0.4, cutoff_mult=cm)
+    assert np.abs(res["g"]).max() < 1e-12 * max(1.0, res["F"])
+
+
+def test_cauchy_schwarz():
+    """Dense mode: F(X,Z,T)^2 <= F(X,X,I) F(Z,Z,I), equality for Z = X, T = I."""
+    r, X, Z, FX, FZ = _cloud_pair(10)
+    kw = dict(blocks=BLOCKS, ell=0.5)
+    fxx = oracle.evaluate(X, X, np.eye(4), FX=FX, FZ=FX, **kw)["F"]
+    fzz = oracle.evaluate(Z, Z, np.eye(4), FX=FZ, FZ=FZ, **kw)["F"]
+    for _ in range(5):
+        T = rand_T(r)
+        f = oracle.evaluate(X, Z, T, FX=FX, FZ=FZ, **kw)["F"]
+        assert f * f <= fxx * fzz * (1 + 1e-12)
+    G = rand_T(r)
+    f_same = oracle.evaluate(X, transform(G, X), np.linalg.inv(G), FX=FX, FZ=FX, **kw)["F"]
+    assert f_same == pytest.approx(fxx, rel=1e-12)
+
+
+def test_remark_norm_sqrt_n():
+    """Remark (Sec. III-C): k -> delta and c_ii = 1 give |f_X| = sqrt(|X|), so
+    the indicator of a cloud with itself tends to 1 as l shrinks below the
+    point spacing."""
+    r = rng(11)
+    X = r.uniform(-1, 1, size=(50, 3))
+    vals = [oracle.indicator(X, X, np.eye(4), ell=ell) for ell in (0.2, 0.05, 0.01, 0.002)]
+    assert vals[0] > vals[1] > vals[2] >= vals[3]
+    assert vals[-1] == pytest.approx(1.0, abs=1e-12)
+    assert math.sqrt(oracle.evaluate(X, X, np.eye(4), ell=0.002)["F"]) == pytest.approx(math.sqrt(50), rel=1e-12)
+
+
+def test_indicator_peaks_at_zero_error():
+    """Fig. 3 (Sec. III-C): rotating or translating a cloud away from itself
+    lowers the indicator, and the maximum is at zero error."""
+    p = scenes.cube_pair(n=600)
+    X, F = p.X.astype(np.float64), p.FX.astype(np.float64)
+    kw = dict(FX=F, FZ=F, blocks=p.blocks, ell=0.1)
+    base = oracle.indicator(X, X, np.eye(4), **kw)
+    axis = np.array([0.3, -0.5, 0.8]) / np.linalg.norm([0.3, -0.5, 0.8])
+    prev = base
+    for deg in (1, 2, 4, 8, 16):
+        T = expm_se3(np.concatenate([axis * math.radians(deg), np.zeros(3)]))
+        cur = oracle.indicator(X, X, T, **kw)
+        assert cur < prev
+        prev = cur
+    prev = base
+    for d in (0.02, 0.05, 0.1, 0.2, 0.4):
+        T = expm_se3(np.concatenate([np.zeros(3), axis * d]))
+        cur = oracle.indicator(X, X, T, **kw)
+        assert cur < prev
+        prev = cur
+
+
+# ---------------------------------------------------------------------------
+# 4. the se(3) gradient and the second derivative by finite differences
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("with_feat", [False, True])
+def test_gradient_central_differences(with_feat):
+    r, X, Z, FX, FZ = _cloud_pair(12, 20, 18)
+    T = rand_T(r, 0.3, 0.3)
+    kw = dict(ell=0.45, sigma=1.3)
+    if with_feat:
+        kw.update(FX=FX, FZ=FZ, blocks=BLOCKS)
+    g = oracle.evaluate(X, Z, T, **kw)["g"]
+    eps = 1e-5
+    fd = np.zeros(6)
+    for k in range(6):
+        e = np.zeros(6)
+        e[k] = eps
+        fp = oracle.evaluate(X, Z, expm_se3(e) @ T, **kw)["F"]
+        fm = oracle.evaluate(X, Z, expm_se3(-e) @ T, **kw)["F"]
+        fd[k] = (fp - fm) / (2 * eps)
+    assert np.abs(g - fd).max() <= 1e-6 * np.linalg.norm(g)
+
+
+def test_second_derivative_along_direction():
+    r, X, Z, FX, FZ = _cloud_pair(13, 20, 18)
+    T = rand_T(r, 0.3, 0.3)
+    kw = dict(FX=FX, FZ=FZ, blocks=BLOCKS, ell=0.45)
+    for _ in range(3):
+        xi = r.normal(size=6)
+        res = oracle.evaluate(X, Z, T, direction=xi, **kw)
+        eps = 1e-4
+        f0 = res["F"]
+        fp = oracle.evaluate(X, Z, expm_se3(eps * xi) @ T, **kw)["F"]
+        fm = oracle.evaluate(X, Z, expm_se3(-eps * xi) @ T, **kw)["F"]
+        fd2 = (fp - 2 * f0 + fm) / eps ** 2
+        assert res["Fpp"] == pytest.approx(fd2, rel=2e-5, abs=1e-6 * abs(f0))
+        # first derivative along xi is g . xi
+        fd1 = (fp - fm) / (2 * eps)
+        assert float(res["g"] @ xi) == pytest.approx(fd1, rel=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# 5. SE(3) exponential / logarithm
+# ---------------------------------------------------------------------------
+
+def test_se3_exp_matches_expm():
+    r = rng(14)
+    for scale in (1e-8, 1e-5, 9e-4, 1.1e-3, 0.1, 1.0, 2.5):
+        for _ in range(4):
+            xi = r.normal(size=6) * scale
+            T = oracle.se3_exp(xi)
+            np.testing.assert_allclose(T, expm_se3(xi), rtol=0, atol=1e-14 * max(1.0, np.abs(xi).max()))
+            assert np.linalg.det(T[:3, :3]) == pytest.approx(1.0, abs=1e-13)
+
+
+def test_se3_log_inverts_exp():
+    r = rng(15)
+    for scale in (1e-9, 1e-6, 1e-3, 0.3, 2.0):
+        for _ in range(4):
+            xi = r.normal(size=6) * scale
+            if np.linalg.norm(xi[:3]) > 3.0:
+                continue
+            back = oracle.se3_log(oracle.se3_exp(xi))
+            np.testing.assert_allclose(back, xi, rtol=1e-9, atol=1e-15)
+    T = rand_T(r)
+    np.testing.assert_allclose(oracle.se3_exp(oracle.se3_log(T)), T, atol=1e-13)
+
+
+def test_se3_small_angle_branch_continuous():
+    axis = np.array([0.48, -0.6, 0.64])
+    v = np.array([0.3, 0.1, -0.2])
+    lo = oracle.se3_exp(np.concatenate([axis * (1e-3 * (1 - 1e-9)), v]))
+    hi = oracle.se3_exp(np.concatenate([axis * (1e-3 * (1 + 1e-9)), v]))
+    np.testing.assert_allclose(lo, hi, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# 6. registration end point: recovery of a known transform
+# ---------------------------------------------------------------------------
+
+def test_recovery_of_known_transform():
+    """Z = T_gt X with the same points: the dense F attains its maximum at
+    T_gt^-1 (Cauchy-Schwarz), and the ascent converges there."""
+    p = scenes.cube_pair(n=300, seed=77)
+    T_out, info, trace = oracle.register(p.X, p.Z, np.eye(4), FX=p.FX, FZ=p.FZ, blocks=p.blocks, ell=0.3,
+                                         max_iters=400, step_tol_rot=1e-9, step_tol_trans=1e-9)
+    assert info["status"] == 0
+    err = oracle.se3_log(np.linalg.inv(p.T_true) @ T_out)
+    assert np.linalg.norm(err[:3]) < 1e-6 and np.linalg.norm(err[3:]) < 1e-6
+    # the objective never decreases along the way
+    F = trace[:, 1]
+    assert np.all(np.diff(F) > -1e-9 * F[:-1])
+
+
+def test_replay_reproduces_annealing_decisions():
+    p = scenes.cube_pair(n=200, seed=78)
+    kw = dict(FX=p.FX, FZ=p.FZ, blocks=p.blocks, ell=0.5, ell_min=0.2, cutoff_mult=3.0, anneal=True,
+              max_iters=40, indicator_tol=5e-3)
+    T1, info1, tr1 = oracle.register(p.X, p.Z, np.eye(4), **kw)
+    assert tr1[:, 8].sum() > 0  # some decays happened
+    T2, info2, tr2 = oracle.register(p.X, p.Z, np.eye(4), replay=tr1[:, 8].astype(int), **kw)
+    np.testing.assert_array_equal(tr1, tr2)
+    np.testing.assert_array_equal(T1, T2)
+    # the lengthscale only shrinks, by the decay factor, never below the floor
+    ells = tr1[:, 0]
+    assert np.all(np.diff(ells) <= 0) and ells.min() >= 0.2
+    steps = ells[1:][np.diff(ells) < 0] / ells[:-1][np.diff(ells) < 0]
+    assert np.all((np.abs(steps - 0.98) < 1e-12) | (ells[1:][np.diff(ells) < 0] == 0.2))
