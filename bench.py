@@ -1,0 +1,332 @@
+"""Benchmark: registrations of the stereo-like street pair on GB300.
+
+One step = one full registration (cvo_register_pair) of the 20,000-point
+street pair: grid and query setup, then up to 100 annealed iterations of the
+fused sweep + on-device step (lengthscale 0.3 -> 0.05 m, cutoff 3
+lengthscales, RGB + 19-class labels).  Inputs are resident in HBM when the
+timed region starts; L2 is flushed (256 MB write) between steps.
+
+value  = in-cutoff kernel-pair evaluations per second, summed over ranks
+e2e    = the same metric through the C ABI with pinned host buffers (host to
+         device copies inside the timed region)
+roofline = the sweep kernel's algorithmic FP32 FLOPs per launch over its
+         event-timed duration, against the FP32 peak from the unit counts
+cpu_baseline = the FP64 oracle's own registration loop on the same pair,
+         first 20 iterations, on the host cores
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cvo|reference]
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "kernel-pair evals/s & registered pairs/s, batched vs plain GPU, at oracle tol"
+UNIT = "pair-evals/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def flops_per_pair(blocks):
+    """Algorithmic FP32 FLOPs of one in-cutoff pair (FMA = 2): offset 3,
+    squared distance 5, exponent scale 1, moments W/E/Q 19; a squared-
+    exponential block of d entries 3d + 1; an inner-product block of d
+    entries 2d - 1 plus the product with the kernel value 1.  The ex2 runs on
+    the XU pipe and is not counted."""
+    f = 3 + 5 + 1 + 19
+    for kind, dim, _, _ in blocks:
+        f += 3 * dim + 1 if kind == "se" else 2 * dim
+    return f
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def profile_traffic(kernel_src):
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "sweep_street-20k.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m or not t:
+        return None
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    return float(t.group(1)) if sha == m.group(1) else None
+
+
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index):
+        self.proc = None
+        self.index = index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup(backend):
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist, world, rank, local
+
+
+def max_over_ranks(dist, world, value, device=None):
+    if world == 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, world, value, device=None):
+    if world == 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def workload():
+    import scenes
+    p = scenes.street_pair()
+    pr = p.params
+    kw = dict(blocks=p.blocks, ell=pr["ell"], ell_min=pr["ell_min"], cutoff_mult=pr["cutoff_mult"],
+              max_iters=pr["max_iters"], anneal=pr["anneal"])
+    config = {"workload": "street-20k", "points_per_cloud": p.n,
+              "features": "rgb (squared-exponential, scale 0.2) x 19-class labels (inner product), float32",
+              "lengthscale": "0.3 -> 0.05 m annealed (2 % decays)", "cutoff": "3 lengthscales",
+              "max_iters": pr["max_iters"], "l2": "flushed between steps (256 MB write)"}
+    return p, kw, config
+
+
+def cpu_baseline(p, kw, iters=20):
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    _, info, _ = oracle.register(p.X, p.Z, np.eye(4), FX=p.FX, FZ=p.FZ, **dict(kw, max_iters=iters))
+    dt = time.perf_counter() - t0
+    return {"value": info["pairs_total"] / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {info['iters']} of <= {kw['max_iters']} iterations of the FP64 oracle's registration "
+                      f"of the full street-20k pair ({info['pairs_total']} in-cutoff pairs, {dt:.1f} s)",
+            "seconds": dt}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step is a bounded sample of the
+    same workload (the first iterations of the oracle's registration)."""
+    dist, world, rank, _ = dist_setup("gloo")
+    if rank != 0:
+        return
+    p, kw, config = workload()
+    iters = 4
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.register(p.X, p.Z, np.eye(4), FX=p.FX, FZ=p.FZ, **dict(kw, max_iters=iters))
+    pairs, total = 0, 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _, info, _ = oracle.register(p.X, p.Z, np.eye(4), FX=p.FX, FZ=p.FZ, **dict(kw, max_iters=iters))
+        total += time.perf_counter() - t0
+        pairs += info["pairs_total"]
+    value = pairs / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config,
+            "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(), "value": value, "unit": UNIT,
+                             "sample": f"each step: first {iters} iterations of the FP64 oracle's registration of "
+                                       f"the full street-20k pair"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cvo", choices=["cvo", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import paper_2012_03683_gb300 as cvo
+
+    dist, world, rank, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p, kw, config = workload()
+    config["parallelism"] = f"replicas x{world}" if world > 1 else "single pair"
+    X = torch.tensor(p.X, device=dev)
+    Z = torch.tensor(p.Z, device=dev)
+    FX = torch.tensor(p.FX, device=dev)
+    FZ = torch.tensor(p.FZ, device=dev)
+    h = cvo.CVO(**kw)
+    cvo.cvo_set_timing(h.h, True)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    T0 = np.eye(4)
+
+    for _ in range(max(args.warmup, 3)):
+        h.register(X, Z, T0, FX, FZ)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs -------------------------------
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = cvo.cvo_kernel_launches()
+    step_ms, pairs, cands, sweep_ms, sweep_n, iters = [], 0, 0, 0.0, 0, []
+    T_last = None
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        T_last, info = h.register(X, Z, T0, FX, FZ)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        pairs += info["pairs"]
+        cands += info["candidates"]
+        iters.append(info["iters"])
+        ms, n = cvo.cvo_sweep_time(h.h)
+        sweep_ms += ms * n
+        sweep_n += n
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = cvo.cvo_kernel_launches() - launches0
+    clocks = sampler.stop()
+    total_ms = float(sum(step_ms))
+    total_ms_max = max_over_ranks(dist, world, total_ms, dev)
+    pairs_all = sum_over_ranks(dist, world, float(pairs), dev)
+    value = pairs_all / (total_ms_max * 1e-3)
+    regs_per_s = world * args.steps / (total_ms_max * 1e-3)
+
+    # ---- end to end: pinned host buffers through the C ABI -----------------
+    Xh, Zh = torch.tensor(p.X).pin_memory(), torch.tensor(p.Z).pin_memory()
+    FXh, FZh = torch.tensor(p.FX).pin_memory(), torch.tensor(p.FZ).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in (Xh, Zh, FXh, FZh))
+    import ctypes
+    d2h = 16 * 8 + ctypes.sizeof(cvo.Info)
+    h.register(Xh, Zh, T0, FXh, FZh)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e2e_ms, e2e_pairs = 0.0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info = h.register(Xh, Zh, T0, FXh, FZh)
+        torch.cuda.synchronize()
+        e2e_ms += 1e3 * (time.perf_counter() - t0)
+        e2e_pairs += info["pairs"]
+    e2e_ms = max_over_ranks(dist, world, e2e_ms, dev)
+    e2e_pairs = sum_over_ranks(dist, world, float(e2e_pairs), dev)
+    h.close()
+
+    if rank != 0:
+        return
+    peaks, peak_src = load_peaks()
+    fpp = flops_per_pair(kw["blocks"])
+    achieved = pairs * fpp / (sweep_ms * 1e-3) / 1e12 if sweep_ms > 0 else None
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    traffic = profile_traffic(os.path.join(ROOT, "paper_2012_03683_gb300", "csrc", "cvo_sweep.cu"))
+    dT = np.linalg.inv(T_last) @ p.T_true
+    pose_err = {"rot_rad": float(math.acos(max(-1.0, min(1.0, (np.trace(dT[:3, :3]) - 1.0) / 2.0)))),
+                "trans_m": float(np.linalg.norm(dT[:3, 3]))}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+        "registered_pairs_per_s": regs_per_s,
+        "pairs_per_registration": pairs / args.steps, "candidates_per_registration": cands / args.steps,
+        "iterations": iters,
+        "e2e": {"value": e2e_pairs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": traffic, "kernel": "k_sweep (fused neighbour sweep)",
+                     "flops_per_pair": fpp, "sweep_ms_avg": sweep_ms / max(sweep_n, 1), "sweep_launches": sweep_n,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz "
+                                    f"(sm_max_mhz {peak_src})"},
+        "clocks": clocks,
+        "final_pose_err_vs_truth": pose_err,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, kw)
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

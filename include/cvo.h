@@ -1,0 +1,192 @@
+/*
+ * cvo.h -- C ABI of the GB300 (sm_103a) library for the RKHS point-cloud
+ * registration of "A New Framework for Registration of Semantic Point Clouds
+ * from Stereo and RGB-D Cameras" (arXiv:2012.03683).
+ *
+ * Two clouds X = {x_i} (N points) and Z = {z_j} (M points) with per-point
+ * feature vectors are aligned by maximising the RKHS inner product of
+ * Problem 1 (Sec. III, Eq. max) over SE(3):
+ *
+ *   F(T) = sum_{i,j} k(x_i, T z_j) * c_ij                    Eq. (double_sum)
+ *   k(x, y) = sigma^2 exp(-|x - y|^2 / (2 l^2))              Eq. (k)
+ *   c_ij = prod_b k_b(u_bi, v_bj)                            Eq. (tensor_product)
+ *     k_b = sigma_b^2 exp(-|u - v|^2 / (2 l_b^2))  (CVO_FEAT_SE,  Eq. newscalar)
+ *     k_b = <u, v>                                 (CVO_FEAT_DOT, Eq. scalar)
+ *
+ * The pose T (row-major 4x4, double) maps Z into X's frame, y_j = R z_j + t;
+ * it is the inverse of the h of Problem 1.  A pair enters the sum when
+ * |x_i - y_j| <= cutoff_mult * l (inclusive; the paper calls the sum sparse,
+ * Sec. III-B, but gives no threshold) or, with cutoff_mult <= 0, always.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: a cvo_status.  On an error the thread-local message of
+ *    cvo_last_error() says what went wrong; outputs are then unspecified.
+ *  - Clouds: cvo_cloud.xyz is N x 3 float32, row major (x, y, z per point).
+ *    cvo_cloud.feat is N x D row major, D = sum of the handle's block dims,
+ *    blocks concatenated in the order of cvo_params.blocks, stored as float32
+ *    or bfloat16 (cvo_cloud.feat_dtype); NULL when D == 0.  With on_device
+ *    = 1 both pointers are device pointers valid on the handle's stream, and
+ *    with on_device = 0 host pointers (the library copies them).  The caller
+ *    owns all input and output buffers; the library keeps no pointer to them
+ *    after the call returns.
+ *  - Empty clouds (N = 0 or M = 0) are not an error: F = 0, gradient 0,
+ *    indicator 0, and a registration returns T_init with status CVO_OK.
+ *  - T: the last row must be (0, 0, 0, 1) and R orthonormal within 1e-6,
+ *    otherwise CVO_ERR_INVALID_ARG.  Non-finite coordinates or features give
+ *    CVO_ERR_INVALID_ARG.
+ *  - Every call is synchronous: it returns after the results are on the host.
+ *  - A handle is not thread safe; use one handle per host thread.  The handle
+ *    owns its device scratch (grids, sorted copies of the clouds, partial
+ *    sums), allocated with cudaMalloc on first use and grown on demand.
+ */
+#ifndef CVO_H
+#define CVO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CVO_OK = 0,
+    CVO_NOT_CONVERGED = 1,     /* registration hit max_iters (not an error) */
+    CVO_ERR_INVALID_ARG = -1,
+    CVO_ERR_CUDA = -2,
+    CVO_ERR_OOM = -3,
+    CVO_ERR_TIMEOUT = -4
+} cvo_status;
+
+typedef enum {
+    CVO_FEAT_SE = 0,   /* sigma_b^2 exp(-|u - v|^2 / (2 scale^2)), Eq. (newscalar) */
+    CVO_FEAT_DOT = 1   /* <u, v>, Eq. (scalar); scale and sigma unused */
+} cvo_feat_kind;
+
+typedef enum { CVO_F32 = 0, CVO_BF16 = 1 } cvo_dtype;
+
+#define CVO_MAX_BLOCKS 4
+#define CVO_MAX_FEAT_DIM 64
+#define CVO_TRACE_STRIDE 22
+
+typedef struct {
+    int dim;        /* entries of this block in each feature row (>= 1) */
+    int kind;       /* cvo_feat_kind */
+    double scale;   /* l_b of a CVO_FEAT_SE block (> 0) */
+    double sigma;   /* sigma_b of a CVO_FEAT_SE block */
+} cvo_feat_block;
+
+typedef struct {
+    const float* xyz;  /* n x 3 float32 */
+    int n;             /* number of points (>= 0) */
+    const void* feat;  /* n x D, float32 or bfloat16 (see feat_dtype); NULL if D == 0 */
+    int feat_dtype;    /* cvo_dtype */
+    int on_device;     /* 1: device pointers, 0: host pointers */
+} cvo_cloud;
+
+typedef struct {
+    double ell;            /* geometric lengthscale l of Eq. (k) (> 0); the first l of a registration */
+    double ell_min;        /* annealing floor (0 < ell_min <= ell) */
+    double sigma;          /* sigma of Eq. (k) */
+    double cutoff_mult;    /* r_c = cutoff_mult * l; <= 0 means every pair (dense) */
+    int n_blocks;          /* 0..CVO_MAX_BLOCKS feature blocks; total dim <= CVO_MAX_FEAT_DIM */
+    cvo_feat_block blocks[CVO_MAX_BLOCKS];
+    int max_iters;         /* iteration cap of a registration (>= 0) */
+    int anneal;            /* 1: lengthscale annealing of Sec. IV */
+    double decay;          /* l <- max(decay * l, ell_min) when the indicator stabilises (0.98: 2 %) */
+    double indicator_tol;  /* "stabilised": |i_k - i_ref| < indicator_tol * |i_ref| at the same l */
+    double step_tol_rot;   /* converged when |t omega| < step_tol_rot ... */
+    double step_tol_trans; /* ... and |t v| < step_tol_trans, with l at its floor */
+    double max_step_rot;   /* clamp of |t omega| per iteration (rad) */
+    double max_step_trans; /* clamp of |t v| per iteration (m); <= 0: 0.5 * current l */
+} cvo_params;
+
+typedef struct {
+    int iters;              /* iterations run */
+    int status;             /* CVO_OK (converged) or CVO_NOT_CONVERGED */
+    double ell_final;       /* lengthscale of the last iteration */
+    double F;               /* F at the last iteration's pose (before its step) */
+    double i_theta;         /* Eq. (indicator_actual) at that pose: F / sqrt(N M) */
+    double last_step_rot;   /* |t omega| of the last step */
+    double last_step_trans; /* |t v| of the last step */
+    long long pairs;        /* pairs inside the cutoff, summed over iterations */
+    long long candidates;   /* point pairs the sweep examined (>= pairs) */
+} cvo_info;
+
+typedef struct {
+    double F;          /* Eq. (double_sum) */
+    double grad[6];    /* (omega; v): d/dxi F(exp(xi^) T) at xi = 0 */
+    double hess[36];   /* row-major Hessian of xi -> F(exp(xi^) T) at 0 (symmetric) */
+    double i_theta;    /* F / sqrt(N M), Eq. (indicator_actual) */
+    long long pairs;   /* pairs inside the cutoff */
+    long long candidates;
+} cvo_eval;
+
+typedef struct cvo_handle_s* cvo_handle;
+
+/* Creates a handle bound to a CUDA stream (a cudaStream_t; NULL = the legacy
+ * default stream) on the current device.  Validates *params (copied).
+ * Allocates nothing on the device until the first computation. */
+cvo_status cvo_create(const cvo_params* params, void* cuda_stream, cvo_handle* out);
+
+/* Releases the handle and its device scratch.  NULL is accepted. */
+cvo_status cvo_destroy(cvo_handle h);
+
+/* Replaces the handle's parameters (validated, copied). */
+cvo_status cvo_set_params(cvo_handle h, const cvo_params* params);
+
+/* F(T) of Eq. (double_sum) at lengthscale params.ell. */
+cvo_status cvo_inner_product(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], double* F);
+
+/* Gradient (omega; v) of xi -> F(exp(xi^) T) at xi = 0 (left perturbation),
+ * the ascent direction of the Lie-group gradient method the paper cites
+ * (Sec. I).  F may be NULL. */
+cvo_status cvo_gradient(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], double grad[6],
+                        double* F);
+
+/* The alignment indicator of Eq. (indicator_actual), i_theta = F / sqrt(N M),
+ * at pose T and lengthscale params.ell. */
+cvo_status cvo_metric(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], double* i_theta);
+
+/* F, gradient, Hessian, indicator and pair counts in one sweep. */
+cvo_status cvo_evaluate(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], cvo_eval* out);
+
+/* Registration (Problem 1): gradient ascent on SE(3) from T_init, one
+ * line-Newton step along the gradient per iteration (t = |g|^2 / -F'' when
+ * F'' < 0, else 1e-3 / |g|, clamped by max_step_rot / max_step_trans),
+ * T <- exp(t g^) T, with the lengthscale annealing of Sec. IV when
+ * params.anneal = 1.  T_out receives the final pose; info (nullable) the
+ * summary.  Returns CVO_OK when converged, CVO_NOT_CONVERGED at max_iters. */
+cvo_status cvo_register_pair(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T_init[16],
+                             double T_out[16], cvo_info* info);
+
+/* Registers npairs independent pairs (X[k], Z[k]) from T_init[16k..16k+15];
+ * T_out and infos (nullable) are indexed the same way.  Returns the worst
+ * status (an error, else CVO_NOT_CONVERGED if any pair hit max_iters). */
+cvo_status cvo_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, const cvo_cloud* Z,
+                              const double* T_init, double* T_out, cvo_info* infos);
+
+/* Copies the per-iteration trace of the handle's last registration into out
+ * (capacity cap iterations, CVO_TRACE_STRIDE doubles each: l, F, i_theta,
+ * |g|, F'' along g, t, |t omega|, |t v|, decayed (0/1), pairs, then the first
+ * three rows of the pose the iteration started from) and returns the number
+ * of iterations, or a negative cvo_status. */
+int cvo_get_trace(cvo_handle h, double* out, int cap);
+
+/* Average device time (ms) of the sweep kernel over the handle's last
+ * registration, measured with CUDA events around each sweep launch when
+ * timing is on (cvo_set_timing), and the number of sweep launches timed. */
+cvo_status cvo_set_timing(cvo_handle h, int on);
+cvo_status cvo_sweep_time(cvo_handle h, double* avg_ms, int* launches);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* cvo_last_error(void);
+
+/* Library version string. */
+const char* cvo_version(void);
+
+/* CUDA kernels this library has launched in the calling process (all
+ * handles, all threads), for launch accounting by benchmarks. */
+long long cvo_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CVO_H */

@@ -32,7 +32,7 @@ _lock = threading.Lock()
 _lib = None
 
 MAX_BLOCKS = 4
-TRACE_STRIDE = 10
+TRACE_STRIDE = 22
 KIND = {"se": 0, "dot": 1}
 
 
@@ -129,6 +129,7 @@ def evaluate(X, Z, T, *, FX=None, FZ=None, blocks=(), ell, cutoff_mult=0.0, sigm
              direction=None, nthreads=0):
     """Brute-force F, its se(3) gradient (omega, v) and, when ``direction`` is
     given, the second derivative of t -> F(exp(t direction^) T) at t = 0.
+    ``gscale`` is the sum of the norms of the gradient's per-pair terms.
     Inputs are upcast exactly to float64.  Returns a dict."""
     lib = _load()
     keep = []
@@ -136,7 +137,7 @@ def evaluate(X, Z, T, *, FX=None, FZ=None, blocks=(), ell, cutoff_mult=0.0, sigm
     cz = _cloud(Z, FZ, keep)
     k = _kernel(list(blocks), ell, cutoff_mult, sigma)
     Tm = _f64(T).reshape(4, 4)
-    out = np.zeros(8)
+    out = np.zeros(9)
     npairs = ctypes.c_longlong(0)
     d = None
     if direction is not None:
@@ -146,7 +147,7 @@ def evaluate(X, Z, T, *, FX=None, FZ=None, blocks=(), ell, cutoff_mult=0.0, sigm
                       out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(npairs), int(nthreads))
     if rc != 0:
         raise ValueError("orc_eval: invalid argument")
-    return dict(F=out[0], g=out[1:7].copy(), Fpp=out[7], npairs=int(npairs.value))
+    return dict(F=out[0], g=out[1:7].copy(), Fpp=out[7], gscale=out[8], npairs=int(npairs.value))
 
 
 def indicator(X, Z, T, **kw):

@@ -116,11 +116,13 @@ static double dot3(const double a[3], const double b[3])
  *   out[1:4] dF/domega              left perturbation
  *   out[4:7] dF/dv
  *   out[7]   d^2F along dir (0 if dir == NULL)
+ *   out[8]   sum over pairs of |w (y x x)| + |w (x - y)|, divided by l^2: the
+ *            scale of the gradient's terms (for rounding-error bounds)
  * npairs receives the number of pairs inside the cutoff.
  * Returns 0, or -1 on an invalid argument.
  */
 int orc_eval(const orc_kernel* k, const orc_cloud* X, const orc_cloud* Z, const double T[16],
-             const double* dir, double out[8], long long* npairs, int nthreads)
+             const double* dir, double out[9], long long* npairs, int nthreads)
 {
     if (!k || !X || !Z || !T || !out || k->ell <= 0.0 || k->n_blocks < 0 || k->n_blocks > ORC_MAX_BLOCKS)
         return -1;
@@ -129,7 +131,7 @@ int orc_eval(const orc_kernel* k, const orc_cloud* X, const orc_cloud* Z, const 
     const double l4 = l2 * l2;
     const double rc2 = k->cutoff_mult > 0.0 ? (k->cutoff_mult * k->ell) * (k->cutoff_mult * k->ell) : -1.0;
     const double s2 = k->sigma * k->sigma;
-    double F = 0.0, gw[3] = {0, 0, 0}, gv[3] = {0, 0, 0}, Fpp = 0.0;
+    double F = 0.0, gw[3] = {0, 0, 0}, gv[3] = {0, 0, 0}, Fpp = 0.0, gab = 0.0;
     long long cnt = 0;
     double om[3] = {0, 0, 0}, vv[3] = {0, 0, 0};
     if (dir) {
@@ -143,7 +145,7 @@ int orc_eval(const orc_kernel* k, const orc_cloud* X, const orc_cloud* Z, const 
 #endif
     /* Per-point partial sums, then one ordered sum: the result does not depend
        on the thread count or schedule. */
-    double* part = (double*)calloc((size_t)(X->n > 0 ? X->n : 1) * 8, sizeof(double));
+    double* part = (double*)calloc((size_t)(X->n > 0 ? X->n : 1) * 9, sizeof(double));
     long long* pcnt = (long long*)calloc((size_t)(X->n > 0 ? X->n : 1), sizeof(long long));
     if (!part || !pcnt) {
         free(part);
@@ -153,7 +155,7 @@ int orc_eval(const orc_kernel* k, const orc_cloud* X, const orc_cloud* Z, const 
 #pragma omp parallel for schedule(dynamic, 16)
     for (int i = 0; i < X->n; ++i) {
         const double* x = X->xyz + 3 * (size_t)i;
-        double Fi = 0.0, gwi[3] = {0, 0, 0}, gvi[3] = {0, 0, 0}, Fppi = 0.0;
+        double Fi = 0.0, gwi[3] = {0, 0, 0}, gvi[3] = {0, 0, 0}, Fppi = 0.0, gabi = 0.0;
         long long ci = 0;
         for (int j = 0; j < Z->n; ++j) {
             const double* z = Z->xyz + 3 * (size_t)j;
@@ -173,6 +175,7 @@ int orc_eval(const orc_kernel* k, const orc_cloud* X, const orc_cloud* Z, const 
                 gwi[r] += w * yx[r] / l2;
                 gvi[r] += -w * e[r] / l2;
             }
+            gabi += fabs(w) * (sqrt(dot3(yx, yx)) + sqrt(d2)) / l2;
             if (dir) {
                 double d[3], od[3];
                 cross3(om, y, d);
@@ -182,19 +185,21 @@ int orc_eval(const orc_kernel* k, const orc_cloud* X, const orc_cloud* Z, const 
                 Fppi += w * (ed * ed / l4 - (dot3(d, d) + dot3(e, od)) / l2);
             }
         }
-        double* p = part + 8 * (size_t)i;
+        double* p = part + 9 * (size_t)i;
         p[0] = Fi;
         p[1] = gwi[0]; p[2] = gwi[1]; p[3] = gwi[2];
         p[4] = gvi[0]; p[5] = gvi[1]; p[6] = gvi[2];
         p[7] = Fppi;
+        p[8] = gabi;
         pcnt[i] = ci;
     }
     for (int i = 0; i < X->n; ++i) {
-        const double* p = part + 8 * (size_t)i;
+        const double* p = part + 9 * (size_t)i;
         F += p[0];
         gw[0] += p[1]; gw[1] += p[2]; gw[2] += p[3];
         gv[0] += p[4]; gv[1] += p[5]; gv[2] += p[6];
         Fpp += p[7];
+        gab += p[8];
         cnt += pcnt[i];
     }
     free(part);
@@ -203,6 +208,7 @@ int orc_eval(const orc_kernel* k, const orc_cloud* X, const orc_cloud* Z, const 
     out[1] = gw[0]; out[2] = gw[1]; out[3] = gw[2];
     out[4] = gv[0]; out[5] = gv[1]; out[6] = gv[2];
     out[7] = Fpp;
+    out[8] = gab;
     if (npairs) *npairs = cnt;
     return 0;
 }
@@ -362,7 +368,7 @@ typedef struct {
     long long pairs_total;
 } orc_info;
 
-#define ORC_TRACE_STRIDE 10 /* ell, F, i_theta, |g|, Fpp, t, |t omega|, |t v|, decayed, pairs */
+#define ORC_TRACE_STRIDE 22 /* ell, F, i_theta, |g|, Fpp, t, |t omega|, |t v|, decayed, pairs, rows 0-2 of T_k */
 
 /*
  * Gradient ascent on SE(3), one line-Newton step along the gradient per
@@ -381,7 +387,8 @@ typedef struct {
  *      the reference is cleared; otherwise i_ref = i_k.
  * replay (optional, max_iters entries): when given, replay[k] in {0,1} forces
  * the decay decision of step 6 instead of the indicator test.
- * trace (optional, max_iters x ORC_TRACE_STRIDE doubles) records each iteration.
+ * trace (optional, max_iters x ORC_TRACE_STRIDE doubles) records each iteration,
+ * including the first three rows of the pose T_k the iteration started from.
  */
 int orc_register(const orc_kernel* kin, const orc_reg* r, const orc_cloud* X, const orc_cloud* Z,
                  const double T_init[16], double T_out[16], orc_info* info, double* trace,
@@ -401,7 +408,9 @@ int orc_register(const orc_kernel* kin, const orc_reg* r, const orc_cloud* X, co
     int it;
     for (it = 0; it < r->max_iters; ++it) {
         k.ell = ell;
-        double out[8];
+        double out[9];
+        double T_k[16];
+        memcpy(T_k, T, sizeof(T_k));
         long long np = 0;
         orc_eval(&k, X, Z, T, NULL, out, &np, nthreads);
         double g[6];
@@ -455,6 +464,7 @@ int orc_register(const orc_kernel* kin, const orc_reg* r, const orc_cloud* X, co
             double* tr = trace + (size_t)ORC_TRACE_STRIDE * it;
             tr[0] = k.ell; tr[1] = F; tr[2] = ith; tr[3] = sqrt(gn2); tr[4] = Fpp;
             tr[5] = t; tr[6] = srot; tr[7] = strans; tr[8] = decayed; tr[9] = (double)np;
+            for (int q = 0; q < 12; ++q) tr[10 + q] = T_k[q];
         }
         if (converged) {
             inf.status = 0;

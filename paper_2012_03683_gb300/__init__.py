@@ -1,0 +1,392 @@
+"""GB300 (sm_103a) RKHS point-cloud registration (arXiv:2012.03683).
+
+A thin ctypes binding over ``libcvo.so`` (include/cvo.h).  It only marshals
+arguments: every step of the computation runs in the library's CUDA kernels.
+PyTorch supplies device memory and the current CUDA stream.  There is no CPU
+fallback: without the built library (``python -m
+paper_2012_03683_gb300.build``) every call raises.
+
+Functions named like the C entry points (``cvo_create``, ``cvo_inner_product``,
+``cvo_gradient``, ``cvo_metric``, ``cvo_evaluate``, ``cvo_register_pair``,
+``cvo_register_batch``, ...) take the same arguments in Python form; the
+``CVO`` class wraps a handle.
+
+Clouds are (N, 3) float32 arrays: torch CUDA tensors are passed as device
+pointers, numpy arrays and CPU tensors as host pointers (the library copies
+them).  Features are (N, D) float32 or bfloat16 (torch.bfloat16) arrays, the
+blocks concatenated in the order given.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["CVO", "cvo_create", "cvo_destroy", "cvo_set_params", "cvo_inner_product", "cvo_gradient", "cvo_metric",
+           "cvo_evaluate", "cvo_register_pair", "cvo_register_batch", "cvo_get_trace", "cvo_set_timing",
+           "cvo_sweep_time", "cvo_last_error", "cvo_version", "cvo_kernel_launches", "load_library", "Status",
+           "CvoError"]
+
+MAX_BLOCKS = 4
+TRACE_STRIDE = 22
+
+
+class Status:
+    OK = 0
+    NOT_CONVERGED = 1
+    ERR_INVALID_ARG = -1
+    ERR_CUDA = -2
+    ERR_OOM = -3
+    ERR_TIMEOUT = -4
+
+
+class CvoError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"cvo status {status}: {msg}")
+        self.status = status
+
+
+class FeatBlock(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("kind", ctypes.c_int), ("scale", ctypes.c_double), ("sigma", ctypes.c_double)]
+
+
+class Cloud(ctypes.Structure):
+    _fields_ = [("xyz", ctypes.c_void_p), ("n", ctypes.c_int), ("feat", ctypes.c_void_p), ("feat_dtype", ctypes.c_int),
+                ("on_device", ctypes.c_int)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("ell", ctypes.c_double), ("ell_min", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("cutoff_mult", ctypes.c_double), ("n_blocks", ctypes.c_int), ("blocks", FeatBlock * MAX_BLOCKS),
+                ("max_iters", ctypes.c_int), ("anneal", ctypes.c_int), ("decay", ctypes.c_double),
+                ("indicator_tol", ctypes.c_double), ("step_tol_rot", ctypes.c_double),
+                ("step_tol_trans", ctypes.c_double), ("max_step_rot", ctypes.c_double),
+                ("max_step_trans", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("ell_final", ctypes.c_double),
+                ("F", ctypes.c_double), ("i_theta", ctypes.c_double), ("last_step_rot", ctypes.c_double),
+                ("last_step_trans", ctypes.c_double), ("pairs", ctypes.c_longlong),
+                ("candidates", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Eval(ctypes.Structure):
+    _fields_ = [("F", ctypes.c_double), ("grad", ctypes.c_double * 6), ("hess", ctypes.c_double * 36),
+                ("i_theta", ctypes.c_double), ("pairs", ctypes.c_longlong), ("candidates", ctypes.c_longlong)]
+
+
+_lib = None
+
+
+def load_library(build_if_missing: bool = True):
+    """Loads libcvo.so (building it first when missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libcvo.so is not built ({path}); run python -m paper_2012_03683_gb300.build")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    lib.cvo_create.argtypes = [P(Params), vp, P(vp)]
+    lib.cvo_destroy.argtypes = [vp]
+    lib.cvo_set_params.argtypes = [vp, P(Params)]
+    for name in ("cvo_inner_product", "cvo_metric"):
+        getattr(lib, name).argtypes = [vp, P(Cloud), P(Cloud), vp, P(ctypes.c_double)]
+    lib.cvo_gradient.argtypes = [vp, P(Cloud), P(Cloud), vp, vp, P(ctypes.c_double)]
+    lib.cvo_evaluate.argtypes = [vp, P(Cloud), P(Cloud), vp, P(Eval)]
+    lib.cvo_register_pair.argtypes = [vp, P(Cloud), P(Cloud), vp, vp, P(Info)]
+    lib.cvo_register_batch.argtypes = [vp, ctypes.c_int, P(Cloud), P(Cloud), vp, vp, P(Info)]
+    lib.cvo_get_trace.argtypes = [vp, vp, ctypes.c_int]
+    lib.cvo_set_timing.argtypes = [vp, ctypes.c_int]
+    lib.cvo_sweep_time.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int)]
+    for name in ("cvo_create", "cvo_destroy", "cvo_set_params", "cvo_inner_product", "cvo_metric", "cvo_gradient",
+                 "cvo_evaluate", "cvo_register_pair", "cvo_register_batch", "cvo_get_trace", "cvo_set_timing",
+                 "cvo_sweep_time"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.cvo_last_error.restype = ctypes.c_char_p
+    lib.cvo_last_error.argtypes = []
+    lib.cvo_version.restype = ctypes.c_char_p
+    lib.cvo_version.argtypes = []
+    lib.cvo_kernel_launches.restype = ctypes.c_longlong
+    lib.cvo_kernel_launches.argtypes = []
+    _lib = lib
+    return lib
+
+
+def cvo_kernel_launches() -> int:
+    return int(load_library().cvo_kernel_launches())
+
+
+def cvo_last_error() -> str:
+    return load_library().cvo_last_error().decode()
+
+
+def cvo_version() -> str:
+    return load_library().cvo_version().decode()
+
+
+def _check(rc):
+    if rc < 0:
+        raise CvoError(rc, cvo_last_error())
+    return rc
+
+
+# ---- argument marshalling ----------------------------------------------------
+
+def _torch():
+    try:
+        import torch
+        return torch
+    except Exception:  # pragma: no cover
+        return None
+
+
+def _current_stream():
+    torch = _torch()
+    if torch is not None and torch.cuda.is_available() and torch.cuda.is_initialized():
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def make_params(blocks=(), ell=0.1, ell_min=None, sigma=1.0, cutoff_mult=3.0, max_iters=100, anneal=False, decay=0.98,
+                indicator_tol=1e-3, step_tol_rot=1e-5, step_tol_trans=1e-5, max_step_rot=0.1,
+                max_step_trans=0.0) -> Params:
+    """blocks: sequence of (kind, dim, scale, sigma), kind "se" (Eq. newscalar) or "dot" (Eq. scalar)."""
+    p = Params()
+    p.ell = float(ell)
+    p.ell_min = float(ell if ell_min is None else ell_min)
+    p.sigma = float(sigma)
+    p.cutoff_mult = float(cutoff_mult)
+    blocks = list(blocks)
+    if len(blocks) > MAX_BLOCKS:
+        raise ValueError("at most 4 feature blocks")
+    p.n_blocks = len(blocks)
+    for b, (kind, dim, scale, sig) in enumerate(blocks):
+        p.blocks[b].dim = int(dim)
+        p.blocks[b].kind = {"se": 0, "dot": 1}[kind]
+        p.blocks[b].scale = float(scale)
+        p.blocks[b].sigma = float(sig)
+    p.max_iters = int(max_iters)
+    p.anneal = int(bool(anneal))
+    p.decay = float(decay)
+    p.indicator_tol = float(indicator_tol)
+    p.step_tol_rot = float(step_tol_rot)
+    p.step_tol_trans = float(step_tol_trans)
+    p.max_step_rot = float(max_step_rot)
+    p.max_step_trans = float(max_step_trans)
+    return p
+
+
+def _as_cloud(xyz, feat, keep):
+    """Builds a Cloud from numpy arrays or torch tensors; keep holds references."""
+    torch = _torch()
+    c = Cloud()
+    if torch is not None and isinstance(xyz, torch.Tensor):
+        t = xyz.detach()
+        if t.dtype != torch.float32 or t.dim() != 2 or t.shape[1] != 3:
+            raise ValueError("xyz must be an (N, 3) float32 tensor")
+        t = t.contiguous()
+        keep.append(t)
+        c.xyz = t.data_ptr() if t.numel() else None
+        c.n = t.shape[0]
+        c.on_device = 1 if t.is_cuda else 0
+        if feat is not None:
+            f = feat.detach()
+            if f.is_cuda != t.is_cuda:
+                raise ValueError("xyz and features must live on the same device")
+            if f.dtype == torch.bfloat16:
+                c.feat_dtype = 1
+            elif f.dtype == torch.float32:
+                c.feat_dtype = 0
+            else:
+                raise ValueError("features must be float32 or bfloat16")
+            f = f.contiguous()
+            keep.append(f)
+            c.feat = f.data_ptr() if f.numel() else None
+        return c
+    a = np.ascontiguousarray(np.asarray(xyz, dtype=np.float32).reshape(-1, 3))
+    keep.append(a)
+    c.xyz = a.ctypes.data if a.size else None
+    c.n = a.shape[0]
+    c.on_device = 0
+    if feat is not None:
+        f = np.asarray(feat)
+        if f.dtype == np.uint16:  # bfloat16 bit patterns
+            c.feat_dtype = 1
+        else:
+            f = f.astype(np.float32, copy=False)
+            c.feat_dtype = 0
+        f = np.ascontiguousarray(f)
+        keep.append(f)
+        c.feat = f.ctypes.data if f.size else None
+    return c
+
+
+def _pose(T):
+    a = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(4, 4))
+    return a
+
+
+# ---- the C entry points --------------------------------------------------------
+
+def cvo_create(params: Params, stream=None):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    s = _current_stream() if stream is None else ctypes.c_void_p(int(stream))
+    _check(lib.cvo_create(ctypes.byref(params), s, ctypes.byref(h)))
+    return h
+
+
+def cvo_destroy(h):
+    return _check(load_library().cvo_destroy(h))
+
+
+def cvo_set_params(h, params: Params):
+    return _check(load_library().cvo_set_params(h, ctypes.byref(params)))
+
+
+def _clouds(X, Z, FX, FZ):
+    keep = []
+    return _as_cloud(X, FX, keep), _as_cloud(Z, FZ, keep), keep
+
+
+def cvo_evaluate(h, X, Z, T, FX=None, FZ=None) -> dict:
+    cx, cz, keep = _clouds(X, Z, FX, FZ)
+    Tm = _pose(T)
+    e = Eval()
+    _check(load_library().cvo_evaluate(h, ctypes.byref(cx), ctypes.byref(cz), Tm.ctypes.data, ctypes.byref(e)))
+    return dict(F=e.F, grad=np.array(e.grad[:]), hess=np.array(e.hess[:]).reshape(6, 6), i_theta=e.i_theta,
+                pairs=int(e.pairs), candidates=int(e.candidates))
+
+
+def cvo_inner_product(h, X, Z, T, FX=None, FZ=None) -> float:
+    cx, cz, keep = _clouds(X, Z, FX, FZ)
+    Tm = _pose(T)
+    out = ctypes.c_double()
+    _check(load_library().cvo_inner_product(h, ctypes.byref(cx), ctypes.byref(cz), Tm.ctypes.data, ctypes.byref(out)))
+    return out.value
+
+
+def cvo_gradient(h, X, Z, T, FX=None, FZ=None):
+    cx, cz, keep = _clouds(X, Z, FX, FZ)
+    Tm = _pose(T)
+    g = np.zeros(6)
+    F = ctypes.c_double()
+    _check(load_library().cvo_gradient(h, ctypes.byref(cx), ctypes.byref(cz), Tm.ctypes.data, g.ctypes.data,
+                                       ctypes.byref(F)))
+    return g, F.value
+
+
+def cvo_metric(h, X, Z, T, FX=None, FZ=None) -> float:
+    cx, cz, keep = _clouds(X, Z, FX, FZ)
+    Tm = _pose(T)
+    out = ctypes.c_double()
+    _check(load_library().cvo_metric(h, ctypes.byref(cx), ctypes.byref(cz), Tm.ctypes.data, ctypes.byref(out)))
+    return out.value
+
+
+def cvo_register_pair(h, X, Z, T_init, FX=None, FZ=None):
+    cx, cz, keep = _clouds(X, Z, FX, FZ)
+    T0 = _pose(T_init)
+    Tout = np.zeros((4, 4))
+    info = Info()
+    rc = _check(load_library().cvo_register_pair(h, ctypes.byref(cx), ctypes.byref(cz), T0.ctypes.data,
+                                                 Tout.ctypes.data, ctypes.byref(info)))
+    d = info.as_dict()
+    d["rc"] = rc
+    return Tout, d
+
+
+def cvo_register_batch(h, pairs):
+    """pairs: sequence of (X, Z, T_init, FX, FZ)."""
+    keep = []
+    n = len(pairs)
+    CX = (Cloud * max(n, 1))()
+    CZ = (Cloud * max(n, 1))()
+    T0 = np.zeros((max(n, 1), 4, 4))
+    for k, (X, Z, T, FX, FZ) in enumerate(pairs):
+        CX[k] = _as_cloud(X, FX, keep)
+        CZ[k] = _as_cloud(Z, FZ, keep)
+        T0[k] = _pose(T)
+    Tout = np.zeros_like(T0)
+    infos = (Info * max(n, 1))()
+    rc = _check(load_library().cvo_register_batch(h, n, CX, CZ, T0.ctypes.data, Tout.ctypes.data, infos))
+    return Tout[:n], [infos[k].as_dict() for k in range(n)], rc
+
+
+def cvo_get_trace(h, cap=100000) -> np.ndarray:
+    out = np.zeros((max(cap, 1), TRACE_STRIDE))
+    n = _check(load_library().cvo_get_trace(h, out.ctypes.data, cap))
+    return out[: min(n, cap)].copy()
+
+
+def cvo_set_timing(h, on=True):
+    return _check(load_library().cvo_set_timing(h, int(bool(on))))
+
+
+def cvo_sweep_time(h):
+    ms = ctypes.c_double()
+    n = ctypes.c_int()
+    _check(load_library().cvo_sweep_time(h, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+class CVO:
+    """A handle with fixed parameters (see make_params for the arguments)."""
+
+    def __init__(self, stream=None, **kw):
+        self.params = make_params(**kw)
+        self.h = cvo_create(self.params, stream)
+
+    def close(self):
+        if self.h is not None:
+            cvo_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_params(self, **kw):
+        self.params = make_params(**kw)
+        cvo_set_params(self.h, self.params)
+
+    def evaluate(self, X, Z, T, FX=None, FZ=None):
+        return cvo_evaluate(self.h, X, Z, T, FX, FZ)
+
+    def inner_product(self, X, Z, T, FX=None, FZ=None):
+        return cvo_inner_product(self.h, X, Z, T, FX, FZ)
+
+    def gradient(self, X, Z, T, FX=None, FZ=None):
+        return cvo_gradient(self.h, X, Z, T, FX, FZ)
+
+    def metric(self, X, Z, T, FX=None, FZ=None):
+        return cvo_metric(self.h, X, Z, T, FX, FZ)
+
+    def register(self, X, Z, T_init=None, FX=None, FZ=None):
+        return cvo_register_pair(self.h, X, Z, np.eye(4) if T_init is None else T_init, FX, FZ)
+
+    def register_batch(self, pairs):
+        return cvo_register_batch(self.h, pairs)
+
+    def trace(self):
+        return cvo_get_trace(self.h)

@@ -1,0 +1,761 @@
+// C ABI of libcvo (declared in include/cvo.h): argument checking, device
+// scratch, the per-pair setup, and the drivers of evaluation and
+// registration.  Every step of the computation runs in this library's CUDA
+// kernels; the host only orders launches and copies results.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cvo.h"
+#include "cvo_internal.cuh"
+
+using namespace cvo;
+
+std::atomic<long long> cvo::g_launch_count{0};
+
+namespace {
+
+thread_local std::string g_err;
+
+cvo_status fail(cvo_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CVO_CUDA(call)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail(e_ == cudaErrorMemoryAllocation ? CVO_ERR_OOM : CVO_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                     \
+    } while (0)
+
+#define CVO_TRY(expr)                 \
+    do {                              \
+        cvo_status s_ = (expr);       \
+        if (s_ < 0) return s_;        \
+    } while (0)
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+cudaError_t ensure(DevBuf& b, size_t bytes)
+{
+    if (bytes <= b.cap && b.p) return cudaSuccess;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    const size_t nb = std::max<size_t>(bytes, 256);
+    cudaError_t e = cudaMalloc(&b.p, nb);
+    if (e == cudaSuccess) b.cap = nb;
+    return e;
+}
+
+void release(DevBuf& b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+struct LevelHost {
+    double h;
+    int nx, ny, nz;
+    float ox, oy, oz;
+    long long ncells;
+    int shift;
+    int ngroups;
+};
+
+constexpr long long kMaxCells = 1LL << 26;
+constexpr int kMiscWords = 64;   // bbox (12), bad flag (1), group totals (<= kMaxLevels)
+
+float decode_orderable(unsigned u)
+{
+    const unsigned b = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+    float f;
+    std::memcpy(&f, &b, 4);
+    return f;
+}
+
+}  // namespace
+
+struct cvo_handle_s {
+    cvo_params p{};
+    cudaStream_t s = nullptr;
+    int device = 0;
+    int num_sms = 152;
+    int timing = 0;
+    DevBuf stage_xyz[2], stage_feat[2];
+    DevBuf keys, vals, keys2, vals2, sort_tmp, flags, gidx;
+    DevBuf xrec, morton;
+    DevBuf zrec[kMaxLevels], cell_start[kMaxLevels], groups[kMaxLevels];
+    DevBuf misc, levels_dev, state, part_stats, part_cnt, trace;
+    IterState* h_state = nullptr;   // pinned mirror
+    unsigned* h_misc = nullptr;     // pinned
+    int last_iters = 0;
+    double sweep_ms = 0.0;
+    int sweep_n = 0;
+    std::vector<cudaEvent_t> evs;
+    // prepared pair
+    int n = 0, m = 0, nlevels = 0, dense = 0, rs = 1, rec_bf16 = 0, D = 0;
+    LevelHost lv[kMaxLevels];
+    double zc[3] = {0, 0, 0};
+    int sweep_blocks = 1;
+    FeatConst fc{};
+    double kappa = 1.0;
+};
+
+namespace {
+
+cvo_status check_params(const cvo_params* p)
+{
+    if (!p) return fail(CVO_ERR_INVALID_ARG, "params is NULL");
+    if (!(p->ell > 0.0) || !std::isfinite(p->ell)) return fail(CVO_ERR_INVALID_ARG, "ell must be > 0");
+    if (!(p->sigma > 0.0) || !std::isfinite(p->sigma)) return fail(CVO_ERR_INVALID_ARG, "sigma must be > 0");
+    if (!std::isfinite(p->cutoff_mult)) return fail(CVO_ERR_INVALID_ARG, "cutoff_mult must be finite");
+    if (p->n_blocks < 0 || p->n_blocks > CVO_MAX_BLOCKS)
+        return fail(CVO_ERR_INVALID_ARG, "n_blocks must be in [0, %d]", CVO_MAX_BLOCKS);
+    int D = 0;
+    for (int b = 0; b < p->n_blocks; ++b) {
+        const cvo_feat_block& fb = p->blocks[b];
+        if (fb.dim < 1) return fail(CVO_ERR_INVALID_ARG, "block %d: dim must be >= 1", b);
+        if (fb.kind != CVO_FEAT_SE && fb.kind != CVO_FEAT_DOT)
+            return fail(CVO_ERR_INVALID_ARG, "block %d: unknown kind %d", b, fb.kind);
+        if (fb.kind == CVO_FEAT_SE && (!(fb.scale > 0.0) || !std::isfinite(fb.scale) || !std::isfinite(fb.sigma)))
+            return fail(CVO_ERR_INVALID_ARG, "block %d: scale must be > 0 and sigma finite", b);
+        D += fb.dim;
+    }
+    if (D > CVO_MAX_FEAT_DIM) return fail(CVO_ERR_INVALID_ARG, "total feature dim %d > %d", D, CVO_MAX_FEAT_DIM);
+    if (p->max_iters < 0) return fail(CVO_ERR_INVALID_ARG, "max_iters must be >= 0");
+    if (p->anneal) {
+        if (!(p->ell_min > 0.0) || p->ell_min > p->ell)
+            return fail(CVO_ERR_INVALID_ARG, "annealing needs 0 < ell_min <= ell");
+        if (!(p->decay > 0.0) || p->decay > 1.0) return fail(CVO_ERR_INVALID_ARG, "decay must be in (0, 1]");
+        if (!(p->indicator_tol >= 0.0)) return fail(CVO_ERR_INVALID_ARG, "indicator_tol must be >= 0");
+    }
+    if (!(p->max_step_rot > 0.0)) return fail(CVO_ERR_INVALID_ARG, "max_step_rot must be > 0");
+    if (!(p->step_tol_rot >= 0.0) || !(p->step_tol_trans >= 0.0))
+        return fail(CVO_ERR_INVALID_ARG, "step tolerances must be >= 0");
+    if (!std::isfinite(p->max_step_trans)) return fail(CVO_ERR_INVALID_ARG, "max_step_trans must be finite");
+    return CVO_OK;
+}
+
+cvo_status check_pose(const double* T, const char* name)
+{
+    if (!T) return fail(CVO_ERR_INVALID_ARG, "%s is NULL", name);
+    for (int k = 0; k < 16; ++k)
+        if (!std::isfinite(T[k])) return fail(CVO_ERR_INVALID_ARG, "%s has a non-finite entry", name);
+    if (T[12] != 0.0 || T[13] != 0.0 || T[14] != 0.0 || T[15] != 1.0)
+        return fail(CVO_ERR_INVALID_ARG, "%s: last row must be (0, 0, 0, 1)", name);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double d = 0.0;
+            for (int k = 0; k < 3; ++k) d += T[4 * k + a] * T[4 * k + b];
+            if (std::fabs(d - (a == b ? 1.0 : 0.0)) > 1e-6)
+                return fail(CVO_ERR_INVALID_ARG, "%s: rotation is not orthonormal within 1e-6", name);
+        }
+    const double det = T[0] * (T[5] * T[10] - T[6] * T[9]) - T[1] * (T[4] * T[10] - T[6] * T[8]) +
+                       T[2] * (T[4] * T[9] - T[5] * T[8]);
+    if (det < 0.0) return fail(CVO_ERR_INVALID_ARG, "%s: rotation has determinant -1", name);
+    return CVO_OK;
+}
+
+int feat_dim(const cvo_params& p)
+{
+    int D = 0;
+    for (int b = 0; b < p.n_blocks; ++b) D += p.blocks[b].dim;
+    return D;
+}
+
+cvo_status check_cloud(const cvo_cloud* c, const char* name, int D)
+{
+    if (!c) return fail(CVO_ERR_INVALID_ARG, "%s is NULL", name);
+    if (c->n < 0) return fail(CVO_ERR_INVALID_ARG, "%s.n < 0", name);
+    if (c->n > 0 && !c->xyz) return fail(CVO_ERR_INVALID_ARG, "%s.xyz is NULL", name);
+    if (c->n > 0 && D > 0 && !c->feat) return fail(CVO_ERR_INVALID_ARG, "%s.feat is NULL but D = %d", name, D);
+    if (c->feat_dtype != CVO_F32 && c->feat_dtype != CVO_BF16)
+        return fail(CVO_ERR_INVALID_ARG, "%s.feat_dtype unknown", name);
+    if (c->on_device && c->n > 0) {
+        const void* ptrs[2] = {c->xyz, D > 0 ? c->feat : nullptr};
+        for (const void* ptr : ptrs) {
+            if (!ptr) continue;
+            cudaPointerAttributes at;
+            if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(CVO_ERR_INVALID_ARG, "%s: pointer is not known to CUDA", name);
+            }
+            if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+                return fail(CVO_ERR_INVALID_ARG, "%s: on_device = 1 but the pointer is not device memory", name);
+        }
+    }
+    return CVO_OK;
+}
+
+// Device copies (or the caller's device pointers) of one cloud.
+cvo_status stage(cvo_handle h, const cvo_cloud* c, int slot, int D, const float** xyz, const void** feat)
+{
+    *xyz = c->xyz;
+    *feat = c->feat;
+    if (c->on_device || c->n == 0) return CVO_OK;
+    const size_t bx = (size_t)c->n * 3 * sizeof(float);
+    CVO_CUDA(ensure(h->stage_xyz[slot], bx));
+    CVO_CUDA(cudaMemcpyAsync(h->stage_xyz[slot].p, c->xyz, bx, cudaMemcpyHostToDevice, h->s));
+    *xyz = (const float*)h->stage_xyz[slot].p;
+    if (D > 0) {
+        const size_t bf = (size_t)c->n * D * (c->feat_dtype == CVO_BF16 ? 2 : 4);
+        CVO_CUDA(ensure(h->stage_feat[slot], bf));
+        CVO_CUDA(cudaMemcpyAsync(h->stage_feat[slot].p, c->feat, bf, cudaMemcpyHostToDevice, h->s));
+        *feat = h->stage_feat[slot].p;
+    }
+    return CVO_OK;
+}
+
+int bits_for(long long v)
+{
+    int b = 1;
+    while (b < 32 && (1LL << b) < v) ++b;
+    return b;
+}
+
+// Sorts (keys, vals) of length n; returns pointers to the sorted arrays.
+cvo_status sort_pairs(cvo_handle h, int n, int nbits, unsigned** ks, unsigned** vs)
+{
+    int alt = 0;
+    CVO_CUDA(ensure(h->sort_tmp, radix_sort_temp_bytes(n)));
+    CVO_CUDA(radix_sort_pairs((unsigned*)h->keys.p, (unsigned*)h->vals.p, (unsigned*)h->keys2.p,
+                              (unsigned*)h->vals2.p, n, nbits, h->sort_tmp.p, &alt, h->s));
+    *ks = (unsigned*)(alt ? h->keys2.p : h->keys.p);
+    *vs = (unsigned*)(alt ? h->vals2.p : h->vals.p);
+    return CVO_OK;
+}
+
+// Builds the grid levels of Z, the Morton-ordered queries of X and their groups
+// for lengthscales in [ell_lo, ell_hi].
+cvo_status prepare(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, double ell_hi, double ell_lo)
+{
+    const cvo_params& p = h->p;
+    const int D = feat_dim(p);
+    const int n = X->n, m = Z->n;
+    h->n = n;
+    h->m = m;
+    h->D = D;
+    const float *xyz_x, *xyz_z;
+    const void *feat_x, *feat_z;
+    CVO_TRY(stage(h, X, 0, D, &xyz_x, &feat_x));
+    CVO_TRY(stage(h, Z, 1, D, &xyz_z, &feat_z));
+
+    // bounding boxes and finiteness
+    CVO_CUDA(ensure(h->misc, kMiscWords * sizeof(unsigned)));
+    unsigned* misc = (unsigned*)h->misc.p;
+    CVO_CUDA(cudaMemsetAsync(misc, 0, kMiscWords * sizeof(unsigned), h->s));
+    CVO_CUDA(cudaMemsetAsync(misc + 0, 0xff, 3 * sizeof(unsigned), h->s));
+    CVO_CUDA(cudaMemsetAsync(misc + 6, 0xff, 3 * sizeof(unsigned), h->s));
+    int* bad = (int*)(misc + 12);
+    CVO_CUDA(launch_bbox(xyz_x, n, misc + 0, bad, h->s));
+    CVO_CUDA(launch_bbox(xyz_z, m, misc + 6, bad, h->s));
+    if (D > 0) {
+        CVO_CUDA(launch_check_feat(feat_x, (long long)n * D, X->feat_dtype == CVO_BF16, bad, h->s));
+        CVO_CUDA(launch_check_feat(feat_z, (long long)m * D, Z->feat_dtype == CVO_BF16, bad, h->s));
+    }
+    CVO_CUDA(cudaMemcpyAsync(h->h_misc, misc, 13 * sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
+    CVO_CUDA(cudaStreamSynchronize(h->s));
+    if (h->h_misc[12]) return fail(CVO_ERR_INVALID_ARG, "non-finite coordinate or feature");
+    float xmin[3], xmax[3], zmin[3], zmax[3];
+    for (int a = 0; a < 3; ++a) {
+        xmin[a] = decode_orderable(h->h_misc[a]);
+        xmax[a] = decode_orderable(h->h_misc[3 + a]);
+        zmin[a] = decode_orderable(h->h_misc[6 + a]);
+        zmax[a] = decode_orderable(h->h_misc[9 + a]);
+        h->zc[a] = 0.5 * ((double)zmin[a] + (double)zmax[a]);
+    }
+
+    // record layout
+    h->rec_bf16 = (D > 0 && X->feat_dtype == CVO_BF16 && Z->feat_dtype == CVO_BF16) ? 1 : 0;
+    const int payload = D * (h->rec_bf16 ? 2 : 4);
+    h->rs = 1 + (payload + 15) / 16;
+    const int rs = h->rs;
+    const int nmax = std::max(n, m);
+    CVO_CUDA(ensure(h->keys, (size_t)nmax * 4));
+    CVO_CUDA(ensure(h->vals, (size_t)nmax * 4));
+    CVO_CUDA(ensure(h->keys2, (size_t)nmax * 4));
+    CVO_CUDA(ensure(h->vals2, (size_t)nmax * 4));
+
+    // grid levels of Z
+    h->dense = !(p.cutoff_mult > 0.0);
+    if (h->dense) {
+        h->nlevels = 1;
+        LevelHost& L = h->lv[0];
+        L.h = 1.0;
+        L.nx = L.ny = L.nz = 1;
+        L.ox = zmin[0]; L.oy = zmin[1]; L.oz = zmin[2];
+        L.ncells = 1;
+    } else {
+        const double rc_hi = p.cutoff_mult * ell_hi, rc_lo = p.cutoff_mult * ell_lo;
+        int nl = 1 + (int)std::floor(std::log(rc_hi / rc_lo) / std::log(std::sqrt(2.0)) + 1e-9);
+        nl = std::max(1, std::min(nl, kMaxLevels));
+        h->nlevels = nl;
+        for (int k = 0; k < nl; ++k) {
+            LevelHost& L = h->lv[k];
+            double hh = rc_hi * 1.0002 / std::pow(std::sqrt(2.0), k);
+            for (;;) {
+                L.nx = (int)std::floor(((double)zmax[0] - zmin[0]) / hh) + 1;
+                L.ny = (int)std::floor(((double)zmax[1] - zmin[1]) / hh) + 1;
+                L.nz = (int)std::floor(((double)zmax[2] - zmin[2]) / hh) + 1;
+                L.ncells = (long long)L.nx * L.ny * L.nz;
+                if (L.ncells <= kMaxCells) break;
+                hh *= 1.26;
+            }
+            L.h = hh;
+            L.ox = zmin[0]; L.oy = zmin[1]; L.oz = zmin[2];
+        }
+    }
+    for (int k = 0; k < h->nlevels; ++k) {
+        LevelHost& L = h->lv[k];
+        CVO_CUDA(ensure(h->zrec[k], (size_t)std::max(m, 1) * rs * sizeof(float4)));
+        CVO_CUDA(ensure(h->cell_start[k], (size_t)(L.ncells + 1) * sizeof(int)));
+        if (h->dense) {
+            const int cs[2] = {0, m};
+            CVO_CUDA(cudaMemcpyAsync(h->cell_start[k].p, cs, sizeof(cs), cudaMemcpyHostToDevice, h->s));
+            CVO_CUDA(launch_pack(xyz_z, feat_z, Z->feat_dtype == CVO_BF16, D, nullptr, m, (float4*)h->zrec[k].p, rs,
+                                 h->rec_bf16, h->s));
+        } else {
+            CVO_CUDA(launch_cell_keys(xyz_z, m, L.ox, L.oy, L.oz, (float)(1.0 / L.h), L.nx, L.ny, L.nz,
+                                      (unsigned*)h->keys.p, (unsigned*)h->vals.p, h->s));
+            unsigned *ks, *vs;
+            CVO_TRY(sort_pairs(h, m, bits_for(L.ncells), &ks, &vs));
+            CVO_CUDA(launch_cell_start(ks, m, (int)L.ncells, (int*)h->cell_start[k].p, h->s));
+            CVO_CUDA(launch_pack(xyz_z, feat_z, Z->feat_dtype == CVO_BF16, D, vs, m, (float4*)h->zrec[k].p, rs,
+                                 h->rec_bf16, h->s));
+        }
+        // keep a synchronous point per level so the shared sort buffers are
+        // never overwritten while in use (the stream orders this anyway)
+    }
+
+    // queries: Morton order of X in its own frame
+    double ext = 0.0;
+    for (int a = 0; a < 3; ++a) ext = std::max(ext, (double)xmax[a] - xmin[a]);
+    const double cell0 = std::max(ext / 1024.0, 1e-6);
+    CVO_CUDA(ensure(h->xrec, (size_t)std::max(n, 1) * rs * sizeof(float4)));
+    CVO_CUDA(ensure(h->morton, (size_t)std::max(n, 1) * 4));
+    CVO_CUDA(launch_morton_keys(xyz_x, n, xmin[0], xmin[1], xmin[2], (float)(1.0 / cell0), (unsigned*)h->keys.p,
+                                (unsigned*)h->vals.p, h->s));
+    {
+        unsigned *ks, *vs;
+        CVO_TRY(sort_pairs(h, n, 30, &ks, &vs));
+        CVO_CUDA(launch_pack(xyz_x, feat_x, X->feat_dtype == CVO_BF16, D, vs, n, (float4*)h->xrec.p, rs, h->rec_bf16,
+                             h->s));
+        CVO_CUDA(cudaMemcpyAsync(h->morton.p, ks, (size_t)n * 4, cudaMemcpyDeviceToDevice, h->s));
+    }
+    // query groups per level
+    CVO_CUDA(ensure(h->flags, (size_t)std::max(n, 1) * 4));
+    CVO_CUDA(ensure(h->gidx, (size_t)std::max(n, 1) * 4));
+    for (int k = 0; k < h->nlevels; ++k) {
+        LevelHost& L = h->lv[k];
+        int sh = 30;
+        if (!h->dense) {
+            const int e = (int)std::floor(std::log2(L.h / cell0));
+            sh = 3 * std::max(0, std::min(10, e));
+        }
+        L.shift = sh;
+        CVO_CUDA(ensure(h->groups[k], (size_t)std::max(n, 1) * sizeof(int2)));
+        CVO_CUDA(launch_group_flags((const unsigned*)h->morton.p, n, sh, (unsigned*)h->flags.p, h->s));
+        CVO_CUDA(exclusive_scan_u32((const unsigned*)h->flags.p, (unsigned*)h->gidx.p, n, misc + 16 + k, h->s));
+        CVO_CUDA(launch_group_write((const unsigned*)h->morton.p, (const unsigned*)h->flags.p,
+                                    (const unsigned*)h->gidx.p, n, sh, (int2*)h->groups[k].p, h->s));
+    }
+    CVO_CUDA(cudaMemcpyAsync(h->h_misc + 16, misc + 16, h->nlevels * sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
+    CVO_CUDA(cudaStreamSynchronize(h->s));
+    int max_items = 1;
+    LevelDesc ld[kMaxLevels];
+    for (int k = 0; k < h->nlevels; ++k) {
+        LevelHost& L = h->lv[k];
+        L.ngroups = n > 0 ? (int)h->h_misc[16 + k] : 0;
+        max_items = std::max(max_items, L.ngroups * kChunks);
+        LevelDesc& d = ld[k];
+        d.h = (float)L.h;
+        d.inv_h = (float)(1.0 / L.h);
+        d.ox = L.ox; d.oy = L.oy; d.oz = L.oz;
+        d.nx = L.nx; d.ny = L.ny; d.nz = L.nz;
+        d.cell_start = (const int*)h->cell_start[k].p;
+        d.zrec = (const float4*)h->zrec[k].p;
+        d.groups = (const int2*)h->groups[k].p;
+        d.ngroups = L.ngroups;
+        d.pad_ = 0;
+    }
+    CVO_CUDA(ensure(h->levels_dev, sizeof(ld)));
+    CVO_CUDA(cudaMemcpyAsync(h->levels_dev.p, ld, h->nlevels * sizeof(LevelDesc), cudaMemcpyHostToDevice, h->s));
+    h->sweep_blocks = std::max(1, std::min((max_items + kSweepWarps - 1) / kSweepWarps, h->num_sms * 8));
+    CVO_CUDA(ensure(h->part_stats, (size_t)kStatN * h->sweep_blocks * sizeof(float2)));
+    CVO_CUDA(ensure(h->part_cnt, (size_t)2 * h->sweep_blocks * sizeof(unsigned long long)));
+
+    // feature constants
+    FeatConst& fc = h->fc;
+    std::memset(&fc, 0, sizeof(fc));
+    fc.n_blocks = p.n_blocks;
+    int off = 0;
+    double kappa = p.sigma * p.sigma;
+    for (int b = 0; b < p.n_blocks; ++b) {
+        fc.dim[b] = p.blocks[b].dim;
+        fc.kind[b] = p.blocks[b].kind;
+        fc.off[b] = off;
+        off += p.blocks[b].dim;
+        if (p.blocks[b].kind == CVO_FEAT_SE) {
+            const double sc = p.blocks[b].scale;
+            fc.s[b] = (float)(-1.4426950408889634 / (2.0 * sc * sc));
+            kappa *= p.blocks[b].sigma * p.blocks[b].sigma;
+        }
+    }
+    fc.D = D;
+    fc.bf16 = h->rec_bf16;
+    h->kappa = kappa;
+    return CVO_OK;
+}
+
+cvo_status init_state(cvo_handle h, const double* T, double ell, int mode)
+{
+    IterState* st = h->h_state;
+    std::memset(st, 0, sizeof(IterState));
+    std::memcpy(st->T, T, 16 * sizeof(double));
+    const cvo_params& p = h->p;
+    st->ell = ell;
+    st->ell_last = ell;
+    st->mode = mode;
+    st->kappa = h->kappa;
+    st->norm = (h->n > 0 && h->m > 0) ? 1.0 / std::sqrt((double)h->n * (double)h->m) : 0.0;
+    st->cutoff_mult = p.cutoff_mult;
+    st->ell_min = p.anneal ? p.ell_min : ell;
+    st->decay = p.decay;
+    st->indicator_tol = p.indicator_tol;
+    st->step_tol_rot = p.step_tol_rot;
+    st->step_tol_trans = p.step_tol_trans;
+    st->max_step_rot = p.max_step_rot;
+    st->max_step_trans = p.max_step_trans;
+    st->max_iters = p.max_iters;
+    st->anneal = p.anneal;
+    st->status = 1;
+    for (int a = 0; a < 3; ++a) st->c[a] = h->zc[a];
+    st->nlevels = h->nlevels;
+    for (int k = 0; k < h->nlevels; ++k) st->level_h[k] = (float)h->lv[k].h;
+    if (mode == 1 && p.max_iters == 0) st->done = 1;
+    CVO_CUDA(ensure(h->state, sizeof(IterState)));
+    CVO_CUDA(cudaMemcpyAsync(h->state.p, st, sizeof(IterState), cudaMemcpyHostToDevice, h->s));
+    CVO_CUDA(launch_init_state((IterState*)h->state.p, h->s));
+    return CVO_OK;
+}
+
+SweepArgs sweep_args(cvo_handle h)
+{
+    SweepArgs a;
+    a.levels = (const LevelDesc*)h->levels_dev.p;
+    a.xrec = (const float4*)h->xrec.p;
+    a.n = h->n;
+    a.m = h->m;
+    a.rs = h->rs;
+    a.dense = h->dense;
+    a.st = (IterState*)h->state.p;
+    a.part_stats = (float2*)h->part_stats.p;
+    a.part_cnt = (unsigned long long*)h->part_cnt.p;
+    a.part_cap = h->sweep_blocks;
+    a.fc = h->fc;
+    return a;
+}
+
+cvo_status fetch_state(cvo_handle h)
+{
+    CVO_CUDA(cudaMemcpyAsync(h->h_state, h->state.p, sizeof(IterState), cudaMemcpyDeviceToHost, h->s));
+    CVO_CUDA(cudaStreamSynchronize(h->s));
+    return CVO_OK;
+}
+
+cvo_status run_eval(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double* T, cvo_eval* out)
+{
+    std::memset(out, 0, sizeof(*out));
+    if (X->n == 0 || Z->n == 0) return CVO_OK;
+    CVO_TRY(prepare(h, X, Z, h->p.ell, h->p.ell));
+    CVO_TRY(init_state(h, T, h->p.ell, 0));
+    const SweepArgs a = sweep_args(h);
+    CVO_CUDA(launch_sweep(a, h->sweep_blocks, h->s));
+    CVO_CUDA(launch_finalize(a.st, a.part_stats, a.part_cnt, a.part_cap, h->sweep_blocks, nullptr, h->s));
+    CVO_TRY(fetch_state(h));
+    const IterState* st = h->h_state;
+    out->F = st->F;
+    for (int q = 0; q < 6; ++q) out->grad[q] = st->grad[q];
+    for (int q = 0; q < 36; ++q) out->hess[q] = st->hess[q];
+    out->i_theta = st->i_theta;
+    out->pairs = st->pairs;
+    out->candidates = st->cands;
+    return CVO_OK;
+}
+
+cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double* T_init, double* T_out,
+                        cvo_info* info)
+{
+    const cvo_params& p = h->p;
+    cvo_info inf;
+    std::memset(&inf, 0, sizeof(inf));
+    h->last_iters = 0;
+    h->sweep_ms = 0.0;
+    h->sweep_n = 0;
+    if (X->n == 0 || Z->n == 0 || p.max_iters == 0) {
+        std::memcpy(T_out, T_init, 16 * sizeof(double));
+        inf.status = (X->n == 0 || Z->n == 0) ? CVO_OK : CVO_NOT_CONVERGED;
+        inf.ell_final = p.ell;
+        if (info) *info = inf;
+        return (cvo_status)inf.status;
+    }
+    const double ell_lo = p.anneal ? p.ell_min : p.ell;
+    CVO_TRY(prepare(h, X, Z, p.ell, ell_lo));
+    CVO_TRY(init_state(h, T_init, p.ell, 1));
+    CVO_CUDA(ensure(h->trace, (size_t)p.max_iters * CVO_TRACE_STRIDE * sizeof(double)));
+    const SweepArgs a = sweep_args(h);
+    double* trace = (double*)h->trace.p;
+    if (h->timing) {
+        const size_t need = (size_t)2 * p.max_iters;
+        while (h->evs.size() < need) {
+            cudaEvent_t e;
+            CVO_CUDA(cudaEventCreate(&e));
+            h->evs.push_back(e);
+        }
+    }
+    // Iterations are queued in batches; the device-side state stops the
+    // kernels once the registration has converged.  The host checks the
+    // done flag of the previous batch while the next one runs.
+    const int batch = 8;
+    int launched = 0;
+    while (launched < p.max_iters) {
+        const int nb = std::min(batch, p.max_iters - launched);
+        for (int k = 0; k < nb; ++k) {
+            const int it = launched + k;
+            if (h->timing) CVO_CUDA(cudaEventRecord(h->evs[2 * it], h->s));
+            CVO_CUDA(launch_sweep(a, h->sweep_blocks, h->s));
+            if (h->timing) CVO_CUDA(cudaEventRecord(h->evs[2 * it + 1], h->s));
+            CVO_CUDA(launch_finalize(a.st, a.part_stats, a.part_cnt, a.part_cap, h->sweep_blocks, trace, h->s));
+        }
+        launched += nb;
+        if (launched >= p.max_iters) break;
+        CVO_CUDA(cudaMemcpyAsync(&h->h_state->done, &((IterState*)h->state.p)->done, sizeof(int),
+                                 cudaMemcpyDeviceToHost, h->s));
+        CVO_CUDA(cudaStreamSynchronize(h->s));
+        if (h->h_state->done) break;
+    }
+    CVO_TRY(fetch_state(h));
+    const IterState* st = h->h_state;
+    std::memcpy(T_out, st->T, 16 * sizeof(double));
+    inf.iters = st->iter;
+    inf.status = st->status == 0 ? CVO_OK : CVO_NOT_CONVERGED;
+    inf.ell_final = st->ell_last;
+    inf.F = st->F;
+    inf.i_theta = st->i_theta;
+    inf.last_step_rot = st->srot;
+    inf.last_step_trans = st->strans;
+    inf.pairs = st->pairs_total;
+    inf.candidates = st->cands_total;
+    h->last_iters = st->iter;
+    if (h->timing) {
+        double tot = 0.0;
+        for (int it = 0; it < st->iter; ++it) {
+            float ms = 0.0f;
+            CVO_CUDA(cudaEventElapsedTime(&ms, h->evs[2 * it], h->evs[2 * it + 1]));
+            tot += ms;
+        }
+        h->sweep_ms = tot;
+        h->sweep_n = st->iter;
+    }
+    if (info) *info = inf;
+    return (cvo_status)inf.status;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* cvo_last_error(void) { return g_err.c_str(); }
+
+const char* cvo_version(void) { return "cvo-gb300 0.1 (sm_103a)"; }
+
+long long cvo_kernel_launches(void) { return g_launch_count.load(); }
+
+cvo_status cvo_create(const cvo_params* params, void* cuda_stream, cvo_handle* out)
+{
+    g_err.clear();
+    if (!out) return fail(CVO_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    CVO_TRY(check_params(params));
+    int dev = 0;
+    CVO_CUDA(cudaGetDevice(&dev));
+    cvo_handle h = new cvo_handle_s();
+    h->p = *params;
+    h->s = (cudaStream_t)cuda_stream;
+    h->device = dev;
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaMallocHost((void**)&h->h_state, sizeof(IterState)) != cudaSuccess ||
+        cudaMallocHost((void**)&h->h_misc, kMiscWords * sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        if (h->h_state) cudaFreeHost(h->h_state);
+        delete h;
+        return fail(CVO_ERR_OOM, "cudaMallocHost failed");
+    }
+    *out = h;
+    return CVO_OK;
+}
+
+cvo_status cvo_destroy(cvo_handle h)
+{
+    if (!h) return CVO_OK;
+    DeviceGuard g(h->device);
+    cudaStreamSynchronize(h->s);
+    DevBuf* bufs[] = {&h->stage_xyz[0], &h->stage_xyz[1], &h->stage_feat[0], &h->stage_feat[1], &h->keys, &h->vals,
+                      &h->keys2, &h->vals2, &h->sort_tmp, &h->flags, &h->gidx, &h->xrec, &h->morton, &h->misc,
+                      &h->levels_dev, &h->state, &h->part_stats, &h->part_cnt, &h->trace};
+    for (DevBuf* b : bufs) release(*b);
+    for (int k = 0; k < kMaxLevels; ++k) {
+        release(h->zrec[k]);
+        release(h->cell_start[k]);
+        release(h->groups[k]);
+    }
+    for (cudaEvent_t e : h->evs) cudaEventDestroy(e);
+    if (h->h_state) cudaFreeHost(h->h_state);
+    if (h->h_misc) cudaFreeHost(h->h_misc);
+    delete h;
+    return CVO_OK;
+}
+
+cvo_status cvo_set_params(cvo_handle h, const cvo_params* params)
+{
+    g_err.clear();
+    if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
+    CVO_TRY(check_params(params));
+    h->p = *params;
+    return CVO_OK;
+}
+
+cvo_status cvo_evaluate(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], cvo_eval* out)
+{
+    g_err.clear();
+    if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
+    if (!out) return fail(CVO_ERR_INVALID_ARG, "out is NULL");
+    const int D = feat_dim(h->p);
+    CVO_TRY(check_cloud(X, "X", D));
+    CVO_TRY(check_cloud(Z, "Z", D));
+    CVO_TRY(check_pose(T, "T"));
+    DeviceGuard g(h->device);
+    return run_eval(h, X, Z, T, out);
+}
+
+cvo_status cvo_inner_product(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], double* F)
+{
+    if (!F) return fail(CVO_ERR_INVALID_ARG, "F is NULL");
+    cvo_eval e;
+    CVO_TRY(cvo_evaluate(h, X, Z, T, &e));
+    *F = e.F;
+    return CVO_OK;
+}
+
+cvo_status cvo_gradient(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], double grad[6],
+                        double* F)
+{
+    if (!grad) return fail(CVO_ERR_INVALID_ARG, "grad is NULL");
+    cvo_eval e;
+    CVO_TRY(cvo_evaluate(h, X, Z, T, &e));
+    for (int q = 0; q < 6; ++q) grad[q] = e.grad[q];
+    if (F) *F = e.F;
+    return CVO_OK;
+}
+
+cvo_status cvo_metric(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], double* i_theta)
+{
+    if (!i_theta) return fail(CVO_ERR_INVALID_ARG, "i_theta is NULL");
+    cvo_eval e;
+    CVO_TRY(cvo_evaluate(h, X, Z, T, &e));
+    *i_theta = e.i_theta;
+    return CVO_OK;
+}
+
+cvo_status cvo_register_pair(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T_init[16],
+                             double T_out[16], cvo_info* info)
+{
+    g_err.clear();
+    if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
+    if (!T_out) return fail(CVO_ERR_INVALID_ARG, "T_out is NULL");
+    const int D = feat_dim(h->p);
+    CVO_TRY(check_cloud(X, "X", D));
+    CVO_TRY(check_cloud(Z, "Z", D));
+    CVO_TRY(check_pose(T_init, "T_init"));
+    DeviceGuard g(h->device);
+    return run_register(h, X, Z, T_init, T_out, info);
+}
+
+cvo_status cvo_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, const cvo_cloud* Z, const double* T_init,
+                              double* T_out, cvo_info* infos)
+{
+    g_err.clear();
+    if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
+    if (npairs < 0) return fail(CVO_ERR_INVALID_ARG, "npairs < 0");
+    if (npairs > 0 && (!X || !Z || !T_init || !T_out)) return fail(CVO_ERR_INVALID_ARG, "NULL array");
+    cvo_status worst = CVO_OK;
+    for (int k = 0; k < npairs; ++k) {
+        cvo_status s = cvo_register_pair(h, X + k, Z + k, T_init + 16 * k, T_out + 16 * k, infos ? infos + k : nullptr);
+        if (s < 0) return s;
+        if (s == CVO_NOT_CONVERGED) worst = CVO_NOT_CONVERGED;
+    }
+    return worst;
+}
+
+int cvo_get_trace(cvo_handle h, double* out, int cap)
+{
+    if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
+    if (cap < 0 || (cap > 0 && !out)) return fail(CVO_ERR_INVALID_ARG, "bad output buffer");
+    const int n = std::min(cap, h->last_iters);
+    if (n > 0) {
+        DeviceGuard g(h->device);
+        if (cudaMemcpy(out, h->trace.p, (size_t)n * CVO_TRACE_STRIDE * sizeof(double), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+            return fail(CVO_ERR_CUDA, "trace copy failed");
+    }
+    return h->last_iters;
+}
+
+cvo_status cvo_set_timing(cvo_handle h, int on)
+{
+    if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
+    h->timing = on ? 1 : 0;
+    return CVO_OK;
+}
+
+cvo_status cvo_sweep_time(cvo_handle h, double* avg_ms, int* launches)
+{
+    if (!h || !avg_ms || !launches) return fail(CVO_ERR_INVALID_ARG, "NULL argument");
+    *launches = h->sweep_n;
+    *avg_ms = h->sweep_n > 0 ? h->sweep_ms / h->sweep_n : 0.0;
+    return CVO_OK;
+}
+
+}  // extern "C"

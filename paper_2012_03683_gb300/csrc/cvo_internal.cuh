@@ -1,0 +1,145 @@
+// Internal declarations shared by the CUDA translation units of libcvo.
+//
+// Data layout in device memory (one handle, one pair):
+//   zrec[level]   M records sorted by grid cell (x fastest), RS float4 each:
+//                 rec[0] = (x, y, z, 0) float32 as given; rec[1..] = the point's
+//                 feature row (float32 or bfloat16, blocks concatenated,
+//                 zero padded to 16 bytes)
+//   cell_start    per level, ncells + 1 ints: records of cell c are
+//                 [cell_start[c], cell_start[c+1])
+//   xrec          N query records in the same layout, in Morton order of X's
+//                 own frame (spatially compact runs)
+//   groups        per level, (first query, count <= 32) of each query group:
+//                 consecutive queries inside one Morton super-cell whose edge
+//                 does not exceed that level's cell edge
+//   IterState     pose, lengthscale, annealing state and the derived
+//                 per-iteration constants, written by the finalize kernel and
+//                 read by the sweep kernel (no host round trip per iteration)
+//   partials      per sweep block: 43 linear statistics as (hi, lo) float
+//                 pairs plus the pair and candidate counts
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+namespace cvo {
+
+constexpr int kStatN = 43;       // linear statistics of the per-query moments
+constexpr int kSweepWarps = 4;   // warps per sweep block
+constexpr int kMaxLevels = 24;   // grid levels of one registration
+constexpr int kChunks = 8;       // chunks a group's candidate stream splits into
+constexpr int kChunkMin = 64;    // shortest chunk worth a work item
+constexpr int kFinalizeThreads = 1024;
+constexpr int kTraceStride = 22;  // doubles per iteration in the trace (CVO_TRACE_STRIDE)
+
+// Offsets of the 43 statistics (see the finalize kernel for their use).
+enum StatIndex {
+    ST_W = 0,     // sum W
+    ST_E = 1,     // sum E (3)
+    ST_Q = 4,     // sum Q (xx, yy, zz, xy, xz, yz)
+    ST_PQ = 10,   // sum [p]x Q (3x3 row major)
+    ST_PQP = 19,  // sum [p]x Q [p]x (xx, yy, zz, xy, xz, yz)
+    ST_WP = 25,   // sum W p (3)
+    ST_WPP = 28,  // sum W p p^T (xx, yy, zz, xy, xz, yz)
+    ST_EP = 34    // sum E p^T (3x3 row major)
+};
+
+struct LevelDesc {
+    float h, inv_h;          // cell edge and its inverse
+    float ox, oy, oz;        // grid origin (minimum corner), Z frame
+    int nx, ny, nz;          // cells per axis
+    const int* cell_start;   // nx*ny*nz + 1
+    const float4* zrec;      // M records sorted by cell
+    const int2* groups;      // query groups (first, count)
+    int ngroups;
+    int pad_;
+};
+
+// Feature-kernel constants (exponent in log2 units).
+struct FeatConst {
+    int n_blocks;
+    int dim[4];
+    int kind[4];             // 0 squared exponential, 1 inner product
+    int off[4];              // column offset of each block
+    float s[4];              // -log2(e) / (2 l_b^2) for squared-exponential blocks
+    int D;                   // total feature dim
+    int bf16;                // storage of the records' features
+};
+
+struct IterState {
+    double T[16];            // current pose, row major
+    double ell;              // current lengthscale
+    double ell_last;         // lengthscale of the last completed iteration
+    // derived constants for the sweep: x' = A x + b with A = R^T, b = -R^T t
+    float Ahi[9], Alo[9], bhi[3], blo[3];
+    float chi[3], clo[3];    // lever centre c (Z frame)
+    float sg;                // -log2(e) / (2 l^2)
+    float rc;                // cutoff radius (m); < 0: dense
+    float rc2;               // rc^2
+    int level;               // grid level for this iteration
+    int done;                // 1: no more iterations
+    int iter;                // iterations completed
+    int mode;                // 0 eval, 1 register
+    int have_ref;
+    double i_ref;
+    // results of the last sweep / step
+    double F, i_theta, gnorm, Fpp, t, srot, strans;
+    double grad[6];
+    double hess[36];
+    long long pairs, cands, pairs_total, cands_total;
+    int status;              // 0 converged, 1 not converged
+    int decayed;
+    // constants of the registration
+    double kappa;            // sigma^2 * prod sigma_b^2 over squared-exponential blocks
+    double norm;             // 1 / sqrt(N M) (0 if empty)
+    double cutoff_mult, ell_min, decay, indicator_tol;
+    double step_tol_rot, step_tol_trans, max_step_rot, max_step_trans;
+    double c[3];             // lever centre (double)
+    int max_iters, anneal;
+    int nlevels;
+    float level_h[kMaxLevels];
+};
+
+struct SweepArgs {
+    const LevelDesc* levels;   // device array [nlevels]
+    const float4* xrec;        // N query records
+    int n, m;
+    int rs;                    // record stride (float4)
+    int dense;
+    IterState* st;
+    float2* part_stats;        // [kStatN][part_cap]
+    unsigned long long* part_cnt; // [2][part_cap]
+    int part_cap;
+    FeatConst fc;
+};
+
+// ---- launchers (host) ------------------------------------------------------
+
+// Kernels launched by this library in this process (every launcher adds its own).
+extern std::atomic<long long> g_launch_count;
+
+cudaError_t launch_sweep(const SweepArgs& a, int nblocks, cudaStream_t s);
+cudaError_t launch_init_state(IterState* st, cudaStream_t s);
+cudaError_t launch_finalize(IterState* st, const float2* part_stats, const unsigned long long* part_cnt,
+                            int part_cap, int nblocks, double* trace, cudaStream_t s);
+
+// setup (cvo_setup.cu)
+cudaError_t launch_bbox(const float* xyz, int n, unsigned* out6, int* bad, cudaStream_t s);
+cudaError_t launch_check_feat(const void* feat, long long count, int bf16, int* bad, cudaStream_t s);
+cudaError_t launch_cell_keys(const float* xyz, int n, float ox, float oy, float oz, float inv_h, int nx, int ny,
+                             int nz, unsigned* keys, unsigned* vals, cudaStream_t s);
+cudaError_t launch_morton_keys(const float* xyz, int n, float ox, float oy, float oz, float inv_cell,
+                               unsigned* keys, unsigned* vals, cudaStream_t s);
+size_t radix_sort_temp_bytes(int n);
+cudaError_t radix_sort_pairs(unsigned* keys, unsigned* vals, unsigned* keys_alt, unsigned* vals_alt, int n,
+                             int nbits, void* temp, int* result_in_alt, cudaStream_t s);
+cudaError_t launch_cell_start(const unsigned* sorted_keys, int n, int ncells, int* cell_start, cudaStream_t s);
+cudaError_t launch_pack(const float* xyz, const void* feat, int feat_bf16, int D, const unsigned* order, int n,
+                        float4* rec, int rs, int rec_bf16, cudaStream_t s);
+cudaError_t launch_group_flags(const unsigned* sorted_morton, int n, int shift, unsigned* flags, cudaStream_t s);
+cudaError_t exclusive_scan_u32(const unsigned* in, unsigned* out, int n, unsigned* total, cudaStream_t s);
+cudaError_t launch_group_write(const unsigned* sorted_morton, const unsigned* flags, const unsigned* gidx, int n,
+                               int shift, int2* groups, cudaStream_t s);
+
+}  // namespace cvo

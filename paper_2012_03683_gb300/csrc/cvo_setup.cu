@@ -1,0 +1,384 @@
+// Setup kernels, run once per cloud pair: bounding boxes, the uniform grid of
+// Z (a stable counting sort by cell key), the Morton order of X and its query
+// groups.  The paper notes that the double sum is sparse (Sec. III-B); the
+// grid is how the sweep visits only the pairs near each query.
+#include "cvo_internal.cuh"
+
+namespace cvo {
+
+namespace {
+
+__device__ __forceinline__ unsigned orderable(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__global__ void k_bbox(const float* __restrict__ xyz, int n, unsigned* out6, int* bad)
+{
+    float mn[3] = {3.0e38f, 3.0e38f, 3.0e38f}, mx[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
+    int nonfinite = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        for (int a = 0; a < 3; ++a) {
+            const float v = xyz[3 * (size_t)i + a];
+            if (!isfinite(v)) {
+                nonfinite = 1;
+                continue;
+            }
+            mn[a] = fminf(mn[a], v);
+            mx[a] = fmaxf(mx[a], v);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+        nonfinite |= __shfl_xor_sync(0xffffffffu, nonfinite, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(out6 + a, orderable(mn[a]));
+            atomicMax(out6 + 3 + a, orderable(mx[a]));
+        }
+        if (nonfinite) atomicOr(bad, 1);
+    }
+}
+
+__global__ void k_check_feat(const void* __restrict__ feat, long long count, int bf16, int* bad)
+{
+    int nonfinite = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        float v;
+        if (bf16) v = __uint_as_float(((unsigned)((const unsigned short*)feat)[i]) << 16);
+        else v = ((const float*)feat)[i];
+        if (!isfinite(v)) nonfinite = 1;
+    }
+    if (__any_sync(0xffffffffu, nonfinite) && (threadIdx.x & 31) == 0) atomicOr(bad, 1);
+}
+
+__device__ __forceinline__ int cell_of(float v, float o, float inv_h, int n)
+{
+    int c = (int)floorf((v - o) * inv_h);
+    return min(max(c, 0), n - 1);
+}
+
+__global__ void k_cell_keys(const float* __restrict__ xyz, int n, float ox, float oy, float oz, float inv_h, int nx,
+                            int ny, int nz, unsigned* keys, unsigned* vals)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int cx = cell_of(xyz[3 * (size_t)j + 0], ox, inv_h, nx);
+    const int cy = cell_of(xyz[3 * (size_t)j + 1], oy, inv_h, ny);
+    const int cz = cell_of(xyz[3 * (size_t)j + 2], oz, inv_h, nz);
+    keys[j] = (unsigned)((cz * ny + cy) * nx + cx);
+    vals[j] = (unsigned)j;
+}
+
+__device__ __forceinline__ unsigned spread10(unsigned v)
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__global__ void k_morton_keys(const float* __restrict__ xyz, int n, float ox, float oy, float oz, float inv_cell,
+                              unsigned* keys, unsigned* vals)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    unsigned q[3];
+    const float o[3] = {ox, oy, oz};
+    for (int a = 0; a < 3; ++a) {
+        int c = (int)floorf((xyz[3 * (size_t)j + a] - o[a]) * inv_cell);
+        q[a] = (unsigned)min(max(c, 0), 1023);
+    }
+    keys[j] = spread10(q[0]) | (spread10(q[1]) << 1) | (spread10(q[2]) << 2);
+    vals[j] = (unsigned)j;
+}
+
+// ---- stable LSD radix sort, 8-bit digits ------------------------------------
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortTile = 4096;                  // keys per block
+constexpr int kSortSub = kSortTile / kSortWarps; // keys per warp
+
+__global__ void k_radix_hist(const unsigned* __restrict__ keys, int n, int shift, unsigned* hist, int nb)
+{
+    __shared__ unsigned cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * kSortTile;
+    for (int k = threadIdx.x; k < kSortTile; k += kSortThreads) {
+        const int i = base + k;
+        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void k_radix_scatter(const unsigned* __restrict__ keys, const unsigned* __restrict__ vals, int n,
+                                int shift, const unsigned* __restrict__ offs, int nb, unsigned* keys_out,
+                                unsigned* vals_out)
+{
+    __shared__ unsigned wcnt[kSortWarps][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < kSortWarps * 256; d += kSortThreads) (&wcnt[0][0])[d] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * kSortTile + warp * kSortSub;
+    for (int r = 0; r < kSortSub; r += 32) {
+        const int i = base + r + lane;
+        if (i < n) atomicAdd(&wcnt[warp][(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    {   // per digit: block offset plus the counts of the earlier warps
+        const int d = threadIdx.x;
+        unsigned run = offs[d * nb + blockIdx.x];
+        for (int w = 0; w < kSortWarps; ++w) {
+            const unsigned c = wcnt[w][d];
+            wcnt[w][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r = 0; r < kSortSub; r += 32) {
+        const int i = base + r + lane;
+        const bool ok = i < n;
+        const unsigned valid = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            const unsigned k = keys[i];
+            const unsigned d = (k >> shift) & 255u;
+            const unsigned peers = __match_any_sync(valid, d);
+            const unsigned pos = wcnt[warp][d] + __popc(peers & lt);
+            keys_out[pos] = k;
+            vals_out[pos] = vals[i];
+            __syncwarp(valid);
+            if ((peers & lt) == 0) wcnt[warp][d] += __popc(peers);
+        }
+        __syncwarp();
+    }
+}
+
+// single-block exclusive scan; total (optional) receives the sum
+__global__ void k_scan_single(const unsigned* __restrict__ in, unsigned* out, int n, unsigned* total)
+{
+    __shared__ unsigned sums[1024];
+    const int t = threadIdx.x;
+    const int chunk = (n + 1023) / 1024;
+    const int lo = min(n, t * chunk), hi = min(n, lo + chunk);
+    unsigned s = 0;
+    for (int i = lo; i < hi; ++i) s += in[i];
+    sums[t] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const unsigned v = t >= o ? sums[t - o] : 0u;
+        __syncthreads();
+        sums[t] += v;
+        __syncthreads();
+    }
+    unsigned run = sums[t] - s;
+    for (int i = lo; i < hi; ++i) {
+        const unsigned v = in[i];
+        out[i] = run;
+        run += v;
+    }
+    if (t == 1023 && total) *total = sums[1023];
+}
+
+__global__ void k_cell_start(const unsigned* __restrict__ keys, int n, int ncells, int* cell_start)
+{
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c > ncells) return;
+    int lo = 0, hi = n;   // first index with key >= c
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((long long)keys[mid] < c) lo = mid + 1;
+        else hi = mid;
+    }
+    cell_start[c] = lo;
+}
+
+__device__ __forceinline__ unsigned short f32_to_bf16_bits(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    return (unsigned short)((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
+}
+
+__global__ void k_pack(const float* __restrict__ xyz, const void* __restrict__ feat, int feat_bf16, int D,
+                       const unsigned* __restrict__ order, int n, float4* rec, int rs, int rec_bf16)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int j = order ? (int)order[s] : s;
+    float4* r = rec + (size_t)s * rs;
+    r[0] = make_float4(xyz[3 * (size_t)j], xyz[3 * (size_t)j + 1], xyz[3 * (size_t)j + 2], 0.0f);
+    if (rs <= 1) return;
+    if (rec_bf16) {
+        unsigned short* dst = (unsigned short*)(r + 1);
+        const int cap = (rs - 1) * 8;
+        for (int k = 0; k < cap; ++k) {
+            unsigned short b = 0;
+            if (k < D) b = feat_bf16 ? ((const unsigned short*)feat)[(size_t)j * D + k]
+                                     : f32_to_bf16_bits(((const float*)feat)[(size_t)j * D + k]);
+            dst[k] = b;
+        }
+    } else {
+        float* dst = (float*)(r + 1);
+        const int cap = (rs - 1) * 4;
+        for (int k = 0; k < cap; ++k) {
+            float v = 0.0f;
+            if (k < D) v = feat_bf16 ? __uint_as_float(((unsigned)((const unsigned short*)feat)[(size_t)j * D + k]) << 16)
+                                     : ((const float*)feat)[(size_t)j * D + k];
+            dst[k] = v;
+        }
+    }
+}
+
+__device__ __forceinline__ int lower_bound_u32(const unsigned* a, int n, unsigned long long v)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((unsigned long long)a[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_group_flags(const unsigned* __restrict__ morton, int n, int shift, unsigned* flags)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned long long seg = (unsigned long long)(morton[i] >> shift);
+    const int start = lower_bound_u32(morton, n, seg << shift);
+    flags[i] = ((i - start) % 32 == 0) ? 1u : 0u;
+}
+
+__global__ void k_group_write(const unsigned* __restrict__ morton, const unsigned* __restrict__ flags,
+                              const unsigned* __restrict__ gidx, int n, int shift, int2* groups)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !flags[i]) return;
+    const unsigned long long seg = (unsigned long long)(morton[i] >> shift);
+    const int end = lower_bound_u32(morton, n, (seg + 1ull) << shift);
+    groups[gidx[i]] = make_int2(i, min(32, end - i));
+}
+
+inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_bbox(const float* xyz, int n, unsigned* out6, int* bad, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int nb = min(blocks_for(n, 256), 1024);
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    k_bbox<<<nb, 256, 0, s>>>(xyz, n, out6, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_feat(const void* feat, long long count, int bf16, int* bad, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    const int nb = (int)min((long long)blocks_for(count, 256), 2048LL);
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    k_check_feat<<<nb, 256, 0, s>>>(feat, count, bf16, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_keys(const float* xyz, int n, float ox, float oy, float oz, float inv_h, int nx, int ny,
+                             int nz, unsigned* keys, unsigned* vals, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    k_cell_keys<<<blocks_for(n, 256), 256, 0, s>>>(xyz, n, ox, oy, oz, inv_h, nx, ny, nz, keys, vals);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_morton_keys(const float* xyz, int n, float ox, float oy, float oz, float inv_cell,
+                               unsigned* keys, unsigned* vals, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    k_morton_keys<<<blocks_for(n, 256), 256, 0, s>>>(xyz, n, ox, oy, oz, inv_cell, keys, vals);
+    return cudaGetLastError();
+}
+
+size_t radix_sort_temp_bytes(int n)
+{
+    const int nb = (n + kSortTile - 1) / kSortTile;
+    return (size_t)2 * 256 * (nb > 0 ? nb : 1) * sizeof(unsigned) + 16;
+}
+
+cudaError_t radix_sort_pairs(unsigned* keys, unsigned* vals, unsigned* keys_alt, unsigned* vals_alt, int n,
+                             int nbits, void* temp, int* result_in_alt, cudaStream_t s)
+{
+    *result_in_alt = 0;
+    if (n <= 1) return cudaSuccess;
+    const int nb = (n + kSortTile - 1) / kSortTile;
+    unsigned* hist = (unsigned*)temp;
+    unsigned* offs = hist + 256 * nb;
+    unsigned *kin = keys, *vin = vals, *kout = keys_alt, *vout = vals_alt;
+    int alt = 0;
+    for (int shift = 0; shift < nbits; shift += 8) {
+        g_launch_count.fetch_add(1, std::memory_order_relaxed);
+        k_radix_hist<<<nb, kSortThreads, 0, s>>>(kin, n, shift, hist, nb);
+        g_launch_count.fetch_add(1, std::memory_order_relaxed);
+        k_scan_single<<<1, 1024, 0, s>>>(hist, offs, 256 * nb, nullptr);
+        g_launch_count.fetch_add(1, std::memory_order_relaxed);
+        k_radix_scatter<<<nb, kSortThreads, 0, s>>>(kin, vin, n, shift, offs, nb, kout, vout);
+        unsigned* t = kin; kin = kout; kout = t;
+        t = vin; vin = vout; vout = t;
+        alt ^= 1;
+    }
+    *result_in_alt = alt;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_start(const unsigned* sorted_keys, int n, int ncells, int* cell_start, cudaStream_t s)
+{
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    k_cell_start<<<blocks_for((long long)ncells + 1, 256), 256, 0, s>>>(sorted_keys, n, ncells, cell_start);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const float* xyz, const void* feat, int feat_bf16, int D, const unsigned* order, int n,
+                        float4* rec, int rs, int rec_bf16, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    k_pack<<<blocks_for(n, 128), 128, 0, s>>>(xyz, feat, feat_bf16, D, order, n, rec, rs, rec_bf16);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_flags(const unsigned* sorted_morton, int n, int shift, unsigned* flags, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    k_group_flags<<<blocks_for(n, 256), 256, 0, s>>>(sorted_morton, n, shift, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t exclusive_scan_u32(const unsigned* in, unsigned* out, int n, unsigned* total, cudaStream_t s)
+{
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    k_scan_single<<<1, 1024, 0, s>>>(in, out, n, total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_write(const unsigned* sorted_morton, const unsigned* flags, const unsigned* gidx, int n,
+                               int shift, int2* groups, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    k_group_write<<<blocks_for(n, 256), 256, 0, s>>>(sorted_morton, flags, gidx, n, shift, groups);
+    return cudaGetLastError();
+}
+
+}  // namespace cvo

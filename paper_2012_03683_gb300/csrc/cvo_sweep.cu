@@ -1,0 +1,449 @@
+// The fused neighbour sweep: the hot loop of the double sum of Eq. (double_sum)
+//
+//   F = sum_{i,j} sigma^2 exp(-|x_i - T z_j|^2 / (2 l^2)) * c_ij
+//
+// evaluated in Z's frame, |x_i - T z_j| = |x'_i - z_j| with x'_i = T^-1 x_i.
+//
+// Work decomposition.  A warp owns one query group: up to 32 queries that lie
+// in one Morton super-cell of X (so they stay spatially compact under any
+// rigid motion), one query per lane.  The group's candidate stream is every Z
+// point in the grid cells that overlap the group's bounding box in Z's frame,
+// grown by the cutoff radius; since the grid sorts Z by cell with x fastest,
+// the stream is a short list of contiguous runs (one per (y, z) cell row).
+// Every lane reads the same candidate record at the same time (a warp-uniform
+// broadcast load), tests its own cutoff, and the warp skips the kernel
+// evaluation when no lane is in range.  A group's stream is split into up to
+// kChunks chunks, each its own work item, for load balance.
+//
+// Per pair: one ex2 (the geometric and squared-exponential feature exponents
+// are added in log2 units), the inner products of the label blocks, and the
+// moments W = sum w, E = sum w e, Q = sum w e e^T (e = z_j - x'_i) in FP32
+// registers.  Per work item, each lane folds its moments into 43 linear
+// statistics (see cvo_internal.cuh) from which the finalize kernel assembles
+// F, the se(3) gradient and the Hessian.
+//
+// Precision.  x'_i is formed in double-float (hi + lo FP32 pair) from the
+// FP32 input coordinates and a double-float copy of T^-1, so the offset
+// e = (z - x'_hi) - x'_lo keeps the coordinates' full precision even 80 m
+// from the origin (GB300's FP64 rate, 1/72 of FP32, rules out FP64 here).
+#include "cvo_internal.cuh"
+
+namespace cvo {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float ex2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// x' = A x + b with A, b given as hi + lo FP32 pairs; result as hi + lo.
+__device__ __forceinline__ void transform_df(const float x[3], const float* Ahi, const float* Alo, const float* bhi,
+                                             const float* blo, float xh[3], float xl[3])
+{
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float s = bhi[r], e = blo[r];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float a = Ahi[3 * r + c];
+            const float p = __fmul_rn(a, x[c]);
+            const float pe = __fmaf_rn(a, x[c], -p);   // exact error of the product
+            float t, te;
+            two_sum(s, p, t, te);
+            s = t;
+            e = __fadd_rn(e, __fadd_rn(te, __fmaf_rn(Alo[3 * r + c], x[c], pe)));
+        }
+        const float hi = __fadd_rn(s, e);
+        xh[r] = hi;
+        xl[r] = __fsub_rn(e, __fsub_rn(hi, s));
+    }
+}
+
+// ---- feature kernels c_ij ---------------------------------------------------
+
+// Eq. (geometric_only): no features, c_ij = 1.
+struct FeatNone {
+    struct Q {};
+    __device__ static void load_query(Q&, const float4*, const FeatConst&) {}
+    __device__ static float pair(const Q&, const float4*, float&, const FeatConst&) { return 1.0f; }
+};
+
+// One squared-exponential block (Eq. newscalar) of DSE entries followed by
+// one inner-product block (Eq. scalar) of DDOT entries; either may be empty.
+template <int DSE, int DDOT, bool BF16>
+struct FeatFixed {
+    static constexpr int D = DSE + DDOT;
+    static constexpr int kVec = BF16 ? (2 * D + 15) / 16 : (4 * D + 15) / 16;
+    struct Q {
+        float v[D];
+    };
+    __device__ static void unpack(const float4* src, float (&v)[D])
+    {
+        if constexpr (BF16) {
+            unsigned w[kVec * 4];
+#pragma unroll
+            for (int k = 0; k < kVec; ++k) {
+                const uint4 u = __ldg(reinterpret_cast<const uint4*>(src) + k);
+                w[4 * k] = u.x; w[4 * k + 1] = u.y; w[4 * k + 2] = u.z; w[4 * k + 3] = u.w;
+            }
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+                v[k] = (k & 1) ? __uint_as_float(w[k >> 1] & 0xffff0000u) : __uint_as_float(w[k >> 1] << 16);
+        } else {
+            float f[kVec * 4];
+#pragma unroll
+            for (int k = 0; k < kVec; ++k) {
+                const float4 u = __ldg(src + k);
+                f[4 * k] = u.x; f[4 * k + 1] = u.y; f[4 * k + 2] = u.z; f[4 * k + 3] = u.w;
+            }
+#pragma unroll
+            for (int k = 0; k < D; ++k) v[k] = f[k];
+        }
+    }
+    __device__ static void load_query(Q& q, const float4* rec, const FeatConst&) { unpack(rec + 1, q.v); }
+    __device__ static float pair(const Q& q, const float4* rec, float& arg, const FeatConst& fc)
+    {
+        float v[D];
+        unpack(rec + 1, v);
+        if constexpr (DSE > 0) {
+            float du2 = 0.0f;
+#pragma unroll
+            for (int k = 0; k < DSE; ++k) {
+                const float d = q.v[k] - v[k];
+                du2 = fmaf(d, d, du2);
+            }
+            arg = fmaf(du2, fc.s[0], arg);
+        }
+        if constexpr (DDOT > 0) {
+            float dot = 0.0f;
+#pragma unroll
+            for (int k = 0; k < DDOT; ++k) dot = fmaf(q.v[DSE + k], v[DSE + k], dot);
+            return dot;
+        }
+        return 1.0f;
+    }
+};
+
+// Any block list (up to 4 blocks, 64 entries): features read per pair.
+struct FeatGeneric {
+    struct Q {
+        const float4* rec;
+    };
+    __device__ static float get(const float4* rec, int k, int bf16)
+    {
+        if (bf16) return __uint_as_float(((unsigned)__ldg(reinterpret_cast<const unsigned short*>(rec + 1) + k)) << 16);
+        return __ldg(reinterpret_cast<const float*>(rec + 1) + k);
+    }
+    __device__ static void load_query(Q& q, const float4* rec, const FeatConst&) { q.rec = rec; }
+    __device__ static float pair(const Q& q, const float4* rec, float& arg, const FeatConst& fc)
+    {
+        float mult = 1.0f;
+        for (int b = 0; b < fc.n_blocks; ++b) {
+            float acc = 0.0f;
+            for (int k = 0; k < fc.dim[b]; ++k) {
+                const float u = get(q.rec, fc.off[b] + k, fc.bf16);
+                const float v = get(rec, fc.off[b] + k, fc.bf16);
+                if (fc.kind[b] == 0) {
+                    const float d = u - v;
+                    acc = fmaf(d, d, acc);
+                } else {
+                    acc = fmaf(u, v, acc);
+                }
+            }
+            if (fc.kind[b] == 0) arg = fmaf(acc, fc.s[b], arg);
+            else mult *= acc;
+        }
+        return mult;
+    }
+};
+
+// ---- the sweep --------------------------------------------------------------
+
+__device__ __forceinline__ int floor_cell(float v, float o, float inv_h)
+{
+    const float c = floorf((v - o) * inv_h);
+    return (int)fminf(fmaxf(c, -2.0e9f), 2.0e9f);
+}
+
+template <class Feat>
+__global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
+{
+    __shared__ float red[kSweepWarps][kStatN];
+    __shared__ unsigned long long redc[kSweepWarps][2];
+    const IterState* st = a.st;
+    if (st->done) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const LevelDesc L = a.levels[st->level];
+    const int rs = a.rs;
+    const bool dense = a.dense != 0;
+    float Ahi[9], Alo[9], bhi[3], blo[3], chi[3], clo[3];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) { Ahi[k] = st->Ahi[k]; Alo[k] = st->Alo[k]; }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { bhi[k] = st->bhi[k]; blo[k] = st->blo[k]; chi[k] = st->chi[k]; clo[k] = st->clo[k]; }
+    const float sg = st->sg, rc = st->rc, rc2 = st->rc2;
+    const FeatConst fc = a.fc;
+
+    float acc[kStatN];
+#pragma unroll
+    for (int k = 0; k < kStatN; ++k) acc[k] = 0.0f;
+    unsigned npairs = 0, ncand = 0;
+
+    const int nitems = L.ngroups * kChunks;
+    for (int item = blockIdx.x * kSweepWarps + warp; item < nitems; item += gridDim.x * kSweepWarps) {
+        const int g = item / kChunks;
+        const int k = item - g * kChunks;
+        const int2 grp = L.groups[g];
+        const bool act = lane < grp.y;
+        const int qi = grp.x + (act ? lane : 0);
+        const float4* qrec = a.xrec + (size_t)qi * rs;
+        const float4 xq4 = __ldg(qrec);
+        const float xq[3] = {xq4.x, xq4.y, xq4.z};
+        float xh[3], xl[3];
+        transform_df(xq, Ahi, Alo, bhi, blo, xh, xl);
+
+        // candidate stream: runs of cells (one per (y, z) cell row)
+        int cx0 = 0, cx1 = 0, cy0 = 0, cz0 = 0, nry = 1, nruns = 1;
+        if (!dense) {
+            float mn[3], mx[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                mn[r] = act ? xh[r] : 3.0e38f;
+                mx[r] = act ? xh[r] : -3.0e38f;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    mn[r] = fminf(mn[r], __shfl_xor_sync(kFull, mn[r], o));
+                    mx[r] = fmaxf(mx[r], __shfl_xor_sync(kFull, mx[r], o));
+                }
+            }
+            const float o3[3] = {L.ox, L.oy, L.oz};
+            const int n3[3] = {L.nx, L.ny, L.nz};
+            int c0[3], c1[3];
+            bool empty = false;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const float pad = rc * 1.0001f + 4.0e-7f * fmaxf(fabsf(mn[r]), fabsf(mx[r])) + 1.0e-6f;
+                c0[r] = floor_cell(mn[r] - pad, o3[r], L.inv_h);
+                c1[r] = floor_cell(mx[r] + pad, o3[r], L.inv_h);
+                if (c1[r] < 0 || c0[r] > n3[r] - 1) empty = true;
+                c0[r] = max(c0[r], 0);
+                c1[r] = min(c1[r], n3[r] - 1);
+            }
+            if (empty) continue;
+            cx0 = c0[0]; cx1 = c1[0]; cy0 = c0[1]; cz0 = c0[2];
+            nry = c1[1] - c0[1] + 1;
+            nruns = nry * (c1[2] - c0[2] + 1);
+        }
+        // total stream length
+        int total = 0;
+        for (int b0 = 0; b0 < nruns; b0 += 32) {
+            int len = 0;
+            const int r = b0 + lane;
+            if (r < nruns) {
+                if (dense) {
+                    len = a.m;
+                } else {
+                    const int cy = cy0 + r % nry, cz = cz0 + r / nry;
+                    const int row = (cz * L.ny + cy) * L.nx;
+                    len = __ldg(L.cell_start + row + cx1 + 1) - __ldg(L.cell_start + row + cx0);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) len += __shfl_xor_sync(kFull, len, o);
+            total += len;
+        }
+        if (total == 0) continue;
+        const int nch = min(kChunks, (total + kChunkMin - 1) / kChunkMin);
+        if (k >= nch) continue;
+        const int clo_ = (int)(((long long)total * k) / nch);
+        const int chi_ = (int)(((long long)total * (k + 1)) / nch);
+
+        typename Feat::Q qf;
+        Feat::load_query(qf, qrec, fc);
+        float W = 0.f, E0 = 0.f, E1 = 0.f, E2 = 0.f;
+        float Qxx = 0.f, Qyy = 0.f, Qzz = 0.f, Qxy = 0.f, Qxz = 0.f, Qyz = 0.f;
+
+        int base = 0;
+        for (int b0 = 0; b0 < nruns && base < chi_; b0 += 32) {
+            int rstart = 0, rlen = 0;
+            const int r = b0 + lane;
+            if (r < nruns) {
+                if (dense) {
+                    rstart = 0;
+                    rlen = a.m;
+                } else {
+                    const int cy = cy0 + r % nry, cz = cz0 + r / nry;
+                    const int row = (cz * L.ny + cy) * L.nx;
+                    rstart = __ldg(L.cell_start + row + cx0);
+                    rlen = __ldg(L.cell_start + row + cx1 + 1) - rstart;
+                }
+            }
+            int incl = rlen;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int roff = incl - rlen;
+            const int btotal = __shfl_sync(kFull, incl, 31);
+            int pos = max(clo_, base);
+            const int end = min(chi_, base + btotal);
+            while (pos < end) {
+                const int rel = pos - base;
+                const unsigned before = __ballot_sync(kFull, (r < nruns) && (roff + rlen <= rel));
+                const int ri = __popc(before);
+                const int s0 = __shfl_sync(kFull, rstart, ri);
+                const int o0 = __shfl_sync(kFull, roff, ri);
+                const int l0 = __shfl_sync(kFull, rlen, ri);
+                const int j0 = s0 + (rel - o0);
+                const int cnt = min(o0 + l0 - rel, end - pos);
+                for (int t = 0; t < cnt; ++t) {
+                    const float4* zr = L.zrec + (size_t)(j0 + t) * rs;
+                    const float4 z = __ldg(zr);
+                    const float dx = __fsub_rn(__fsub_rn(z.x, xh[0]), xl[0]);
+                    const float dy = __fsub_rn(__fsub_rn(z.y, xh[1]), xl[1]);
+                    const float dz = __fsub_rn(__fsub_rn(z.z, xh[2]), xl[2]);
+                    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const bool in = act && (dense || d2 <= rc2);
+                    ncand += act ? 1u : 0u;
+                    if (__any_sync(kFull, in)) {
+                        float arg = d2 * sg;
+                        const float mult = Feat::pair(qf, zr, arg, fc);
+                        const float w = in ? ex2(arg) * mult : 0.0f;
+                        npairs += in ? 1u : 0u;
+                        W += w;
+                        const float wx = w * dx, wy = w * dy, wz = w * dz;
+                        E0 += wx; E1 += wy; E2 += wz;
+                        Qxx = fmaf(wx, dx, Qxx); Qyy = fmaf(wy, dy, Qyy); Qzz = fmaf(wz, dz, Qzz);
+                        Qxy = fmaf(wx, dy, Qxy); Qxz = fmaf(wx, dz, Qxz); Qyz = fmaf(wy, dz, Qyz);
+                    }
+                }
+                pos += cnt;
+            }
+            base += btotal;
+        }
+        if (act) {
+            // lever arm p = x' - c
+            const float p0 = (xh[0] - chi[0]) + (xl[0] - clo[0]);
+            const float p1 = (xh[1] - chi[1]) + (xl[1] - clo[1]);
+            const float p2 = (xh[2] - chi[2]) + (xl[2] - clo[2]);
+            const float Q[3][3] = {{Qxx, Qxy, Qxz}, {Qxy, Qyy, Qyz}, {Qxz, Qyz, Qzz}};
+            float PQ[3][3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                PQ[0][c] = -p2 * Q[1][c] + p1 * Q[2][c];
+                PQ[1][c] = p2 * Q[0][c] - p0 * Q[2][c];
+                PQ[2][c] = -p1 * Q[0][c] + p0 * Q[1][c];
+            }
+            acc[ST_W] += W;
+            acc[ST_E + 0] += E0; acc[ST_E + 1] += E1; acc[ST_E + 2] += E2;
+            acc[ST_Q + 0] += Qxx; acc[ST_Q + 1] += Qyy; acc[ST_Q + 2] += Qzz;
+            acc[ST_Q + 3] += Qxy; acc[ST_Q + 4] += Qxz; acc[ST_Q + 5] += Qyz;
+#pragma unroll
+            for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc[ST_PQ + 3 * rr + c] += PQ[rr][c];
+            // [p]x Q [p]x, symmetric: (0,0) (1,1) (2,2) (0,1) (0,2) (1,2)
+            acc[ST_PQP + 0] += PQ[0][1] * p2 - PQ[0][2] * p1;
+            acc[ST_PQP + 1] += -PQ[1][0] * p2 + PQ[1][2] * p0;
+            acc[ST_PQP + 2] += PQ[2][0] * p1 - PQ[2][1] * p0;
+            acc[ST_PQP + 3] += -PQ[0][0] * p2 + PQ[0][2] * p0;
+            acc[ST_PQP + 4] += PQ[0][0] * p1 - PQ[0][1] * p0;
+            acc[ST_PQP + 5] += PQ[1][0] * p1 - PQ[1][1] * p0;
+            const float Wp0 = W * p0, Wp1 = W * p1, Wp2 = W * p2;
+            acc[ST_WP + 0] += Wp0; acc[ST_WP + 1] += Wp1; acc[ST_WP + 2] += Wp2;
+            acc[ST_WPP + 0] += Wp0 * p0; acc[ST_WPP + 1] += Wp1 * p1; acc[ST_WPP + 2] += Wp2 * p2;
+            acc[ST_WPP + 3] += Wp0 * p1; acc[ST_WPP + 4] += Wp0 * p2; acc[ST_WPP + 5] += Wp1 * p2;
+            const float Ev[3] = {E0, E1, E2}, pv[3] = {p0, p1, p2};
+#pragma unroll
+            for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc[ST_EP + 3 * rr + c] += Ev[rr] * pv[c];
+        }
+    }
+
+    // warp tree (FP32, fixed order), then the block's warps in double-float
+#pragma unroll
+    for (int k = 0; k < kStatN; ++k) {
+        float v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        if (lane == 0) red[warp][k] = v;
+    }
+    unsigned long long cp = npairs, cc = ncand;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cp += __shfl_xor_sync(kFull, cp, o);
+        cc += __shfl_xor_sync(kFull, cc, o);
+    }
+    if (lane == 0) {
+        redc[warp][0] = cp;
+        redc[warp][1] = cc;
+    }
+    __syncthreads();
+    if (threadIdx.x < kStatN) {
+        float hi = 0.0f, lo = 0.0f;
+        for (int w = 0; w < kSweepWarps; ++w) {
+            float s, e;
+            two_sum(hi, red[w][threadIdx.x], s, e);
+            e = __fadd_rn(e, lo);
+            hi = __fadd_rn(s, e);
+            lo = __fsub_rn(e, __fsub_rn(hi, s));
+        }
+        a.part_stats[(size_t)threadIdx.x * a.part_cap + blockIdx.x] = make_float2(hi, lo);
+    } else if (threadIdx.x == kStatN) {
+        unsigned long long t0 = 0, t1 = 0;
+        for (int w = 0; w < kSweepWarps; ++w) {
+            t0 += redc[w][0];
+            t1 += redc[w][1];
+        }
+        a.part_cnt[blockIdx.x] = t0;
+        a.part_cnt[(size_t)a.part_cap + blockIdx.x] = t1;
+    }
+}
+
+template <class Feat>
+cudaError_t launch_t(const SweepArgs& a, int nblocks, cudaStream_t s)
+{
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    k_sweep<Feat><<<nblocks, kSweepWarps * 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Picks the feature specialisation for the handle's block list.
+cudaError_t launch_sweep(const SweepArgs& a, int nblocks, cudaStream_t s)
+{
+    const FeatConst& f = a.fc;
+    if (f.n_blocks == 0) return launch_t<FeatNone>(a, nblocks, s);
+    const bool se3 = f.n_blocks >= 1 && f.kind[0] == 0 && f.dim[0] == 3;
+    if (f.n_blocks == 1 && se3) {
+        return f.bf16 ? launch_t<FeatFixed<3, 0, true>>(a, nblocks, s) : launch_t<FeatFixed<3, 0, false>>(a, nblocks, s);
+    }
+    if (f.n_blocks == 2 && se3 && f.kind[1] == 1 && f.dim[1] == 19) {
+        return f.bf16 ? launch_t<FeatFixed<3, 19, true>>(a, nblocks, s)
+                      : launch_t<FeatFixed<3, 19, false>>(a, nblocks, s);
+    }
+    if (f.n_blocks == 1 && f.kind[0] == 1 && f.dim[0] == 19) {
+        return f.bf16 ? launch_t<FeatFixed<0, 19, true>>(a, nblocks, s)
+                      : launch_t<FeatFixed<0, 19, false>>(a, nblocks, s);
+    }
+    return launch_t<FeatGeneric>(a, nblocks, s);
+}
+
+}  // namespace cvo
