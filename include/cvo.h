@@ -186,6 +186,42 @@ const char* cvo_version(void);
  * handles, all threads), for launch accounting by benchmarks. */
 long long cvo_kernel_launches(void);
 
+/* Dense evaluation that allocates nothing.  This entry point is an addition
+ * of this library: the paper has no counterpart.
+ *
+ * Who needs it: callers that must not allocate device memory once they are
+ * running -- a real-time odometry loop that fixed its memory budget at
+ * start-up (cudaMalloc / cudaFree can synchronise the device and stall the
+ * loop, or fail half way through a run), or a plugin inside a host
+ * application whose memory pool owns the GPU.  The handle-based calls above
+ * allocate scratch on demand, so they cannot serve these callers.
+ *
+ * What it computes: the same F, gradient, Hessian, indicator and pair counts
+ * as cvo_evaluate with cutoff_mult <= 0 (every pair), with the same kernels.
+ * It needs no handle and calls no cudaMalloc, cudaFree or other allocating
+ * routine: all scratch lives in one fixed 4.5 MiB array inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ *
+ * Arguments: params as for cvo_create (cutoff_mult must be <= 0); cuda_stream
+ * a cudaStream_t (NULL: legacy default stream); X and Z with on_device = 1
+ * (device pointers, float32 or bfloat16 features); T a host row-major pose;
+ * out_device a DEVICE pointer to one cvo_eval that receives the results.
+ *
+ * Limits: at most 16384 points per cloud and 24 feature entries per point;
+ * larger requests return CVO_ERR_INVALID_ARG with a message naming the limit.
+ *
+ * Behaviour: asynchronous -- the work is queued on cuda_stream and
+ * *out_device is valid once the stream has reached it.  Because the call does
+ * not wait for the GPU, non-finite coordinates or features are reported as
+ * NaN results, not as an error code.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call reuses the same
+ * array, which keeps the previous call's contents (each call rewrites all it
+ * reads): calls that overlap on the GPU -- on two streams, or from two host
+ * threads on one device -- race and must be serialised by the caller. */
+cvo_status cvo_evaluate_dense_noalloc(const cvo_params* params, void* cuda_stream, const cvo_cloud* X,
+                                      const cvo_cloud* Z, const double T[16], cvo_eval* out_device);
+
 #ifdef __cplusplus
 }
 #endif

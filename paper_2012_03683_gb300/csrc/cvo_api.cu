@@ -19,6 +19,10 @@ using namespace cvo;
 
 std::atomic<long long> cvo::g_launch_count{0};
 
+namespace cvo {
+void set_error_message(const char* msg);
+}
+
 namespace {
 
 thread_local std::string g_err;
@@ -93,6 +97,9 @@ float decode_orderable(unsigned u)
 }
 
 }  // namespace
+
+// Lets other translation units report an error through cvo_last_error().
+void cvo::set_error_message(const char* msg) { g_err = msg ? msg : ""; }
 
 struct cvo_handle_s {
     cvo_params p{};
