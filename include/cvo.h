@@ -170,6 +170,12 @@ cvo_status cvo_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
  * of iterations, or a negative cvo_status. */
 int cvo_get_trace(cvo_handle h, double* out, int cap);
 
+/* Tuning of the neighbour sweep (performance only; results do not depend on
+ * it beyond rounding): grid cell edge = cell_factor * cutoff radius
+ * (0.25..4), query groups drawn from Morton super-cells about
+ * 2^super_delta cutoff radii wide (-2..6).  Defaults 0.5 and 2. */
+cvo_status cvo_set_tuning(cvo_handle h, double cell_factor, int super_delta);
+
 /* Average device time (ms) of the sweep kernel over the handle's last
  * registration, measured with CUDA events around each sweep launch when
  * timing is on (cvo_set_timing), and the number of sweep launches timed. */

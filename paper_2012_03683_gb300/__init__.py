@@ -109,6 +109,8 @@ def load_library(build_if_missing: bool = True):
     lib.cvo_register_batch.argtypes = [vp, ctypes.c_int, P(Cloud), P(Cloud), vp, vp, P(Info)]
     lib.cvo_get_trace.argtypes = [vp, vp, ctypes.c_int]
     lib.cvo_set_timing.argtypes = [vp, ctypes.c_int]
+    lib.cvo_set_tuning.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+    lib.cvo_set_tuning.restype = ctypes.c_int
     lib.cvo_sweep_time.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int)]
     for name in ("cvo_create", "cvo_destroy", "cvo_set_params", "cvo_inner_product", "cvo_metric", "cvo_gradient",
                  "cvo_evaluate", "cvo_register_pair", "cvo_register_batch", "cvo_get_trace", "cvo_set_timing",
@@ -333,6 +335,10 @@ def cvo_get_trace(h, cap=100000) -> np.ndarray:
 
 def cvo_set_timing(h, on=True):
     return _check(load_library().cvo_set_timing(h, int(bool(on))))
+
+
+def cvo_set_tuning(h, cell_factor=0.5, super_delta=2):
+    return _check(load_library().cvo_set_tuning(h, float(cell_factor), int(super_delta)))
 
 
 def cvo_sweep_time(h):

@@ -77,7 +77,8 @@ void release(DevBuf& b)
 }
 
 struct LevelHost {
-    double h;
+    double h;         // cell edge
+    double rdesign;   // cutoff radius the level is built for (cell edge = cell_factor * rdesign)
     int nx, ny, nz;
     float ox, oy, oz;
     long long ncells;
@@ -125,6 +126,10 @@ struct cvo_handle_s {
     int sweep_blocks = 1;
     FeatConst fc{};
     double kappa = 1.0;
+    // tuning: grid cell edge = cell_factor * cutoff radius; query groups live in
+    // Morton super-cells about 2^super_delta cutoff radii wide
+    double cell_factor = 0.5;
+    int super_delta = 2;
 };
 
 namespace {
@@ -308,6 +313,7 @@ cvo_status prepare(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, double 
         h->nlevels = 1;
         LevelHost& L = h->lv[0];
         L.h = 1.0;
+        L.rdesign = 1.0;
         L.nx = L.ny = L.nz = 1;
         L.ox = zmin[0]; L.oy = zmin[1]; L.oz = zmin[2];
         L.ncells = 1;
@@ -318,7 +324,8 @@ cvo_status prepare(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, double 
         h->nlevels = nl;
         for (int k = 0; k < nl; ++k) {
             LevelHost& L = h->lv[k];
-            double hh = rc_hi * 1.0002 / std::pow(std::sqrt(2.0), k);
+            L.rdesign = rc_hi * 1.0002 / std::pow(std::sqrt(2.0), k);
+            double hh = h->cell_factor * L.rdesign;
             for (;;) {
                 L.nx = (int)std::floor(((double)zmax[0] - zmin[0]) / hh) + 1;
                 L.ny = (int)std::floor(((double)zmax[1] - zmin[1]) / hh) + 1;
@@ -375,7 +382,9 @@ cvo_status prepare(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, double 
         LevelHost& L = h->lv[k];
         int sh = 30;
         if (!h->dense) {
-            const int e = (int)std::floor(std::log2(L.h / cell0));
+            // Morton super-cells of edge about 2^super_delta times the
+            // level's cutoff radius hold the query groups
+            const int e = (int)std::floor(std::log2(L.rdesign / cell0)) + h->super_delta;
             sh = 3 * std::max(0, std::min(10, e));
         }
         L.shift = sh;
@@ -457,7 +466,7 @@ cvo_status init_state(cvo_handle h, const double* T, double ell, int mode)
     st->status = 1;
     for (int a = 0; a < 3; ++a) st->c[a] = h->zc[a];
     st->nlevels = h->nlevels;
-    for (int k = 0; k < h->nlevels; ++k) st->level_h[k] = (float)h->lv[k].h;
+    for (int k = 0; k < h->nlevels; ++k) st->level_h[k] = (float)h->lv[k].rdesign;
     if (mode == 1 && p.max_iters == 0) st->done = 1;
     CVO_CUDA(ensure(h->state, sizeof(IterState)));
     CVO_CUDA(cudaMemcpyAsync(h->state.p, st, sizeof(IterState), cudaMemcpyHostToDevice, h->s));
@@ -748,6 +757,16 @@ int cvo_get_trace(cvo_handle h, double* out, int cap)
             return fail(CVO_ERR_CUDA, "trace copy failed");
     }
     return h->last_iters;
+}
+
+cvo_status cvo_set_tuning(cvo_handle h, double cell_factor, int super_delta)
+{
+    if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
+    if (!(cell_factor >= 0.25 && cell_factor <= 4.0)) return fail(CVO_ERR_INVALID_ARG, "cell_factor must be in [0.25, 4]");
+    if (super_delta < -2 || super_delta > 6) return fail(CVO_ERR_INVALID_ARG, "super_delta must be in [-2, 6]");
+    h->cell_factor = cell_factor;
+    h->super_delta = super_delta;
+    return CVO_OK;
 }
 
 cvo_status cvo_set_timing(cvo_handle h, int on)

@@ -4,20 +4,25 @@
 // 1. Sums the 43 statistics over the sweep blocks in double-float (hi + lo
 //    FP32 pairs, error-free two-sum), one warp per statistic, in block order:
 //    deterministic, and as accurate as FP64 accumulation at FP32 speed.
-// 2. In FP64 (one thread): F = kappa S_W; the gradient and Hessian of
-//    eta -> F(T exp(eta^)) about the lever centre c in Z's frame; mapped to the
-//    left perturbation exp(xi^) T by xi_c = A Ad_{T^-1} xi,
-//    A = [[I, 0], [-[c]x, I]].  The indicator of Eq. (indicator_actual) is
-//    F / sqrt(N M).
+// 2. In FP64 (one thread): F = kappa S_W; the gradient of
+//    eta -> F(T exp(eta^)) about the lever centre c in Z's frame, mapped to
+//    the left perturbation exp(xi^) T.  With gc = (gc_w, gc_v) the centred
+//    gradient, R, t the pose:  g_v = R gc_v,  g_w = R (gc_w + c x gc_v) + t x g_v.
+//    The indicator of Eq. (indicator_actual) is F / sqrt(N M).
 // 3. Registration: the step along the gradient (the method is gradient ascent
 //    on SE(3), Sec. I), t = |g|^2 / -F'' with F'' = g^T H g when negative,
 //    else 1e-3 / |g|; the clamps; T <- exp(t g^) T (closed-form SE(3)
 //    exponential, Rodrigues + left Jacobian); Gram-Schmidt on R every 16
 //    iterations; the stopping test; the lengthscale annealing of Sec. IV
 //    (l <- max(decay l, l_min) once the indicator at the current l changes by
-//    less than indicator_tol relative).
+//    less than indicator_tol relative).  F'' is the quadratic form of the
+//    centred Hessian at (w~, v~) = (R^T g_w, -c x w~ + R^T (g_v - t x g_w)).
 // 4. Writes the derived constants of the next sweep (double-float T^-1,
 //    exponent scale, cutoff, grid level).
+// An evaluation (no step) also assembles the full 6x6 Hessian.
+//
+// GB300 runs FP64 at 1/72 of the FP32 rate, so this serial code is kept to
+// closed forms (no 6x6 products on the registration path).
 #include <math.h>
 
 #include "cvo_internal.cuh"
@@ -41,72 +46,114 @@ __device__ __forceinline__ void split_df(double v, float& hi, float& lo)
     lo = (float)(v - (double)hi);
 }
 
-__device__ void skew3(const double a[3], double M[9])
+struct V3 {
+    double x, y, z;
+};
+__device__ __forceinline__ V3 v3(double x, double y, double z) { return {x, y, z}; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+__device__ __forceinline__ double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 add(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 sub(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 scale(V3 a, double s) { return {a.x * s, a.y * s, a.z * s}; }
+// R a and R^T a with R the rotation block of a row-major 4x4 pose
+__device__ __forceinline__ V3 rmul(const double* T, V3 a)
 {
-    M[0] = 0.0;   M[1] = -a[2]; M[2] = a[1];
-    M[3] = a[2];  M[4] = 0.0;   M[5] = -a[0];
-    M[6] = -a[1]; M[7] = a[0];  M[8] = 0.0;
+    return {T[0] * a.x + T[1] * a.y + T[2] * a.z, T[4] * a.x + T[5] * a.y + T[6] * a.z,
+            T[8] * a.x + T[9] * a.y + T[10] * a.z};
+}
+__device__ __forceinline__ V3 rtmul(const double* T, V3 a)
+{
+    return {T[0] * a.x + T[4] * a.y + T[8] * a.z, T[1] * a.x + T[5] * a.y + T[9] * a.z,
+            T[2] * a.x + T[6] * a.y + T[10] * a.z};
+}
+// a^T M b with M symmetric from (xx, yy, zz, xy, xz, yz)
+__device__ __forceinline__ double symq(const double* m, V3 a, V3 b)
+{
+    return m[0] * a.x * b.x + m[1] * a.y * b.y + m[2] * a.z * b.z + m[3] * (a.x * b.y + a.y * b.x) +
+           m[4] * (a.x * b.z + a.z * b.x) + m[5] * (a.y * b.z + a.z * b.y);
+}
+// a^T M b with M full 3x3 row major
+__device__ __forceinline__ double fullq(const double* m, V3 a, V3 b)
+{
+    return a.x * (m[0] * b.x + m[1] * b.y + m[2] * b.z) + a.y * (m[3] * b.x + m[4] * b.y + m[5] * b.z) +
+           a.z * (m[6] * b.x + m[7] * b.y + m[8] * b.z);
 }
 
-// exp of xi = (omega, v) in SE(3), row-major 4x4
-__device__ void se3_exp_dev(const double xi[6], double E[16])
+// sin(th)/th, (1 - cos th)/th^2, (th - sin th)/th^3: Taylor series in th^2
+// (alternating series, truncation below 1e-19 for th < 0.5), else sincos.
+__device__ void se3_coeffs(double th2, double& a, double& b, double& c)
 {
-    const double wx = xi[0], wy = xi[1], wz = xi[2];
-    const double th2 = wx * wx + wy * wy + wz * wz;
-    const double th = sqrt(th2);
-    double a, b, c;   // sin(th)/th, (1-cos th)/th^2, (th - sin th)/th^3
-    if (th < 1e-3) {
-        a = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
-        b = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
-        c = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
+    if (th2 < 0.25) {
+        // Horner in th^2 over 1/(2k+1)!, 1/(2k+2)!, 1/(2k+3)!, k = 8 .. 0
+        double pa = 1.0 / 355687428096000.0, pb = 1.0 / 6402373705728000.0, pc = 1.0 / 121645100408832000.0;
+        const double fa[8] = {1.0 / 1307674368000.0, 1.0 / 6227020800.0, 1.0 / 39916800.0, 1.0 / 362880.0,
+                              1.0 / 5040.0, 1.0 / 120.0, 1.0 / 6.0, 1.0};
+        const double fb[8] = {1.0 / 20922789888000.0, 1.0 / 87178291200.0, 1.0 / 479001600.0, 1.0 / 3628800.0,
+                              1.0 / 40320.0, 1.0 / 720.0, 1.0 / 24.0, 1.0 / 2.0};
+        const double fc[8] = {1.0 / 355687428096000.0, 1.0 / 1307674368000.0, 1.0 / 6227020800.0,
+                              1.0 / 39916800.0, 1.0 / 362880.0, 1.0 / 5040.0, 1.0 / 120.0, 1.0 / 6.0};
+        for (int k = 0; k < 8; ++k) {
+            pa = fa[k] - th2 * pa;
+            pb = fb[k] - th2 * pb;
+            pc = fc[k] - th2 * pc;
+        }
+        a = pa;
+        b = pb;
+        c = pc;
     } else {
+        const double th = sqrt(th2);
         double s, co;
         sincos(th, &s, &co);
         a = s / th;
         b = (1.0 - co) / th2;
         c = (th - s) / (th2 * th);
     }
-    double K[9], K2[9];
-    const double w[3] = {wx, wy, wz};
-    skew3(w, K);
+}
+
+// exp of xi = (omega, v) in SE(3), row-major 4x4
+__device__ void se3_exp_dev(const double xi[6], double E[16])
+{
+    const V3 w = v3(xi[0], xi[1], xi[2]);
+    const V3 v = v3(xi[3], xi[4], xi[5]);
+    double a, b, c;
+    se3_coeffs(dot(w, w), a, b, c);
+    // R = I + a W + b W^2, V v = v + b (w x v) + c (w x (w x v)); W^2 = w w^T - |w|^2 I
+    const double ww = dot(w, w);
+    const double W[9] = {0.0, -w.z, w.y, w.z, 0.0, -w.x, -w.y, w.x, 0.0};
+    const double wv[3] = {w.x, w.y, w.z};
     for (int r = 0; r < 3; ++r)
-        for (int q = 0; q < 3; ++q) K2[3 * r + q] = K[3 * r] * K[q] + K[3 * r + 1] * K[3 + q] + K[3 * r + 2] * K[6 + q];
-    for (int r = 0; r < 3; ++r) {
-        double tv = 0.0;
         for (int q = 0; q < 3; ++q) {
-            const double id = (r == q) ? 1.0 : 0.0;
-            E[4 * r + q] = id + a * K[3 * r + q] + b * K2[3 * r + q];
-            tv += (id + b * K[3 * r + q] + c * K2[3 * r + q]) * xi[3 + q];
+            const double w2 = wv[r] * wv[q] - (r == q ? ww : 0.0);
+            E[4 * r + q] = (r == q ? 1.0 : 0.0) + a * W[3 * r + q] + b * w2;
         }
-        E[4 * r + 3] = tv;
-    }
+    const V3 wxv = cross(w, v);
+    const V3 wxwxv = cross(w, wxv);
+    E[3] = v.x + b * wxv.x + c * wxwxv.x;
+    E[7] = v.y + b * wxv.y + c * wxwxv.y;
+    E[11] = v.z + b * wxv.z + c * wxwxv.z;
     E[12] = 0.0; E[13] = 0.0; E[14] = 0.0; E[15] = 1.0;
 }
 
-__device__ void mul44(const double A[16], const double B[16], double C[16])
+// T <- E T for rigid motions (last rows (0, 0, 0, 1))
+__device__ void compose(const double E[16], double T[16])
 {
-    double t[16];
-    for (int r = 0; r < 4; ++r)
+    double t[12];
+    for (int r = 0; r < 3; ++r)
         for (int q = 0; q < 4; ++q)
-            t[4 * r + q] = A[4 * r] * B[q] + A[4 * r + 1] * B[4 + q] + A[4 * r + 2] * B[8 + q] + A[4 * r + 3] * B[12 + q];
-    for (int k = 0; k < 16; ++k) C[k] = t[k];
+            t[4 * r + q] = E[4 * r] * T[q] + E[4 * r + 1] * T[4 + q] + E[4 * r + 2] * T[8 + q] + (q == 3 ? E[4 * r + 3] : 0.0);
+    for (int k = 0; k < 12; ++k) T[k] = t[k];
 }
 
 __device__ void orthonormalize(double T[16])
 {
-    double c0[3] = {T[0], T[4], T[8]}, c1[3] = {T[1], T[5], T[9]};
-    const double n0 = sqrt(c0[0] * c0[0] + c0[1] * c0[1] + c0[2] * c0[2]);
-    for (int r = 0; r < 3; ++r) c0[r] /= n0;
-    const double d = c0[0] * c1[0] + c0[1] * c1[1] + c0[2] * c1[2];
-    for (int r = 0; r < 3; ++r) c1[r] -= d * c0[r];
-    const double n1 = sqrt(c1[0] * c1[0] + c1[1] * c1[1] + c1[2] * c1[2]);
-    for (int r = 0; r < 3; ++r) c1[r] /= n1;
-    const double c2[3] = {c0[1] * c1[2] - c0[2] * c1[1], c0[2] * c1[0] - c0[0] * c1[2], c0[0] * c1[1] - c0[1] * c1[0]};
-    for (int r = 0; r < 3; ++r) {
-        T[4 * r] = c0[r];
-        T[4 * r + 1] = c1[r];
-        T[4 * r + 2] = c2[r];
-    }
+    V3 c0 = v3(T[0], T[4], T[8]), c1 = v3(T[1], T[5], T[9]);
+    c0 = scale(c0, 1.0 / sqrt(dot(c0, c0)));
+    c1 = sub(c1, scale(c0, dot(c0, c1)));
+    c1 = scale(c1, 1.0 / sqrt(dot(c1, c1)));
+    const V3 c2 = cross(c0, c1);
+    T[0] = c0.x; T[4] = c0.y; T[8] = c0.z;
+    T[1] = c1.x; T[5] = c1.y; T[9] = c1.z;
+    T[2] = c2.x; T[6] = c2.y; T[10] = c2.z;
 }
 
 // Constants the next sweep reads.
@@ -144,6 +191,70 @@ __global__ void k_init_state(IterState* st)
 {
     for (int r = 0; r < 3; ++r) split_df(st->c[r], st->chi[r], st->clo[r]);
     update_derived(st);
+}
+
+// Full Hessian of xi -> F(exp(xi^) T) (evaluation only): H = B^T Hc B with
+// B = [[R^T, 0], [-[c]x R^T - R^T [t]x, R^T]].
+__device__ void full_hessian(const double* s, double L2, double L4, const double* T, const double* c, double* H)
+{
+    double Hc[36];
+    const double* Q = s + ST_Q;
+    const double* PQP = s + ST_PQP;
+    const double* Wpp = s + ST_WPP;
+    const double* PQ = s + ST_PQ;
+    const double* Ep = s + ST_EP;
+    const double* E = s + ST_E;
+    const double* Wp = s + ST_WP;
+    const double W = s[ST_W];
+    auto symv = [](const double* m, int r, int q) {
+        if (r == q) return m[r];
+        const int a = r < q ? r : q, b = r < q ? q : r;
+        return a == 0 ? (b == 1 ? m[3] : m[4]) : m[5];
+    };
+    auto skew = [](const double* a, int r, int q) {
+        const double M[9] = {0.0, -a[2], a[1], a[2], 0.0, -a[0], -a[1], a[0], 0.0};
+        return M[3 * r + q];
+    };
+    const double trWpp = Wpp[0] + Wpp[1] + Wpp[2];
+    const double trEp = Ep[0] + Ep[4] + Ep[8];
+    for (int r = 0; r < 3; ++r)
+        for (int q = 0; q < 3; ++q) {
+            const double id = (r == q) ? 1.0 : 0.0;
+            Hc[6 * r + q] = -symv(PQP, r, q) / L4 - (trWpp * id - symv(Wpp, r, q)) / L2 +
+                            0.5 * (Ep[3 * r + q] + Ep[3 * q + r] - 2.0 * trEp * id) / L2;
+            const double hwv = PQ[3 * r + q] / L4 - skew(Wp, r, q) / L2 - 0.5 * skew(E, r, q) / L2;
+            Hc[6 * r + 3 + q] = hwv;
+            Hc[6 * (3 + q) + r] = hwv;
+            Hc[6 * (3 + r) + 3 + q] = symv(Q, r, q) / L4 - W * id / L2;
+        }
+    double B[36];
+    for (int k = 0; k < 36; ++k) B[k] = 0.0;
+    const double tv[3] = {T[3], T[7], T[11]};
+    for (int r = 0; r < 3; ++r)
+        for (int q = 0; q < 3; ++q) {
+            const double rt = T[4 * q + r];
+            B[6 * r + q] = rt;
+            B[6 * (3 + r) + 3 + q] = rt;
+            double a1 = 0.0, a2 = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                a1 += skew(c, r, k) * T[4 * q + k];
+                a2 += T[4 * k + r] * skew(tv, k, q);
+            }
+            B[6 * (3 + r) + q] = -a1 - a2;
+        }
+    double HB[36];
+    for (int r = 0; r < 6; ++r)
+        for (int q = 0; q < 6; ++q) {
+            double acc = 0.0;
+            for (int k = 0; k < 6; ++k) acc += Hc[6 * r + k] * B[6 * k + q];
+            HB[6 * r + q] = acc;
+        }
+    for (int r = 0; r < 6; ++r)
+        for (int q = 0; q < 6; ++q) {
+            double acc = 0.0;
+            for (int k = 0; k < 6; ++k) acc += B[6 * k + r] * HB[6 * k + q];
+            H[6 * r + q] = acc;
+        }
 }
 
 __global__ void __launch_bounds__(kFinalizeThreads)
@@ -190,82 +301,17 @@ k_finalize(IterState* st, const float2* __restrict__ ps, const unsigned long lon
     }
     const double kap = st->kappa;
     const double ell = st->ell, L2 = ell * ell, L4 = L2 * L2;
-    double s[kStatN];
-    for (int k = 0; k < kStatN; ++k) s[k] = kap * S[k];
-    const double F = s[ST_W];
-
-    // symmetric 3x3 from (xx, yy, zz, xy, xz, yz)
-    auto sym = [](const double* v, double M[9]) {
-        M[0] = v[0]; M[4] = v[1]; M[8] = v[2];
-        M[1] = M[3] = v[3]; M[2] = M[6] = v[4]; M[5] = M[7] = v[5];
-    };
-    double Q[9], PQP[9], Wpp[9];
-    sym(s + ST_Q, Q);
-    sym(s + ST_PQP, PQP);
-    sym(s + ST_WPP, Wpp);
-    const double* PQ = s + ST_PQ;
-    const double* Ep = s + ST_EP;
-    const double* E = s + ST_E;
-    const double* Wp = s + ST_WP;
-    const double W = s[ST_W];
-    // gradient in the centred Z-frame coordinates
-    double gc[6];
-    gc[0] = (Ep[5] - Ep[7]) / L2;   // (E x p)_0 = Ep[1][2] - Ep[2][1]
-    gc[1] = (Ep[6] - Ep[2]) / L2;   // (E x p)_1 = Ep[2][0] - Ep[0][2]
-    gc[2] = (Ep[1] - Ep[3]) / L2;   // (E x p)_2 = Ep[0][1] - Ep[1][0]
-    gc[3] = -E[0] / L2;
-    gc[4] = -E[1] / L2;
-    gc[5] = -E[2] / L2;
-    // Hessian blocks in the same coordinates
-    double Hc[36];
-    const double trWpp = Wpp[0] + Wpp[4] + Wpp[8];
-    const double trEp = Ep[0] + Ep[4] + Ep[8];
-    double KWp[9], KE[9];
-    skew3(Wp, KWp);
-    skew3(E, KE);
-    for (int r = 0; r < 3; ++r)
-        for (int q = 0; q < 3; ++q) {
-            const double id = (r == q) ? 1.0 : 0.0;
-            const double hww = -PQP[3 * r + q] / L4 - (trWpp * id - Wpp[3 * r + q]) / L2 +
-                               0.5 * (Ep[3 * r + q] + Ep[3 * q + r] - 2.0 * trEp * id) / L2;
-            const double hwv = PQ[3 * r + q] / L4 - KWp[3 * r + q] / L2 - 0.5 * KE[3 * r + q] / L2;
-            const double hvv = Q[3 * r + q] / L4 - W * id / L2;
-            Hc[6 * r + q] = hww;
-            Hc[6 * r + 3 + q] = hwv;
-            Hc[6 * (3 + q) + r] = hwv;
-            Hc[6 * (3 + r) + 3 + q] = hvv;
-        }
-    // B = A Ad_{T^-1} = [[R^T, 0], [B21, R^T]],  B21 = -[c]x R^T - R^T [t]x
-    const double* T = st->T;
-    double Rt[9], Kc[9], Kt[9], B21[9];
-    for (int r = 0; r < 3; ++r)
-        for (int q = 0; q < 3; ++q) Rt[3 * r + q] = T[4 * q + r];
-    const double tv[3] = {T[3], T[7], T[11]};
-    skew3(st->c, Kc);
-    skew3(tv, Kt);
-    for (int r = 0; r < 3; ++r)
-        for (int q = 0; q < 3; ++q) {
-            double a1 = 0.0, a2 = 0.0;
-            for (int k = 0; k < 3; ++k) {
-                a1 += Kc[3 * r + k] * Rt[3 * k + q];
-                a2 += Rt[3 * r + k] * Kt[3 * k + q];
-            }
-            B21[3 * r + q] = -a1 - a2;
-        }
-    double B[36];
-    for (int k = 0; k < 36; ++k) B[k] = 0.0;
-    for (int r = 0; r < 3; ++r)
-        for (int q = 0; q < 3; ++q) {
-            B[6 * r + q] = Rt[3 * r + q];
-            B[6 * (3 + r) + 3 + q] = Rt[3 * r + q];
-            B[6 * (3 + r) + q] = B21[3 * r + q];
-        }
-    double g[6];
-    for (int q = 0; q < 6; ++q) {
-        double acc = 0.0;
-        for (int r = 0; r < 6; ++r) acc += B[6 * r + q] * gc[r];
-        g[q] = acc;
-    }
+    const double F = kap * S[ST_W];
+    const double* Ep = S + ST_EP;
+    // centred gradient (kappa applied here)
+    const V3 gcw = scale(v3(Ep[5] - Ep[7], Ep[6] - Ep[2], Ep[1] - Ep[3]), kap / L2);
+    const V3 gcv = scale(v3(S[ST_E], S[ST_E + 1], S[ST_E + 2]), -kap / L2);
+    double* T = st->T;
+    const V3 c = v3(st->c[0], st->c[1], st->c[2]);
+    const V3 tt = v3(T[3], T[7], T[11]);
+    const V3 gv = rmul(T, gcv);
+    const V3 gw = add(rmul(T, add(gcw, cross(c, gcv))), cross(tt, gv));
+    const double g[6] = {gw.x, gw.y, gw.z, gv.x, gv.y, gv.z};
     const double ith = F * st->norm;
     st->F = F;
     st->i_theta = ith;
@@ -274,56 +320,47 @@ k_finalize(IterState* st, const float2* __restrict__ ps, const unsigned long lon
     for (int q = 0; q < 6; ++q) st->grad[q] = g[q];
 
     if (st->mode == 0) {
-        // full Hessian H = B^T Hc B
-        double HB[36];
-        for (int r = 0; r < 6; ++r)
-            for (int q = 0; q < 6; ++q) {
-                double acc = 0.0;
-                for (int k = 0; k < 6; ++k) acc += Hc[6 * r + k] * B[6 * k + q];
-                HB[6 * r + q] = acc;
-            }
-        for (int r = 0; r < 6; ++r)
-            for (int q = 0; q < 6; ++q) {
-                double acc = 0.0;
-                for (int k = 0; k < 6; ++k) acc += B[6 * k + r] * HB[6 * k + q];
-                st->hess[6 * r + q] = acc;
-            }
+        double s[kStatN];
+        for (int k = 0; k < kStatN; ++k) s[k] = kap * S[k];
+        full_hessian(s, L2, L4, T, st->c, st->hess);
         st->done = 1;
         return;
     }
 
     // ---- registration step --------------------------------------------------
     const int it = st->iter;
-    double xc[6];   // B g: the gradient direction in the centred coordinates
-    for (int r = 0; r < 6; ++r) {
-        double acc = 0.0;
-        for (int q = 0; q < 6; ++q) acc += B[6 * r + q] * g[q];
-        xc[r] = acc;
-    }
-    double Fpp = 0.0;
-    for (int r = 0; r < 6; ++r) {
-        double acc = 0.0;
-        for (int q = 0; q < 6; ++q) acc += Hc[6 * r + q] * xc[q];
-        Fpp += xc[r] * acc;
-    }
+    // the gradient direction in the centred coordinates
+    const V3 wt = rtmul(T, gw);
+    const V3 vt = add(scale(cross(c, wt), -1.0), rtmul(T, sub(gv, cross(tt, gw))));
+    // F'' = w~^T Hww w~ + 2 w~^T Hwv v~ + v~^T Hvv v~ (centred Hessian blocks)
+    const double trWpp = S[ST_WPP] + S[ST_WPP + 1] + S[ST_WPP + 2];
+    const double trEp = Ep[0] + Ep[4] + Ep[8];
+    const double ww = dot(wt, wt), vv = dot(vt, vt);
+    const double hww = -symq(S + ST_PQP, wt, wt) / L4 - (trWpp * ww - symq(S + ST_WPP, wt, wt)) / L2 +
+                       (fullq(Ep, wt, wt) - trEp * ww) / L2;
+    const V3 Ev = v3(S[ST_E], S[ST_E + 1], S[ST_E + 2]);
+    const V3 Wpv = v3(S[ST_WP], S[ST_WP + 1], S[ST_WP + 2]);
+    const double hwv = fullq(S + ST_PQ, wt, vt) / L4 - dot(wt, cross(Wpv, vt)) / L2 - 0.5 * dot(wt, cross(Ev, vt)) / L2;
+    const double hvv = symq(S + ST_Q, vt, vt) / L4 - S[ST_W] * vv / L2;
+    const double Fpp = kap * (hww + 2.0 * hwv + hvv);
     double gn2 = 0.0;
     for (int q = 0; q < 6; ++q) gn2 += g[q] * g[q];
     double t = 0.0;
     if (gn2 > 0.0) {
         t = (Fpp < 0.0) ? gn2 / (-Fpp) : 1e-3 / sqrt(gn2);
-        const double wn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-        const double vn = sqrt(g[3] * g[3] + g[4] * g[4] + g[5] * g[5]);
+        const double wn = sqrt(dot(gw, gw));
+        const double vn = sqrt(dot(gv, gv));
         const double max_tr = st->max_step_trans > 0.0 ? st->max_step_trans : 0.5 * ell;
         if (t * wn > st->max_step_rot) t = st->max_step_rot / wn;
         if (t * vn > max_tr) t = max_tr / vn;
     }
     double T_k[12];
-    for (int q = 0; q < 12; ++q) T_k[q] = st->T[q];
+    for (int q = 0; q < 12; ++q) T_k[q] = T[q];
     double xi[6], Ex[16];
     for (int q = 0; q < 6; ++q) xi[q] = t * g[q];
     se3_exp_dev(xi, Ex);
-    mul44(Ex, st->T, st->T);
-    if ((it + 1) % 16 == 0) orthonormalize(st->T);
+    compose(Ex, T);
+    if ((it + 1) % 16 == 0) orthonormalize(T);
     const double srot = sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
     const double strans = sqrt(xi[3] * xi[3] + xi[4] * xi[4] + xi[5] * xi[5]);
     st->pairs_total += (long long)pairs;

@@ -10,17 +10,21 @@
 // point in the grid cells that overlap the group's bounding box in Z's frame,
 // grown by the cutoff radius; since the grid sorts Z by cell with x fastest,
 // the stream is a short list of contiguous runs (one per (y, z) cell row).
-// Every lane reads the same candidate record at the same time (a warp-uniform
-// broadcast load), tests its own cutoff, and the warp skips the kernel
-// evaluation when no lane is in range.  A group's stream is split into up to
-// kChunks chunks, each its own work item, for load balance.
+// A group's stream is split into up to kChunks chunks, each its own work item.
+//
+// Staging.  The warp copies its stream into shared memory 32 records at a
+// time with cp.async (one record per lane, so the copies are independent and
+// in flight together), double buffered: while the warp evaluates batch b
+// from shared memory, batch b + 1 is on its way.  Every lane then reads the
+// same record (a broadcast), tests its own cutoff, and the warp skips the
+// kernel evaluation when no lane is in range.
 //
 // Per pair: one ex2 (the geometric and squared-exponential feature exponents
 // are added in log2 units), the inner products of the label blocks, and the
 // moments W = sum w, E = sum w e, Q = sum w e e^T (e = z_j - x'_i) in FP32
 // registers.  Per work item, each lane folds its moments into 43 linear
-// statistics (see cvo_internal.cuh) from which the finalize kernel assembles
-// F, the se(3) gradient and the Hessian.
+// statistics held in shared memory (see cvo_internal.cuh), from which the
+// finalize kernel assembles F, the se(3) gradient and the Hessian.
 //
 // Precision.  x'_i is formed in double-float (hi + lo FP32 pair) from the
 // FP32 input coordinates and a double-float copy of T^-1, so the offset
@@ -70,7 +74,18 @@ __device__ __forceinline__ void transform_df(const float x[3], const float* Ahi,
     }
 }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
 // ---- feature kernels c_ij ---------------------------------------------------
+// Records are read through generic pointers: the query from global memory,
+// the candidates from the shared-memory staging buffer.
 
 // Eq. (geometric_only): no features, c_ij = 1.
 struct FeatNone {
@@ -94,7 +109,7 @@ struct FeatFixed {
             unsigned w[kVec * 4];
 #pragma unroll
             for (int k = 0; k < kVec; ++k) {
-                const uint4 u = __ldg(reinterpret_cast<const uint4*>(src) + k);
+                const uint4 u = reinterpret_cast<const uint4*>(src)[k];
                 w[4 * k] = u.x; w[4 * k + 1] = u.y; w[4 * k + 2] = u.z; w[4 * k + 3] = u.w;
             }
 #pragma unroll
@@ -104,7 +119,7 @@ struct FeatFixed {
             float f[kVec * 4];
 #pragma unroll
             for (int k = 0; k < kVec; ++k) {
-                const float4 u = __ldg(src + k);
+                const float4 u = src[k];
                 f[4 * k] = u.x; f[4 * k + 1] = u.y; f[4 * k + 2] = u.z; f[4 * k + 3] = u.w;
             }
 #pragma unroll
@@ -142,8 +157,8 @@ struct FeatGeneric {
     };
     __device__ static float get(const float4* rec, int k, int bf16)
     {
-        if (bf16) return __uint_as_float(((unsigned)__ldg(reinterpret_cast<const unsigned short*>(rec + 1) + k)) << 16);
-        return __ldg(reinterpret_cast<const float*>(rec + 1) + k);
+        if (bf16) return __uint_as_float(((unsigned)reinterpret_cast<const unsigned short*>(rec + 1)[k]) << 16);
+        return reinterpret_cast<const float*>(rec + 1)[k];
     }
     __device__ static void load_query(Q& q, const float4* rec, const FeatConst&) { q.rec = rec; }
     __device__ static float pair(const Q& q, const float4* rec, float& arg, const FeatConst& fc)
@@ -176,28 +191,65 @@ __device__ __forceinline__ int floor_cell(float v, float o, float inv_h)
     return (int)fminf(fmaxf(c, -2.0e9f), 2.0e9f);
 }
 
+struct Moments {
+    float W, E0, E1, E2, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz;
+};
+
+// Evaluates the cnt staged candidates of one batch for this lane's query.
+template <class Feat>
+__device__ __forceinline__ void eval_batch(const float4* sb, int cnt, int rs, const typename Feat::Q& qf,
+                                           const float xh[3], const float xl[3], bool act, bool dense, float sg,
+                                           float rc2, const FeatConst& fc, Moments& mo, unsigned& npairs)
+{
+#pragma unroll 2
+    for (int c = 0; c < cnt; ++c) {
+        const float4* zr = sb + c * rs;
+        const float4 z = zr[0];
+        const float dx = __fsub_rn(__fsub_rn(z.x, xh[0]), xl[0]);
+        const float dy = __fsub_rn(__fsub_rn(z.y, xh[1]), xl[1]);
+        const float dz = __fsub_rn(__fsub_rn(z.z, xh[2]), xl[2]);
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const bool in = act && (dense || d2 <= rc2);
+        if (__any_sync(kFull, in)) {
+            float arg = d2 * sg;
+            const float mult = Feat::pair(qf, zr, arg, fc);
+            const float w = in ? ex2(arg) * mult : 0.0f;
+            npairs += in ? 1u : 0u;
+            mo.W += w;
+            const float wx = w * dx, wy = w * dy, wz = w * dz;
+            mo.E0 += wx; mo.E1 += wy; mo.E2 += wz;
+            mo.Qxx = fmaf(wx, dx, mo.Qxx); mo.Qyy = fmaf(wy, dy, mo.Qyy); mo.Qzz = fmaf(wz, dz, mo.Qzz);
+            mo.Qxy = fmaf(wx, dy, mo.Qxy); mo.Qxz = fmaf(wx, dz, mo.Qxz); mo.Qyz = fmaf(wy, dz, mo.Qyz);
+        }
+    }
+}
+
 template <class Feat>
 __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
 {
-    __shared__ float red[kSweepWarps][kStatN];
+    extern __shared__ float4 stage_mem[];   // [kSweepWarps][2][32][rs]
+    __shared__ float acc_s[kSweepWarps][kStatN][32];
     __shared__ unsigned long long redc[kSweepWarps][2];
+    __shared__ float cst[30];               // Ahi, Alo, bhi, blo, chi, clo
     const IterState* st = a.st;
     if (st->done) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < 30) cst[threadIdx.x] = (&st->Ahi[0])[threadIdx.x];
+#pragma unroll
+    for (int k = 0; k < kStatN; ++k) acc_s[warp][k][lane] = 0.0f;
+    __syncthreads();
+    const float* Ahi = cst;
+    const float* Alo = cst + 9;
+    const float* bhi = cst + 18;
+    const float* blo = cst + 21;
+    const float* chi = cst + 24;
+    const float* clo = cst + 27;
     const LevelDesc L = a.levels[st->level];
     const int rs = a.rs;
     const bool dense = a.dense != 0;
-    float Ahi[9], Alo[9], bhi[3], blo[3], chi[3], clo[3];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) { Ahi[k] = st->Ahi[k]; Alo[k] = st->Alo[k]; }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) { bhi[k] = st->bhi[k]; blo[k] = st->blo[k]; chi[k] = st->chi[k]; clo[k] = st->clo[k]; }
     const float sg = st->sg, rc = st->rc, rc2 = st->rc2;
     const FeatConst fc = a.fc;
-
-    float acc[kStatN];
-#pragma unroll
-    for (int k = 0; k < kStatN; ++k) acc[k] = 0.0f;
+    float4* stage = stage_mem + (size_t)warp * 2 * 32 * rs;
     unsigned npairs = 0, ncand = 0;
 
     const int nitems = L.ngroups * kChunks;
@@ -208,7 +260,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
         const bool act = lane < grp.y;
         const int qi = grp.x + (act ? lane : 0);
         const float4* qrec = a.xrec + (size_t)qi * rs;
-        const float4 xq4 = __ldg(qrec);
+        const float4 xq4 = qrec[0];
         const float xq[3] = {xq4.x, xq4.y, xq4.z};
         float xh[3], xl[3];
         transform_df(xq, Ahi, Alo, bhi, blo, xh, xl);
@@ -274,8 +326,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
 
         typename Feat::Q qf;
         Feat::load_query(qf, qrec, fc);
-        float W = 0.f, E0 = 0.f, E1 = 0.f, E2 = 0.f;
-        float Qxx = 0.f, Qyy = 0.f, Qzz = 0.f, Qxy = 0.f, Qxz = 0.f, Qyz = 0.f;
+        Moments mo = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 
         int base = 0;
         for (int b0 = 0; b0 < nruns && base < chi_; b0 += 32) {
@@ -300,39 +351,46 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
             }
             const int roff = incl - rlen;
             const int btotal = __shfl_sync(kFull, incl, 31);
-            int pos = max(clo_, base);
-            const int end = min(chi_, base + btotal);
-            while (pos < end) {
-                const int rel = pos - base;
-                const unsigned before = __ballot_sync(kFull, (r < nruns) && (roff + rlen <= rel));
-                const int ri = __popc(before);
-                const int s0 = __shfl_sync(kFull, rstart, ri);
-                const int o0 = __shfl_sync(kFull, roff, ri);
-                const int l0 = __shfl_sync(kFull, rlen, ri);
-                const int j0 = s0 + (rel - o0);
-                const int cnt = min(o0 + l0 - rel, end - pos);
-                for (int t = 0; t < cnt; ++t) {
-                    const float4* zr = L.zrec + (size_t)(j0 + t) * rs;
-                    const float4 z = __ldg(zr);
-                    const float dx = __fsub_rn(__fsub_rn(z.x, xh[0]), xl[0]);
-                    const float dy = __fsub_rn(__fsub_rn(z.y, xh[1]), xl[1]);
-                    const float dz = __fsub_rn(__fsub_rn(z.z, xh[2]), xl[2]);
-                    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const bool in = act && (dense || d2 <= rc2);
-                    ncand += act ? 1u : 0u;
-                    if (__any_sync(kFull, in)) {
-                        float arg = d2 * sg;
-                        const float mult = Feat::pair(qf, zr, arg, fc);
-                        const float w = in ? ex2(arg) * mult : 0.0f;
-                        npairs += in ? 1u : 0u;
-                        W += w;
-                        const float wx = w * dx, wy = w * dy, wz = w * dz;
-                        E0 += wx; E1 += wy; E2 += wz;
-                        Qxx = fmaf(wx, dx, Qxx); Qyy = fmaf(wy, dy, Qyy); Qzz = fmaf(wz, dz, Qzz);
-                        Qxy = fmaf(wx, dy, Qxy); Qxz = fmaf(wx, dz, Qxz); Qyz = fmaf(wy, dz, Qyz);
+            const int lo = max(clo_, base) - base;   // positions relative to this pass
+            const int hi = min(chi_, base + btotal) - base;
+            if (lo < hi) {
+                const int nbat = (hi - lo + 31) >> 5;
+                // stage batch bi (positions lo + 32 bi + lane) into buffer bi & 1
+                auto issue = [&](int bi) {
+                    const int p0 = lo + 32 * bi;
+                    const int p = p0 + lane;
+                    // first run that ends after p0
+                    const unsigned before = __ballot_sync(kFull, (r < nruns) && (roff + rlen <= p0));
+                    int j = -1;
+                    for (int ri = __popc(before); ri < 32; ++ri) {
+                        const int o = __shfl_sync(kFull, roff, ri);
+                        const int l = __shfl_sync(kFull, rlen, ri);
+                        const int s0 = __shfl_sync(kFull, rstart, ri);
+                        if (o >= p0 + 32 || o >= hi) break;
+                        if (p < hi && p >= o && p < o + l) j = s0 + (p - o);
                     }
+                    if (j >= 0) {
+                        const float4* src = L.zrec + (size_t)j * rs;
+                        float4* dst = stage + ((bi & 1) * 32 + lane) * rs;
+                        for (int q = 0; q < rs; ++q) cp_async16(dst + q, src + q);
+                    }
+                    cp_async_commit();
+                };
+                issue(0);
+                for (int bi = 0; bi < nbat; ++bi) {
+                    if (bi + 1 < nbat) {
+                        issue(bi + 1);
+                        cp_async_wait_one();
+                    } else {
+                        cp_async_wait_all();
+                    }
+                    __syncwarp();
+                    const int cnt = min(32, hi - (lo + 32 * bi));
+                    eval_batch<Feat>(stage + (bi & 1) * 32 * rs, cnt, rs, qf, xh, xl, act, dense, sg, rc2, fc, mo,
+                                     npairs);
+                    ncand += act ? (unsigned)cnt : 0u;
+                    __syncwarp();
                 }
-                pos += cnt;
             }
             base += btotal;
         }
@@ -341,7 +399,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
             const float p0 = (xh[0] - chi[0]) + (xl[0] - clo[0]);
             const float p1 = (xh[1] - chi[1]) + (xl[1] - clo[1]);
             const float p2 = (xh[2] - chi[2]) + (xl[2] - clo[2]);
-            const float Q[3][3] = {{Qxx, Qxy, Qxz}, {Qxy, Qyy, Qyz}, {Qxz, Qyz, Qzz}};
+            const float Q[3][3] = {{mo.Qxx, mo.Qxy, mo.Qxz}, {mo.Qxy, mo.Qyy, mo.Qyz}, {mo.Qxz, mo.Qyz, mo.Qzz}};
             float PQ[3][3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -349,40 +407,42 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
                 PQ[1][c] = p2 * Q[0][c] - p0 * Q[2][c];
                 PQ[2][c] = -p1 * Q[0][c] + p0 * Q[1][c];
             }
-            acc[ST_W] += W;
-            acc[ST_E + 0] += E0; acc[ST_E + 1] += E1; acc[ST_E + 2] += E2;
-            acc[ST_Q + 0] += Qxx; acc[ST_Q + 1] += Qyy; acc[ST_Q + 2] += Qzz;
-            acc[ST_Q + 3] += Qxy; acc[ST_Q + 4] += Qxz; acc[ST_Q + 5] += Qyz;
+            float* acc = &acc_s[warp][0][lane];
+            auto add = [&](int s, float v) { acc[s * 32] += v; };
+            add(ST_W, mo.W);
+            add(ST_E + 0, mo.E0); add(ST_E + 1, mo.E1); add(ST_E + 2, mo.E2);
+            add(ST_Q + 0, mo.Qxx); add(ST_Q + 1, mo.Qyy); add(ST_Q + 2, mo.Qzz);
+            add(ST_Q + 3, mo.Qxy); add(ST_Q + 4, mo.Qxz); add(ST_Q + 5, mo.Qyz);
 #pragma unroll
             for (int rr = 0; rr < 3; ++rr)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) acc[ST_PQ + 3 * rr + c] += PQ[rr][c];
+                for (int c = 0; c < 3; ++c) add(ST_PQ + 3 * rr + c, PQ[rr][c]);
             // [p]x Q [p]x, symmetric: (0,0) (1,1) (2,2) (0,1) (0,2) (1,2)
-            acc[ST_PQP + 0] += PQ[0][1] * p2 - PQ[0][2] * p1;
-            acc[ST_PQP + 1] += -PQ[1][0] * p2 + PQ[1][2] * p0;
-            acc[ST_PQP + 2] += PQ[2][0] * p1 - PQ[2][1] * p0;
-            acc[ST_PQP + 3] += -PQ[0][0] * p2 + PQ[0][2] * p0;
-            acc[ST_PQP + 4] += PQ[0][0] * p1 - PQ[0][1] * p0;
-            acc[ST_PQP + 5] += PQ[1][0] * p1 - PQ[1][1] * p0;
-            const float Wp0 = W * p0, Wp1 = W * p1, Wp2 = W * p2;
-            acc[ST_WP + 0] += Wp0; acc[ST_WP + 1] += Wp1; acc[ST_WP + 2] += Wp2;
-            acc[ST_WPP + 0] += Wp0 * p0; acc[ST_WPP + 1] += Wp1 * p1; acc[ST_WPP + 2] += Wp2 * p2;
-            acc[ST_WPP + 3] += Wp0 * p1; acc[ST_WPP + 4] += Wp0 * p2; acc[ST_WPP + 5] += Wp1 * p2;
-            const float Ev[3] = {E0, E1, E2}, pv[3] = {p0, p1, p2};
+            add(ST_PQP + 0, PQ[0][1] * p2 - PQ[0][2] * p1);
+            add(ST_PQP + 1, -PQ[1][0] * p2 + PQ[1][2] * p0);
+            add(ST_PQP + 2, PQ[2][0] * p1 - PQ[2][1] * p0);
+            add(ST_PQP + 3, -PQ[0][0] * p2 + PQ[0][2] * p0);
+            add(ST_PQP + 4, PQ[0][0] * p1 - PQ[0][1] * p0);
+            add(ST_PQP + 5, PQ[1][0] * p1 - PQ[1][1] * p0);
+            const float Wp0 = mo.W * p0, Wp1 = mo.W * p1, Wp2 = mo.W * p2;
+            add(ST_WP + 0, Wp0); add(ST_WP + 1, Wp1); add(ST_WP + 2, Wp2);
+            add(ST_WPP + 0, Wp0 * p0); add(ST_WPP + 1, Wp1 * p1); add(ST_WPP + 2, Wp2 * p2);
+            add(ST_WPP + 3, Wp0 * p1); add(ST_WPP + 4, Wp0 * p2); add(ST_WPP + 5, Wp1 * p2);
+            const float Ev[3] = {mo.E0, mo.E1, mo.E2}, pv[3] = {p0, p1, p2};
 #pragma unroll
             for (int rr = 0; rr < 3; ++rr)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) acc[ST_EP + 3 * rr + c] += Ev[rr] * pv[c];
+                for (int c = 0; c < 3; ++c) add(ST_EP + 3 * rr + c, Ev[rr] * pv[c]);
         }
     }
 
     // warp tree (FP32, fixed order), then the block's warps in double-float
-#pragma unroll
+    __syncwarp();
     for (int k = 0; k < kStatN; ++k) {
-        float v = acc[k];
+        float v = acc_s[warp][k][lane];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-        if (lane == 0) red[warp][k] = v;
+        if (lane == 0) acc_s[warp][k][0] = v;
     }
     unsigned long long cp = npairs, cc = ncand;
 #pragma unroll
@@ -399,7 +459,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
         float hi = 0.0f, lo = 0.0f;
         for (int w = 0; w < kSweepWarps; ++w) {
             float s, e;
-            two_sum(hi, red[w][threadIdx.x], s, e);
+            two_sum(hi, acc_s[w][threadIdx.x][0], s, e);
             e = __fadd_rn(e, lo);
             hi = __fadd_rn(s, e);
             lo = __fsub_rn(e, __fsub_rn(hi, s));
@@ -419,8 +479,15 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
 template <class Feat>
 cudaError_t launch_t(const SweepArgs& a, int nblocks, cudaStream_t s)
 {
+    const size_t smem = (size_t)kSweepWarps * 2 * 32 * a.rs * sizeof(float4);
+    static bool attr_set = false;   // one-time opt-in above the 48 KB default
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_sweep<Feat>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
-    k_sweep<Feat><<<nblocks, kSweepWarps * 32, 0, s>>>(a);
+    k_sweep<Feat><<<nblocks, kSweepWarps * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
