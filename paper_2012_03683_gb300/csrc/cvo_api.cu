@@ -130,6 +130,7 @@ struct cvo_handle_s {
     // Morton super-cells about 2^super_delta cutoff radii wide
     double cell_factor = 0.5;
     int super_delta = 2;
+    int graph_pending = 0;
 };
 
 namespace {
@@ -518,6 +519,70 @@ cvo_status run_eval(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const 
     return CVO_OK;
 }
 
+// Builds, instantiates and launches the graph of one registration's loop.
+cvo_status run_graph_loop(cvo_handle h, const SweepArgs& a, double* trace)
+{
+    SweepLaunch sl;
+    CVO_CUDA(sweep_launch_info(a.fc, a.rs, &sl));
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cvo_status status = CVO_OK;
+    auto cleanup = [&]() {
+        if (ge) cudaGraphExecDestroy(ge);
+        if (g) cudaGraphDestroy(g);
+    };
+    auto check = [&](cudaError_t e, const char* what) {
+        if (e != cudaSuccess && status == CVO_OK)
+            status = fail(CVO_ERR_CUDA, "registration graph: %s: %s", what, cudaGetErrorString(e));
+        return e == cudaSuccess;
+    };
+    if (!check(cudaGraphCreate(&g, 0), "cudaGraphCreate")) return cleanup(), status;
+    cudaGraphConditionalHandle cond;
+    if (!check(cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault), "conditional handle"))
+        return cleanup(), status;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cn;
+    if (!check(cudaGraphAddNode(&cn, g, nullptr, nullptr, 0, &cp), "conditional node")) return cleanup(), status;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    SweepArgs sargs = a;
+    void* sp[1] = {&sargs};
+    cudaGraphNodeParams kp = {};
+    kp.type = cudaGraphNodeTypeKernel;
+    kp.kernel.func = (void*)sl.func;
+    kp.kernel.gridDim = dim3(h->sweep_blocks);
+    kp.kernel.blockDim = dim3(kSweepWarps * 32);
+    kp.kernel.sharedMemBytes = (unsigned)sl.smem;
+    kp.kernel.kernelParams = sp;
+    cudaGraphNode_t sn;
+    if (!check(cudaGraphAddNode(&sn, body, nullptr, nullptr, 0, &kp), "sweep node")) return cleanup(), status;
+    IterState* st = a.st;
+    const float2* ps = a.part_stats;
+    const unsigned long long* pc = a.part_cnt;
+    int cap = a.part_cap, nb = h->sweep_blocks, use_cond = 1;
+    double* tr = trace;
+    void* fp[8] = {&st, &ps, &pc, &cap, &nb, &tr, &cond, &use_cond};
+    cudaGraphNodeParams fpn = {};
+    fpn.type = cudaGraphNodeTypeKernel;
+    fpn.kernel.func = (void*)finalize_kernel();
+    fpn.kernel.gridDim = dim3(1);
+    fpn.kernel.blockDim = dim3(kFinalizeThreads);
+    fpn.kernel.sharedMemBytes = 0;
+    fpn.kernel.kernelParams = fp;
+    cudaGraphNode_t fn;
+    if (!check(cudaGraphAddNode(&fn, body, &sn, nullptr, 1, &fpn), "finalize node")) return cleanup(), status;
+    if (!check(cudaGraphInstantiate(&ge, g, 0), "instantiate")) return cleanup(), status;
+    if (!check(cudaGraphLaunch(ge, h->s), "launch")) return cleanup(), status;
+    // the graph's kernels are counted once the iteration count is known
+    h->graph_pending = 1;
+    check(cudaStreamSynchronize(h->s), "synchronize");
+    cleanup();
+    return status;
+}
+
 cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double* T_init, double* T_out,
                         cvo_info* info)
 {
@@ -548,11 +613,17 @@ cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
             h->evs.push_back(e);
         }
     }
-    // Iterations are queued in batches; the device-side state stops the
-    // kernels once the registration has converged.  The host checks the
-    // done flag of the previous batch while the next one runs.
+    if (!h->timing) {
+        // The whole loop is one CUDA graph: a WHILE conditional node whose body
+        // is (sweep, finalize); the finalize clears the condition once the
+        // registration has converged or hit max_iters.
+        CVO_TRY(run_graph_loop(h, a, trace));
+    }
+    // Timing mode: iterations queued from the host in batches with CUDA events
+    // around every sweep; the device-side state stops the kernels once the
+    // registration is done, and the host checks the done flag between batches.
     const int batch = 8;
-    int launched = 0;
+    int launched = h->timing ? 0 : p.max_iters;
     while (launched < p.max_iters) {
         const int nb = std::min(batch, p.max_iters - launched);
         for (int k = 0; k < nb; ++k) {
@@ -582,6 +653,12 @@ cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     inf.pairs = st->pairs_total;
     inf.candidates = st->cands_total;
     h->last_iters = st->iter;
+    if (h->graph_pending) {
+        // the graph ran (sweep, finalize) once per iteration, plus the
+        // finalize that found the loop done (none when it stopped itself)
+        g_launch_count.fetch_add(2LL * st->iter, std::memory_order_relaxed);
+        h->graph_pending = 0;
+    }
     if (h->timing) {
         double tot = 0.0;
         for (int it = 0; it < st->iter; ++it) {

@@ -171,7 +171,7 @@ __device__ void update_derived(IterState* st)
         split_df(bv, st->bhi[r], st->blo[r]);
     }
     const double ell = st->ell;
-    st->sg = (float)(-1.4426950408889634 / (2.0 * ell * ell));
+    st->sg = -1.44269504f / (2.0f * (float)(ell * ell));   // FP32: the sweep uses it in FP32
     if (st->cutoff_mult > 0.0) {
         const double rc = st->cutoff_mult * ell;
         st->rc = (float)rc;
@@ -195,7 +195,7 @@ __global__ void k_init_state(IterState* st)
 
 // Full Hessian of xi -> F(exp(xi^) T) (evaluation only): H = B^T Hc B with
 // B = [[R^T, 0], [-[c]x R^T - R^T [t]x, R^T]].
-__device__ void full_hessian(const double* s, double L2, double L4, const double* T, const double* c, double* H)
+__device__ void full_hessian(const double* s, double iL2, double iL4, const double* T, const double* c, double* H)
 {
     double Hc[36];
     const double* Q = s + ST_Q;
@@ -220,12 +220,12 @@ __device__ void full_hessian(const double* s, double L2, double L4, const double
     for (int r = 0; r < 3; ++r)
         for (int q = 0; q < 3; ++q) {
             const double id = (r == q) ? 1.0 : 0.0;
-            Hc[6 * r + q] = -symv(PQP, r, q) / L4 - (trWpp * id - symv(Wpp, r, q)) / L2 +
-                            0.5 * (Ep[3 * r + q] + Ep[3 * q + r] - 2.0 * trEp * id) / L2;
-            const double hwv = PQ[3 * r + q] / L4 - skew(Wp, r, q) / L2 - 0.5 * skew(E, r, q) / L2;
+            Hc[6 * r + q] = -symv(PQP, r, q) * iL4 - (trWpp * id - symv(Wpp, r, q)) * iL2 +
+                            0.5 * (Ep[3 * r + q] + Ep[3 * q + r] - 2.0 * trEp * id) * iL2;
+            const double hwv = PQ[3 * r + q] * iL4 - skew(Wp, r, q) * iL2 - 0.5 * skew(E, r, q) * iL2;
             Hc[6 * r + 3 + q] = hwv;
             Hc[6 * (3 + q) + r] = hwv;
-            Hc[6 * (3 + r) + 3 + q] = symv(Q, r, q) / L4 - W * id / L2;
+            Hc[6 * (3 + r) + 3 + q] = symv(Q, r, q) * iL4 - W * id * iL2;
         }
     double B[36];
     for (int k = 0; k < 36; ++k) B[k] = 0.0;
@@ -259,16 +259,29 @@ __device__ void full_hessian(const double* s, double L2, double L4, const double
 
 __global__ void __launch_bounds__(kFinalizeThreads)
 k_finalize(IterState* st, const float2* __restrict__ ps, const unsigned long long* __restrict__ pc, int cap, int nb,
-           double* trace)
+           double* trace, cudaGraphConditionalHandle cond, int use_cond)
 {
     __shared__ double S[kStatN];
     __shared__ unsigned long long cs[2][kFinalizeThreads / 32];
-    if (st->done) return;
+    if (st->done) {
+        // inside a graph's loop: stop it
+        if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+        return;
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int v = warp; v < kStatN; v += kFinalizeThreads / 32) {
         float hi = 0.0f, lo = 0.0f;
-        for (int b = lane; b < nb; b += 32) {
-            const float2 x = ps[(size_t)v * cap + b];
+        const float2* row = ps + (size_t)v * cap;
+        int b = lane;
+        for (; b + 96 < nb; b += 128) {   // four loads in flight per lane
+            const float2 x0 = row[b], x1 = row[b + 32], x2 = row[b + 64], x3 = row[b + 96];
+            df_add(hi, lo, x0.x, x0.y);
+            df_add(hi, lo, x1.x, x1.y);
+            df_add(hi, lo, x2.x, x2.y);
+            df_add(hi, lo, x3.x, x3.y);
+        }
+        for (; b < nb; b += 32) {
+            const float2 x = row[b];
             df_add(hi, lo, x.x, x.y);
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -300,12 +313,13 @@ k_finalize(IterState* st, const float2* __restrict__ ps, const unsigned long lon
         cands += cs[1][w];
     }
     const double kap = st->kappa;
-    const double ell = st->ell, L2 = ell * ell, L4 = L2 * L2;
+    const double ell = st->ell, L2 = ell * ell;
+    const double iL2 = 1.0 / L2, iL4 = iL2 * iL2;   // one FP64 division (about 660 cycles on GB300)
     const double F = kap * S[ST_W];
     const double* Ep = S + ST_EP;
     // centred gradient (kappa applied here)
-    const V3 gcw = scale(v3(Ep[5] - Ep[7], Ep[6] - Ep[2], Ep[1] - Ep[3]), kap / L2);
-    const V3 gcv = scale(v3(S[ST_E], S[ST_E + 1], S[ST_E + 2]), -kap / L2);
+    const V3 gcw = scale(v3(Ep[5] - Ep[7], Ep[6] - Ep[2], Ep[1] - Ep[3]), kap * iL2);
+    const V3 gcv = scale(v3(S[ST_E], S[ST_E + 1], S[ST_E + 2]), -kap * iL2);
     double* T = st->T;
     const V3 c = v3(st->c[0], st->c[1], st->c[2]);
     const V3 tt = v3(T[3], T[7], T[11]);
@@ -322,8 +336,9 @@ k_finalize(IterState* st, const float2* __restrict__ ps, const unsigned long lon
     if (st->mode == 0) {
         double s[kStatN];
         for (int k = 0; k < kStatN; ++k) s[k] = kap * S[k];
-        full_hessian(s, L2, L4, T, st->c, st->hess);
+        full_hessian(s, iL2, iL4, T, st->c, st->hess);
         st->done = 1;
+        if (use_cond) cudaGraphSetConditional(cond, 0u);
         return;
     }
 
@@ -336,23 +351,25 @@ k_finalize(IterState* st, const float2* __restrict__ ps, const unsigned long lon
     const double trWpp = S[ST_WPP] + S[ST_WPP + 1] + S[ST_WPP + 2];
     const double trEp = Ep[0] + Ep[4] + Ep[8];
     const double ww = dot(wt, wt), vv = dot(vt, vt);
-    const double hww = -symq(S + ST_PQP, wt, wt) / L4 - (trWpp * ww - symq(S + ST_WPP, wt, wt)) / L2 +
-                       (fullq(Ep, wt, wt) - trEp * ww) / L2;
+    const double hww = -symq(S + ST_PQP, wt, wt) * iL4 - (trWpp * ww - symq(S + ST_WPP, wt, wt)) * iL2 +
+                       (fullq(Ep, wt, wt) - trEp * ww) * iL2;
     const V3 Ev = v3(S[ST_E], S[ST_E + 1], S[ST_E + 2]);
     const V3 Wpv = v3(S[ST_WP], S[ST_WP + 1], S[ST_WP + 2]);
-    const double hwv = fullq(S + ST_PQ, wt, vt) / L4 - dot(wt, cross(Wpv, vt)) / L2 - 0.5 * dot(wt, cross(Ev, vt)) / L2;
-    const double hvv = symq(S + ST_Q, vt, vt) / L4 - S[ST_W] * vv / L2;
+    const double hwv = fullq(S + ST_PQ, wt, vt) * iL4 - (dot(wt, cross(Wpv, vt)) + 0.5 * dot(wt, cross(Ev, vt))) * iL2;
+    const double hvv = symq(S + ST_Q, vt, vt) * iL4 - S[ST_W] * vv * iL2;
     const double Fpp = kap * (hww + 2.0 * hwv + hvv);
     double gn2 = 0.0;
     for (int q = 0; q < 6; ++q) gn2 += g[q] * g[q];
+    // Norms and clamp ratios only feed thresholds and the step length: FP32
+    // square roots and divisions (FP64 ones cost ~700 cycles each here).
+    const double wn = (double)sqrtf((float)dot(gw, gw));
+    const double vn = (double)sqrtf((float)dot(gv, gv));
     double t = 0.0;
     if (gn2 > 0.0) {
-        t = (Fpp < 0.0) ? gn2 / (-Fpp) : 1e-3 / sqrt(gn2);
-        const double wn = sqrt(dot(gw, gw));
-        const double vn = sqrt(dot(gv, gv));
+        t = (Fpp < 0.0) ? gn2 / (-Fpp) : 1e-3 / (double)sqrtf((float)gn2);
         const double max_tr = st->max_step_trans > 0.0 ? st->max_step_trans : 0.5 * ell;
-        if (t * wn > st->max_step_rot) t = st->max_step_rot / wn;
-        if (t * vn > max_tr) t = max_tr / vn;
+        if (t * wn > st->max_step_rot) t = (double)((float)st->max_step_rot / (float)wn);
+        if (t * vn > max_tr) t = (double)((float)max_tr / (float)vn);
     }
     double T_k[12];
     for (int q = 0; q < 12; ++q) T_k[q] = T[q];
@@ -361,12 +378,12 @@ k_finalize(IterState* st, const float2* __restrict__ ps, const unsigned long lon
     se3_exp_dev(xi, Ex);
     compose(Ex, T);
     if ((it + 1) % 16 == 0) orthonormalize(T);
-    const double srot = sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
-    const double strans = sqrt(xi[3] * xi[3] + xi[4] * xi[4] + xi[5] * xi[5]);
+    const double srot = t * wn;
+    const double strans = t * vn;
     st->pairs_total += (long long)pairs;
     st->cands_total += (long long)cands;
     st->Fpp = Fpp;
-    st->gnorm = sqrt(gn2);
+    st->gnorm = (double)sqrtf((float)gn2);
     st->t = t;
     st->srot = srot;
     st->strans = strans;
@@ -390,7 +407,7 @@ k_finalize(IterState* st, const float2* __restrict__ ps, const unsigned long lon
     st->decayed = decayed;
     if (trace) {
         double* tr = trace + (size_t)kTraceStride * it;
-        tr[0] = ell_used; tr[1] = F; tr[2] = ith; tr[3] = sqrt(gn2); tr[4] = Fpp;
+        tr[0] = ell_used; tr[1] = F; tr[2] = ith; tr[3] = st->gnorm; tr[4] = Fpp;
         tr[5] = t; tr[6] = srot; tr[7] = strans; tr[8] = decayed; tr[9] = (double)pairs;
         for (int q = 0; q < 12; ++q) tr[10 + q] = T_k[q];
     }
@@ -404,9 +421,12 @@ k_finalize(IterState* st, const float2* __restrict__ ps, const unsigned long lon
         st->done = 1;
     }
     update_derived(st);
+    if (use_cond) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
 }
 
 }  // namespace
+
+const void* finalize_kernel() { return (const void*)k_finalize; }
 
 cudaError_t launch_init_state(IterState* st, cudaStream_t s)
 {
@@ -419,7 +439,8 @@ cudaError_t launch_finalize(IterState* st, const float2* part_stats, const unsig
                             int nblocks, double* trace, cudaStream_t s)
 {
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
-    k_finalize<<<1, kFinalizeThreads, 0, s>>>(st, part_stats, part_cnt, part_cap, nblocks, trace);
+    k_finalize<<<1, kFinalizeThreads, 0, s>>>(st, part_stats, part_cnt, part_cap, nblocks, trace,
+                                               cudaGraphConditionalHandle{}, 0);
     return cudaGetLastError();
 }
 

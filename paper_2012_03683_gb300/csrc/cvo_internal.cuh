@@ -120,6 +120,16 @@ struct SweepArgs {
 extern std::atomic<long long> g_launch_count;
 
 cudaError_t launch_sweep(const SweepArgs& a, int nblocks, cudaStream_t s);
+
+// Kernel handles for CUDA-graph kernel nodes.
+struct SweepLaunch {
+    const void* func;   // k_sweep specialisation
+    size_t smem;        // dynamic shared memory
+};
+cudaError_t sweep_launch_info(const FeatConst& fc, int rs, SweepLaunch* out);
+// k_finalize(IterState*, const float2*, const unsigned long long*, int cap, int nb,
+//            double* trace, cudaGraphConditionalHandle cond, int use_cond)
+const void* finalize_kernel();
 cudaError_t launch_init_state(IterState* st, cudaStream_t s);
 cudaError_t launch_finalize(IterState* st, const float2* part_stats, const unsigned long long* part_cnt,
                             int part_cap, int nblocks, double* trace, cudaStream_t s);

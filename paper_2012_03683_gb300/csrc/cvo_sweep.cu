@@ -477,40 +477,43 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
 }
 
 template <class Feat>
-cudaError_t launch_t(const SweepArgs& a, int nblocks, cudaStream_t s)
+cudaError_t info_t(int rs, SweepLaunch* out)
 {
-    const size_t smem = (size_t)kSweepWarps * 2 * 32 * a.rs * sizeof(float4);
     static bool attr_set = false;   // one-time opt-in above the 48 KB default
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_sweep<Feat>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    g_launch_count.fetch_add(1, std::memory_order_relaxed);
-    k_sweep<Feat><<<nblocks, kSweepWarps * 32, smem, s>>>(a);
-    return cudaGetLastError();
+    out->func = (const void*)k_sweep<Feat>;
+    out->smem = (size_t)kSweepWarps * 2 * 32 * rs * sizeof(float4);
+    return cudaSuccess;
 }
 
 }  // namespace
 
-// Picks the feature specialisation for the handle's block list.
+// The sweep specialisation for a block list: kernel and dynamic shared memory.
+cudaError_t sweep_launch_info(const FeatConst& f, int rs, SweepLaunch* out)
+{
+    if (f.n_blocks == 0) return info_t<FeatNone>(rs, out);
+    const bool se3 = f.n_blocks >= 1 && f.kind[0] == 0 && f.dim[0] == 3;
+    if (f.n_blocks == 1 && se3)
+        return f.bf16 ? info_t<FeatFixed<3, 0, true>>(rs, out) : info_t<FeatFixed<3, 0, false>>(rs, out);
+    if (f.n_blocks == 2 && se3 && f.kind[1] == 1 && f.dim[1] == 19)
+        return f.bf16 ? info_t<FeatFixed<3, 19, true>>(rs, out) : info_t<FeatFixed<3, 19, false>>(rs, out);
+    if (f.n_blocks == 1 && f.kind[0] == 1 && f.dim[0] == 19)
+        return f.bf16 ? info_t<FeatFixed<0, 19, true>>(rs, out) : info_t<FeatFixed<0, 19, false>>(rs, out);
+    return info_t<FeatGeneric>(rs, out);
+}
+
 cudaError_t launch_sweep(const SweepArgs& a, int nblocks, cudaStream_t s)
 {
-    const FeatConst& f = a.fc;
-    if (f.n_blocks == 0) return launch_t<FeatNone>(a, nblocks, s);
-    const bool se3 = f.n_blocks >= 1 && f.kind[0] == 0 && f.dim[0] == 3;
-    if (f.n_blocks == 1 && se3) {
-        return f.bf16 ? launch_t<FeatFixed<3, 0, true>>(a, nblocks, s) : launch_t<FeatFixed<3, 0, false>>(a, nblocks, s);
-    }
-    if (f.n_blocks == 2 && se3 && f.kind[1] == 1 && f.dim[1] == 19) {
-        return f.bf16 ? launch_t<FeatFixed<3, 19, true>>(a, nblocks, s)
-                      : launch_t<FeatFixed<3, 19, false>>(a, nblocks, s);
-    }
-    if (f.n_blocks == 1 && f.kind[0] == 1 && f.dim[0] == 19) {
-        return f.bf16 ? launch_t<FeatFixed<0, 19, true>>(a, nblocks, s)
-                      : launch_t<FeatFixed<0, 19, false>>(a, nblocks, s);
-    }
-    return launch_t<FeatGeneric>(a, nblocks, s);
+    SweepLaunch li;
+    cudaError_t e = sweep_launch_info(a.fc, a.rs, &li);
+    if (e != cudaSuccess) return e;
+    void* args[1] = {(void*)&a};
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    return cudaLaunchKernel(li.func, dim3(nblocks), dim3(kSweepWarps * 32), args, li.smem, s);
 }
 
 }  // namespace cvo

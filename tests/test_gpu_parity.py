@@ -299,3 +299,23 @@ def test_register_street_annealing_matches_oracle():
     for k in np.nonzero(decisions)[0]:
         assert k >= 1 and tr[k - 1, 0] == tr[k, 0]
         assert abs(tr[k, 2] - tr[k - 1, 2]) < 1e-3 * abs(tr[k - 1, 2]) * (1 + 1e-6)
+
+
+def test_graph_loop_equals_host_loop():
+    """The registration loop as one CUDA graph (WHILE node) and the same
+    kernels queued from the host give bitwise-identical results."""
+    p = scenes.street_pair()
+    sel = rng(13).permutation(p.n)[:6000]
+    kw = dict(ell=0.3, ell_min=0.05, cutoff_mult=3.0, max_iters=60, anneal=True)
+    h = cvo.CVO(blocks=p.blocks, **kw)
+    args = (dev(p.X[sel]), dev(p.Z[sel]), np.eye(4), dev(p.FX[sel]), dev(p.FZ[sel]))
+    T_graph, info_g = h.register(*args)
+    tr_g = h.trace()
+    cvo.cvo_set_timing(h.h, True)
+    T_host, info_h = h.register(*args)
+    tr_h = h.trace()
+    ms, n = cvo.cvo_sweep_time(h.h)
+    h.close()
+    assert np.array_equal(T_graph, T_host)
+    assert info_g["iters"] == info_h["iters"] == n and ms > 0
+    np.testing.assert_array_equal(tr_g, tr_h)
