@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -112,7 +113,7 @@ struct cvo_handle_s {
     DevBuf keys, vals, keys2, vals2, sort_tmp, flags, gidx;
     DevBuf xrec, morton;
     DevBuf zrec[kMaxLevels], cell_start[kMaxLevels], groups[kMaxLevels];
-    DevBuf misc, levels_dev, state, part_stats, part_cnt, trace;
+    DevBuf misc, levels_dev, state, part_stats, part_cnt, grp_stats, grp_cnt, grp_arrivals, trace;
     IterState* h_state = nullptr;   // pinned mirror
     unsigned* h_misc = nullptr;     // pinned
     int last_iters = 0;
@@ -131,6 +132,7 @@ struct cvo_handle_s {
     double cell_factor = 0.5;
     int super_delta = 2;
     int graph_pending = 0;
+    int use_graph = 1;
 };
 
 namespace {
@@ -419,6 +421,10 @@ cvo_status prepare(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, double 
     h->sweep_blocks = std::max(1, std::min((max_items + kSweepWarps - 1) / kSweepWarps, h->num_sms * 8));
     CVO_CUDA(ensure(h->part_stats, (size_t)kStatN * h->sweep_blocks * sizeof(float2)));
     CVO_CUDA(ensure(h->part_cnt, (size_t)2 * h->sweep_blocks * sizeof(unsigned long long)));
+    CVO_CUDA(ensure(h->grp_stats, (size_t)kStatN * kMaxGroups * sizeof(float2)));
+    CVO_CUDA(ensure(h->grp_cnt, (size_t)2 * kMaxGroups * sizeof(unsigned long long)));
+    CVO_CUDA(ensure(h->grp_arrivals, (size_t)kMaxGroups * sizeof(unsigned)));
+    CVO_CUDA(cudaMemsetAsync(h->grp_arrivals.p, 0, (size_t)kMaxGroups * sizeof(unsigned), h->s));
 
     // feature constants
     FeatConst& fc = h->fc;
@@ -487,6 +493,9 @@ SweepArgs sweep_args(cvo_handle h)
     a.st = (IterState*)h->state.p;
     a.part_stats = (float2*)h->part_stats.p;
     a.part_cnt = (unsigned long long*)h->part_cnt.p;
+    a.grp_stats = (float2*)h->grp_stats.p;
+    a.grp_cnt = (unsigned long long*)h->grp_cnt.p;
+    a.grp_arrivals = (unsigned*)h->grp_arrivals.p;
     a.part_cap = h->sweep_blocks;
     a.fc = h->fc;
     return a;
@@ -507,7 +516,7 @@ cvo_status run_eval(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const 
     CVO_TRY(init_state(h, T, h->p.ell, 0));
     const SweepArgs a = sweep_args(h);
     CVO_CUDA(launch_sweep(a, h->sweep_blocks, h->s));
-    CVO_CUDA(launch_finalize(a.st, a.part_stats, a.part_cnt, a.part_cap, h->sweep_blocks, nullptr, h->s));
+    CVO_CUDA(launch_finalize(a.st, a.grp_stats, a.grp_cnt, h->sweep_blocks, nullptr, h->s));
     CVO_TRY(fetch_state(h));
     const IterState* st = h->h_state;
     out->F = st->F;
@@ -560,11 +569,11 @@ cvo_status run_graph_loop(cvo_handle h, const SweepArgs& a, double* trace)
     cudaGraphNode_t sn;
     if (!check(cudaGraphAddNode(&sn, body, nullptr, nullptr, 0, &kp), "sweep node")) return cleanup(), status;
     IterState* st = a.st;
-    const float2* ps = a.part_stats;
-    const unsigned long long* pc = a.part_cnt;
-    int cap = a.part_cap, nb = h->sweep_blocks, use_cond = 1;
+    const float2* gs = a.grp_stats;
+    const unsigned long long* gcn = a.grp_cnt;
+    int ngroups = (h->sweep_blocks + kGroupBlocks - 1) / kGroupBlocks, use_cond = 1;
     double* tr = trace;
-    void* fp[8] = {&st, &ps, &pc, &cap, &nb, &tr, &cond, &use_cond};
+    void* fp[7] = {&st, &gs, &gcn, &ngroups, &tr, &cond, &use_cond};
     cudaGraphNodeParams fpn = {};
     fpn.type = cudaGraphNodeTypeKernel;
     fpn.kernel.func = (void*)finalize_kernel();
@@ -599,7 +608,11 @@ cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
         if (info) *info = inf;
         return (cvo_status)inf.status;
     }
-    const double ell_lo = p.anneal ? p.ell_min : p.ell;
+    // A decay needs a reference indicator from the previous iteration at the
+    // same lengthscale, so at most one decay happens every two iterations: no
+    // grid level below decay^(max_iters/2) * ell is ever used.
+    double ell_lo = p.ell;
+    if (p.anneal) ell_lo = std::max(p.ell_min, p.ell * std::pow(p.decay, (double)(p.max_iters / 2)) * 0.9999);
     CVO_TRY(prepare(h, X, Z, p.ell, ell_lo));
     CVO_TRY(init_state(h, T_init, p.ell, 1));
     CVO_CUDA(ensure(h->trace, (size_t)p.max_iters * CVO_TRACE_STRIDE * sizeof(double)));
@@ -613,7 +626,8 @@ cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
             h->evs.push_back(e);
         }
     }
-    if (!h->timing) {
+    const bool graph = !h->timing && h->use_graph;
+    if (graph) {
         // The whole loop is one CUDA graph: a WHILE conditional node whose body
         // is (sweep, finalize); the finalize clears the condition once the
         // registration has converged or hit max_iters.
@@ -623,7 +637,7 @@ cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     // around every sweep; the device-side state stops the kernels once the
     // registration is done, and the host checks the done flag between batches.
     const int batch = 8;
-    int launched = h->timing ? 0 : p.max_iters;
+    int launched = graph ? p.max_iters : 0;
     while (launched < p.max_iters) {
         const int nb = std::min(batch, p.max_iters - launched);
         for (int k = 0; k < nb; ++k) {
@@ -631,7 +645,7 @@ cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
             if (h->timing) CVO_CUDA(cudaEventRecord(h->evs[2 * it], h->s));
             CVO_CUDA(launch_sweep(a, h->sweep_blocks, h->s));
             if (h->timing) CVO_CUDA(cudaEventRecord(h->evs[2 * it + 1], h->s));
-            CVO_CUDA(launch_finalize(a.st, a.part_stats, a.part_cnt, a.part_cap, h->sweep_blocks, trace, h->s));
+            CVO_CUDA(launch_finalize(a.st, a.grp_stats, a.grp_cnt, h->sweep_blocks, trace, h->s));
         }
         launched += nb;
         if (launched >= p.max_iters) break;
@@ -708,6 +722,13 @@ cvo_status cvo_create(const cvo_params* params, void* cuda_stream, cvo_handle* o
     h->p = *params;
     h->s = (cudaStream_t)cuda_stream;
     h->device = dev;
+    // CVO_GRAPH=0 queues the loop's kernels from the host instead of running
+    // it as one CUDA graph (profilers cannot attribute time to the kernel
+    // nodes of a graph with conditional nodes); the kernels are the same.
+    {
+        const char* gv = std::getenv("CVO_GRAPH");
+        h->use_graph = !(gv && gv[0] == '0');
+    }
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (cudaMallocHost((void**)&h->h_state, sizeof(IterState)) != cudaSuccess ||
         cudaMallocHost((void**)&h->h_misc, kMiscWords * sizeof(unsigned)) != cudaSuccess) {
@@ -727,7 +748,8 @@ cvo_status cvo_destroy(cvo_handle h)
     cudaStreamSynchronize(h->s);
     DevBuf* bufs[] = {&h->stage_xyz[0], &h->stage_xyz[1], &h->stage_feat[0], &h->stage_feat[1], &h->keys, &h->vals,
                       &h->keys2, &h->vals2, &h->sort_tmp, &h->flags, &h->gidx, &h->xrec, &h->morton, &h->misc,
-                      &h->levels_dev, &h->state, &h->part_stats, &h->part_cnt, &h->trace};
+                      &h->levels_dev, &h->state, &h->part_stats, &h->part_cnt, &h->grp_stats,
+                      &h->grp_cnt, &h->grp_arrivals, &h->trace};
     for (DevBuf* b : bufs) release(*b);
     for (int k = 0; k < kMaxLevels; ++k) {
         release(h->zrec[k]);

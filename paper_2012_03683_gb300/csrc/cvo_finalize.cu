@@ -257,61 +257,12 @@ __device__ void full_hessian(const double* s, double iL2, double iL4, const doub
         }
 }
 
-__global__ void __launch_bounds__(kFinalizeThreads)
-k_finalize(IterState* st, const float2* __restrict__ ps, const unsigned long long* __restrict__ pc, int cap, int nb,
-           double* trace, cudaGraphConditionalHandle cond, int use_cond)
+// One thread takes the step on a shared-memory copy of the state: global
+// loads after global stores to the same struct would each wait a full L2
+// round trip.
+__device__ void take_step(IterState* st, const double* S, unsigned long long pairs, unsigned long long cands,
+                          double* trace)
 {
-    __shared__ double S[kStatN];
-    __shared__ unsigned long long cs[2][kFinalizeThreads / 32];
-    if (st->done) {
-        // inside a graph's loop: stop it
-        if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
-        return;
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int v = warp; v < kStatN; v += kFinalizeThreads / 32) {
-        float hi = 0.0f, lo = 0.0f;
-        const float2* row = ps + (size_t)v * cap;
-        int b = lane;
-        for (; b + 96 < nb; b += 128) {   // four loads in flight per lane
-            const float2 x0 = row[b], x1 = row[b + 32], x2 = row[b + 64], x3 = row[b + 96];
-            df_add(hi, lo, x0.x, x0.y);
-            df_add(hi, lo, x1.x, x1.y);
-            df_add(hi, lo, x2.x, x2.y);
-            df_add(hi, lo, x3.x, x3.y);
-        }
-        for (; b < nb; b += 32) {
-            const float2 x = row[b];
-            df_add(hi, lo, x.x, x.y);
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
-            const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
-            df_add(hi, lo, oh, ol);
-        }
-        if (lane == 0) S[v] = (double)hi + (double)lo;
-    }
-    unsigned long long c0 = 0, c1 = 0;
-    for (int b = threadIdx.x; b < nb; b += kFinalizeThreads) {
-        c0 += pc[b];
-        c1 += pc[(size_t)cap + b];
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        c0 += __shfl_xor_sync(0xffffffffu, c0, o);
-        c1 += __shfl_xor_sync(0xffffffffu, c1, o);
-    }
-    if (lane == 0) {
-        cs[0][warp] = c0;
-        cs[1][warp] = c1;
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-
-    unsigned long long pairs = 0, cands = 0;
-    for (int w = 0; w < kFinalizeThreads / 32; ++w) {
-        pairs += cs[0][w];
-        cands += cs[1][w];
-    }
     const double kap = st->kappa;
     const double ell = st->ell, L2 = ell * ell;
     const double iL2 = 1.0 / L2, iL4 = iL2 * iL2;   // one FP64 division (about 660 cycles on GB300)
@@ -338,7 +289,6 @@ k_finalize(IterState* st, const float2* __restrict__ ps, const unsigned long lon
         for (int k = 0; k < kStatN; ++k) s[k] = kap * S[k];
         full_hessian(s, iL2, iL4, T, st->c, st->hess);
         st->done = 1;
-        if (use_cond) cudaGraphSetConditional(cond, 0u);
         return;
     }
 
@@ -421,7 +371,281 @@ k_finalize(IterState* st, const float2* __restrict__ ps, const unsigned long lon
         st->done = 1;
     }
     update_derived(st);
-    if (use_cond) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
+}
+
+// Horner coefficients (highest order first) of sin(th)/th, (1 - cos th)/th^2
+// and (th - sin th)/th^3 in th^2: 1/(2k+1)!, 1/(2k+2)!, 1/(2k+3)!, k = 8 .. 0.
+__constant__ double c_se3_series[3][9] = {
+    {1.0 / 355687428096000.0, 1.0 / 1307674368000.0, 1.0 / 6227020800.0, 1.0 / 39916800.0, 1.0 / 362880.0,
+     1.0 / 5040.0, 1.0 / 120.0, 1.0 / 6.0, 1.0},
+    {1.0 / 6402373705728000.0, 1.0 / 20922789888000.0, 1.0 / 87178291200.0, 1.0 / 479001600.0, 1.0 / 3628800.0,
+     1.0 / 40320.0, 1.0 / 720.0, 1.0 / 24.0, 1.0 / 2.0},
+    {1.0 / 121645100408832000.0, 1.0 / 355687428096000.0, 1.0 / 1307674368000.0, 1.0 / 6227020800.0,
+     1.0 / 39916800.0, 1.0 / 362880.0, 1.0 / 5040.0, 1.0 / 120.0, 1.0 / 6.0}};
+
+// The registration step, run by one warp on the shared-memory state.
+// GB300 issues an FP64 warp instruction in about 80 cycles whether one lane
+// or all 32 are active, so the pose arithmetic (FP64) is spread over lanes:
+// the three exponential coefficients on lanes 0-2, the exponential's and the
+// new pose's 12 entries on lanes 0-11, the 12 derived constants on lanes
+// 0-11.  The gradient direction, F'' along it and the step length come from
+// the double-float sums in FP32: they set a direction and a length, while the
+// pose they update stays in FP64.
+__device__ void step_warp(IterState* st, const double* S, const float* Shi, const float* Slo,
+                          unsigned long long pairs, unsigned long long cands, double* trace)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    auto sf = [&](int k) { return Shi[k] + Slo[k]; };
+    const int it = st->iter;
+    const float ellf = (float)st->ell;
+    const float il2 = 1.0f / (ellf * ellf), il4 = il2 * il2;
+    const float kapf = (float)st->kappa;
+    const float kl = kapf * il2;
+    // centred gradient: antisymmetric part of sum E p^T, and -sum E
+    const float gcw[3] = {((Shi[ST_EP + 5] - Shi[ST_EP + 7]) + (Slo[ST_EP + 5] - Slo[ST_EP + 7])) * kl,
+                          ((Shi[ST_EP + 6] - Shi[ST_EP + 2]) + (Slo[ST_EP + 6] - Slo[ST_EP + 2])) * kl,
+                          ((Shi[ST_EP + 1] - Shi[ST_EP + 3]) + (Slo[ST_EP + 1] - Slo[ST_EP + 3])) * kl};
+    const float gcv[3] = {-sf(ST_E) * kl, -sf(ST_E + 1) * kl, -sf(ST_E + 2) * kl};
+    // R = A^T, t = -R b, and the lever centre c, from the FP32 derived constants
+    float R[9], tt[3], cc[3], bv[3];
+    for (int r = 0; r < 3; ++r)
+        for (int q = 0; q < 3; ++q) R[3 * r + q] = st->Ahi[3 * q + r] + st->Alo[3 * q + r];
+    for (int r = 0; r < 3; ++r) {
+        bv[r] = st->bhi[r] + st->blo[r];
+        cc[r] = st->chi[r] + st->clo[r];
+    }
+    for (int r = 0; r < 3; ++r) tt[r] = -(R[3 * r] * bv[0] + R[3 * r + 1] * bv[1] + R[3 * r + 2] * bv[2]);
+    auto rm = [&](const float* a, float* o) {
+        for (int r = 0; r < 3; ++r) o[r] = R[3 * r] * a[0] + R[3 * r + 1] * a[1] + R[3 * r + 2] * a[2];
+    };
+    auto rtm = [&](const float* a, float* o) {
+        for (int r = 0; r < 3; ++r) o[r] = R[r] * a[0] + R[3 + r] * a[1] + R[6 + r] * a[2];
+    };
+    auto cr = [](const float* a, const float* b, float* o) {
+        o[0] = a[1] * b[2] - a[2] * b[1];
+        o[1] = a[2] * b[0] - a[0] * b[2];
+        o[2] = a[0] * b[1] - a[1] * b[0];
+    };
+    float gv[3], gw[3], tmp[3], tmp2[3];
+    rm(gcv, gv);
+    cr(cc, gcv, tmp);
+    for (int r = 0; r < 3; ++r) tmp[r] += gcw[r];
+    rm(tmp, gw);
+    cr(tt, gv, tmp);
+    for (int r = 0; r < 3; ++r) gw[r] += tmp[r];
+    // w~ = R^T g_w, v~ = -c x w~ + R^T (g_v - t x g_w)
+    float wt[3], vt[3];
+    rtm(gw, wt);
+    cr(tt, gw, tmp);
+    for (int r = 0; r < 3; ++r) tmp[r] = gv[r] - tmp[r];
+    rtm(tmp, vt);
+    cr(cc, wt, tmp2);
+    for (int r = 0; r < 3; ++r) vt[r] -= tmp2[r];
+    auto symqf = [&](int base, const float* a, const float* b) {
+        return sf(base) * a[0] * b[0] + sf(base + 1) * a[1] * b[1] + sf(base + 2) * a[2] * b[2] +
+               sf(base + 3) * (a[0] * b[1] + a[1] * b[0]) + sf(base + 4) * (a[0] * b[2] + a[2] * b[0]) +
+               sf(base + 5) * (a[1] * b[2] + a[2] * b[1]);
+    };
+    auto fullqf = [&](int base, const float* a, const float* b) {
+        float s = 0.0f;
+        for (int r = 0; r < 3; ++r)
+            s += a[r] * (sf(base + 3 * r) * b[0] + sf(base + 3 * r + 1) * b[1] + sf(base + 3 * r + 2) * b[2]);
+        return s;
+    };
+    const float ww = wt[0] * wt[0] + wt[1] * wt[1] + wt[2] * wt[2];
+    const float vv = vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2];
+    const float trWpp = sf(ST_WPP) + sf(ST_WPP + 1) + sf(ST_WPP + 2);
+    const float trEp = sf(ST_EP) + sf(ST_EP + 4) + sf(ST_EP + 8);
+    const float hww = -symqf(ST_PQP, wt, wt) * il4 - (trWpp * ww - symqf(ST_WPP, wt, wt)) * il2 +
+                      (fullqf(ST_EP, wt, wt) - trEp * ww) * il2;
+    const float Ev[3] = {sf(ST_E), sf(ST_E + 1), sf(ST_E + 2)};
+    const float Wpv[3] = {sf(ST_WP), sf(ST_WP + 1), sf(ST_WP + 2)};
+    cr(Wpv, vt, tmp);
+    cr(Ev, vt, tmp2);
+    const float hwv = fullqf(ST_PQ, wt, vt) * il4 -
+                      ((wt[0] * tmp[0] + wt[1] * tmp[1] + wt[2] * tmp[2]) +
+                       0.5f * (wt[0] * tmp2[0] + wt[1] * tmp2[1] + wt[2] * tmp2[2])) * il2;
+    const float hvv = symqf(ST_Q, vt, vt) * il4 - sf(ST_W) * vv * il2;
+    const float Fpp = kapf * (hww + 2.0f * hwv + hvv);
+    const float g[6] = {gw[0], gw[1], gw[2], gv[0], gv[1], gv[2]};
+    float gn2 = 0.0f;
+    for (int q = 0; q < 6; ++q) gn2 += g[q] * g[q];
+    const float wn = sqrtf(gw[0] * gw[0] + gw[1] * gw[1] + gw[2] * gw[2]);
+    const float vn = sqrtf(gv[0] * gv[0] + gv[1] * gv[1] + gv[2] * gv[2]);
+    float t = 0.0f;
+    if (gn2 > 0.0f) {
+        t = (Fpp < 0.0f) ? gn2 / (-Fpp) : 1e-3f / sqrtf(gn2);
+        const float max_tr = st->max_step_trans > 0.0 ? (float)st->max_step_trans : 0.5f * ellf;
+        const float max_rot = (float)st->max_step_rot;
+        if (t * wn > max_rot) t = max_rot / wn;
+        if (t * vn > max_tr) t = max_tr / vn;
+    }
+    // ---- FP64: exp(t g^) and T <- exp(t g^) T, across lanes ---------------
+    double xd[6];
+    for (int q = 0; q < 6; ++q) xd[q] = (double)(t * g[q]);
+    const double th2 = xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2];
+    double coef = 0.0;
+    if (th2 < 0.25) {
+        const int s = lane < 3 ? lane : 0;
+        double p = c_se3_series[s][0];
+#pragma unroll
+        for (int k = 1; k < 9; ++k) p = c_se3_series[s][k] - th2 * p;
+        coef = p;
+    } else {
+        const double th = sqrt(th2);
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        coef = lane == 0 ? sn / th : (lane == 1 ? (1.0 - cs) / th2 : (th - sn) / (th2 * th));
+    }
+    const double ca = __shfl_sync(full, coef, 0), cb = __shfl_sync(full, coef, 1), ccf = __shfl_sync(full, coef, 2);
+    const int r = (lane < 12) ? (lane >> 2) : 0;
+    const int q = lane & 3;
+    double e = 0.0;
+    {
+        const double w[3] = {xd[0], xd[1], xd[2]}, v[3] = {xd[3], xd[4], xd[5]};
+        if (q < 3) {
+            const double Wrq = (r == q) ? 0.0 : ((r == 0) ? (q == 1 ? -w[2] : w[1]) : (r == 1) ? (q == 0 ? w[2] : -w[0]) : (q == 0 ? -w[1] : w[0]));
+            const double w2 = w[r] * w[q] - (r == q ? th2 : 0.0);
+            e = (r == q ? 1.0 : 0.0) + ca * Wrq + cb * w2;
+        } else {
+            const double wxv[3] = {w[1] * v[2] - w[2] * v[1], w[2] * v[0] - w[0] * v[2], w[0] * v[1] - w[1] * v[0]};
+            const double wwv[3] = {w[1] * wxv[2] - w[2] * wxv[1], w[2] * wxv[0] - w[0] * wxv[2], w[0] * wxv[1] - w[1] * wxv[0]};
+            e = v[r] + cb * wxv[r] + ccf * wwv[r];
+        }
+    }
+    const double Er0 = __shfl_sync(full, e, 4 * r), Er1 = __shfl_sync(full, e, 4 * r + 1);
+    const double Er2 = __shfl_sync(full, e, 4 * r + 2), Er3 = __shfl_sync(full, e, 4 * r + 3);
+    double* T = st->T;
+    const double told = (lane < 12) ? T[lane] : 0.0;
+    const double tn = Er0 * T[q] + Er1 * T[4 + q] + Er2 * T[8 + q] + (q == 3 ? Er3 : 0.0);
+    if (trace && lane < 12) trace[(size_t)kTraceStride * it + 10 + lane] = told;
+    __syncwarp();
+    if (lane < 12) T[lane] = tn;
+    __syncwarp();
+    if (lane == 0) {
+        if ((it + 1) % 16 == 0) orthonormalize(T);
+        const double F = st->kappa * S[ST_W];
+        const double ith = F * st->norm;
+        const double srot = (double)(t * wn), strans = (double)(t * vn);
+        st->F = F;
+        st->i_theta = ith;
+        st->pairs = (long long)pairs;
+        st->cands = (long long)cands;
+        for (int k = 0; k < 6; ++k) st->grad[k] = (double)g[k];
+        st->pairs_total += (long long)pairs;
+        st->cands_total += (long long)cands;
+        st->Fpp = (double)Fpp;
+        st->gnorm = (double)sqrtf(gn2);
+        st->t = (double)t;
+        st->srot = srot;
+        st->strans = strans;
+        const double ell = st->ell;
+        const int at_floor = !st->anneal || ell <= st->ell_min;
+        const int converged = at_floor && srot < st->step_tol_rot && strans < st->step_tol_trans;
+        int decayed = 0;
+        if (!converged && st->anneal && ell > st->ell_min) {
+            const int fire = st->have_ref && fabs(ith - st->i_ref) < st->indicator_tol * fabs(st->i_ref);
+            if (fire) {
+                double nl = st->decay * ell;
+                if (nl < st->ell_min) nl = st->ell_min;
+                st->ell = nl;
+                st->have_ref = 0;
+                decayed = 1;
+            } else {
+                st->i_ref = ith;
+                st->have_ref = 1;
+            }
+        }
+        st->decayed = decayed;
+        if (trace) {
+            double* tr = trace + (size_t)kTraceStride * it;
+            tr[0] = ell; tr[1] = F; tr[2] = ith; tr[3] = st->gnorm; tr[4] = (double)Fpp;
+            tr[5] = (double)t; tr[6] = srot; tr[7] = strans; tr[8] = decayed; tr[9] = (double)pairs;
+        }
+        st->ell_last = ell;
+        st->iter = it + 1;
+        if (converged) {
+            st->status = 0;
+            st->done = 1;
+        } else if (it + 1 >= st->max_iters) {
+            st->status = 1;
+            st->done = 1;
+        }
+        // scalar derived constants
+        const float ln = (float)st->ell;
+        st->sg = -1.44269504f / (2.0f * ln * ln);
+        if (st->cutoff_mult > 0.0) {
+            const float rc = (float)st->cutoff_mult * ln;
+            st->rc = rc;
+            st->rc2 = rc * rc;
+            int lv = 0;
+            for (int k = 1; k < st->nlevels; ++k)
+                if (st->level_h[k] >= rc * 1.0001f) lv = k;
+            st->level = lv;
+        } else {
+            st->rc = -1.0f;
+            st->rc2 = -1.0f;
+            st->level = 0;
+        }
+    }
+    __syncwarp();
+    // derived T^-1 = (R^T, -R^T t) as double-float pairs, one entry per lane
+    if (lane < 9) {
+        const int rr = lane / 3, qq = lane % 3;
+        split_df(T[4 * qq + rr], st->Ahi[lane], st->Alo[lane]);
+    } else if (lane < 12) {
+        const int rr = lane - 9;
+        const double bvd = -(T[rr] * T[3] + T[4 + rr] * T[7] + T[8 + rr] * T[11]);
+        split_df(bvd, st->bhi[rr], st->blo[rr]);
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kFinalizeThreads)
+k_finalize(IterState* st, const float2* __restrict__ gs, const unsigned long long* __restrict__ gc_, int ngroups,
+           double* trace, cudaGraphConditionalHandle cond, int use_cond)
+{
+    static_assert(sizeof(IterState) % 8 == 0, "state is copied in 8-byte words");
+    constexpr int kWords = (int)(sizeof(IterState) / 8);
+    __shared__ double S[kStatN];
+    __shared__ float Shi[kStatN], Slo[kStatN];
+    __shared__ unsigned long long cs[2];
+    __shared__ unsigned long long sbuf[kWords];
+    if (st->done) {
+        // inside a graph's loop: stop it
+        if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+        return;
+    }
+    for (int i = threadIdx.x; i < kWords; i += kFinalizeThreads) sbuf[i] = reinterpret_cast<const unsigned long long*>(st)[i];
+    // one thread per statistic: the group sums in group order, all loads first
+    if (threadIdx.x < kStatN) {
+        const float2* row = gs + (size_t)threadIdx.x * kMaxGroups;
+        float2 v[kMaxGroups];
+#pragma unroll
+        for (int g = 0; g < kMaxGroups; ++g) v[g] = g < ngroups ? row[g] : make_float2(0.0f, 0.0f);
+        float hi = 0.0f, lo = 0.0f;
+#pragma unroll
+        for (int g = 0; g < kMaxGroups; ++g) df_add(hi, lo, v[g].x, v[g].y);
+        S[threadIdx.x] = (double)hi + (double)lo;
+        Shi[threadIdx.x] = hi;
+        Slo[threadIdx.x] = lo;
+    } else if (threadIdx.x == kStatN || threadIdx.x == kStatN + 1) {
+        const int c = threadIdx.x - kStatN;
+        unsigned long long t = 0;
+        for (int g = 0; g < ngroups; ++g) t += gc_[(size_t)c * kMaxGroups + g];
+        cs[c] = t;
+    }
+    __syncthreads();
+    IterState* sst = reinterpret_cast<IterState*>(sbuf);
+    if (sst->mode == 0) {
+        if (threadIdx.x == 0) take_step(sst, S, cs[0], cs[1], trace);
+    } else if (threadIdx.x < 32) {
+        step_warp(sst, S, Shi, Slo, cs[0], cs[1], trace);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kWords; i += kFinalizeThreads) reinterpret_cast<unsigned long long*>(st)[i] = sbuf[i];
+    if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, sst->done ? 0u : 1u);
 }
 
 }  // namespace
@@ -435,12 +659,12 @@ cudaError_t launch_init_state(IterState* st, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(IterState* st, const float2* part_stats, const unsigned long long* part_cnt, int part_cap,
-                            int nblocks, double* trace, cudaStream_t s)
+cudaError_t launch_finalize(IterState* st, const float2* grp_stats, const unsigned long long* grp_cnt, int nblocks,
+                            double* trace, cudaStream_t s)
 {
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
-    k_finalize<<<1, kFinalizeThreads, 0, s>>>(st, part_stats, part_cnt, part_cap, nblocks, trace,
-                                               cudaGraphConditionalHandle{}, 0);
+    const int ngroups = (nblocks + kGroupBlocks - 1) / kGroupBlocks;
+    k_finalize<<<1, kFinalizeThreads, 0, s>>>(st, grp_stats, grp_cnt, ngroups, trace, cudaGraphConditionalHandle{}, 0);
     return cudaGetLastError();
 }
 

@@ -30,7 +30,9 @@ constexpr int kSweepWarps = 4;   // warps per sweep block
 constexpr int kMaxLevels = 24;   // grid levels of one registration
 constexpr int kChunks = 8;       // chunks a group's candidate stream splits into
 constexpr int kChunkMin = 64;    // shortest chunk worth a work item
-constexpr int kFinalizeThreads = 1024;
+constexpr int kFinalizeThreads = 64;
+constexpr int kGroupBlocks = 32;   // sweep blocks per reduction group (the group's last block sums them)
+constexpr int kMaxGroups = 64;     // reduction groups per sweep launch (so at most 2048 sweep blocks)
 constexpr int kTraceStride = 22;  // doubles per iteration in the trace (CVO_TRACE_STRIDE)
 
 // Offsets of the 43 statistics (see the finalize kernel for their use).
@@ -108,9 +110,12 @@ struct SweepArgs {
     int rs;                    // record stride (float4)
     int dense;
     IterState* st;
-    float2* part_stats;        // [kStatN][part_cap]
+    float2* part_stats;        // [kStatN][part_cap] per-block sums
     unsigned long long* part_cnt; // [2][part_cap]
     int part_cap;
+    float2* grp_stats;         // [kStatN][kMaxGroups] per-group sums (read by the finalize)
+    unsigned long long* grp_cnt;  // [2][kMaxGroups]
+    unsigned* grp_arrivals;    // [kMaxGroups] arrival counters, zero between launches
     FeatConst fc;
 };
 
@@ -127,12 +132,13 @@ struct SweepLaunch {
     size_t smem;        // dynamic shared memory
 };
 cudaError_t sweep_launch_info(const FeatConst& fc, int rs, SweepLaunch* out);
-// k_finalize(IterState*, const float2*, const unsigned long long*, int cap, int nb,
-//            double* trace, cudaGraphConditionalHandle cond, int use_cond)
+// k_finalize(IterState*, const float2* grp_stats, const unsigned long long* grp_cnt,
+//            int ngroups, double* trace, cudaGraphConditionalHandle cond, int use_cond)
 const void* finalize_kernel();
 cudaError_t launch_init_state(IterState* st, cudaStream_t s);
-cudaError_t launch_finalize(IterState* st, const float2* part_stats, const unsigned long long* part_cnt,
-                            int part_cap, int nblocks, double* trace, cudaStream_t s);
+// Reduces the ceil(nblocks / kGroupBlocks) group sums of a sweep and takes the step.
+cudaError_t launch_finalize(IterState* st, const float2* grp_stats, const unsigned long long* grp_cnt, int nblocks,
+                            double* trace, cudaStream_t s);
 
 // setup (cvo_setup.cu)
 cudaError_t launch_bbox(const float* xyz, int n, unsigned* out6, int* bad, cudaStream_t s);

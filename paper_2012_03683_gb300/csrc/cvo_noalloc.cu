@@ -56,7 +56,10 @@ constexpr size_t kOffMisc = align256(kOffLevel + sizeof(LevelDesc));
 constexpr size_t kOffGroups = align256(kOffMisc + 16 * sizeof(unsigned));
 constexpr size_t kOffStats = align256(kOffGroups + sizeof(int2) * (kNoAllocMaxPoints / 32));
 constexpr size_t kOffCnt = align256(kOffStats + sizeof(float2) * kStatN * kNoAllocBlocks);
-constexpr size_t kOffX = align256(kOffCnt + sizeof(unsigned long long) * 2 * kNoAllocBlocks);
+constexpr size_t kOffGStats = align256(kOffCnt + sizeof(unsigned long long) * 2 * kNoAllocBlocks);
+constexpr size_t kOffGCnt = align256(kOffGStats + sizeof(float2) * kStatN * kMaxGroups);
+constexpr size_t kOffGArr = align256(kOffGCnt + sizeof(unsigned long long) * 2 * kMaxGroups);
+constexpr size_t kOffX = align256(kOffGArr + sizeof(unsigned) * kMaxGroups);
 constexpr size_t kOffZ = align256(kOffX + sizeof(float4) * kNoAllocMaxRec * kNoAllocMaxPoints);
 constexpr size_t kUsedBytes = align256(kOffZ + sizeof(float4) * kNoAllocMaxRec * kNoAllocMaxPoints);
 constexpr size_t kScratchBytes = 4608 * 1024;   // 4.5 MiB
@@ -117,9 +120,10 @@ bool is_device_pointer(const void* p)
 // Writes the state block, the level descriptor and the query groups, and
 // resets the bounding-box counters (min to all ones, max and flag to zero).
 __global__ void k_na_setup(IterState init, LevelDesc ld, int n, IterState* st, LevelDesc* lv, int2* groups,
-                           unsigned* misc)
+                           unsigned* misc, unsigned* arrivals)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid < kMaxGroups) arrivals[tid] = 0u;   // the sweep's group counters start at zero
     if (tid == 0) {
         *st = init;
         *lv = ld;
@@ -276,6 +280,9 @@ extern "C" cvo_status cvo_evaluate_dense_noalloc(const cvo_params* p, void* cuda
     int2* groups = (int2*)(base + kOffGroups);
     float2* stats = (float2*)(base + kOffStats);
     unsigned long long* cnt = (unsigned long long*)(base + kOffCnt);
+    float2* gstats = (float2*)(base + kOffGStats);
+    unsigned long long* gcnt = (unsigned long long*)(base + kOffGCnt);
+    unsigned* garr = (unsigned*)(base + kOffGArr);
     float4* xrec = (float4*)(base + kOffX);
     float4* zrec = (float4*)(base + kOffZ);
     const int rs = 1 + (D * 4 + 15) / 16;
@@ -304,7 +311,7 @@ extern "C" cvo_status cvo_evaluate_dense_noalloc(const cvo_params* p, void* cuda
     ld.ngroups = (n + 31) / 32;
 
     g_launch_count.fetch_add(2, std::memory_order_relaxed);
-    k_na_setup<<<(ld.ngroups + 255) / 256, 256, 0, s>>>(init, ld, n, st, lv, groups, misc);
+    k_na_setup<<<(ld.ngroups + 255) / 256, 256, 0, s>>>(init, ld, n, st, lv, groups, misc, garr);
     NA_CUDA(cudaGetLastError());
     NA_CUDA(launch_bbox(Z->xyz, m, misc, (int*)(misc + 6), s));
     NA_CUDA(launch_bbox(X->xyz, n, misc + 8, (int*)(misc + 6), s));   // finiteness of X (box unused)
@@ -328,11 +335,14 @@ extern "C" cvo_status cvo_evaluate_dense_noalloc(const cvo_params* p, void* cuda
     a.part_stats = stats;
     a.part_cnt = cnt;
     a.part_cap = kNoAllocBlocks;
+    a.grp_stats = gstats;
+    a.grp_cnt = gcnt;
+    a.grp_arrivals = garr;
     a.fc = fc;
     const int items = ld.ngroups * kChunks;
     const int nblocks = std::max(1, std::min((items + kSweepWarps - 1) / kSweepWarps, kNoAllocBlocks));
     NA_CUDA(launch_sweep(a, nblocks, s));
-    NA_CUDA(launch_finalize(st, stats, cnt, kNoAllocBlocks, nblocks, nullptr, s));
+    NA_CUDA(launch_finalize(st, gstats, gcnt, nblocks, nullptr, s));
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
     k_na_output<<<1, 64, 0, s>>>(st, misc, out_device);
     NA_CUDA(cudaGetLastError());

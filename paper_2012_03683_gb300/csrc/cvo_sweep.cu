@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
     __shared__ unsigned long long redc[kSweepWarps][2];
     __shared__ float cst[30];               // Ahi, Alo, bhi, blo, chi, clo
     const IterState* st = a.st;
-    if (st->done) return;
+    if (st->done) return;   // uniform: no block arrives at the group counters
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x < 30) cst[threadIdx.x] = (&st->Ahi[0])[threadIdx.x];
 #pragma unroll
@@ -474,6 +474,42 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
         a.part_cnt[blockIdx.x] = t0;
         a.part_cnt[(size_t)a.part_cap + blockIdx.x] = t1;
     }
+
+    // Group reduction: the last block of each group of kGroupBlocks blocks to
+    // arrive sums the group's partials in block order (deterministic; nothing
+    // waits) and resets the group's arrival counter for the next launch.
+    __shared__ int is_last;
+    const int grp = blockIdx.x / kGroupBlocks;
+    const int first = grp * kGroupBlocks;
+    const int members = min(kGroupBlocks, (int)gridDim.x - first);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(&a.grp_arrivals[grp], 1u) == (unsigned)(members - 1));
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (threadIdx.x < kStatN) {
+        const float2* row = a.part_stats + (size_t)threadIdx.x * a.part_cap + first;
+        float2 v[kGroupBlocks];
+#pragma unroll
+        for (int b = 0; b < kGroupBlocks; ++b) v[b] = b < members ? __ldcg(row + b) : make_float2(0.0f, 0.0f);
+        float hi = 0.0f, lo = 0.0f;
+#pragma unroll
+        for (int b = 0; b < kGroupBlocks; ++b) {
+            float s, e;
+            two_sum(hi, v[b].x, s, e);
+            e = __fadd_rn(e, __fadd_rn(lo, v[b].y));
+            hi = __fadd_rn(s, e);
+            lo = __fsub_rn(e, __fsub_rn(hi, s));
+        }
+        a.grp_stats[(size_t)threadIdx.x * kMaxGroups + grp] = make_float2(hi, lo);
+    } else if (threadIdx.x == kStatN || threadIdx.x == kStatN + 1) {
+        const int c = threadIdx.x - kStatN;
+        unsigned long long t = 0;
+        for (int b = 0; b < members; ++b) t += __ldcg(a.part_cnt + (size_t)c * a.part_cap + first + b);
+        a.grp_cnt[(size_t)c * kMaxGroups + grp] = t;
+    }
+    if (threadIdx.x == 0) a.grp_arrivals[grp] = 0u;
 }
 
 template <class Feat>
