@@ -160,6 +160,54 @@ def workload():
     return p, kw, config
 
 
+def batch_section(cvo, torch, dev, flush, reps=2):
+    """64 cube pairs of 5k-60k points (RGB + labels in bf16): one batched
+    registration (one graph launch for the whole batch) against the same pairs
+    registered one after another through cvo_register_pair."""
+    import scenes
+    pairs = scenes.batch_pairs()
+    pr = pairs[0].params
+    kw = dict(blocks=pairs[0].blocks, ell=pr["ell"], cutoff_mult=pr["cutoff_mult"], max_iters=pr["max_iters"])
+    args = []
+    for p in pairs:
+        args.append((torch.tensor(p.X, device=dev), torch.tensor(p.Z, device=dev), np.eye(4),
+                     torch.tensor(p.FX, device=dev).to(torch.bfloat16),
+                     torch.tensor(p.FZ, device=dev).to(torch.bfloat16)))
+    out = {"workload": "batch-64: cube pairs, 5k-60k points per cloud, rgb + 19 labels in bf16, "
+                       f"l = {pr['ell']}, cutoff 3 l, {pr['max_iters']} iterations",
+           "pairs": len(pairs), "points": int(sum(p.n + p.m for p in pairs))}
+    with cvo.CVO(**kw) as h:
+        h.register_batch(args)
+        torch.cuda.synchronize()
+        t_b, evals_b = 0.0, 0
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, infos, _ = h.register_batch(args)
+            torch.cuda.synchronize()
+            t_b += time.perf_counter() - t0
+            evals_b += sum(i["pairs"] for i in infos)
+        for a in args[:2]:
+            h.register(*a)
+        t_p, evals_p = 0.0, 0
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for a in args:
+                _, info = h.register(*a)
+                evals_p += info["pairs"]
+            torch.cuda.synchronize()
+            t_p += time.perf_counter() - t0
+    out["batched"] = {"registered_pairs_per_s": reps * len(pairs) / t_b, "pair_evals_per_s": evals_b / t_b,
+                      "ms_per_batch": 1e3 * t_b / reps}
+    out["plain"] = {"registered_pairs_per_s": reps * len(pairs) / t_p, "pair_evals_per_s": evals_p / t_p,
+                    "ms_per_batch": 1e3 * t_p / reps}
+    out["speedup"] = t_p / t_b
+    return out
+
+
 def cpu_baseline(p, kw, iters=20):
     import oracle
     oracle.build()
@@ -209,6 +257,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cvo", choices=["cvo", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain section")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -305,6 +354,7 @@ def main():
     e2e_ms = max_over_ranks(dist, world, e2e_ms, dev)
     e2e_pairs = sum_over_ranks(dist, world, float(e2e_pairs), dev)
     h.close()
+    batch = batch_section(cvo, torch, dev, flush) if (rank == 0 and not args.no_batch) else None
 
     if rank != 0:
         return
@@ -337,6 +387,7 @@ def main():
                                     f"(sm_max_mhz {peak_src})"},
         "clocks": clocks,
         "final_pose_err_vs_truth": pose_err,
+        "batch": batch,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, kw)

@@ -1,7 +1,7 @@
 // C ABI of libcvo (declared in include/cvo.h): argument checking, device
-// scratch, the per-pair setup, and the drivers of evaluation and
-// registration.  Every step of the computation runs in this library's CUDA
-// kernels; the host only orders launches and copies results.
+// scratch, the per-pair setup, and the drivers of evaluation, registration
+// and batched registration.  Every step of the computation runs in this
+// library's CUDA kernels; the host only orders launches and copies results.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -98,6 +98,28 @@ float decode_orderable(unsigned u)
     return f;
 }
 
+// Device resources of one prepared pair: grid levels of Z, Morton-ordered
+// queries of X and their groups, the iteration state.
+struct PairRes {
+    DevBuf xrec, morton, levels_dev, state;
+    DevBuf zrec[kMaxLevels], cell_start[kMaxLevels], groups[kMaxLevels];
+    int n = 0, m = 0, nlevels = 0;
+    LevelHost lv[kMaxLevels];
+    double zc[3] = {0, 0, 0};
+    int max_items = 1;
+
+    void free_all()
+    {
+        DevBuf* bufs[] = {&xrec, &morton, &levels_dev, &state};
+        for (DevBuf* b : bufs) release(*b);
+        for (int k = 0; k < kMaxLevels; ++k) {
+            release(zrec[k]);
+            release(cell_start[k]);
+            release(groups[k]);
+        }
+    }
+};
+
 }  // namespace
 
 // Lets other translation units report an error through cvo_last_error().
@@ -109,30 +131,29 @@ struct cvo_handle_s {
     int device = 0;
     int num_sms = 152;
     int timing = 0;
+    int use_graph = 1;
+    // scratch shared by every pair's setup (used one pair at a time)
     DevBuf stage_xyz[2], stage_feat[2];
-    DevBuf keys, vals, keys2, vals2, sort_tmp, flags, gidx;
-    DevBuf xrec, morton;
-    DevBuf zrec[kMaxLevels], cell_start[kMaxLevels], groups[kMaxLevels];
-    DevBuf misc, levels_dev, state, part_stats, part_cnt, grp_stats, grp_cnt, grp_arrivals, trace;
-    IterState* h_state = nullptr;   // pinned mirror
+    DevBuf keys, vals, keys2, vals2, sort_tmp, flags, gidx, misc;
+    // sweep / finalize scratch
+    DevBuf part_stats, part_cnt, grp_stats, grp_cnt, grp_arrivals, pairs_dev, counters, trace;
+    std::vector<PairRes> pr;
+    IterState* h_state = nullptr;   // pinned mirror(s)
+    int h_state_cap = 0;
     unsigned* h_misc = nullptr;     // pinned
     int last_iters = 0;
     double sweep_ms = 0.0;
     int sweep_n = 0;
     std::vector<cudaEvent_t> evs;
-    // prepared pair
-    int n = 0, m = 0, nlevels = 0, dense = 0, rs = 1, rec_bf16 = 0, D = 0;
-    LevelHost lv[kMaxLevels];
-    double zc[3] = {0, 0, 0};
-    int sweep_blocks = 1;
+    // shared by the pairs of one call
+    int dense = 0, rs = 1, rec_bf16 = 0, D = 0;
     FeatConst fc{};
     double kappa = 1.0;
+    int sweep_blocks = 1;
     // tuning: grid cell edge = cell_factor * cutoff radius; query groups live in
     // Morton super-cells about 2^super_delta cutoff radii wide
     double cell_factor = 0.5;
     int super_delta = 2;
-    int graph_pending = 0;
-    int use_graph = 1;
 };
 
 namespace {
@@ -259,16 +280,44 @@ cvo_status sort_pairs(cvo_handle h, int n, int nbits, unsigned** ks, unsigned** 
     return CVO_OK;
 }
 
-// Builds the grid levels of Z, the Morton-ordered queries of X and their groups
-// for lengthscales in [ell_lo, ell_hi].
-cvo_status prepare(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, double ell_hi, double ell_lo)
+// Feature constants and kappa = sigma^2 prod sigma_b^2 (shared by all pairs).
+void set_features(cvo_handle h, int rec_bf16)
 {
     const cvo_params& p = h->p;
-    const int D = feat_dim(p);
+    FeatConst& fc = h->fc;
+    std::memset(&fc, 0, sizeof(fc));
+    fc.n_blocks = p.n_blocks;
+    int off = 0;
+    double kappa = p.sigma * p.sigma;
+    for (int b = 0; b < p.n_blocks; ++b) {
+        fc.dim[b] = p.blocks[b].dim;
+        fc.kind[b] = p.blocks[b].kind;
+        fc.off[b] = off;
+        off += p.blocks[b].dim;
+        if (p.blocks[b].kind == CVO_FEAT_SE) {
+            const double sc = p.blocks[b].scale;
+            fc.s[b] = (float)(-1.4426950408889634 / (2.0 * sc * sc));
+            kappa *= p.blocks[b].sigma * p.blocks[b].sigma;
+        }
+    }
+    fc.D = off;
+    fc.bf16 = rec_bf16;
+    h->kappa = kappa;
+    h->D = off;
+    h->rec_bf16 = rec_bf16;
+    h->rs = 1 + (off * (rec_bf16 ? 2 : 4) + 15) / 16;
+    h->dense = !(p.cutoff_mult > 0.0);
+}
+
+// Builds the grid levels of Z, the Morton-ordered queries of X and their groups
+// for lengthscales in [ell_lo, ell_hi].  Uses the handle's shared scratch.
+cvo_status prepare(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud* Z, double ell_hi, double ell_lo)
+{
+    const cvo_params& p = h->p;
+    const int D = h->D;
     const int n = X->n, m = Z->n;
-    h->n = n;
-    h->m = m;
-    h->D = D;
+    P.n = n;
+    P.m = m;
     const float *xyz_x, *xyz_z;
     const void *feat_x, *feat_z;
     CVO_TRY(stage(h, X, 0, D, &xyz_x, &feat_x));
@@ -296,13 +345,9 @@ cvo_status prepare(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, double 
         xmax[a] = decode_orderable(h->h_misc[3 + a]);
         zmin[a] = decode_orderable(h->h_misc[6 + a]);
         zmax[a] = decode_orderable(h->h_misc[9 + a]);
-        h->zc[a] = 0.5 * ((double)zmin[a] + (double)zmax[a]);
+        P.zc[a] = 0.5 * ((double)zmin[a] + (double)zmax[a]);
     }
 
-    // record layout
-    h->rec_bf16 = (D > 0 && X->feat_dtype == CVO_BF16 && Z->feat_dtype == CVO_BF16) ? 1 : 0;
-    const int payload = D * (h->rec_bf16 ? 2 : 4);
-    h->rs = 1 + (payload + 15) / 16;
     const int rs = h->rs;
     const int nmax = std::max(n, m);
     CVO_CUDA(ensure(h->keys, (size_t)nmax * 4));
@@ -311,10 +356,9 @@ cvo_status prepare(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, double 
     CVO_CUDA(ensure(h->vals2, (size_t)nmax * 4));
 
     // grid levels of Z
-    h->dense = !(p.cutoff_mult > 0.0);
     if (h->dense) {
-        h->nlevels = 1;
-        LevelHost& L = h->lv[0];
+        P.nlevels = 1;
+        LevelHost& L = P.lv[0];
         L.h = 1.0;
         L.rdesign = 1.0;
         L.nx = L.ny = L.nz = 1;
@@ -324,9 +368,9 @@ cvo_status prepare(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, double 
         const double rc_hi = p.cutoff_mult * ell_hi, rc_lo = p.cutoff_mult * ell_lo;
         int nl = 1 + (int)std::floor(std::log(rc_hi / rc_lo) / std::log(std::sqrt(2.0)) + 1e-9);
         nl = std::max(1, std::min(nl, kMaxLevels));
-        h->nlevels = nl;
+        P.nlevels = nl;
         for (int k = 0; k < nl; ++k) {
-            LevelHost& L = h->lv[k];
+            LevelHost& L = P.lv[k];
             L.rdesign = rc_hi * 1.0002 / std::pow(std::sqrt(2.0), k);
             double hh = h->cell_factor * L.rdesign;
             for (;;) {
@@ -341,48 +385,46 @@ cvo_status prepare(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, double 
             L.ox = zmin[0]; L.oy = zmin[1]; L.oz = zmin[2];
         }
     }
-    for (int k = 0; k < h->nlevels; ++k) {
-        LevelHost& L = h->lv[k];
-        CVO_CUDA(ensure(h->zrec[k], (size_t)std::max(m, 1) * rs * sizeof(float4)));
-        CVO_CUDA(ensure(h->cell_start[k], (size_t)(L.ncells + 1) * sizeof(int)));
+    for (int k = 0; k < P.nlevels; ++k) {
+        LevelHost& L = P.lv[k];
+        CVO_CUDA(ensure(P.zrec[k], (size_t)std::max(m, 1) * rs * sizeof(float4)));
+        CVO_CUDA(ensure(P.cell_start[k], (size_t)(L.ncells + 1) * sizeof(int)));
         if (h->dense) {
             const int cs[2] = {0, m};
-            CVO_CUDA(cudaMemcpyAsync(h->cell_start[k].p, cs, sizeof(cs), cudaMemcpyHostToDevice, h->s));
-            CVO_CUDA(launch_pack(xyz_z, feat_z, Z->feat_dtype == CVO_BF16, D, nullptr, m, (float4*)h->zrec[k].p, rs,
+            CVO_CUDA(cudaMemcpyAsync(P.cell_start[k].p, cs, sizeof(cs), cudaMemcpyHostToDevice, h->s));
+            CVO_CUDA(launch_pack(xyz_z, feat_z, Z->feat_dtype == CVO_BF16, D, nullptr, m, (float4*)P.zrec[k].p, rs,
                                  h->rec_bf16, h->s));
         } else {
             CVO_CUDA(launch_cell_keys(xyz_z, m, L.ox, L.oy, L.oz, (float)(1.0 / L.h), L.nx, L.ny, L.nz,
                                       (unsigned*)h->keys.p, (unsigned*)h->vals.p, h->s));
             unsigned *ks, *vs;
             CVO_TRY(sort_pairs(h, m, bits_for(L.ncells), &ks, &vs));
-            CVO_CUDA(launch_cell_start(ks, m, (int)L.ncells, (int*)h->cell_start[k].p, h->s));
-            CVO_CUDA(launch_pack(xyz_z, feat_z, Z->feat_dtype == CVO_BF16, D, vs, m, (float4*)h->zrec[k].p, rs,
+            CVO_CUDA(launch_cell_start(ks, m, (int)L.ncells, (int*)P.cell_start[k].p, h->s));
+            CVO_CUDA(launch_pack(xyz_z, feat_z, Z->feat_dtype == CVO_BF16, D, vs, m, (float4*)P.zrec[k].p, rs,
                                  h->rec_bf16, h->s));
         }
-        // keep a synchronous point per level so the shared sort buffers are
-        // never overwritten while in use (the stream orders this anyway)
     }
 
     // queries: Morton order of X in its own frame
     double ext = 0.0;
     for (int a = 0; a < 3; ++a) ext = std::max(ext, (double)xmax[a] - xmin[a]);
     const double cell0 = std::max(ext / 1024.0, 1e-6);
-    CVO_CUDA(ensure(h->xrec, (size_t)std::max(n, 1) * rs * sizeof(float4)));
-    CVO_CUDA(ensure(h->morton, (size_t)std::max(n, 1) * 4));
+    CVO_CUDA(ensure(P.xrec, (size_t)std::max(n, 1) * rs * sizeof(float4)));
+    CVO_CUDA(ensure(P.morton, (size_t)std::max(n, 1) * 4));
     CVO_CUDA(launch_morton_keys(xyz_x, n, xmin[0], xmin[1], xmin[2], (float)(1.0 / cell0), (unsigned*)h->keys.p,
                                 (unsigned*)h->vals.p, h->s));
     {
         unsigned *ks, *vs;
         CVO_TRY(sort_pairs(h, n, 30, &ks, &vs));
-        CVO_CUDA(launch_pack(xyz_x, feat_x, X->feat_dtype == CVO_BF16, D, vs, n, (float4*)h->xrec.p, rs, h->rec_bf16,
+        CVO_CUDA(launch_pack(xyz_x, feat_x, X->feat_dtype == CVO_BF16, D, vs, n, (float4*)P.xrec.p, rs, h->rec_bf16,
                              h->s));
-        CVO_CUDA(cudaMemcpyAsync(h->morton.p, ks, (size_t)n * 4, cudaMemcpyDeviceToDevice, h->s));
+        CVO_CUDA(cudaMemcpyAsync(P.morton.p, ks, (size_t)n * 4, cudaMemcpyDeviceToDevice, h->s));
     }
     // query groups per level
     CVO_CUDA(ensure(h->flags, (size_t)std::max(n, 1) * 4));
     CVO_CUDA(ensure(h->gidx, (size_t)std::max(n, 1) * 4));
-    for (int k = 0; k < h->nlevels; ++k) {
-        LevelHost& L = h->lv[k];
+    for (int k = 0; k < P.nlevels; ++k) {
+        LevelHost& L = P.lv[k];
         int sh = 30;
         if (!h->dense) {
             // Morton super-cells of edge about 2^super_delta times the
@@ -391,18 +433,18 @@ cvo_status prepare(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, double 
             sh = 3 * std::max(0, std::min(10, e));
         }
         L.shift = sh;
-        CVO_CUDA(ensure(h->groups[k], (size_t)std::max(n, 1) * sizeof(int2)));
-        CVO_CUDA(launch_group_flags((const unsigned*)h->morton.p, n, sh, (unsigned*)h->flags.p, h->s));
+        CVO_CUDA(ensure(P.groups[k], (size_t)std::max(n, 1) * sizeof(int2)));
+        CVO_CUDA(launch_group_flags((const unsigned*)P.morton.p, n, sh, (unsigned*)h->flags.p, h->s));
         CVO_CUDA(exclusive_scan_u32((const unsigned*)h->flags.p, (unsigned*)h->gidx.p, n, misc + 16 + k, h->s));
-        CVO_CUDA(launch_group_write((const unsigned*)h->morton.p, (const unsigned*)h->flags.p,
-                                    (const unsigned*)h->gidx.p, n, sh, (int2*)h->groups[k].p, h->s));
+        CVO_CUDA(launch_group_write((const unsigned*)P.morton.p, (const unsigned*)h->flags.p,
+                                    (const unsigned*)h->gidx.p, n, sh, (int2*)P.groups[k].p, h->s));
     }
-    CVO_CUDA(cudaMemcpyAsync(h->h_misc + 16, misc + 16, h->nlevels * sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
+    CVO_CUDA(cudaMemcpyAsync(h->h_misc + 16, misc + 16, P.nlevels * sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
     CVO_CUDA(cudaStreamSynchronize(h->s));
     int max_items = 1;
     LevelDesc ld[kMaxLevels];
-    for (int k = 0; k < h->nlevels; ++k) {
-        LevelHost& L = h->lv[k];
+    for (int k = 0; k < P.nlevels; ++k) {
+        LevelHost& L = P.lv[k];
         L.ngroups = n > 0 ? (int)h->h_misc[16 + k] : 0;
         max_items = std::max(max_items, L.ngroups * kChunks);
         LevelDesc& d = ld[k];
@@ -410,48 +452,33 @@ cvo_status prepare(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, double 
         d.inv_h = (float)(1.0 / L.h);
         d.ox = L.ox; d.oy = L.oy; d.oz = L.oz;
         d.nx = L.nx; d.ny = L.ny; d.nz = L.nz;
-        d.cell_start = (const int*)h->cell_start[k].p;
-        d.zrec = (const float4*)h->zrec[k].p;
-        d.groups = (const int2*)h->groups[k].p;
+        d.cell_start = (const int*)P.cell_start[k].p;
+        d.zrec = (const float4*)P.zrec[k].p;
+        d.groups = (const int2*)P.groups[k].p;
         d.ngroups = L.ngroups;
         d.pad_ = 0;
     }
-    CVO_CUDA(ensure(h->levels_dev, sizeof(ld)));
-    CVO_CUDA(cudaMemcpyAsync(h->levels_dev.p, ld, h->nlevels * sizeof(LevelDesc), cudaMemcpyHostToDevice, h->s));
-    h->sweep_blocks = std::max(1, std::min((max_items + kSweepWarps - 1) / kSweepWarps, h->num_sms * 8));
-    CVO_CUDA(ensure(h->part_stats, (size_t)kStatN * h->sweep_blocks * sizeof(float2)));
-    CVO_CUDA(ensure(h->part_cnt, (size_t)2 * h->sweep_blocks * sizeof(unsigned long long)));
-    CVO_CUDA(ensure(h->grp_stats, (size_t)kStatN * kMaxGroups * sizeof(float2)));
-    CVO_CUDA(ensure(h->grp_cnt, (size_t)2 * kMaxGroups * sizeof(unsigned long long)));
-    CVO_CUDA(ensure(h->grp_arrivals, (size_t)kMaxGroups * sizeof(unsigned)));
-    CVO_CUDA(cudaMemsetAsync(h->grp_arrivals.p, 0, (size_t)kMaxGroups * sizeof(unsigned), h->s));
-
-    // feature constants
-    FeatConst& fc = h->fc;
-    std::memset(&fc, 0, sizeof(fc));
-    fc.n_blocks = p.n_blocks;
-    int off = 0;
-    double kappa = p.sigma * p.sigma;
-    for (int b = 0; b < p.n_blocks; ++b) {
-        fc.dim[b] = p.blocks[b].dim;
-        fc.kind[b] = p.blocks[b].kind;
-        fc.off[b] = off;
-        off += p.blocks[b].dim;
-        if (p.blocks[b].kind == CVO_FEAT_SE) {
-            const double sc = p.blocks[b].scale;
-            fc.s[b] = (float)(-1.4426950408889634 / (2.0 * sc * sc));
-            kappa *= p.blocks[b].sigma * p.blocks[b].sigma;
-        }
-    }
-    fc.D = D;
-    fc.bf16 = h->rec_bf16;
-    h->kappa = kappa;
+    P.max_items = max_items;
+    CVO_CUDA(ensure(P.levels_dev, sizeof(ld)));
+    CVO_CUDA(cudaMemcpyAsync(P.levels_dev.p, ld, P.nlevels * sizeof(LevelDesc), cudaMemcpyHostToDevice, h->s));
     return CVO_OK;
 }
 
-cvo_status init_state(cvo_handle h, const double* T, double ell, int mode)
+cvo_status ensure_host_states(cvo_handle h, int n)
 {
-    IterState* st = h->h_state;
+    if (n <= h->h_state_cap) return CVO_OK;
+    if (h->h_state) cudaFreeHost(h->h_state);
+    h->h_state = nullptr;
+    h->h_state_cap = 0;
+    CVO_CUDA(cudaMallocHost((void**)&h->h_state, (size_t)n * sizeof(IterState)));
+    h->h_state_cap = n;
+    return CVO_OK;
+}
+
+// Initial state of one pair; host copy in h->h_state[slot].
+cvo_status init_state(cvo_handle h, PairRes& P, int slot, const double* T, double ell, int mode)
+{
+    IterState* st = h->h_state + slot;
     std::memset(st, 0, sizeof(IterState));
     std::memcpy(st->T, T, 16 * sizeof(double));
     const cvo_params& p = h->p;
@@ -459,7 +486,7 @@ cvo_status init_state(cvo_handle h, const double* T, double ell, int mode)
     st->ell_last = ell;
     st->mode = mode;
     st->kappa = h->kappa;
-    st->norm = (h->n > 0 && h->m > 0) ? 1.0 / std::sqrt((double)h->n * (double)h->m) : 0.0;
+    st->norm = (P.n > 0 && P.m > 0) ? 1.0 / std::sqrt((double)P.n * (double)P.m) : 0.0;
     st->cutoff_mult = p.cutoff_mult;
     st->ell_min = p.anneal ? p.ell_min : ell;
     st->decay = p.decay;
@@ -471,53 +498,111 @@ cvo_status init_state(cvo_handle h, const double* T, double ell, int mode)
     st->max_iters = p.max_iters;
     st->anneal = p.anneal;
     st->status = 1;
-    for (int a = 0; a < 3; ++a) st->c[a] = h->zc[a];
-    st->nlevels = h->nlevels;
-    for (int k = 0; k < h->nlevels; ++k) st->level_h[k] = (float)h->lv[k].rdesign;
+    for (int a = 0; a < 3; ++a) st->c[a] = P.zc[a];
+    st->nlevels = P.nlevels;
+    for (int k = 0; k < P.nlevels; ++k) st->level_h[k] = (float)P.lv[k].rdesign;
     if (mode == 1 && p.max_iters == 0) st->done = 1;
-    CVO_CUDA(ensure(h->state, sizeof(IterState)));
-    CVO_CUDA(cudaMemcpyAsync(h->state.p, st, sizeof(IterState), cudaMemcpyHostToDevice, h->s));
-    CVO_CUDA(launch_init_state((IterState*)h->state.p, h->s));
+    CVO_CUDA(ensure(P.state, sizeof(IterState)));
+    CVO_CUDA(cudaMemcpyAsync(P.state.p, st, sizeof(IterState), cudaMemcpyHostToDevice, h->s));
+    CVO_CUDA(launch_init_state((IterState*)P.state.p, h->s));
     return CVO_OK;
 }
 
-SweepArgs sweep_args(cvo_handle h)
+// Sweep scratch sized for nblocks blocks; the pair table uploaded.
+cvo_status setup_sweep(cvo_handle h, const std::vector<PairDesc>& table, int nblocks, SweepArgs* a, bool groups)
 {
-    SweepArgs a;
-    a.levels = (const LevelDesc*)h->levels_dev.p;
-    a.xrec = (const float4*)h->xrec.p;
-    a.n = h->n;
-    a.m = h->m;
-    a.rs = h->rs;
-    a.dense = h->dense;
-    a.st = (IterState*)h->state.p;
-    a.part_stats = (float2*)h->part_stats.p;
-    a.part_cnt = (unsigned long long*)h->part_cnt.p;
-    a.grp_stats = (float2*)h->grp_stats.p;
-    a.grp_cnt = (unsigned long long*)h->grp_cnt.p;
-    a.grp_arrivals = (unsigned*)h->grp_arrivals.p;
-    a.part_cap = h->sweep_blocks;
-    a.fc = h->fc;
-    return a;
+    h->sweep_blocks = nblocks;
+    CVO_CUDA(ensure(h->part_stats, (size_t)kStatN * nblocks * sizeof(float2)));
+    CVO_CUDA(ensure(h->part_cnt, (size_t)2 * nblocks * sizeof(unsigned long long)));
+    CVO_CUDA(ensure(h->grp_stats, (size_t)kStatN * kMaxGroups * sizeof(float2)));
+    CVO_CUDA(ensure(h->grp_cnt, (size_t)2 * kMaxGroups * sizeof(unsigned long long)));
+    CVO_CUDA(ensure(h->grp_arrivals, (size_t)kMaxGroups * sizeof(unsigned)));
+    CVO_CUDA(ensure(h->counters, 16 * sizeof(unsigned)));
+    CVO_CUDA(cudaMemsetAsync(h->grp_arrivals.p, 0, (size_t)kMaxGroups * sizeof(unsigned), h->s));
+    CVO_CUDA(cudaMemsetAsync(h->counters.p, 0, 16 * sizeof(unsigned), h->s));
+    CVO_CUDA(ensure(h->pairs_dev, table.size() * sizeof(PairDesc)));
+    CVO_CUDA(cudaMemcpyAsync(h->pairs_dev.p, table.data(), table.size() * sizeof(PairDesc), cudaMemcpyHostToDevice,
+                             h->s));
+    a->pairs = (const PairDesc*)h->pairs_dev.p;
+    a->npairs = (int)table.size();
+    a->rs = h->rs;
+    a->dense = h->dense;
+    a->part_stats = (float2*)h->part_stats.p;
+    a->part_cnt = (unsigned long long*)h->part_cnt.p;
+    a->part_cap = nblocks;
+    a->grp_stats = (float2*)h->grp_stats.p;
+    a->grp_cnt = (unsigned long long*)h->grp_cnt.p;
+    a->grp_arrivals = groups ? (unsigned*)h->grp_arrivals.p : nullptr;
+    a->fc = h->fc;
+    return CVO_OK;
 }
 
-cvo_status fetch_state(cvo_handle h)
+PairDesc pair_desc(const PairRes& P, int b0, int b1)
 {
-    CVO_CUDA(cudaMemcpyAsync(h->h_state, h->state.p, sizeof(IterState), cudaMemcpyDeviceToHost, h->s));
+    PairDesc d;
+    d.levels = (const LevelDesc*)P.levels_dev.p;
+    d.xrec = (const float4*)P.xrec.p;
+    d.st = (IterState*)P.state.p;
+    d.n = P.n;
+    d.m = P.m;
+    d.b0 = b0;
+    d.b1 = b1;
+    return d;
+}
+
+int single_pair_blocks(cvo_handle h, const PairRes& P)
+{
+    return std::max(1, std::min((P.max_items + kSweepWarps - 1) / kSweepWarps, h->num_sms * 8));
+}
+
+cvo_status fetch_states(cvo_handle h, int npairs)
+{
+    for (int k = 0; k < npairs; ++k)
+        CVO_CUDA(cudaMemcpyAsync(h->h_state + k, h->pr[k].state.p, sizeof(IterState), cudaMemcpyDeviceToHost, h->s));
     CVO_CUDA(cudaStreamSynchronize(h->s));
     return CVO_OK;
+}
+
+void fill_info(const IterState* st, cvo_info* inf)
+{
+    inf->iters = st->iter;
+    inf->status = st->status == 0 ? CVO_OK : CVO_NOT_CONVERGED;
+    inf->ell_final = st->ell_last;
+    inf->F = st->F;
+    inf->i_theta = st->i_theta;
+    inf->last_step_rot = st->srot;
+    inf->last_step_trans = st->strans;
+    inf->pairs = st->pairs_total;
+    inf->candidates = st->cands_total;
+}
+
+cvo_status begin_call(cvo_handle h, int rec_bf16, int npairs)
+{
+    set_features(h, rec_bf16);
+    if ((int)h->pr.size() < npairs) h->pr.resize(npairs);
+    CVO_TRY(ensure_host_states(h, npairs));
+    return CVO_OK;
+}
+
+int rec_bf16_of(const cvo_params& p, const cvo_cloud* X, const cvo_cloud* Z)
+{
+    return (feat_dim(p) > 0 && X->feat_dtype == CVO_BF16 && Z->feat_dtype == CVO_BF16) ? 1 : 0;
 }
 
 cvo_status run_eval(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double* T, cvo_eval* out)
 {
     std::memset(out, 0, sizeof(*out));
     if (X->n == 0 || Z->n == 0) return CVO_OK;
-    CVO_TRY(prepare(h, X, Z, h->p.ell, h->p.ell));
-    CVO_TRY(init_state(h, T, h->p.ell, 0));
-    const SweepArgs a = sweep_args(h);
-    CVO_CUDA(launch_sweep(a, h->sweep_blocks, h->s));
-    CVO_CUDA(launch_finalize(a.st, a.grp_stats, a.grp_cnt, h->sweep_blocks, nullptr, h->s));
-    CVO_TRY(fetch_state(h));
+    CVO_TRY(begin_call(h, rec_bf16_of(h->p, X, Z), 1));
+    PairRes& P = h->pr[0];
+    CVO_TRY(prepare(h, P, X, Z, h->p.ell, h->p.ell));
+    CVO_TRY(init_state(h, P, 0, T, h->p.ell, 0));
+    const int nb = single_pair_blocks(h, P);
+    SweepArgs a;
+    CVO_TRY(setup_sweep(h, std::vector<PairDesc>{pair_desc(P, 0, nb)}, nb, &a, true));
+    CVO_CUDA(launch_sweep(a, nb, h->s));
+    CVO_CUDA(launch_finalize((IterState*)P.state.p, a.grp_stats, a.grp_cnt, nb, nullptr, h->s));
+    CVO_TRY(fetch_states(h, 1));
     const IterState* st = h->h_state;
     out->F = st->F;
     for (int q = 0; q < 6; ++q) out->grad[q] = st->grad[q];
@@ -528,8 +613,11 @@ cvo_status run_eval(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const 
     return CVO_OK;
 }
 
-// Builds, instantiates and launches the graph of one registration's loop.
-cvo_status run_graph_loop(cvo_handle h, const SweepArgs& a, double* trace)
+// Builds, instantiates and launches the graph of a registration loop: a WHILE
+// conditional node whose body is (sweep, finalize); the finalize (single pair)
+// or the batched finalize's last block (batch) clears the condition.
+cvo_status run_graph_loop(cvo_handle h, const SweepArgs& a, bool batch, IterState* st_single, double* trace,
+                          long long trace_stride)
 {
     SweepLaunch sl;
     CVO_CUDA(sweep_launch_info(a.fc, a.rs, &sl));
@@ -568,28 +656,72 @@ cvo_status run_graph_loop(cvo_handle h, const SweepArgs& a, double* trace)
     kp.kernel.kernelParams = sp;
     cudaGraphNode_t sn;
     if (!check(cudaGraphAddNode(&sn, body, nullptr, nullptr, 0, &kp), "sweep node")) return cleanup(), status;
-    IterState* st = a.st;
-    const float2* gs = a.grp_stats;
-    const unsigned long long* gcn = a.grp_cnt;
-    int ngroups = (h->sweep_blocks + kGroupBlocks - 1) / kGroupBlocks, use_cond = 1;
+    int use_cond = 1;
     double* tr = trace;
-    void* fp[7] = {&st, &gs, &gcn, &ngroups, &tr, &cond, &use_cond};
     cudaGraphNodeParams fpn = {};
     fpn.type = cudaGraphNodeTypeKernel;
-    fpn.kernel.func = (void*)finalize_kernel();
-    fpn.kernel.gridDim = dim3(1);
     fpn.kernel.blockDim = dim3(kFinalizeThreads);
     fpn.kernel.sharedMemBytes = 0;
-    fpn.kernel.kernelParams = fp;
+    // single pair
+    IterState* st = st_single;
+    const float2* gs = a.grp_stats;
+    const unsigned long long* gcn = a.grp_cnt;
+    int ngroups = (h->sweep_blocks + kGroupBlocks - 1) / kGroupBlocks;
+    void* fp1[7] = {&st, &gs, &gcn, &ngroups, &tr, &cond, &use_cond};
+    // batch
+    const PairDesc* pairs = a.pairs;
+    int npairs = a.npairs;
+    const float2* ps = a.part_stats;
+    const unsigned long long* pc = a.part_cnt;
+    int cap = a.part_cap;
+    long long tstride = trace_stride;
+    unsigned* counters = (unsigned*)h->counters.p;
+    void* fpb[10] = {&pairs, &npairs, &ps, &pc, &cap, &tr, &tstride, &counters, &cond, &use_cond};
+    if (batch) {
+        fpn.kernel.func = (void*)finalize_batch_kernel();
+        fpn.kernel.gridDim = dim3(npairs);
+        fpn.kernel.kernelParams = fpb;
+    } else {
+        fpn.kernel.func = (void*)finalize_kernel();
+        fpn.kernel.gridDim = dim3(1);
+        fpn.kernel.kernelParams = fp1;
+    }
     cudaGraphNode_t fn;
     if (!check(cudaGraphAddNode(&fn, body, &sn, nullptr, 1, &fpn), "finalize node")) return cleanup(), status;
     if (!check(cudaGraphInstantiate(&ge, g, 0), "instantiate")) return cleanup(), status;
     if (!check(cudaGraphLaunch(ge, h->s), "launch")) return cleanup(), status;
-    // the graph's kernels are counted once the iteration count is known
-    h->graph_pending = 1;
     check(cudaStreamSynchronize(h->s), "synchronize");
     cleanup();
     return status;
+}
+
+void ensure_events(cvo_handle h, int iters)
+{
+    const size_t need = (size_t)2 * iters;
+    while (h->evs.size() < need) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) break;
+        h->evs.push_back(e);
+    }
+}
+
+double sum_sweep_events(cvo_handle h, int iters)
+{
+    double tot = 0.0;
+    for (int it = 0; it < iters && 2 * it + 1 < (int)h->evs.size(); ++it) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, h->evs[2 * it], h->evs[2 * it + 1]) == cudaSuccess) tot += ms;
+    }
+    return tot;
+}
+
+// lengthscales a registration can reach: a decay needs a reference indicator
+// from the previous iteration at the same lengthscale, so at most one decay
+// happens every two iterations and no grid level below this one is used
+double reachable_ell_lo(const cvo_params& p)
+{
+    if (!p.anneal) return p.ell;
+    return std::max(p.ell_min, p.ell * std::pow(p.decay, (double)(p.max_iters / 2)) * 0.9999);
 }
 
 cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double* T_init, double* T_out,
@@ -608,83 +740,154 @@ cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
         if (info) *info = inf;
         return (cvo_status)inf.status;
     }
-    // A decay needs a reference indicator from the previous iteration at the
-    // same lengthscale, so at most one decay happens every two iterations: no
-    // grid level below decay^(max_iters/2) * ell is ever used.
-    double ell_lo = p.ell;
-    if (p.anneal) ell_lo = std::max(p.ell_min, p.ell * std::pow(p.decay, (double)(p.max_iters / 2)) * 0.9999);
-    CVO_TRY(prepare(h, X, Z, p.ell, ell_lo));
-    CVO_TRY(init_state(h, T_init, p.ell, 1));
+    CVO_TRY(begin_call(h, rec_bf16_of(p, X, Z), 1));
+    PairRes& P = h->pr[0];
+    CVO_TRY(prepare(h, P, X, Z, p.ell, reachable_ell_lo(p)));
+    CVO_TRY(init_state(h, P, 0, T_init, p.ell, 1));
     CVO_CUDA(ensure(h->trace, (size_t)p.max_iters * CVO_TRACE_STRIDE * sizeof(double)));
-    const SweepArgs a = sweep_args(h);
+    const int nb = single_pair_blocks(h, P);
+    SweepArgs a;
+    CVO_TRY(setup_sweep(h, std::vector<PairDesc>{pair_desc(P, 0, nb)}, nb, &a, true));
     double* trace = (double*)h->trace.p;
-    if (h->timing) {
-        const size_t need = (size_t)2 * p.max_iters;
-        while (h->evs.size() < need) {
-            cudaEvent_t e;
-            CVO_CUDA(cudaEventCreate(&e));
-            h->evs.push_back(e);
-        }
-    }
+    IterState* dst = (IterState*)P.state.p;
     const bool graph = !h->timing && h->use_graph;
     if (graph) {
-        // The whole loop is one CUDA graph: a WHILE conditional node whose body
-        // is (sweep, finalize); the finalize clears the condition once the
-        // registration has converged or hit max_iters.
-        CVO_TRY(run_graph_loop(h, a, trace));
-    }
-    // Timing mode: iterations queued from the host in batches with CUDA events
-    // around every sweep; the device-side state stops the kernels once the
-    // registration is done, and the host checks the done flag between batches.
-    const int batch = 8;
-    int launched = graph ? p.max_iters : 0;
-    while (launched < p.max_iters) {
-        const int nb = std::min(batch, p.max_iters - launched);
-        for (int k = 0; k < nb; ++k) {
-            const int it = launched + k;
-            if (h->timing) CVO_CUDA(cudaEventRecord(h->evs[2 * it], h->s));
-            CVO_CUDA(launch_sweep(a, h->sweep_blocks, h->s));
-            if (h->timing) CVO_CUDA(cudaEventRecord(h->evs[2 * it + 1], h->s));
-            CVO_CUDA(launch_finalize(a.st, a.grp_stats, a.grp_cnt, h->sweep_blocks, trace, h->s));
+        CVO_TRY(run_graph_loop(h, a, false, dst, trace, 0));
+    } else {
+        // iterations queued from the host in batches (CUDA events around each
+        // sweep when timing); the device-side state stops the kernels once the
+        // registration is done, and the host checks between batches
+        if (h->timing) ensure_events(h, p.max_iters);
+        const int batch = 8;
+        int launched = 0;
+        while (launched < p.max_iters) {
+            const int n = std::min(batch, p.max_iters - launched);
+            for (int k = 0; k < n; ++k) {
+                const int it = launched + k;
+                const bool ev = h->timing && 2 * it + 1 < (int)h->evs.size();
+                if (ev) CVO_CUDA(cudaEventRecord(h->evs[2 * it], h->s));
+                CVO_CUDA(launch_sweep(a, nb, h->s));
+                if (ev) CVO_CUDA(cudaEventRecord(h->evs[2 * it + 1], h->s));
+                CVO_CUDA(launch_finalize(dst, a.grp_stats, a.grp_cnt, nb, trace, h->s));
+            }
+            launched += n;
+            if (launched >= p.max_iters) break;
+            CVO_CUDA(cudaMemcpyAsync(&h->h_state->done, &dst->done, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+            CVO_CUDA(cudaStreamSynchronize(h->s));
+            if (h->h_state->done) break;
         }
-        launched += nb;
-        if (launched >= p.max_iters) break;
-        CVO_CUDA(cudaMemcpyAsync(&h->h_state->done, &((IterState*)h->state.p)->done, sizeof(int),
-                                 cudaMemcpyDeviceToHost, h->s));
-        CVO_CUDA(cudaStreamSynchronize(h->s));
-        if (h->h_state->done) break;
     }
-    CVO_TRY(fetch_state(h));
+    CVO_TRY(fetch_states(h, 1));
     const IterState* st = h->h_state;
     std::memcpy(T_out, st->T, 16 * sizeof(double));
-    inf.iters = st->iter;
-    inf.status = st->status == 0 ? CVO_OK : CVO_NOT_CONVERGED;
-    inf.ell_final = st->ell_last;
-    inf.F = st->F;
-    inf.i_theta = st->i_theta;
-    inf.last_step_rot = st->srot;
-    inf.last_step_trans = st->strans;
-    inf.pairs = st->pairs_total;
-    inf.candidates = st->cands_total;
+    fill_info(st, &inf);
     h->last_iters = st->iter;
-    if (h->graph_pending) {
-        // the graph ran (sweep, finalize) once per iteration, plus the
-        // finalize that found the loop done (none when it stopped itself)
-        g_launch_count.fetch_add(2LL * st->iter, std::memory_order_relaxed);
-        h->graph_pending = 0;
-    }
+    if (graph) g_launch_count.fetch_add(2LL * st->iter, std::memory_order_relaxed);
     if (h->timing) {
-        double tot = 0.0;
-        for (int it = 0; it < st->iter; ++it) {
-            float ms = 0.0f;
-            CVO_CUDA(cudaEventElapsedTime(&ms, h->evs[2 * it], h->evs[2 * it + 1]));
-            tot += ms;
-        }
-        h->sweep_ms = tot;
+        h->sweep_ms = sum_sweep_events(h, st->iter);
         h->sweep_n = st->iter;
     }
     if (info) *info = inf;
     return (cvo_status)inf.status;
+}
+
+cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, const cvo_cloud* Z, const double* T_init,
+                              double* T_out, cvo_info* infos)
+{
+    const cvo_params& p = h->p;
+    h->last_iters = 0;
+    h->sweep_ms = 0.0;
+    h->sweep_n = 0;
+    // pairs that need iterations; the rest return T_init
+    std::vector<int> live;
+    for (int k = 0; k < npairs; ++k) {
+        const bool empty = X[k].n == 0 || Z[k].n == 0;
+        if (empty || p.max_iters == 0) {
+            std::memcpy(T_out + 16 * k, T_init + 16 * k, 16 * sizeof(double));
+            if (infos) {
+                std::memset(infos + k, 0, sizeof(cvo_info));
+                infos[k].status = empty ? CVO_OK : CVO_NOT_CONVERGED;
+                infos[k].ell_final = p.ell;
+            }
+        } else {
+            live.push_back(k);
+        }
+    }
+    const int nl = (int)live.size();
+    if (nl == 0) return p.max_iters == 0 && npairs > 0 ? CVO_NOT_CONVERGED : CVO_OK;
+    int bf = 1;
+    for (int k : live) bf &= rec_bf16_of(p, X + k, Z + k);
+    CVO_TRY(begin_call(h, bf, nl));
+    const double ell_lo = reachable_ell_lo(p);
+    long long work = 0;
+    for (int i = 0; i < nl; ++i) {
+        CVO_TRY(prepare(h, h->pr[i], X + live[i], Z + live[i], p.ell, ell_lo));
+        CVO_TRY(init_state(h, h->pr[i], i, T_init + 16 * live[i], p.ell, 1));
+        work += h->pr[i].max_items;
+    }
+    // split the grid among the pairs in proportion to their work items
+    const int budget = std::max(nl, h->num_sms * 8);
+    std::vector<PairDesc> table;
+    int b = 0;
+    for (int i = 0; i < nl; ++i) {
+        const PairRes& P = h->pr[i];
+        int nb = (int)std::llround((double)budget * P.max_items / (double)std::max(work, 1LL));
+        nb = std::max(1, std::min(nb, (P.max_items + kSweepWarps - 1) / kSweepWarps));
+        table.push_back(pair_desc(P, b, b + nb));
+        b += nb;
+    }
+    SweepArgs a;
+    CVO_TRY(setup_sweep(h, table, b, &a, false));
+    const long long tstride = (long long)p.max_iters * CVO_TRACE_STRIDE;
+    CVO_CUDA(ensure(h->trace, (size_t)nl * tstride * sizeof(double)));
+    double* traces = (double*)h->trace.p;
+    const bool graph = !h->timing && h->use_graph;
+    if (graph) {
+        CVO_TRY(run_graph_loop(h, a, true, nullptr, traces, tstride));
+    } else {
+        if (h->timing) ensure_events(h, p.max_iters);
+        unsigned* counters = (unsigned*)h->counters.p;
+        const int batch = 8;
+        int launched = 0;
+        while (launched < p.max_iters) {
+            const int n = std::min(batch, p.max_iters - launched);
+            for (int k = 0; k < n; ++k) {
+                const int it = launched + k;
+                const bool ev = h->timing && 2 * it + 1 < (int)h->evs.size();
+                if (ev) CVO_CUDA(cudaEventRecord(h->evs[2 * it], h->s));
+                CVO_CUDA(launch_sweep(a, b, h->s));
+                if (ev) CVO_CUDA(cudaEventRecord(h->evs[2 * it + 1], h->s));
+                CVO_CUDA(launch_finalize_batch(a.pairs, nl, a.part_stats, a.part_cnt, a.part_cap, traces, tstride,
+                                               counters, h->s));
+            }
+            launched += n;
+            if (launched >= p.max_iters) break;
+            CVO_CUDA(cudaMemcpyAsync(h->h_misc + 40, counters + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
+            CVO_CUDA(cudaStreamSynchronize(h->s));
+            if (h->h_misc[40] == 0) break;
+        }
+    }
+    CVO_TRY(fetch_states(h, nl));
+    cvo_status worst = CVO_OK;
+    int max_it = 0;
+    for (int i = 0; i < nl; ++i) {
+        const IterState* st = h->h_state + i;
+        const int k = live[i];
+        std::memcpy(T_out + 16 * k, st->T, 16 * sizeof(double));
+        if (infos) {
+            std::memset(infos + k, 0, sizeof(cvo_info));
+            fill_info(st, infos + k);
+        }
+        if (st->status != 0) worst = CVO_NOT_CONVERGED;
+        max_it = std::max(max_it, st->iter);
+    }
+    if (graph) g_launch_count.fetch_add(2LL * max_it, std::memory_order_relaxed);
+    if (h->timing) {
+        h->sweep_ms = sum_sweep_events(h, max_it);
+        h->sweep_n = max_it;
+    }
+    h->last_iters = 0;   // per-pair traces are not exposed through cvo_get_trace
+    return worst;
 }
 
 struct DeviceGuard {
@@ -730,7 +933,7 @@ cvo_status cvo_create(const cvo_params* params, void* cuda_stream, cvo_handle* o
         h->use_graph = !(gv && gv[0] == '0');
     }
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaMallocHost((void**)&h->h_state, sizeof(IterState)) != cudaSuccess ||
+    if (ensure_host_states(h, 1) != CVO_OK ||
         cudaMallocHost((void**)&h->h_misc, kMiscWords * sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
         if (h->h_state) cudaFreeHost(h->h_state);
@@ -747,15 +950,10 @@ cvo_status cvo_destroy(cvo_handle h)
     DeviceGuard g(h->device);
     cudaStreamSynchronize(h->s);
     DevBuf* bufs[] = {&h->stage_xyz[0], &h->stage_xyz[1], &h->stage_feat[0], &h->stage_feat[1], &h->keys, &h->vals,
-                      &h->keys2, &h->vals2, &h->sort_tmp, &h->flags, &h->gidx, &h->xrec, &h->morton, &h->misc,
-                      &h->levels_dev, &h->state, &h->part_stats, &h->part_cnt, &h->grp_stats,
-                      &h->grp_cnt, &h->grp_arrivals, &h->trace};
+                      &h->keys2, &h->vals2, &h->sort_tmp, &h->flags, &h->gidx, &h->misc, &h->part_stats, &h->part_cnt,
+                      &h->grp_stats, &h->grp_cnt, &h->grp_arrivals, &h->pairs_dev, &h->counters, &h->trace};
     for (DevBuf* b : bufs) release(*b);
-    for (int k = 0; k < kMaxLevels; ++k) {
-        release(h->zrec[k]);
-        release(h->cell_start[k]);
-        release(h->groups[k]);
-    }
+    for (PairRes& P : h->pr) P.free_all();
     for (cudaEvent_t e : h->evs) cudaEventDestroy(e);
     if (h->h_state) cudaFreeHost(h->h_state);
     if (h->h_misc) cudaFreeHost(h->h_misc);
@@ -834,14 +1032,16 @@ cvo_status cvo_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
     g_err.clear();
     if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
     if (npairs < 0) return fail(CVO_ERR_INVALID_ARG, "npairs < 0");
-    if (npairs > 0 && (!X || !Z || !T_init || !T_out)) return fail(CVO_ERR_INVALID_ARG, "NULL array");
-    cvo_status worst = CVO_OK;
+    if (npairs == 0) return CVO_OK;
+    if (!X || !Z || !T_init || !T_out) return fail(CVO_ERR_INVALID_ARG, "NULL array");
+    const int D = feat_dim(h->p);
     for (int k = 0; k < npairs; ++k) {
-        cvo_status s = cvo_register_pair(h, X + k, Z + k, T_init + 16 * k, T_out + 16 * k, infos ? infos + k : nullptr);
-        if (s < 0) return s;
-        if (s == CVO_NOT_CONVERGED) worst = CVO_NOT_CONVERGED;
+        CVO_TRY(check_cloud(X + k, "X[k]", D));
+        CVO_TRY(check_cloud(Z + k, "Z[k]", D));
+        CVO_TRY(check_pose(T_init + 16 * k, "T_init[k]"));
     }
-    return worst;
+    DeviceGuard g(h->device);
+    return run_register_batch(h, npairs, X, Z, T_init, T_out, infos);
 }
 
 int cvo_get_trace(cvo_handle h, double* out, int cap)

@@ -648,9 +648,84 @@ k_finalize(IterState* st, const float2* __restrict__ gs, const unsigned long lon
     if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, sst->done ? 0u : 1u);
 }
 
+// Batch: block p sums pair p's block partials [b0, b1) in block order and takes
+// its step (pairs already done are skipped: their convergence mask).  The last
+// block to arrive publishes the number of pairs still running and, inside a
+// graph, keeps the loop going while any pair runs.  Counters are left at zero.
+__global__ void __launch_bounds__(kFinalizeThreads)
+k_finalize_batch(const PairDesc* __restrict__ pairs, int npairs, const float2* __restrict__ ps,
+                 const unsigned long long* __restrict__ pc, int cap, double* traces, long long trace_stride,
+                 unsigned* counters, cudaGraphConditionalHandle cond, int use_cond)
+{
+    constexpr int kWords = (int)(sizeof(IterState) / 8);
+    __shared__ double S[kStatN];
+    __shared__ float Shi[kStatN], Slo[kStatN];
+    __shared__ unsigned long long cs[2];
+    __shared__ unsigned long long sbuf[kWords];
+    const PairDesc P = pairs[blockIdx.x];
+    IterState* st = P.st;
+    const bool was_done = st->done != 0;
+    IterState* sst = reinterpret_cast<IterState*>(sbuf);
+    if (!was_done) {
+        for (int i = threadIdx.x; i < kWords; i += kFinalizeThreads)
+            sbuf[i] = reinterpret_cast<const unsigned long long*>(st)[i];
+        if (threadIdx.x < kStatN) {
+            const float2* row = ps + (size_t)threadIdx.x * cap;
+            float hi = 0.0f, lo = 0.0f;
+            int b = P.b0;
+            for (; b + 8 <= P.b1; b += 8) {
+                float2 v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v[k] = row[b + k];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) df_add(hi, lo, v[k].x, v[k].y);
+            }
+            for (; b < P.b1; ++b) df_add(hi, lo, row[b].x, row[b].y);
+            S[threadIdx.x] = (double)hi + (double)lo;
+            Shi[threadIdx.x] = hi;
+            Slo[threadIdx.x] = lo;
+        } else if (threadIdx.x == kStatN || threadIdx.x == kStatN + 1) {
+            const int c = threadIdx.x - kStatN;
+            unsigned long long t = 0;
+            for (int b = P.b0; b < P.b1; ++b) t += pc[(size_t)c * cap + b];
+            cs[c] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32)
+            step_warp(sst, S, Shi, Slo, cs[0], cs[1], traces ? traces + (size_t)blockIdx.x * trace_stride : nullptr);
+        __syncthreads();
+        for (int i = threadIdx.x; i < kWords; i += kFinalizeThreads)
+            reinterpret_cast<unsigned long long*>(st)[i] = sbuf[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!was_done && !sst->done) atomicAdd(&counters[1], 1u);
+        __threadfence();
+        if (atomicAdd(&counters[0], 1u) == (unsigned)(npairs - 1)) {
+            __threadfence();
+            const unsigned active = atomicAdd(&counters[1], 0u);
+            counters[2] = active;
+            counters[0] = 0u;
+            counters[1] = 0u;
+            if (use_cond) cudaGraphSetConditional(cond, active > 0u ? 1u : 0u);
+        }
+    }
+}
+
 }  // namespace
 
 const void* finalize_kernel() { return (const void*)k_finalize; }
+const void* finalize_batch_kernel() { return (const void*)k_finalize_batch; }
+
+cudaError_t launch_finalize_batch(const PairDesc* pairs, int npairs, const float2* part_stats,
+                                  const unsigned long long* part_cnt, int part_cap, double* traces,
+                                  long long trace_stride, unsigned* counters, cudaStream_t s)
+{
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    k_finalize_batch<<<npairs, kFinalizeThreads, 0, s>>>(pairs, npairs, part_stats, part_cnt, part_cap, traces,
+                                                         trace_stride, counters, cudaGraphConditionalHandle{}, 0);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_init_state(IterState* st, cudaStream_t s)
 {

@@ -103,19 +103,29 @@ struct IterState {
     float level_h[kMaxLevels];
 };
 
-struct SweepArgs {
+// One registration pair as the sweep sees it.  Sweep blocks [b0, b1) work on
+// this pair (a batch splits the grid among its pairs in proportion to their
+// work); each block's partial sums belong to one pair.
+struct PairDesc {
     const LevelDesc* levels;   // device array [nlevels]
     const float4* xrec;        // N query records
+    IterState* st;
     int n, m;
+    int b0, b1;
+};
+
+struct SweepArgs {
+    const PairDesc* pairs;     // device array [npairs], ordered by b0
+    int npairs;
     int rs;                    // record stride (float4)
     int dense;
-    IterState* st;
     float2* part_stats;        // [kStatN][part_cap] per-block sums
     unsigned long long* part_cnt; // [2][part_cap]
     int part_cap;
     float2* grp_stats;         // [kStatN][kMaxGroups] per-group sums (read by the finalize)
     unsigned long long* grp_cnt;  // [2][kMaxGroups]
-    unsigned* grp_arrivals;    // [kMaxGroups] arrival counters, zero between launches
+    unsigned* grp_arrivals;    // [kMaxGroups] arrival counters, zero between launches;
+                               // NULL in a batch (its finalize sums the block partials)
     FeatConst fc;
 };
 
@@ -125,6 +135,19 @@ struct SweepArgs {
 extern std::atomic<long long> g_launch_count;
 
 cudaError_t launch_sweep(const SweepArgs& a, int nblocks, cudaStream_t s);
+
+// Batched step: one block per pair sums that pair's block partials and takes
+// its step; the last block to finish writes the number of pairs still
+// running to *active and, inside a graph, sets the loop's condition.
+// traces: npairs x trace_stride doubles (NULL: no trace).
+cudaError_t launch_finalize_batch(const PairDesc* pairs, int npairs, const float2* part_stats,
+                                  const unsigned long long* part_cnt, int part_cap, double* traces,
+                                  long long trace_stride, unsigned* counters, cudaStream_t s);
+// k_finalize_batch(const PairDesc*, int npairs, const float2*, const unsigned long long*, int cap,
+//                  double* traces, long long trace_stride, unsigned* counters,
+//                  cudaGraphConditionalHandle cond, int use_cond); counters[0] arrivals,
+//                  counters[1] active pairs being counted, counters[2] the last count
+const void* finalize_batch_kernel();
 
 // Kernel handles for CUDA-graph kernel nodes.
 struct SweepLaunch {

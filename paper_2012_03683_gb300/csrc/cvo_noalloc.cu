@@ -52,7 +52,8 @@ constexpr int kMaxDevices = 64;
 constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 constexpr size_t kOffState = 0;
 constexpr size_t kOffLevel = align256(kOffState + sizeof(IterState));
-constexpr size_t kOffMisc = align256(kOffLevel + sizeof(LevelDesc));
+constexpr size_t kOffPair = align256(kOffLevel + sizeof(LevelDesc));
+constexpr size_t kOffMisc = align256(kOffPair + sizeof(PairDesc));
 constexpr size_t kOffGroups = align256(kOffMisc + 16 * sizeof(unsigned));
 constexpr size_t kOffStats = align256(kOffGroups + sizeof(int2) * (kNoAllocMaxPoints / 32));
 constexpr size_t kOffCnt = align256(kOffStats + sizeof(float2) * kStatN * kNoAllocBlocks);
@@ -119,7 +120,8 @@ bool is_device_pointer(const void* p)
 
 // Writes the state block, the level descriptor and the query groups, and
 // resets the bounding-box counters (min to all ones, max and flag to zero).
-__global__ void k_na_setup(IterState init, LevelDesc ld, int n, IterState* st, LevelDesc* lv, int2* groups,
+__global__ void k_na_setup(IterState init, LevelDesc ld, PairDesc pd, int n, IterState* st, LevelDesc* lv,
+                           PairDesc* pair, int2* groups,
                            unsigned* misc, unsigned* arrivals)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -127,6 +129,7 @@ __global__ void k_na_setup(IterState init, LevelDesc ld, int n, IterState* st, L
     if (tid == 0) {
         *st = init;
         *lv = ld;
+        *pair = pd;
         for (int a = 0; a < 3; ++a) {
             misc[a] = 0xffffffffu;       // Z box minimum
             misc[3 + a] = 0u;            // Z box maximum
@@ -310,8 +313,20 @@ extern "C" cvo_status cvo_evaluate_dense_noalloc(const cvo_params* p, void* cuda
     ld.groups = groups;
     ld.ngroups = (n + 31) / 32;
 
+    const int items = ld.ngroups * kChunks;
+    const int nblocks = std::max(1, std::min((items + kSweepWarps - 1) / kSweepWarps, kNoAllocBlocks));
+    PairDesc pd;
+    pd.levels = lv;
+    pd.xrec = xrec;
+    pd.st = st;
+    pd.n = n;
+    pd.m = m;
+    pd.b0 = 0;
+    pd.b1 = nblocks;
+    PairDesc* pair = (PairDesc*)(base + kOffPair);
+
     g_launch_count.fetch_add(2, std::memory_order_relaxed);
-    k_na_setup<<<(ld.ngroups + 255) / 256, 256, 0, s>>>(init, ld, n, st, lv, groups, misc, garr);
+    k_na_setup<<<(ld.ngroups + 255) / 256, 256, 0, s>>>(init, ld, pd, n, st, lv, pair, groups, misc, garr);
     NA_CUDA(cudaGetLastError());
     NA_CUDA(launch_bbox(Z->xyz, m, misc, (int*)(misc + 6), s));
     NA_CUDA(launch_bbox(X->xyz, n, misc + 8, (int*)(misc + 6), s));   // finiteness of X (box unused)
@@ -325,13 +340,10 @@ extern "C" cvo_status cvo_evaluate_dense_noalloc(const cvo_params* p, void* cuda
     NA_CUDA(launch_pack(X->xyz, X->feat, X->feat_dtype == CVO_BF16, D, nullptr, n, xrec, rs, 0, s));
     NA_CUDA(launch_pack(Z->xyz, Z->feat, Z->feat_dtype == CVO_BF16, D, nullptr, m, zrec, rs, 0, s));
     SweepArgs a;
-    a.levels = lv;
-    a.xrec = xrec;
-    a.n = n;
-    a.m = m;
+    a.pairs = pair;
+    a.npairs = 1;
     a.rs = rs;
     a.dense = 1;
-    a.st = st;
     a.part_stats = stats;
     a.part_cnt = cnt;
     a.part_cap = kNoAllocBlocks;
@@ -339,8 +351,6 @@ extern "C" cvo_status cvo_evaluate_dense_noalloc(const cvo_params* p, void* cuda
     a.grp_cnt = gcnt;
     a.grp_arrivals = garr;
     a.fc = fc;
-    const int items = ld.ngroups * kChunks;
-    const int nblocks = std::max(1, std::min((items + kSweepWarps - 1) / kSweepWarps, kNoAllocBlocks));
     NA_CUDA(launch_sweep(a, nblocks, s));
     NA_CUDA(launch_finalize(st, gstats, gcnt, nblocks, nullptr, s));
     g_launch_count.fetch_add(1, std::memory_order_relaxed);

@@ -231,8 +231,20 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
     __shared__ float acc_s[kSweepWarps][kStatN][32];
     __shared__ unsigned long long redc[kSweepWarps][2];
     __shared__ float cst[30];               // Ahi, Alo, bhi, blo, chi, clo
-    const IterState* st = a.st;
-    if (st->done) return;   // uniform: no block arrives at the group counters
+    // the pair this block works on (blocks [b0, b1) of pair pi)
+    int pi = 0;
+    if (a.npairs > 1) {
+        int lo = 0, hi = a.npairs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.pairs[mid].b0 <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        pi = lo;
+    }
+    const PairDesc P = a.pairs[pi];
+    const IterState* st = P.st;
+    if (st->done) return;   // uniform per pair; a single pair's blocks all return together
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x < 30) cst[threadIdx.x] = (&st->Ahi[0])[threadIdx.x];
 #pragma unroll
@@ -244,7 +256,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
     const float* blo = cst + 21;
     const float* chi = cst + 24;
     const float* clo = cst + 27;
-    const LevelDesc L = a.levels[st->level];
+    const LevelDesc L = P.levels[st->level];
     const int rs = a.rs;
     const bool dense = a.dense != 0;
     const float sg = st->sg, rc = st->rc, rc2 = st->rc2;
@@ -253,13 +265,14 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
     unsigned npairs = 0, ncand = 0;
 
     const int nitems = L.ngroups * kChunks;
-    for (int item = blockIdx.x * kSweepWarps + warp; item < nitems; item += gridDim.x * kSweepWarps) {
+    const int nblk = P.b1 - P.b0, bloc = (int)blockIdx.x - P.b0;
+    for (int item = bloc * kSweepWarps + warp; item < nitems; item += nblk * kSweepWarps) {
         const int g = item / kChunks;
         const int k = item - g * kChunks;
         const int2 grp = L.groups[g];
         const bool act = lane < grp.y;
         const int qi = grp.x + (act ? lane : 0);
-        const float4* qrec = a.xrec + (size_t)qi * rs;
+        const float4* qrec = P.xrec + (size_t)qi * rs;
         const float4 xq4 = qrec[0];
         const float xq[3] = {xq4.x, xq4.y, xq4.z};
         float xh[3], xl[3];
@@ -307,7 +320,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
             const int r = b0 + lane;
             if (r < nruns) {
                 if (dense) {
-                    len = a.m;
+                    len = P.m;
                 } else {
                     const int cy = cy0 + r % nry, cz = cz0 + r / nry;
                     const int row = (cz * L.ny + cy) * L.nx;
@@ -335,7 +348,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
             if (r < nruns) {
                 if (dense) {
                     rstart = 0;
-                    rlen = a.m;
+                    rlen = P.m;
                 } else {
                     const int cy = cy0 + r % nry, cz = cz0 + r / nry;
                     const int row = (cz * L.ny + cy) * L.nx;
@@ -478,6 +491,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
     // Group reduction: the last block of each group of kGroupBlocks blocks to
     // arrive sums the group's partials in block order (deterministic; nothing
     // waits) and resets the group's arrival counter for the next launch.
+    if (a.grp_arrivals == nullptr) return;   // batch: the finalize sums the block partials per pair
     __shared__ int is_last;
     const int grp = blockIdx.x / kGroupBlocks;
     const int first = grp * kGroupBlocks;
