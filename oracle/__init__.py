@@ -158,6 +158,19 @@ def indicator(X, Z, T, **kw):
     return evaluate(X, Z, T, **kw)["F"] / np.sqrt(float(n) * float(m))
 
 
+def cosine(X, Z, T, FX=None, FZ=None, **kw):
+    """Eq. (indicator): the cosine of the angle between f_X and the moved f_Z,
+    <f_X, f_Z'> / (|f_X| |f_Z'|); the norms are the same double sum of each
+    cloud with itself at the identity (a rigid motion preserves the norm)."""
+    n, m = np.asarray(X).reshape(-1, 3).shape[0], np.asarray(Z).reshape(-1, 3).shape[0]
+    if n == 0 or m == 0:
+        return 0.0
+    I = np.eye(4)
+    fxx = evaluate(X, X, I, FX=FX, FZ=FX, **kw)["F"]
+    fzz = evaluate(Z, Z, I, FX=FZ, FZ=FZ, **kw)["F"]
+    return evaluate(X, Z, T, FX=FX, FZ=FZ, **kw)["F"] / np.sqrt(fxx * fzz)
+
+
 def count_band(X, Z, T, lo, hi):
     """Pairs whose squared distance lies in [lo, hi] (cutoff-boundary census)."""
     lib = _load()
@@ -218,3 +231,29 @@ def register(X, Z, T_init, *, FX=None, FZ=None, blocks=(), ell, ell_min=None, cu
              last_step_rot=info.last_step_rot, last_step_trans=info.last_step_trans,
              pairs_total=int(info.pairs_total))
     return Tout, d, trace[: info.iters].copy()
+
+
+def backward(X, Z, T, *, FX=None, FZ=None, blocks=(), ell, cutoff_mult=0.0, sigma=1.0, nthreads=0):
+    """Gradients of F with respect to X, Z (float64, (N,3), (M,3)), the
+    features (N,D), (M,D) and the lengthscale, for the pairs inside the
+    cutoff (see cvo_oracle.c).  Returns a dict."""
+    lib = _load()
+    lib.orc_backward.restype = ctypes.c_int
+    keep = []
+    cx = _cloud(X, FX, keep)
+    cz = _cloud(Z, FZ, keep)
+    k = _kernel(list(blocks), ell, cutoff_mult, sigma)
+    D = sum(int(b[1]) for b in blocks)
+    Tm = _f64(T).reshape(4, 4)
+    dX = np.zeros((cx.n, 3))
+    dZ = np.zeros((cz.n, 3))
+    dFX = np.zeros((cx.n, D))
+    dFZ = np.zeros((cz.n, D))
+    dell = ctypes.c_double(0.0)
+    vp = ctypes.c_void_p
+    rc = lib.orc_backward(ctypes.byref(k), ctypes.byref(cx), ctypes.byref(cz), Tm.ctypes.data_as(vp),
+                          dX.ctypes.data_as(vp), dFX.ctypes.data_as(vp) if D else None, dZ.ctypes.data_as(vp),
+                          dFZ.ctypes.data_as(vp) if D else None, ctypes.byref(dell), int(nthreads))
+    if rc != 0:
+        raise ValueError("orc_backward: invalid argument")
+    return dict(dX=dX, dZ=dZ, dFX=dFX, dFZ=dFZ, dell=dell.value)

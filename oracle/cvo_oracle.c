@@ -486,3 +486,127 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Gradients of F with respect to the inputs (derived from Eq. double_sum   */
+/* for the pairs inside the cutoff; the pair set is held fixed, i.e. the    */
+/* derivative almost everywhere).  With w = sigma^2 exp(-d^2/(2 l^2)) c_ij,  */
+/* y_j = R z_j + t, d = |x_i - y_j|:                                        */
+/*   dF/dx_i = sum_j w (y_j - x_i) / l^2                                    */
+/*   dF/dz_j = R^T sum_i w (x_i - y_j) / l^2                                */
+/*   dF/dl   = sum w d^2 / l^3                                              */
+/*   squared-exponential block b:  dF/du_bi = -sum_j w (u_bi - v_bj) / l_b^2 */
+/*   inner-product block b:        dF/du_bi = sum_j w_(b) v_bj, with w_(b)  */
+/*     the weight with block b's factor left out (the other blocks' product) */
+/* and the same with the roles of (x, u) and (z, v) exchanged.              */
+/* Pinned by central finite differences of F (tests).                       */
+/* ------------------------------------------------------------------------ */
+
+/* weight of pair (i, j) with block `skip` left out (skip < 0: full weight) */
+static double pair_weight(const orc_kernel* k, double d2, const double* u, const double* v, int skip)
+{
+    double c = k->sigma * k->sigma * exp(-d2 / (2.0 * k->ell * k->ell));
+    int off = 0;
+    for (int b = 0; b < k->n_blocks; ++b) {
+        const int d = k->dim[b];
+        if (b != skip) {
+            if (k->kind[b] == 0) {
+                double s = 0.0;
+                for (int a = 0; a < d; ++a) s += (u[off + a] - v[off + a]) * (u[off + a] - v[off + a]);
+                c *= k->sigk[b] * k->sigk[b] * exp(-s / (2.0 * k->scale[b] * k->scale[b]));
+            } else {
+                double s = 0.0;
+                for (int a = 0; a < d; ++a) s += u[off + a] * v[off + a];
+                c *= s;
+            }
+        }
+        off += d;
+    }
+    return c;
+}
+
+/* gradient of the pair's weight with respect to the first point's features */
+static void feature_grad(const orc_kernel* k, double d2, const double* u, const double* v, double w, double* g)
+{
+    int off = 0;
+    for (int b = 0; b < k->n_blocks; ++b) {
+        const int d = k->dim[b];
+        if (k->kind[b] == 0) {
+            for (int a = 0; a < d; ++a) g[off + a] += -w * (u[off + a] - v[off + a]) / (k->scale[b] * k->scale[b]);
+        } else {
+            const double wb = pair_weight(k, d2, u, v, b);
+            for (int a = 0; a < d; ++a) g[off + a] += wb * v[off + a];
+        }
+        off += d;
+    }
+}
+
+int orc_backward(const orc_kernel* k, const orc_cloud* X, const orc_cloud* Z, const double T[16], double* dX,
+                 double* dFX, double* dZ, double* dFZ, double* dell, int nthreads)
+{
+    if (!k || !X || !Z || !T || k->ell <= 0.0) return -1;
+    const int D = feat_dim(k);
+    const double l2 = k->ell * k->ell, l3 = l2 * k->ell;
+    const double rc2 = k->cutoff_mult > 0.0 ? (k->cutoff_mult * k->ell) * (k->cutoff_mult * k->ell) : -1.0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    double* dl_part = (double*)calloc((size_t)(X->n > 0 ? X->n : 1), sizeof(double));
+    if (!dl_part) return -1;
+    /* X side: loop i outer */
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int i = 0; i < X->n; ++i) {
+        const double* x = X->xyz + 3 * (size_t)i;
+        const double* u = D > 0 ? X->feat + (size_t)D * i : NULL;
+        double gx[3] = {0, 0, 0}, dl = 0.0;
+        double* gu = dFX ? dFX + (size_t)D * i : NULL;
+        if (gu) for (int a = 0; a < D; ++a) gu[a] = 0.0;
+        for (int j = 0; j < Z->n; ++j) {
+            const double* z = Z->xyz + 3 * (size_t)j;
+            double y[3], e[3];
+            for (int r = 0; r < 3; ++r) {
+                y[r] = T[4 * r + 0] * z[0] + T[4 * r + 1] * z[1] + T[4 * r + 2] * z[2] + T[4 * r + 3];
+                e[r] = y[r] - x[r];
+            }
+            const double d2 = dot3(e, e);
+            if (rc2 >= 0.0 && !(d2 <= rc2)) continue;
+            const double* v = D > 0 ? Z->feat + (size_t)D * j : NULL;
+            const double w = pair_weight(k, d2, u, v, -1);
+            for (int r = 0; r < 3; ++r) gx[r] += w * e[r] / l2;
+            dl += w * d2 / l3;
+            if (gu) feature_grad(k, d2, u, v, w, gu);
+        }
+        if (dX) for (int r = 0; r < 3; ++r) dX[3 * (size_t)i + r] = gx[r];
+        dl_part[i] = dl;
+    }
+    double dls = 0.0;
+    for (int i = 0; i < X->n; ++i) dls += dl_part[i];
+    free(dl_part);
+    if (dell) *dell = dls;
+    /* Z side: loop j outer */
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int j = 0; j < Z->n; ++j) {
+        const double* z = Z->xyz + 3 * (size_t)j;
+        const double* v = D > 0 ? Z->feat + (size_t)D * j : NULL;
+        double y[3];
+        for (int r = 0; r < 3; ++r) y[r] = T[4 * r + 0] * z[0] + T[4 * r + 1] * z[1] + T[4 * r + 2] * z[2] + T[4 * r + 3];
+        double gy[3] = {0, 0, 0};
+        double* gv = dFZ ? dFZ + (size_t)D * j : NULL;
+        if (gv) for (int a = 0; a < D; ++a) gv[a] = 0.0;
+        for (int i = 0; i < X->n; ++i) {
+            const double* x = X->xyz + 3 * (size_t)i;
+            const double e[3] = {y[0] - x[0], y[1] - x[1], y[2] - x[2]};
+            const double d2 = dot3(e, e);
+            if (rc2 >= 0.0 && !(d2 <= rc2)) continue;
+            const double* u = D > 0 ? X->feat + (size_t)D * i : NULL;
+            const double w = pair_weight(k, d2, u, v, -1);
+            for (int r = 0; r < 3; ++r) gy[r] += -w * e[r] / l2;
+            if (gv) feature_grad(k, d2, v, u, w, gv);
+        }
+        if (dZ) /* dF/dz = R^T dF/dy */
+            for (int c = 0; c < 3; ++c) dZ[3 * (size_t)j + c] = T[c] * gy[0] + T[4 + c] * gy[1] + T[8 + c] * gy[2];
+    }
+    return 0;
+}

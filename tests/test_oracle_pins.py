@@ -272,6 +272,37 @@ def test_remark_norm_sqrt_n():
     assert math.sqrt(oracle.evaluate(X, X, np.eye(4), ell=0.002)["F"]) == pytest.approx(math.sqrt(50), rel=1e-12)
 
 
+def test_cosine_by_quadrature():
+    """Eq. (indicator): the cosine of the embedded functions, each inner
+    product taken by quadrature of the Gaussian fields (independent of the
+    oracle's double sum)."""
+    r = rng(30)
+    X = r.uniform(-0.5, 0.5, size=(4, 3))
+    Z = r.uniform(-0.5, 0.5, size=(3, 3))
+    T = rand_T(r, 0.3, 0.2)
+    ell = 0.3
+    Y = transform(T, Z)
+    ref = quad_F(X, Y, ell, 1.0) / math.sqrt(quad_F(X, X, ell, 1.0) * quad_F(Y, Y, ell, 1.0))
+    assert oracle.cosine(X, Z, T, ell=ell, sigma=1.7) == pytest.approx(ref, rel=1e-10)
+
+
+def test_cosine_bounds_and_remark():
+    """Dense mode: |cos| <= 1 with equality for Z = G X, T = G^-1; with
+    l below the point spacing (the Remark, Sec. III-C) the exact cosine and
+    the indicator of Eq. (indicator_actual) coincide."""
+    r, X, Z, FX, FZ = _cloud_pair(31)
+    kw = dict(blocks=BLOCKS, ell=0.5)
+    for _ in range(4):
+        c = oracle.cosine(X, Z, rand_T(r), FX=FX, FZ=FZ, **kw)
+        assert abs(c) <= 1.0 + 1e-12
+    G = rand_T(r)
+    assert oracle.cosine(X, transform(G, X), np.linalg.inv(G), FX=FX, FZ=FX, **kw) == pytest.approx(1.0, abs=1e-12)
+    P = r.uniform(-1, 1, size=(40, 3))
+    Q = P + r.normal(size=P.shape) * 1e-4
+    assert oracle.cosine(P, Q, np.eye(4), ell=1e-3) == pytest.approx(oracle.indicator(P, Q, np.eye(4), ell=1e-3),
+                                                                     rel=1e-9)
+
+
 def test_indicator_peaks_at_zero_error():
     """Fig. 3 (Sec. III-C): rotating or translating a cloud away from itself
     lowers the indicator, and the maximum is at zero error."""
@@ -402,3 +433,49 @@ def test_replay_reproduces_annealing_decisions():
     assert np.all(np.diff(ells) <= 0) and ells.min() >= 0.2
     steps = ells[1:][np.diff(ells) < 0] / ells[:-1][np.diff(ells) < 0]
     assert np.all((np.abs(steps - 0.98) < 1e-12) | (ells[1:][np.diff(ells) < 0] == 0.2))
+
+
+# ---------------------------------------------------------------------------
+# 7. gradients with respect to points, features and the lengthscale
+# ---------------------------------------------------------------------------
+
+def test_backward_central_differences():
+    r, X, Z, FX, FZ = _cloud_pair(21, 14, 12)
+    T = rand_T(r, 0.2, 0.2)
+    kw = dict(blocks=BLOCKS, ell=0.5, sigma=1.1)
+    g = oracle.backward(X, Z, T, FX=FX, FZ=FZ, **kw)
+
+    def F(X_=X, Z_=Z, FX_=FX, FZ_=FZ, ell=0.5):
+        return oracle.evaluate(X_, Z_, T, FX=FX_, FZ=FZ_, blocks=BLOCKS, ell=ell, sigma=1.1)["F"]
+
+    eps = 1e-6
+    for (i, a) in [(0, 0), (3, 1), (7, 2)]:
+        Xp, Xm = X.copy(), X.copy()
+        Xp[i, a] += eps
+        Xm[i, a] -= eps
+        assert g["dX"][i, a] == pytest.approx((F(X_=Xp) - F(X_=Xm)) / (2 * eps), rel=1e-6, abs=1e-9)
+    for (j, a) in [(1, 0), (5, 2)]:
+        Zp, Zm = Z.copy(), Z.copy()
+        Zp[j, a] += eps
+        Zm[j, a] -= eps
+        assert g["dZ"][j, a] == pytest.approx((F(Z_=Zp) - F(Z_=Zm)) / (2 * eps), rel=1e-6, abs=1e-9)
+    for (i, a) in [(2, 0), (4, 2), (6, 3), (9, 5)]:   # squared-exponential and inner-product entries
+        Fp, Fm = FX.copy(), FX.copy()
+        Fp[i, a] += eps
+        Fm[i, a] -= eps
+        assert g["dFX"][i, a] == pytest.approx((F(FX_=Fp) - F(FX_=Fm)) / (2 * eps), rel=1e-6, abs=1e-9)
+    for (j, a) in [(0, 1), (3, 4)]:
+        Fp, Fm = FZ.copy(), FZ.copy()
+        Fp[j, a] += eps
+        Fm[j, a] -= eps
+        assert g["dFZ"][j, a] == pytest.approx((F(FZ_=Fp) - F(FZ_=Fm)) / (2 * eps), rel=1e-6, abs=1e-9)
+    assert g["dell"] == pytest.approx((F(ell=0.5 + eps) - F(ell=0.5 - eps)) / (2 * eps), rel=1e-6)
+
+
+def test_backward_translation_invariance():
+    """Moving both clouds together leaves F unchanged: sum dX + R sum dZ = 0."""
+    r, X, Z, FX, FZ = _cloud_pair(22, 20, 17)
+    T = rand_T(r, 0.3, 0.3)
+    g = oracle.backward(X, Z, T, FX=FX, FZ=FZ, blocks=BLOCKS, ell=0.4, cutoff_mult=2.5)
+    total = g["dX"].sum(0) + g["dZ"].sum(0) @ T[:3, :3].T
+    assert np.abs(total).max() < 1e-10 * max(1.0, np.abs(g["dX"]).max())
