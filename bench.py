@@ -208,6 +208,44 @@ def batch_section(cvo, torch, dev, flush, reps=2):
     return out
 
 
+def backward_section(cvo, torch, dev, flush, reps=5):
+    """Room pair (19,200 points per cloud, rgb, l = 0.1, cutoff 3 l): one
+    forward evaluation and one backward pass (gradients for both clouds'
+    points and features and for l, device outputs), CUDA-event timed."""
+    import scenes
+    p = scenes.room_pair()
+    pr = p.params
+    X, Z = torch.tensor(p.X, device=dev), torch.tensor(p.Z, device=dev)
+    FX, FZ = torch.tensor(p.FX, device=dev), torch.tensor(p.FZ, device=dev)
+    T = p.T_true
+    out = {"workload": f"room-19k: {p.n} + {p.m} points, rgb, l = {pr['ell']}, cutoff 3 l"}
+    with cvo.CVO(blocks=p.blocks, ell=pr["ell"], cutoff_mult=pr["cutoff_mult"]) as h:
+        ev = h.evaluate(X, Z, T, FX, FZ)
+        h.backward(X, Z, T, FX, FZ)
+        stream = torch.cuda.current_stream()
+        t = {"forward": 0.0, "backward": 0.0}
+        for _ in range(reps):
+            for name in ("forward", "backward"):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if name == "forward":
+                    h.evaluate(X, Z, T, FX, FZ)
+                else:
+                    h.backward(X, Z, T, FX, FZ)
+                e1.record(stream)
+                e1.synchronize()
+                t[name] += e0.elapsed_time(e1)
+    out["pairs"] = int(ev["pairs"])
+    out["ms_forward"] = t["forward"] / reps
+    out["ms_backward"] = t["backward"] / reps
+    # the backward sweeps every in-cutoff pair twice (once per cloud)
+    out["backward_pair_evals_per_s"] = 2 * ev["pairs"] / (1e-3 * out["ms_backward"])
+    out["timing"] = "whole calls (setup, sweeps, copies) between CUDA events, L2 flushed before each"
+    return out
+
+
 def cpu_baseline(p, kw, iters=20):
     import oracle
     oracle.build()
@@ -258,6 +296,7 @@ def main():
     ap.add_argument("--impl", default="cvo", choices=["cvo", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain section")
+    ap.add_argument("--no-backward", action="store_true", help="skip the forward/backward section")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -355,6 +394,7 @@ def main():
     e2e_pairs = sum_over_ranks(dist, world, float(e2e_pairs), dev)
     h.close()
     batch = batch_section(cvo, torch, dev, flush) if (rank == 0 and not args.no_batch) else None
+    backward = backward_section(cvo, torch, dev, flush) if (rank == 0 and not args.no_backward) else None
 
     if rank != 0:
         return
@@ -388,6 +428,7 @@ def main():
         "clocks": clocks,
         "final_pose_err_vs_truth": pose_err,
         "batch": batch,
+        "backward": backward,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, kw)

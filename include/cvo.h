@@ -145,8 +145,50 @@ cvo_status cvo_gradient(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
  * at pose T and lengthscale params.ell. */
 cvo_status cvo_metric(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], double* i_theta);
 
+/* The exact alignment indicator of Eq. (indicator): the cosine of the angle
+ * between f_X and the moved f_Z in the RKHS,
+ *   cos_theta = F(X, Z, T) / sqrt(F(X, X, I) F(Z, Z, I)),
+ * of which cvo_metric is the approximation of Eq. (indicator_actual).  The
+ * squared norms F(X, X, I) and F(Z, Z, I) do not depend on T: with
+ * norms2_in = NULL they are computed (two extra sweeps, each cloud against
+ * itself with the same kernel and cutoff) and, when norms2_out is not NULL,
+ * returned there so that later calls for other poses can pass them back in
+ * through norms2_in.  An empty cloud gives cos_theta = 0.  With every pair
+ * (cutoff_mult <= 0) the kernel is positive definite and |cos_theta| <= 1;
+ * with a cutoff the same truncated sums are used throughout, for which the
+ * bound is not guaranteed. */
+cvo_status cvo_cosine(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16],
+                      const double* norms2_in, double* cos_theta, double* norms2_out);
+
 /* F, gradient, Hessian, indicator and pair counts in one sweep. */
 cvo_status cvo_evaluate(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], cvo_eval* out);
+
+/* Gradients of dF * F(T) (Eq. double_sum at lengthscale params.ell) with
+ * respect to the inputs, for using F or the indicator as a differentiable
+ * loss (the learning use the paper proposes as future work, Sec. VI).  The
+ * set of pairs inside the cutoff is held fixed, so these are the derivatives
+ * almost everywhere.  With w_ij the pair's weight, y_j = R z_j + t and
+ * d_ij = x_i - y_j:
+ *   dX[i]  = dF/dx_i = -(1/l^2) sum_j w_ij d_ij                    (N x 3)
+ *   dZ[j]  = dF/dz_j = (1/l^2) R^T sum_i w_ij d_ij                 (M x 3)
+ *   dFX[i] = dF/du_i: for a CVO_FEAT_SE block -(1/l_b^2) sum_j w_ij (u_bi - v_bj),
+ *            for a CVO_FEAT_DOT block sum_j w_ij^(b) v_bj, w_ij^(b) being
+ *            the weight without that block's factor                (N x D)
+ *   dFZ[j] = dF/dv_j, the same with the clouds' roles exchanged    (M x D)
+ *   *dell  = dF/dl = (1/l^3) sum_ij w_ij |d_ij|^2
+ * all multiplied by dF (the upstream gradient).  Outputs are float32, row
+ * major, in the clouds' own point order; features give float32 gradients
+ * whatever their storage type (with bfloat16 features, the gradient at the
+ * bfloat16 values).  Any output may be NULL and is then neither computed nor
+ * written.  outputs_on_device = 1: dX, dFX, dZ, dFZ are device pointers
+ * (written on the handle's stream); 0: host pointers.  dell is a host
+ * pointer either way.  The gradient with respect to the pose is the se(3)
+ * gradient of cvo_gradient.  Precision: float32 accumulation per point
+ * (relative error about 1e-6 of the largest term); dF/dl summed in
+ * double-float.  Cost: one sweep per requested side, each about the cost of
+ * one cvo_evaluate. */
+cvo_status cvo_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], double dF,
+                        float* dX, float* dFX, float* dZ, float* dFZ, double* dell, int outputs_on_device);
 
 /* Registration (Problem 1): gradient ascent on SE(3) from T_init, one
  * line-Newton step along the gradient per iteration (t = |g|^2 / -F'' when

@@ -26,7 +26,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["CVO", "cvo_create", "cvo_destroy", "cvo_set_params", "cvo_inner_product", "cvo_gradient", "cvo_metric",
-           "cvo_evaluate", "cvo_register_pair", "cvo_register_batch", "cvo_get_trace", "cvo_set_timing",
+           "cvo_evaluate", "cvo_backward", "cvo_cosine", "CVOInnerProduct", "inner_product_fn", "metric_fn", "cvo_register_pair", "cvo_register_batch", "cvo_get_trace", "cvo_set_timing",
            "cvo_sweep_time", "cvo_last_error", "cvo_version", "cvo_kernel_launches", "load_library", "Status",
            "CvoError"]
 
@@ -105,6 +105,9 @@ def load_library(build_if_missing: bool = True):
         getattr(lib, name).argtypes = [vp, P(Cloud), P(Cloud), vp, P(ctypes.c_double)]
     lib.cvo_gradient.argtypes = [vp, P(Cloud), P(Cloud), vp, vp, P(ctypes.c_double)]
     lib.cvo_evaluate.argtypes = [vp, P(Cloud), P(Cloud), vp, P(Eval)]
+    lib.cvo_cosine.argtypes = [vp, P(Cloud), P(Cloud), vp, vp, P(ctypes.c_double), vp]
+    lib.cvo_backward.argtypes = [vp, P(Cloud), P(Cloud), vp, ctypes.c_double, vp, vp, vp, vp, P(ctypes.c_double),
+                                 ctypes.c_int]
     lib.cvo_register_pair.argtypes = [vp, P(Cloud), P(Cloud), vp, vp, P(Info)]
     lib.cvo_register_batch.argtypes = [vp, ctypes.c_int, P(Cloud), P(Cloud), vp, vp, P(Info)]
     lib.cvo_get_trace.argtypes = [vp, vp, ctypes.c_int]
@@ -113,7 +116,7 @@ def load_library(build_if_missing: bool = True):
     lib.cvo_set_tuning.restype = ctypes.c_int
     lib.cvo_sweep_time.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int)]
     for name in ("cvo_create", "cvo_destroy", "cvo_set_params", "cvo_inner_product", "cvo_metric", "cvo_gradient",
-                 "cvo_evaluate", "cvo_register_pair", "cvo_register_batch", "cvo_get_trace", "cvo_set_timing",
+                 "cvo_evaluate", "cvo_backward", "cvo_cosine", "cvo_register_pair", "cvo_register_batch", "cvo_get_trace", "cvo_set_timing",
                  "cvo_sweep_time"):
         getattr(lib, name).restype = ctypes.c_int
     lib.cvo_last_error.restype = ctypes.c_char_p
@@ -272,6 +275,58 @@ def cvo_evaluate(h, X, Z, T, FX=None, FZ=None) -> dict:
                 pairs=int(e.pairs), candidates=int(e.candidates))
 
 
+_GRAD_NAMES = ("dX", "dFX", "dZ", "dFZ")
+
+
+def cvo_backward(h, X, Z, T, FX=None, FZ=None, dF=1.0, want=("dX", "dFX", "dZ", "dFZ", "dell")) -> dict:
+    """Gradients of dF * F(T) with respect to the points, the features and the
+    lengthscale (see cvo_backward in cvo.h).  Outputs are float32 torch CUDA
+    tensors when X is a CUDA tensor, numpy arrays otherwise; names not in
+    `want` are neither computed nor returned."""
+    cx, cz, keep = _clouds(X, Z, FX, FZ)
+    Tm = _pose(T)
+    D = 0
+    for f in (FX, FZ):
+        if f is not None and len(f.shape) == 2:
+            D = int(f.shape[1])
+    shapes = {"dX": (cx.n, 3), "dFX": (cx.n, D), "dZ": (cz.n, 3), "dFZ": (cz.n, D)}
+    on_dev = bool(cx.on_device)
+    out = {}
+    ptrs = []
+    for name in _GRAD_NAMES:
+        if name not in want or (name in ("dFX", "dFZ") and D == 0):
+            ptrs.append(None)
+            continue
+        if on_dev:
+            torch = _torch()
+            t = torch.empty(shapes[name], dtype=torch.float32, device=X.device)
+            out[name] = t
+            ptrs.append(t.data_ptr() if t.numel() else None)
+        else:
+            a = np.zeros(shapes[name], dtype=np.float32)
+            out[name] = a
+            ptrs.append(a.ctypes.data if a.size else None)
+    dell = ctypes.c_double()
+    _check(load_library().cvo_backward(h, ctypes.byref(cx), ctypes.byref(cz), Tm.ctypes.data, float(dF), *ptrs,
+                                       ctypes.byref(dell) if "dell" in want else None, int(on_dev)))
+    if "dell" in want:
+        out["dell"] = dell.value
+    return out
+
+
+def cvo_cosine(h, X, Z, T, FX=None, FZ=None, norms2=None):
+    """Exact indicator of Eq. (indicator): returns (cos_theta, (|f_X|^2, |f_Z|^2)).
+    Pass the returned norms back as norms2 to skip the two self sweeps."""
+    cx, cz, keep = _clouds(X, Z, FX, FZ)
+    Tm = _pose(T)
+    nin = None if norms2 is None else np.ascontiguousarray(np.asarray(norms2, dtype=np.float64).reshape(2))
+    nout = np.zeros(2)
+    c = ctypes.c_double()
+    _check(load_library().cvo_cosine(h, ctypes.byref(cx), ctypes.byref(cz), Tm.ctypes.data,
+                                     None if nin is None else nin.ctypes.data, ctypes.byref(c), nout.ctypes.data))
+    return c.value, (float(nout[0]), float(nout[1]))
+
+
 def cvo_inner_product(h, X, Z, T, FX=None, FZ=None) -> float:
     cx, cz, keep = _clouds(X, Z, FX, FZ)
     Tm = _pose(T)
@@ -388,6 +443,12 @@ class CVO:
     def metric(self, X, Z, T, FX=None, FZ=None):
         return cvo_metric(self.h, X, Z, T, FX, FZ)
 
+    def cosine(self, X, Z, T, FX=None, FZ=None, norms2=None):
+        return cvo_cosine(self.h, X, Z, T, FX, FZ, norms2)
+
+    def backward(self, X, Z, T, FX=None, FZ=None, dF=1.0, want=("dX", "dFX", "dZ", "dFZ", "dell")):
+        return cvo_backward(self.h, X, Z, T, FX, FZ, dF, want)
+
     def register(self, X, Z, T_init=None, FX=None, FZ=None):
         return cvo_register_pair(self.h, X, Z, np.eye(4) if T_init is None else T_init, FX, FZ)
 
@@ -396,3 +457,96 @@ class CVO:
 
     def trace(self):
         return cvo_get_trace(self.h)
+
+
+# ---- differentiable form ---------------------------------------------------------
+
+def _autograd_function():
+    torch = _torch()
+    if torch is None:  # pragma: no cover
+        raise RuntimeError("the differentiable form needs PyTorch")
+
+    class _InnerProduct(torch.autograd.Function):
+        """F(T) of Eq. (double_sum) as a function of X, Z, their features and
+        the lengthscale; the backward pass runs the library's gradient sweeps.
+        T is a constant here: the pose gradient is cvo_gradient's se(3)
+        vector."""
+
+        @staticmethod
+        def forward(ctx, X, Z, FX, FZ, ell, T, cvo):
+            params = cvo.params
+            ell_v = float(ell) if ell is not None else params.ell
+            p = Params.from_buffer_copy(params)
+            p.ell = ell_v
+            cvo_set_params(cvo.h, p)
+            try:
+                F = cvo_inner_product(cvo.h, X, Z, T, FX, FZ)
+            finally:
+                cvo_set_params(cvo.h, params)
+            ctx.cvo = cvo
+            ctx.T = np.array(_pose(T))
+            ctx.ell = ell_v
+            ctx.save_for_backward(X, Z, FX, FZ)
+            ctx.ell_meta = (ell.dtype, ell.device) if isinstance(ell, torch.Tensor) else None
+            dev = X.device if isinstance(X, torch.Tensor) else "cpu"
+            return torch.tensor(F, dtype=torch.float64, device=dev)
+
+        @staticmethod
+        def backward(ctx, gF):
+            X, Z, FX, FZ = ctx.saved_tensors
+            need = ctx.needs_input_grad
+            want = [n for n, k in (("dX", 0), ("dZ", 1), ("dFX", 2), ("dFZ", 3)) if need[k]]
+            if need[4]:
+                want.append("dell")
+            if not want:
+                return (None,) * 7
+            cvo = ctx.cvo
+            params = cvo.params
+            p = Params.from_buffer_copy(params)
+            p.ell = ctx.ell
+            cvo_set_params(cvo.h, p)
+            try:
+                out = cvo_backward(cvo.h, X, Z, ctx.T, FX, FZ, dF=float(gF), want=tuple(want))
+            finally:
+                cvo_set_params(cvo.h, params)
+
+            def as_grad(name, like):
+                if name not in out:
+                    return None
+                g = out[name]
+                if not isinstance(g, torch.Tensor):
+                    g = torch.from_numpy(g)
+                return g.to(dtype=like.dtype, device=like.device)
+
+            dell = None
+            if "dell" in out and ctx.ell_meta is not None:
+                dell = torch.tensor(out["dell"], dtype=ctx.ell_meta[0], device=ctx.ell_meta[1])
+            return (as_grad("dX", X), as_grad("dZ", Z), as_grad("dFX", FX) if FX is not None else None,
+                    as_grad("dFZ", FZ) if FZ is not None else None, dell, None, None)
+
+    return _InnerProduct
+
+
+_fn_cache = {}
+
+
+def CVOInnerProduct():
+    """The torch.autograd.Function class of the differentiable F (built on
+    first use so that importing this package does not need PyTorch)."""
+    if "f" not in _fn_cache:
+        _fn_cache["f"] = _autograd_function()
+    return _fn_cache["f"]
+
+
+def inner_product_fn(cvo: "CVO", X, Z, T, FX=None, FZ=None, ell=None):
+    """Differentiable F(T) (a float64 scalar tensor) of torch tensors X (N, 3),
+    Z (M, 3), features FX, FZ and an optional lengthscale tensor ell (else the
+    handle's params.ell); gradients flow to every input that requires them."""
+    return CVOInnerProduct().apply(X, Z, FX, FZ, ell, T, cvo)
+
+
+def metric_fn(cvo: "CVO", X, Z, T, FX=None, FZ=None, ell=None):
+    """Differentiable indicator i_theta = F / sqrt(N M) of Eq. (indicator_actual)."""
+    n, m = int(X.shape[0]), int(Z.shape[0])
+    F = inner_product_fn(cvo, X, Z, T, FX, FZ, ell)
+    return F / float(np.sqrt(n * m)) if n and m else F * 0.0

@@ -137,6 +137,9 @@ struct cvo_handle_s {
     DevBuf keys, vals, keys2, vals2, sort_tmp, flags, gidx, misc;
     // sweep / finalize scratch
     DevBuf part_stats, part_cnt, grp_stats, grp_cnt, grp_arrivals, pairs_dev, counters, trace;
+    // gradients with respect to the inputs: device outputs for host callers,
+    // per-query terms of dF/dl and their sum
+    DevBuf bw_out[4], bw_tq, bw_dell;
     std::vector<PairRes> pr;
     IterState* h_state = nullptr;   // pinned mirror(s)
     int h_state_cap = 0;
@@ -890,6 +893,106 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
     return worst;
 }
 
+// Gradients of F(T) with respect to both clouds' points and features and to
+// the lengthscale: one gradient sweep per cloud, each with that cloud as the
+// queries over a grid of the other (no atomics, so the result is
+// deterministic), and a fixed-order sum for dF/dl.
+cvo_status run_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double* T, double dF, float* dX,
+                        float* dFX, float* dZ, float* dFZ, double* dell, int on_dev)
+{
+    const cvo_params& p = h->p;
+    const int D = feat_dim(p);
+    const int n = X->n, m = Z->n;
+    float* outs[4] = {dX, dFX, dZ, dFZ};
+    const size_t bytes[4] = {(size_t)n * 3 * sizeof(float), (size_t)n * D * sizeof(float),
+                             (size_t)m * 3 * sizeof(float), (size_t)m * D * sizeof(float)};
+    if (dell) *dell = 0.0;
+    if (n == 0 || m == 0) {
+        // no pair: every gradient is zero
+        for (int k = 0; k < 4; ++k) {
+            if (!outs[k] || bytes[k] == 0) continue;
+            if (on_dev) CVO_CUDA(cudaMemsetAsync(outs[k], 0, bytes[k], h->s));
+            else std::memset(outs[k], 0, bytes[k]);
+        }
+        CVO_CUDA(cudaStreamSynchronize(h->s));
+        return CVO_OK;
+    }
+    CVO_TRY(begin_call(h, rec_bf16_of(p, X, Z), 2));
+    // device destinations
+    float* dev[4];
+    for (int k = 0; k < 4; ++k) {
+        dev[k] = nullptr;
+        if (!outs[k] || bytes[k] == 0) continue;
+        if (on_dev) {
+            dev[k] = outs[k];
+        } else {
+            CVO_CUDA(ensure(h->bw_out[k], bytes[k]));
+            dev[k] = (float*)h->bw_out[k].p;
+        }
+    }
+    const double ell = p.ell;
+    const double sc = dF * h->kappa;
+    GradArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.rs = h->rs;
+    g.dense = h->dense;
+    g.fc = h->fc;
+    g.scale_pos = (float)(sc / (ell * ell));
+    g.scale_feat = (float)sc;
+    g.scale_ell = (float)(sc / (ell * ell * ell));
+    for (int b = 0; b < p.n_blocks; ++b)
+        g.inv_lb2[b] = p.blocks[b].kind == CVO_FEAT_SE ? (float)(1.0 / (p.blocks[b].scale * p.blocks[b].scale)) : 0.0f;
+    auto sweep = [&](int slot, const cvo_cloud* Q, const cvo_cloud* G, const double* Tq, bool rout_transpose,
+                     float* pos, float* feat, float* tq) -> cvo_status {
+        PairRes& P = h->pr[slot];
+        CVO_TRY(prepare(h, P, Q, G, ell, ell));
+        CVO_TRY(init_state(h, P, slot, Tq, ell, 0));
+        g.levels = (const LevelDesc*)P.levels_dev.p;
+        g.xrec = (const float4*)P.xrec.p;
+        g.st = (const IterState*)P.state.p;
+        g.m = P.m;
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) g.Rout[3 * r + c] = (float)(rout_transpose ? T[4 * c + r] : T[4 * r + c]);
+        g.out_pos = pos;
+        g.out_feat = D > 0 ? feat : nullptr;
+        g.out_tq = tq;
+        const int ngroups = P.lv[0].ngroups;
+        const int nb = std::max(1, std::min((ngroups + kSweepWarps - 1) / kSweepWarps, h->num_sms * 16));
+        CVO_CUDA(launch_grad(g, nb, h->s));
+        return CVO_OK;
+    };
+    if (dev[0] || dev[1] || dell) {
+        float* tq = nullptr;
+        if (dell) {
+            CVO_CUDA(ensure(h->bw_tq, (size_t)n * sizeof(float)));
+            CVO_CUDA(ensure(h->bw_dell, sizeof(double)));
+            tq = (float*)h->bw_tq.p;
+        }
+        CVO_TRY(sweep(0, X, Z, T, false, dev[0], dev[1], tq));
+        if (dell) {
+            CVO_CUDA(launch_sum_f32(tq, n, (double*)h->bw_dell.p, h->s));
+            CVO_CUDA(cudaMemcpyAsync(dell, h->bw_dell.p, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+        }
+    }
+    if (dev[2] || dev[3]) {
+        // Z as the queries over the grid of X: the query transform is T itself
+        // (T^-1 of the inverse pose), and dF/dz = R^T dF/dy
+        double Ti[16];
+        for (int r = 0; r < 3; ++r) {
+            for (int c = 0; c < 3; ++c) Ti[4 * r + c] = T[4 * c + r];
+            Ti[4 * r + 3] = -(T[r] * T[3] + T[4 + r] * T[7] + T[8 + r] * T[11]);
+        }
+        Ti[12] = Ti[13] = Ti[14] = 0.0;
+        Ti[15] = 1.0;
+        CVO_TRY(sweep(1, Z, X, Ti, true, dev[2], dev[3], nullptr));
+    }
+    if (!on_dev)
+        for (int k = 0; k < 4; ++k)
+            if (dev[k]) CVO_CUDA(cudaMemcpyAsync(outs[k], dev[k], bytes[k], cudaMemcpyDeviceToHost, h->s));
+    CVO_CUDA(cudaStreamSynchronize(h->s));
+    return CVO_OK;
+}
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev)
@@ -951,7 +1054,8 @@ cvo_status cvo_destroy(cvo_handle h)
     cudaStreamSynchronize(h->s);
     DevBuf* bufs[] = {&h->stage_xyz[0], &h->stage_xyz[1], &h->stage_feat[0], &h->stage_feat[1], &h->keys, &h->vals,
                       &h->keys2, &h->vals2, &h->sort_tmp, &h->flags, &h->gidx, &h->misc, &h->part_stats, &h->part_cnt,
-                      &h->grp_stats, &h->grp_cnt, &h->grp_arrivals, &h->pairs_dev, &h->counters, &h->trace};
+                      &h->grp_stats, &h->grp_cnt, &h->grp_arrivals, &h->pairs_dev, &h->counters, &h->trace,
+                      &h->bw_out[0], &h->bw_out[1], &h->bw_out[2], &h->bw_out[3], &h->bw_tq, &h->bw_dell};
     for (DevBuf* b : bufs) release(*b);
     for (PairRes& P : h->pr) P.free_all();
     for (cudaEvent_t e : h->evs) cudaEventDestroy(e);
@@ -981,6 +1085,71 @@ cvo_status cvo_evaluate(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     CVO_TRY(check_pose(T, "T"));
     DeviceGuard g(h->device);
     return run_eval(h, X, Z, T, out);
+}
+
+cvo_status cvo_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], double dF,
+                        float* dX, float* dFX, float* dZ, float* dFZ, double* dell, int outputs_on_device)
+{
+    g_err.clear();
+    if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
+    if (!std::isfinite(dF)) return fail(CVO_ERR_INVALID_ARG, "dF must be finite");
+    const int D = feat_dim(h->p);
+    CVO_TRY(check_cloud(X, "X", D));
+    CVO_TRY(check_cloud(Z, "Z", D));
+    CVO_TRY(check_pose(T, "T"));
+    DeviceGuard g(h->device);
+    if (outputs_on_device) {
+        float* outs[4] = {dX, dFX, dZ, dFZ};
+        for (float* o : outs) {
+            if (!o) continue;
+            cudaPointerAttributes at;
+            if (cudaPointerGetAttributes(&at, o) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(CVO_ERR_INVALID_ARG, "output pointer is not known to CUDA");
+            }
+            if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+                return fail(CVO_ERR_INVALID_ARG, "outputs_on_device = 1 but an output is not device memory");
+        }
+    }
+    return run_backward(h, X, Z, T, dF, dX, dFX, dZ, dFZ, dell, outputs_on_device ? 1 : 0);
+}
+
+cvo_status cvo_cosine(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16],
+                      const double* norms2_in, double* cos_theta, double* norms2_out)
+{
+    g_err.clear();
+    if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
+    if (!cos_theta) return fail(CVO_ERR_INVALID_ARG, "cos_theta is NULL");
+    const int D = feat_dim(h->p);
+    CVO_TRY(check_cloud(X, "X", D));
+    CVO_TRY(check_cloud(Z, "Z", D));
+    CVO_TRY(check_pose(T, "T"));
+    DeviceGuard g(h->device);
+    double nn[2];
+    if (norms2_in) {
+        if (!(norms2_in[0] >= 0.0) || !(norms2_in[1] >= 0.0))
+            return fail(CVO_ERR_INVALID_ARG, "norms2_in must be two values >= 0");
+        nn[0] = norms2_in[0];
+        nn[1] = norms2_in[1];
+    } else {
+        // self inner products at the identity: independent of T, so callers
+        // that evaluate many poses pass them back in through norms2_in
+        static const double I[16] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1};
+        cvo_eval e;
+        CVO_TRY(run_eval(h, X, X, I, &e));
+        nn[0] = e.F;
+        CVO_TRY(run_eval(h, Z, Z, I, &e));
+        nn[1] = e.F;
+    }
+    cvo_eval e;
+    CVO_TRY(run_eval(h, X, Z, T, &e));
+    const double den = std::sqrt(nn[0] * nn[1]);
+    *cos_theta = den > 0.0 ? e.F / den : 0.0;
+    if (norms2_out) {
+        norms2_out[0] = nn[0];
+        norms2_out[1] = nn[1];
+    }
+    return CVO_OK;
 }
 
 cvo_status cvo_inner_product(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], double* F)

@@ -2,7 +2,8 @@
 //
 // Data layout in device memory (one handle, one pair):
 //   zrec[level]   M records sorted by grid cell (x fastest), RS float4 each:
-//                 rec[0] = (x, y, z, 0) float32 as given; rec[1..] = the point's
+//                 rec[0] = (x, y, z, index) float32 as given, the w lane
+//                 holding the point's index bits; rec[1..] = the point's
 //                 feature row (float32 or bfloat16, blocks concatenated,
 //                 zero padded to 16 bytes)
 //   cell_start    per level, ncells + 1 ints: records of cell c are
@@ -162,6 +163,30 @@ cudaError_t launch_init_state(IterState* st, cudaStream_t s);
 // Reduces the ceil(nblocks / kGroupBlocks) group sums of a sweep and takes the step.
 cudaError_t launch_finalize(IterState* st, const float2* grp_stats, const unsigned long long* grp_cnt, int nblocks,
                             double* trace, cudaStream_t s);
+
+// Gradients of F with respect to one cloud's points and features: a sweep with
+// that cloud as the queries (see cvo_sweep.cu, k_grad).
+struct GradArgs {
+    const LevelDesc* levels;   // grid of the other cloud
+    const float4* xrec;        // queries; record w = the point's index in the caller's order
+    const IterState* st;       // query transform, lengthscale, cutoff, level
+    int m;                     // points in the other cloud
+    int rs, dense;
+    FeatConst fc;
+    float Rout[9];             // rotation from the sweep frame to the queries' frame (row major)
+    float scale_pos;           // dF * kappa / l^2
+    float scale_feat;          // dF * kappa
+    float scale_ell;           // dF * kappa / l^3
+    float inv_lb2[4];          // 1 / l_b^2 of the squared-exponential blocks
+    float* out_pos;            // N x 3, or NULL
+    float* out_feat;           // N x D, or NULL
+    float* out_tq;             // N per-query terms of dF/dl, or NULL
+};
+// One warp per query group over the group's whole candidate stream; every
+// query's outputs are written (zero when it has no pair in range).
+cudaError_t launch_grad(const GradArgs& g, int nblocks, cudaStream_t s);
+// Deterministic sum of n floats into *out (one block).
+cudaError_t launch_sum_f32(const float* v, int n, double* out, cudaStream_t s);
 
 // setup (cvo_setup.cu)
 cudaError_t launch_bbox(const float* xyz, int n, unsigned* out6, int* bad, cudaStream_t s);

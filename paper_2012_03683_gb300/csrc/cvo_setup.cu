@@ -217,7 +217,8 @@ __global__ void k_pack(const float* __restrict__ xyz, const void* __restrict__ f
     if (s >= n) return;
     const int j = order ? (int)order[s] : s;
     float4* r = rec + (size_t)s * rs;
-    r[0] = make_float4(xyz[3 * (size_t)j], xyz[3 * (size_t)j + 1], xyz[3 * (size_t)j + 2], 0.0f);
+    // w carries the point's index in the caller's order (for per-point outputs)
+    r[0] = make_float4(xyz[3 * (size_t)j], xyz[3 * (size_t)j + 1], xyz[3 * (size_t)j + 2], __int_as_float(j));
     if (rs <= 1) return;
     if (rec_bf16) {
         unsigned short* dst = (unsigned short*)(r + 1);
@@ -270,9 +271,40 @@ __global__ void k_group_write(const unsigned* __restrict__ morton, const unsigne
     groups[gidx[i]] = make_int2(i, min(32, end - i));
 }
 
+// Deterministic sum of n floats: per-thread double-float partials in a fixed
+// stride, then a fixed-order block reduction.  One block.
+__global__ void k_sum_f32(const float* __restrict__ v, int n, double* out)
+{
+    __shared__ float sh[1024], sl[1024];
+    float hi = 0.0f, lo = 0.0f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float s = __fadd_rn(hi, v[i]);
+        const float bb = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v[i], bb));
+        const float t = __fadd_rn(lo, e);
+        hi = __fadd_rn(s, t);
+        lo = __fsub_rn(t, __fsub_rn(hi, s));
+    }
+    sh[threadIdx.x] = hi;
+    sl[threadIdx.x] = lo;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double acc = 0.0;
+        for (int t = 0; t < (int)blockDim.x; ++t) acc += (double)sh[t] + (double)sl[t];
+        *out = acc;
+    }
+}
+
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
+
+cudaError_t launch_sum_f32(const float* v, int n, double* out, cudaStream_t s)
+{
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    k_sum_f32<<<1, 1024, 0, s>>>(v, n, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_bbox(const float* xyz, int n, unsigned* out6, int* bad, cudaStream_t s)
 {

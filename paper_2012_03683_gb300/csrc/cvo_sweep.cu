@@ -191,6 +191,145 @@ __device__ __forceinline__ int floor_cell(float v, float o, float inv_h)
     return (int)fminf(fmaxf(c, -2.0e9f), 2.0e9f);
 }
 
+// A query group's candidate stream: the runs of grid cells (one per (y, z)
+// cell row) that overlap the group's bounding box grown by the cutoff radius.
+struct Stream {
+    int cx0, cx1, cy0, cz0, nry, nruns, total;
+};
+
+// Warp-uniform.  Returns false when the grown box misses the grid.
+__device__ __forceinline__ bool stream_setup(const LevelDesc& L, int m, bool dense, bool act, const float xh[3],
+                                             float rc, int lane, Stream& s)
+{
+    s.cx0 = s.cx1 = s.cy0 = s.cz0 = 0;
+    s.nry = 1;
+    s.nruns = 1;
+    if (!dense) {
+        float mn[3], mx[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            mn[r] = act ? xh[r] : 3.0e38f;
+            mx[r] = act ? xh[r] : -3.0e38f;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                mn[r] = fminf(mn[r], __shfl_xor_sync(kFull, mn[r], o));
+                mx[r] = fmaxf(mx[r], __shfl_xor_sync(kFull, mx[r], o));
+            }
+        }
+        const float o3[3] = {L.ox, L.oy, L.oz};
+        const int n3[3] = {L.nx, L.ny, L.nz};
+        int c0[3], c1[3];
+        bool empty = false;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const float pad = rc * 1.0001f + 4.0e-7f * fmaxf(fabsf(mn[r]), fabsf(mx[r])) + 1.0e-6f;
+            c0[r] = floor_cell(mn[r] - pad, o3[r], L.inv_h);
+            c1[r] = floor_cell(mx[r] + pad, o3[r], L.inv_h);
+            if (c1[r] < 0 || c0[r] > n3[r] - 1) empty = true;
+            c0[r] = max(c0[r], 0);
+            c1[r] = min(c1[r], n3[r] - 1);
+        }
+        if (empty) return false;
+        s.cx0 = c0[0]; s.cx1 = c1[0]; s.cy0 = c0[1]; s.cz0 = c0[2];
+        s.nry = c1[1] - c0[1] + 1;
+        s.nruns = s.nry * (c1[2] - c0[2] + 1);
+    }
+    int total = 0;
+    for (int b0 = 0; b0 < s.nruns; b0 += 32) {
+        int len = 0;
+        const int r = b0 + lane;
+        if (r < s.nruns) {
+            if (dense) {
+                len = m;
+            } else {
+                const int cy = s.cy0 + r % s.nry, cz = s.cz0 + r / s.nry;
+                const int row = (cz * L.ny + cy) * L.nx;
+                len = __ldg(L.cell_start + row + s.cx1 + 1) - __ldg(L.cell_start + row + s.cx0);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) len += __shfl_xor_sync(kFull, len, o);
+        total += len;
+    }
+    s.total = total;
+    return true;
+}
+
+// Stages the stream positions [clo, chi) into shared memory 32 records at a
+// time (cp.async, one record per lane, double buffered) and calls
+// op(batch, count) on each staged batch.  Warp-uniform.
+template <class Op>
+__device__ __forceinline__ void stream_walk(const LevelDesc& L, int m, bool dense, const Stream& s, int clo, int chi,
+                                            int rs, float4* stage, int lane, Op&& op)
+{
+    int base = 0;
+    for (int b0 = 0; b0 < s.nruns && base < chi; b0 += 32) {
+        int rstart = 0, rlen = 0;
+        const int r = b0 + lane;
+        if (r < s.nruns) {
+            if (dense) {
+                rstart = 0;
+                rlen = m;
+            } else {
+                const int cy = s.cy0 + r % s.nry, cz = s.cz0 + r / s.nry;
+                const int row = (cz * L.ny + cy) * L.nx;
+                rstart = __ldg(L.cell_start + row + s.cx0);
+                rlen = __ldg(L.cell_start + row + s.cx1 + 1) - rstart;
+            }
+        }
+        int incl = rlen;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int roff = incl - rlen;
+        const int btotal = __shfl_sync(kFull, incl, 31);
+        const int lo = max(clo, base) - base;   // positions relative to this pass
+        const int hi = min(chi, base + btotal) - base;
+        if (lo < hi) {
+            const int nbat = (hi - lo + 31) >> 5;
+            // stage batch bi (positions lo + 32 bi + lane) into buffer bi & 1
+            auto issue = [&](int bi) {
+                const int p0 = lo + 32 * bi;
+                const int p = p0 + lane;
+                // first run that ends after p0
+                const unsigned before = __ballot_sync(kFull, (r < s.nruns) && (roff + rlen <= p0));
+                int j = -1;
+                for (int ri = __popc(before); ri < 32; ++ri) {
+                    const int o = __shfl_sync(kFull, roff, ri);
+                    const int l = __shfl_sync(kFull, rlen, ri);
+                    const int s0 = __shfl_sync(kFull, rstart, ri);
+                    if (o >= p0 + 32 || o >= hi) break;
+                    if (p < hi && p >= o && p < o + l) j = s0 + (p - o);
+                }
+                if (j >= 0) {
+                    const float4* src = L.zrec + (size_t)j * rs;
+                    float4* dst = stage + ((bi & 1) * 32 + lane) * rs;
+                    for (int q = 0; q < rs; ++q) cp_async16(dst + q, src + q);
+                }
+                cp_async_commit();
+            };
+            issue(0);
+            for (int bi = 0; bi < nbat; ++bi) {
+                if (bi + 1 < nbat) {
+                    issue(bi + 1);
+                    cp_async_wait_one();
+                } else {
+                    cp_async_wait_all();
+                }
+                __syncwarp();
+                op(stage + (bi & 1) * 32 * rs, min(32, hi - (lo + 32 * bi)));
+                __syncwarp();
+            }
+        }
+        base += btotal;
+    }
+}
+
 struct Moments {
     float W, E0, E1, E2, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz;
 };
@@ -278,59 +417,9 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
         float xh[3], xl[3];
         transform_df(xq, Ahi, Alo, bhi, blo, xh, xl);
 
-        // candidate stream: runs of cells (one per (y, z) cell row)
-        int cx0 = 0, cx1 = 0, cy0 = 0, cz0 = 0, nry = 1, nruns = 1;
-        if (!dense) {
-            float mn[3], mx[3];
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                mn[r] = act ? xh[r] : 3.0e38f;
-                mx[r] = act ? xh[r] : -3.0e38f;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    mn[r] = fminf(mn[r], __shfl_xor_sync(kFull, mn[r], o));
-                    mx[r] = fmaxf(mx[r], __shfl_xor_sync(kFull, mx[r], o));
-                }
-            }
-            const float o3[3] = {L.ox, L.oy, L.oz};
-            const int n3[3] = {L.nx, L.ny, L.nz};
-            int c0[3], c1[3];
-            bool empty = false;
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                const float pad = rc * 1.0001f + 4.0e-7f * fmaxf(fabsf(mn[r]), fabsf(mx[r])) + 1.0e-6f;
-                c0[r] = floor_cell(mn[r] - pad, o3[r], L.inv_h);
-                c1[r] = floor_cell(mx[r] + pad, o3[r], L.inv_h);
-                if (c1[r] < 0 || c0[r] > n3[r] - 1) empty = true;
-                c0[r] = max(c0[r], 0);
-                c1[r] = min(c1[r], n3[r] - 1);
-            }
-            if (empty) continue;
-            cx0 = c0[0]; cx1 = c1[0]; cy0 = c0[1]; cz0 = c0[2];
-            nry = c1[1] - c0[1] + 1;
-            nruns = nry * (c1[2] - c0[2] + 1);
-        }
-        // total stream length
-        int total = 0;
-        for (int b0 = 0; b0 < nruns; b0 += 32) {
-            int len = 0;
-            const int r = b0 + lane;
-            if (r < nruns) {
-                if (dense) {
-                    len = P.m;
-                } else {
-                    const int cy = cy0 + r % nry, cz = cz0 + r / nry;
-                    const int row = (cz * L.ny + cy) * L.nx;
-                    len = __ldg(L.cell_start + row + cx1 + 1) - __ldg(L.cell_start + row + cx0);
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) len += __shfl_xor_sync(kFull, len, o);
-            total += len;
-        }
+        Stream sm;
+        if (!stream_setup(L, P.m, dense, act, xh, rc, lane, sm)) continue;
+        const int total = sm.total;
         if (total == 0) continue;
         const int nch = min(kChunks, (total + kChunkMin - 1) / kChunkMin);
         if (k >= nch) continue;
@@ -341,72 +430,10 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
         Feat::load_query(qf, qrec, fc);
         Moments mo = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 
-        int base = 0;
-        for (int b0 = 0; b0 < nruns && base < chi_; b0 += 32) {
-            int rstart = 0, rlen = 0;
-            const int r = b0 + lane;
-            if (r < nruns) {
-                if (dense) {
-                    rstart = 0;
-                    rlen = P.m;
-                } else {
-                    const int cy = cy0 + r % nry, cz = cz0 + r / nry;
-                    const int row = (cz * L.ny + cy) * L.nx;
-                    rstart = __ldg(L.cell_start + row + cx0);
-                    rlen = __ldg(L.cell_start + row + cx1 + 1) - rstart;
-                }
-            }
-            int incl = rlen;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += v;
-            }
-            const int roff = incl - rlen;
-            const int btotal = __shfl_sync(kFull, incl, 31);
-            const int lo = max(clo_, base) - base;   // positions relative to this pass
-            const int hi = min(chi_, base + btotal) - base;
-            if (lo < hi) {
-                const int nbat = (hi - lo + 31) >> 5;
-                // stage batch bi (positions lo + 32 bi + lane) into buffer bi & 1
-                auto issue = [&](int bi) {
-                    const int p0 = lo + 32 * bi;
-                    const int p = p0 + lane;
-                    // first run that ends after p0
-                    const unsigned before = __ballot_sync(kFull, (r < nruns) && (roff + rlen <= p0));
-                    int j = -1;
-                    for (int ri = __popc(before); ri < 32; ++ri) {
-                        const int o = __shfl_sync(kFull, roff, ri);
-                        const int l = __shfl_sync(kFull, rlen, ri);
-                        const int s0 = __shfl_sync(kFull, rstart, ri);
-                        if (o >= p0 + 32 || o >= hi) break;
-                        if (p < hi && p >= o && p < o + l) j = s0 + (p - o);
-                    }
-                    if (j >= 0) {
-                        const float4* src = L.zrec + (size_t)j * rs;
-                        float4* dst = stage + ((bi & 1) * 32 + lane) * rs;
-                        for (int q = 0; q < rs; ++q) cp_async16(dst + q, src + q);
-                    }
-                    cp_async_commit();
-                };
-                issue(0);
-                for (int bi = 0; bi < nbat; ++bi) {
-                    if (bi + 1 < nbat) {
-                        issue(bi + 1);
-                        cp_async_wait_one();
-                    } else {
-                        cp_async_wait_all();
-                    }
-                    __syncwarp();
-                    const int cnt = min(32, hi - (lo + 32 * bi));
-                    eval_batch<Feat>(stage + (bi & 1) * 32 * rs, cnt, rs, qf, xh, xl, act, dense, sg, rc2, fc, mo,
-                                     npairs);
-                    ncand += act ? (unsigned)cnt : 0u;
-                    __syncwarp();
-                }
-            }
-            base += btotal;
-        }
+        stream_walk(L, P.m, dense, sm, clo_, chi_, rs, stage, lane, [&](const float4* sb, int cnt) {
+            eval_batch<Feat>(sb, cnt, rs, qf, xh, xl, act, dense, sg, rc2, fc, mo, npairs);
+            ncand += act ? (unsigned)cnt : 0u;
+        });
         if (act) {
             // lever arm p = x' - c
             const float p0 = (xh[0] - chi[0]) + (xl[0] - clo[0]);
@@ -526,6 +553,261 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
     if (threadIdx.x == 0) a.grp_arrivals[grp] = 0u;
 }
 
+// ---- gradients with respect to the inputs -----------------------------------
+//
+// For the pairs inside the cutoff (the pair set held fixed) and the weight
+// w = kappa * 2^(arg) * prod(inner products) of one pair, e = z - x' in the
+// sweep frame, d^2 = |e|^2:
+//   dF/dx      = Rout * sum w e / l^2          (x the query point)
+//   dF/dl      = sum w d^2 / l^3
+//   dF/du_SE   = -sum w (u - v) / l_b^2        (squared-exponential block)
+//   dF/du_DOT  = sum w_(b) v                   (inner-product block; w_(b)
+//                                               is w without that block's factor)
+// The same kernel serves both clouds: with X as the queries (Rout = R) and
+// with Z as the queries over the grid of X (Rout = R^T).
+// A policy per block list supplies the per-candidate feature work.
+
+template <int DSE, int DDOT, bool BF16>
+struct GradFixed {
+    using F = FeatFixed<DSE, DDOT, BF16>;
+    static constexpr int D = F::D;
+    static constexpr bool kSharedAcc = false;
+    using Q = typename F::Q;
+    struct V {
+        float v[D];
+    };
+    struct Acc {
+        float a[D > 0 ? D : 1];   // SE entries: sum w (u - v); inner-product entries: sum w_(b) v
+    };
+    __device__ static void load_query(Q& q, const float4* rec, const FeatConst& fc) { F::load_query(q, rec, fc); }
+    __device__ static void zero(Acc& a, float*, const FeatConst&)
+    {
+#pragma unroll
+        for (int k = 0; k < D; ++k) a.a[k] = 0.0f;
+    }
+    // adds the feature exponent to arg; returns the inner-product factor
+    __device__ static float pair(const Q& q, const float4* rec, float& arg, V& c, const FeatConst& fc)
+    {
+        F::unpack(rec + 1, c.v);
+        if constexpr (DSE > 0) {
+            float du2 = 0.0f;
+#pragma unroll
+            for (int k = 0; k < DSE; ++k) {
+                const float d = q.v[k] - c.v[k];
+                du2 = fmaf(d, d, du2);
+            }
+            arg = fmaf(du2, fc.s[0], arg);
+        }
+        if constexpr (DDOT > 0) {
+            float dot = 0.0f;
+#pragma unroll
+            for (int k = 0; k < DDOT; ++k) dot = fmaf(q.v[DSE + k], c.v[DSE + k], dot);
+            return dot;
+        }
+        return 1.0f;
+    }
+    // base: the weight without the inner-product factor; w: the full weight
+    __device__ static void accum(Acc& a, const Q& q, const float4*, const V& c, float base, float w, float*,
+                                 const FeatConst&)
+    {
+#pragma unroll
+        for (int k = 0; k < DSE; ++k) a.a[k] = fmaf(w, q.v[k] - c.v[k], a.a[k]);
+#pragma unroll
+        for (int k = 0; k < DDOT; ++k) a.a[DSE + k] = fmaf(base, c.v[DSE + k], a.a[DSE + k]);
+    }
+    __device__ static void write(const Acc& a, const float*, const GradArgs& g, float* out)
+    {
+#pragma unroll
+        for (int k = 0; k < DSE; ++k) out[k] = -g.scale_feat * g.inv_lb2[0] * a.a[k];
+#pragma unroll
+        for (int k = 0; k < DDOT; ++k) out[DSE + k] = g.scale_feat * a.a[DSE + k];
+    }
+};
+
+// Geometric kernel only (Eq. geometric_only): no feature outputs.
+struct GradNone {
+    static constexpr bool kSharedAcc = false;
+    struct Q {};
+    struct V {};
+    struct Acc {};
+    __device__ static void load_query(Q&, const float4*, const FeatConst&) {}
+    __device__ static void zero(Acc&, float*, const FeatConst&) {}
+    __device__ static float pair(const Q&, const float4*, float&, V&, const FeatConst&) { return 1.0f; }
+    __device__ static void accum(Acc&, const Q&, const float4*, const V&, float, float, float*, const FeatConst&) {}
+    __device__ static void write(const Acc&, const float*, const GradArgs&, float*) {}
+};
+
+// Any block list: per-lane feature accumulators in shared memory (stride 32).
+struct GradGeneric {
+    static constexpr bool kSharedAcc = true;
+    struct Q {
+        const float4* rec;
+    };
+    struct V {
+        float val[4];   // per block: squared distance (SE) or inner product (DOT)
+    };
+    struct Acc {};
+    __device__ static float get(const float4* rec, int k, int bf16)
+    {
+        if (bf16) return __uint_as_float(((unsigned)reinterpret_cast<const unsigned short*>(rec + 1)[k]) << 16);
+        return reinterpret_cast<const float*>(rec + 1)[k];
+    }
+    __device__ static void load_query(Q& q, const float4* rec, const FeatConst&) { q.rec = rec; }
+    __device__ static void zero(Acc&, float* sacc, const FeatConst& fc)
+    {
+        for (int k = 0; k < fc.D; ++k) sacc[32 * k] = 0.0f;
+    }
+    __device__ static float pair(const Q& q, const float4* rec, float& arg, V& c, const FeatConst& fc)
+    {
+        float mult = 1.0f;
+        for (int b = 0; b < fc.n_blocks; ++b) {
+            float acc = 0.0f;
+            for (int k = 0; k < fc.dim[b]; ++k) {
+                const float u = get(q.rec, fc.off[b] + k, fc.bf16);
+                const float v = get(rec, fc.off[b] + k, fc.bf16);
+                if (fc.kind[b] == 0) {
+                    const float d = u - v;
+                    acc = fmaf(d, d, acc);
+                } else {
+                    acc = fmaf(u, v, acc);
+                }
+            }
+            c.val[b] = acc;
+            if (fc.kind[b] == 0) arg = fmaf(acc, fc.s[b], arg);
+            else mult *= acc;
+        }
+        return mult;
+    }
+    __device__ static void accum(Acc&, const Q& q, const float4* rec, const V& c, float base, float w, float* sacc,
+                                 const FeatConst& fc)
+    {
+        for (int b = 0; b < fc.n_blocks; ++b) {
+            const int off = fc.off[b];
+            if (fc.kind[b] == 0) {
+                for (int k = 0; k < fc.dim[b]; ++k)
+                    sacc[32 * (off + k)] = fmaf(w, get(q.rec, off + k, fc.bf16) - get(rec, off + k, fc.bf16),
+                                                sacc[32 * (off + k)]);
+            } else {
+                float wb = base;
+                for (int b2 = 0; b2 < fc.n_blocks; ++b2)
+                    if (b2 != b && fc.kind[b2] == 1) wb *= c.val[b2];
+                for (int k = 0; k < fc.dim[b]; ++k)
+                    sacc[32 * (off + k)] = fmaf(wb, get(rec, off + k, fc.bf16), sacc[32 * (off + k)]);
+            }
+        }
+    }
+    __device__ static void write(const Acc&, const float* sacc, const GradArgs& g, float* out)
+    {
+        for (int b = 0; b < g.fc.n_blocks; ++b) {
+            const int off = g.fc.off[b];
+            const float sc = g.fc.kind[b] == 0 ? -g.scale_feat * g.inv_lb2[b] : g.scale_feat;
+            for (int k = 0; k < g.fc.dim[b]; ++k) out[off + k] = sc * sacc[32 * (off + k)];
+        }
+    }
+};
+
+template <class G>
+__global__ void __launch_bounds__(kSweepWarps * 32) k_grad(GradArgs g)
+{
+    extern __shared__ float4 stage_mem[];   // [kSweepWarps][2][32][rs], then (generic) [kSweepWarps][D][32] floats
+    __shared__ float cst[30];
+    const IterState* st = g.st;
+    if (threadIdx.x < 30) cst[threadIdx.x] = (&st->Ahi[0])[threadIdx.x];
+    __syncthreads();
+    const float* Ahi = cst;
+    const float* Alo = cst + 9;
+    const float* bhi = cst + 18;
+    const float* blo = cst + 21;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const LevelDesc L = g.levels[st->level];
+    const int rs = g.rs;
+    const bool dense = g.dense != 0;
+    const float sg = st->sg, rc = st->rc, rc2 = st->rc2;
+    const FeatConst& fc = g.fc;
+    float4* stage = stage_mem + (size_t)warp * 2 * 32 * rs;
+    float* sacc = nullptr;
+    if constexpr (G::kSharedAcc)
+        sacc = reinterpret_cast<float*>(stage_mem + (size_t)kSweepWarps * 2 * 32 * rs) + (size_t)warp * fc.D * 32 +
+               lane;
+
+    for (int gi = blockIdx.x * kSweepWarps + warp; gi < L.ngroups; gi += gridDim.x * kSweepWarps) {
+        const int2 grp = L.groups[gi];
+        const bool act = lane < grp.y;
+        const int qi = grp.x + (act ? lane : 0);
+        const float4* qrec = g.xrec + (size_t)qi * rs;
+        const float4 xq4 = qrec[0];
+        const float xq[3] = {xq4.x, xq4.y, xq4.z};
+        float xh[3], xl[3];
+        transform_df(xq, Ahi, Alo, bhi, blo, xh, xl);
+
+        typename G::Q qf;
+        G::load_query(qf, qrec, fc);
+        typename G::Acc fa;
+        G::zero(fa, sacc, fc);
+        float W = 0.0f, E0 = 0.0f, E1 = 0.0f, E2 = 0.0f, TQ = 0.0f;
+
+        Stream sm;
+        if (stream_setup(L, g.m, dense, act, xh, rc, lane, sm) && sm.total > 0) {
+            stream_walk(L, g.m, dense, sm, 0, sm.total, rs, stage, lane, [&](const float4* sb, int cnt) {
+#pragma unroll 1
+                for (int c = 0; c < cnt; ++c) {
+                    const float4* zr = sb + c * rs;
+                    const float4 z = zr[0];
+                    const float dx = __fsub_rn(__fsub_rn(z.x, xh[0]), xl[0]);
+                    const float dy = __fsub_rn(__fsub_rn(z.y, xh[1]), xl[1]);
+                    const float dz = __fsub_rn(__fsub_rn(z.z, xh[2]), xl[2]);
+                    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const bool in = act && (dense || d2 <= rc2);
+                    if (!__any_sync(kFull, in)) continue;
+                    float arg = d2 * sg;
+                    typename G::V cv;
+                    const float mult = G::pair(qf, zr, arg, cv, fc);
+                    const float base = in ? ex2(arg) : 0.0f;
+                    const float w = base * mult;
+                    W += w;
+                    E0 = fmaf(w, dx, E0);
+                    E1 = fmaf(w, dy, E1);
+                    E2 = fmaf(w, dz, E2);
+                    TQ = fmaf(w, d2, TQ);
+                    if (in) {
+                        G::accum(fa, qf, zr, cv, base, w, sacc, fc);
+                    }
+                }
+            });
+        }
+        if (act) {
+            const int idx = __float_as_int(xq4.w);
+            const float Ev[3] = {E0, E1, E2};
+            if (g.out_pos) {
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+                    g.out_pos[3 * (size_t)idx + r] =
+                        g.scale_pos *
+                        fmaf(g.Rout[3 * r], Ev[0], fmaf(g.Rout[3 * r + 1], Ev[1], g.Rout[3 * r + 2] * Ev[2]));
+            }
+            if (g.out_tq) g.out_tq[idx] = g.scale_ell * TQ;
+            if (g.out_feat) G::write(fa, sacc, g, g.out_feat + (size_t)idx * fc.D);
+        }
+        __syncwarp();
+    }
+}
+
+template <class G>
+cudaError_t grad_t(const GradArgs& g, int nblocks, cudaStream_t s)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_grad<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    size_t smem = (size_t)kSweepWarps * 2 * 32 * g.rs * sizeof(float4);
+    if (G::kSharedAcc) smem += (size_t)kSweepWarps * g.fc.D * 32 * sizeof(float);
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    k_grad<G><<<nblocks, kSweepWarps * 32, smem, s>>>(g);
+    return cudaGetLastError();
+}
+
 template <class Feat>
 cudaError_t info_t(int rs, SweepLaunch* out)
 {
@@ -554,6 +836,24 @@ cudaError_t sweep_launch_info(const FeatConst& f, int rs, SweepLaunch* out)
     if (f.n_blocks == 1 && f.kind[0] == 1 && f.dim[0] == 19)
         return f.bf16 ? info_t<FeatFixed<0, 19, true>>(rs, out) : info_t<FeatFixed<0, 19, false>>(rs, out);
     return info_t<FeatGeneric>(rs, out);
+}
+
+// Gradient sweep specialisation for the block list (the same families as the
+// sweep; any other block list takes the generic policy).
+cudaError_t launch_grad(const GradArgs& g, int nblocks, cudaStream_t s)
+{
+    const FeatConst& f = g.fc;
+    if (f.n_blocks == 0) return grad_t<GradNone>(g, nblocks, s);
+    const bool se3 = f.n_blocks >= 1 && f.kind[0] == 0 && f.dim[0] == 3;
+    if (f.n_blocks == 1 && se3)
+        return f.bf16 ? grad_t<GradFixed<3, 0, true>>(g, nblocks, s) : grad_t<GradFixed<3, 0, false>>(g, nblocks, s);
+    if (f.n_blocks == 2 && se3 && f.kind[1] == 1 && f.dim[1] == 19)
+        return f.bf16 ? grad_t<GradFixed<3, 19, true>>(g, nblocks, s)
+                      : grad_t<GradFixed<3, 19, false>>(g, nblocks, s);
+    if (f.n_blocks == 1 && f.kind[0] == 1 && f.dim[0] == 19)
+        return f.bf16 ? grad_t<GradFixed<0, 19, true>>(g, nblocks, s)
+                      : grad_t<GradFixed<0, 19, false>>(g, nblocks, s);
+    return grad_t<GradGeneric>(g, nblocks, s);
 }
 
 cudaError_t launch_sweep(const SweepArgs& a, int nblocks, cudaStream_t s)
