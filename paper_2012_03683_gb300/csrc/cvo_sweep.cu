@@ -141,10 +141,10 @@ struct FeatFixed {
             arg = fmaf(du2, fc.s[0], arg);
         }
         if constexpr (DDOT > 0) {
-            float dot = 0.0f;
+            float d4[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // four independent chains
 #pragma unroll
-            for (int k = 0; k < DDOT; ++k) dot = fmaf(q.v[DSE + k], v[DSE + k], dot);
-            return dot;
+            for (int k = 0; k < DDOT; ++k) d4[k & 3] = fmaf(q.v[DSE + k], v[DSE + k], d4[k & 3]);
+            return (d4[0] + d4[1]) + (d4[2] + d4[3]);
         }
         return 1.0f;
     }
@@ -334,31 +334,67 @@ struct Moments {
     float W, E0, E1, E2, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz;
 };
 
+// Offset e = z - x' (double-float query) and its squared length.
+struct Offset {
+    float dx, dy, dz, d2;
+};
+__device__ __forceinline__ Offset offset_to(const float4& z, const float xh[3], const float xl[3])
+{
+    Offset o;
+    o.dx = __fsub_rn(__fsub_rn(z.x, xh[0]), xl[0]);
+    o.dy = __fsub_rn(__fsub_rn(z.y, xh[1]), xl[1]);
+    o.dz = __fsub_rn(__fsub_rn(z.z, xh[2]), xl[2]);
+    o.d2 = fmaf(o.dx, o.dx, fmaf(o.dy, o.dy, o.dz * o.dz));
+    return o;
+}
+
+__device__ __forceinline__ void add_moments(Moments& mo, float w, const Offset& o)
+{
+    mo.W += w;
+    const float wx = w * o.dx, wy = w * o.dy, wz = w * o.dz;
+    mo.E0 += wx; mo.E1 += wy; mo.E2 += wz;
+    mo.Qxx = fmaf(wx, o.dx, mo.Qxx); mo.Qyy = fmaf(wy, o.dy, mo.Qyy); mo.Qzz = fmaf(wz, o.dz, mo.Qzz);
+    mo.Qxy = fmaf(wx, o.dy, mo.Qxy); mo.Qxz = fmaf(wx, o.dz, mo.Qxz); mo.Qyz = fmaf(wy, o.dz, mo.Qyz);
+}
+
 // Evaluates the cnt staged candidates of one batch for this lane's query.
+// Candidates go two at a time under one warp vote: the two evaluations are
+// independent chains (staged loads, feature products, ex2), which hides
+// latency at this kernel's occupancy; a pair with no lane in range is skipped.
 template <class Feat>
 __device__ __forceinline__ void eval_batch(const float4* sb, int cnt, int rs, const typename Feat::Q& qf,
                                            const float xh[3], const float xl[3], bool act, bool dense, float sg,
                                            float rc2, const FeatConst& fc, Moments& mo, unsigned& npairs)
 {
-#pragma unroll 2
-    for (int c = 0; c < cnt; ++c) {
+    int c = 0;
+    for (; c + 1 < cnt; c += 2) {
+        const float4* zr0 = sb + c * rs;
+        const float4* zr1 = zr0 + rs;
+        const Offset o0 = offset_to(zr0[0], xh, xl);
+        const Offset o1 = offset_to(zr1[0], xh, xl);
+        const bool in0 = act && (dense || o0.d2 <= rc2);
+        const bool in1 = act && (dense || o1.d2 <= rc2);
+        if (__any_sync(kFull, in0 || in1)) {
+            float a0 = o0.d2 * sg, a1 = o1.d2 * sg;
+            const float m0 = Feat::pair(qf, zr0, a0, fc);
+            const float m1 = Feat::pair(qf, zr1, a1, fc);
+            const float w0 = in0 ? ex2(a0) * m0 : 0.0f;
+            const float w1 = in1 ? ex2(a1) * m1 : 0.0f;
+            npairs += (in0 ? 1u : 0u) + (in1 ? 1u : 0u);
+            add_moments(mo, w0, o0);
+            add_moments(mo, w1, o1);
+        }
+    }
+    if (c < cnt) {
         const float4* zr = sb + c * rs;
-        const float4 z = zr[0];
-        const float dx = __fsub_rn(__fsub_rn(z.x, xh[0]), xl[0]);
-        const float dy = __fsub_rn(__fsub_rn(z.y, xh[1]), xl[1]);
-        const float dz = __fsub_rn(__fsub_rn(z.z, xh[2]), xl[2]);
-        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const bool in = act && (dense || d2 <= rc2);
+        const Offset o = offset_to(zr[0], xh, xl);
+        const bool in = act && (dense || o.d2 <= rc2);
         if (__any_sync(kFull, in)) {
-            float arg = d2 * sg;
+            float arg = o.d2 * sg;
             const float mult = Feat::pair(qf, zr, arg, fc);
             const float w = in ? ex2(arg) * mult : 0.0f;
             npairs += in ? 1u : 0u;
-            mo.W += w;
-            const float wx = w * dx, wy = w * dy, wz = w * dz;
-            mo.E0 += wx; mo.E1 += wy; mo.E2 += wz;
-            mo.Qxx = fmaf(wx, dx, mo.Qxx); mo.Qyy = fmaf(wy, dy, mo.Qyy); mo.Qzz = fmaf(wz, dz, mo.Qzz);
-            mo.Qxy = fmaf(wx, dy, mo.Qxy); mo.Qxz = fmaf(wx, dz, mo.Qxz); mo.Qyz = fmaf(wy, dz, mo.Qyz);
+            add_moments(mo, w, o);
         }
     }
 }
