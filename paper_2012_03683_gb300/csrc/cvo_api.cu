@@ -85,6 +85,7 @@ struct LevelHost {
     long long ncells;
     int shift;
     int ngroups;
+    int chunks;
 };
 
 constexpr long long kMaxCells = 1LL << 26;
@@ -314,7 +315,11 @@ void set_features(cvo_handle h, int rec_bf16)
 
 // Builds the grid levels of Z, the Morton-ordered queries of X and their groups
 // for lengthscales in [ell_lo, ell_hi].  Uses the handle's shared scratch.
-cvo_status prepare(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud* Z, double ell_hi, double ell_lo)
+// alone: the pair has the GPU to itself, so a level with few query groups
+// splits their streams into more chunks (work items) to fill the SMs; pairs
+// of a batch keep the default and share the grid.
+cvo_status prepare(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud* Z, double ell_hi, double ell_lo,
+                   bool alone = true)
 {
     const cvo_params& p = h->p;
     const int D = h->D;
@@ -449,7 +454,15 @@ cvo_status prepare(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud
     for (int k = 0; k < P.nlevels; ++k) {
         LevelHost& L = P.lv[k];
         L.ngroups = n > 0 ? (int)h->h_misc[16 + k] : 0;
-        max_items = std::max(max_items, L.ngroups * kChunks);
+        int chunks = kChunks;
+        if (alone && L.ngroups > 0) {
+            // about 8 work items per SM (measured best on a dense 2,000-point
+            // pair; levels with many groups keep the default)
+            const long long target = (long long)h->num_sms * 8;
+            chunks = (int)std::min<long long>(kMaxChunks, std::max<long long>(kChunks, (target + L.ngroups - 1) / L.ngroups));
+        }
+        L.chunks = chunks;
+        max_items = std::max(max_items, L.ngroups * chunks);
         LevelDesc& d = ld[k];
         d.h = (float)L.h;
         d.inv_h = (float)(1.0 / L.h);
@@ -459,7 +472,7 @@ cvo_status prepare(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud
         d.zrec = (const float4*)P.zrec[k].p;
         d.groups = (const int2*)P.groups[k].p;
         d.ngroups = L.ngroups;
-        d.pad_ = 0;
+        d.chunks = L.chunks;
     }
     P.max_items = max_items;
     CVO_CUDA(ensure(P.levels_dev, sizeof(ld)));
@@ -824,7 +837,7 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
     const double ell_lo = reachable_ell_lo(p);
     long long work = 0;
     for (int i = 0; i < nl; ++i) {
-        CVO_TRY(prepare(h, h->pr[i], X + live[i], Z + live[i], p.ell, ell_lo));
+        CVO_TRY(prepare(h, h->pr[i], X + live[i], Z + live[i], p.ell, ell_lo, false));
         CVO_TRY(init_state(h, h->pr[i], i, T_init + 16 * live[i], p.ell, 1));
         work += h->pr[i].max_items;
     }

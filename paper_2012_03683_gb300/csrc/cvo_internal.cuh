@@ -29,7 +29,8 @@ namespace cvo {
 constexpr int kStatN = 43;       // linear statistics of the per-query moments
 constexpr int kSweepWarps = 4;   // warps per sweep block
 constexpr int kMaxLevels = 24;   // grid levels of one registration
-constexpr int kChunks = 8;       // chunks a group's candidate stream splits into
+constexpr int kChunks = 8;       // default chunks a group's candidate stream splits into
+constexpr int kMaxChunks = 64;   // upper limit of a level's chunk count
 constexpr int kChunkMin = 64;    // shortest chunk worth a work item
 constexpr int kFinalizeThreads = 64;
 constexpr int kGroupBlocks = 32;   // sweep blocks per reduction group (the group's last block sums them)
@@ -56,7 +57,7 @@ struct LevelDesc {
     const float4* zrec;      // M records sorted by cell
     const int2* groups;      // query groups (first, count)
     int ngroups;
-    int pad_;
+    int chunks;              // work items per query group (its stream is split into up to this many)
 };
 
 // Feature-kernel constants (exponent in log2 units).

@@ -312,8 +312,9 @@ extern "C" cvo_status cvo_evaluate_dense_noalloc(const cvo_params* p, void* cuda
     ld.zrec = zrec;
     ld.groups = groups;
     ld.ngroups = (n + 31) / 32;
+    ld.chunks = kChunks;
 
-    const int items = ld.ngroups * kChunks;
+    const int items = ld.ngroups * ld.chunks;
     const int nblocks = std::max(1, std::min((items + kSweepWarps - 1) / kSweepWarps, kNoAllocBlocks));
     PairDesc pd;
     pd.levels = lv;

@@ -439,11 +439,11 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
     float4* stage = stage_mem + (size_t)warp * 2 * 32 * rs;
     unsigned npairs = 0, ncand = 0;
 
-    const int nitems = L.ngroups * kChunks;
+    const int nitems = L.ngroups * L.chunks;
     const int nblk = P.b1 - P.b0, bloc = (int)blockIdx.x - P.b0;
     for (int item = bloc * kSweepWarps + warp; item < nitems; item += nblk * kSweepWarps) {
-        const int g = item / kChunks;
-        const int k = item - g * kChunks;
+        const int g = item / L.chunks;
+        const int k = item - g * L.chunks;
         const int2 grp = L.groups[g];
         const bool act = lane < grp.y;
         const int qi = grp.x + (act ? lane : 0);
@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
         if (!stream_setup(L, P.m, dense, act, xh, rc, lane, sm)) continue;
         const int total = sm.total;
         if (total == 0) continue;
-        const int nch = min(kChunks, (total + kChunkMin - 1) / kChunkMin);
+        const int nch = min(L.chunks, (total + kChunkMin - 1) / kChunkMin);
         if (k >= nch) continue;
         const int clo_ = (int)(((long long)total * k) / nch);
         const int chi_ = (int)(((long long)total * (k + 1)) / nch);
