@@ -205,6 +205,19 @@ cvo_status cvo_register_pair(cvo_handle h, const cvo_cloud* X, const cvo_cloud* 
 cvo_status cvo_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, const cvo_cloud* Z,
                               const double* T_init, double* T_out, cvo_info* infos);
 
+/* Frame-to-frame odometry (Sec. IV and V-A): registers frame k+1 onto frame
+ * k for k = 0 .. nframes - 2.  The first registration starts from T_first
+ * (NULL: identity) with lengthscale ell_first (the paper starts the first
+ * frame of a sequence at a larger lengthscale); every later one starts from
+ * the previous relative estimate with params.ell, the other parameters as
+ * set on the handle.  T_rel (nframes - 1 poses of 16 doubles) receives the
+ * motion mapping frame k+1 into frame k; T_abs (nullable, nframes poses)
+ * the poses of every frame in frame 0 (T_abs[0] = I, T_abs[k+1] =
+ * T_abs[k] T_rel[k]); infos (nullable, nframes - 1) the registrations'
+ * summaries.  Returns the worst status (an error stops the sequence). */
+cvo_status cvo_register_sequence(cvo_handle h, int nframes, const cvo_cloud* frames, double ell_first,
+                                 const double T_first[16], double* T_rel, double* T_abs, cvo_info* infos);
+
 /* Copies the per-iteration trace of the handle's last registration into out
  * (capacity cap iterations, CVO_TRACE_STRIDE doubles each: l, F, i_theta,
  * |g|, F'' along g, t, |t omega|, |t v|, decayed (0/1), pairs, then the first

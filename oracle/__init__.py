@@ -257,3 +257,21 @@ def backward(X, Z, T, *, FX=None, FZ=None, blocks=(), ell, cutoff_mult=0.0, sigm
     if rc != 0:
         raise ValueError("orc_backward: invalid argument")
     return dict(dX=dX, dZ=dZ, dFX=dFX, dFZ=dFZ, dell=dell.value)
+
+
+def register_sequence(frames, ell_first, T_first=None, *, ell, **kw):
+    """Frame-to-frame odometry (Sec. IV, V-A) with the oracle's registration:
+    frame k+1 onto frame k, the first pair from T_first (identity) at
+    lengthscale ell_first, each later pair from the previous relative motion
+    at ell.  Returns (T_rel list, T_abs list, infos)."""
+    T_rel, infos = [], []
+    T_abs = [np.eye(4)]
+    for k in range(len(frames) - 1):
+        (X, FX), (Z, FZ) = frames[k], frames[k + 1]
+        init = (np.eye(4) if T_first is None else np.asarray(T_first, np.float64)) if k == 0 else T_rel[-1]
+        l0 = ell_first if k == 0 else ell
+        T, info, _ = register(X, Z, init, FX=FX, FZ=FZ, ell=l0, **kw)
+        T_rel.append(T)
+        infos.append(info)
+        T_abs.append(T_abs[-1] @ T)
+    return T_rel, T_abs, infos

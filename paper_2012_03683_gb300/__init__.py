@@ -26,7 +26,8 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["CVO", "cvo_create", "cvo_destroy", "cvo_set_params", "cvo_inner_product", "cvo_gradient", "cvo_metric",
-           "cvo_evaluate", "cvo_backward", "cvo_cosine", "CVOInnerProduct", "inner_product_fn", "metric_fn", "cvo_register_pair", "cvo_register_batch", "cvo_get_trace", "cvo_set_timing",
+           "cvo_evaluate", "cvo_backward", "cvo_cosine", "CVOInnerProduct", "inner_product_fn", "metric_fn",
+           "cvo_register_pair", "cvo_register_batch", "cvo_register_sequence", "cvo_get_trace", "cvo_set_timing",
            "cvo_sweep_time", "cvo_last_error", "cvo_version", "cvo_kernel_launches", "load_library", "Status",
            "CvoError"]
 
@@ -111,13 +112,14 @@ def load_library(build_if_missing: bool = True):
     lib.cvo_register_pair.argtypes = [vp, P(Cloud), P(Cloud), vp, vp, P(Info)]
     lib.cvo_register_batch.argtypes = [vp, ctypes.c_int, P(Cloud), P(Cloud), vp, vp, P(Info)]
     lib.cvo_get_trace.argtypes = [vp, vp, ctypes.c_int]
+    lib.cvo_register_sequence.argtypes = [vp, ctypes.c_int, P(Cloud), ctypes.c_double, vp, vp, vp, P(Info)]
     lib.cvo_set_timing.argtypes = [vp, ctypes.c_int]
     lib.cvo_set_tuning.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     lib.cvo_set_tuning.restype = ctypes.c_int
     lib.cvo_sweep_time.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int)]
     for name in ("cvo_create", "cvo_destroy", "cvo_set_params", "cvo_inner_product", "cvo_metric", "cvo_gradient",
-                 "cvo_evaluate", "cvo_backward", "cvo_cosine", "cvo_register_pair", "cvo_register_batch", "cvo_get_trace", "cvo_set_timing",
-                 "cvo_sweep_time"):
+                 "cvo_evaluate", "cvo_backward", "cvo_cosine", "cvo_register_pair", "cvo_register_sequence",
+                 "cvo_register_batch", "cvo_get_trace", "cvo_set_timing", "cvo_sweep_time"):
         getattr(lib, name).restype = ctypes.c_int
     lib.cvo_last_error.restype = ctypes.c_char_p
     lib.cvo_last_error.argtypes = []
@@ -382,6 +384,23 @@ def cvo_register_batch(h, pairs):
     return Tout[:n], [infos[k].as_dict() for k in range(n)], rc
 
 
+def cvo_register_sequence(h, frames, ell_first, T_first=None):
+    """frames: sequence of (xyz, features) per frame.  Returns (T_rel
+    (nframes-1, 4, 4), T_abs (nframes, 4, 4), infos, rc)."""
+    keep = []
+    n = len(frames)
+    C = (Cloud * max(n, 1))()
+    for k, (P, F) in enumerate(frames):
+        C[k] = _as_cloud(P, F, keep)
+    T_rel = np.zeros((max(n - 1, 1), 4, 4))
+    T_abs = np.zeros((max(n, 1), 4, 4))
+    infos = (Info * max(n - 1, 1))()
+    T0 = None if T_first is None else _pose(T_first)
+    rc = _check(load_library().cvo_register_sequence(h, n, C, float(ell_first), None if T0 is None else T0.ctypes.data,
+                                                     T_rel.ctypes.data, T_abs.ctypes.data, infos))
+    return T_rel[: max(n - 1, 0)], T_abs[:n], [infos[k].as_dict() for k in range(max(n - 1, 0))], rc
+
+
 def cvo_get_trace(h, cap=100000) -> np.ndarray:
     out = np.zeros((max(cap, 1), TRACE_STRIDE))
     n = _check(load_library().cvo_get_trace(h, out.ctypes.data, cap))
@@ -454,6 +473,9 @@ class CVO:
 
     def register_batch(self, pairs):
         return cvo_register_batch(self.h, pairs)
+
+    def register_sequence(self, frames, ell_first, T_first=None):
+        return cvo_register_sequence(self.h, frames, ell_first, T_first)
 
     def trace(self):
         return cvo_get_trace(self.h)

@@ -1226,6 +1226,54 @@ cvo_status cvo_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
     return run_register_batch(h, npairs, X, Z, T_init, T_out, infos);
 }
 
+cvo_status cvo_register_sequence(cvo_handle h, int nframes, const cvo_cloud* frames, double ell_first,
+                                 const double T_first[16], double* T_rel, double* T_abs, cvo_info* infos)
+{
+    g_err.clear();
+    if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
+    if (nframes < 0) return fail(CVO_ERR_INVALID_ARG, "nframes < 0");
+    if (nframes > 0 && !frames) return fail(CVO_ERR_INVALID_ARG, "frames is NULL");
+    if (nframes > 1 && !T_rel) return fail(CVO_ERR_INVALID_ARG, "T_rel is NULL");
+    if (!(ell_first > 0.0) || !std::isfinite(ell_first)) return fail(CVO_ERR_INVALID_ARG, "ell_first must be > 0");
+    const cvo_params base = h->p;
+    if (base.anneal && ell_first < base.ell_min)
+        return fail(CVO_ERR_INVALID_ARG, "ell_first must be >= ell_min when annealing");
+    const int D = feat_dim(base);
+    for (int k = 0; k < nframes; ++k) CVO_TRY(check_cloud(frames + k, "frames[k]", D));
+    static const double I[16] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1};
+    if (T_first) CVO_TRY(check_pose(T_first, "T_first"));
+    DeviceGuard g(h->device);
+    if (T_abs && nframes > 0) std::memcpy(T_abs, I, sizeof(I));
+    cvo_status worst = CVO_OK;
+    for (int k = 0; k + 1 < nframes; ++k) {
+        // the first pair has no prior: start from T_first with the larger
+        // lengthscale; every later pair starts from the previous relative
+        // motion (constant velocity) with params.ell
+        h->p = base;
+        if (k == 0) h->p.ell = ell_first;
+        const double* init = (k == 0) ? (T_first ? T_first : I) : T_rel + 16 * (k - 1);
+        cvo_info inf;
+        const cvo_status s = run_register(h, frames + k, frames + k + 1, init, T_rel + 16 * k, &inf);
+        h->p = base;
+        if (s < 0) return s;
+        if (s == CVO_NOT_CONVERGED) worst = CVO_NOT_CONVERGED;
+        if (infos) infos[k] = inf;
+        if (T_abs) {
+            // T_abs[k+1] = T_abs[k] T_rel[k] (maps frame k+1 into frame 0)
+            const double* A = T_abs + 16 * k;
+            const double* B = T_rel + 16 * k;
+            double* C = T_abs + 16 * (k + 1);
+            for (int r = 0; r < 4; ++r)
+                for (int c = 0; c < 4; ++c) {
+                    double acc = 0.0;
+                    for (int q = 0; q < 4; ++q) acc += A[4 * r + q] * B[4 * q + c];
+                    C[4 * r + c] = acc;
+                }
+        }
+    }
+    return worst;
+}
+
 int cvo_get_trace(cvo_handle h, double* out, int cap)
 {
     if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");

@@ -302,6 +302,32 @@ def street_pair(n=20000, seed=SEED_BASE + 2, max_angle_deg=10.0, max_trans=0.5) 
                 name="street-20k")
 
 
+def street_sequence(n_frames=6, n=10000, seed=SEED_BASE + 6, step=0.8, max_yaw_deg=2.0):
+    """Odometry sequence in the street world: a camera 1.6 m above the ground
+    drives forward along +z about ``step`` m per frame (10 Hz at ~8 m/s, as a
+    KITTI sequence) with a random yaw of at most ``max_yaw_deg`` per frame and
+    small pitch/roll/height jitter; every frame is an independent ray cast of
+    ``n`` points with RGB + 19-class labels, as in street_pair.  Returns
+    (frames, C): frames a list of (xyz float32 (n, 3), features float32
+    (n, 22)) in each camera's frame, C the world-from-camera poses; the true
+    relative motion of frame k+1 into frame k is inverse(C[k]) @ C[k+1]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    boxes, base = _street_world(rng)
+    C = [rigid(np.eye(3), np.array([0.0, 1.6, 0.0]))]
+    for _ in range(n_frames - 1):
+        yaw = math.radians(rng.uniform(-max_yaw_deg, max_yaw_deg))
+        jit = quat_rotation(rng.normal(size=3), math.radians(rng.uniform(0.0, 0.3)))
+        R = quat_rotation([0.0, 1.0, 0.0], yaw) @ jit
+        t = np.array([rng.normal(0.0, 0.02), rng.normal(0.0, 0.01), step * rng.uniform(0.9, 1.1)])
+        C.append(C[-1] @ rigid(R, t))
+    frames = []
+    for Ck in C:
+        P, rgb, cl = _stereo_view(rng, Ck, boxes, base, n)
+        F = np.concatenate([rgb, label_distribution(rng, cl)], axis=1).astype(np.float32)
+        frames.append((P.astype(np.float32), F))
+    return frames, C
+
+
 # ---------------------------------------------------------------------------
 # workload 3: RGB-D-like room
 # ---------------------------------------------------------------------------

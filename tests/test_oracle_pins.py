@@ -479,3 +479,21 @@ def test_backward_translation_invariance():
     g = oracle.backward(X, Z, T, FX=FX, FZ=FZ, blocks=BLOCKS, ell=0.4, cutoff_mult=2.5)
     total = g["dX"].sum(0) + g["dZ"].sum(0) @ T[:3, :3].T
     assert np.abs(total).max() < 1e-10 * max(1.0, np.abs(g["dX"]).max())
+
+
+def test_sequence_recovers_exact_motions():
+    """Odometry chaining (Sec. V-A): frames that are exact rigid copies of one
+    cloud; each registration recovers the true relative motion (dense F is
+    maximal there, Cauchy-Schwarz) and the absolute poses are their products."""
+    r = rng(40)
+    W = r.uniform(-1.0, 1.0, size=(250, 3))
+    C = [np.eye(4)]
+    for _ in range(3):
+        C.append(C[-1] @ rand_T(r, 0.05, 0.05))
+    frames = [(transform(np.linalg.inv(Ck), W), None) for Ck in C]
+    T_rel, T_abs, infos = oracle.register_sequence(frames, 0.3, ell=0.3, max_iters=300)
+    for k in range(3):
+        truth = np.linalg.inv(C[k]) @ C[k + 1]
+        assert np.abs(T_rel[k] - truth).max() < 1e-5
+        assert np.abs(T_abs[k + 1] - C[k + 1]).max() < 1e-5
+        assert infos[k]["status"] == 0
