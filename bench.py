@@ -177,6 +177,9 @@ def batch_section(cvo, torch, dev, flush, reps=2):
                        f"l = {pr['ell']}, cutoff 3 l, {pr['max_iters']} iterations",
            "pairs": len(pairs), "points": int(sum(p.n + p.m for p in pairs))}
     with cvo.CVO(**kw) as h:
+        # cell size and query-group extent tuned on the largest pair (untimed)
+        big = max(range(len(pairs)), key=lambda k: pairs[k].n + pairs[k].m)
+        out["tuning"] = h.autotune(*args[big])
         h.register_batch(args)
         torch.cuda.synchronize()
         t_b, evals_b = 0.0, 0
@@ -315,6 +318,8 @@ def main():
     FX = torch.tensor(p.FX, device=dev)
     FZ = torch.tensor(p.FZ, device=dev)
     h = cvo.CVO(**kw)
+    # sweep tuning for this pair at its start (untimed, before the warm-up)
+    tuning = h.autotune(X, Z, np.eye(4), FX, FZ)
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     T0 = np.eye(4)
@@ -416,6 +421,7 @@ def main():
         "e2e": {"value": e2e_pairs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "tuning": tuning,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None,
                      "traffic": traffic, "kernel": "k_sweep (fused neighbour sweep)",

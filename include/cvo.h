@@ -231,6 +231,36 @@ int cvo_get_trace(cvo_handle h, double* out, int cap);
  * 2^super_delta cutoff radii wide (-2..6).  Defaults 0.5 and 2. */
 cvo_status cvo_set_tuning(cvo_handle h, double cell_factor, int super_delta);
 
+/* Tuning of the neighbour sweep: grid cell edge (cell_factor x cutoff
+ * radius), query-group extent (Morton super-cells about 2^super_delta
+ * cutoff radii wide) and work split (a single pair whose grid level has few
+ * query groups splits each group's candidate stream into chunks until about
+ * items_per_sm work items per SM exist, so that up to that many lanes of
+ * different warps serve one query).  sweep_ms: the measured sweep time of
+ * the tuning (cvo_autotune), else 0. */
+typedef struct {
+    double cell_factor;
+    int super_delta;
+    int items_per_sm;
+    double sweep_ms;
+} cvo_tuning;
+
+/* Autotuner: prepares the pair (X, Z) under each tuning of a small grid
+ * (cell_factor 0.35 / 0.5 / 0.7 / 1.0, super_delta 1 / 2 / 3, items_per_sm
+ * 4 / 8 / 16 / 32; with cutoff_mult <= 0 only the work split, the others
+ * staying as they are), times its
+ * sweep at pose T and lengthscale params.ell with CUDA events (best of 3),
+ * keeps the fastest on the handle and returns it in *out.  Results do not
+ * depend on the tuning beyond rounding; every tuning's F is checked against
+ * the first (CVO_ERR_CUDA if they differ by more than 1e-4 relative).  Costs
+ * one setup and four sweeps per tuning (tens of milliseconds). */
+cvo_status cvo_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], cvo_tuning* out);
+
+/* The handle's current tuning (sweep_ms = 0), and setting it (validated as
+ * cvo_set_tuning, items_per_sm in [1, 256]). */
+cvo_status cvo_get_tuning(cvo_handle h, cvo_tuning* out);
+cvo_status cvo_apply_tuning(cvo_handle h, const cvo_tuning* t);
+
 /* Average device time (ms) of the sweep kernel over the handle's last
  * registration, measured with CUDA events around each sweep launch when
  * timing is on (cvo_set_timing), and the number of sweep launches timed. */

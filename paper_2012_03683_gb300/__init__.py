@@ -28,6 +28,7 @@ from . import build as _build
 __all__ = ["CVO", "cvo_create", "cvo_destroy", "cvo_set_params", "cvo_inner_product", "cvo_gradient", "cvo_metric",
            "cvo_evaluate", "cvo_backward", "cvo_cosine", "CVOInnerProduct", "inner_product_fn", "metric_fn",
            "cvo_register_pair", "cvo_register_batch", "cvo_register_sequence", "cvo_get_trace", "cvo_set_timing",
+           "cvo_autotune", "cvo_get_tuning", "cvo_apply_tuning",
            "cvo_sweep_time", "cvo_last_error", "cvo_version", "cvo_kernel_launches", "load_library", "Status",
            "CvoError"]
 
@@ -78,6 +79,14 @@ class Info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("cell_factor", ctypes.c_double), ("super_delta", ctypes.c_int), ("items_per_sm", ctypes.c_int),
+                ("sweep_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Eval(ctypes.Structure):
     _fields_ = [("F", ctypes.c_double), ("grad", ctypes.c_double * 6), ("hess", ctypes.c_double * 36),
                 ("i_theta", ctypes.c_double), ("pairs", ctypes.c_longlong), ("candidates", ctypes.c_longlong)]
@@ -117,9 +126,13 @@ def load_library(build_if_missing: bool = True):
     lib.cvo_set_tuning.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     lib.cvo_set_tuning.restype = ctypes.c_int
     lib.cvo_sweep_time.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int)]
+    lib.cvo_autotune.argtypes = [vp, P(Cloud), P(Cloud), vp, P(Tuning)]
+    lib.cvo_get_tuning.argtypes = [vp, P(Tuning)]
+    lib.cvo_apply_tuning.argtypes = [vp, P(Tuning)]
     for name in ("cvo_create", "cvo_destroy", "cvo_set_params", "cvo_inner_product", "cvo_metric", "cvo_gradient",
                  "cvo_evaluate", "cvo_backward", "cvo_cosine", "cvo_register_pair", "cvo_register_sequence",
-                 "cvo_register_batch", "cvo_get_trace", "cvo_set_timing", "cvo_sweep_time"):
+                 "cvo_register_batch", "cvo_get_trace", "cvo_set_timing", "cvo_sweep_time", "cvo_autotune",
+                 "cvo_get_tuning", "cvo_apply_tuning"):
         getattr(lib, name).restype = ctypes.c_int
     lib.cvo_last_error.restype = ctypes.c_char_p
     lib.cvo_last_error.argtypes = []
@@ -415,6 +428,27 @@ def cvo_set_tuning(h, cell_factor=0.5, super_delta=2):
     return _check(load_library().cvo_set_tuning(h, float(cell_factor), int(super_delta)))
 
 
+def cvo_autotune(h, X, Z, T, FX=None, FZ=None) -> dict:
+    """Times the sweep of (X, Z) at pose T under a grid of tunings and keeps
+    the fastest on the handle (see cvo_autotune in cvo.h)."""
+    cx, cz, keep = _clouds(X, Z, FX, FZ)
+    Tm = _pose(T)
+    out = Tuning()
+    _check(load_library().cvo_autotune(h, ctypes.byref(cx), ctypes.byref(cz), Tm.ctypes.data, ctypes.byref(out)))
+    return out.as_dict()
+
+
+def cvo_get_tuning(h) -> dict:
+    out = Tuning()
+    _check(load_library().cvo_get_tuning(h, ctypes.byref(out)))
+    return out.as_dict()
+
+
+def cvo_apply_tuning(h, cell_factor, super_delta, items_per_sm):
+    t = Tuning(float(cell_factor), int(super_delta), int(items_per_sm), 0.0)
+    return _check(load_library().cvo_apply_tuning(h, ctypes.byref(t)))
+
+
 def cvo_sweep_time(h):
     ms = ctypes.c_double()
     n = ctypes.c_int()
@@ -479,6 +513,15 @@ class CVO:
 
     def trace(self):
         return cvo_get_trace(self.h)
+
+    def autotune(self, X, Z, T=None, FX=None, FZ=None):
+        return cvo_autotune(self.h, X, Z, np.eye(4) if T is None else T, FX, FZ)
+
+    def tuning(self):
+        return cvo_get_tuning(self.h)
+
+    def apply_tuning(self, cell_factor, super_delta, items_per_sm):
+        return cvo_apply_tuning(self.h, cell_factor, super_delta, items_per_sm)
 
 
 # ---- differentiable form ---------------------------------------------------------

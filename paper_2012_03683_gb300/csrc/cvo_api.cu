@@ -158,6 +158,12 @@ struct cvo_handle_s {
     // Morton super-cells about 2^super_delta cutoff radii wide
     double cell_factor = 0.5;
     int super_delta = 2;
+    // work split: a single pair whose level has few query groups splits each
+    // group's stream into chunks (work items) until about items_per_sm items
+    // per SM exist, i.e. up to that many lanes share one query's candidates;
+    // a batch uses batch_chunks per group
+    int items_per_sm = 8;
+    int batch_chunks = kChunks;
 };
 
 namespace {
@@ -454,11 +460,12 @@ cvo_status prepare(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud
     for (int k = 0; k < P.nlevels; ++k) {
         LevelHost& L = P.lv[k];
         L.ngroups = n > 0 ? (int)h->h_misc[16 + k] : 0;
-        int chunks = kChunks;
+        int chunks = alone ? kChunks : h->batch_chunks;
         if (alone && L.ngroups > 0) {
-            // about 8 work items per SM (measured best on a dense 2,000-point
-            // pair; levels with many groups keep the default)
-            const long long target = (long long)h->num_sms * 8;
+            // about items_per_sm work items per SM (8 by default, measured best
+            // on a dense 2,000-point pair); levels with many groups keep the
+            // default split
+            const long long target = (long long)h->num_sms * h->items_per_sm;
             chunks = (int)std::min<long long>(kMaxChunks, std::max<long long>(kChunks, (target + L.ngroups - 1) / L.ngroups));
         }
         L.chunks = chunks;
@@ -1006,6 +1013,97 @@ cvo_status run_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     return CVO_OK;
 }
 
+// Times the sweep of one prepared pair at pose T (eval mode): the best of
+// `reps` launches, CUDA events on the handle's stream.
+cvo_status time_sweep(cvo_handle h, PairRes& P, const double* T, int reps, double* ms, double* F)
+{
+    CVO_TRY(init_state(h, P, 0, T, h->p.ell, 0));
+    const int nb = single_pair_blocks(h, P);
+    SweepArgs a;
+    CVO_TRY(setup_sweep(h, std::vector<PairDesc>{pair_desc(P, 0, nb)}, nb, &a, true));
+    ensure_events(h, 1);
+    if (h->evs.size() < 2) return fail(CVO_ERR_CUDA, "cudaEventCreate failed");
+    // the sweep leaves the state alone (the finalize would mark an
+    // evaluation done), so it is launched reps + 1 times and finalized once
+    double best = 1e30;
+    for (int r = 0; r <= reps; ++r) {   // the first launch warms up
+        CVO_CUDA(cudaEventRecord(h->evs[0], h->s));
+        CVO_CUDA(launch_sweep(a, nb, h->s));
+        CVO_CUDA(cudaEventRecord(h->evs[1], h->s));
+        CVO_CUDA(cudaEventSynchronize(h->evs[1]));
+        float t = 0.0f;
+        CVO_CUDA(cudaEventElapsedTime(&t, h->evs[0], h->evs[1]));
+        if (r > 0) best = std::min(best, (double)t);
+    }
+    CVO_CUDA(launch_finalize((IterState*)P.state.p, a.grp_stats, a.grp_cnt, nb, nullptr, h->s));
+    CVO_TRY(fetch_states(h, 1));
+    *ms = best;
+    *F = h->h_state->F;
+    return CVO_OK;
+}
+
+// Autotuner: every (cell_factor, super_delta, items_per_sm) of a small grid
+// is prepared and its sweep timed on the caller's pair; the fastest is kept.
+// The results must not depend on the tuning beyond rounding: F of every
+// candidate is checked against the first one.
+cvo_status run_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double* T, cvo_tuning* out)
+{
+    static const double kCell[] = {0.35, 0.5, 0.7, 1.0};
+    static const int kSuper[] = {1, 2, 3};
+    static const int kItems[] = {4, 8, 16, 32};
+    const double cf0 = h->cell_factor;
+    const int sd0 = h->super_delta, ip0 = h->items_per_sm;
+    cvo_tuning best{cf0, sd0, ip0, 1e30};
+    std::memset(out, 0, sizeof(*out));
+    if (X->n == 0 || Z->n == 0) {
+        *out = cvo_tuning{cf0, sd0, ip0, 0.0};
+        return CVO_OK;
+    }
+    CVO_TRY(begin_call(h, rec_bf16_of(h->p, X, Z), 1));
+    PairRes& P = h->pr[0];
+    double F_ref = 0.0;
+    bool have_ref = false;
+    cvo_status st = CVO_OK;
+    // the dense sum has no grid and no super-cells: only the work split is tuned
+    const std::vector<double> cells = h->dense ? std::vector<double>{cf0} : std::vector<double>(kCell, kCell + 4);
+    const std::vector<int> supers = h->dense ? std::vector<int>{sd0} : std::vector<int>(kSuper, kSuper + 3);
+    for (double cf : cells) {
+        for (int sd : supers) {
+            for (int ip : kItems) {
+                h->cell_factor = cf;
+                h->super_delta = sd;
+                h->items_per_sm = ip;
+                st = prepare(h, P, X, Z, h->p.ell, h->p.ell);
+                if (st < 0) break;
+                double ms = 0.0, F = 0.0;
+                st = time_sweep(h, P, T, 3, &ms, &F);
+                if (st < 0) break;
+                if (!have_ref) {
+                    F_ref = F;
+                    have_ref = true;
+                } else if (std::fabs(F - F_ref) > 1e-4 * std::fabs(F_ref) + 1e-300) {
+                    st = fail(CVO_ERR_CUDA, "autotune: F differs between tunings (%g vs %g)", F, F_ref);
+                    break;
+                }
+                if (ms < best.sweep_ms) best = cvo_tuning{cf, sd, ip, ms};
+            }
+            if (st < 0) break;
+        }
+        if (st < 0) break;
+    }
+    if (st < 0) {
+        h->cell_factor = cf0;
+        h->super_delta = sd0;
+        h->items_per_sm = ip0;
+        return st;
+    }
+    h->cell_factor = best.cell_factor;
+    h->super_delta = best.super_delta;
+    h->items_per_sm = best.items_per_sm;
+    *out = best;
+    return CVO_OK;
+}
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev)
@@ -1295,6 +1393,35 @@ cvo_status cvo_set_tuning(cvo_handle h, double cell_factor, int super_delta)
     if (super_delta < -2 || super_delta > 6) return fail(CVO_ERR_INVALID_ARG, "super_delta must be in [-2, 6]");
     h->cell_factor = cell_factor;
     h->super_delta = super_delta;
+    return CVO_OK;
+}
+
+cvo_status cvo_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], cvo_tuning* out)
+{
+    g_err.clear();
+    if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
+    if (!out) return fail(CVO_ERR_INVALID_ARG, "out is NULL");
+    const int D = feat_dim(h->p);
+    CVO_TRY(check_cloud(X, "X", D));
+    CVO_TRY(check_cloud(Z, "Z", D));
+    CVO_TRY(check_pose(T, "T"));
+    DeviceGuard g(h->device);
+    return run_autotune(h, X, Z, T, out);
+}
+
+cvo_status cvo_get_tuning(cvo_handle h, cvo_tuning* out)
+{
+    if (!h || !out) return fail(CVO_ERR_INVALID_ARG, "NULL argument");
+    *out = cvo_tuning{h->cell_factor, h->super_delta, h->items_per_sm, 0.0};
+    return CVO_OK;
+}
+
+cvo_status cvo_apply_tuning(cvo_handle h, const cvo_tuning* t)
+{
+    if (!h || !t) return fail(CVO_ERR_INVALID_ARG, "NULL argument");
+    if (t->items_per_sm < 1 || t->items_per_sm > 256) return fail(CVO_ERR_INVALID_ARG, "items_per_sm must be in [1, 256]");
+    CVO_TRY(cvo_set_tuning(h, t->cell_factor, t->super_delta));
+    h->items_per_sm = t->items_per_sm;
     return CVO_OK;
 }
 

@@ -1,0 +1,69 @@
+"""The sweep autotuner (cvo_autotune): it picks a tuning from its grid, the
+tuning sticks to the handle, and results under the chosen tuning keep the
+oracle parity of the default one (F relative 1e-5, gradient 1e-4 of |g|)."""
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+torch = pytest.importorskip("torch")
+import paper_2012_03683_gb300 as cvo  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a)).to("cuda")
+
+
+def check_parity(h, X, Z, FX, FZ, T, kw):
+    got = h.evaluate(dev(X), dev(Z), T, dev(FX), dev(FZ))
+    ref = oracle.evaluate(X, Z, T, FX=FX, FZ=FZ, **kw)
+    assert got["F"] == pytest.approx(ref["F"], rel=1e-5)
+    gtol = 1e-4 * np.linalg.norm(ref["g"]) + 1e-7 * ref["gscale"]
+    assert np.abs(got["grad"] - ref["g"]).max() <= gtol
+
+
+def test_autotune_street_slice():
+    p = scenes.street_pair()
+    r = np.random.Generator(np.random.PCG64(3))
+    ix = r.permutation(len(p.X))[:6000]
+    iz = r.permutation(len(p.Z))[:6000]
+    X, Z, FX, FZ = p.X[ix], p.Z[iz], p.FX[ix], p.FZ[iz]
+    kw = dict(blocks=p.blocks, ell=0.2, cutoff_mult=3.0)
+    h = cvo.CVO(**kw)
+    assert h.tuning()["cell_factor"] == 0.5 and h.tuning()["super_delta"] == 2
+    t = h.autotune(dev(X), dev(Z), p.T_true, dev(FX), dev(FZ))
+    assert t["cell_factor"] in (0.35, 0.5, 0.7, 1.0) and t["super_delta"] in (1, 2, 3)
+    assert t["items_per_sm"] in (4, 8, 16, 32) and t["sweep_ms"] > 0.0
+    # the timed sweep did the work: no faster than the pairs it evaluates allow
+    # (6,000 x 6,000 points at l = 0.2 take tens of microseconds)
+    ev = h.evaluate(dev(X), dev(Z), p.T_true, dev(FX), dev(FZ))
+    assert ev["pairs"] > 1e5 and t["sweep_ms"] > 0.01
+    cur = h.tuning()
+    assert (cur["cell_factor"], cur["super_delta"], cur["items_per_sm"]) == \
+        (t["cell_factor"], t["super_delta"], t["items_per_sm"])
+    check_parity(h, X, Z, FX, FZ, p.T_true, kw)
+    # every tuning of the grid keeps parity (spot-check the extremes)
+    for cf, sd, ip in [(0.35, 1, 4), (1.0, 3, 32)]:
+        h.apply_tuning(cf, sd, ip)
+        check_parity(h, X, Z, FX, FZ, p.T_true, kw)
+
+
+def test_autotune_dense_and_invalid():
+    p = scenes.cube_pair(n=1500)
+    kw = dict(blocks=p.blocks, ell=0.1, cutoff_mult=0.0)
+    h = cvo.CVO(**kw)
+    t = h.autotune(dev(p.X), dev(p.Z), p.T_true, dev(p.FX), dev(p.FZ))
+    # dense: no grid, so only the work split is tuned
+    assert t["cell_factor"] == 0.5 and t["super_delta"] == 2 and t["items_per_sm"] in (4, 8, 16, 32)
+    check_parity(h, p.X, p.Z, p.FX, p.FZ, p.T_true, kw)
+    with pytest.raises(cvo.CvoError):
+        h.apply_tuning(0.1, 2, 8)
+    with pytest.raises(cvo.CvoError):
+        h.apply_tuning(0.5, 2, 0)
+    # empty clouds: nothing to time, the tuning is unchanged
+    before = h.tuning()
+    t = h.autotune(dev(p.X[:0]), dev(p.Z), p.T_true, dev(p.FX[:0]), dev(p.FZ))
+    assert t["sweep_ms"] == 0.0 and h.tuning() == before
