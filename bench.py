@@ -35,6 +35,7 @@ METRIC = "kernel-pair evals/s & registered pairs/s, batched vs plain GPU, at ora
 UNIT = "pair-evals/s"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+EX2_PER_CLK_SM = 29   # measured ex2.approx.f32 throughput per SM per clock on a GB300
 
 
 def flops_per_pair(blocks):
@@ -249,6 +250,42 @@ def backward_section(cvo, torch, dev, flush, reps=5):
     return out
 
 
+def large_section(cvo, torch, dev, flush, reps=2):
+    """The large semantic pair (200,000 points per cloud, 20 x 10 x 80 m box,
+    rgb + 19 labels, l 0.5 -> 0.05 m, cutoff 3 l, <= 200 iterations): full
+    registration latency (inputs resident, CUDA events) and the indicator."""
+    import scenes
+    p = scenes.large_pair()
+    pr = p.params
+    kw = dict(blocks=p.blocks, ell=pr["ell"], ell_min=pr["ell_min"], cutoff_mult=pr["cutoff_mult"],
+              max_iters=pr["max_iters"], anneal=pr["anneal"])
+    X, Z = torch.tensor(p.X, device=dev), torch.tensor(p.Z, device=dev)
+    FX, FZ = torch.tensor(p.FX, device=dev), torch.tensor(p.FZ, device=dev)
+    out = {"workload": f"box80-200k: {p.n} + {p.m} points, rgb + 19 labels, l 0.5 -> 0.05 m, cutoff 3 l, "
+                       f"<= {pr['max_iters']} iterations"}
+    with cvo.CVO(**kw) as h:
+        out["tuning"] = h.autotune(X, Z, np.eye(4), FX, FZ)
+        h.register(X, Z, np.eye(4), FX, FZ)
+        stream = torch.cuda.current_stream()
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            T, info = h.register(X, Z, np.eye(4), FX, FZ)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    D = np.linalg.inv(T) @ p.T_true
+    out.update({"ms_per_registration": float(np.mean(ms)), "iterations": info["iters"],
+                "ell_final": info["ell_final"], "i_theta": info["i_theta"], "pairs": info["pairs"],
+                "pair_evals_per_s": info["pairs"] / (1e-3 * float(np.mean(ms))),
+                "pose_err_vs_truth": {"rot_rad": float(math.acos(max(-1.0, min(1.0, (np.trace(D[:3, :3]) - 1) / 2)))),
+                                      "trans_m": float(np.linalg.norm(D[:3, 3]))}})
+    return out
+
+
 def cpu_baseline(p, kw, iters=20):
     import oracle
     oracle.build()
@@ -300,6 +337,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain section")
     ap.add_argument("--no-backward", action="store_true", help="skip the forward/backward section")
+    ap.add_argument("--no-large", action="store_true", help="skip the 200,000-point section")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -400,6 +438,7 @@ def main():
     h.close()
     batch = batch_section(cvo, torch, dev, flush) if (rank == 0 and not args.no_batch) else None
     backward = backward_section(cvo, torch, dev, flush) if (rank == 0 and not args.no_backward) else None
+    large = large_section(cvo, torch, dev, flush) if (rank == 0 and not args.no_large) else None
 
     if rank != 0:
         return
@@ -430,11 +469,20 @@ def main():
                                "from the host (the timed steps run the loop as one CUDA graph)",
                      "ms_per_registration_event_timed": timed_ms / args.steps,
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz "
-                                    f"(sm_max_mhz {peak_src})"},
+                                    f"(sm_max_mhz {peak_src})",
+                     # the one ex2 per in-cutoff pair against the XU pipe's rate
+                     "sfu": {"achieved_ex2_per_s": (sweep_pairs / (sweep_ms * 1e-3)) if sweep_ms > 0 else None,
+                             "peak_ex2_per_s": SM_COUNT * EX2_PER_CLK_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6,
+                             "frac": (sweep_pairs / (sweep_ms * 1e-3)) /
+                                     (SM_COUNT * EX2_PER_CLK_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6)
+                                     if sweep_ms > 0 else None,
+                             "peak_source": f"152 SMs x {EX2_PER_CLK_SM} ex2/clk/SM (measured on a GB300 with an "
+                                            "independent-chain ex2.approx throughput loop) x sm_max_mhz"}},
         "clocks": clocks,
         "final_pose_err_vs_truth": pose_err,
         "batch": batch,
         "backward": backward,
+        "large": large,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, kw)
