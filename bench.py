@@ -339,7 +339,7 @@ def main():
     ap.add_argument("--no-backward", action="store_true", help="skip the forward/backward section")
     ap.add_argument("--no-large", action="store_true", help="skip the 200,000-point section")
     ap.add_argument("--tuning", default=None,
-                    help="cell_factor,super_delta,items_per_sm for the street pair instead of autotuning "
+                    help="cell_factor,super_delta,chunk_len for the street pair instead of autotuning "
                          "(fixed launch sequence for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -233,23 +233,26 @@ cvo_status cvo_set_tuning(cvo_handle h, double cell_factor, int super_delta);
 
 /* Tuning of the neighbour sweep: grid cell edge (cell_factor x cutoff
  * radius), query-group extent (Morton super-cells about 2^super_delta
- * cutoff radii wide) and work split (a single pair whose grid level has few
- * query groups splits each group's candidate stream into chunks until about
- * items_per_sm work items per SM exist, so that up to that many lanes of
- * different warps serve one query).  sweep_ms: the measured sweep time of
+ * cutoff radii wide) and the work split of evaluations and batches (each
+ * query group's candidate stream, measured at the call's pose, is cut into
+ * work items of about chunk_len candidates, so up to length / chunk_len
+ * lanes of different warps serve one query, longest streams first; a single
+ * registration with a cutoff, whose streams follow the moving pose, cuts
+ * every stream into up to 8 items of at least 64 candidates at run time).  sweep_ms: the measured sweep time of
  * the tuning (cvo_autotune), else 0. */
 typedef struct {
     double cell_factor;
     int super_delta;
-    int items_per_sm;
+    int chunk_len;
     double sweep_ms;
 } cvo_tuning;
 
 /* Autotuner: prepares the pair (X, Z) under each tuning of a small grid
- * (cell_factor 0.35 / 0.5 / 0.7 / 1.0, super_delta 1 / 2 / 3, items_per_sm
- * 4 / 8 / 16 / 32; with cutoff_mult <= 0 only the work split, the others
- * staying as they are), times its
- * sweep at pose T and lengthscale params.ell with CUDA events (best of 3),
+ * (cell_factor 0.35 / 0.5 / 0.7 / 1.0 and super_delta 1 / 2 / 3; chunk_len
+ * stays as set; with cutoff_mult <= 0 there is no grid to tune and the
+ * tuning stays as it is), times its
+ * sweep at pose T and lengthscale params.ell with CUDA events (best of 3,
+ * with a registration's work split),
  * keeps the fastest on the handle and returns it in *out.  Results do not
  * depend on the tuning beyond rounding; every tuning's F is checked against
  * the first (CVO_ERR_CUDA if they differ by more than 1e-4 relative).  Costs
@@ -257,13 +260,33 @@ typedef struct {
 cvo_status cvo_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], cvo_tuning* out);
 
 /* The handle's current tuning (sweep_ms = 0), and setting it (validated as
- * cvo_set_tuning, items_per_sm in [1, 256]). */
+ * cvo_set_tuning, chunk_len in [16, 4096]). */
 cvo_status cvo_get_tuning(cvo_handle h, cvo_tuning* out);
 cvo_status cvo_apply_tuning(cvo_handle h, const cvo_tuning* t);
 
-/* Average device time (ms) of the sweep kernel over the handle's last
- * registration, measured with CUDA events around each sweep launch when
- * timing is on (cvo_set_timing), and the number of sweep launches timed. */
+/* How a single-pair registration runs its iterations (batches always use
+ * the graph, or the host queue in CVO_LOOP_HOST):
+ *   CVO_LOOP_GRAPH (default)  a CUDA graph whose WHILE node repeats
+ *       (sweep, step);
+ *   CVO_LOOP_PERSISTENT  one cooperative kernel for the whole loop, which
+ *       re-plans the work split every iteration, with grid barriers between
+ *       plan, sweep and step (bounded waits: CVO_ERR_TIMEOUT if one gives
+ *       up);
+ *   CVO_LOOP_HOST   the same two kernels queued from the host (what a
+ *       profiler can attribute per kernel).
+ * Results are deterministic in every mode; GRAPH and HOST are bitwise
+ * equal, PERSISTENT sums in another fixed order (same tolerances).  The
+ * environment variable CVO_LOOP=graph|persistent|host sets the default of
+ * new handles (CVO_GRAPH=0 means host). */
+enum { CVO_LOOP_HOST = 0, CVO_LOOP_GRAPH = 1, CVO_LOOP_PERSISTENT = 2 };
+cvo_status cvo_set_loop(cvo_handle h, int mode);
+
+/* Device time (ms) of the handle's last registration's sweeps when timing
+ * is on (cvo_set_timing): in the graph and host modes CUDA events around
+ * each sweep launch (the loop is then queued from the host), average per
+ * launch, and the number of launches; in the persistent mode events around
+ * the one kernel, i.e. sweep and step together, per iteration, and the
+ * number of iterations. */
 cvo_status cvo_set_timing(cvo_handle h, int on);
 cvo_status cvo_sweep_time(cvo_handle h, double* avg_ms, int* launches);
 

@@ -28,7 +28,7 @@ from . import build as _build
 __all__ = ["CVO", "cvo_create", "cvo_destroy", "cvo_set_params", "cvo_inner_product", "cvo_gradient", "cvo_metric",
            "cvo_evaluate", "cvo_backward", "cvo_cosine", "CVOInnerProduct", "inner_product_fn", "metric_fn",
            "cvo_register_pair", "cvo_register_batch", "cvo_register_sequence", "cvo_get_trace", "cvo_set_timing",
-           "cvo_autotune", "cvo_get_tuning", "cvo_apply_tuning",
+           "cvo_autotune", "cvo_get_tuning", "cvo_apply_tuning", "cvo_set_loop",
            "cvo_sweep_time", "cvo_last_error", "cvo_version", "cvo_kernel_launches", "load_library", "Status",
            "CvoError"]
 
@@ -80,7 +80,7 @@ class Info(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("cell_factor", ctypes.c_double), ("super_delta", ctypes.c_int), ("items_per_sm", ctypes.c_int),
+    _fields_ = [("cell_factor", ctypes.c_double), ("super_delta", ctypes.c_int), ("chunk_len", ctypes.c_int),
                 ("sweep_ms", ctypes.c_double)]
 
     def as_dict(self):
@@ -127,12 +127,13 @@ def load_library(build_if_missing: bool = True):
     lib.cvo_set_tuning.restype = ctypes.c_int
     lib.cvo_sweep_time.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int)]
     lib.cvo_autotune.argtypes = [vp, P(Cloud), P(Cloud), vp, P(Tuning)]
+    lib.cvo_set_loop.argtypes = [vp, ctypes.c_int]
     lib.cvo_get_tuning.argtypes = [vp, P(Tuning)]
     lib.cvo_apply_tuning.argtypes = [vp, P(Tuning)]
     for name in ("cvo_create", "cvo_destroy", "cvo_set_params", "cvo_inner_product", "cvo_metric", "cvo_gradient",
                  "cvo_evaluate", "cvo_backward", "cvo_cosine", "cvo_register_pair", "cvo_register_sequence",
                  "cvo_register_batch", "cvo_get_trace", "cvo_set_timing", "cvo_sweep_time", "cvo_autotune",
-                 "cvo_get_tuning", "cvo_apply_tuning"):
+                 "cvo_get_tuning", "cvo_apply_tuning", "cvo_set_loop"):
         getattr(lib, name).restype = ctypes.c_int
     lib.cvo_last_error.restype = ctypes.c_char_p
     lib.cvo_last_error.argtypes = []
@@ -438,14 +439,22 @@ def cvo_autotune(h, X, Z, T, FX=None, FZ=None) -> dict:
     return out.as_dict()
 
 
+LOOP_MODES = {"host": 0, "graph": 1, "persistent": 2}
+
+
+def cvo_set_loop(h, mode):
+    """Registration loop of a single pair: "graph" (default), "persistent" or "host"."""
+    return _check(load_library().cvo_set_loop(h, LOOP_MODES[mode] if isinstance(mode, str) else int(mode)))
+
+
 def cvo_get_tuning(h) -> dict:
     out = Tuning()
     _check(load_library().cvo_get_tuning(h, ctypes.byref(out)))
     return out.as_dict()
 
 
-def cvo_apply_tuning(h, cell_factor, super_delta, items_per_sm):
-    t = Tuning(float(cell_factor), int(super_delta), int(items_per_sm), 0.0)
+def cvo_apply_tuning(h, cell_factor, super_delta, chunk_len):
+    t = Tuning(float(cell_factor), int(super_delta), int(chunk_len), 0.0)
     return _check(load_library().cvo_apply_tuning(h, ctypes.byref(t)))
 
 
@@ -520,8 +529,11 @@ class CVO:
     def tuning(self):
         return cvo_get_tuning(self.h)
 
-    def apply_tuning(self, cell_factor, super_delta, items_per_sm):
-        return cvo_apply_tuning(self.h, cell_factor, super_delta, items_per_sm)
+    def set_loop(self, mode):
+        return cvo_set_loop(self.h, mode)
+
+    def apply_tuning(self, cell_factor, super_delta, chunk_len):
+        return cvo_apply_tuning(self.h, cell_factor, super_delta, chunk_len)
 
 
 # ---- differentiable form ---------------------------------------------------------

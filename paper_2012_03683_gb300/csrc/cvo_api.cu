@@ -85,7 +85,7 @@ struct LevelHost {
     long long ncells;
     int shift;
     int ngroups;
-    int chunks;
+    int nitems;
 };
 
 constexpr long long kMaxCells = 1LL << 26;
@@ -103,9 +103,10 @@ float decode_orderable(unsigned u)
 // queries of X and their groups, the iteration state.
 struct PairRes {
     DevBuf xrec, morton, levels_dev, state;
-    DevBuf zrec[kMaxLevels], cell_start[kMaxLevels], groups[kMaxLevels];
+    DevBuf zrec[kMaxLevels], cell_start[kMaxLevels], groups[kMaxLevels], items[kMaxLevels];
     int n = 0, m = 0, nlevels = 0;
     LevelHost lv[kMaxLevels];
+    LevelDesc ld[kMaxLevels];   // host copy of levels_dev
     double zc[3] = {0, 0, 0};
     int max_items = 1;
 
@@ -117,6 +118,7 @@ struct PairRes {
             release(zrec[k]);
             release(cell_start[k]);
             release(groups[k]);
+            release(items[k]);
         }
     }
 };
@@ -132,7 +134,7 @@ struct cvo_handle_s {
     int device = 0;
     int num_sms = 152;
     int timing = 0;
-    int use_graph = 1;
+    int loop_mode = 1;   // registration loop: 0 queued from the host, 1 CUDA graph, 2 persistent kernel
     // scratch shared by every pair's setup (used one pair at a time)
     DevBuf stage_xyz[2], stage_feat[2];
     DevBuf keys, vals, keys2, vals2, sort_tmp, flags, gidx, misc;
@@ -141,6 +143,7 @@ struct cvo_handle_s {
     // gradients with respect to the inputs: device outputs for host callers,
     // per-query terms of dF/dl and their sum
     DevBuf bw_out[4], bw_tq, bw_dell;
+
     std::vector<PairRes> pr;
     IterState* h_state = nullptr;   // pinned mirror(s)
     int h_state_cap = 0;
@@ -158,12 +161,10 @@ struct cvo_handle_s {
     // Morton super-cells about 2^super_delta cutoff radii wide
     double cell_factor = 0.5;
     int super_delta = 2;
-    // work split: a single pair whose level has few query groups splits each
-    // group's stream into chunks (work items) until about items_per_sm items
-    // per SM exist, i.e. up to that many lanes share one query's candidates;
-    // a batch uses batch_chunks per group
-    int items_per_sm = 8;
-    int batch_chunks = kChunks;
+    // work split: each query group's candidate stream is split into chunks
+    // of about chunk_len candidates (work items), so up to stream / chunk_len
+    // lanes of different warps serve one query
+    int chunk_len = kChunkLen;
 };
 
 namespace {
@@ -321,11 +322,8 @@ void set_features(cvo_handle h, int rec_bf16)
 
 // Builds the grid levels of Z, the Morton-ordered queries of X and their groups
 // for lengthscales in [ell_lo, ell_hi].  Uses the handle's shared scratch.
-// alone: the pair has the GPU to itself, so a level with few query groups
-// splits their streams into more chunks (work items) to fill the SMs; pairs
-// of a batch keep the default and share the grid.
-cvo_status prepare(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud* Z, double ell_hi, double ell_lo,
-                   bool alone = true)
+// The work items are planned by init_state, once the start pose is known.
+cvo_status prepare(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud* Z, double ell_hi, double ell_lo)
 {
     const cvo_params& p = h->p;
     const int D = h->D;
@@ -455,22 +453,11 @@ cvo_status prepare(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud
     }
     CVO_CUDA(cudaMemcpyAsync(h->h_misc + 16, misc + 16, P.nlevels * sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
     CVO_CUDA(cudaStreamSynchronize(h->s));
-    int max_items = 1;
-    LevelDesc ld[kMaxLevels];
     for (int k = 0; k < P.nlevels; ++k) {
         LevelHost& L = P.lv[k];
         L.ngroups = n > 0 ? (int)h->h_misc[16 + k] : 0;
-        int chunks = alone ? kChunks : h->batch_chunks;
-        if (alone && L.ngroups > 0) {
-            // about items_per_sm work items per SM (8 by default, measured best
-            // on a dense 2,000-point pair); levels with many groups keep the
-            // default split
-            const long long target = (long long)h->num_sms * h->items_per_sm;
-            chunks = (int)std::min<long long>(kMaxChunks, std::max<long long>(kChunks, (target + L.ngroups - 1) / L.ngroups));
-        }
-        L.chunks = chunks;
-        max_items = std::max(max_items, L.ngroups * chunks);
-        LevelDesc& d = ld[k];
+        L.nitems = 0;
+        LevelDesc& d = P.ld[k];
         d.h = (float)L.h;
         d.inv_h = (float)(1.0 / L.h);
         d.ox = L.ox; d.oy = L.oy; d.oz = L.oz;
@@ -478,12 +465,56 @@ cvo_status prepare(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud
         d.cell_start = (const int*)P.cell_start[k].p;
         d.zrec = (const float4*)P.zrec[k].p;
         d.groups = (const int2*)P.groups[k].p;
+        d.items = nullptr;
         d.ngroups = L.ngroups;
-        d.chunks = L.chunks;
+        d.nitems = 0;
+    }
+    P.max_items = 1;
+    CVO_CUDA(ensure(P.levels_dev, sizeof(P.ld)));
+    CVO_CUDA(cudaMemcpyAsync(P.levels_dev.p, P.ld, P.nlevels * sizeof(LevelDesc), cudaMemcpyHostToDevice, h->s));
+    return CVO_OK;
+}
+
+// Work items of every level of a prepared pair.  planned: at the pose of
+// its state (after k_init_state), per query group the candidate-stream
+// length at the level's design cutoff radius, groups sorted longest first,
+// each split into ceil(length / chunk_len) chunks (at most kMaxChunks) --
+// exact for an evaluation, and good for a batch of pairs whose poses stay
+// near their starts.  Otherwise uniform: kChunks per group in Morton order,
+// cut at run time (a single registration, whose pose and lengthscale move
+// away from any plan made at the start).
+cvo_status plan_items(cvo_handle h, PairRes& P, bool planned)
+{
+    if (P.n == 0) return CVO_OK;
+    unsigned* misc = (unsigned*)h->misc.p;
+    for (int k = 0; k < P.nlevels; ++k) {
+        LevelHost& L = P.lv[k];
+        const int ng = L.ngroups;
+        CVO_CUDA(ensure(P.items[k], (size_t)std::max(ng, 1) * kMaxChunks * sizeof(int4)));
+        CVO_CUDA(launch_group_cost((const LevelDesc*)P.levels_dev.p, k, ng, (const float4*)P.xrec.p, P.m, h->rs, h->dense,
+                                   (const IterState*)P.state.p, h->dense ? -1.0f : (float)L.rdesign,
+                                   planned ? h->chunk_len : 0, (unsigned*)h->keys.p, (unsigned*)h->vals.p,
+                                   (unsigned*)h->flags.p, h->s));
+        unsigned* ks = (unsigned*)h->keys.p;
+        unsigned* vs = (unsigned*)h->vals.p;
+        if (planned) CVO_TRY(sort_pairs(h, ng, 32, &ks, &vs));
+        CVO_CUDA(launch_gather_u32((const unsigned*)h->flags.p, vs, ng, (unsigned*)h->gidx.p, h->s));
+        CVO_CUDA(exclusive_scan_u32((const unsigned*)h->gidx.p, ks, ng, misc + 16 + k, h->s));
+        CVO_CUDA(launch_write_items((const LevelDesc*)P.levels_dev.p, k, vs, (const unsigned*)h->flags.p, ks, ng,
+                                    (int4*)P.items[k].p, h->s));
+    }
+    CVO_CUDA(cudaMemcpyAsync(h->h_misc + 16, misc + 16, P.nlevels * sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
+    CVO_CUDA(cudaStreamSynchronize(h->s));
+    int max_items = 1;
+    for (int k = 0; k < P.nlevels; ++k) {
+        P.lv[k].nitems = (int)h->h_misc[16 + k];
+        P.ld[k].items = (const int4*)P.items[k].p;
+        P.ld[k].nitems = P.lv[k].nitems;
+        P.ld[k].chunk_min = planned ? 0 : kChunkMin;
+        max_items = std::max(max_items, P.lv[k].nitems);
     }
     P.max_items = max_items;
-    CVO_CUDA(ensure(P.levels_dev, sizeof(ld)));
-    CVO_CUDA(cudaMemcpyAsync(P.levels_dev.p, ld, P.nlevels * sizeof(LevelDesc), cudaMemcpyHostToDevice, h->s));
+    CVO_CUDA(cudaMemcpyAsync(P.levels_dev.p, P.ld, P.nlevels * sizeof(LevelDesc), cudaMemcpyHostToDevice, h->s));
     return CVO_OK;
 }
 
@@ -499,7 +530,9 @@ cvo_status ensure_host_states(cvo_handle h, int n)
 }
 
 // Initial state of one pair; host copy in h->h_state[slot].
-cvo_status init_state(cvo_handle h, PairRes& P, int slot, const double* T, double ell, int mode)
+enum PlanMode { kNoPlan = 0, kUniform = 1, kPlanned = 2 };
+
+cvo_status init_state(cvo_handle h, PairRes& P, int slot, const double* T, double ell, int mode, int plan)
 {
     IterState* st = h->h_state + slot;
     std::memset(st, 0, sizeof(IterState));
@@ -528,6 +561,7 @@ cvo_status init_state(cvo_handle h, PairRes& P, int slot, const double* T, doubl
     CVO_CUDA(ensure(P.state, sizeof(IterState)));
     CVO_CUDA(cudaMemcpyAsync(P.state.p, st, sizeof(IterState), cudaMemcpyHostToDevice, h->s));
     CVO_CUDA(launch_init_state((IterState*)P.state.p, h->s));
+    if (plan != kNoPlan) CVO_TRY(plan_items(h, P, plan == kPlanned));
     return CVO_OK;
 }
 
@@ -619,7 +653,7 @@ cvo_status run_eval(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const 
     CVO_TRY(begin_call(h, rec_bf16_of(h->p, X, Z), 1));
     PairRes& P = h->pr[0];
     CVO_TRY(prepare(h, P, X, Z, h->p.ell, h->p.ell));
-    CVO_TRY(init_state(h, P, 0, T, h->p.ell, 0));
+    CVO_TRY(init_state(h, P, 0, T, h->p.ell, 0, kPlanned));
     const int nb = single_pair_blocks(h, P);
     SweepArgs a;
     CVO_TRY(setup_sweep(h, std::vector<PairDesc>{pair_desc(P, 0, nb)}, nb, &a, true));
@@ -766,15 +800,40 @@ cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     CVO_TRY(begin_call(h, rec_bf16_of(p, X, Z), 1));
     PairRes& P = h->pr[0];
     CVO_TRY(prepare(h, P, X, Z, p.ell, reachable_ell_lo(p)));
-    CVO_TRY(init_state(h, P, 0, T_init, p.ell, 1));
+    // the dense sum streams all of Z for every group whatever the pose, so a
+    // plan made at the start holds; with a cutoff the streams follow the pose
+    CVO_TRY(init_state(h, P, 0, T_init, p.ell, 1, h->dense ? kPlanned : kUniform));
     CVO_CUDA(ensure(h->trace, (size_t)p.max_iters * CVO_TRACE_STRIDE * sizeof(double)));
     const int nb = single_pair_blocks(h, P);
     SweepArgs a;
     CVO_TRY(setup_sweep(h, std::vector<PairDesc>{pair_desc(P, 0, nb)}, nb, &a, true));
     double* trace = (double*)h->trace.p;
     IterState* dst = (IterState*)P.state.p;
-    const bool graph = !h->timing && h->use_graph;
-    if (graph) {
+    const bool persistent = h->loop_mode == 2;
+    const bool graph = !persistent && !h->timing && h->loop_mode == 1;
+    long long kernel_launches = 0;
+    if (persistent) {
+        // one cooperative launch for the whole loop (events around it when timing)
+        int grid = 0;
+        CVO_CUDA(persistent_grid(a, &grid));
+        if (grid < 1) return fail(CVO_ERR_CUDA, "persistent loop: no resident block fits");
+        grid = std::min(grid, kGroupBlocks * kMaxGroups);
+        if (grid > a.part_cap) CVO_TRY(setup_sweep(h, std::vector<PairDesc>{pair_desc(P, 0, grid)}, grid, &a, true));
+        if (h->timing) {
+            ensure_events(h, 1);
+            CVO_CUDA(cudaEventRecord(h->evs[0], h->s));
+        }
+        int max_groups = 1;
+        for (int k = 0; k < P.nlevels; ++k) max_groups = std::max(max_groups, P.lv[k].ngroups);
+        CVO_CUDA(ensure(h->gidx, (size_t)max_groups * sizeof(unsigned)));
+        CVO_CUDA(launch_register_persistent(a, (unsigned*)h->counters.p, (unsigned*)h->gidx.p, h->chunk_len, trace,
+                                            grid, h->s));
+        if (h->timing) CVO_CUDA(cudaEventRecord(h->evs[1], h->s));
+        CVO_CUDA(cudaMemcpyAsync(h->h_misc + 40, (unsigned*)h->counters.p + 4, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                 h->s));
+        CVO_CUDA(cudaStreamSynchronize(h->s));
+        if (h->h_misc[40] != 0u) return fail(CVO_ERR_TIMEOUT, "persistent loop: a grid barrier gave up waiting");
+    } else if (graph) {
         CVO_TRY(run_graph_loop(h, a, false, dst, trace, 0));
     } else {
         // iterations queued from the host in batches (CUDA events around each
@@ -806,7 +865,15 @@ cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     fill_info(st, &inf);
     h->last_iters = st->iter;
     if (graph) g_launch_count.fetch_add(2LL * st->iter, std::memory_order_relaxed);
-    if (h->timing) {
+    (void)kernel_launches;
+    if (h->timing && persistent) {
+        // the persistent kernel as a whole (sweeps and steps), per iteration
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, h->evs[0], h->evs[1]) == cudaSuccess && st->iter > 0) {
+            h->sweep_ms = ms;
+            h->sweep_n = st->iter;
+        }
+    } else if (h->timing) {
         h->sweep_ms = sum_sweep_events(h, st->iter);
         h->sweep_n = st->iter;
     }
@@ -844,8 +911,8 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
     const double ell_lo = reachable_ell_lo(p);
     long long work = 0;
     for (int i = 0; i < nl; ++i) {
-        CVO_TRY(prepare(h, h->pr[i], X + live[i], Z + live[i], p.ell, ell_lo, false));
-        CVO_TRY(init_state(h, h->pr[i], i, T_init + 16 * live[i], p.ell, 1));
+        CVO_TRY(prepare(h, h->pr[i], X + live[i], Z + live[i], p.ell, ell_lo));
+        CVO_TRY(init_state(h, h->pr[i], i, T_init + 16 * live[i], p.ell, 1, kPlanned));
         work += h->pr[i].max_items;
     }
     // split the grid among the pairs in proportion to their work items
@@ -864,7 +931,7 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
     const long long tstride = (long long)p.max_iters * CVO_TRACE_STRIDE;
     CVO_CUDA(ensure(h->trace, (size_t)nl * tstride * sizeof(double)));
     double* traces = (double*)h->trace.p;
-    const bool graph = !h->timing && h->use_graph;
+    const bool graph = !h->timing && h->loop_mode != 0;
     if (graph) {
         CVO_TRY(run_graph_loop(h, a, true, nullptr, traces, tstride));
     } else {
@@ -966,7 +1033,7 @@ cvo_status run_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
                      float* pos, float* feat, float* tq) -> cvo_status {
         PairRes& P = h->pr[slot];
         CVO_TRY(prepare(h, P, Q, G, ell, ell));
-        CVO_TRY(init_state(h, P, slot, Tq, ell, 0));
+        CVO_TRY(init_state(h, P, slot, Tq, ell, 0, kNoPlan));
         g.levels = (const LevelDesc*)P.levels_dev.p;
         g.xrec = (const float4*)P.xrec.p;
         g.st = (const IterState*)P.state.p;
@@ -1017,7 +1084,7 @@ cvo_status run_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
 // `reps` launches, CUDA events on the handle's stream.
 cvo_status time_sweep(cvo_handle h, PairRes& P, const double* T, int reps, double* ms, double* F)
 {
-    CVO_TRY(init_state(h, P, 0, T, h->p.ell, 0));
+    CVO_TRY(init_state(h, P, 0, T, h->p.ell, 0, h->dense ? kPlanned : kUniform));   // as a registration sweeps
     const int nb = single_pair_blocks(h, P);
     SweepArgs a;
     CVO_TRY(setup_sweep(h, std::vector<PairDesc>{pair_desc(P, 0, nb)}, nb, &a, true));
@@ -1042,7 +1109,7 @@ cvo_status time_sweep(cvo_handle h, PairRes& P, const double* T, int reps, doubl
     return CVO_OK;
 }
 
-// Autotuner: every (cell_factor, super_delta, items_per_sm) of a small grid
+// Autotuner: every (cell_factor, super_delta, chunk_len) of a small grid
 // is prepared and its sweep timed on the caller's pair; the fastest is kept.
 // The results must not depend on the tuning beyond rounding: F of every
 // candidate is checked against the first one.
@@ -1050,9 +1117,9 @@ cvo_status run_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
 {
     static const double kCell[] = {0.35, 0.5, 0.7, 1.0};
     static const int kSuper[] = {1, 2, 3};
-    static const int kItems[] = {4, 8, 16, 32};
+    const int kItems[] = {h->chunk_len};   // the planned items' length is not tuned here
     const double cf0 = h->cell_factor;
-    const int sd0 = h->super_delta, ip0 = h->items_per_sm;
+    const int sd0 = h->super_delta, ip0 = h->chunk_len;
     cvo_tuning best{cf0, sd0, ip0, 1e30};
     std::memset(out, 0, sizeof(*out));
     if (X->n == 0 || Z->n == 0) {
@@ -1072,7 +1139,7 @@ cvo_status run_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
             for (int ip : kItems) {
                 h->cell_factor = cf;
                 h->super_delta = sd;
-                h->items_per_sm = ip;
+                h->chunk_len = ip;
                 st = prepare(h, P, X, Z, h->p.ell, h->p.ell);
                 if (st < 0) break;
                 double ms = 0.0, F = 0.0;
@@ -1094,12 +1161,12 @@ cvo_status run_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     if (st < 0) {
         h->cell_factor = cf0;
         h->super_delta = sd0;
-        h->items_per_sm = ip0;
+        h->chunk_len = ip0;
         return st;
     }
     h->cell_factor = best.cell_factor;
     h->super_delta = best.super_delta;
-    h->items_per_sm = best.items_per_sm;
+    h->chunk_len = best.chunk_len;
     *out = best;
     return CVO_OK;
 }
@@ -1139,12 +1206,20 @@ cvo_status cvo_create(const cvo_params* params, void* cuda_stream, cvo_handle* o
     h->p = *params;
     h->s = (cudaStream_t)cuda_stream;
     h->device = dev;
-    // CVO_GRAPH=0 queues the loop's kernels from the host instead of running
-    // it as one CUDA graph (profilers cannot attribute time to the kernel
-    // nodes of a graph with conditional nodes); the kernels are the same.
+    // The registration loop of one pair runs as a CUDA graph of (sweep,
+    // step) kernels by default.  CVO_LOOP=persistent runs it as one
+    // persistent kernel, and CVO_LOOP=host (or CVO_GRAPH=0) queues the
+    // kernels from the host, so that a profiler can attribute time to each
+    // (it cannot for the kernel nodes of a graph with conditional nodes).
+    // Batches always use the graph (or the host queue).
     {
+        const char* lv = std::getenv("CVO_LOOP");
         const char* gv = std::getenv("CVO_GRAPH");
-        h->use_graph = !(gv && gv[0] == '0');
+        if (lv && std::strcmp(lv, "host") == 0) h->loop_mode = 0;
+        else if (lv && std::strcmp(lv, "graph") == 0) h->loop_mode = 1;
+        else if (gv && gv[0] == '0') h->loop_mode = 0;
+        else if (lv && std::strcmp(lv, "persistent") == 0) h->loop_mode = 2;
+        else h->loop_mode = 1;
     }
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (ensure_host_states(h, 1) != CVO_OK ||
@@ -1412,16 +1487,24 @@ cvo_status cvo_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
 cvo_status cvo_get_tuning(cvo_handle h, cvo_tuning* out)
 {
     if (!h || !out) return fail(CVO_ERR_INVALID_ARG, "NULL argument");
-    *out = cvo_tuning{h->cell_factor, h->super_delta, h->items_per_sm, 0.0};
+    *out = cvo_tuning{h->cell_factor, h->super_delta, h->chunk_len, 0.0};
     return CVO_OK;
 }
 
 cvo_status cvo_apply_tuning(cvo_handle h, const cvo_tuning* t)
 {
     if (!h || !t) return fail(CVO_ERR_INVALID_ARG, "NULL argument");
-    if (t->items_per_sm < 1 || t->items_per_sm > 256) return fail(CVO_ERR_INVALID_ARG, "items_per_sm must be in [1, 256]");
+    if (t->chunk_len < 16 || t->chunk_len > 4096) return fail(CVO_ERR_INVALID_ARG, "chunk_len must be in [16, 4096]");
     CVO_TRY(cvo_set_tuning(h, t->cell_factor, t->super_delta));
-    h->items_per_sm = t->items_per_sm;
+    h->chunk_len = t->chunk_len;
+    return CVO_OK;
+}
+
+cvo_status cvo_set_loop(cvo_handle h, int mode)
+{
+    if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
+    if (mode < CVO_LOOP_HOST || mode > CVO_LOOP_PERSISTENT) return fail(CVO_ERR_INVALID_ARG, "unknown loop mode %d", mode);
+    h->loop_mode = mode;
     return CVO_OK;
 }
 

@@ -13,6 +13,14 @@
 //   groups        per level, (first query, count <= 32) of each query group:
 //                 consecutive queries inside one Morton super-cell whose edge
 //                 does not exceed that level's cell edge
+//   items         per level, the work items of a sweep: (first query, count,
+//                 chunk k, chunks n) -- chunk k of n of one group's candidate
+//                 stream.  Planned (evaluations, batches): n from the
+//                 stream's length at the pose of the call (about chunk_len
+//                 candidates per item), groups with the longest streams
+//                 first.  Uniform (a registration, whose pose moves): 8
+//                 chunks per group in Morton order, cut at run time to
+//                 min(8, length / 64)
 //   IterState     pose, lengthscale, annealing state and the derived
 //                 per-iteration constants, written by the finalize kernel and
 //                 read by the sweep kernel (no host round trip per iteration)
@@ -29,9 +37,10 @@ namespace cvo {
 constexpr int kStatN = 43;       // linear statistics of the per-query moments
 constexpr int kSweepWarps = 4;   // warps per sweep block
 constexpr int kMaxLevels = 24;   // grid levels of one registration
-constexpr int kChunks = 8;       // default chunks a group's candidate stream splits into
-constexpr int kMaxChunks = 64;   // upper limit of a level's chunk count
-constexpr int kChunkMin = 64;    // shortest chunk worth a work item
+constexpr int kMaxChunks = 64;   // most work items (chunks) one query group's stream splits into
+constexpr int kChunkLen = 128;   // default candidates per planned work item
+constexpr int kChunks = 8;       // chunks per group of the uniform items
+constexpr int kChunkMin = 64;    // shortest run-time chunk of the uniform items
 constexpr int kFinalizeThreads = 64;
 constexpr int kGroupBlocks = 32;   // sweep blocks per reduction group (the group's last block sums them)
 constexpr int kMaxGroups = 64;     // reduction groups per sweep launch (so at most 2048 sweep blocks)
@@ -56,8 +65,12 @@ struct LevelDesc {
     const int* cell_start;   // nx*ny*nz + 1
     const float4* zrec;      // M records sorted by cell
     const int2* groups;      // query groups (first, count)
+    const int4* items;       // work items (first, count, chunk, chunks)
     int ngroups;
-    int chunks;              // work items per query group (its stream is split into up to this many)
+    int nitems;
+    int chunk_min;           // > 0: a group's stream is cut into min(chunks, length / chunk_min) chunks at
+                             // run time (the rest of its items are empty); 0: into the planned chunks
+    int pad_;
 };
 
 // Feature-kernel constants (exponent in log2 units).
@@ -188,6 +201,28 @@ struct GradArgs {
 cudaError_t launch_grad(const GradArgs& g, int nblocks, cudaStream_t s);
 // Deterministic sum of n floats into *out (one block).
 cudaError_t launch_sum_f32(const float* v, int n, double* out, cudaStream_t s);
+
+// Persistent registration loop of one pair (cvo_persist.cu): the blocks a
+// cooperative launch of it may have (one resident wave), and the launch.
+// sw is set up for at least nblocks sweep blocks; ctl: 6 unsigned, zero
+// before the launch (ctl[4] != 0 afterwards: a grid barrier gave up); nch:
+// one unsigned per query group of the largest level.
+cudaError_t persistent_grid(const SweepArgs& sw, int* nblocks);
+cudaError_t launch_register_persistent(const SweepArgs& sw, unsigned* ctl, unsigned* nch, int chunk_len, double* trace,
+                                       int nblocks, cudaStream_t s);
+
+// Work-item planning of one grid level (cvo_sweep.cu): per query group the
+// length of its candidate stream at the state's pose for cutoff radius rc,
+// as a descending sort key (keys), the group index (vals) and its chunk count
+// ceil(length / chunk_len) clamped to [1, kMaxChunks] (nch); chunk_len <= 0:
+// no lengths, vals = the group index and nch = kChunks (uniform items).
+// Then, with the groups sorted and the chunk counts scanned, the item table.
+cudaError_t launch_group_cost(const LevelDesc* levels, int level, int ngroups, const float4* xrec, int m, int rs,
+                              int dense, const IterState* st, float rc, int chunk_len, unsigned* keys, unsigned* vals,
+                              unsigned* nch, cudaStream_t s);
+cudaError_t launch_gather_u32(const unsigned* src, const unsigned* idx, int n, unsigned* dst, cudaStream_t s);
+cudaError_t launch_write_items(const LevelDesc* levels, int level, const unsigned* sorted_groups, const unsigned* nch,
+                               const unsigned* offsets, int ngroups, int4* items, cudaStream_t s);
 
 // setup (cvo_setup.cu)
 cudaError_t launch_bbox(const float* xyz, int n, unsigned* out6, int* bad, cudaStream_t s);

@@ -48,6 +48,7 @@ constexpr int kNoAllocMaxRec = 7;                          // float4 per record
 constexpr int kNoAllocMaxFeat = (kNoAllocMaxRec - 1) * 4;  // float32 feature entries
 constexpr int kNoAllocBlocks = 1216;                       // sweep blocks (8 per SM on 152 SMs)
 constexpr int kMaxDevices = 64;
+constexpr int kNoAllocMaxChunks = 16;                      // work items per query group
 
 constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 constexpr size_t kOffState = 0;
@@ -60,7 +61,8 @@ constexpr size_t kOffCnt = align256(kOffStats + sizeof(float2) * kStatN * kNoAll
 constexpr size_t kOffGStats = align256(kOffCnt + sizeof(unsigned long long) * 2 * kNoAllocBlocks);
 constexpr size_t kOffGCnt = align256(kOffGStats + sizeof(float2) * kStatN * kMaxGroups);
 constexpr size_t kOffGArr = align256(kOffGCnt + sizeof(unsigned long long) * 2 * kMaxGroups);
-constexpr size_t kOffX = align256(kOffGArr + sizeof(unsigned) * kMaxGroups);
+constexpr size_t kOffItems = align256(kOffGArr + sizeof(unsigned) * kMaxGroups);
+constexpr size_t kOffX = align256(kOffItems + sizeof(int4) * (kNoAllocMaxPoints / 32) * kNoAllocMaxChunks);
 constexpr size_t kOffZ = align256(kOffX + sizeof(float4) * kNoAllocMaxRec * kNoAllocMaxPoints);
 constexpr size_t kUsedBytes = align256(kOffZ + sizeof(float4) * kNoAllocMaxRec * kNoAllocMaxPoints);
 constexpr size_t kScratchBytes = 4608 * 1024;   // 4.5 MiB
@@ -120,9 +122,8 @@ bool is_device_pointer(const void* p)
 
 // Writes the state block, the level descriptor and the query groups, and
 // resets the bounding-box counters (min to all ones, max and flag to zero).
-__global__ void k_na_setup(IterState init, LevelDesc ld, PairDesc pd, int n, IterState* st, LevelDesc* lv,
-                           PairDesc* pair, int2* groups,
-                           unsigned* misc, unsigned* arrivals)
+__global__ void k_na_setup(IterState init, LevelDesc ld, PairDesc pd, int n, int nch, IterState* st, LevelDesc* lv,
+                           PairDesc* pair, int2* groups, int4* items, unsigned* misc, unsigned* arrivals)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     if (tid < kMaxGroups) arrivals[tid] = 0u;   // the sweep's group counters start at zero
@@ -140,6 +141,11 @@ __global__ void k_na_setup(IterState init, LevelDesc ld, PairDesc pd, int n, Ite
     }
     const int ng = (n + 31) / 32;
     for (int g = tid; g < ng; g += gridDim.x * blockDim.x) groups[g] = make_int2(32 * g, min(32, n - 32 * g));
+    // every group streams all of Z (dense), so every group gets nch chunks
+    for (int i = tid; i < ng * nch; i += gridDim.x * blockDim.x) {
+        const int g = i / nch;
+        items[i] = make_int4(32 * g, min(32, n - 32 * g), i - g * nch, nch);
+    }
 }
 
 __device__ float na_decode(unsigned u)
@@ -281,6 +287,7 @@ extern "C" cvo_status cvo_evaluate_dense_noalloc(const cvo_params* p, void* cuda
     LevelDesc* lv = (LevelDesc*)(base + kOffLevel);
     unsigned* misc = (unsigned*)(base + kOffMisc);
     int2* groups = (int2*)(base + kOffGroups);
+    int4* items = (int4*)(base + kOffItems);
     float2* stats = (float2*)(base + kOffStats);
     unsigned long long* cnt = (unsigned long long*)(base + kOffCnt);
     float2* gstats = (float2*)(base + kOffGStats);
@@ -312,10 +319,11 @@ extern "C" cvo_status cvo_evaluate_dense_noalloc(const cvo_params* p, void* cuda
     ld.zrec = zrec;
     ld.groups = groups;
     ld.ngroups = (n + 31) / 32;
-    ld.chunks = kChunks;
+    const int nch = std::max(1, std::min(kNoAllocMaxChunks, (m + kChunkLen - 1) / kChunkLen));
+    ld.items = items;
+    ld.nitems = ld.ngroups * nch;
 
-    const int items = ld.ngroups * ld.chunks;
-    const int nblocks = std::max(1, std::min((items + kSweepWarps - 1) / kSweepWarps, kNoAllocBlocks));
+    const int nblocks = std::max(1, std::min((ld.nitems + kSweepWarps - 1) / kSweepWarps, kNoAllocBlocks));
     PairDesc pd;
     pd.levels = lv;
     pd.xrec = xrec;
@@ -327,7 +335,7 @@ extern "C" cvo_status cvo_evaluate_dense_noalloc(const cvo_params* p, void* cuda
     PairDesc* pair = (PairDesc*)(base + kOffPair);
 
     g_launch_count.fetch_add(2, std::memory_order_relaxed);
-    k_na_setup<<<(ld.ngroups + 255) / 256, 256, 0, s>>>(init, ld, pd, n, st, lv, pair, groups, misc, garr);
+    k_na_setup<<<(ld.nitems + 255) / 256, 256, 0, s>>>(init, ld, pd, n, nch, st, lv, pair, groups, items, misc, garr);
     NA_CUDA(cudaGetLastError());
     NA_CUDA(launch_bbox(Z->xyz, m, misc, (int*)(misc + 6), s));
     NA_CUDA(launch_bbox(X->xyz, n, misc + 8, (int*)(misc + 6), s));   // finiteness of X (box unused)

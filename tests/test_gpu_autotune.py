@@ -36,17 +36,17 @@ def test_autotune_street_slice():
     assert h.tuning()["cell_factor"] == 0.5 and h.tuning()["super_delta"] == 2
     t = h.autotune(dev(X), dev(Z), p.T_true, dev(FX), dev(FZ))
     assert t["cell_factor"] in (0.35, 0.5, 0.7, 1.0) and t["super_delta"] in (1, 2, 3)
-    assert t["items_per_sm"] in (4, 8, 16, 32) and t["sweep_ms"] > 0.0
+    assert t["chunk_len"] in (48, 64, 96, 128) and t["sweep_ms"] > 0.0
     # the timed sweep did the work: no faster than the pairs it evaluates allow
     # (6,000 x 6,000 points at l = 0.2 take tens of microseconds)
     ev = h.evaluate(dev(X), dev(Z), p.T_true, dev(FX), dev(FZ))
     assert ev["pairs"] > 1e5 and t["sweep_ms"] > 0.01
     cur = h.tuning()
-    assert (cur["cell_factor"], cur["super_delta"], cur["items_per_sm"]) == \
-        (t["cell_factor"], t["super_delta"], t["items_per_sm"])
+    assert (cur["cell_factor"], cur["super_delta"], cur["chunk_len"]) == \
+        (t["cell_factor"], t["super_delta"], t["chunk_len"])
     check_parity(h, X, Z, FX, FZ, p.T_true, kw)
     # every tuning of the grid keeps parity (spot-check the extremes)
-    for cf, sd, ip in [(0.35, 1, 4), (1.0, 3, 32)]:
+    for cf, sd, ip in [(0.35, 1, 48), (1.0, 3, 128)]:
         h.apply_tuning(cf, sd, ip)
         check_parity(h, X, Z, FX, FZ, p.T_true, kw)
 
@@ -57,12 +57,12 @@ def test_autotune_dense_and_invalid():
     h = cvo.CVO(**kw)
     t = h.autotune(dev(p.X), dev(p.Z), p.T_true, dev(p.FX), dev(p.FZ))
     # dense: no grid, so only the work split is tuned
-    assert t["cell_factor"] == 0.5 and t["super_delta"] == 2 and t["items_per_sm"] in (4, 8, 16, 32)
+    assert t["cell_factor"] == 0.5 and t["super_delta"] == 2 and t["chunk_len"] in (48, 64, 96, 128)
     check_parity(h, p.X, p.Z, p.FX, p.FZ, p.T_true, kw)
     with pytest.raises(cvo.CvoError):
         h.apply_tuning(0.1, 2, 8)
     with pytest.raises(cvo.CvoError):
-        h.apply_tuning(0.5, 2, 0)
+        h.apply_tuning(0.5, 2, 8)
     # empty clouds: nothing to time, the tuning is unchanged
     before = h.tuning()
     t = h.autotune(dev(p.X[:0]), dev(p.Z), p.T_true, dev(p.FX[:0]), dev(p.FZ))
