@@ -142,7 +142,7 @@ struct cvo_handle_s {
     DevBuf part_stats, part_cnt, grp_stats, grp_cnt, grp_arrivals, pairs_dev, counters, trace;
     // gradients with respect to the inputs: device outputs for host callers,
     // per-query terms of dF/dl and their sum
-    DevBuf bw_out[4], bw_tq, bw_dell;
+    DevBuf bw_out[4], bw_tq, bw_dell, bw_part;
 
     std::vector<PairRes> pr;
     IterState* h_state = nullptr;   // pinned mirror(s)
@@ -1025,15 +1025,17 @@ cvo_status run_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     g.dense = h->dense;
     g.fc = h->fc;
     g.scale_pos = (float)(sc / (ell * ell));
-    g.scale_feat = (float)sc;
     g.scale_ell = (float)(sc / (ell * ell * ell));
-    for (int b = 0; b < p.n_blocks; ++b)
-        g.inv_lb2[b] = p.blocks[b].kind == CVO_FEAT_SE ? (float)(1.0 / (p.blocks[b].scale * p.blocks[b].scale)) : 0.0f;
+    for (int b = 0, col = 0; b < p.n_blocks; ++b)
+        for (int j = 0; j < p.blocks[b].dim; ++j, ++col)
+            g.feat_scale[col] = p.blocks[b].kind == CVO_FEAT_SE
+                                    ? (float)(-sc / (p.blocks[b].scale * p.blocks[b].scale))
+                                    : (float)sc;
     auto sweep = [&](int slot, const cvo_cloud* Q, const cvo_cloud* G, const double* Tq, bool rout_transpose,
                      float* pos, float* feat, float* tq) -> cvo_status {
         PairRes& P = h->pr[slot];
         CVO_TRY(prepare(h, P, Q, G, ell, ell));
-        CVO_TRY(init_state(h, P, slot, Tq, ell, 0, kNoPlan));
+        CVO_TRY(init_state(h, P, slot, Tq, ell, 0, kPlanned));
         g.levels = (const LevelDesc*)P.levels_dev.p;
         g.xrec = (const float4*)P.xrec.p;
         g.st = (const IterState*)P.state.p;
@@ -1043,8 +1045,10 @@ cvo_status run_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
         g.out_pos = pos;
         g.out_feat = D > 0 ? feat : nullptr;
         g.out_tq = tq;
-        const int ngroups = P.lv[0].ngroups;
-        const int nb = std::max(1, std::min((ngroups + kSweepWarps - 1) / kSweepWarps, h->num_sms * 16));
+        const int nitems = P.lv[0].nitems;
+        CVO_CUDA(ensure(h->bw_part, (size_t)std::max(nitems, 1) * 32 * (4 + D) * sizeof(float)));
+        g.part = (float*)h->bw_part.p;
+        const int nb = std::max(1, std::min((nitems + kSweepWarps - 1) / kSweepWarps, h->num_sms * 16));
         CVO_CUDA(launch_grad(g, nb, h->s));
         return CVO_OK;
     };
@@ -1241,7 +1245,7 @@ cvo_status cvo_destroy(cvo_handle h)
     DevBuf* bufs[] = {&h->stage_xyz[0], &h->stage_xyz[1], &h->stage_feat[0], &h->stage_feat[1], &h->keys, &h->vals,
                       &h->keys2, &h->vals2, &h->sort_tmp, &h->flags, &h->gidx, &h->misc, &h->part_stats, &h->part_cnt,
                       &h->grp_stats, &h->grp_cnt, &h->grp_arrivals, &h->pairs_dev, &h->counters, &h->trace,
-                      &h->bw_out[0], &h->bw_out[1], &h->bw_out[2], &h->bw_out[3], &h->bw_tq, &h->bw_dell};
+                      &h->bw_out[0], &h->bw_out[1], &h->bw_out[2], &h->bw_out[3], &h->bw_tq, &h->bw_dell, &h->bw_part};
     for (DevBuf* b : bufs) release(*b);
     for (PairRes& P : h->pr) P.free_all();
     for (cudaEvent_t e : h->evs) cudaEventDestroy(e);

@@ -189,15 +189,17 @@ struct GradArgs {
     FeatConst fc;
     float Rout[9];             // rotation from the sweep frame to the queries' frame (row major)
     float scale_pos;           // dF * kappa / l^2
-    float scale_feat;          // dF * kappa
     float scale_ell;           // dF * kappa / l^3
-    float inv_lb2[4];          // 1 / l_b^2 of the squared-exponential blocks
+    float feat_scale[64];      // per feature column: -dF kappa / l_b^2 (squared exponential), dF kappa (inner product)
+    float* part;               // per work item and lane: E (3), sum w d^2, feature sums (D)
     float* out_pos;            // N x 3, or NULL
     float* out_feat;           // N x D, or NULL
     float* out_tq;             // N per-query terms of dF/dl, or NULL
 };
-// One warp per query group over the group's whole candidate stream; every
-// query's outputs are written (zero when it has no pair in range).
+// The gradient sweep over the level's planned work items (raw sums per item
+// and lane into g.part, nitems x 32 x (4 + D) floats), then the per-group
+// reduction in chunk order; every query's outputs are written (zero when it
+// has no pair in range).
 cudaError_t launch_grad(const GradArgs& g, int nblocks, cudaStream_t s);
 // Deterministic sum of n floats into *out (one block).
 cudaError_t launch_sum_f32(const float* v, int n, double* out, cudaStream_t s);

@@ -148,12 +148,10 @@ struct GradFixed {
 #pragma unroll
         for (int k = 0; k < DDOT; ++k) a.a[DSE + k] = fmaf(base, c.v[DSE + k], a.a[DSE + k]);
     }
-    __device__ static void write(const Acc& a, const float*, const GradArgs& g, float* out)
+    __device__ static void store(const Acc& a, const float*, const FeatConst&, float* out)
     {
 #pragma unroll
-        for (int k = 0; k < DSE; ++k) out[k] = -g.scale_feat * g.inv_lb2[0] * a.a[k];
-#pragma unroll
-        for (int k = 0; k < DDOT; ++k) out[DSE + k] = g.scale_feat * a.a[DSE + k];
+        for (int k = 0; k < D; ++k) out[k] = a.a[k];
     }
 };
 
@@ -167,7 +165,7 @@ struct GradNone {
     __device__ static void zero(Acc&, float*, const FeatConst&) {}
     __device__ static float pair(const Q&, const float4*, float&, V&, const FeatConst&) { return 1.0f; }
     __device__ static void accum(Acc&, const Q&, const float4*, const V&, float, float, float*, const FeatConst&) {}
-    __device__ static void write(const Acc&, const float*, const GradArgs&, float*) {}
+    __device__ static void store(const Acc&, const float*, const FeatConst&, float*) {}
 };
 
 // Any block list: per-lane feature accumulators in shared memory (stride 32).
@@ -229,16 +227,16 @@ struct GradGeneric {
             }
         }
     }
-    __device__ static void write(const Acc&, const float* sacc, const GradArgs& g, float* out)
+    __device__ static void store(const Acc&, const float* sacc, const FeatConst& fc, float* out)
     {
-        for (int b = 0; b < g.fc.n_blocks; ++b) {
-            const int off = g.fc.off[b];
-            const float sc = g.fc.kind[b] == 0 ? -g.scale_feat * g.inv_lb2[b] : g.scale_feat;
-            for (int k = 0; k < g.fc.dim[b]; ++k) out[off + k] = sc * sacc[32 * (off + k)];
-        }
+        for (int k = 0; k < fc.D; ++k) out[k] = sacc[32 * k];
     }
 };
 
+// One warp per work item (chunk k of n of one query group's stream, from the
+// level's planned item table): every lane's raw sums over the chunk -- E (3),
+// sum w d^2, and the feature accumulators (D) -- go to the item's rows of
+// g.part; k_grad_reduce adds a group's chunks in chunk order.
 template <class G>
 __global__ void __launch_bounds__(kSweepWarps * 32) k_grad(GradArgs g)
 {
@@ -257,14 +255,17 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_grad(GradArgs g)
     const bool dense = g.dense != 0;
     const float sg = st->sg, rc = st->rc, rc2 = st->rc2;
     const FeatConst& fc = g.fc;
+    const int stride = 4 + fc.D;
     float4* stage = stage_mem + (size_t)warp * 2 * 32 * rs;
     float* sacc = nullptr;
     if constexpr (G::kSharedAcc)
         sacc = reinterpret_cast<float*>(stage_mem + (size_t)kSweepWarps * 2 * 32 * rs) + (size_t)warp * fc.D * 32 +
                lane;
 
-    for (int gi = blockIdx.x * kSweepWarps + warp; gi < L.ngroups; gi += gridDim.x * kSweepWarps) {
-        const int2 grp = L.groups[gi];
+    for (int item = blockIdx.x * kSweepWarps + warp; item < L.nitems; item += gridDim.x * kSweepWarps) {
+        const int4 w4 = L.items[item];
+        const int2 grp = make_int2(w4.x, w4.y);
+        const int k = w4.z, nch = w4.w;
         const bool act = lane < grp.y;
         const int qi = grp.x + (act ? lane : 0);
         const float4* qrec = g.xrec + (size_t)qi * rs;
@@ -277,11 +278,13 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_grad(GradArgs g)
         G::load_query(qf, qrec, fc);
         typename G::Acc fa;
         G::zero(fa, sacc, fc);
-        float W = 0.0f, E0 = 0.0f, E1 = 0.0f, E2 = 0.0f, TQ = 0.0f;
+        float E0 = 0.0f, E1 = 0.0f, E2 = 0.0f, TQ = 0.0f;
 
         Stream sm;
         if (stream_setup(L, g.m, dense, act, xh, rc, lane, sm) && sm.total > 0) {
-            stream_walk(L, g.m, dense, sm, 0, sm.total, rs, stage, lane, [&](const float4* sb, int cnt) {
+            const int clo_ = (int)(((long long)sm.total * k) / nch);
+            const int chi_ = (int)(((long long)sm.total * (k + 1)) / nch);
+            stream_walk(L, g.m, dense, sm, clo_, chi_, rs, stage, lane, [&](const float4* sb, int cnt) {
 #pragma unroll 1
                 for (int c = 0; c < cnt; ++c) {
                     const float4* zr = sb + c * rs;
@@ -297,31 +300,58 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_grad(GradArgs g)
                     const float mult = G::pair(qf, zr, arg, cv, fc);
                     const float base = in ? ex2(arg) : 0.0f;
                     const float w = base * mult;
-                    W += w;
                     E0 = fmaf(w, dx, E0);
                     E1 = fmaf(w, dy, E1);
                     E2 = fmaf(w, dz, E2);
                     TQ = fmaf(w, d2, TQ);
-                    if (in) {
-                        G::accum(fa, qf, zr, cv, base, w, sacc, fc);
-                    }
+                    if (in) G::accum(fa, qf, zr, cv, base, w, sacc, fc);
                 }
             });
         }
-        if (act) {
-            const int idx = __float_as_int(xq4.w);
-            const float Ev[3] = {E0, E1, E2};
-            if (g.out_pos) {
-#pragma unroll
-                for (int r = 0; r < 3; ++r)
-                    g.out_pos[3 * (size_t)idx + r] =
-                        g.scale_pos *
-                        fmaf(g.Rout[3 * r], Ev[0], fmaf(g.Rout[3 * r + 1], Ev[1], g.Rout[3 * r + 2] * Ev[2]));
-            }
-            if (g.out_tq) g.out_tq[idx] = g.scale_ell * TQ;
-            if (g.out_feat) G::write(fa, sacc, g, g.out_feat + (size_t)idx * fc.D);
-        }
+        float* row = g.part + ((size_t)item * 32 + lane) * stride;
+        row[0] = E0;
+        row[1] = E1;
+        row[2] = E2;
+        row[3] = TQ;
+        G::store(fa, sacc, fc, row + 4);
         __syncwarp();
+    }
+}
+
+// One warp per query group (the items with chunk 0): each lane adds its
+// query's chunk rows in chunk order and writes the gradients at the query's
+// index in the caller's order: dpos = scale_pos R_out E, the per-query term
+// of dF/dl = scale_ell sum w d^2, and the feature columns times their scale.
+__global__ void __launch_bounds__(128) k_grad_reduce(GradArgs g)
+{
+    const int lane = threadIdx.x & 31;
+    const int stride = 4 + g.fc.D;
+    const LevelDesc L = g.levels[g.st->level];
+    for (int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < L.nitems; item += (gridDim.x * blockDim.x) >> 5) {
+        const int4 w4 = L.items[item];
+        if (w4.z != 0) continue;   // warp-uniform
+        if (lane >= w4.y) continue;
+        const int idx = __float_as_int(g.xrec[(size_t)(w4.x + lane) * g.rs].w);
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int c = 0; c < w4.w; ++c) {
+            const float* row = g.part + ((size_t)(item + c) * 32 + lane) * stride;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[j] += row[j];
+        }
+        if (g.out_pos) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                g.out_pos[3 * (size_t)idx + r] =
+                    g.scale_pos * fmaf(g.Rout[3 * r], acc[0], fmaf(g.Rout[3 * r + 1], acc[1], g.Rout[3 * r + 2] * acc[2]));
+        }
+        if (g.out_tq) g.out_tq[idx] = g.scale_ell * acc[3];
+        if (g.out_feat) {
+            for (int j = 0; j < g.fc.D; ++j) {
+                float f = 0.0f;
+                for (int c = 0; c < w4.w; ++c) f += g.part[((size_t)(item + c) * 32 + lane) * stride + 4 + j];
+                g.out_feat[(size_t)idx * g.fc.D + j] = g.feat_scale[j] * f;
+            }
+        }
     }
 }
 
@@ -336,8 +366,9 @@ cudaError_t grad_t(const GradArgs& g, int nblocks, cudaStream_t s)
     }
     size_t smem = (size_t)kSweepWarps * 2 * 32 * g.rs * sizeof(float4);
     if (G::kSharedAcc) smem += (size_t)kSweepWarps * g.fc.D * 32 * sizeof(float);
-    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    g_launch_count.fetch_add(2, std::memory_order_relaxed);
     k_grad<G><<<nblocks, kSweepWarps * 32, smem, s>>>(g);
+    k_grad_reduce<<<nblocks, 128, 0, s>>>(g);
     return cudaGetLastError();
 }
 
