@@ -87,8 +87,6 @@ template <class Feat>
 __global__ void __launch_bounds__(kSweepWarps * 32, 4) k_register(PersistArgs a)
 {
     extern __shared__ float4 stage_mem[];   // [kSweepWarps][2][32][rs]
-    __shared__ float acc_s[kSweepWarps][kStatN][32];
-    __shared__ unsigned long long redc[kSweepWarps][2];
     __shared__ float cst[30];
     __shared__ double S[kStatN];
     __shared__ float Shi[kStatN], Slo[kStatN];
@@ -111,9 +109,9 @@ __global__ void __launch_bounds__(kSweepWarps * 32, 4) k_register(PersistArgs a)
         // the state as block 0 left it (read around the L1: another SM wrote it)
         if (threadIdx.x == 0) s_done = (int)__ldcg(&st->done);
         if (threadIdx.x < 30) cst[threadIdx.x] = __ldcg(&st->Ahi[0] + threadIdx.x);
-#pragma unroll
-        for (int k = 0; k < kStatN; ++k) acc_s[warp][k][lane] = 0.0f;
         __syncthreads();
+        StatAcc acc;
+        stat_acc_init(acc, lane);
         if (s_done) break;
         const int level = __ldcg(&st->level);
         const float sg = __ldcg(&st->sg), rc = __ldcg(&st->rc), rc2 = __ldcg(&st->rc2);
@@ -155,12 +153,9 @@ __global__ void __launch_bounds__(kSweepWarps * 32, 4) k_register(PersistArgs a)
             if (!sweep_chunk<Feat>(P, L, L.groups[g], k, n, cst, rs, dense, sg, rc, rc2, fc, stage, lane, mo, p, act,
                                    npairs, ncand))
                 continue;
-            if (act) {
-                float* acc = &acc_s[warp][0][lane];
-                for_each_stat(mo, p, [&](int s2, float v) { acc[s2 * 32] += v; });
-            }
+            stat_acc_add(acc, mo, p, act, lane);
         }
-        sweep_epilogue(acc_s, redc, npairs, ncand, a.sw, (int)blockIdx.x, (int)nblocks);
+        sweep_epilogue(acc, npairs, ncand, a.sw, (int)blockIdx.x, (int)nblocks);
         if (!grid_barrier(a.ctl, nblocks)) return;
 
         // ---- step (block 0) ---------------------------------------------------

@@ -39,8 +39,6 @@ template <class Feat>
 __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
 {
     extern __shared__ float4 stage_mem[];   // [kSweepWarps][2][32][rs]
-    __shared__ float acc_s[kSweepWarps][kStatN][32];
-    __shared__ unsigned long long redc[kSweepWarps][2];
     __shared__ float cst[30];               // Ahi, Alo, bhi, blo, chi, clo
     // the pair this block works on (blocks [b0, b1) of pair pi)
     int pi = 0;
@@ -58,9 +56,9 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
     if (st->done) return;   // uniform per pair; a single pair's blocks all return together
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x < 30) cst[threadIdx.x] = (&st->Ahi[0])[threadIdx.x];
-#pragma unroll
-    for (int k = 0; k < kStatN; ++k) acc_s[warp][k][lane] = 0.0f;
     __syncthreads();
+    StatAcc acc;
+    stat_acc_init(acc, lane);
     const LevelDesc L = P.levels[st->level];
     const int rs = a.rs;
     const bool dense = a.dense != 0;
@@ -77,13 +75,10 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
         bool act;
         if (!sweep_item<Feat>(P, L, item, cst, rs, dense, sg, rc, rc2, fc, stage, lane, mo, p, act, npairs, ncand))
             continue;
-        if (act) {
-            float* acc = &acc_s[warp][0][lane];
-            for_each_stat(mo, p, [&](int s, float v) { acc[s * 32] += v; });
-        }
+        stat_acc_add(acc, mo, p, act, lane);
     }
 
-    sweep_epilogue(acc_s, redc, npairs, ncand, a, (int)blockIdx.x, (int)gridDim.x);
+    sweep_epilogue(acc, npairs, ncand, a, (int)blockIdx.x, (int)gridDim.x);
 }
 
 // ---- gradients with respect to the inputs -----------------------------------

@@ -472,26 +472,80 @@ __device__ __forceinline__ void for_each_stat(const Moments& mo, const float p[3
         for (int c = 0; c < 3; ++c) f(ST_EP + 3 * rr + c, Ev[rr] * p[c]);
 }
 
-// End of a sweep block's work: the warps' per-lane statistics (acc_s) summed
-// in a fixed tree, the block's sums written as its partials (double-float),
-// and the group reduction: the last block of each group of kGroupBlocks
-// blocks to arrive sums the group's partials in block order (deterministic;
-// nothing waits) and resets the group's arrival counter for the next sweep.
-// block / nblocks: this block's index and the number of sweep blocks.
-__device__ __forceinline__ void sweep_epilogue(float (&acc_s)[kSweepWarps][kStatN][32],
-                                               unsigned long long (&redc)[kSweepWarps][2], unsigned npairs,
-                                               unsigned ncand, const SweepArgs& a, int block, int nblocks)
+// ---- the 43 statistics, summed over a warp after every work item ------------
+// The lanes' statistics of one item (48 slots, 43 used) are summed over the
+// warp in a fixed butterfly: each step keeps half of a lane's values and adds
+// the partner lane's copy of the same half.  Lane l ends with the sums of two
+// statistics whose indices depend on l only, so it keeps running sums of
+// those two across its work items (no per-lane table of 43 in shared memory).
+constexpr int kStatPad = 48;
+
+template <int H>
+__device__ __forceinline__ void stat_butterfly(float (&v)[kStatPad], int lane, int off)
 {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        const float keep = up ? v[j + H] : v[j];
+        const float send = up ? v[j] : v[j + H];
+        v[j] = keep + __shfl_xor_sync(kFull, send, off);
+    }
+}
+
+struct StatAcc {
+    float s0, s1;   // running sums of statistics i0, i1 (-1: none)
+    int i0, i1;
+};
+
+__device__ __forceinline__ void stat_acc_init(StatAcc& a, int lane)
+{
+    // halves kept at the butterfly steps over bits 4..1: 24, 12, 6, 3 slots;
+    // the last step splits the remaining 3 (padded to 4) over bit 0
+    const int base = ((lane >> 4) & 1) * 24 + ((lane >> 3) & 1) * 12 + ((lane >> 2) & 1) * 6 + ((lane >> 1) & 1) * 3;
+    const bool up = (lane & 1) != 0;
+    a.i0 = base + (up ? 2 : 0);
+    a.i1 = up ? -1 : base + 1;
+    if (a.i0 >= kStatN) a.i0 = -1;
+    if (a.i1 >= kStatN) a.i1 = -1;
+    a.s0 = 0.0f;
+    a.s1 = 0.0f;
+}
+
+// Adds one work item's statistics (zero for an inactive lane).  Warp-uniform.
+__device__ __forceinline__ void stat_acc_add(StatAcc& a, const Moments& mo, const float p[3], bool act, int lane)
+{
+    float v[kStatPad];
+#pragma unroll
+    for (int s = 0; s < kStatPad; ++s) v[s] = 0.0f;
+    if (act) for_each_stat(mo, p, [&](int s, float x) { v[s] = x; });
+    stat_butterfly<24>(v, lane, 16);
+    stat_butterfly<12>(v, lane, 8);
+    stat_butterfly<6>(v, lane, 4);
+    stat_butterfly<3>(v, lane, 2);
+    const bool up = (lane & 1) != 0;
+    const float a0 = up ? v[2] : v[0];
+    const float a1 = up ? 0.0f : v[1];
+    const float b0 = up ? v[0] : v[2];
+    const float b1 = up ? v[1] : 0.0f;
+    a.s0 += a0 + __shfl_xor_sync(kFull, b0, 1);
+    a.s1 += a1 + __shfl_xor_sync(kFull, b1, 1);
+}
+
+// End of a sweep block's work: the warps' running sums added over the block's
+// warps in double-float and written as the block's partials, and the group
+// reduction: the last block of each group of kGroupBlocks blocks to arrive
+// sums the group's partials in block order (deterministic; nothing waits)
+// and resets the group's arrival counter for the next sweep.
+// block / nblocks: this block's index and the number of sweep blocks.
+__device__ __forceinline__ void sweep_epilogue(const StatAcc& acc, unsigned npairs, unsigned ncand,
+                                               const SweepArgs& a, int block, int nblocks)
+{
+    __shared__ float red[kSweepWarps][kStatPad];
+    __shared__ unsigned long long redc[kSweepWarps][2];
     __shared__ int is_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // warp tree (FP32, fixed order), then the block's warps in double-float
-    __syncwarp();
-    for (int k = 0; k < kStatN; ++k) {
-        float v = acc_s[warp][k][lane];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-        if (lane == 0) acc_s[warp][k][0] = v;
-    }
+    if (acc.i0 >= 0) red[warp][acc.i0] = acc.s0;
+    if (acc.i1 >= 0) red[warp][acc.i1] = acc.s1;
     unsigned long long cp = npairs, cc = ncand;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -507,7 +561,7 @@ __device__ __forceinline__ void sweep_epilogue(float (&acc_s)[kSweepWarps][kStat
         float hi = 0.0f, lo = 0.0f;
         for (int w = 0; w < kSweepWarps; ++w) {
             float s, e;
-            two_sum(hi, acc_s[w][threadIdx.x][0], s, e);
+            two_sum(hi, red[w][threadIdx.x], s, e);
             e = __fadd_rn(e, lo);
             hi = __fadd_rn(s, e);
             lo = __fsub_rn(e, __fsub_rn(hi, s));
@@ -523,9 +577,6 @@ __device__ __forceinline__ void sweep_epilogue(float (&acc_s)[kSweepWarps][kStat
         a.part_cnt[(size_t)a.part_cap + block] = t1;
     }
 
-    // Group reduction: the last block of each group of kGroupBlocks blocks to
-    // arrive sums the group's partials in block order (deterministic; nothing
-    // waits) and resets the group's arrival counter for the next launch.
     if (a.grp_arrivals == nullptr) return;   // batch: the finalize sums the block partials per pair
     const int grp = block / kGroupBlocks;
     const int first = grp * kGroupBlocks;
