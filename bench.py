@@ -60,7 +60,8 @@ def load_peaks():
 
 def profile_traffic(kernel_src):
     """DRAM bytes per sweep launch from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
+    taken on the current kernel source (the files in kernel_src, hashed in
+    order); else None."""
     path = os.path.join(ROOT, "profiles", "sweep_street-20k.md")
     if not os.path.exists(path):
         return None
@@ -69,7 +70,8 @@ def profile_traffic(kernel_src):
     t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     if not m or not t:
         return None
-    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    data = b"".join(open(f, "rb").read() for f in kernel_src)
+    sha = hashlib.sha256(data).hexdigest()
     return float(t.group(1)) if sha == m.group(1) else None
 
 
@@ -454,7 +456,8 @@ def main():
     fpp = flops_per_pair(kw["blocks"])
     achieved = sweep_pairs * fpp / (sweep_ms * 1e-3) / 1e12 if sweep_ms > 0 else None
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    traffic = profile_traffic(os.path.join(ROOT, "paper_2012_03683_gb300", "csrc", "cvo_sweep.cu"))
+    csrc = os.path.join(ROOT, "paper_2012_03683_gb300", "csrc")
+    traffic = profile_traffic([os.path.join(csrc, "cvo_sweep.cu"), os.path.join(csrc, "cvo_sweep_dev.cuh")])
     dT = np.linalg.inv(T_last) @ p.T_true
     pose_err = {"rot_rad": float(math.acos(max(-1.0, min(1.0, (np.trace(dT[:3, :3]) - 1.0) / 2.0)))),
                 "trans_m": float(np.linalg.norm(dT[:3, 3]))}

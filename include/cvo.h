@@ -250,13 +250,14 @@ typedef struct {
 /* Autotuner: prepares the pair (X, Z) under each tuning of a small grid
  * (cell_factor 0.35 / 0.5 / 0.7 / 1.0 and super_delta 1 / 2 / 3; chunk_len
  * stays as set; with cutoff_mult <= 0 there is no grid to tune and the
- * tuning stays as it is), times its
- * sweep at pose T and lengthscale params.ell with CUDA events (best of 3,
- * with a registration's work split),
- * keeps the fastest on the handle and returns it in *out.  Results do not
- * depend on the tuning beyond rounding; every tuning's F is checked against
- * the first (CVO_ERR_CUDA if they differ by more than 1e-4 relative).  Costs
- * one setup and four sweeps per tuning (tens of milliseconds). */
+ * tuning stays as it is), times its sweep at pose T with CUDA events (best
+ * of 3, with a registration's work split) at lengthscale params.ell and,
+ * when annealing, at the smallest lengthscale a registration can reach,
+ * keeps the tuning with the least total time on the handle and returns it
+ * in *out (sweep_ms: that total).  Results do not depend on the tuning
+ * beyond rounding; every tuning's F is checked against the first
+ * (CVO_ERR_CUDA if they differ by more than 1e-4 relative).  Costs one setup
+ * and up to eight sweeps per tuning (tens of milliseconds). */
 cvo_status cvo_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], cvo_tuning* out);
 
 /* The handle's current tuning (sweep_ms = 0), and setting it (validated as

@@ -1086,9 +1086,9 @@ cvo_status run_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
 
 // Times the sweep of one prepared pair at pose T (eval mode): the best of
 // `reps` launches, CUDA events on the handle's stream.
-cvo_status time_sweep(cvo_handle h, PairRes& P, const double* T, int reps, double* ms, double* F)
+cvo_status time_sweep(cvo_handle h, PairRes& P, const double* T, double ell, int reps, double* ms, double* F)
 {
-    CVO_TRY(init_state(h, P, 0, T, h->p.ell, 0, h->dense ? kPlanned : kUniform));   // as a registration sweeps
+    CVO_TRY(init_state(h, P, 0, T, ell, 0, h->dense ? kPlanned : kUniform));   // as a registration sweeps
     const int nb = single_pair_blocks(h, P);
     SweepArgs a;
     CVO_TRY(setup_sweep(h, std::vector<PairDesc>{pair_desc(P, 0, nb)}, nb, &a, true));
@@ -1132,6 +1132,7 @@ cvo_status run_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     }
     CVO_TRY(begin_call(h, rec_bf16_of(h->p, X, Z), 1));
     PairRes& P = h->pr[0];
+    const double ell_lo = reachable_ell_lo(h->p);
     double F_ref = 0.0;
     bool have_ref = false;
     cvo_status st = CVO_OK;
@@ -1144,11 +1145,18 @@ cvo_status run_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
                 h->cell_factor = cf;
                 h->super_delta = sd;
                 h->chunk_len = ip;
-                st = prepare(h, P, X, Z, h->p.ell, h->p.ell);
+                // the grid levels of a registration; timed at its first and
+                // its smallest reachable lengthscale
+                st = prepare(h, P, X, Z, h->p.ell, ell_lo);
                 if (st < 0) break;
-                double ms = 0.0, F = 0.0;
-                st = time_sweep(h, P, T, 3, &ms, &F);
+                double ms = 0.0, F = 0.0, ms_lo = 0.0, F_lo = 0.0;
+                st = time_sweep(h, P, T, h->p.ell, 3, &ms, &F);
                 if (st < 0) break;
+                if (ell_lo < h->p.ell) {
+                    st = time_sweep(h, P, T, ell_lo, 3, &ms_lo, &F_lo);
+                    if (st < 0) break;
+                    ms += ms_lo;
+                }
                 if (!have_ref) {
                     F_ref = F;
                     have_ref = true;
