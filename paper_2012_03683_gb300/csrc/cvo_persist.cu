@@ -150,8 +150,8 @@ __global__ void __launch_bounds__(kSweepWarps * 32, 4) k_register(PersistArgs a)
             Moments mo;
             float p[3];
             bool act;
-            if (!sweep_chunk<Feat>(P, L, L.groups[g], k, n, cst, rs, dense, sg, rc, rc2, fc, stage, lane, mo, p, act,
-                                   npairs, ncand))
+            if (!sweep_chunk<Feat>(P, L, L.groups[g], k, n, cst, rs, dense, sg, rc, rc2, fc, stage, nullptr, lane, mo, p,
+                                   act, npairs, ncand))
                 continue;
             stat_acc_add(acc, mo, p, act, lane);
         }

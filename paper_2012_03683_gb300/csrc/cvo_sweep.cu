@@ -65,6 +65,8 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
     const float sg = st->sg, rc = st->rc, rc2 = st->rc2;
     const FeatConst fc = a.fc;
     float4* stage = stage_mem + (size_t)warp * 2 * 32 * rs;
+    unsigned char* scratch =
+        reinterpret_cast<unsigned char*>(stage_mem + (size_t)kSweepWarps * 2 * 32 * rs) + (size_t)warp * Feat::kScratch;
     unsigned npairs = 0, ncand = 0;
 
     const int nitems = L.nitems;
@@ -73,7 +75,8 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
         Moments mo;
         float p[3];
         bool act;
-        if (!sweep_item<Feat>(P, L, item, cst, rs, dense, sg, rc, rc2, fc, stage, lane, mo, p, act, npairs, ncand))
+        if (!sweep_item<Feat>(P, L, item, cst, rs, dense, sg, rc, rc2, fc, stage, scratch, lane, mo, p, act, npairs,
+                              ncand))
             continue;
         stat_acc_add(acc, mo, p, act, lane);
     }
@@ -107,7 +110,7 @@ struct GradFixed {
     struct Acc {
         float a[D > 0 ? D : 1];   // SE entries: sum w (u - v); inner-product entries: sum w_(b) v
     };
-    __device__ static void load_query(Q& q, const float4* rec, const FeatConst& fc) { F::load_query(q, rec, fc); }
+    __device__ static void load_query(Q& q, const float4* rec, const FeatConst& fc) { F::load_query(q, rec, fc, nullptr, 0); }
     __device__ static void zero(Acc& a, float*, const FeatConst&)
     {
 #pragma unroll
@@ -435,7 +438,7 @@ cudaError_t info_t(int rs, SweepLaunch* out)
         attr_set = true;
     }
     out->func = (const void*)k_sweep<Feat>;
-    out->smem = (size_t)kSweepWarps * 2 * 32 * rs * sizeof(float4);
+    out->smem = (size_t)kSweepWarps * 2 * 32 * rs * sizeof(float4) + (size_t)kSweepWarps * Feat::kScratch;
     return cudaSuccess;
 }
 
@@ -448,10 +451,11 @@ cudaError_t sweep_launch_info(const FeatConst& f, int rs, SweepLaunch* out)
     const bool se3 = f.n_blocks >= 1 && f.kind[0] == 0 && f.dim[0] == 3;
     if (f.n_blocks == 1 && se3)
         return f.bf16 ? info_t<FeatFixed<3, 0, true>>(rs, out) : info_t<FeatFixed<3, 0, false>>(rs, out);
+    // bfloat16 labels: the label inner products on the tensor cores
     if (f.n_blocks == 2 && se3 && f.kind[1] == 1 && f.dim[1] == 19)
-        return f.bf16 ? info_t<FeatFixed<3, 19, true>>(rs, out) : info_t<FeatFixed<3, 19, false>>(rs, out);
+        return f.bf16 ? info_t<FeatMMA<3>>(rs, out) : info_t<FeatFixed<3, 19, false>>(rs, out);
     if (f.n_blocks == 1 && f.kind[0] == 1 && f.dim[0] == 19)
-        return f.bf16 ? info_t<FeatFixed<0, 19, true>>(rs, out) : info_t<FeatFixed<0, 19, false>>(rs, out);
+        return f.bf16 ? info_t<FeatMMA<0>>(rs, out) : info_t<FeatFixed<0, 19, false>>(rs, out);
     return info_t<FeatGeneric>(rs, out);
 }
 

@@ -61,16 +61,23 @@ __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wai
 // the candidates from the shared-memory staging buffer.
 
 // Eq. (geometric_only): no features, c_ij = 1.
+// Interface of a feature policy: kScratch bytes of shared memory per warp;
+// load_query once per work item; batch once per staged batch of candidates
+// (warp-uniform); pair per candidate c of the batch, adding the feature
+// exponent to arg and returning the product of the inner-product factors.
 struct FeatNone {
+    static constexpr int kScratch = 0;
     struct Q {};
-    __device__ static void load_query(Q&, const float4*, const FeatConst&) {}
-    __device__ static float pair(const Q&, const float4*, float&, const FeatConst&) { return 1.0f; }
+    __device__ static void load_query(Q&, const float4*, const FeatConst&, unsigned char*, int) {}
+    __device__ static void batch(Q&, const float4*, int, int, int) {}
+    __device__ static float pair(const Q&, const float4*, int, float&, const FeatConst&) { return 1.0f; }
 };
 
 // One squared-exponential block (Eq. newscalar) of DSE entries followed by
 // one inner-product block (Eq. scalar) of DDOT entries; either may be empty.
 template <int DSE, int DDOT, bool BF16>
 struct FeatFixed {
+    static constexpr int kScratch = 0;
     static constexpr int D = DSE + DDOT;
     static constexpr int kVec = BF16 ? (2 * D + 15) / 16 : (4 * D + 15) / 16;
     struct Q {
@@ -99,8 +106,12 @@ struct FeatFixed {
             for (int k = 0; k < D; ++k) v[k] = f[k];
         }
     }
-    __device__ static void load_query(Q& q, const float4* rec, const FeatConst&) { unpack(rec + 1, q.v); }
-    __device__ static float pair(const Q& q, const float4* rec, float& arg, const FeatConst& fc)
+    __device__ static void load_query(Q& q, const float4* rec, const FeatConst&, unsigned char*, int)
+    {
+        unpack(rec + 1, q.v);
+    }
+    __device__ static void batch(Q&, const float4*, int, int, int) {}
+    __device__ static float pair(const Q& q, const float4* rec, int, float& arg, const FeatConst& fc)
     {
         float v[D];
         unpack(rec + 1, v);
@@ -125,6 +136,7 @@ struct FeatFixed {
 
 // Any block list (up to 4 blocks, 64 entries): features read per pair.
 struct FeatGeneric {
+    static constexpr int kScratch = 0;
     struct Q {
         const float4* rec;
     };
@@ -133,8 +145,9 @@ struct FeatGeneric {
         if (bf16) return __uint_as_float(((unsigned)reinterpret_cast<const unsigned short*>(rec + 1)[k]) << 16);
         return reinterpret_cast<const float*>(rec + 1)[k];
     }
-    __device__ static void load_query(Q& q, const float4* rec, const FeatConst&) { q.rec = rec; }
-    __device__ static float pair(const Q& q, const float4* rec, float& arg, const FeatConst& fc)
+    __device__ static void load_query(Q& q, const float4* rec, const FeatConst&, unsigned char*, int) { q.rec = rec; }
+    __device__ static void batch(Q&, const float4*, int, int, int) {}
+    __device__ static float pair(const Q& q, const float4* rec, int, float& arg, const FeatConst& fc)
     {
         float mult = 1.0f;
         for (int b = 0; b < fc.n_blocks; ++b) {
@@ -153,6 +166,151 @@ struct FeatGeneric {
             else mult *= acc;
         }
         return mult;
+    }
+};
+
+// One squared-exponential block of DSE entries (0 or 3) and one inner-product
+// block of 19 labels, stored in bfloat16: the label inner products of a
+// warp's 32 queries with a staged batch of 32 candidates form a 32 x 32 x 19
+// contraction, done on the tensor cores (mma.sync m16n8k16, bfloat16 inputs,
+// float32 accumulation: the products of bfloat16 values are exact, so this
+// matches the scalar float32 sum up to its order).  Per warp scratch: a
+// 32 x 40 bfloat16 tile (the queries' labels once per item, then each
+// batch's candidate labels) and the 32 x 33 float results.
+template <int DSE>
+struct FeatMMA {
+    static constexpr int kL = 19;
+    static constexpr int D = DSE + kL;
+    static constexpr int kRowBytes = 80;                      // 32 labels + pad: conflict-free fragment loads
+    static constexpr int kTileBytes = 32 * kRowBytes;
+    static constexpr int kCsStride = 33;
+    static constexpr int kScratch = kTileBytes + 32 * kCsStride * 4;
+    struct Q {
+        float se[DSE > 0 ? DSE : 1];
+        unsigned a[2][2][4];        // A fragments [m tile][k step][register]
+        unsigned char* tile;
+        float* cs;
+        int lane;
+    };
+    // label pairs (l, l + 1), l = 0, 2, ..., 30 (zero past the 19th) of a
+    // record's bfloat16 feature row
+    __device__ static void label_pairs(const float4* feat, unsigned (&out)[16])
+    {
+        unsigned w[12];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint4 u = reinterpret_cast<const uint4*>(feat)[k];
+            w[4 * k] = u.x; w[4 * k + 1] = u.y; w[4 * k + 2] = u.z; w[4 * k + 3] = u.w;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int l = 2 * j;
+            if (l >= 20) {
+                out[j] = 0u;
+            } else if constexpr (DSE & 1) {
+                out[j] = __byte_perm(w[(DSE + l) >> 1], w[((DSE + l) >> 1) + 1], 0x5432);
+            } else {
+                out[j] = w[(DSE + l) >> 1];
+            }
+        }
+        // the 20th entry of the last pair is the row's zero padding (or, with
+        // an odd DSE, the next feature slot, also padding)
+    }
+    __device__ static void store_row(unsigned char* tile, int row, const unsigned (&v)[16])
+    {
+        uint4* dst = reinterpret_cast<uint4*>(tile + row * kRowBytes);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dst[k] = make_uint4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    }
+    __device__ static unsigned word(const unsigned char* tile, int row, int col)
+    {
+        return reinterpret_cast<const unsigned*>(tile + row * kRowBytes)[col];
+    }
+    __device__ static void load_query(Q& q, const float4* rec, const FeatConst&, unsigned char* scratch, int lane)
+    {
+        q.tile = scratch;
+        q.cs = reinterpret_cast<float*>(scratch + kTileBytes);
+        q.lane = lane;
+        if constexpr (DSE > 0) {
+            const uint4 u = reinterpret_cast<const uint4*>(rec + 1)[0];
+            const unsigned w[2] = {u.x, u.y};
+#pragma unroll
+            for (int k = 0; k < DSE; ++k)
+                q.se[k] = (k & 1) ? __uint_as_float(w[k >> 1] & 0xffff0000u) : __uint_as_float(w[k >> 1] << 16);
+        }
+        unsigned v[16];
+        label_pairs(rec + 1, v);
+        __syncwarp();
+        store_row(q.tile, lane, v);
+        __syncwarp();
+        const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                q.a[mt][ks][0] = word(q.tile, g + 16 * mt, t + 8 * ks);
+                q.a[mt][ks][1] = word(q.tile, g + 8 + 16 * mt, t + 8 * ks);
+                q.a[mt][ks][2] = word(q.tile, g + 16 * mt, t + 4 + 8 * ks);
+                q.a[mt][ks][3] = word(q.tile, g + 8 + 16 * mt, t + 4 + 8 * ks);
+            }
+        __syncwarp();
+    }
+    // the 32 x 32 label inner products of the batch, into cs (query-major)
+    __device__ static void batch(Q& q, const float4* sb, int cnt, int rs, int lane)
+    {
+        unsigned v[16];
+        if (lane < cnt) {
+            label_pairs(sb + (size_t)lane * rs + 1, v);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = 0u;
+        }
+        store_row(q.tile, lane, v);
+        __syncwarp();
+        const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            unsigned b[2][2];
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                b[ks][0] = word(q.tile, g + 8 * nt, t + 8 * ks);
+                b[ks][1] = word(q.tile, g + 8 * nt, t + 4 + 8 * ks);
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, c3 = 0.0f;
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks)
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                        "{%8, %9}, {%0, %1, %2, %3};\n"
+                        : "+f"(c0), "+f"(c1), "+f"(c2), "+f"(c3)
+                        : "r"(q.a[mt][ks][0]), "r"(q.a[mt][ks][1]), "r"(q.a[mt][ks][2]), "r"(q.a[mt][ks][3]),
+                          "r"(b[ks][0]), "r"(b[ks][1]));
+                const int r0 = g + 16 * mt, col = 2 * t + 8 * nt;
+                q.cs[r0 * kCsStride + col] = c0;
+                q.cs[r0 * kCsStride + col + 1] = c1;
+                q.cs[(r0 + 8) * kCsStride + col] = c2;
+                q.cs[(r0 + 8) * kCsStride + col + 1] = c3;
+            }
+        }
+        __syncwarp();
+    }
+    __device__ static float pair(const Q& q, const float4* rec, int c, float& arg, const FeatConst& fc)
+    {
+        if constexpr (DSE > 0) {
+            const uint4 u = reinterpret_cast<const uint4*>(rec + 1)[0];
+            const unsigned w[2] = {u.x, u.y};
+            float du2 = 0.0f;
+#pragma unroll
+            for (int k = 0; k < DSE; ++k) {
+                const float v = (k & 1) ? __uint_as_float(w[k >> 1] & 0xffff0000u) : __uint_as_float(w[k >> 1] << 16);
+                const float d = q.se[k] - v;
+                du2 = fmaf(d, d, du2);
+            }
+            arg = fmaf(du2, fc.s[0], arg);
+        }
+        return q.cs[q.lane * kCsStride + c];
     }
 };
 
@@ -335,10 +493,11 @@ __device__ __forceinline__ void add_moments(Moments& mo, float w, const Offset& 
 // independent chains (staged loads, feature products, ex2), which hides
 // latency at this kernel's occupancy; a pair with no lane in range is skipped.
 template <class Feat>
-__device__ __forceinline__ void eval_batch(const float4* sb, int cnt, int rs, const typename Feat::Q& qf,
+__device__ __forceinline__ void eval_batch(const float4* sb, int cnt, int rs, typename Feat::Q& qf,
                                            const float xh[3], const float xl[3], bool act, bool dense, float sg,
-                                           float rc2, const FeatConst& fc, Moments& mo, unsigned& npairs)
+                                           float rc2, const FeatConst& fc, Moments& mo, unsigned& npairs, int lane)
 {
+    Feat::batch(qf, sb, cnt, rs, lane);
     int c = 0;
     for (; c + 1 < cnt; c += 2) {
         const float4* zr0 = sb + c * rs;
@@ -349,8 +508,8 @@ __device__ __forceinline__ void eval_batch(const float4* sb, int cnt, int rs, co
         const bool in1 = act && (dense || o1.d2 <= rc2);
         if (__any_sync(kFull, in0 || in1)) {
             float a0 = o0.d2 * sg, a1 = o1.d2 * sg;
-            const float m0 = Feat::pair(qf, zr0, a0, fc);
-            const float m1 = Feat::pair(qf, zr1, a1, fc);
+            const float m0 = Feat::pair(qf, zr0, c, a0, fc);
+            const float m1 = Feat::pair(qf, zr1, c + 1, a1, fc);
             const float w0 = in0 ? ex2(a0) * m0 : 0.0f;
             const float w1 = in1 ? ex2(a1) * m1 : 0.0f;
             npairs += (in0 ? 1u : 0u) + (in1 ? 1u : 0u);
@@ -364,7 +523,7 @@ __device__ __forceinline__ void eval_batch(const float4* sb, int cnt, int rs, co
         const bool in = act && (dense || o.d2 <= rc2);
         if (__any_sync(kFull, in)) {
             float arg = o.d2 * sg;
-            const float mult = Feat::pair(qf, zr, arg, fc);
+            const float mult = Feat::pair(qf, zr, c, arg, fc);
             const float w = in ? ex2(arg) * mult : 0.0f;
             npairs += in ? 1u : 0u;
             add_moments(mo, w, o);
@@ -379,8 +538,9 @@ __device__ __forceinline__ void eval_batch(const float4* sb, int cnt, int rs, co
 template <class Feat>
 __device__ __forceinline__ bool sweep_chunk(const PairDesc& P, const LevelDesc& L, int2 grp, int k, int nch,
                                             const float* cst, int rs, bool dense, float sg, float rc, float rc2,
-                                            const FeatConst& fc, float4* stage, int lane, Moments& mo, float p[3],
-                                            bool& act, unsigned& npairs, unsigned& ncand, int chunk_min = 0)
+                                            const FeatConst& fc, float4* stage, unsigned char* scratch, int lane,
+                                            Moments& mo, float p[3], bool& act, unsigned& npairs, unsigned& ncand,
+                                            int chunk_min = 0)
 {
     const float* Ahi = cst;
     const float* Alo = cst + 9;
@@ -408,10 +568,10 @@ __device__ __forceinline__ bool sweep_chunk(const PairDesc& P, const LevelDesc& 
     const int chi_ = (int)(((long long)total * (k + 1)) / nch);
 
     typename Feat::Q qf;
-    Feat::load_query(qf, qrec, fc);
+    Feat::load_query(qf, qrec, fc, scratch, lane);
     mo = Moments{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     stream_walk(L, P.m, dense, sm, clo_, chi_, rs, stage, lane, [&](const float4* sb, int cnt) {
-        eval_batch<Feat>(sb, cnt, rs, qf, xh, xl, act, dense, sg, rc2, fc, mo, npairs);
+        eval_batch<Feat>(sb, cnt, rs, qf, xh, xl, act, dense, sg, rc2, fc, mo, npairs, lane);
         ncand += act ? (unsigned)cnt : 0u;
     });
     p[0] = (xh[0] - chi[0]) + (xl[0] - clo[0]);
@@ -424,12 +584,12 @@ __device__ __forceinline__ bool sweep_chunk(const PairDesc& P, const LevelDesc& 
 template <class Feat>
 __device__ __forceinline__ bool sweep_item(const PairDesc& P, const LevelDesc& L, int item, const float* cst, int rs,
                                            bool dense, float sg, float rc, float rc2, const FeatConst& fc,
-                                           float4* stage, int lane, Moments& mo, float p[3], bool& act,
-                                           unsigned& npairs, unsigned& ncand)
+                                           float4* stage, unsigned char* scratch, int lane, Moments& mo, float p[3],
+                                           bool& act, unsigned& npairs, unsigned& ncand)
 {
     const int4 w = L.items[item];
-    return sweep_chunk<Feat>(P, L, make_int2(w.x, w.y), w.z, w.w, cst, rs, dense, sg, rc, rc2, fc, stage, lane, mo, p,
-                             act, npairs, ncand, L.chunk_min);
+    return sweep_chunk<Feat>(P, L, make_int2(w.x, w.y), w.z, w.w, cst, rs, dense, sg, rc, rc2, fc, stage, scratch, lane,
+                             mo, p, act, npairs, ncand, L.chunk_min);
 }
 
 // The 43 linear statistics of one query's moments about the lever centre
