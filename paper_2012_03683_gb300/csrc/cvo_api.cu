@@ -671,8 +671,9 @@ cvo_status run_eval(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const 
 }
 
 // Builds, instantiates and launches the graph of a registration loop: a WHILE
-// conditional node whose body is (sweep, finalize); the finalize (single pair)
-// or the batched finalize's last block (batch) clears the condition.
+// conditional node whose body is (sweep, finalize, sweep, finalize); the
+// finalize (single pair) or the batched finalize's last block (batch) clears
+// the condition.
 cvo_status run_graph_loop(cvo_handle h, const SweepArgs& a, bool batch, IterState* st_single, double* trace,
                           long long trace_stride)
 {
@@ -743,8 +744,13 @@ cvo_status run_graph_loop(cvo_handle h, const SweepArgs& a, bool batch, IterStat
         fpn.kernel.gridDim = dim3(1);
         fpn.kernel.kernelParams = fp1;
     }
-    cudaGraphNode_t fn;
+    // two iterations per pass of the loop body (halves the conditional
+    // node's per-pass overhead; a sweep or step after the last iteration
+    // sees the state done and returns at once)
+    cudaGraphNode_t fn, sn2, fn2;
     if (!check(cudaGraphAddNode(&fn, body, &sn, nullptr, 1, &fpn), "finalize node")) return cleanup(), status;
+    if (!check(cudaGraphAddNode(&sn2, body, &fn, nullptr, 1, &kp), "sweep node")) return cleanup(), status;
+    if (!check(cudaGraphAddNode(&fn2, body, &sn2, nullptr, 1, &fpn), "finalize node")) return cleanup(), status;
     if (!check(cudaGraphInstantiate(&ge, g, 0), "instantiate")) return cleanup(), status;
     if (!check(cudaGraphLaunch(ge, h->s), "launch")) return cleanup(), status;
     check(cudaStreamSynchronize(h->s), "synchronize");
@@ -864,7 +870,8 @@ cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     std::memcpy(T_out, st->T, 16 * sizeof(double));
     fill_info(st, &inf);
     h->last_iters = st->iter;
-    if (graph) g_launch_count.fetch_add(2LL * st->iter, std::memory_order_relaxed);
+    // four kernels per pass of the graph's loop body, two iterations a pass
+    if (graph) g_launch_count.fetch_add(4LL * ((st->iter + 1) / 2), std::memory_order_relaxed);
     (void)kernel_launches;
     if (h->timing && persistent) {
         // the persistent kernel as a whole (sweeps and steps), per iteration
@@ -971,7 +978,7 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
         if (st->status != 0) worst = CVO_NOT_CONVERGED;
         max_it = std::max(max_it, st->iter);
     }
-    if (graph) g_launch_count.fetch_add(2LL * max_it, std::memory_order_relaxed);
+    if (graph) g_launch_count.fetch_add(4LL * ((max_it + 1) / 2), std::memory_order_relaxed);
     if (h->timing) {
         h->sweep_ms = sum_sweep_events(h, max_it);
         h->sweep_n = max_it;
