@@ -40,7 +40,7 @@ class _Kernel(ctypes.Structure):
     _fields_ = [("ell", ctypes.c_double), ("sigma", ctypes.c_double), ("cutoff_mult", ctypes.c_double),
                 ("n_blocks", ctypes.c_int), ("dim", ctypes.c_int * MAX_BLOCKS),
                 ("kind", ctypes.c_int * MAX_BLOCKS), ("scale", ctypes.c_double * MAX_BLOCKS),
-                ("sigk", ctypes.c_double * MAX_BLOCKS)]
+                ("sigk", ctypes.c_double * MAX_BLOCKS), ("feat_cutoff_mult", ctypes.c_double)]
 
 
 class _Cloud(ctypes.Structure):
@@ -94,11 +94,12 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def _kernel(blocks, ell, cutoff_mult, sigma):
+def _kernel(blocks, ell, cutoff_mult, sigma, feat_cutoff_mult=0.0):
     k = _Kernel()
     k.ell = float(ell)
     k.sigma = float(sigma)
     k.cutoff_mult = float(cutoff_mult)
+    k.feat_cutoff_mult = float(feat_cutoff_mult)
     k.n_blocks = len(blocks)
     if len(blocks) > MAX_BLOCKS:
         raise ValueError("at most 4 feature blocks")
@@ -126,7 +127,7 @@ def _cloud(P, F, keep):
 
 
 def evaluate(X, Z, T, *, FX=None, FZ=None, blocks=(), ell, cutoff_mult=0.0, sigma=1.0,
-             direction=None, nthreads=0):
+             direction=None, nthreads=0, feat_cutoff_mult=0.0):
     """Brute-force F, its se(3) gradient (omega, v) and, when ``direction`` is
     given, the second derivative of t -> F(exp(t direction^) T) at t = 0.
     ``gscale`` is the sum of the norms of the gradient's per-pair terms.
@@ -135,7 +136,7 @@ def evaluate(X, Z, T, *, FX=None, FZ=None, blocks=(), ell, cutoff_mult=0.0, sigm
     keep = []
     cx = _cloud(X, FX, keep)
     cz = _cloud(Z, FZ, keep)
-    k = _kernel(list(blocks), ell, cutoff_mult, sigma)
+    k = _kernel(list(blocks), ell, cutoff_mult, sigma, feat_cutoff_mult)
     Tm = _f64(T).reshape(4, 4)
     out = np.zeros(9)
     npairs = ctypes.c_longlong(0)
@@ -201,13 +202,14 @@ def se3_log(T):
 
 def register(X, Z, T_init, *, FX=None, FZ=None, blocks=(), ell, ell_min=None, cutoff_mult=0.0, sigma=1.0,
              max_iters=50, anneal=False, decay=0.98, indicator_tol=1e-3, step_tol_rot=1e-5,
-             step_tol_trans=1e-5, max_step_rot=0.1, max_step_trans=0.0, replay=None, nthreads=0):
+             step_tol_trans=1e-5, max_step_rot=0.1, max_step_trans=0.0, replay=None, nthreads=0,
+             feat_cutoff_mult=0.0):
     """Registration loop (see cvo_oracle.c).  Returns (T_out, info dict, trace array)."""
     lib = _load()
     keep = []
     cx = _cloud(X, FX, keep)
     cz = _cloud(Z, FZ, keep)
-    k = _kernel(list(blocks), ell, cutoff_mult, sigma)
+    k = _kernel(list(blocks), ell, cutoff_mult, sigma, feat_cutoff_mult)
     r = _Reg(ell_init=float(ell), ell_min=float(ell if ell_min is None else ell_min), decay=float(decay),
              indicator_tol=float(indicator_tol), max_iters=int(max_iters), anneal=int(bool(anneal)),
              step_tol_rot=float(step_tol_rot), step_tol_trans=float(step_tol_trans),
@@ -233,7 +235,8 @@ def register(X, Z, T_init, *, FX=None, FZ=None, blocks=(), ell, ell_min=None, cu
     return Tout, d, trace[: info.iters].copy()
 
 
-def backward(X, Z, T, *, FX=None, FZ=None, blocks=(), ell, cutoff_mult=0.0, sigma=1.0, nthreads=0):
+def backward(X, Z, T, *, FX=None, FZ=None, blocks=(), ell, cutoff_mult=0.0, sigma=1.0, nthreads=0,
+             feat_cutoff_mult=0.0):
     """Gradients of F with respect to X, Z (float64, (N,3), (M,3)), the
     features (N,D), (M,D) and the lengthscale, for the pairs inside the
     cutoff (see cvo_oracle.c).  Returns a dict."""
@@ -242,7 +245,7 @@ def backward(X, Z, T, *, FX=None, FZ=None, blocks=(), ell, cutoff_mult=0.0, sigm
     keep = []
     cx = _cloud(X, FX, keep)
     cz = _cloud(Z, FZ, keep)
-    k = _kernel(list(blocks), ell, cutoff_mult, sigma)
+    k = _kernel(list(blocks), ell, cutoff_mult, sigma, feat_cutoff_mult)
     D = sum(int(b[1]) for b in blocks)
     Tm = _f64(T).reshape(4, 4)
     dX = np.zeros((cx.n, 3))

@@ -22,7 +22,11 @@
  *
  * A pair enters the sum when the cutoff is off (cutoff_mult <= 0) or when
  * |x_i - y_j|^2 <= (cutoff_mult * l)^2 (inclusive, in double precision).  The
- * paper says the sum is sparse (Sec. III-B) but fixes no threshold.
+ * paper says the sum is sparse (Sec. III-B) but fixes no threshold.  The same
+ * passage names pairs far apart in feature space as the other source of
+ * sparsity: with feat_cutoff_mult > 0 a pair also needs, for every
+ * squared-exponential block k, |u_k - v_k|^2 <= (feat_cutoff_mult * l_k)^2
+ * (off by default: it changes F).
  *
  * The gradient, the second derivative, the step rule and the stopping rules
  * are not printed in the paper (it cites gradient ascent on the Lie group,
@@ -59,6 +63,7 @@ typedef struct {
     int kind[ORC_MAX_BLOCKS];     /* 0: squared exponential, Eq. (newscalar); 1: inner product, Eq. (scalar) */
     double scale[ORC_MAX_BLOCKS]; /* l_k of a squared-exponential block */
     double sigk[ORC_MAX_BLOCKS];  /* sigma_k of a squared-exponential block */
+    double feat_cutoff_mult;      /* > 0: squared-exponential blocks need |u-v| <= feat_cutoff_mult*l_k */
 } orc_kernel;
 
 typedef struct {
@@ -96,6 +101,27 @@ static double feature_kernel(const orc_kernel* k, const double* u, const double*
         off += d;
     }
     return c;
+}
+
+/* Whether a pair passes the feature-space cutoff (always when it is off). */
+static int feature_in(const orc_kernel* k, const double* u, const double* v)
+{
+    if (!(k->feat_cutoff_mult > 0.0)) return 1;
+    int off = 0;
+    for (int b = 0; b < k->n_blocks; ++b) {
+        const int d = k->dim[b];
+        if (k->kind[b] == 0) {
+            double s = 0.0;
+            for (int a = 0; a < d; ++a) {
+                const double diff = u[off + a] - v[off + a];
+                s += diff * diff;
+            }
+            const double r = k->feat_cutoff_mult * k->scale[b];
+            if (!(s <= r * r)) return 0;
+        }
+        off += d;
+    }
+    return 1;
 }
 
 static void cross3(const double a[3], const double b[3], double out[3])
@@ -164,6 +190,7 @@ int orc_eval(const orc_kernel* k, const orc_cloud* X, const orc_cloud* Z, const 
             const double e[3] = {y[0] - x[0], y[1] - x[1], y[2] - x[2]};
             const double d2 = dot3(e, e);
             if (rc2 >= 0.0 && !(d2 <= rc2)) continue;
+            if (D > 0 && !feature_in(k, X->feat + (size_t)D * i, Z->feat + (size_t)D * j)) continue;
             double c = 1.0;
             if (D > 0) c = feature_kernel(k, X->feat + (size_t)D * i, Z->feat + (size_t)D * j);
             const double w = s2 * exp(-d2 / (2.0 * l2)) * c;
@@ -573,6 +600,7 @@ int orc_backward(const orc_kernel* k, const orc_cloud* X, const orc_cloud* Z, co
             const double d2 = dot3(e, e);
             if (rc2 >= 0.0 && !(d2 <= rc2)) continue;
             const double* v = D > 0 ? Z->feat + (size_t)D * j : NULL;
+            if (D > 0 && !feature_in(k, u, v)) continue;
             const double w = pair_weight(k, d2, u, v, -1);
             for (int r = 0; r < 3; ++r) gx[r] += w * e[r] / l2;
             dl += w * d2 / l3;
@@ -601,6 +629,7 @@ int orc_backward(const orc_kernel* k, const orc_cloud* X, const orc_cloud* Z, co
             const double d2 = dot3(e, e);
             if (rc2 >= 0.0 && !(d2 <= rc2)) continue;
             const double* u = D > 0 ? X->feat + (size_t)D * i : NULL;
+            if (D > 0 && !feature_in(k, u, v)) continue;
             const double w = pair_weight(k, d2, u, v, -1);
             for (int r = 0; r < 3; ++r) gy[r] += -w * e[r] / l2;
             if (gv) feature_grad(k, d2, v, u, w, gv);

@@ -497,3 +497,40 @@ def test_sequence_recovers_exact_motions():
         assert np.abs(T_rel[k] - truth).max() < 1e-5
         assert np.abs(T_abs[k + 1] - C[k + 1]).max() < 1e-5
         assert infos[k]["status"] == 0
+
+
+def test_feature_cutoff_by_brute_force():
+    """Sec. III-B's sparsity in feature space, as the optional feature cutoff:
+    F equals the numpy double sum over the pairs inside both cutoffs (the
+    colour distance of every squared-exponential block within the cutoff
+    times its scale); a cutoff wide enough to keep every pair changes
+    nothing."""
+    r = rng(50)
+    X = r.uniform(-0.6, 0.6, size=(40, 3))
+    Z = r.uniform(-0.6, 0.6, size=(35, 3))
+    FX = np.concatenate([r.uniform(0, 1, size=(40, 3)), r.dirichlet(np.ones(4), size=40)], axis=1)
+    FZ = np.concatenate([r.uniform(0, 1, size=(35, 3)), r.dirichlet(np.ones(4), size=35)], axis=1)
+    blocks = [("se", 3, 0.25, 1.3), ("dot", 4, 1.0, 1.0)]
+    T = rand_T(r, 0.2, 0.1)
+    ell, cm, fm = 0.3, 2.5, 1.5
+    Y = transform(T, Z)
+    d2 = ((X[:, None, :] - Y[None, :, :]) ** 2).sum(-1)
+    c2 = ((FX[:, None, :3] - FZ[None, :, :3]) ** 2).sum(-1)
+    keep = (d2 <= (cm * ell) ** 2) & (c2 <= (fm * 0.25) ** 2)
+    w = np.exp(-d2 / (2 * ell ** 2)) * 1.3 ** 2 * np.exp(-c2 / (2 * 0.25 ** 2)) * (FX[:, None, 3:] * FZ[None, :, 3:]).sum(-1)
+    ref = (w * keep).sum()
+    got = oracle.evaluate(X, Z, T, FX=FX, FZ=FZ, blocks=blocks, ell=ell, cutoff_mult=cm, feat_cutoff_mult=fm)
+    assert got["F"] == pytest.approx(ref, rel=1e-12)
+    assert got["npairs"] == int(keep.sum()) and 0 < keep.sum() < (d2 <= (cm * ell) ** 2).sum()
+    wide = oracle.evaluate(X, Z, T, FX=FX, FZ=FZ, blocks=blocks, ell=ell, cutoff_mult=cm, feat_cutoff_mult=100.0)
+    plain = oracle.evaluate(X, Z, T, FX=FX, FZ=FZ, blocks=blocks, ell=ell, cutoff_mult=cm)
+    assert wide["F"] == plain["F"] and wide["npairs"] == plain["npairs"]
+    # the input gradients use the same pair set: central differences of F
+    g = oracle.backward(X, Z, T, FX=FX, FZ=FZ, blocks=blocks, ell=ell, cutoff_mult=cm, feat_cutoff_mult=fm)
+    eps = 1e-6
+    Xp, Xm = X.copy(), X.copy()
+    Xp[3, 1] += eps
+    Xm[3, 1] -= eps
+    fd = (oracle.evaluate(Xp, Z, T, FX=FX, FZ=FZ, blocks=blocks, ell=ell, cutoff_mult=cm, feat_cutoff_mult=fm)["F"]
+          - oracle.evaluate(Xm, Z, T, FX=FX, FZ=FZ, blocks=blocks, ell=ell, cutoff_mult=cm, feat_cutoff_mult=fm)["F"]) / (2 * eps)
+    assert g["dX"][3, 1] == pytest.approx(fd, rel=1e-6, abs=1e-9)
