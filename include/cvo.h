@@ -96,6 +96,9 @@ typedef struct {
     double step_tol_trans; /* ... and |t v| < step_tol_trans, with l at its floor */
     double max_step_rot;   /* clamp of |t omega| per iteration (rad) */
     double max_step_trans; /* clamp of |t v| per iteration (m); <= 0: 0.5 * current l */
+    double feat_cutoff_mult; /* > 0: a pair also needs |u_b - v_b| <= feat_cutoff_mult * scale_b for every
+                                CVO_FEAT_SE block b (the feature-space sparsity of Sec. III-B; changes F);
+                                <= 0: off (default) */
 } cvo_params;
 
 typedef struct {

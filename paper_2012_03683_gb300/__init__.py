@@ -66,7 +66,7 @@ class Params(ctypes.Structure):
                 ("max_iters", ctypes.c_int), ("anneal", ctypes.c_int), ("decay", ctypes.c_double),
                 ("indicator_tol", ctypes.c_double), ("step_tol_rot", ctypes.c_double),
                 ("step_tol_trans", ctypes.c_double), ("max_step_rot", ctypes.c_double),
-                ("max_step_trans", ctypes.c_double)]
+                ("max_step_trans", ctypes.c_double), ("feat_cutoff_mult", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -182,8 +182,10 @@ def _current_stream():
 
 def make_params(blocks=(), ell=0.1, ell_min=None, sigma=1.0, cutoff_mult=3.0, max_iters=100, anneal=False, decay=0.98,
                 indicator_tol=1e-3, step_tol_rot=1e-5, step_tol_trans=1e-5, max_step_rot=0.1,
-                max_step_trans=0.0) -> Params:
-    """blocks: sequence of (kind, dim, scale, sigma), kind "se" (Eq. newscalar) or "dot" (Eq. scalar)."""
+                max_step_trans=0.0, feat_cutoff_mult=0.0) -> Params:
+    """blocks: sequence of (kind, dim, scale, sigma), kind "se" (Eq. newscalar) or "dot" (Eq. scalar).
+    feat_cutoff_mult > 0 also drops pairs whose "se" features lie further apart than
+    feat_cutoff_mult * scale in any block (the feature-space sparsity of Sec. III-B)."""
     p = Params()
     p.ell = float(ell)
     p.ell_min = float(ell if ell_min is None else ell_min)
@@ -206,6 +208,7 @@ def make_params(blocks=(), ell=0.1, ell_min=None, sigma=1.0, cutoff_mult=3.0, ma
     p.step_tol_trans = float(step_tol_trans)
     p.max_step_rot = float(max_step_rot)
     p.max_step_trans = float(max_step_trans)
+    p.feat_cutoff_mult = float(feat_cutoff_mult)
     return p
 
 

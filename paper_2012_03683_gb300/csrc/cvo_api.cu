@@ -199,6 +199,7 @@ cvo_status check_params(const cvo_params* p)
     if (!(p->step_tol_rot >= 0.0) || !(p->step_tol_trans >= 0.0))
         return fail(CVO_ERR_INVALID_ARG, "step tolerances must be >= 0");
     if (!std::isfinite(p->max_step_trans)) return fail(CVO_ERR_INVALID_ARG, "max_step_trans must be finite");
+    if (!std::isfinite(p->feat_cutoff_mult)) return fail(CVO_ERR_INVALID_ARG, "feat_cutoff_mult must be finite");
     return CVO_OK;
 }
 
@@ -305,10 +306,12 @@ void set_features(cvo_handle h, int rec_bf16)
         fc.kind[b] = p.blocks[b].kind;
         fc.off[b] = off;
         off += p.blocks[b].dim;
+        fc.fcut2[b] = 3.0e38f;
         if (p.blocks[b].kind == CVO_FEAT_SE) {
             const double sc = p.blocks[b].scale;
             fc.s[b] = (float)(-1.4426950408889634 / (2.0 * sc * sc));
             kappa *= p.blocks[b].sigma * p.blocks[b].sigma;
+            if (p.feat_cutoff_mult > 0.0) fc.fcut2[b] = (float)((p.feat_cutoff_mult * sc) * (p.feat_cutoff_mult * sc));
         }
     }
     fc.D = off;

@@ -80,6 +80,7 @@ struct FeatConst {
     int kind[4];             // 0 squared exponential, 1 inner product
     int off[4];              // column offset of each block
     float s[4];              // -log2(e) / (2 l_b^2) for squared-exponential blocks
+    float fcut2[4];          // feature-space cutoff of squared-exponential blocks: |u - v|^2 <= fcut2 (3e38: off)
     int D;                   // total feature dim
     int bf16;                // storage of the records' features
 };

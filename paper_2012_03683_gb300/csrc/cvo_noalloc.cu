@@ -227,6 +227,8 @@ extern "C" cvo_status cvo_evaluate_dense_noalloc(const cvo_params* p, void* cuda
                        "cvo_evaluate_dense_noalloc: evaluates the dense sum only (cutoff_mult must be <= 0)");
     if (p->n_blocks < 0 || p->n_blocks > CVO_MAX_BLOCKS)
         return na_fail(CVO_ERR_INVALID_ARG, "cvo_evaluate_dense_noalloc: n_blocks out of range");
+    if (!std::isfinite(p->feat_cutoff_mult))
+        return na_fail(CVO_ERR_INVALID_ARG, "cvo_evaluate_dense_noalloc: feat_cutoff_mult must be finite");
     FeatConst fc;
     std::memset(&fc, 0, sizeof(fc));
     double kappa = p->sigma * p->sigma;
@@ -239,9 +241,12 @@ extern "C" cvo_status cvo_evaluate_dense_noalloc(const cvo_params* p, void* cuda
         fc.dim[b] = fb.dim;
         fc.kind[b] = fb.kind;
         fc.off[b] = D;
+        fc.fcut2[b] = 3.0e38f;
         if (fb.kind == CVO_FEAT_SE) {
             fc.s[b] = (float)(-1.4426950408889634 / (2.0 * fb.scale * fb.scale));
             kappa *= fb.sigma * fb.sigma;
+            if (p->feat_cutoff_mult > 0.0)
+                fc.fcut2[b] = (float)((p->feat_cutoff_mult * fb.scale) * (p->feat_cutoff_mult * fb.scale));
         }
         D += fb.dim;
     }

@@ -116,8 +116,9 @@ struct GradFixed {
 #pragma unroll
         for (int k = 0; k < D; ++k) a.a[k] = 0.0f;
     }
-    // adds the feature exponent to arg; returns the inner-product factor
-    __device__ static float pair(const Q& q, const float4* rec, float& arg, V& c, const FeatConst& fc)
+    // adds the feature exponent to arg, clears in when the feature-space
+    // cutoff excludes the pair; returns the inner-product factor
+    __device__ static float pair(const Q& q, const float4* rec, float& arg, bool& in, V& c, const FeatConst& fc)
     {
         F::unpack(rec + 1, c.v);
         if constexpr (DSE > 0) {
@@ -128,6 +129,7 @@ struct GradFixed {
                 du2 = fmaf(d, d, du2);
             }
             arg = fmaf(du2, fc.s[0], arg);
+            if (du2 > fc.fcut2[0]) in = false;
         }
         if constexpr (DDOT > 0) {
             float dot = 0.0f;
@@ -161,7 +163,7 @@ struct GradNone {
     struct Acc {};
     __device__ static void load_query(Q&, const float4*, const FeatConst&) {}
     __device__ static void zero(Acc&, float*, const FeatConst&) {}
-    __device__ static float pair(const Q&, const float4*, float&, V&, const FeatConst&) { return 1.0f; }
+    __device__ static float pair(const Q&, const float4*, float&, bool&, V&, const FeatConst&) { return 1.0f; }
     __device__ static void accum(Acc&, const Q&, const float4*, const V&, float, float, float*, const FeatConst&) {}
     __device__ static void store(const Acc&, const float*, const FeatConst&, float*) {}
 };
@@ -186,7 +188,7 @@ struct GradGeneric {
     {
         for (int k = 0; k < fc.D; ++k) sacc[32 * k] = 0.0f;
     }
-    __device__ static float pair(const Q& q, const float4* rec, float& arg, V& c, const FeatConst& fc)
+    __device__ static float pair(const Q& q, const float4* rec, float& arg, bool& in, V& c, const FeatConst& fc)
     {
         float mult = 1.0f;
         for (int b = 0; b < fc.n_blocks; ++b) {
@@ -202,8 +204,12 @@ struct GradGeneric {
                 }
             }
             c.val[b] = acc;
-            if (fc.kind[b] == 0) arg = fmaf(acc, fc.s[b], arg);
-            else mult *= acc;
+            if (fc.kind[b] == 0) {
+                arg = fmaf(acc, fc.s[b], arg);
+                if (acc > fc.fcut2[b]) in = false;
+            } else {
+                mult *= acc;
+            }
         }
         return mult;
     }
@@ -291,11 +297,11 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_grad(GradArgs g)
                     const float dy = __fsub_rn(__fsub_rn(z.y, xh[1]), xl[1]);
                     const float dz = __fsub_rn(__fsub_rn(z.z, xh[2]), xl[2]);
                     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const bool in = act && (dense || d2 <= rc2);
+                    bool in = act && (dense || d2 <= rc2);
                     if (!__any_sync(kFull, in)) continue;
                     float arg = d2 * sg;
                     typename G::V cv;
-                    const float mult = G::pair(qf, zr, arg, cv, fc);
+                    const float mult = G::pair(qf, zr, arg, in, cv, fc);
                     const float base = in ? ex2(arg) : 0.0f;
                     const float w = base * mult;
                     E0 = fmaf(w, dx, E0);

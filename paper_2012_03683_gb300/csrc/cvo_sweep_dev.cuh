@@ -64,13 +64,14 @@ __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wai
 // Interface of a feature policy: kScratch bytes of shared memory per warp;
 // load_query once per work item; batch once per staged batch of candidates
 // (warp-uniform); pair per candidate c of the batch, adding the feature
-// exponent to arg and returning the product of the inner-product factors.
+// exponent to arg, clearing in when the feature-space cutoff excludes the
+// pair, and returning the product of the inner-product factors.
 struct FeatNone {
     static constexpr int kScratch = 0;
     struct Q {};
     __device__ static void load_query(Q&, const float4*, const FeatConst&, unsigned char*, int) {}
     __device__ static void batch(Q&, const float4*, int, int, int) {}
-    __device__ static float pair(const Q&, const float4*, int, float&, const FeatConst&) { return 1.0f; }
+    __device__ static float pair(const Q&, const float4*, int, float&, bool&, const FeatConst&) { return 1.0f; }
 };
 
 // One squared-exponential block (Eq. newscalar) of DSE entries followed by
@@ -111,7 +112,7 @@ struct FeatFixed {
         unpack(rec + 1, q.v);
     }
     __device__ static void batch(Q&, const float4*, int, int, int) {}
-    __device__ static float pair(const Q& q, const float4* rec, int, float& arg, const FeatConst& fc)
+    __device__ static float pair(const Q& q, const float4* rec, int, float& arg, bool& in, const FeatConst& fc)
     {
         float v[D];
         unpack(rec + 1, v);
@@ -123,6 +124,7 @@ struct FeatFixed {
                 du2 = fmaf(d, d, du2);
             }
             arg = fmaf(du2, fc.s[0], arg);
+            if (du2 > fc.fcut2[0]) in = false;
         }
         if constexpr (DDOT > 0) {
             float d4[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // four independent chains
@@ -147,7 +149,7 @@ struct FeatGeneric {
     }
     __device__ static void load_query(Q& q, const float4* rec, const FeatConst&, unsigned char*, int) { q.rec = rec; }
     __device__ static void batch(Q&, const float4*, int, int, int) {}
-    __device__ static float pair(const Q& q, const float4* rec, int, float& arg, const FeatConst& fc)
+    __device__ static float pair(const Q& q, const float4* rec, int, float& arg, bool& in, const FeatConst& fc)
     {
         float mult = 1.0f;
         for (int b = 0; b < fc.n_blocks; ++b) {
@@ -162,8 +164,12 @@ struct FeatGeneric {
                     acc = fmaf(u, v, acc);
                 }
             }
-            if (fc.kind[b] == 0) arg = fmaf(acc, fc.s[b], arg);
-            else mult *= acc;
+            if (fc.kind[b] == 0) {
+                arg = fmaf(acc, fc.s[b], arg);
+                if (acc > fc.fcut2[b]) in = false;
+            } else {
+                mult *= acc;
+            }
         }
         return mult;
     }
@@ -296,7 +302,7 @@ struct FeatMMA {
         }
         __syncwarp();
     }
-    __device__ static float pair(const Q& q, const float4* rec, int c, float& arg, const FeatConst& fc)
+    __device__ static float pair(const Q& q, const float4* rec, int c, float& arg, bool& in, const FeatConst& fc)
     {
         if constexpr (DSE > 0) {
             const uint4 u = reinterpret_cast<const uint4*>(rec + 1)[0];
@@ -309,6 +315,7 @@ struct FeatMMA {
                 du2 = fmaf(d, d, du2);
             }
             arg = fmaf(du2, fc.s[0], arg);
+            if (du2 > fc.fcut2[0]) in = false;
         }
         return q.cs[q.lane * kCsStride + c];
     }
@@ -504,12 +511,12 @@ __device__ __forceinline__ void eval_batch(const float4* sb, int cnt, int rs, ty
         const float4* zr1 = zr0 + rs;
         const Offset o0 = offset_to(zr0[0], xh, xl);
         const Offset o1 = offset_to(zr1[0], xh, xl);
-        const bool in0 = act && (dense || o0.d2 <= rc2);
-        const bool in1 = act && (dense || o1.d2 <= rc2);
+        bool in0 = act && (dense || o0.d2 <= rc2);
+        bool in1 = act && (dense || o1.d2 <= rc2);
         if (__any_sync(kFull, in0 || in1)) {
             float a0 = o0.d2 * sg, a1 = o1.d2 * sg;
-            const float m0 = Feat::pair(qf, zr0, c, a0, fc);
-            const float m1 = Feat::pair(qf, zr1, c + 1, a1, fc);
+            const float m0 = Feat::pair(qf, zr0, c, a0, in0, fc);
+            const float m1 = Feat::pair(qf, zr1, c + 1, a1, in1, fc);
             const float w0 = in0 ? ex2(a0) * m0 : 0.0f;
             const float w1 = in1 ? ex2(a1) * m1 : 0.0f;
             npairs += (in0 ? 1u : 0u) + (in1 ? 1u : 0u);
@@ -520,10 +527,10 @@ __device__ __forceinline__ void eval_batch(const float4* sb, int cnt, int rs, ty
     if (c < cnt) {
         const float4* zr = sb + c * rs;
         const Offset o = offset_to(zr[0], xh, xl);
-        const bool in = act && (dense || o.d2 <= rc2);
+        bool in = act && (dense || o.d2 <= rc2);
         if (__any_sync(kFull, in)) {
             float arg = o.d2 * sg;
-            const float mult = Feat::pair(qf, zr, c, arg, fc);
+            const float mult = Feat::pair(qf, zr, c, arg, in, fc);
             const float w = in ? ex2(arg) * mult : 0.0f;
             npairs += in ? 1u : 0u;
             add_moments(mo, w, o);
