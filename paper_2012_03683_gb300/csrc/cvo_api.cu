@@ -594,6 +594,9 @@ cvo_status setup_sweep(cvo_handle h, const std::vector<PairDesc>& table, int nbl
     a->grp_cnt = (unsigned long long*)h->grp_cnt.p;
     a->grp_arrivals = groups ? (unsigned*)h->grp_arrivals.p : nullptr;
     a->fc = h->fc;
+    a->nch_next = nullptr;
+    a->swept_level = (int*)h->counters.p + 10;
+    a->chunk_len = h->chunk_len;
     return CVO_OK;
 }
 
@@ -612,7 +615,7 @@ PairDesc pair_desc(const PairRes& P, int b0, int b1)
 
 int single_pair_blocks(cvo_handle h, const PairRes& P)
 {
-    return std::max(1, std::min((P.max_items + kSweepWarps - 1) / kSweepWarps, h->num_sms * 8));
+    return std::max(1, std::min((P.max_items + kSweepWarps - 1) / kSweepWarps, h->num_sms * kSweepBlocksPerSm));
 }
 
 cvo_status fetch_states(cvo_handle h, int npairs)
@@ -678,7 +681,7 @@ cvo_status run_eval(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const 
 // finalize (single pair) or the batched finalize's last block (batch) clears
 // the condition.
 cvo_status run_graph_loop(cvo_handle h, const SweepArgs& a, bool batch, IterState* st_single, double* trace,
-                          long long trace_stride)
+                          long long trace_stride, LevelDesc* levels)
 {
     SweepLaunch sl;
     CVO_CUDA(sweep_launch_info(a.fc, a.rs, &sl));
@@ -729,6 +732,18 @@ cvo_status run_graph_loop(cvo_handle h, const SweepArgs& a, bool batch, IterStat
     const unsigned long long* gcn = a.grp_cnt;
     int ngroups = (h->sweep_blocks + kGroupBlocks - 1) / kGroupBlocks;
     void* fp1[7] = {&st, &gs, &gcn, &ngroups, &tr, &cond, &use_cond};
+    // single pair with a cutoff: the next sweep's items laid out beside each step
+    const bool lay = !batch && a.nch_next != nullptr;
+    LevelDesc* lv = levels;
+    const int* swl = a.swept_level;
+    const unsigned* nn = a.nch_next;
+    void* lp[3] = {&lv, &swl, &nn};
+    cudaGraphNodeParams lpn = {};
+    lpn.type = cudaGraphNodeTypeKernel;
+    lpn.kernel.func = (void*)layout_kernel();
+    lpn.kernel.gridDim = dim3(1);
+    lpn.kernel.blockDim = dim3(kLayoutThreads);
+    lpn.kernel.kernelParams = lp;
     // batch
     const PairDesc* pairs = a.pairs;
     int npairs = a.npairs;
@@ -750,10 +765,13 @@ cvo_status run_graph_loop(cvo_handle h, const SweepArgs& a, bool batch, IterStat
     // two iterations per pass of the loop body (halves the conditional
     // node's per-pass overhead; a sweep or step after the last iteration
     // sees the state done and returns at once)
-    cudaGraphNode_t fn, sn2, fn2;
+    cudaGraphNode_t fn, sn2, fn2, ln[2];
     if (!check(cudaGraphAddNode(&fn, body, &sn, nullptr, 1, &fpn), "finalize node")) return cleanup(), status;
-    if (!check(cudaGraphAddNode(&sn2, body, &fn, nullptr, 1, &kp), "sweep node")) return cleanup(), status;
+    if (lay && !check(cudaGraphAddNode(&ln[0], body, &sn, nullptr, 1, &lpn), "layout node")) return cleanup(), status;
+    cudaGraphNode_t dep2[2] = {fn, lay ? ln[0] : fn};
+    if (!check(cudaGraphAddNode(&sn2, body, dep2, nullptr, lay ? 2 : 1, &kp), "sweep node")) return cleanup(), status;
     if (!check(cudaGraphAddNode(&fn2, body, &sn2, nullptr, 1, &fpn), "finalize node")) return cleanup(), status;
+    if (lay && !check(cudaGraphAddNode(&ln[1], body, &sn2, nullptr, 1, &lpn), "layout node")) return cleanup(), status;
     if (!check(cudaGraphInstantiate(&ge, g, 0), "instantiate")) return cleanup(), status;
     if (!check(cudaGraphLaunch(ge, h->s), "launch")) return cleanup(), status;
     check(cudaStreamSynchronize(h->s), "synchronize");
@@ -810,15 +828,26 @@ cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     PairRes& P = h->pr[0];
     CVO_TRY(prepare(h, P, X, Z, p.ell, reachable_ell_lo(p)));
     // the dense sum streams all of Z for every group whatever the pose, so a
-    // plan made at the start holds; with a cutoff the streams follow the pose
+    // plan made at the start holds; with a cutoff the streams follow the pose:
+    // the first sweep of a level takes uniform items, and each sweep measures
+    // every group's stream, from which the step kernel lays out the next
+    // sweep's items (at most chunk_len candidates each)
     CVO_TRY(init_state(h, P, 0, T_init, p.ell, 1, h->dense ? kPlanned : kUniform));
     CVO_CUDA(ensure(h->trace, (size_t)p.max_iters * CVO_TRACE_STRIDE * sizeof(double)));
-    const int nb = single_pair_blocks(h, P);
+    const bool persistent = h->loop_mode == 2;
+    const bool replan = !h->dense && !persistent;
+    const int nb = replan ? h->num_sms * kSweepBlocksPerSm : single_pair_blocks(h, P);
     SweepArgs a;
     CVO_TRY(setup_sweep(h, std::vector<PairDesc>{pair_desc(P, 0, nb)}, nb, &a, true));
     double* trace = (double*)h->trace.p;
     IterState* dst = (IterState*)P.state.p;
-    const bool persistent = h->loop_mode == 2;
+    int max_groups = 1;
+    for (int k = 0; k < P.nlevels; ++k) max_groups = std::max(max_groups, P.lv[k].ngroups);
+    CVO_CUDA(ensure(h->gidx, (size_t)std::max(max_groups, P.n) * sizeof(unsigned)));
+    LevelDesc* levels = replan ? (LevelDesc*)P.levels_dev.p : nullptr;
+    unsigned* nch_next = replan ? (unsigned*)h->gidx.p : nullptr;
+    a.nch_next = nch_next;
+    a.chunk_len = h->chunk_len;
     const bool graph = !persistent && !h->timing && h->loop_mode == 1;
     long long kernel_launches = 0;
     if (persistent) {
@@ -832,9 +861,6 @@ cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
             ensure_events(h, 1);
             CVO_CUDA(cudaEventRecord(h->evs[0], h->s));
         }
-        int max_groups = 1;
-        for (int k = 0; k < P.nlevels; ++k) max_groups = std::max(max_groups, P.lv[k].ngroups);
-        CVO_CUDA(ensure(h->gidx, (size_t)max_groups * sizeof(unsigned)));
         CVO_CUDA(launch_register_persistent(a, (unsigned*)h->counters.p, (unsigned*)h->gidx.p, h->chunk_len, trace,
                                             grid, h->s));
         if (h->timing) CVO_CUDA(cudaEventRecord(h->evs[1], h->s));
@@ -843,7 +869,7 @@ cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
         CVO_CUDA(cudaStreamSynchronize(h->s));
         if (h->h_misc[40] != 0u) return fail(CVO_ERR_TIMEOUT, "persistent loop: a grid barrier gave up waiting");
     } else if (graph) {
-        CVO_TRY(run_graph_loop(h, a, false, dst, trace, 0));
+        CVO_TRY(run_graph_loop(h, a, false, dst, trace, 0, levels));
     } else {
         // iterations queued from the host in batches (CUDA events around each
         // sweep when timing); the device-side state stops the kernels once the
@@ -859,6 +885,7 @@ cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
                 if (ev) CVO_CUDA(cudaEventRecord(h->evs[2 * it], h->s));
                 CVO_CUDA(launch_sweep(a, nb, h->s));
                 if (ev) CVO_CUDA(cudaEventRecord(h->evs[2 * it + 1], h->s));
+                if (replan) CVO_CUDA(launch_layout(levels, a.swept_level, nch_next, h->s));
                 CVO_CUDA(launch_finalize(dst, a.grp_stats, a.grp_cnt, nb, trace, h->s));
             }
             launched += n;
@@ -873,8 +900,8 @@ cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     std::memcpy(T_out, st->T, 16 * sizeof(double));
     fill_info(st, &inf);
     h->last_iters = st->iter;
-    // four kernels per pass of the graph's loop body, two iterations a pass
-    if (graph) g_launch_count.fetch_add(4LL * ((st->iter + 1) / 2), std::memory_order_relaxed);
+    // four kernels (six with the layout) per pass of the graph's loop body, two iterations a pass
+    if (graph) g_launch_count.fetch_add((replan ? 6LL : 4LL) * ((st->iter + 1) / 2), std::memory_order_relaxed);
     (void)kernel_launches;
     if (h->timing && persistent) {
         // the persistent kernel as a whole (sweeps and steps), per iteration
@@ -926,7 +953,7 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
         work += h->pr[i].max_items;
     }
     // split the grid among the pairs in proportion to their work items
-    const int budget = std::max(nl, h->num_sms * 8);
+    const int budget = std::max(nl, h->num_sms * kSweepBlocksPerSm);
     std::vector<PairDesc> table;
     int b = 0;
     for (int i = 0; i < nl; ++i) {
@@ -943,7 +970,7 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
     double* traces = (double*)h->trace.p;
     const bool graph = !h->timing && h->loop_mode != 0;
     if (graph) {
-        CVO_TRY(run_graph_loop(h, a, true, nullptr, traces, tstride));
+        CVO_TRY(run_graph_loop(h, a, true, nullptr, traces, tstride, nullptr));
     } else {
         if (h->timing) ensure_events(h, p.max_iters);
         unsigned* counters = (unsigned*)h->counters.p;
@@ -1058,7 +1085,7 @@ cvo_status run_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
         const int nitems = P.lv[0].nitems;
         CVO_CUDA(ensure(h->bw_part, (size_t)std::max(nitems, 1) * 32 * (4 + D) * sizeof(float)));
         g.part = (float*)h->bw_part.p;
-        const int nb = std::max(1, std::min((nitems + kSweepWarps - 1) / kSweepWarps, h->num_sms * 16));
+        const int nb = std::max(1, std::min((nitems + kSweepWarps - 1) / kSweepWarps, h->num_sms * 2 * kSweepBlocksPerSm));
         CVO_CUDA(launch_grad(g, nb, h->s));
         return CVO_OK;
     };
@@ -1099,9 +1126,16 @@ cvo_status run_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
 cvo_status time_sweep(cvo_handle h, PairRes& P, const double* T, double ell, int reps, double* ms, double* F)
 {
     CVO_TRY(init_state(h, P, 0, T, ell, 0, h->dense ? kPlanned : kUniform));   // as a registration sweeps
-    const int nb = single_pair_blocks(h, P);
+    const int nb = h->dense ? single_pair_blocks(h, P) : h->num_sms * kSweepBlocksPerSm;
     SweepArgs a;
     CVO_TRY(setup_sweep(h, std::vector<PairDesc>{pair_desc(P, 0, nb)}, nb, &a, true));
+    if (!h->dense) {   // the items a registration's sweep gets at this pose
+        int max_groups = 1;
+        for (int k = 0; k < P.nlevels; ++k) max_groups = std::max(max_groups, P.lv[k].ngroups);
+        CVO_CUDA(ensure(h->gidx, (size_t)max_groups * sizeof(unsigned)));
+        CVO_CUDA(launch_replan((LevelDesc*)P.levels_dev.p, (const float4*)P.xrec.p, P.m, h->rs, (IterState*)P.state.p,
+                               h->chunk_len, (unsigned*)h->gidx.p, (unsigned*)h->counters.p + 8, max_groups, h->s));
+    }
     ensure_events(h, 1);
     if (h->evs.size() < 2) return fail(CVO_ERR_CUDA, "cudaEventCreate failed");
     // the sweep leaves the state alone (the finalize would mark an
@@ -1123,15 +1157,16 @@ cvo_status time_sweep(cvo_handle h, PairRes& P, const double* T, double ell, int
     return CVO_OK;
 }
 
-// Autotuner: every (cell_factor, super_delta, chunk_len) of a small grid
-// is prepared and its sweep timed on the caller's pair; the fastest is kept.
+// Autotuner: every (cell_factor, super_delta) of a small grid is prepared
+// and its sweep timed on the caller's pair; then, for the fastest, a few
+// work-item lengths (chunk_len); the fastest is kept.
 // The results must not depend on the tuning beyond rounding: F of every
 // candidate is checked against the first one.
 cvo_status run_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double* T, cvo_tuning* out)
 {
     static const double kCell[] = {0.35, 0.5, 0.7, 1.0};
     static const int kSuper[] = {1, 2, 3};
-    const int kItems[] = {h->chunk_len};   // the planned items' length is not tuned here
+    static const int kItemLens[] = {64, 96, 128, 192};
     const double cf0 = h->cell_factor;
     const int sd0 = h->super_delta, ip0 = h->chunk_len;
     cvo_tuning best{cf0, sd0, ip0, 1e30};
@@ -1149,36 +1184,51 @@ cvo_status run_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     // the dense sum has no grid and no super-cells: only the work split is tuned
     const std::vector<double> cells = h->dense ? std::vector<double>{cf0} : std::vector<double>(kCell, kCell + 4);
     const std::vector<int> supers = h->dense ? std::vector<int>{sd0} : std::vector<int>(kSuper, kSuper + 3);
+    auto try_one = [&](double cf, int sd, int ip, bool regrid) {
+        h->cell_factor = cf;
+        h->super_delta = sd;
+        h->chunk_len = ip;
+        // the grid levels of a registration; timed at its first and
+        // its smallest reachable lengthscale
+        if (regrid) {
+            st = prepare(h, P, X, Z, h->p.ell, ell_lo);
+            if (st < 0) return;
+        }
+        double ms = 0.0, F = 0.0, ms_lo = 0.0, F_lo = 0.0;
+        st = time_sweep(h, P, T, h->p.ell, 3, &ms, &F);
+        if (st < 0) return;
+        if (ell_lo < h->p.ell) {
+            st = time_sweep(h, P, T, ell_lo, 3, &ms_lo, &F_lo);
+            if (st < 0) return;
+            ms += ms_lo;
+        }
+        if (!have_ref) {
+            F_ref = F;
+            have_ref = true;
+        } else if (std::fabs(F - F_ref) > 1e-4 * std::fabs(F_ref) + 1e-300) {
+            st = fail(CVO_ERR_CUDA, "autotune: F differs between tunings (%g vs %g)", F, F_ref);
+            return;
+        }
+        if (ms < best.sweep_ms) best = cvo_tuning{cf, sd, ip, ms};
+    };
     for (double cf : cells) {
         for (int sd : supers) {
-            for (int ip : kItems) {
-                h->cell_factor = cf;
-                h->super_delta = sd;
-                h->chunk_len = ip;
-                // the grid levels of a registration; timed at its first and
-                // its smallest reachable lengthscale
-                st = prepare(h, P, X, Z, h->p.ell, ell_lo);
-                if (st < 0) break;
-                double ms = 0.0, F = 0.0, ms_lo = 0.0, F_lo = 0.0;
-                st = time_sweep(h, P, T, h->p.ell, 3, &ms, &F);
-                if (st < 0) break;
-                if (ell_lo < h->p.ell) {
-                    st = time_sweep(h, P, T, ell_lo, 3, &ms_lo, &F_lo);
-                    if (st < 0) break;
-                    ms += ms_lo;
-                }
-                if (!have_ref) {
-                    F_ref = F;
-                    have_ref = true;
-                } else if (std::fabs(F - F_ref) > 1e-4 * std::fabs(F_ref) + 1e-300) {
-                    st = fail(CVO_ERR_CUDA, "autotune: F differs between tunings (%g vs %g)", F, F_ref);
-                    break;
-                }
-                if (ms < best.sweep_ms) best = cvo_tuning{cf, sd, ip, ms};
-            }
+            try_one(cf, sd, ip0, true);
             if (st < 0) break;
         }
         if (st < 0) break;
+    }
+    // the item length for the best grid (it changes only the work split)
+    if (st >= 0) {
+        const double cfb = best.cell_factor;
+        const int sdb = best.super_delta;
+        bool gridded = false;
+        for (int ip : kItemLens) {
+            if (ip == ip0) continue;
+            try_one(cfb, sdb, ip, !gridded);
+            gridded = true;
+            if (st < 0) break;
+        }
     }
     if (st < 0) {
         h->cell_factor = cf0;

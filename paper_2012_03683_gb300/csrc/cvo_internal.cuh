@@ -36,6 +36,7 @@ namespace cvo {
 
 constexpr int kStatN = 43;       // linear statistics of the per-query moments
 constexpr int kSweepWarps = 4;   // warps per sweep block
+constexpr int kSweepBlocksPerSm = 8;   // most sweep blocks launched per SM (two waves of four resident blocks)
 constexpr int kMaxLevels = 24;   // grid levels of one registration
 constexpr int kMaxChunks = 64;   // most work items (chunks) one query group's stream splits into
 constexpr int kChunkLen = 128;   // default candidates per planned work item
@@ -65,7 +66,7 @@ struct LevelDesc {
     const int* cell_start;   // nx*ny*nz + 1
     const float4* zrec;      // M records sorted by cell
     const int2* groups;      // query groups (first, count)
-    const int4* items;       // work items (first, count, chunk, chunks)
+    const int4* items;       // work items (first query, count, chunk | chunks << 16, group index)
     int ngroups;
     int nitems;
     int chunk_min;           // > 0: a group's stream is cut into min(chunks, length / chunk_min) chunks at
@@ -143,6 +144,11 @@ struct SweepArgs {
     unsigned* grp_arrivals;    // [kMaxGroups] arrival counters, zero between launches;
                                // NULL in a batch (its finalize sums the block partials)
     FeatConst fc;
+    unsigned* nch_next;        // registration with a cutoff: each group's chunk count for the next sweep,
+                               // ceil(stream length / chunk_len), written by the group's item with chunk 0
+                               // (NULL: not recorded)
+    int chunk_len;
+    int* swept_level;          // with nch_next: the level the sweep covered (written by block 0)
 };
 
 // ---- launchers (host) ------------------------------------------------------
@@ -178,6 +184,13 @@ cudaError_t launch_init_state(IterState* st, cudaStream_t s);
 // Reduces the ceil(nblocks / kGroupBlocks) group sums of a sweep and takes the step.
 cudaError_t launch_finalize(IterState* st, const float2* grp_stats, const unsigned long long* grp_cnt, int nblocks,
                             double* trace, cudaStream_t s);
+// Lays out the swept level's work items for the next sweep from the chunk
+// counts the sweep recorded (registration with a cutoff; one block, run
+// beside the step).  k_layout(LevelDesc* levels, const int* swept_level,
+// const unsigned* nch_next), kLayoutThreads threads.
+constexpr int kLayoutThreads = 256;
+cudaError_t launch_layout(LevelDesc* levels, const int* swept_level, const unsigned* nch_next, cudaStream_t s);
+const void* layout_kernel();
 
 // Gradients of F with respect to one cloud's points and features: a sweep with
 // that cloud as the queries (see cvo_sweep.cu, k_grad).
@@ -224,6 +237,16 @@ cudaError_t launch_group_cost(const LevelDesc* levels, int level, int ngroups, c
                               int dense, const IterState* st, float rc, int chunk_len, unsigned* keys, unsigned* vals,
                               unsigned* nch, cudaStream_t s);
 cudaError_t launch_gather_u32(const unsigned* src, const unsigned* idx, int n, unsigned* dst, cudaStream_t s);
+// Re-plans the current level's work items at the current pose (registration
+// with a cutoff, before each sweep): nch has room for max_groups counts, each
+// level's item table for ngroups * kMaxChunks items; *arrivals is zero
+// between launches.  k_replan(LevelDesc*, const float4* xrec, int m, int rs,
+// const IterState*, int chunk_len, unsigned* nch, unsigned* arrivals) runs on
+// replan_blocks(max_groups) blocks of 256 threads.
+cudaError_t launch_replan(LevelDesc* levels, const float4* xrec, int m, int rs, const IterState* st, int chunk_len,
+                          unsigned* nch, unsigned* arrivals, int max_groups, cudaStream_t s);
+const void* replan_kernel();
+int replan_blocks(int max_groups);
 cudaError_t launch_write_items(const LevelDesc* levels, int level, const unsigned* sorted_groups, const unsigned* nch,
                                const unsigned* offsets, int ngroups, int4* items, cudaStream_t s);
 

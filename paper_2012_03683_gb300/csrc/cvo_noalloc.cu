@@ -144,7 +144,7 @@ __global__ void k_na_setup(IterState init, LevelDesc ld, PairDesc pd, int n, int
     // every group streams all of Z (dense), so every group gets nch chunks
     for (int i = tid; i < ng * nch; i += gridDim.x * blockDim.x) {
         const int g = i / nch;
-        items[i] = make_int4(32 * g, min(32, n - 32 * g), i - g * nch, nch);
+        items[i] = make_int4(32 * g, min(32, n - 32 * g), (i - g * nch) | (nch << 16), g);
     }
 }
 

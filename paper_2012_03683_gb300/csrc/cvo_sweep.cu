@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
     if (st->done) return;   // uniform per pair; a single pair's blocks all return together
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x < 30) cst[threadIdx.x] = (&st->Ahi[0])[threadIdx.x];
+    if (a.nch_next != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *a.swept_level = st->level;
     __syncthreads();
     StatAcc acc;
     stat_acc_init(acc, lane);
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
         float p[3];
         bool act;
         if (!sweep_item<Feat>(P, L, item, cst, rs, dense, sg, rc, rc2, fc, stage, scratch, lane, mo, p, act, npairs,
-                              ncand))
+                              ncand, a.nch_next, a.chunk_len))
             continue;
         stat_acc_add(acc, mo, p, act, lane);
     }
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_grad(GradArgs g)
     for (int item = blockIdx.x * kSweepWarps + warp; item < L.nitems; item += gridDim.x * kSweepWarps) {
         const int4 w4 = L.items[item];
         const int2 grp = make_int2(w4.x, w4.y);
-        const int k = w4.z, nch = w4.w;
+        const int k = w4.z & 0xffff, nch = w4.z >> 16;
         const bool act = lane < grp.y;
         const int qi = grp.x + (act ? lane : 0);
         const float4* qrec = g.xrec + (size_t)qi * rs;
@@ -333,11 +334,12 @@ __global__ void __launch_bounds__(128) k_grad_reduce(GradArgs g)
     const LevelDesc L = g.levels[g.st->level];
     for (int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < L.nitems; item += (gridDim.x * blockDim.x) >> 5) {
         const int4 w4 = L.items[item];
-        if (w4.z != 0) continue;   // warp-uniform
+        if ((w4.z & 0xffff) != 0) continue;   // warp-uniform
+        const int nch = w4.z >> 16;
         if (lane >= w4.y) continue;
         const int idx = __float_as_int(g.xrec[(size_t)(w4.x + lane) * g.rs].w);
         float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        for (int c = 0; c < w4.w; ++c) {
+        for (int c = 0; c < nch; ++c) {
             const float* row = g.part + ((size_t)(item + c) * 32 + lane) * stride;
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[j] += row[j];
@@ -352,7 +354,7 @@ __global__ void __launch_bounds__(128) k_grad_reduce(GradArgs g)
         if (g.out_feat) {
             for (int j = 0; j < g.fc.D; ++j) {
                 float f = 0.0f;
-                for (int c = 0; c < w4.w; ++c) f += g.part[((size_t)(item + c) * 32 + lane) * stride + 4 + j];
+                for (int c = 0; c < nch; ++c) f += g.part[((size_t)(item + c) * 32 + lane) * stride + 4 + j];
                 g.out_feat[(size_t)idx * g.fc.D + j] = g.feat_scale[j] * f;
             }
         }
@@ -413,6 +415,147 @@ __global__ void __launch_bounds__(128) k_group_cost(const LevelDesc* __restrict_
     }
 }
 
+// Re-plans the work items of the current level at the current pose, before
+// each sweep of a registration with a cutoff (the streams follow the pose, so
+// a plan made at the start goes stale).  One warp per query group measures
+// its candidate stream and takes ceil(length / chunk_len) chunks (at most
+// kMaxChunks); the last block to finish lays the items out group after group
+// (an exclusive scan of the chunk counts) into the level's item table and
+// publishes their number in the level's descriptor.  Every item then holds
+// at most chunk_len candidates, so a fixed round-robin deal of items to warps
+// is balanced.
+constexpr int kReplanThreads = 256;
+__global__ void __launch_bounds__(kReplanThreads) k_replan(LevelDesc* levels, const float4* __restrict__ xrec, int m,
+                                                        int rs, const IterState* __restrict__ st, int chunk_len,
+                                                        unsigned* nch, unsigned* arrivals)
+{
+    __shared__ unsigned part[kReplanThreads];
+    __shared__ int is_last;
+    if (st->done) return;   // uniform over the grid
+    const int level = st->level;
+    LevelDesc* Ld = levels + level;
+    const LevelDesc L = *Ld;
+    const int lane = threadIdx.x & 31;
+    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (g < L.ngroups) {   // warp-uniform
+        const int2 grp = L.groups[g];
+        const bool act = lane < grp.y;
+        const float4 q = xrec[(size_t)(grp.x + (act ? lane : 0)) * rs];
+        const float xq[3] = {q.x, q.y, q.z};
+        float xh[3], xl[3];
+        transform_df(xq, st->Ahi, st->Alo, st->bhi, st->blo, xh, xl);
+        Stream sm;
+        const int total = stream_setup(L, m, false, act, xh, st->rc, lane, sm) ? sm.total : 0;
+        if (lane == 0) nch[g] = total == 0 ? 0u : (unsigned)min(kMaxChunks, (total + chunk_len - 1) / chunk_len);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(arrivals, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    // exclusive scan of the chunk counts: thread t owns groups [t * per, (t + 1) * per)
+    const int ng = L.ngroups;
+    const int per = (ng + kReplanThreads - 1) / kReplanThreads;
+    const int g0 = min(ng, (int)threadIdx.x * per), g1 = min(ng, g0 + per);
+    unsigned s = 0;
+    for (int k = g0; k < g1; ++k) s += __ldcg(nch + k);
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < kReplanThreads; o <<= 1) {   // inclusive Hillis-Steele scan
+        const unsigned v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned off = part[threadIdx.x] - s;
+    int4* items = const_cast<int4*>(L.items);
+    for (int k = g0; k < g1; ++k) {
+        const int2 grp = L.groups[k];
+        const int n = (int)__ldcg(nch + k);
+        for (int c = 0; c < n; ++c) items[off + c] = make_int4(grp.x, grp.y, c | (n << 16), k);
+        off += (unsigned)n;
+    }
+    if (threadIdx.x == kReplanThreads - 1) {
+        Ld->nitems = (int)part[kReplanThreads - 1];
+        Ld->chunk_min = 0;
+        *arrivals = 0u;
+    }
+}
+
+// Work items of level Ld for the next sweep, group after group in group
+// order, from the chunk counts the sweep recorded per group.  Warps
+// 0 .. nw - 1 of the caller (w, lane) each own a contiguous range of groups,
+// handled 32 * kLayAhead groups per round: all loads of a round first, the
+// round's count to the other warps through part[] behind a barrier of their
+// own (named barrier 1, nw warps), then a warp scan for the offsets and each
+// lane writes its own group's items (a warp-wide loop over the groups with
+// shuffles measured seven times slower).
+constexpr int kLayAhead = 4;
+__device__ void lay_out_items(LevelDesc* Ld, const unsigned* __restrict__ nch_next, int w, int nw, int lane,
+                              unsigned* part)
+{
+    const unsigned full = 0xffffffffu;
+    const int ng = Ld->ngroups;
+    const int2* groups = Ld->groups;
+    int4* items = const_cast<int4*>(Ld->items);
+    constexpr int kRound = 32 * kLayAhead;
+    const int rounds = (ng + kRound * nw - 1) / (kRound * nw);
+    unsigned base = 0;   // items before this round's range of warp w
+    for (int r = 0; r < rounds; ++r) {
+        const int g0 = (r * nw + w) * kRound;
+        int2 grp[kLayAhead];
+        unsigned n[kLayAhead];
+        unsigned s = 0;
+#pragma unroll
+        for (int a = 0; a < kLayAhead; ++a) {
+            const int g = g0 + 32 * a + lane;
+            grp[a] = g < ng ? groups[g] : make_int2(0, 0);
+            n[a] = g < ng ? nch_next[g] : 0u;
+        }
+#pragma unroll
+        for (int a = 0; a < kLayAhead; ++a) s += n[a];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(full, s, o);
+        if (lane == 0) part[w] = s;
+        asm volatile("bar.sync 1, %0;" ::"r"(nw * 32) : "memory");
+        unsigned before = 0, all = 0;
+        for (int k = 0; k < nw; ++k) {
+            const unsigned v = part[k];
+            before += k < w ? v : 0u;
+            all += v;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(nw * 32) : "memory");   // part[] is reused next round
+        unsigned off0 = base + before;
+#pragma unroll
+        for (int a = 0; a < kLayAhead; ++a) {
+            unsigned incl = n[a];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned t = __shfl_up_sync(full, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const unsigned off = off0 + incl - n[a];
+            const int gbase = g0 + 32 * a;
+            for (unsigned c = 0; c < n[a]; ++c)
+                items[off + c] = make_int4(grp[a].x, grp[a].y, (int)(c | (n[a] << 16)), gbase + lane);
+            off0 += __shfl_sync(full, incl, 31);
+        }
+        base += all;
+    }
+    if (w == 0 && lane == 0) {
+        Ld->nitems = (int)base;
+        Ld->chunk_min = 0;
+    }
+}
+
+__global__ void __launch_bounds__(kLayoutThreads) k_layout(LevelDesc* levels, const int* swept_level,
+                                                        const unsigned* __restrict__ nch_next)
+{
+    __shared__ unsigned part[kLayoutThreads / 32];
+    lay_out_items(levels + *swept_level, nch_next, threadIdx.x >> 5, kLayoutThreads / 32, threadIdx.x & 31, part);
+}
+
 __global__ void k_gather_u32(const unsigned* __restrict__ src, const unsigned* __restrict__ idx, int n, unsigned* dst)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -431,7 +574,7 @@ __global__ void k_write_items(const LevelDesc* __restrict__ levels, int level, c
     const int2 grp = levels[level].groups[g];
     const int n = (int)nch[g];
     const unsigned off = offsets[i];
-    for (int k = 0; k < n; ++k) items[off + k] = make_int4(grp.x, grp.y, k, n);
+    for (int k = 0; k < n; ++k) items[off + k] = make_int4(grp.x, grp.y, k | (n << 16), g);
 }
 
 template <class Feat>
@@ -491,6 +634,31 @@ cudaError_t launch_group_cost(const LevelDesc* levels, int level, int ngroups, c
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
     k_group_cost<<<(ngroups + 3) / 4, 128, 0, s>>>(levels, level, ngroups, xrec, m, rs, dense, st, rc, chunk_len, keys,
                                                    vals, nch);
+    return cudaGetLastError();
+}
+
+const void* replan_kernel() { return (const void*)k_replan; }
+
+const void* layout_kernel() { return (const void*)k_layout; }
+
+cudaError_t launch_layout(LevelDesc* levels, const int* swept_level, const unsigned* nch_next, cudaStream_t s)
+{
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    k_layout<<<1, kLayoutThreads, 0, s>>>(levels, swept_level, nch_next);
+    return cudaGetLastError();
+}
+
+int replan_blocks(int max_groups)
+{
+    const int b = (max_groups * 32 + kReplanThreads - 1) / kReplanThreads;
+    return b > 1 ? b : 1;
+}
+
+cudaError_t launch_replan(LevelDesc* levels, const float4* xrec, int m, int rs, const IterState* st, int chunk_len,
+                          unsigned* nch, unsigned* arrivals, int max_groups, cudaStream_t s)
+{
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    k_replan<<<replan_blocks(max_groups), kReplanThreads, 0, s>>>(levels, xrec, m, rs, st, chunk_len, nch, arrivals);
     return cudaGetLastError();
 }
 

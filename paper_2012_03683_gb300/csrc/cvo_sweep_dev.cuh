@@ -547,7 +547,8 @@ __device__ __forceinline__ bool sweep_chunk(const PairDesc& P, const LevelDesc& 
                                             const float* cst, int rs, bool dense, float sg, float rc, float rc2,
                                             const FeatConst& fc, float4* stage, unsigned char* scratch, int lane,
                                             Moments& mo, float p[3], bool& act, unsigned& npairs, unsigned& ncand,
-                                            int chunk_min = 0)
+                                            int chunk_min = 0, unsigned* nch_next = nullptr, int chunk_len = 0,
+                                            int group = 0)
 {
     const float* Ahi = cst;
     const float* Alo = cst + 9;
@@ -564,8 +565,9 @@ __device__ __forceinline__ bool sweep_chunk(const PairDesc& P, const LevelDesc& 
     transform_df(xq, Ahi, Alo, bhi, blo, xh, xl);
 
     Stream sm;
-    if (!stream_setup(L, P.m, dense, act, xh, rc, lane, sm)) return false;
-    const int total = sm.total;
+    const int total = stream_setup(L, P.m, dense, act, xh, rc, lane, sm) ? sm.total : 0;
+    if (nch_next != nullptr && k == 0 && lane == 0)   // the group's items in the next sweep (one even if empty)
+        nch_next[group] = total == 0 ? 1u : (unsigned)min(kMaxChunks, (total + chunk_len - 1) / chunk_len);
     if (total == 0) return false;
     if (chunk_min > 0) {   // cut at run time: no chunk shorter than chunk_min
         nch = min(nch, (total + chunk_min - 1) / chunk_min);
@@ -592,11 +594,12 @@ template <class Feat>
 __device__ __forceinline__ bool sweep_item(const PairDesc& P, const LevelDesc& L, int item, const float* cst, int rs,
                                            bool dense, float sg, float rc, float rc2, const FeatConst& fc,
                                            float4* stage, unsigned char* scratch, int lane, Moments& mo, float p[3],
-                                           bool& act, unsigned& npairs, unsigned& ncand)
+                                           bool& act, unsigned& npairs, unsigned& ncand, unsigned* nch_next = nullptr,
+                                           int chunk_len = 0)
 {
     const int4 w = L.items[item];
-    return sweep_chunk<Feat>(P, L, make_int2(w.x, w.y), w.z, w.w, cst, rs, dense, sg, rc, rc2, fc, stage, scratch, lane,
-                             mo, p, act, npairs, ncand, L.chunk_min);
+    return sweep_chunk<Feat>(P, L, make_int2(w.x, w.y), w.z & 0xffff, w.z >> 16, cst, rs, dense, sg, rc, rc2, fc, stage,
+                             scratch, lane, mo, p, act, npairs, ncand, L.chunk_min, nch_next, chunk_len, w.w);
 }
 
 // The 43 linear statistics of one query's moments about the lever centre
