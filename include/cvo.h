@@ -236,34 +236,34 @@ cvo_status cvo_set_tuning(cvo_handle h, double cell_factor, int super_delta);
 
 /* Tuning of the neighbour sweep: grid cell edge (cell_factor x cutoff
  * radius), query-group extent (Morton super-cells about 2^super_delta
- * cutoff radii wide) and the work split of evaluations and batches (each
- * query group's candidate stream, measured at the call's pose, is cut into
- * work items of about chunk_len candidates, so up to length / chunk_len
- * lanes of different warps serve one query, longest streams first; a single
- * registration with a cutoff, whose streams follow the moving pose, cuts
- * every stream into up to 8 items of at least 64 candidates at run time).  sweep_ms: the measured sweep time of
- * the tuning (cvo_autotune), else 0. */
+ * cutoff radii wide) and the work split (each query group's candidate
+ * stream is cut into work items of about chunk_len candidates, so up to
+ * length / chunk_len warps serve one query group: evaluations, batches and
+ * dense registrations measure the streams at the call's pose, longest
+ * first; a single registration with a cutoff measures them again in every
+ * sweep and lays out the next sweep's items from them, since its streams
+ * follow the moving pose).  measured_ms: the time cvo_autotune measured for
+ * the tuning it kept, else 0. */
 typedef struct {
     double cell_factor;
     int super_delta;
     int chunk_len;
-    double sweep_ms;
+    double measured_ms;
 } cvo_tuning;
 
-/* Autotuner: prepares the pair (X, Z) under each tuning of a small grid
- * (cell_factor 0.35 / 0.5 / 0.7 / 1.0 and super_delta 1 / 2 / 3; chunk_len
- * stays as set; with cutoff_mult <= 0 there is no grid to tune and the
- * tuning stays as it is), times its sweep at pose T with CUDA events (best
- * of 3, with a registration's work split) at lengthscale params.ell and,
- * when annealing, at the smallest lengthscale a registration can reach,
- * keeps the tuning with the least total time on the handle and returns it
- * in *out (sweep_ms: that total).  Results do not depend on the tuning
- * beyond rounding; every tuning's F is checked against the first
- * (CVO_ERR_CUDA if they differ by more than 1e-4 relative).  Costs one setup
- * and up to eight sweeps per tuning (tens of milliseconds). */
+/* Autotuner: registers (X, Z) from pose T with the handle's parameters
+ * under each tuning of a small grid (cell_factor 0.35 / 0.5 / 0.7 / 1.0 and
+ * super_delta 1 / 2 / 3 at the current chunk_len; with cutoff_mult <= 0 there
+ * is no grid and these stay as they are), then, for the fastest, chunk_len
+ * 64 / 96 / 128 / 192; each timed on the host clock as a caller sees it
+ * (setup, iterations, result copies; best of two runs).  Keeps the fastest
+ * tuning on the handle and returns it in *out (measured_ms: its time).
+ * Results do not depend on the tuning beyond rounding; every tuning's F at
+ * the start pose is checked against the first (CVO_ERR_CUDA if they differ
+ * by more than 1e-4 relative).  Costs up to 30 registrations. */
 cvo_status cvo_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], cvo_tuning* out);
 
-/* The handle's current tuning (sweep_ms = 0), and setting it (validated as
+/* The handle's current tuning (measured_ms = 0), and setting it (validated as
  * cvo_set_tuning, chunk_len in [16, 4096]). */
 cvo_status cvo_get_tuning(cvo_handle h, cvo_tuning* out);
 cvo_status cvo_apply_tuning(cvo_handle h, const cvo_tuning* t);

@@ -81,7 +81,7 @@ class Info(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("cell_factor", ctypes.c_double), ("super_delta", ctypes.c_int), ("chunk_len", ctypes.c_int),
-                ("sweep_ms", ctypes.c_double)]
+                ("measured_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -433,8 +433,8 @@ def cvo_set_tuning(h, cell_factor=0.5, super_delta=2):
 
 
 def cvo_autotune(h, X, Z, T, FX=None, FZ=None) -> dict:
-    """Times the sweep of (X, Z) at pose T under a grid of tunings and keeps
-    the fastest on the handle (see cvo_autotune in cvo.h)."""
+    """Times a registration of (X, Z) from pose T under a grid of tunings and
+    keeps the fastest on the handle (see cvo_autotune in cvo.h)."""
     cx, cz, keep = _clouds(X, Z, FX, FZ)
     Tm = _pose(T)
     out = Tuning()

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -1121,47 +1122,13 @@ cvo_status run_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     return CVO_OK;
 }
 
-// Times the sweep of one prepared pair at pose T (eval mode): the best of
-// `reps` launches, CUDA events on the handle's stream.
-cvo_status time_sweep(cvo_handle h, PairRes& P, const double* T, double ell, int reps, double* ms, double* F)
-{
-    CVO_TRY(init_state(h, P, 0, T, ell, 0, h->dense ? kPlanned : kUniform));   // as a registration sweeps
-    const int nb = h->dense ? single_pair_blocks(h, P) : h->num_sms * kSweepBlocksPerSm;
-    SweepArgs a;
-    CVO_TRY(setup_sweep(h, std::vector<PairDesc>{pair_desc(P, 0, nb)}, nb, &a, true));
-    if (!h->dense) {   // the items a registration's sweep gets at this pose
-        int max_groups = 1;
-        for (int k = 0; k < P.nlevels; ++k) max_groups = std::max(max_groups, P.lv[k].ngroups);
-        CVO_CUDA(ensure(h->gidx, (size_t)max_groups * sizeof(unsigned)));
-        CVO_CUDA(launch_replan((LevelDesc*)P.levels_dev.p, (const float4*)P.xrec.p, P.m, h->rs, (IterState*)P.state.p,
-                               h->chunk_len, (unsigned*)h->gidx.p, (unsigned*)h->counters.p + 8, max_groups, h->s));
-    }
-    ensure_events(h, 1);
-    if (h->evs.size() < 2) return fail(CVO_ERR_CUDA, "cudaEventCreate failed");
-    // the sweep leaves the state alone (the finalize would mark an
-    // evaluation done), so it is launched reps + 1 times and finalized once
-    double best = 1e30;
-    for (int r = 0; r <= reps; ++r) {   // the first launch warms up
-        CVO_CUDA(cudaEventRecord(h->evs[0], h->s));
-        CVO_CUDA(launch_sweep(a, nb, h->s));
-        CVO_CUDA(cudaEventRecord(h->evs[1], h->s));
-        CVO_CUDA(cudaEventSynchronize(h->evs[1]));
-        float t = 0.0f;
-        CVO_CUDA(cudaEventElapsedTime(&t, h->evs[0], h->evs[1]));
-        if (r > 0) best = std::min(best, (double)t);
-    }
-    CVO_CUDA(launch_finalize((IterState*)P.state.p, a.grp_stats, a.grp_cnt, nb, nullptr, h->s));
-    CVO_TRY(fetch_states(h, 1));
-    *ms = best;
-    *F = h->h_state->F;
-    return CVO_OK;
-}
-
-// Autotuner: every (cell_factor, super_delta) of a small grid is prepared
-// and its sweep timed on the caller's pair; then, for the fastest, a few
-// work-item lengths (chunk_len); the fastest is kept.
-// The results must not depend on the tuning beyond rounding: F of every
-// candidate is checked against the first one.
+// Autotuner: one registration of (X, Z) from T with the handle's parameters
+// under every tuning of a small grid, timed on the host clock as a caller
+// sees it (setup, iterations, result copies; best of two runs); the fastest
+// is kept.  First the grid cell and query-group extent (with a cutoff),
+// then, for the best of those, the work-item length.  The results must not
+// depend on the tuning beyond rounding: F at the start pose (the first
+// iteration's) of every tuning is checked against the first one's.
 cvo_status run_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double* T, cvo_tuning* out)
 {
     static const double kCell[] = {0.35, 0.5, 0.7, 1.0};
@@ -1171,62 +1138,60 @@ cvo_status run_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     const int sd0 = h->super_delta, ip0 = h->chunk_len;
     cvo_tuning best{cf0, sd0, ip0, 1e30};
     std::memset(out, 0, sizeof(*out));
-    if (X->n == 0 || Z->n == 0) {
+    if (X->n == 0 || Z->n == 0 || h->p.max_iters == 0) {
         *out = cvo_tuning{cf0, sd0, ip0, 0.0};
         return CVO_OK;
     }
-    CVO_TRY(begin_call(h, rec_bf16_of(h->p, X, Z), 1));
-    PairRes& P = h->pr[0];
-    const double ell_lo = reachable_ell_lo(h->p);
     double F_ref = 0.0;
     bool have_ref = false;
     cvo_status st = CVO_OK;
-    // the dense sum has no grid and no super-cells: only the work split is tuned
-    const std::vector<double> cells = h->dense ? std::vector<double>{cf0} : std::vector<double>(kCell, kCell + 4);
-    const std::vector<int> supers = h->dense ? std::vector<int>{sd0} : std::vector<int>(kSuper, kSuper + 3);
-    auto try_one = [&](double cf, int sd, int ip, bool regrid) {
+    double T_out[16];
+    cvo_info inf;
+    auto try_one = [&](double cf, int sd, int ip) {
         h->cell_factor = cf;
         h->super_delta = sd;
         h->chunk_len = ip;
-        // the grid levels of a registration; timed at its first and
-        // its smallest reachable lengthscale
-        if (regrid) {
-            st = prepare(h, P, X, Z, h->p.ell, ell_lo);
+        double ms = 1e30;
+        for (int rep = 0; rep < 2; ++rep) {
+            const auto t0 = std::chrono::steady_clock::now();
+            st = run_register(h, X, Z, T, T_out, &inf);
             if (st < 0) return;
+            const auto t1 = std::chrono::steady_clock::now();
+            ms = std::min(ms, std::chrono::duration<double, std::milli>(t1 - t0).count());
         }
-        double ms = 0.0, F = 0.0, ms_lo = 0.0, F_lo = 0.0;
-        st = time_sweep(h, P, T, h->p.ell, 3, &ms, &F);
-        if (st < 0) return;
-        if (ell_lo < h->p.ell) {
-            st = time_sweep(h, P, T, ell_lo, 3, &ms_lo, &F_lo);
-            if (st < 0) return;
-            ms += ms_lo;
-        }
-        if (!have_ref) {
-            F_ref = F;
-            have_ref = true;
-        } else if (std::fabs(F - F_ref) > 1e-4 * std::fabs(F_ref) + 1e-300) {
-            st = fail(CVO_ERR_CUDA, "autotune: F differs between tunings (%g vs %g)", F, F_ref);
+        st = CVO_OK;
+        double row[2] = {0.0, 0.0};   // l and F of the first iteration
+        if (cudaMemcpy(row, h->trace.p, sizeof(row), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            st = fail(CVO_ERR_CUDA, "autotune: trace copy failed");
             return;
         }
-        if (ms < best.sweep_ms) best = cvo_tuning{cf, sd, ip, ms};
+        if (!have_ref) {
+            F_ref = row[1];
+            have_ref = true;
+        } else if (std::fabs(row[1] - F_ref) > 1e-4 * std::fabs(F_ref) + 1e-300) {
+            st = fail(CVO_ERR_CUDA, "autotune: F differs between tunings (%g vs %g)", row[1], F_ref);
+            return;
+        }
+        if (ms < best.measured_ms) best = cvo_tuning{cf, sd, ip, ms};
     };
-    for (double cf : cells) {
-        for (int sd : supers) {
-            try_one(cf, sd, ip0, true);
+    // the dense sum has no grid and no super-cells: only the work split is tuned
+    if (!(h->p.cutoff_mult > 0.0)) {
+        try_one(cf0, sd0, ip0);
+    } else {
+        for (double cf : kCell) {
+            for (int sd : kSuper) {
+                try_one(cf, sd, ip0);
+                if (st < 0) break;
+            }
             if (st < 0) break;
         }
-        if (st < 0) break;
     }
-    // the item length for the best grid (it changes only the work split)
     if (st >= 0) {
         const double cfb = best.cell_factor;
         const int sdb = best.super_delta;
-        bool gridded = false;
         for (int ip : kItemLens) {
             if (ip == ip0) continue;
-            try_one(cfb, sdb, ip, !gridded);
-            gridded = true;
+            try_one(cfb, sdb, ip);
             if (st < 0) break;
         }
     }

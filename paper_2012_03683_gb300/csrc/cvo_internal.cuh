@@ -237,16 +237,6 @@ cudaError_t launch_group_cost(const LevelDesc* levels, int level, int ngroups, c
                               int dense, const IterState* st, float rc, int chunk_len, unsigned* keys, unsigned* vals,
                               unsigned* nch, cudaStream_t s);
 cudaError_t launch_gather_u32(const unsigned* src, const unsigned* idx, int n, unsigned* dst, cudaStream_t s);
-// Re-plans the current level's work items at the current pose (registration
-// with a cutoff, before each sweep): nch has room for max_groups counts, each
-// level's item table for ngroups * kMaxChunks items; *arrivals is zero
-// between launches.  k_replan(LevelDesc*, const float4* xrec, int m, int rs,
-// const IterState*, int chunk_len, unsigned* nch, unsigned* arrivals) runs on
-// replan_blocks(max_groups) blocks of 256 threads.
-cudaError_t launch_replan(LevelDesc* levels, const float4* xrec, int m, int rs, const IterState* st, int chunk_len,
-                          unsigned* nch, unsigned* arrivals, int max_groups, cudaStream_t s);
-const void* replan_kernel();
-int replan_blocks(int max_groups);
 cudaError_t launch_write_items(const LevelDesc* levels, int level, const unsigned* sorted_groups, const unsigned* nch,
                                const unsigned* offsets, int ngroups, int4* items, cudaStream_t s);
 

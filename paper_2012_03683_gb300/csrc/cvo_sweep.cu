@@ -415,74 +415,6 @@ __global__ void __launch_bounds__(128) k_group_cost(const LevelDesc* __restrict_
     }
 }
 
-// Re-plans the work items of the current level at the current pose, before
-// each sweep of a registration with a cutoff (the streams follow the pose, so
-// a plan made at the start goes stale).  One warp per query group measures
-// its candidate stream and takes ceil(length / chunk_len) chunks (at most
-// kMaxChunks); the last block to finish lays the items out group after group
-// (an exclusive scan of the chunk counts) into the level's item table and
-// publishes their number in the level's descriptor.  Every item then holds
-// at most chunk_len candidates, so a fixed round-robin deal of items to warps
-// is balanced.
-constexpr int kReplanThreads = 256;
-__global__ void __launch_bounds__(kReplanThreads) k_replan(LevelDesc* levels, const float4* __restrict__ xrec, int m,
-                                                        int rs, const IterState* __restrict__ st, int chunk_len,
-                                                        unsigned* nch, unsigned* arrivals)
-{
-    __shared__ unsigned part[kReplanThreads];
-    __shared__ int is_last;
-    if (st->done) return;   // uniform over the grid
-    const int level = st->level;
-    LevelDesc* Ld = levels + level;
-    const LevelDesc L = *Ld;
-    const int lane = threadIdx.x & 31;
-    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (g < L.ngroups) {   // warp-uniform
-        const int2 grp = L.groups[g];
-        const bool act = lane < grp.y;
-        const float4 q = xrec[(size_t)(grp.x + (act ? lane : 0)) * rs];
-        const float xq[3] = {q.x, q.y, q.z};
-        float xh[3], xl[3];
-        transform_df(xq, st->Ahi, st->Alo, st->bhi, st->blo, xh, xl);
-        Stream sm;
-        const int total = stream_setup(L, m, false, act, xh, st->rc, lane, sm) ? sm.total : 0;
-        if (lane == 0) nch[g] = total == 0 ? 0u : (unsigned)min(kMaxChunks, (total + chunk_len - 1) / chunk_len);
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) is_last = atomicAdd(arrivals, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    // exclusive scan of the chunk counts: thread t owns groups [t * per, (t + 1) * per)
-    const int ng = L.ngroups;
-    const int per = (ng + kReplanThreads - 1) / kReplanThreads;
-    const int g0 = min(ng, (int)threadIdx.x * per), g1 = min(ng, g0 + per);
-    unsigned s = 0;
-    for (int k = g0; k < g1; ++k) s += __ldcg(nch + k);
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 1; o < kReplanThreads; o <<= 1) {   // inclusive Hillis-Steele scan
-        const unsigned v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    unsigned off = part[threadIdx.x] - s;
-    int4* items = const_cast<int4*>(L.items);
-    for (int k = g0; k < g1; ++k) {
-        const int2 grp = L.groups[k];
-        const int n = (int)__ldcg(nch + k);
-        for (int c = 0; c < n; ++c) items[off + c] = make_int4(grp.x, grp.y, c | (n << 16), k);
-        off += (unsigned)n;
-    }
-    if (threadIdx.x == kReplanThreads - 1) {
-        Ld->nitems = (int)part[kReplanThreads - 1];
-        Ld->chunk_min = 0;
-        *arrivals = 0u;
-    }
-}
-
 // Work items of level Ld for the next sweep, group after group in group
 // order, from the chunk counts the sweep recorded per group.  Warps
 // 0 .. nw - 1 of the caller (w, lane) each own a contiguous range of groups,
@@ -637,28 +569,12 @@ cudaError_t launch_group_cost(const LevelDesc* levels, int level, int ngroups, c
     return cudaGetLastError();
 }
 
-const void* replan_kernel() { return (const void*)k_replan; }
-
 const void* layout_kernel() { return (const void*)k_layout; }
 
 cudaError_t launch_layout(LevelDesc* levels, const int* swept_level, const unsigned* nch_next, cudaStream_t s)
 {
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
     k_layout<<<1, kLayoutThreads, 0, s>>>(levels, swept_level, nch_next);
-    return cudaGetLastError();
-}
-
-int replan_blocks(int max_groups)
-{
-    const int b = (max_groups * 32 + kReplanThreads - 1) / kReplanThreads;
-    return b > 1 ? b : 1;
-}
-
-cudaError_t launch_replan(LevelDesc* levels, const float4* xrec, int m, int rs, const IterState* st, int chunk_len,
-                          unsigned* nch, unsigned* arrivals, int max_groups, cudaStream_t s)
-{
-    g_launch_count.fetch_add(1, std::memory_order_relaxed);
-    k_replan<<<replan_blocks(max_groups), kReplanThreads, 0, s>>>(levels, xrec, m, rs, st, chunk_len, nch, arrivals);
     return cudaGetLastError();
 }
 

@@ -67,7 +67,7 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu\n", offsetof(cvo_params, blocks), offsetof(cvo_params, max_iters),
          offsetof(cvo_params, max_step_trans), offsetof(cvo_params, feat_cutoff_mult), offsetof(cvo_info, pairs));
   printf("%zu %zu\n", offsetof(cvo_cloud, feat_dtype), offsetof(cvo_eval, candidates));
-  printf("%zu %zu %zu\n", sizeof(cvo_tuning), offsetof(cvo_tuning, chunk_len), offsetof(cvo_tuning, sweep_ms));
+  printf("%zu %zu %zu\n", sizeof(cvo_tuning), offsetof(cvo_tuning, chunk_len), offsetof(cvo_tuning, measured_ms));
   return 0;
 }
 ''')
@@ -79,5 +79,5 @@ int main(void) {
            ctypes.sizeof(cvo.Info), ctypes.sizeof(cvo.Eval),
            cvo.Params.blocks.offset, cvo.Params.max_iters.offset, cvo.Params.max_step_trans.offset,
            cvo.Params.feat_cutoff_mult.offset, cvo.Info.pairs.offset, cvo.Cloud.feat_dtype.offset, cvo.Eval.candidates.offset,
-           ctypes.sizeof(cvo.Tuning), cvo.Tuning.chunk_len.offset, cvo.Tuning.sweep_ms.offset]
+           ctypes.sizeof(cvo.Tuning), cvo.Tuning.chunk_len.offset, cvo.Tuning.measured_ms.offset]
     assert vals == got
