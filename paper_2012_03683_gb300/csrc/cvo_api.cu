@@ -662,7 +662,7 @@ cvo_status run_eval(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const 
     CVO_TRY(prepare(h, P, X, Z, h->p.ell, h->p.ell));
     CVO_TRY(init_state(h, P, 0, T, h->p.ell, 0, kPlanned));
     const int nb = single_pair_blocks(h, P);
-    SweepArgs a;
+    SweepArgs a{};
     CVO_TRY(setup_sweep(h, std::vector<PairDesc>{pair_desc(P, 0, nb)}, nb, &a, true));
     CVO_CUDA(launch_sweep(a, nb, h->s));
     CVO_CUDA(launch_finalize((IterState*)P.state.p, a.grp_stats, a.grp_cnt, nb, nullptr, h->s));
@@ -838,7 +838,7 @@ cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     const bool persistent = h->loop_mode == 2;
     const bool replan = !h->dense && !persistent;
     const int nb = replan ? h->num_sms * kSweepBlocksPerSm : single_pair_blocks(h, P);
-    SweepArgs a;
+    SweepArgs a{};
     CVO_TRY(setup_sweep(h, std::vector<PairDesc>{pair_desc(P, 0, nb)}, nb, &a, true));
     double* trace = (double*)h->trace.p;
     IterState* dst = (IterState*)P.state.p;
@@ -964,7 +964,7 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
         table.push_back(pair_desc(P, b, b + nb));
         b += nb;
     }
-    SweepArgs a;
+    SweepArgs a{};
     CVO_TRY(setup_sweep(h, table, b, &a, false));
     const long long tstride = (long long)p.max_iters * CVO_TRACE_STRIDE;
     CVO_CUDA(ensure(h->trace, (size_t)nl * tstride * sizeof(double)));

@@ -353,7 +353,7 @@ extern "C" cvo_status cvo_evaluate_dense_noalloc(const cvo_params* p, void* cuda
     NA_CUDA(launch_init_state(st, s));
     NA_CUDA(launch_pack(X->xyz, X->feat, X->feat_dtype == CVO_BF16, D, nullptr, n, xrec, rs, 0, s));
     NA_CUDA(launch_pack(Z->xyz, Z->feat, Z->feat_dtype == CVO_BF16, D, nullptr, m, zrec, rs, 0, s));
-    SweepArgs a;
+    SweepArgs a{};
     a.pairs = pair;
     a.npairs = 1;
     a.rs = rs;
@@ -365,6 +365,8 @@ extern "C" cvo_status cvo_evaluate_dense_noalloc(const cvo_params* p, void* cuda
     a.grp_cnt = gcnt;
     a.grp_arrivals = garr;
     a.fc = fc;
+    a.len_next = nullptr;   // no re-planning: the dense plan holds
+    a.swept_level = nullptr;
     NA_CUDA(launch_sweep(a, nblocks, s));
     NA_CUDA(launch_finalize(st, gstats, gcnt, nblocks, nullptr, s));
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
