@@ -365,7 +365,7 @@ extern "C" cvo_status cvo_evaluate_dense_noalloc(const cvo_params* p, void* cuda
     a.grp_cnt = gcnt;
     a.grp_arrivals = garr;
     a.fc = fc;
-    a.len_next = nullptr;   // no re-planning: the dense plan holds
+    a.nch_next = nullptr;   // no re-planning: the dense plan holds
     a.swept_level = nullptr;
     NA_CUDA(launch_sweep(a, nblocks, s));
     NA_CUDA(launch_finalize(st, gstats, gcnt, nblocks, nullptr, s));
