@@ -761,6 +761,7 @@ cvo_status run_graph_loop(cvo_handle h, const SweepArgs& a, bool batch, IterStat
     } else {
         fpn.kernel.func = (void*)finalize_kernel();
         fpn.kernel.gridDim = dim3(1);
+        fpn.kernel.blockDim = dim3(kStepThreads);
         fpn.kernel.kernelParams = fp1;
     }
     // two iterations per pass of the loop body (halves the conditional

@@ -1,9 +1,12 @@
 // One block per iteration: reduces the sweep's per-block statistics and takes
 // the step on the device, so a registration never waits on the host.
 //
-// 1. Sums the 43 statistics over the sweep blocks in double-float (hi + lo
-//    FP32 pairs, error-free two-sum), one warp per statistic, in block order:
-//    deterministic, and as accurate as FP64 accumulation at FP32 speed.
+// 1. Sums the 43 statistics over the sweep's group sums (each the sum of
+//    kGroupBlocks block partials, added by the group's last block) in
+//    double-float (hi + lo FP32 pairs, error-free two-sum): a warp per
+//    statistic, each lane over every 32nd group in group order, then a
+//    butterfly over the lanes; a fixed order, so deterministic, and as
+//    accurate as FP64 accumulation at FP32 speed.
 // 2. In FP64 (one thread): F = kappa S_W; the gradient of
 //    eta -> F(T exp(eta^)) about the lever centre c in Z's frame, mapped to
 //    the left perturbation exp(xi^) T.  With gc = (gc_w, gc_v) the centred
@@ -34,56 +37,67 @@ __global__ void k_init_state(IterState* st)
     update_derived(st);
 }
 
-__global__ void __launch_bounds__(kFinalizeThreads)
+__global__ void __launch_bounds__(kStepThreads)
 k_finalize(IterState* st, const float2* __restrict__ gs, const unsigned long long* __restrict__ gc_, int ngroups,
            double* trace, cudaGraphConditionalHandle cond, int use_cond)
 {
     static_assert(sizeof(IterState) % 8 == 0, "state is copied in 8-byte words");
     constexpr int kWords = (int)(sizeof(IterState) / 8);
+    constexpr int kWarps = kStepThreads / 32;
     __shared__ double S[kStatN];
     __shared__ float Shi[kStatN], Slo[kStatN];
     __shared__ unsigned long long cs[2];
     __shared__ unsigned long long sbuf[kWords];
-    if (st->done) {
-        // inside a graph's loop: stop it
-        if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
-        return;
-    }
-    for (int i = threadIdx.x; i < kWords; i += kFinalizeThreads) sbuf[i] = reinterpret_cast<const unsigned long long*>(st)[i];
-    // one thread per statistic: the group sums in group order, all loads first
-    if (threadIdx.x < kStatN) {
-        const float2* row = gs + (size_t)threadIdx.x * kMaxGroups;
-        float2 v[kMaxGroups];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kWords; i += kStepThreads) sbuf[i] = reinterpret_cast<const unsigned long long*>(st)[i];
+    // statistic k by warp k % kWarps: each lane adds every 32nd group sum in
+    // group order (all its loads first), then the lanes' sums are combined by
+    // a butterfly (lane 0's result is kept); fixed order, so deterministic
+    constexpr int kPerLane = kMaxGroups / 32;
+    for (int k = warp; k < kStatN; k += kWarps) {
+        const float2* row = gs + (size_t)k * kMaxGroups;
+        float2 v[kPerLane];
 #pragma unroll
-        for (int g = 0; g < kMaxGroups; ++g) v[g] = g < ngroups ? row[g] : make_float2(0.0f, 0.0f);
+        for (int j = 0; j < kPerLane; ++j) v[j] = lane + 32 * j < ngroups ? row[lane + 32 * j] : make_float2(0.0f, 0.0f);
         float hi = 0.0f, lo = 0.0f;
 #pragma unroll
-        for (int g = 0; g < kMaxGroups; ++g) df_add(hi, lo, v[g].x, v[g].y);
-        S[threadIdx.x] = (double)hi + (double)lo;
-        Shi[threadIdx.x] = hi;
-        Slo[threadIdx.x] = lo;
-    } else if (threadIdx.x == kStatN || threadIdx.x == kStatN + 1) {
-        const int c = threadIdx.x - kStatN;
-        unsigned long long t = 0;
-        for (int g = 0; g < ngroups; ++g) t += gc_[(size_t)c * kMaxGroups + g];
-        cs[c] = t;
+        for (int j = 0; j < kPerLane; ++j) df_add(hi, lo, v[j].x, v[j].y);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+            df_add(hi, lo, oh, ol);
+        }
+        if (lane == 0) {
+            S[k] = (double)hi + (double)lo;
+            Shi[k] = hi;
+            Slo[k] = lo;
+        }
+    }
+    if (warp == kWarps - 1) {   // pair and candidate counts
+        for (int c = 0; c < 2; ++c) {
+            unsigned long long t = 0;
+            for (int g = lane; g < ngroups; g += 32) t += gc_[(size_t)c * kMaxGroups + g];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) cs[c] = t;
+        }
     }
     __syncthreads();
     IterState* sst = reinterpret_cast<IterState*>(sbuf);
+    if (sst->done) {   // the sweep did nothing; inside a graph's loop: stop it
+        if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+        return;
+    }
     if (sst->mode == 0) {
         if (threadIdx.x == 0) take_step(sst, S, cs[0], cs[1], trace);
     } else if (threadIdx.x < 32) {
         step_warp(sst, S, Shi, Slo, cs[0], cs[1], trace);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kWords; i += kFinalizeThreads) reinterpret_cast<unsigned long long*>(st)[i] = sbuf[i];
+    for (int i = threadIdx.x; i < kWords; i += kStepThreads) reinterpret_cast<unsigned long long*>(st)[i] = sbuf[i];
     if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, sst->done ? 0u : 1u);
 }
 
-// Batch: block p sums pair p's block partials [b0, b1) in block order and takes
-// its step (pairs already done are skipped: their convergence mask).  The last
-// block to arrive publishes the number of pairs still running and, inside a
-// graph, keeps the loop going while any pair runs.  Counters are left at zero.
 __global__ void __launch_bounds__(kFinalizeThreads)
 k_finalize_batch(const PairDesc* __restrict__ pairs, int npairs, const float2* __restrict__ ps,
                  const unsigned long long* __restrict__ pc, int cap, double* traces, long long trace_stride,
@@ -171,7 +185,7 @@ cudaError_t launch_finalize(IterState* st, const float2* grp_stats, const unsign
 {
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
     const int ngroups = (nblocks + kGroupBlocks - 1) / kGroupBlocks;
-    k_finalize<<<1, kFinalizeThreads, 0, s>>>(st, grp_stats, grp_cnt, ngroups, trace, cudaGraphConditionalHandle{}, 0);
+    k_finalize<<<1, kStepThreads, 0, s>>>(st, grp_stats, grp_cnt, ngroups, trace, cudaGraphConditionalHandle{}, 0);
     return cudaGetLastError();
 }
 

@@ -42,9 +42,10 @@ constexpr int kMaxChunks = 64;   // most work items (chunks) one query group's s
 constexpr int kChunkLen = 128;   // default candidates per planned work item
 constexpr int kChunks = 8;       // chunks per group of the uniform items
 constexpr int kChunkMin = 64;    // shortest run-time chunk of the uniform items
-constexpr int kFinalizeThreads = 64;
-constexpr int kGroupBlocks = 32;   // sweep blocks per reduction group (the group's last block sums them)
-constexpr int kMaxGroups = 64;     // reduction groups per sweep launch (so at most 2048 sweep blocks)
+constexpr int kFinalizeThreads = 64;   // threads of a batched step block
+constexpr int kStepThreads = 384;      // threads of the single-pair step block (its registers allow 12 warps)
+constexpr int kGroupBlocks = 8;    // sweep blocks per reduction group (the group's last block sums them)
+constexpr int kMaxGroups = 256;    // reduction groups per sweep launch (so at most kGroupBlocks * kMaxGroups sweep blocks)
 constexpr int kTraceStride = 22;  // doubles per iteration in the trace (CVO_TRACE_STRIDE)
 
 // Offsets of the 43 statistics (see the finalize kernel for their use).
@@ -177,8 +178,8 @@ struct SweepLaunch {
     size_t smem;        // dynamic shared memory
 };
 cudaError_t sweep_launch_info(const FeatConst& fc, int rs, SweepLaunch* out);
-// k_finalize(IterState*, const float2* grp_stats, const unsigned long long* grp_cnt,
-//            int ngroups, double* trace, cudaGraphConditionalHandle cond, int use_cond)
+// k_finalize(IterState*, const float2* grp_stats, const unsigned long long* grp_cnt, int ngroups,
+//            double* trace, cudaGraphConditionalHandle cond, int use_cond), kStepThreads threads
 const void* finalize_kernel();
 cudaError_t launch_init_state(IterState* st, cudaStream_t s);
 // Reduces the ceil(nblocks / kGroupBlocks) group sums of a sweep and takes the step.

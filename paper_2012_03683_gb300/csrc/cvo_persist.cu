@@ -165,9 +165,12 @@ __global__ void __launch_bounds__(kSweepWarps * 32, 4) k_register(PersistArgs a)
             if (threadIdx.x < kStatN) {
                 const float2* row = a.sw.grp_stats + (size_t)threadIdx.x * kMaxGroups;
                 float hi = 0.0f, lo = 0.0f;
-                for (int g = 0; g < ngroups; ++g) {
-                    const float2 x = __ldcg(row + g);
-                    df_add(hi, lo, x.x, x.y);
+                for (int g0 = 0; g0 < ngroups; g0 += 8) {   // eight loads in flight
+                    float2 x[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) x[j] = g0 + j < ngroups ? __ldcg(row + g0 + j) : make_float2(0.0f, 0.0f);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) df_add(hi, lo, x[j].x, x[j].y);
                 }
                 S[threadIdx.x] = (double)hi + (double)lo;
                 Shi[threadIdx.x] = hi;
