@@ -14,18 +14,23 @@
 //                 consecutive queries inside one Morton super-cell whose edge
 //                 does not exceed that level's cell edge
 //   items         per level, the work items of a sweep: (first query, count,
-//                 chunk k, chunks n) -- chunk k of n of one group's candidate
-//                 stream.  Planned (evaluations, batches): n from the
-//                 stream's length at the pose of the call (about chunk_len
-//                 candidates per item), groups with the longest streams
-//                 first.  Uniform (a registration, whose pose moves): 8
-//                 chunks per group in Morton order, cut at run time to
-//                 min(8, length / 64)
+//                 chunk k | chunks n << 16, group index) -- chunk k of n of one
+//                 group's candidate stream.  Planned (evaluations, batches,
+//                 dense registrations): n from the stream's length at the
+//                 pose of the call (about chunk_len candidates per item),
+//                 groups with the longest streams first.  A registration with
+//                 a cutoff, whose pose moves: the first sweep of a level takes
+//                 uniform items (8 chunks per group in Morton order, cut at
+//                 run time to min(8, length / 64)); every sweep records each
+//                 group's stream length and k_layout lays out the next sweep's
+//                 items from them (n = ceil(length / chunk_len), group order)
 //   IterState     pose, lengthscale, annealing state and the derived
 //                 per-iteration constants, written by the finalize kernel and
 //                 read by the sweep kernel (no host round trip per iteration)
 //   partials      per sweep block: 43 linear statistics as (hi, lo) float
-//                 pairs plus the pair and candidate counts
+//                 pairs plus the pair and candidate counts; a single pair's
+//                 blocks are also summed in groups of kGroupBlocks by each
+//                 group's last block (the group sums the step kernel adds)
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>

@@ -10,7 +10,8 @@
 // point in the grid cells that overlap the group's bounding box in Z's frame,
 // grown by the cutoff radius; since the grid sorts Z by cell with x fastest,
 // the stream is a short list of contiguous runs (one per (y, z) cell row).
-// A group's stream is split into up to kChunks chunks, each its own work item.
+// A group's stream is split into chunks, each its own work item (see the
+// item layouts in cvo_internal.cuh).
 //
 // Staging.  The warp copies its stream into shared memory 32 records at a
 // time with cp.async (one record per lane, so the copies are independent and
@@ -22,9 +23,10 @@
 // Per pair: one ex2 (the geometric and squared-exponential feature exponents
 // are added in log2 units), the inner products of the label blocks, and the
 // moments W = sum w, E = sum w e, Q = sum w e e^T (e = z_j - x'_i) in FP32
-// registers.  Per work item, each lane folds its moments into 43 linear
-// statistics held in shared memory (see cvo_internal.cuh), from which the
-// finalize kernel assembles F, the se(3) gradient and the Hessian.
+// registers.  Per work item, the lanes' moments become 43 linear statistics
+// (a warp butterfly after each item; running double-float sums per lane),
+// summed per block and per group of blocks, from which the step kernel
+// assembles F, the se(3) gradient and the Hessian.
 //
 // Precision.  x'_i is formed in double-float (hi + lo FP32 pair) from the
 // FP32 input coordinates and a double-float copy of T^-1, so the offset
