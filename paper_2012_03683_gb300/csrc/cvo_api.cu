@@ -148,7 +148,8 @@ struct cvo_handle_s {
     std::vector<PairRes> pr;
     IterState* h_state = nullptr;   // pinned mirror(s)
     int h_state_cap = 0;
-    unsigned* h_misc = nullptr;     // pinned
+    unsigned* h_misc = nullptr;     // pinned, h_misc_cap words
+    int h_misc_cap = 0;
     int last_iters = 0;
     double sweep_ms = 0.0;
     int sweep_n = 0;
@@ -324,46 +325,61 @@ void set_features(cvo_handle h, int rec_bf16)
     h->dense = !(p.cutoff_mult > 0.0);
 }
 
-// Builds the grid levels of Z, the Morton-ordered queries of X and their groups
-// for lengthscales in [ell_lo, ell_hi].  Uses the handle's shared scratch.
-// The work items are planned by init_state, once the start pose is known.
-cvo_status prepare(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud* Z, double ell_hi, double ell_lo)
+// Device pointers of a pair's inputs (the caller's, or staged copies).
+struct Staged {
+    const float* xyz_x = nullptr;
+    const float* xyz_z = nullptr;
+    const void* feat_x = nullptr;
+    const void* feat_z = nullptr;
+};
+
+// prepare() in three phases, each ending where the host needs a device
+// result, so that a batch can run every pair's phase before one wait:
+// dev / hm are the pair's kMiscWords slot of scratch on the device and its
+// host copy.
+// Phase 1: inputs staged; bounding boxes and the finiteness flag into dev.
+cvo_status prepare_bbox(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud* Z, unsigned* dev, Staged* sg)
 {
-    const cvo_params& p = h->p;
     const int D = h->D;
     const int n = X->n, m = Z->n;
     P.n = n;
     P.m = m;
-    const float *xyz_x, *xyz_z;
-    const void *feat_x, *feat_z;
-    CVO_TRY(stage(h, X, 0, D, &xyz_x, &feat_x));
-    CVO_TRY(stage(h, Z, 1, D, &xyz_z, &feat_z));
-
-    // bounding boxes and finiteness
-    CVO_CUDA(ensure(h->misc, kMiscWords * sizeof(unsigned)));
-    unsigned* misc = (unsigned*)h->misc.p;
-    CVO_CUDA(cudaMemsetAsync(misc, 0, kMiscWords * sizeof(unsigned), h->s));
-    CVO_CUDA(cudaMemsetAsync(misc + 0, 0xff, 3 * sizeof(unsigned), h->s));
-    CVO_CUDA(cudaMemsetAsync(misc + 6, 0xff, 3 * sizeof(unsigned), h->s));
-    int* bad = (int*)(misc + 12);
-    CVO_CUDA(launch_bbox(xyz_x, n, misc + 0, bad, h->s));
-    CVO_CUDA(launch_bbox(xyz_z, m, misc + 6, bad, h->s));
+    CVO_TRY(stage(h, X, 0, D, &sg->xyz_x, &sg->feat_x));
+    CVO_TRY(stage(h, Z, 1, D, &sg->xyz_z, &sg->feat_z));
+    CVO_CUDA(cudaMemsetAsync(dev, 0, kMiscWords * sizeof(unsigned), h->s));
+    CVO_CUDA(cudaMemsetAsync(dev + 0, 0xff, 3 * sizeof(unsigned), h->s));
+    CVO_CUDA(cudaMemsetAsync(dev + 6, 0xff, 3 * sizeof(unsigned), h->s));
+    int* bad = (int*)(dev + 12);
+    CVO_CUDA(launch_bbox(sg->xyz_x, n, dev + 0, bad, h->s));
+    CVO_CUDA(launch_bbox(sg->xyz_z, m, dev + 6, bad, h->s));
     if (D > 0) {
-        CVO_CUDA(launch_check_feat(feat_x, (long long)n * D, X->feat_dtype == CVO_BF16, bad, h->s));
-        CVO_CUDA(launch_check_feat(feat_z, (long long)m * D, Z->feat_dtype == CVO_BF16, bad, h->s));
+        CVO_CUDA(launch_check_feat(sg->feat_x, (long long)n * D, X->feat_dtype == CVO_BF16, bad, h->s));
+        CVO_CUDA(launch_check_feat(sg->feat_z, (long long)m * D, Z->feat_dtype == CVO_BF16, bad, h->s));
     }
-    CVO_CUDA(cudaMemcpyAsync(h->h_misc, misc, 13 * sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
-    CVO_CUDA(cudaStreamSynchronize(h->s));
-    if (h->h_misc[12]) return fail(CVO_ERR_INVALID_ARG, "non-finite coordinate or feature");
+    return CVO_OK;
+}
+
+// Phase 2: from the boxes (hm), the grid levels of Z, the Morton-ordered
+// queries of X and their groups (group counts into dev + 16 + level).
+cvo_status prepare_build(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud* Z, double ell_hi,
+                         double ell_lo, const Staged& sg, const unsigned* hm, unsigned* dev)
+{
+    const cvo_params& p = h->p;
+    const int D = h->D;
+    const int n = X->n, m = Z->n;
+    const float* xyz_x = sg.xyz_x;
+    const float* xyz_z = sg.xyz_z;
+    const void* feat_x = sg.feat_x;
+    const void* feat_z = sg.feat_z;
+    if (hm[12]) return fail(CVO_ERR_INVALID_ARG, "non-finite coordinate or feature");
     float xmin[3], xmax[3], zmin[3], zmax[3];
     for (int a = 0; a < 3; ++a) {
-        xmin[a] = decode_orderable(h->h_misc[a]);
-        xmax[a] = decode_orderable(h->h_misc[3 + a]);
-        zmin[a] = decode_orderable(h->h_misc[6 + a]);
-        zmax[a] = decode_orderable(h->h_misc[9 + a]);
+        xmin[a] = decode_orderable(hm[a]);
+        xmax[a] = decode_orderable(hm[3 + a]);
+        zmin[a] = decode_orderable(hm[6 + a]);
+        zmax[a] = decode_orderable(hm[9 + a]);
         P.zc[a] = 0.5 * ((double)zmin[a] + (double)zmax[a]);
     }
-
     const int rs = h->rs;
     const int nmax = std::max(n, m);
     CVO_CUDA(ensure(h->keys, (size_t)nmax * 4));
@@ -451,15 +467,20 @@ cvo_status prepare(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud
         L.shift = sh;
         CVO_CUDA(ensure(P.groups[k], (size_t)std::max(n, 1) * sizeof(int2)));
         CVO_CUDA(launch_group_flags((const unsigned*)P.morton.p, n, sh, (unsigned*)h->flags.p, h->s));
-        CVO_CUDA(exclusive_scan_u32((const unsigned*)h->flags.p, (unsigned*)h->gidx.p, n, misc + 16 + k, h->s));
+        CVO_CUDA(exclusive_scan_u32((const unsigned*)h->flags.p, (unsigned*)h->gidx.p, n, dev + 16 + k, h->s));
         CVO_CUDA(launch_group_write((const unsigned*)P.morton.p, (const unsigned*)h->flags.p,
                                     (const unsigned*)h->gidx.p, n, sh, (int2*)P.groups[k].p, h->s));
     }
-    CVO_CUDA(cudaMemcpyAsync(h->h_misc + 16, misc + 16, P.nlevels * sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
-    CVO_CUDA(cudaStreamSynchronize(h->s));
+    return CVO_OK;
+}
+
+// Phase 3: the level descriptors, with the group counts (hm).
+cvo_status prepare_finish(cvo_handle h, PairRes& P, const unsigned* hm)
+{
+    const int n = P.n;
     for (int k = 0; k < P.nlevels; ++k) {
         LevelHost& L = P.lv[k];
-        L.ngroups = n > 0 ? (int)h->h_misc[16 + k] : 0;
+        L.ngroups = n > 0 ? (int)hm[16 + k] : 0;
         L.nitems = 0;
         LevelDesc& d = P.ld[k];
         d.h = (float)L.h;
@@ -479,6 +500,23 @@ cvo_status prepare(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud
     return CVO_OK;
 }
 
+// Builds the grid levels of Z, the Morton-ordered queries of X and their groups
+// for lengthscales in [ell_lo, ell_hi].  Uses the handle's shared scratch.
+// The work items are planned by init_state, once the start pose is known.
+cvo_status prepare(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud* Z, double ell_hi, double ell_lo)
+{
+    CVO_CUDA(ensure(h->misc, kMiscWords * sizeof(unsigned)));
+    unsigned* dev = (unsigned*)h->misc.p;
+    Staged sg;
+    CVO_TRY(prepare_bbox(h, P, X, Z, dev, &sg));
+    CVO_CUDA(cudaMemcpyAsync(h->h_misc, dev, 13 * sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
+    CVO_CUDA(cudaStreamSynchronize(h->s));
+    CVO_TRY(prepare_build(h, P, X, Z, ell_hi, ell_lo, sg, h->h_misc, dev));
+    CVO_CUDA(cudaMemcpyAsync(h->h_misc + 16, dev + 16, P.nlevels * sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
+    CVO_CUDA(cudaStreamSynchronize(h->s));
+    return prepare_finish(h, P, h->h_misc);
+}
+
 // Work items of every level of a prepared pair.  planned: at the pose of
 // its state (after k_init_state), per query group the candidate-stream
 // length at the level's design cutoff radius, groups sorted longest first,
@@ -487,10 +525,11 @@ cvo_status prepare(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud
 // near their starts.  Otherwise uniform: kChunks per group in Morton order,
 // cut at run time (a single registration, whose pose and lengthscale move
 // away from any plan made at the start).
-cvo_status plan_items(cvo_handle h, PairRes& P, bool planned)
+// In two phases (the item counts go to dev + 16 + level, then are read from
+// their host copy hm), so that a batch waits once for all its pairs.
+cvo_status plan_launch(cvo_handle h, PairRes& P, bool planned, unsigned* dev)
 {
     if (P.n == 0) return CVO_OK;
-    unsigned* misc = (unsigned*)h->misc.p;
     for (int k = 0; k < P.nlevels; ++k) {
         LevelHost& L = P.lv[k];
         const int ng = L.ngroups;
@@ -503,15 +542,19 @@ cvo_status plan_items(cvo_handle h, PairRes& P, bool planned)
         unsigned* vs = (unsigned*)h->vals.p;
         if (planned) CVO_TRY(sort_pairs(h, ng, 32, &ks, &vs));
         CVO_CUDA(launch_gather_u32((const unsigned*)h->flags.p, vs, ng, (unsigned*)h->gidx.p, h->s));
-        CVO_CUDA(exclusive_scan_u32((const unsigned*)h->gidx.p, ks, ng, misc + 16 + k, h->s));
+        CVO_CUDA(exclusive_scan_u32((const unsigned*)h->gidx.p, ks, ng, dev + 16 + k, h->s));
         CVO_CUDA(launch_write_items((const LevelDesc*)P.levels_dev.p, k, vs, (const unsigned*)h->flags.p, ks, ng,
                                     (int4*)P.items[k].p, h->s));
     }
-    CVO_CUDA(cudaMemcpyAsync(h->h_misc + 16, misc + 16, P.nlevels * sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
-    CVO_CUDA(cudaStreamSynchronize(h->s));
+    return CVO_OK;
+}
+
+cvo_status plan_finish(cvo_handle h, PairRes& P, bool planned, const unsigned* hm)
+{
+    if (P.n == 0) return CVO_OK;
     int max_items = 1;
     for (int k = 0; k < P.nlevels; ++k) {
-        P.lv[k].nitems = (int)h->h_misc[16 + k];
+        P.lv[k].nitems = (int)hm[16 + k];
         P.ld[k].items = (const int4*)P.items[k].p;
         P.ld[k].nitems = P.lv[k].nitems;
         P.ld[k].chunk_min = planned ? 0 : kChunkMin;
@@ -519,6 +562,30 @@ cvo_status plan_items(cvo_handle h, PairRes& P, bool planned)
     }
     P.max_items = max_items;
     CVO_CUDA(cudaMemcpyAsync(P.levels_dev.p, P.ld, P.nlevels * sizeof(LevelDesc), cudaMemcpyHostToDevice, h->s));
+    return CVO_OK;
+}
+
+cvo_status plan_items(cvo_handle h, PairRes& P, bool planned)
+{
+    if (P.n == 0) return CVO_OK;
+    unsigned* dev = (unsigned*)h->misc.p;
+    CVO_TRY(plan_launch(h, P, planned, dev));
+    CVO_CUDA(cudaMemcpyAsync(h->h_misc + 16, dev + 16, P.nlevels * sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
+    CVO_CUDA(cudaStreamSynchronize(h->s));
+    return plan_finish(h, P, planned, h->h_misc);
+}
+
+cvo_status ensure_host_misc(cvo_handle h, int words)
+{
+    if (words <= h->h_misc_cap) return CVO_OK;
+    unsigned* p = nullptr;
+    if (cudaMallocHost((void**)&p, (size_t)words * sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CVO_ERR_OOM, "cudaMallocHost failed");
+    }
+    cudaFreeHost(h->h_misc);
+    h->h_misc = p;
+    h->h_misc_cap = words;
     return CVO_OK;
 }
 
@@ -967,10 +1034,50 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
     CVO_TRY(begin_call(h, bf, nl));
     const double ell_lo = reachable_ell_lo(p);
     long long work = 0;
-    for (int i = 0; i < nl; ++i) {
-        CVO_TRY(prepare(h, h->pr[i], X + live[i], Z + live[i], p.ell, ell_lo));
-        CVO_TRY(init_state(h, h->pr[i], i, T_init + 16 * live[i], p.ell, 1, kPlanned));
-        work += h->pr[i].max_items;
+    bool on_device = true;
+    for (int k : live) on_device = on_device && X[k].on_device && Z[k].on_device;
+    if (on_device && nl > 1) {
+        // every pair's setup phase before one wait per phase (a wait per pair
+        // and phase left the device idle between small kernels); the pairs
+        // share the handle's scratch in stream order, each with its own slot
+        // of results
+        CVO_CUDA(ensure(h->misc, (size_t)nl * kMiscWords * sizeof(unsigned)));
+        CVO_TRY(ensure_host_misc(h, nl * kMiscWords));
+        unsigned* dev = (unsigned*)h->misc.p;
+        unsigned* hm = h->h_misc;
+        const size_t slots = (size_t)nl * kMiscWords * sizeof(unsigned);
+        int nmax = 1;
+        for (int k : live) nmax = std::max(nmax, std::max(X[k].n, Z[k].n));
+        for (DevBuf* b : {&h->keys, &h->vals, &h->keys2, &h->vals2, &h->flags, &h->gidx})
+            CVO_CUDA(ensure(*b, (size_t)nmax * 4));   // once, before any pair queues work on them
+        CVO_CUDA(ensure(h->sort_tmp, radix_sort_temp_bytes(nmax)));
+        std::vector<Staged> sg(nl);
+        for (int i = 0; i < nl; ++i)
+            CVO_TRY(prepare_bbox(h, h->pr[i], X + live[i], Z + live[i], dev + (size_t)i * kMiscWords, &sg[i]));
+        CVO_CUDA(cudaMemcpyAsync(hm, dev, slots, cudaMemcpyDeviceToHost, h->s));
+        CVO_CUDA(cudaStreamSynchronize(h->s));
+        for (int i = 0; i < nl; ++i)
+            CVO_TRY(prepare_build(h, h->pr[i], X + live[i], Z + live[i], p.ell, ell_lo, sg[i], hm + (size_t)i * kMiscWords,
+                                  dev + (size_t)i * kMiscWords));
+        CVO_CUDA(cudaMemcpyAsync(hm, dev, slots, cudaMemcpyDeviceToHost, h->s));
+        CVO_CUDA(cudaStreamSynchronize(h->s));
+        for (int i = 0; i < nl; ++i) {
+            CVO_TRY(prepare_finish(h, h->pr[i], hm + (size_t)i * kMiscWords));
+            CVO_TRY(init_state(h, h->pr[i], i, T_init + 16 * live[i], p.ell, 1, kNoPlan));
+            CVO_TRY(plan_launch(h, h->pr[i], true, dev + (size_t)i * kMiscWords));
+        }
+        CVO_CUDA(cudaMemcpyAsync(hm, dev, slots, cudaMemcpyDeviceToHost, h->s));
+        CVO_CUDA(cudaStreamSynchronize(h->s));
+        for (int i = 0; i < nl; ++i) {
+            CVO_TRY(plan_finish(h, h->pr[i], true, hm + (size_t)i * kMiscWords));
+            work += h->pr[i].max_items;
+        }
+    } else {
+        for (int i = 0; i < nl; ++i) {
+            CVO_TRY(prepare(h, h->pr[i], X + live[i], Z + live[i], p.ell, ell_lo));
+            CVO_TRY(init_state(h, h->pr[i], i, T_init + 16 * live[i], p.ell, 1, kPlanned));
+            work += h->pr[i].max_items;
+        }
     }
     // split eight waves of resident blocks among the pairs in proportion to
     // their work items (largest remainders, at least one item per warp): the
@@ -1310,6 +1417,7 @@ cvo_status cvo_create(const cvo_params* params, void* cuda_stream, cvo_handle* o
         delete h;
         return fail(CVO_ERR_OOM, "cudaMallocHost failed");
     }
+    h->h_misc_cap = kMiscWords;
     *out = h;
     return CVO_OK;
 }

@@ -105,7 +105,7 @@ __global__ void k_morton_keys(const float* __restrict__ xyz, int n, float ox, fl
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortTile = 4096;                  // keys per block
+constexpr int kSortTile = 1024;                  // keys per block (small tiles: the sorts here are short and latency bound)
 constexpr int kSortSub = kSortTile / kSortWarps; // keys per warp
 
 __global__ void k_radix_hist(const unsigned* __restrict__ keys, int n, int shift, unsigned* hist, int nb)

@@ -83,3 +83,19 @@ def test_batch_with_empty_pair_and_host_buffers():
     assert er <= POSE_TOL and et <= POSE_TOL
     er, et = pose_err(T_batch[2], T_host_single)
     assert er <= POSE_TOL and et <= POSE_TOL
+
+
+def test_phased_setup_of_device_batches_equals_per_pair_setup():
+    """A batch of device-resident pairs runs each setup phase for all pairs
+    before one wait; a batch with a host-resident pair sets the pairs up one
+    after another.  The kernels and their order per pair are the same, so the
+    results are bitwise equal."""
+    pairs, args = small_batch(n_pairs=4, seed=31)
+    host_last = args[:3] + [(pairs[3].X, pairs[3].Z, np.eye(4), scenes.bf16_bits(pairs[3].FX),
+                             scenes.bf16_bits(pairs[3].FZ))]
+    with cvo.CVO(blocks=pairs[0].blocks, **KW) as h:
+        T_dev, infos_dev, _ = h.register_batch(args)
+        T_mix, infos_mix, _ = h.register_batch(host_last)
+    for k in range(4):
+        assert np.array_equal(T_dev[k], T_mix[k]), k
+        assert infos_dev[k]["F"] == infos_mix[k]["F"] and infos_dev[k]["pairs"] == infos_mix[k]["pairs"]
