@@ -165,6 +165,88 @@ __global__ void k_radix_scatter(const unsigned* __restrict__ keys, const unsigne
     }
 }
 
+// Short arrays (n <= kSmallSort): the whole LSD radix sort in one block, in
+// shared memory, one launch instead of three per digit.  Each warp owns a
+// contiguous run of n / 32 keys; per digit pass: the warps' digit counts, the
+// digit offsets (totals of smaller digits plus the counts of earlier warps),
+// then a stable scatter (warps in order, lanes in order within a warp).
+constexpr int kSmallSort = 8192;
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallWarps = kSmallThreads / 32;
+constexpr size_t kSmallSmem = (size_t)4 * kSmallSort * sizeof(unsigned) + (size_t)kSmallWarps * 256 * sizeof(unsigned);
+
+__global__ void __launch_bounds__(kSmallThreads) k_sort_small(unsigned* keys, unsigned* vals, int n, int nbits)
+{
+    extern __shared__ unsigned sm[];
+    unsigned* kb[2] = {sm, sm + kSmallSort};
+    unsigned* vb[2] = {sm + 2 * kSmallSort, sm + 3 * kSmallSort};
+    unsigned* wcnt = sm + 4 * kSmallSort;   // [kSmallWarps][256]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < n; i += kSmallThreads) {
+        kb[0][i] = keys[i];
+        vb[0][i] = vals[i];
+    }
+    const int per = (n + kSmallWarps - 1) / kSmallWarps;
+    const int w0 = min(n, warp * per), w1 = min(n, w0 + per);
+    const unsigned lt = (1u << lane) - 1u;
+    int cur = 0;
+    for (int shift = 0; shift < nbits; shift += 8) {
+        for (int d = threadIdx.x; d < kSmallWarps * 256; d += kSmallThreads) wcnt[d] = 0u;
+        __syncthreads();
+        const unsigned* kin = kb[cur];
+        for (int i = w0 + lane; i < w1; i += 32) atomicAdd(&wcnt[warp * 256 + ((kin[i] >> shift) & 255u)], 1u);
+        __syncthreads();
+        if (threadIdx.x < 256) {   // per digit: running offsets over the warps, then over the digits
+            const int d = threadIdx.x;
+            unsigned run = 0;
+            for (int w = 0; w < kSmallWarps; ++w) {
+                const unsigned c = wcnt[w * 256 + d];
+                wcnt[w * 256 + d] = run;
+                run += c;
+            }
+            // exclusive scan of the digit totals across the 256 threads (8 warps)
+            unsigned incl = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            __shared__ unsigned wsum[8];
+            if (lane == 31) wsum[warp] = incl;
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            unsigned before = incl - run;
+            for (int w = 0; w < warp; ++w) before += wsum[w];
+            for (int w = 0; w < kSmallWarps; ++w) wcnt[w * 256 + d] += before;
+        }
+        __syncthreads();
+        unsigned* kout = kb[cur ^ 1];
+        unsigned* vout = vb[cur ^ 1];
+        const unsigned* vin = vb[cur];
+        for (int r = w0; r < w1; r += 32) {
+            const int i = r + lane;
+            const bool ok = i < w1;
+            const unsigned valid = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                const unsigned k = kin[i];
+                const unsigned d = (k >> shift) & 255u;
+                const unsigned peers = __match_any_sync(valid, d);
+                const unsigned pos = wcnt[warp * 256 + d] + __popc(peers & lt);
+                kout[pos] = k;
+                vout[pos] = vin[i];
+                __syncwarp(valid);
+                if ((peers & lt) == 0) wcnt[warp * 256 + d] += __popc(peers);
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    for (int i = threadIdx.x; i < n; i += kSmallThreads) {
+        keys[i] = kb[cur][i];
+        vals[i] = vb[cur][i];
+    }
+}
+
 // single-block exclusive scan; total (optional) receives the sum
 __global__ void k_scan_single(const unsigned* __restrict__ in, unsigned* out, int n, unsigned* total)
 {
@@ -353,6 +435,18 @@ cudaError_t radix_sort_pairs(unsigned* keys, unsigned* vals, unsigned* keys_alt,
 {
     *result_in_alt = 0;
     if (n <= 1) return cudaSuccess;
+    if (n <= kSmallSort) {
+        static bool attr_set = false;   // one-time opt-in above the 48 KB default
+        if (!attr_set) {
+            const cudaError_t e = cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)kSmallSmem);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        g_launch_count.fetch_add(1, std::memory_order_relaxed);
+        k_sort_small<<<1, kSmallThreads, kSmallSmem, s>>>(keys, vals, n, nbits);
+        return cudaGetLastError();
+    }
     const int nb = (n + kSortTile - 1) / kSortTile;
     unsigned* hist = (unsigned*)temp;
     unsigned* offs = hist + 256 * nb;
