@@ -59,6 +59,15 @@ struct DevBuf {
     size_t cap = 0;
 };
 
+// A stream with its own setup scratch: the pairs of a batch are set up on
+// several of these at once (their kernels are small and overlap).
+constexpr int kSetupLanes = 4;
+struct SetupLane {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    DevBuf keys, vals, keys2, vals2, sort_tmp, flags, gidx;
+};
+
 cudaError_t ensure(DevBuf& b, size_t bytes)
 {
     if (bytes <= b.cap && b.p) return cudaSuccess;
@@ -139,6 +148,9 @@ struct cvo_handle_s {
     // scratch shared by every pair's setup (used one pair at a time)
     DevBuf stage_xyz[2], stage_feat[2];
     DevBuf keys, vals, keys2, vals2, sort_tmp, flags, gidx, misc;
+    // a batch sets its pairs up on kSetupLanes streams, each with its own
+    // copy of the setup scratch (created on first use)
+    SetupLane lanes[kSetupLanes];
     // sweep / finalize scratch
     DevBuf part_stats, part_cnt, grp_stats, grp_cnt, grp_arrivals, pairs_dev, counters, trace;
     // gradients with respect to the inputs: device outputs for host callers,
@@ -586,6 +598,39 @@ cvo_status ensure_host_misc(cvo_handle h, int words)
     cudaFreeHost(h->h_misc);
     h->h_misc = p;
     h->h_misc_cap = words;
+    return CVO_OK;
+}
+
+// Exchanges the handle's stream and setup scratch with a lane's, so that the
+// setup functions run on the lane; a second call restores them.
+void swap_lane(cvo_handle h, SetupLane& L)
+{
+    std::swap(h->s, L.s);
+    std::swap(h->keys, L.keys);
+    std::swap(h->vals, L.vals);
+    std::swap(h->keys2, L.keys2);
+    std::swap(h->vals2, L.vals2);
+    std::swap(h->sort_tmp, L.sort_tmp);
+    std::swap(h->flags, L.flags);
+    std::swap(h->gidx, L.gidx);
+}
+
+cvo_status ensure_lanes(cvo_handle h)
+{
+    for (SetupLane& L : h->lanes) {
+        if (!L.s) CVO_CUDA(cudaStreamCreateWithFlags(&L.s, cudaStreamNonBlocking));
+        if (!L.ev) CVO_CUDA(cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming));
+    }
+    return CVO_OK;
+}
+
+// The handle's stream waits for every lane's work so far.
+cvo_status join_lanes(cvo_handle h)
+{
+    for (SetupLane& L : h->lanes) {
+        CVO_CUDA(cudaEventRecord(L.ev, L.s));
+        CVO_CUDA(cudaStreamWaitEvent(h->s, L.ev, 0));
+    }
     return CVO_OK;
 }
 
@@ -1038,34 +1083,54 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
     for (int k : live) on_device = on_device && X[k].on_device && Z[k].on_device;
     if (on_device && nl > 1) {
         // every pair's setup phase before one wait per phase (a wait per pair
-        // and phase left the device idle between small kernels); the pairs
-        // share the handle's scratch in stream order, each with its own slot
-        // of results
+        // and phase left the device idle between small kernels), the pairs
+        // spread over kSetupLanes streams, each with its own scratch, so
+        // that their small kernels overlap; each pair has its own slot of
+        // results
         CVO_CUDA(ensure(h->misc, (size_t)nl * kMiscWords * sizeof(unsigned)));
         CVO_TRY(ensure_host_misc(h, nl * kMiscWords));
+        CVO_TRY(ensure_lanes(h));
         unsigned* dev = (unsigned*)h->misc.p;
         unsigned* hm = h->h_misc;
         const size_t slots = (size_t)nl * kMiscWords * sizeof(unsigned);
         int nmax = 1;
         for (int k : live) nmax = std::max(nmax, std::max(X[k].n, Z[k].n));
-        for (DevBuf* b : {&h->keys, &h->vals, &h->keys2, &h->vals2, &h->flags, &h->gidx})
-            CVO_CUDA(ensure(*b, (size_t)nmax * 4));   // once, before any pair queues work on them
-        CVO_CUDA(ensure(h->sort_tmp, radix_sort_temp_bytes(nmax)));
+        for (SetupLane& L : h->lanes) {   // sized once, before any pair queues work on them
+            for (DevBuf* b : {&L.keys, &L.vals, &L.keys2, &L.vals2, &L.flags, &L.gidx})
+                CVO_CUDA(ensure(*b, (size_t)nmax * 4));
+            CVO_CUDA(ensure(L.sort_tmp, radix_sort_temp_bytes(nmax)));
+            CVO_CUDA(cudaEventRecord(L.ev, h->s));   // the lanes start after the handle's stream
+            CVO_CUDA(cudaStreamWaitEvent(L.s, L.ev, 0));
+        }
+        // runs f(i) for every pair on its lane, then joins the lanes
+        auto on_lanes = [&](auto&& f) -> cvo_status {
+            cvo_status st = CVO_OK;
+            for (int i = 0; i < nl && st == CVO_OK; ++i) {
+                SetupLane& L = h->lanes[i % kSetupLanes];
+                swap_lane(h, L);
+                st = f(i);
+                swap_lane(h, L);
+            }
+            if (st != CVO_OK) return st;
+            return join_lanes(h);
+        };
         std::vector<Staged> sg(nl);
-        for (int i = 0; i < nl; ++i)
-            CVO_TRY(prepare_bbox(h, h->pr[i], X + live[i], Z + live[i], dev + (size_t)i * kMiscWords, &sg[i]));
+        CVO_TRY(on_lanes([&](int i) {
+            return prepare_bbox(h, h->pr[i], X + live[i], Z + live[i], dev + (size_t)i * kMiscWords, &sg[i]);
+        }));
         CVO_CUDA(cudaMemcpyAsync(hm, dev, slots, cudaMemcpyDeviceToHost, h->s));
         CVO_CUDA(cudaStreamSynchronize(h->s));
-        for (int i = 0; i < nl; ++i)
-            CVO_TRY(prepare_build(h, h->pr[i], X + live[i], Z + live[i], p.ell, ell_lo, sg[i], hm + (size_t)i * kMiscWords,
-                                  dev + (size_t)i * kMiscWords));
+        CVO_TRY(on_lanes([&](int i) {
+            return prepare_build(h, h->pr[i], X + live[i], Z + live[i], p.ell, ell_lo, sg[i],
+                                 hm + (size_t)i * kMiscWords, dev + (size_t)i * kMiscWords);
+        }));
         CVO_CUDA(cudaMemcpyAsync(hm, dev, slots, cudaMemcpyDeviceToHost, h->s));
         CVO_CUDA(cudaStreamSynchronize(h->s));
-        for (int i = 0; i < nl; ++i) {
+        CVO_TRY(on_lanes([&](int i) {
             CVO_TRY(prepare_finish(h, h->pr[i], hm + (size_t)i * kMiscWords));
             CVO_TRY(init_state(h, h->pr[i], i, T_init + 16 * live[i], p.ell, 1, kNoPlan));
-            CVO_TRY(plan_launch(h, h->pr[i], true, dev + (size_t)i * kMiscWords));
-        }
+            return plan_launch(h, h->pr[i], true, dev + (size_t)i * kMiscWords);
+        }));
         CVO_CUDA(cudaMemcpyAsync(hm, dev, slots, cudaMemcpyDeviceToHost, h->s));
         CVO_CUDA(cudaStreamSynchronize(h->s));
         for (int i = 0; i < nl; ++i) {
@@ -1432,6 +1497,12 @@ cvo_status cvo_destroy(cvo_handle h)
                       &h->grp_stats, &h->grp_cnt, &h->grp_arrivals, &h->pairs_dev, &h->counters, &h->trace,
                       &h->bw_out[0], &h->bw_out[1], &h->bw_out[2], &h->bw_out[3], &h->bw_tq, &h->bw_dell, &h->bw_part};
     for (DevBuf* b : bufs) release(*b);
+    for (SetupLane& L : h->lanes) {
+        if (L.s) cudaStreamSynchronize(L.s);
+        for (DevBuf* b : {&L.keys, &L.vals, &L.keys2, &L.vals2, &L.sort_tmp, &L.flags, &L.gidx}) release(*b);
+        if (L.ev) cudaEventDestroy(L.ev);
+        if (L.s) cudaStreamDestroy(L.s);
+    }
     for (PairRes& P : h->pr) P.free_all();
     for (cudaEvent_t e : h->evs) cudaEventDestroy(e);
     if (h->h_state) cudaFreeHost(h->h_state);
