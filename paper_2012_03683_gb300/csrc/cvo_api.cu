@@ -582,8 +582,12 @@ cvo_status plan_items(cvo_handle h, PairRes& P, bool planned)
     if (P.n == 0) return CVO_OK;
     unsigned* dev = (unsigned*)h->misc.p;
     CVO_TRY(plan_launch(h, P, planned, dev));
-    CVO_CUDA(cudaMemcpyAsync(h->h_misc + 16, dev + 16, P.nlevels * sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
-    CVO_CUDA(cudaStreamSynchronize(h->s));
+    if (planned) {
+        CVO_CUDA(cudaMemcpyAsync(h->h_misc + 16, dev + 16, P.nlevels * sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
+        CVO_CUDA(cudaStreamSynchronize(h->s));
+    } else {   // uniform: kChunks items for every group, known without a wait
+        for (int k = 0; k < P.nlevels; ++k) h->h_misc[16 + k] = (unsigned)(kChunks * P.lv[k].ngroups);
+    }
     return plan_finish(h, P, planned, h->h_misc);
 }
 
