@@ -58,8 +58,9 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def profile_traffic(kernel_src):
-    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+def profile_value(kernel_src, key):
+    """A per-launch figure of the sweep (key: traffic_bytes_per_launch,
+    warp_instructions_per_launch) from the committed ncu summary, if it was
     taken on the current kernel source (the files in kernel_src, hashed in
     order); else None."""
     path = os.path.join(ROOT, "profiles", "sweep_street-20k.md")
@@ -67,7 +68,7 @@ def profile_traffic(kernel_src):
         return None
     text = open(path).read()
     m = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
-    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    t = re.search(key + r":\s*([0-9.eE+]+)", text)
     if not m or not t:
         return None
     data = b"".join(open(f, "rb").read() for f in kernel_src)
@@ -457,7 +458,22 @@ def main():
     achieved = sweep_pairs * fpp / (sweep_ms * 1e-3) / 1e12 if sweep_ms > 0 else None
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     csrc = os.path.join(ROOT, "paper_2012_03683_gb300", "csrc")
-    traffic = profile_traffic([os.path.join(csrc, "cvo_sweep.cu"), os.path.join(csrc, "cvo_sweep_dev.cuh")])
+    sweep_src = [os.path.join(csrc, "cvo_sweep.cu"), os.path.join(csrc, "cvo_sweep_dev.cuh")]
+    traffic = profile_value(sweep_src, "traffic_bytes_per_launch")
+    winst = profile_value(sweep_src, "warp_instructions_per_launch")
+    sweep_ms_avg = sweep_ms / max(sweep_n, 1)
+    # the same launches against the SM's instruction issue rate (one warp
+    # instruction per scheduler per clock, 4 schedulers per SM): the bound of
+    # a kernel whose FP32 pipes are not the limit
+    issue_peak = SM_COUNT * 4 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    issue = {"achieved_warp_inst_per_s": winst / (sweep_ms_avg * 1e-3) if (winst and sweep_ms_avg > 0) else None,
+             "peak_warp_inst_per_s": issue_peak,
+             "frac": (winst / (sweep_ms_avg * 1e-3) / issue_peak) if (winst and sweep_ms_avg > 0) else None,
+             "warp_instructions_per_launch": winst,
+             "source": "smsp__inst_executed.sum, mean of the 3 launches of the committed ncu capture "
+                       "(profiles/sweep_street-20k.md, "
+                       "same source hash) over the CUDA-event time per launch; peak: 152 SMs x 4 schedulers "
+                       "x sm_max_mhz"}
     dT = np.linalg.inv(T_last) @ p.T_true
     pose_err = {"rot_rad": float(math.acos(max(-1.0, min(1.0, (np.trace(dT[:3, :3]) - 1.0) / 2.0)))),
                 "trans_m": float(np.linalg.norm(dT[:3, 3]))}
@@ -475,7 +491,7 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None,
                      "traffic": traffic, "kernel": "k_sweep (fused neighbour sweep)",
-                     "flops_per_pair": fpp, "sweep_ms_avg": sweep_ms / max(sweep_n, 1), "sweep_launches": sweep_n,
+                     "flops_per_pair": fpp, "sweep_ms_avg": sweep_ms_avg, "sweep_launches": sweep_n,
                      "timing": "CUDA events around each sweep launch, over the same registrations queued "
                                "from the host (the timed steps run the loop as one CUDA graph)",
                      "ms_per_registration_event_timed": timed_ms / args.steps,
@@ -488,7 +504,8 @@ def main():
                                      (SM_COUNT * EX2_PER_CLK_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6)
                                      if sweep_ms > 0 else None,
                              "peak_source": f"152 SMs x {EX2_PER_CLK_SM} ex2/clk/SM (measured on a GB300 with an "
-                                            "independent-chain ex2.approx throughput loop) x sm_max_mhz"}},
+                                            "independent-chain ex2.approx throughput loop) x sm_max_mhz"},
+                     "issue": issue},
         "clocks": clocks,
         "final_pose_err_vs_truth": pose_err,
         "batch": batch,
