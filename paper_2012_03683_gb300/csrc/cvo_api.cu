@@ -337,6 +337,39 @@ void set_features(cvo_handle h, int rec_bf16)
     h->dense = !(p.cutoff_mult > 0.0);
 }
 
+// Exchanges the handle's stream and setup scratch with a lane's, so that the
+// setup functions run on the lane; a second call restores them.
+void swap_lane(cvo_handle h, SetupLane& L)
+{
+    std::swap(h->s, L.s);
+    std::swap(h->keys, L.keys);
+    std::swap(h->vals, L.vals);
+    std::swap(h->keys2, L.keys2);
+    std::swap(h->vals2, L.vals2);
+    std::swap(h->sort_tmp, L.sort_tmp);
+    std::swap(h->flags, L.flags);
+    std::swap(h->gidx, L.gidx);
+}
+
+cvo_status ensure_lanes(cvo_handle h)
+{
+    for (SetupLane& L : h->lanes) {
+        if (!L.s) CVO_CUDA(cudaStreamCreateWithFlags(&L.s, cudaStreamNonBlocking));
+        if (!L.ev) CVO_CUDA(cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming));
+    }
+    return CVO_OK;
+}
+
+// The handle's stream waits for every lane's work so far.
+cvo_status join_lanes(cvo_handle h)
+{
+    for (SetupLane& L : h->lanes) {
+        CVO_CUDA(cudaEventRecord(L.ev, L.s));
+        CVO_CUDA(cudaStreamWaitEvent(h->s, L.ev, 0));
+    }
+    return CVO_OK;
+}
+
 // Device pointers of a pair's inputs (the caller's, or staged copies).
 struct Staged {
     const float* xyz_x = nullptr;
@@ -374,7 +407,7 @@ cvo_status prepare_bbox(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_
 // Phase 2: from the boxes (hm), the grid levels of Z, the Morton-ordered
 // queries of X and their groups (group counts into dev + 16 + level).
 cvo_status prepare_build(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud* Z, double ell_hi,
-                         double ell_lo, const Staged& sg, const unsigned* hm, unsigned* dev)
+                         double ell_lo, const Staged& sg, const unsigned* hm, unsigned* dev, bool fan_out)
 {
     const cvo_params& p = h->p;
     const int D = h->D;
@@ -394,10 +427,14 @@ cvo_status prepare_build(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo
     }
     const int rs = h->rs;
     const int nmax = std::max(n, m);
+    // the handle's own setup scratch, which the work plan uses after this
+    // (with fan_out the builds below run on the lanes' copies)
     CVO_CUDA(ensure(h->keys, (size_t)nmax * 4));
     CVO_CUDA(ensure(h->vals, (size_t)nmax * 4));
     CVO_CUDA(ensure(h->keys2, (size_t)nmax * 4));
     CVO_CUDA(ensure(h->vals2, (size_t)nmax * 4));
+    CVO_CUDA(ensure(h->flags, (size_t)std::max(n, 1) * 4));
+    CVO_CUDA(ensure(h->gidx, (size_t)std::max(n, 1) * 4));
 
     // grid levels of Z
     if (h->dense) {
@@ -429,8 +466,39 @@ cvo_status prepare_build(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo
             L.ox = zmin[0]; L.oy = zmin[1]; L.oz = zmin[2];
         }
     }
+    // with fan_out, the grid levels and the queries are built on the setup
+    // lanes at once (each lane its own scratch), joined at the end
+    if (fan_out) {
+        CVO_TRY(ensure_lanes(h));
+        for (SetupLane& L : h->lanes) {
+            for (DevBuf* b : {&L.keys, &L.vals, &L.keys2, &L.vals2, &L.flags, &L.gidx})
+                CVO_CUDA(ensure(*b, (size_t)std::max(nmax, 1) * 4));
+            CVO_CUDA(ensure(L.sort_tmp, radix_sort_temp_bytes(nmax)));
+            CVO_CUDA(cudaEventRecord(L.ev, h->s));   // after the inputs' staging and the boxes
+            CVO_CUDA(cudaStreamWaitEvent(L.s, L.ev, 0));
+        }
+    }
+    // the lane whose stream and scratch the handle holds now; given back on
+    // every way out of this function
+    struct Held {
+        cvo_handle h;
+        SetupLane* lane = nullptr;
+        void drop()
+        {
+            if (lane) swap_lane(h, *lane);
+            lane = nullptr;
+        }
+        ~Held() { drop(); }
+    } held{h};
+    auto use_lane = [&](int i) {
+        if (!fan_out) return;
+        held.drop();
+        held.lane = &h->lanes[i % kSetupLanes];
+        swap_lane(h, *held.lane);
+    };
     for (int k = 0; k < P.nlevels; ++k) {
         LevelHost& L = P.lv[k];
+        use_lane(1 + k % (kSetupLanes - 1));
         CVO_CUDA(ensure(P.zrec[k], (size_t)std::max(m, 1) * rs * sizeof(float4)));
         CVO_CUDA(ensure(P.cell_start[k], (size_t)(L.ncells + 1) * sizeof(int)));
         if (h->dense) {
@@ -450,6 +518,7 @@ cvo_status prepare_build(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo
     }
 
     // queries: Morton order of X in its own frame
+    use_lane(0);
     double ext = 0.0;
     for (int a = 0; a < 3; ++a) ext = std::max(ext, (double)xmax[a] - xmin[a]);
     const double cell0 = std::max(ext / 1024.0, 1e-6);
@@ -483,6 +552,8 @@ cvo_status prepare_build(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo
         CVO_CUDA(launch_group_write((const unsigned*)P.morton.p, (const unsigned*)h->flags.p,
                                     (const unsigned*)h->gidx.p, n, sh, (int2*)P.groups[k].p, h->s));
     }
+    held.drop();
+    if (fan_out) CVO_TRY(join_lanes(h));
     return CVO_OK;
 }
 
@@ -523,7 +594,7 @@ cvo_status prepare(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud
     CVO_TRY(prepare_bbox(h, P, X, Z, dev, &sg));
     CVO_CUDA(cudaMemcpyAsync(h->h_misc, dev, 13 * sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
     CVO_CUDA(cudaStreamSynchronize(h->s));
-    CVO_TRY(prepare_build(h, P, X, Z, ell_hi, ell_lo, sg, h->h_misc, dev));
+    CVO_TRY(prepare_build(h, P, X, Z, ell_hi, ell_lo, sg, h->h_misc, dev, true));
     CVO_CUDA(cudaMemcpyAsync(h->h_misc + 16, dev + 16, P.nlevels * sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
     CVO_CUDA(cudaStreamSynchronize(h->s));
     return prepare_finish(h, P, h->h_misc);
@@ -602,39 +673,6 @@ cvo_status ensure_host_misc(cvo_handle h, int words)
     cudaFreeHost(h->h_misc);
     h->h_misc = p;
     h->h_misc_cap = words;
-    return CVO_OK;
-}
-
-// Exchanges the handle's stream and setup scratch with a lane's, so that the
-// setup functions run on the lane; a second call restores them.
-void swap_lane(cvo_handle h, SetupLane& L)
-{
-    std::swap(h->s, L.s);
-    std::swap(h->keys, L.keys);
-    std::swap(h->vals, L.vals);
-    std::swap(h->keys2, L.keys2);
-    std::swap(h->vals2, L.vals2);
-    std::swap(h->sort_tmp, L.sort_tmp);
-    std::swap(h->flags, L.flags);
-    std::swap(h->gidx, L.gidx);
-}
-
-cvo_status ensure_lanes(cvo_handle h)
-{
-    for (SetupLane& L : h->lanes) {
-        if (!L.s) CVO_CUDA(cudaStreamCreateWithFlags(&L.s, cudaStreamNonBlocking));
-        if (!L.ev) CVO_CUDA(cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming));
-    }
-    return CVO_OK;
-}
-
-// The handle's stream waits for every lane's work so far.
-cvo_status join_lanes(cvo_handle h)
-{
-    for (SetupLane& L : h->lanes) {
-        CVO_CUDA(cudaEventRecord(L.ev, L.s));
-        CVO_CUDA(cudaStreamWaitEvent(h->s, L.ev, 0));
-    }
     return CVO_OK;
 }
 
@@ -1126,7 +1164,7 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
         CVO_CUDA(cudaStreamSynchronize(h->s));
         CVO_TRY(on_lanes([&](int i) {
             return prepare_build(h, h->pr[i], X + live[i], Z + live[i], p.ell, ell_lo, sg[i],
-                                 hm + (size_t)i * kMiscWords, dev + (size_t)i * kMiscWords);
+                                 hm + (size_t)i * kMiscWords, dev + (size_t)i * kMiscWords, false);
         }));
         CVO_CUDA(cudaMemcpyAsync(hm, dev, slots, cudaMemcpyDeviceToHost, h->s));
         CVO_CUDA(cudaStreamSynchronize(h->s));
