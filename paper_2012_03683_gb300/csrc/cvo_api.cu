@@ -606,8 +606,9 @@ cvo_status prepare(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud
 // each split into ceil(length / chunk_len) chunks (at most kMaxChunks) --
 // exact for an evaluation, and good for a batch of pairs whose poses stay
 // near their starts.  Otherwise uniform: kChunks per group in Morton order,
-// cut at run time (a single registration, whose pose and lengthscale move
-// away from any plan made at the start).
+// cut at run time: the first sweep of each grid level of a registration
+// with a cutoff, whose later sweeps take the items k_layout lays out from
+// the stream lengths the previous sweep recorded.
 // In two phases (the item counts go to dev + 16 + level, then are read from
 // their host copy hm), so that a batch waits once for all its pairs.
 cvo_status plan_launch(cvo_handle h, PairRes& P, bool planned, unsigned* dev)
