@@ -157,3 +157,21 @@ def test_register_cube_matches_oracle():
     np.testing.assert_allclose(tr[:, 1], tro[:, 1], rtol=F_RTOL)
     xi = oracle.se3_log(np.linalg.inv(T_gpu) @ T_orc)
     assert np.linalg.norm(xi[:3]) <= 1e-4 and np.linalg.norm(xi[3:]) <= 1e-4
+
+
+def test_batch_with_feature_cutoff_matches_single_pairs():
+    """Batched registration with the feature cutoff agrees with registering
+    each pair alone with it (the batch shares the kernels, split differently)."""
+    pairs = scenes.batch_pairs(n_pairs=3, seed=515, n_range=(1500, 4000))
+    args = []
+    for q in pairs:
+        FXq = np.hstack([np.round(q.FX[:, :3] * 8.0) / 8.0, q.FX[:, 3:]]).astype(np.float32)
+        FZq = np.hstack([np.round(q.FZ[:, :3] * 8.0) / 8.0, q.FZ[:, 3:]]).astype(np.float32)
+        args.append((dev(q.X), dev(q.Z), np.eye(4), dev(FXq), dev(FZq)))
+    with cvo.CVO(blocks=pairs[0].blocks, ell=0.2, cutoff_mult=3.0, max_iters=30, feat_cutoff_mult=FCM) as h:
+        T_batch, infos, _ = h.register_batch(args)
+        singles = [h.register(*a) for a in args]
+    for k, (Ts, info_s) in enumerate(singles):
+        xi = oracle.se3_log(np.linalg.inv(T_batch[k]) @ Ts)
+        assert np.linalg.norm(xi[:3]) <= 1e-4 and np.linalg.norm(xi[3:]) <= 1e-4, k
+        assert infos[k]["F"] == pytest.approx(info_s["F"], rel=1e-4)

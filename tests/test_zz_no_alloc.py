@@ -100,3 +100,21 @@ def test_noalloc_rejects_requests_beyond_its_limits():
     with pytest.raises(cvo.CvoError) as e:
         noalloc_eval(cvo.make_params(ell=0.1, cutoff_mult=3.0), Z, Z, None, None, np.eye(4))
     assert "dense" in str(e.value)
+
+
+def test_noalloc_with_feature_cutoff_matches_oracle():
+    """The feature-space cutoff reaches the allocation-free entry too: its F and
+    pair count follow the oracle with the same cutoff (colours quantised to
+    1/8, so no squared colour distance lies near the cutoff radius)."""
+    p = scenes.cube_pair(n=1300, seed=61)
+    F = (np.round(p.FX * 8.0) / 8.0).astype(np.float32)
+    kw = dict(blocks=p.blocks, ell=0.1, cutoff_mult=0.0)
+    T = np.eye(4)
+    X, Z = torch.tensor(p.X, device="cuda"), torch.tensor(p.Z, device="cuda")
+    Fd = torch.tensor(F, device="cuda")
+    got = noalloc_eval(cvo.make_params(feat_cutoff_mult=1.6, **kw), X, Z, Fd, Fd, T)
+    ref = oracle.evaluate(p.X, p.Z, T, FX=F, FZ=F, feat_cutoff_mult=1.6, **kw)
+    full = oracle.evaluate(p.X, p.Z, T, FX=F, FZ=F, **kw)
+    assert ref["npairs"] < full["npairs"]
+    assert got["F"] == pytest.approx(ref["F"], rel=1e-5)
+    assert got["pairs"] == ref["npairs"]
