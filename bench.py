@@ -10,7 +10,12 @@ value  = in-cutoff kernel-pair evaluations per second, summed over ranks
 e2e    = the same metric through the C ABI with pinned host buffers (host to
          device copies inside the timed region)
 roofline = the sweep kernel's algorithmic FP32 FLOPs per launch over its
-         event-timed duration, against the FP32 peak from the unit counts
+         event-timed duration, against the FP32 peak from the unit counts;
+         with the DRAM traffic and the warp-instruction issue rate of the
+         committed ncu capture when it was taken on the current source
+sections = batch (64 cube pairs batched vs one by one), backward (room pair),
+         large (200,000-point pair), tuning (the autotuner's choice, timed
+         registrations; untimed here)
 cpu_baseline = the FP64 oracle's own registration loop on the same pair,
          first 20 iterations, on the host cores
 
