@@ -534,3 +534,43 @@ def test_feature_cutoff_by_brute_force():
     fd = (oracle.evaluate(Xp, Z, T, FX=FX, FZ=FZ, blocks=blocks, ell=ell, cutoff_mult=cm, feat_cutoff_mult=fm)["F"]
           - oracle.evaluate(Xm, Z, T, FX=FX, FZ=FZ, blocks=blocks, ell=ell, cutoff_mult=cm, feat_cutoff_mult=fm)["F"]) / (2 * eps)
     assert g["dX"][3, 1] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+def test_feature_cutoff_input_gradients_by_central_differences():
+    """The oracle's input gradients with the feature cutoff (the pair set held
+    fixed) against central differences of its F, for a point of Z and for a
+    colour and a label entry of X and of Z; each perturbed point is chosen
+    with no colour distance near the cutoff radius, so the pair set does not
+    change between the two evaluations."""
+    r = rng(51)
+    X = r.uniform(-0.5, 0.5, size=(30, 3))
+    Z = r.uniform(-0.5, 0.5, size=(28, 3))
+    FX = np.concatenate([r.uniform(0, 1, size=(30, 3)), r.dirichlet(np.ones(4), size=30)], axis=1)
+    FZ = np.concatenate([r.uniform(0, 1, size=(28, 3)), r.dirichlet(np.ones(4), size=28)], axis=1)
+    blocks = [("se", 3, 0.25, 1.2), ("dot", 4, 1.0, 1.0)]
+    T = rand_T(r, 0.15, 0.1)
+    kw = dict(blocks=blocks, ell=0.35, cutoff_mult=2.5, feat_cutoff_mult=1.4)
+    rad = 1.4 * 0.25
+    c = np.sqrt(((FX[:, None, :3] - FZ[None, :, :3]) ** 2).sum(-1))
+    far = np.abs(c - rad) > 1e-3          # colour distances well away from the radius
+    i = int(np.argmax(far.all(1)))        # a point of X with none near it
+    j = int(np.argmax(far.all(0)))        # a point of Z with none near it
+    assert far[i].all() and far[:, j].all()
+    g = oracle.backward(X, Z, T, FX=FX, FZ=FZ, **kw)
+    eps = 1e-6
+
+    def F(Xa, Za, FXa, FZa):
+        return oracle.evaluate(Xa, Za, T, FX=FXa, FZ=FZa, **kw)["F"]
+
+    def fd(which, idx):
+        arrs = [X.copy(), Z.copy(), FX.copy(), FZ.copy()]
+        arrs[which][idx] += eps
+        fp = F(*arrs)
+        arrs[which][idx] -= 2 * eps
+        fm = F(*arrs)
+        return (fp - fm) / (2 * eps)
+
+    assert g["dZ"][j, 2] == pytest.approx(fd(1, (j, 2)), rel=1e-6, abs=1e-9)
+    assert g["dFX"][i, 1] == pytest.approx(fd(2, (i, 1)), rel=1e-6, abs=1e-9)   # colour
+    assert g["dFX"][i, 4] == pytest.approx(fd(2, (i, 4)), rel=1e-6, abs=1e-9)   # label
+    assert g["dFZ"][j, 0] == pytest.approx(fd(3, (j, 0)), rel=1e-6, abs=1e-9)   # colour
