@@ -1024,7 +1024,6 @@ cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     a.nch_next = nch_next;
     a.chunk_len = h->chunk_len;
     const bool graph = !persistent && !h->timing && h->loop_mode == 1;
-    long long kernel_launches = 0;
     if (persistent) {
         // one cooperative launch for the whole loop (events around it when timing)
         int grid = 0;
@@ -1077,7 +1076,6 @@ cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     h->last_iters = st->iter;
     // four kernels (six with the layout) per pass of the graph's loop body, two iterations a pass
     if (graph) g_launch_count.fetch_add((replan ? 6LL : 4LL) * ((st->iter + 1) / 2), std::memory_order_relaxed);
-    (void)kernel_launches;
     if (h->timing && persistent) {
         // the persistent kernel as a whole (sweeps and steps), per iteration
         float ms = 0.0f;
