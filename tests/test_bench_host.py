@@ -1,0 +1,77 @@
+"""Host logic of bench.py that needs no GPU: the algorithmic FLOP count per
+pair, the per-launch figures taken from the committed ncu summary (only
+while its source hash matches the kernel source), and the parsing of the
+clock samples (median SM clock, the throttle reasons seen)."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+CSRC = os.path.join(ROOT, "paper_2012_03683_gb300", "csrc")
+SWEEP_SRC = [os.path.join(CSRC, "cvo_sweep.cu"), os.path.join(CSRC, "cvo_sweep_dev.cuh")]
+
+
+def test_flops_per_pair():
+    # offset 3, distance 5, scale 1, moments 19; SE block 3d + 1; dot block 2d
+    assert bench.flops_per_pair([]) == 28
+    assert bench.flops_per_pair([("se", 3, 0.2, 1.0)]) == 28 + 10
+    assert bench.flops_per_pair([("se", 3, 0.2, 1.0), ("dot", 19, 1.0, 1.0)]) == 76
+
+
+def test_profile_values_follow_the_source_hash(tmp_path):
+    import hashlib
+    import re
+    text = open(os.path.join(ROOT, "profiles", "sweep_street-20k.md")).read()
+    recorded = re.search(r"source_sha256:\s*([0-9a-f]{64})", text).group(1)
+    current = hashlib.sha256(b"".join(open(f, "rb").read() for f in SWEEP_SRC)).hexdigest()
+    traffic = bench.profile_value(SWEEP_SRC, "traffic_bytes_per_launch")
+    winst = bench.profile_value(SWEEP_SRC, "warp_instructions_per_launch")
+    if current == recorded:   # the summary was taken on this source: its figures are reported
+        assert traffic is not None and 1e6 < traffic < 1e8
+        assert winst is not None and 1e6 < winst < 1e9
+    else:                     # the kernel changed since: none are
+        assert traffic is None and winst is None
+    # any other source (a changed kernel) gets no figure
+    other = tmp_path / "changed.cu"
+    other.write_text(open(SWEEP_SRC[0]).read() + "\n// changed\n")
+    assert bench.profile_value([str(other), SWEEP_SRC[1]], "traffic_bytes_per_launch") is None
+    assert bench.profile_value(SWEEP_SRC, "no_such_key") is None
+
+
+class _FakeProc:
+    def __init__(self, text):
+        self.text = text
+
+    def terminate(self):
+        pass
+
+    def communicate(self, timeout=None):
+        return self.text, ""
+
+    def kill(self):
+        pass
+
+
+def test_clock_samples_parsed():
+    rows = [
+        "2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "2055, 2070, 1100.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "2070, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+    ]
+    s = bench.ClockSampler(0)
+    s.proc = _FakeProc("\n".join(rows) + "\n")
+    out = s.stop()
+    assert out["samples"] == 3
+    assert out["sm_mhz"] == pytest.approx(2070.0)
+    assert out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_sampler_without_nvidia_smi():
+    s = bench.ClockSampler(0)
+    assert s.stop() is None
