@@ -81,3 +81,25 @@ int main(void) {
            cvo.Params.feat_cutoff_mult.offset, cvo.Info.pairs.offset, cvo.Cloud.feat_dtype.offset, cvo.Eval.candidates.offset,
            ctypes.sizeof(cvo.Tuning), cvo.Tuning.chunk_len.offset, cvo.Tuning.measured_ms.offset]
     assert vals == got
+
+
+def test_every_field_offset_matches_header(tmp_path):
+    """Every field of every structure the binding mirrors sits at the
+    header's offset (a C probe prints offsetof for each ctypes field name)."""
+    structs = {"cvo_feat_block": cvo.FeatBlock, "cvo_cloud": cvo.Cloud, "cvo_params": cvo.Params,
+               "cvo_info": cvo.Info, "cvo_tuning": cvo.Tuning, "cvo_eval": cvo.Eval}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "cvo.h"', 'int main(void) {']
+    expected = []
+    for cname, ct in structs.items():
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+        expected.append(ctypes.sizeof(ct))
+        for fname, _ in ct._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {fname}));')
+            expected.append(getattr(ct, fname).offset)
+    lines += ['  return 0;', '}']
+    src = tmp_path / "fields.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "fields"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == expected
