@@ -86,18 +86,28 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
               "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
 
-    def __init__(self, index):
+    def __init__(self, index, command=None):
         self.proc = None
+        self.first = ""
         self.index = index
+        self.command = command or ["nvidia-smi", "-i", str(index), "--query-gpu=" + ",".join(self.FIELDS),
+                                   "--format=csv,noheader,nounits", "-lms", "100"]
 
     def start(self):
+        """Starts sampling and waits (at most 3 s) for the first sample, so
+        that the samples cover the timed region from its start."""
+        import select
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
-                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=subprocess.PIPE,
-                stderr=subprocess.DEVNULL, text=True)
+            self.proc = subprocess.Popen(self.command, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+            return
+        try:
+            ready, _, _ = select.select([self.proc.stdout], [], [], 3.0)
+            if ready:
+                self.first = self.proc.stdout.readline()
+        except Exception:
+            self.first = ""
 
     def stop(self):
         if self.proc is None:
@@ -108,6 +118,7 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
             out, _ = self.proc.communicate()
+        out = (self.first or "") + (out or "")
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():
@@ -339,7 +350,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cvo", choices=["cvo", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

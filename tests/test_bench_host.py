@@ -75,3 +75,32 @@ def test_clock_samples_parsed():
 def test_clock_sampler_without_nvidia_smi():
     s = bench.ClockSampler(0)
     assert s.stop() is None
+
+
+def test_clock_sampler_end_to_end_with_a_stand_in_command(tmp_path):
+    """start() waits for the first sample and stop() keeps it: a stand-in for
+    nvidia-smi prints one sample line every 20 ms until it is terminated."""
+    import subprocess
+    import time
+    script = tmp_path / "fake_smi.py"
+    script.write_text(
+        "import sys, time\n"
+        "i = 0\n"
+        "while True:\n"
+        "    print(f'{2000 + i % 3}, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active', flush=True)\n"
+        "    i += 1\n"
+        "    time.sleep(0.02)\n")
+    s = bench.ClockSampler(0, command=[sys.executable, str(script)])
+    s.start()
+    assert s.first.startswith("20")
+    time.sleep(0.15)
+    out = s.stop()
+    assert out["samples"] >= 3 and out["sm_max_mhz"] == 2070.0 and out["reasons"] == []
+    assert 2000.0 <= out["sm_mhz"] <= 2002.0
+    assert s.proc.poll() is not None   # the sampler process is gone
+
+
+def test_clock_sampler_with_a_missing_command():
+    s = bench.ClockSampler(0, command=["/nonexistent/nvidia-smi-stand-in"])
+    s.start()
+    assert s.proc is None and s.stop() is None
