@@ -11,9 +11,12 @@ by quadrature of the Gaussian convolution identity and by the explicit tensor
 product of Eq. (tensor_product); symmetry, rigid invariance, Cauchy-Schwarz,
 the Remark of Sec. III-C, the gradient and second derivative by central finite
 differences on se(3), the SE(3) exponential by the matrix exponential.
-Parity unpinned: the step rule, the annealing trigger and the stopping rule
-(readings of Sec. I and Sec. IV); only the registration's end point is pinned,
-by recovery of a known transform.
+The step rule, its clamps and the left-composed update (a reading: the paper
+names a step size without a rule) by closed-form Newton iterates on problems
+with a one-variable objective along the gradient (tests/test_oracle_step_rule.py).
+The annealing trigger and the stopping rule (readings of Sec. IV, no closed
+form) are checked as the control sequence the reading states along traces;
+the registration's end point by recovery of a known transform.
 """
 from __future__ import annotations
 

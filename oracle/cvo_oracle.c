@@ -39,10 +39,13 @@
  *             = sum w [ (e.d)^2 / l^4 - (|d|^2 + e.(omega x d)) / l^2 ]
  *
  * The gradient and the second derivative are pinned by central finite
- * differences of F (tests).  The step rule, the annealing trigger and the
- * convergence test are readings of the paper (Sec. IV for annealing) and are
- * PARITY UNPINNED beyond their fixed point: the registration's end point is
- * pinned by recovery of a known transform, its trajectory is not.
+ * differences of F (tests).  The step rule is a reading (the paper names a
+ * step size without a rule); it, its clamps, its fixed-step fallback and the
+ * left-composed update are pinned by closed-form Newton iterates on problems
+ * whose objective along the gradient line has one variable.  The annealing
+ * trigger and the convergence test are readings of Sec. IV with no closed
+ * form: tests check them as the control sequence the reading states, along
+ * registration traces, and the end point by recovery of a known transform.
  */
 #include <math.h>
 #include <stdint.h>
