@@ -268,19 +268,27 @@ long long orc_count_band(const orc_cloud* X, const orc_cloud* Z, const double T[
 /* and Sastry), xi = (omega, v), hat(xi) = [[omega]x, v; 0, 0].             */
 /* ------------------------------------------------------------------------ */
 
-/* A = sin(th)/th, B = (1-cos th)/th^2, C = (th - sin th)/th^3 with series for small th. */
+/* A = sin(th)/th, B = (1-cos th)/th^2, C = (th - sin th)/th^3.
+ * A and B take their Taylor series below 1e-3; above it B is written as
+ * 2 sin^2(th/2)/th^2, the same quantity without the cancellation of 1 - cos.
+ * The difference th - sin th cancels for small th (about 7 digits at 1e-3),
+ * so C takes its Taylor series below 0.1, to the th^8 term (the first term
+ * left out is below 1e-19 there). */
 static void se3_coeffs(double th, double* A, double* B, double* C)
 {
     const double t2 = th * th;
     if (th < 1e-3) {
         *A = 1.0 - t2 / 6.0 + t2 * t2 / 120.0;
         *B = 0.5 - t2 / 24.0 + t2 * t2 / 720.0;
-        *C = 1.0 / 6.0 - t2 / 120.0 + t2 * t2 / 5040.0;
     } else {
+        const double h = sin(0.5 * th);
         *A = sin(th) / th;
-        *B = (1.0 - cos(th)) / t2;
-        *C = (th - sin(th)) / (t2 * th);
+        *B = 2.0 * h * h / t2;
     }
+    if (th < 0.1)
+        *C = 1.0 / 6.0 - t2 / 120.0 + t2 * t2 / 5040.0 - t2 * t2 * t2 / 362880.0 + t2 * t2 * t2 * t2 / 39916800.0;
+    else
+        *C = (th - sin(th)) / (t2 * th);
 }
 
 void orc_se3_exp(const double xi[6], double T[16])

@@ -393,6 +393,50 @@ def test_se3_log_inverts_exp():
     np.testing.assert_allclose(oracle.se3_exp(oracle.se3_log(T)), T, atol=1e-13)
 
 
+def test_se3_exp_in_extended_precision():
+    """The closed form and its small-angle series against the matrix
+    exponential of the 4x4 twist in 40-digit arithmetic, at angles on both
+    sides of the series' switch and with a long translation, so that an error
+    in a series term (a few parts in 1e14 of the result) exceeds rounding."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    r = rng(16)
+    for th in (1e-6, 3e-4, 9.9e-4, 1.01e-3, 0.05, 0.099, 0.101, 1.3, 3.0):
+        for _ in range(3):
+            axis = r.normal(size=3)
+            axis /= np.linalg.norm(axis)
+            v = r.normal(size=3)
+            v *= 1e4 / np.linalg.norm(v)
+            xi = np.concatenate([axis * th, v])
+            ref = mpmath.expm(mpmath.matrix(hat(xi).tolist()))
+            ref = np.array([[float(ref[i, j]) for j in range(4)] for i in range(4)])
+            T = oracle.se3_exp(xi)
+            np.testing.assert_allclose(T[:3, :3], ref[:3, :3], rtol=0, atol=8e-16)
+            np.testing.assert_allclose(T[:3, 3], ref[:3, 3], rtol=0, atol=2e-15 * 1e4)
+
+
+def test_se3_log_in_extended_precision():
+    """The logarithm of a pose against the matrix logarithm of the same
+    (rounded) pose in 40-digit arithmetic, on both sides of its series switch."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    r = rng(17)
+    for th in (1e-6, 9.9e-4, 1.01e-3, 0.05, 1.3, 2.5):
+        for _ in range(3):
+            axis = r.normal(size=3)
+            axis /= np.linalg.norm(axis)
+            v = r.normal(size=3)
+            v *= 1e2 / np.linalg.norm(v)
+            E = mpmath.expm(mpmath.matrix(hat(np.concatenate([axis * th, v])).tolist()))
+            T = np.array([[float(E[i, j]) for j in range(4)] for i in range(4)])
+            L = mpmath.logm(mpmath.matrix(T.tolist()))
+            ref = np.array([float(L[2, 1]), float(L[0, 2]), float(L[1, 0]),
+                            float(L[0, 3]), float(L[1, 3]), float(L[2, 3])])
+            got = oracle.se3_log(T)
+            np.testing.assert_allclose(got[:3], ref[:3], rtol=0, atol=4e-15)
+            np.testing.assert_allclose(got[3:], ref[3:], rtol=0, atol=4e-14 * 1e2)
+
+
 def test_se3_small_angle_branch_continuous():
     axis = np.array([0.48, -0.6, 0.64])
     v = np.array([0.3, 0.1, -0.2])
@@ -534,6 +578,31 @@ def test_feature_cutoff_by_brute_force():
     fd = (oracle.evaluate(Xp, Z, T, FX=FX, FZ=FZ, blocks=blocks, ell=ell, cutoff_mult=cm, feat_cutoff_mult=fm)["F"]
           - oracle.evaluate(Xm, Z, T, FX=FX, FZ=FZ, blocks=blocks, ell=ell, cutoff_mult=cm, feat_cutoff_mult=fm)["F"]) / (2 * eps)
     assert g["dX"][3, 1] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+def test_feature_cutoff_leaves_inner_product_blocks_uncut():
+    """The feature cutoff applies to squared-exponential blocks alone: with an
+    inner-product block whose vectors lie far apart (off the simplex, so that
+    most distances exceed any radius the cutoff would give them), F and the
+    pair count equal the numpy double sum cut on the colour block only."""
+    r = rng(52)
+    X = r.uniform(-0.5, 0.5, size=(36, 3))
+    Z = r.uniform(-0.5, 0.5, size=(33, 3))
+    FX = np.concatenate([r.uniform(0, 1, size=(36, 2)), r.uniform(0, 4, size=(36, 3))], axis=1)
+    FZ = np.concatenate([r.uniform(0, 1, size=(33, 2)), r.uniform(0, 4, size=(33, 3))], axis=1)
+    blocks = [("se", 2, 0.3, 1.0), ("dot", 3, 1.0, 1.0)]
+    T = rand_T(r, 0.1, 0.05)
+    ell, cm, fm = 0.4, 3.0, 1.2
+    Y = transform(T, Z)
+    d2 = ((X[:, None, :] - Y[None, :, :]) ** 2).sum(-1)
+    c2 = ((FX[:, None, :2] - FZ[None, :, :2]) ** 2).sum(-1)
+    p2 = ((FX[:, None, 2:] - FZ[None, :, 2:]) ** 2).sum(-1)
+    keep = (d2 <= (cm * ell) ** 2) & (c2 <= (fm * 0.3) ** 2)
+    assert (p2[keep] > (fm * 1.0) ** 2).mean() > 0.5      # a cut on the inner-product block would bite
+    w = np.exp(-d2 / (2 * ell ** 2)) * np.exp(-c2 / (2 * 0.3 ** 2)) * (FX[:, None, 2:] * FZ[None, :, 2:]).sum(-1)
+    got = oracle.evaluate(X, Z, T, FX=FX, FZ=FZ, blocks=blocks, ell=ell, cutoff_mult=cm, feat_cutoff_mult=fm)
+    assert got["F"] == pytest.approx((w * keep).sum(), rel=1e-12)
+    assert got["npairs"] == int(keep.sum())
 
 
 def test_feature_cutoff_input_gradients_by_central_differences():
