@@ -90,6 +90,21 @@ def test_translation_newton_iterates():
     assert abs(T[0, 3] - delta) < 1e-12
 
 
+def test_single_pair_converges_onto_its_maximiser_set():
+    """For one pair of points F = exp(-|x - T z|^2 / 2 l^2) is maximal exactly
+    on the poses with T z = x (a set, since rotations about the line through
+    x are free); from an off-axis start the ascent, rotation included, ends
+    on it and stops by its step test."""
+    X = np.array([[0.4, -0.2, 0.9]])
+    Z = np.array([[0.5, 0.05, 0.8]])
+    T, info, tr = oracle.register(X, Z, np.eye(4), ell=ELL, max_iters=300, step_tol_rot=1e-12,
+                                  step_tol_trans=1e-12)
+    assert info["status"] == 0 and info["iters"] < 300
+    assert tr[0, C_SROT] > 0.0                       # the path rotates as well as translates
+    assert np.linalg.norm(T[:3, :3] @ Z[0] + T[:3, 3] - X[0]) < 1e-10
+    assert info["F"] == pytest.approx(1.0, abs=1e-15)
+
+
 def test_translation_clamp_half_lengthscale():
     delta = 0.45 * ELL                       # Newton step 0.564 l, clamped to 0.5 l
     assert newton_translation(delta) > 0.5 * ELL
