@@ -1,0 +1,88 @@
+"""The batch-64 workload at full size (64 cube pairs of 5,000-60,000 points
+per cloud, RGB + 19 labels stored in bfloat16, l = 0.1, cutoff 3 l, <= 50
+iterations) in the launch configuration the benchmark times: tuned on the
+largest pair, all pairs registered by one batched graph launch.
+
+Checks: sampled pairs (the smallest, the median and the largest) registered
+alone give the batch's result (the single-pair path is held to the oracle by
+the one-step parity tests); at the batch's final poses of those pairs the
+double sum, its gradient and the pair count agree with the FP64 oracle,
+evaluated in full (up to 3.6e9 pair tests); every pair's indicator is
+F / sqrt(N M).  Tolerances as in the other parity tests."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+torch = pytest.importorskip("torch")
+import paper_2012_03683_gb300 as cvo  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+F_RTOL = 1e-5
+G_TOL = 1e-4
+G_FLOOR = 1e-7
+POSE_TOL = 1e-4
+
+
+def pose_err(Ta, Tb):
+    xi = oracle.se3_log(np.linalg.inv(Ta) @ Tb)
+    return np.linalg.norm(xi[:3]), np.linalg.norm(xi[3:])
+
+
+@pytest.fixture(scope="module")
+def batch_run():
+    pairs = scenes.batch_pairs()
+    pr = pairs[0].params
+    kw = dict(blocks=pairs[0].blocks, ell=pr["ell"], cutoff_mult=pr["cutoff_mult"], max_iters=pr["max_iters"])
+    args = []
+    for p in pairs:
+        args.append((torch.tensor(p.X, device="cuda"), torch.tensor(p.Z, device="cuda"), np.eye(4),
+                     torch.tensor(p.FX, device="cuda").to(torch.bfloat16),
+                     torch.tensor(p.FZ, device="cuda").to(torch.bfloat16)))
+    order = sorted(range(len(pairs)), key=lambda k: pairs[k].n + pairs[k].m)
+    picks = [order[0], order[len(order) // 2], order[-1]]
+    with cvo.CVO(**kw) as h:
+        h.autotune(*args[order[-1]])
+        T_batch, infos, rc = h.register_batch(args)
+        singles = {k: h.register(*args[k]) for k in picks}
+        evals = {k: h.evaluate(args[k][0], args[k][1], T_batch[k], args[k][3], args[k][4]) for k in picks}
+    return pairs, kw, T_batch, infos, rc, singles, evals
+
+
+def test_batch_full_size_runs(batch_run):
+    pairs, kw, T_batch, infos, rc, _, _ = batch_run
+    assert rc in (cvo.Status.OK, cvo.Status.NOT_CONVERGED)
+    assert len(infos) == len(pairs) == 64
+    for k, (p, info) in enumerate(zip(pairs, infos)):
+        assert 1 <= info["iters"] <= kw["max_iters"], k
+        assert info["i_theta"] == pytest.approx(info["F"] / math.sqrt(p.n * p.m), rel=1e-12), k
+        R = T_batch[k][:3, :3]
+        assert np.abs(R.T @ R - np.eye(3)).max() < 1e-9 and np.linalg.det(R) > 0, k
+
+
+def test_batch_full_size_equals_single_pairs(batch_run):
+    _, _, T_batch, infos, _, singles, _ = batch_run
+    for k, (Ts, info_s) in singles.items():
+        er, et = pose_err(T_batch[k], Ts)
+        assert er <= POSE_TOL and et <= POSE_TOL, (k, er, et)
+        assert abs(infos[k]["iters"] - info_s["iters"]) <= 1, k
+        assert infos[k]["F"] == pytest.approx(info_s["F"], rel=1e-4), k
+        assert infos[k]["pairs"] == pytest.approx(info_s["pairs"], rel=1e-3), k
+
+
+def test_batch_full_size_final_poses_match_oracle(batch_run):
+    pairs, kw, T_batch, _, _, _, evals = batch_run
+    for k, got in evals.items():
+        p = pairs[k]
+        ref = oracle.evaluate(p.X, p.Z, T_batch[k], FX=p.FX, FZ=p.FZ, blocks=kw["blocks"], ell=kw["ell"],
+                              cutoff_mult=kw["cutoff_mult"])
+        assert got["F"] == pytest.approx(ref["F"], rel=F_RTOL), k
+        gtol = G_TOL * np.linalg.norm(ref["g"]) + G_FLOOR * ref["gscale"]
+        assert np.abs(got["grad"] - ref["g"]).max() <= gtol, (k, got["grad"], ref["g"])
+        rc2 = (kw["cutoff_mult"] * kw["ell"]) ** 2
+        band = oracle.count_band(p.X, p.Z, T_batch[k], rc2 * (1 - 1e-5), rc2 * (1 + 1e-5))
+        assert abs(got["pairs"] - ref["npairs"]) <= band, k
