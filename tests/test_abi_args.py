@@ -113,3 +113,58 @@ def test_noalloc_rejects_before_device_work(lib):
     bad = cvo.make_params(cutoff_mult=0.0, blocks=[("se", 3, 0.2, 1.0)])
     bad.blocks[0].scale = 0.0
     expect_invalid(call(bad), "invalid feature block")
+
+
+C_CLIENT = r'''
+#include <stdio.h>
+#include "cvo.h"
+
+int main(void)
+{
+    cvo_params p = {0};
+    p.ell = 0.3; p.ell_min = 0.3; p.sigma = 1.0; p.cutoff_mult = 3.0; p.max_iters = 20;
+    p.decay = 0.98; p.indicator_tol = 1e-3; p.step_tol_rot = 1e-5; p.step_tol_trans = 1e-5;
+    p.max_step_rot = 0.1;
+    cvo_handle h;
+    cvo_status s = cvo_create(&p, NULL, &h);
+    if (s != CVO_OK) {
+        printf("create failed: %d: %s\n", (int)s, cvo_last_error());
+        return 3;
+    }
+    const float X[6] = {0.f, 0.f, 0.f, 0.5f, 0.f, 0.f}, Z[6] = {0.02f, 0.f, 0.f, 0.52f, 0.f, 0.f};
+    cvo_cloud cx = {X, 2, NULL, CVO_F32, 0}, cz = {Z, 2, NULL, CVO_F32, 0};
+    const double I[16] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1};
+    double T[16];
+    cvo_info info;
+    s = cvo_register_pair(h, &cx, &cz, I, T, &info);
+    cvo_destroy(h);
+    printf("register: %d, %d iterations, t_x = %.6f\n", (int)s, info.iters, T[3]);
+    return s < 0 ? 4 : 0;
+}
+'''
+
+
+def test_c_client_builds_and_runs(lib, tmp_path):
+    """A plain C program includes the header, links the library with gcc and
+    runs: without a GPU it gets CVO_ERR_CUDA and a message from cvo_create;
+    with one, the two-point registration moves Z onto X (t_x = -0.02)."""
+    import os
+    import subprocess
+    from paper_2012_03683_gb300 import build as cvo_build
+    so = cvo_build.build()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(so)
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(root, "include"), str(src),
+                    "-L", libdir, "-lcvo", f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        assert r.returncode == 0, r.stdout + r.stderr
+        t_x = float(r.stdout.strip().rsplit("=", 1)[1])
+        assert t_x == pytest.approx(-0.02, abs=1e-4)
+    else:
+        assert r.returncode == 3, r.stdout + r.stderr
+        assert "create failed: -2" in r.stdout and "cudaGetDevice" in r.stdout
