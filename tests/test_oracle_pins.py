@@ -348,6 +348,73 @@ def test_gradient_central_differences(with_feat):
     assert np.abs(g - fd).max() <= 1e-6 * np.linalg.norm(g)
 
 
+@pytest.mark.parametrize("cut", [False, True])
+def test_derivatives_in_extended_precision(cut):
+    """F, its se(3) gradient and the second derivative along the gradient
+    against the double sum written out in 30-digit arithmetic, differentiated
+    by mpmath (the pose perturbed on the left through the 4x4 matrix
+    exponential), on a tiny cloud pair with both kinds of feature block.
+    With a cutoff, no pair lies within 5 % of its radius, so the pair set is
+    the same throughout the differentiation."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 30
+    r = rng(60)
+    n, m = 5, 4
+    X = r.uniform(-0.4, 0.4, (n, 3))
+    Z = r.uniform(-0.4, 0.4, (m, 3))
+    FX = np.hstack([r.uniform(0, 1, (n, 3)), r.dirichlet(np.ones(4), n)])
+    FZ = np.hstack([r.uniform(0, 1, (m, 3)), r.dirichlet(np.ones(4), m)])
+    blocks = [("se", 3, 0.3, 1.2), ("dot", 4, 1.0, 1.0)]
+    ell, sigma = 0.35, 1.1
+    T = rand_T(r, 0.2, 0.2)
+    mp = mpmath.mpf
+    T0 = mpmath.matrix(T.tolist())
+    Xm = [[mp(v) for v in row] for row in X]
+    Zm = [mpmath.matrix([mp(v) for v in row] + [1]) for row in Z]
+    c = [[mp(1.2) ** 2 * mpmath.exp(-sum((mp(a) - mp(b)) ** 2 for a, b in zip(FX[i, :3], FZ[j, :3]))
+                                      / (2 * mp(0.3) ** 2))
+          * sum(mp(a) * mp(b) for a, b in zip(FX[i, 3:], FZ[j, 3:])) for j in range(m)] for i in range(n)]
+    Y = transform(T, Z)
+    d2 = ((X[:, None, :] - Y[None, :, :]) ** 2).sum(-1)
+    cm = 0.0
+    inside = np.ones((n, m), bool)
+    if cut:   # the first cutoff multiple with every pair at least 5 % away from the radius
+        cm = next(k for k in np.arange(1.0, 3.01, 0.1)
+                  if np.all(np.abs(np.sqrt(d2) / (k * ell) - 1.0) > 0.05))
+        inside = d2 <= (cm * ell) ** 2
+        assert 0 < inside.sum() < n * m
+
+    def hat_mp(xi):
+        w, v = xi[:3], xi[3:]
+        return mpmath.matrix([[0, -w[2], w[1], v[0]], [w[2], 0, -w[0], v[1]], [-w[1], w[0], 0, v[2]],
+                              [0, 0, 0, 0]])
+
+    def F(xi):
+        Tx = mpmath.expm(hat_mp(xi)) * T0
+        s = mp(0)
+        for j in range(m):
+            y = Tx * Zm[j]
+            for i in range(n):
+                if inside[i, j]:
+                    e2 = sum((Xm[i][q] - y[q]) ** 2 for q in range(3))
+                    s += mp(sigma) ** 2 * mpmath.exp(-e2 / (2 * mp(ell) ** 2)) * c[i][j]
+        return s
+
+    def along(k):
+        return lambda h: F([h if q == k else mp(0) for q in range(6)])
+
+    g_ref = np.array([float(mpmath.diff(along(k), 0)) for k in range(6)])
+    kw = dict(FX=FX, FZ=FZ, blocks=blocks, ell=ell, sigma=sigma, cutoff_mult=cm)
+    res = oracle.evaluate(X, Z, T, **kw)
+    assert res["F"] == pytest.approx(float(F([mp(0)] * 6)), rel=1e-13)
+    assert res["npairs"] == int(inside.sum())
+    assert np.abs(res["g"] - g_ref).max() <= 1e-12 * np.abs(g_ref).max()
+    d = res["g"]
+    fpp_ref = float(mpmath.diff(lambda h: F([h * mp(a) for a in d]), 0, 2))
+    fpp = oracle.evaluate(X, Z, T, direction=d, **kw)["Fpp"]
+    assert fpp == pytest.approx(fpp_ref, rel=1e-11)
+
+
 def test_second_derivative_along_direction():
     r, X, Z, FX, FZ = _cloud_pair(13, 20, 18)
     T = rand_T(r, 0.3, 0.3)
