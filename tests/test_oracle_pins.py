@@ -10,6 +10,9 @@ against an independent route:
   * scipy.linalg.expm for the SE(3) exponential;
   * central finite differences of F on se(3) for the gradient and the second
     derivative;
+  * the double sum, the SE(3) exponential and logarithm written out in 30- or
+    40-digit arithmetic (mpmath), differentiated by mpmath for the se(3)
+    gradient, the second derivative and every input gradient;
   * invariants: symmetry of the inner product, invariance under a common rigid
     motion, Cauchy-Schwarz, the Remark of Sec. III-C, the behaviour of Fig. 3,
     and recovery of a known transform.
@@ -581,6 +584,55 @@ def test_backward_central_differences():
         Fm[j, a] -= eps
         assert g["dFZ"][j, a] == pytest.approx((F(FZ_=Fp) - F(FZ_=Fm)) / (2 * eps), rel=1e-6, abs=1e-9)
     assert g["dell"] == pytest.approx((F(ell=0.5 + eps) - F(ell=0.5 - eps)) / (2 * eps), rel=1e-6)
+
+
+def test_backward_in_extended_precision():
+    """Every input gradient (points, both clouds' squared-exponential and
+    inner-product feature entries, the lengthscale) against mpmath's
+    derivative of the double sum written out in 30-digit arithmetic, on a
+    tiny dense pair."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 30
+    mp = mpmath.mpf
+    r, X, Z, FX, FZ = _cloud_pair(61, 5, 4)
+    T = rand_T(r, 0.2, 0.2)
+    ell0, sigma = 0.5, 1.1
+    Rm = [[mp(T[a, b]) for b in range(3)] for a in range(3)]
+    tm = [mp(T[a, 3]) for a in range(3)]
+    (_, d_se, l_se, s_se), (_, d_dot, _, _) = BLOCKS
+    base = dict(X=[[mp(v) for v in row] for row in X], Z=[[mp(v) for v in row] for row in Z],
+                FX=[[mp(v) for v in row] for row in FX], FZ=[[mp(v) for v in row] for row in FZ], ell=mp(ell0))
+
+    def F(a):
+        s = mp(0)
+        for j, z in enumerate(a["Z"]):
+            y = [sum(Rm[q][b] * z[b] for b in range(3)) + tm[q] for q in range(3)]
+            v = a["FZ"][j]
+            for i, x in enumerate(a["X"]):
+                u = a["FX"][i]
+                e2 = sum((x[q] - y[q]) ** 2 for q in range(3))
+                c = mp(s_se) ** 2 * mpmath.exp(-sum((u[q] - v[q]) ** 2 for q in range(d_se)) / (2 * mp(l_se) ** 2))
+                c *= sum(u[q] * v[q] for q in range(d_se, d_se + d_dot))
+                s += mp(sigma) ** 2 * mpmath.exp(-e2 / (2 * a["ell"] ** 2)) * c
+        return s
+
+    def deriv(key, i=None, k=None):
+        def f(h):
+            a = dict(base)
+            if key == "ell":
+                a["ell"] = base["ell"] + h
+            else:
+                rows = [list(row) for row in base[key]]
+                rows[i][k] += h
+                a[key] = rows
+            return F(a)
+        return float(mpmath.diff(f, 0))
+
+    g = oracle.backward(X, Z, T, FX=FX, FZ=FZ, blocks=BLOCKS, ell=ell0, sigma=sigma)
+    for key, arr in (("X", "dX"), ("Z", "dZ"), ("FX", "dFX"), ("FZ", "dFZ")):
+        ref = np.array([[deriv(key, i, k) for k in range(len(base[key][0]))] for i in range(len(base[key]))])
+        assert np.abs(g[arr] - ref).max() <= 1e-12 * np.abs(ref).max(), arr
+    assert g["dell"] == pytest.approx(deriv("ell"), rel=1e-12)
 
 
 def test_backward_translation_invariance():
