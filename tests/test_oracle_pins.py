@@ -191,6 +191,20 @@ def test_cutoff_pair_set_matches_kdtree():
     assert dense["F"] - res["F"] == pytest.approx(far, rel=1e-9, abs=1e-12)
 
 
+def test_band_census_by_brute_force():
+    """The census of pairs near the cutoff radius (the pair-count tolerance of
+    the GPU parity tests) counts the squared distances in [lo, hi] as numpy
+    does."""
+    r = rng(62)
+    X = r.uniform(-1, 1, size=(300, 3))
+    Z = r.uniform(-1, 1, size=(280, 3))
+    T = rand_T(r, 0.3, 0.2)
+    d2 = ((X[:, None, :] - transform(T, Z)[None, :, :]) ** 2).sum(-1)
+    for lo, hi in ((0.25, 0.36), (0.0, 0.01), (1.0, 1.0 + 1e-3)):
+        assert oracle.count_band(X, Z, T, lo, hi) == int(((d2 >= lo) & (d2 <= hi)).sum())
+    assert oracle.count_band(X, Z, T, 0.0, 100.0) == 300 * 280
+
+
 def test_empty_clouds_give_zero():
     X = np.zeros((0, 3))
     Z = np.ones((5, 3))
