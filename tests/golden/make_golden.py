@@ -1,5 +1,6 @@
 """Writes oracle_fixtures.json: stored outputs of the FP64 oracle on small
-seeded inputs, a regression record of the oracle's arithmetic.
+seeded inputs, a regression record of the oracle's arithmetic, and a digest
+of every synthetic workload the benchmark and the tests use.
 
 The paper prints no worked example with numbers, so these values are not
 the paper's: each is written by this script, which calls only the oracle and
@@ -10,6 +11,7 @@ must then be rewritten by this script in the same commit.
 
     python tests/golden/make_golden.py          # rewrite the fixture
 """
+import hashlib
 import json
 import os
 import sys
@@ -60,6 +62,33 @@ CASES = [
 ]
 
 
+# The benchmark's and the tests' synthetic workloads, recorded by a digest of
+# every array they hold, so that a change to a generator (or to the random
+# streams it draws from) cannot silently change a measured workload.
+SCENES = {
+    "cube-2000": lambda: [scenes.cube_pair()],
+    "street-20k": lambda: [scenes.street_pair()],
+    "room-19k": lambda: [scenes.room_pair()],
+    "batch-64": lambda: scenes.batch_pairs(),
+    "box80-200k": lambda: [scenes.large_pair()],
+}
+
+
+def scene_digest(name):
+    h = hashlib.sha256()
+    pairs = SCENES[name]()
+    points = 0
+    for p in pairs:
+        for a in (p.X, p.Z, p.FX, p.FZ):
+            a = np.ascontiguousarray(a, dtype=np.float32)
+            h.update(str(a.shape).encode())
+            h.update(a.tobytes())
+        h.update(np.ascontiguousarray(p.T_true, dtype=np.float64).tobytes())
+        h.update(repr((p.blocks, sorted(p.params.items()))).encode())
+        points += p.n + p.m
+    return {"pairs": len(pairs), "points": points, "sha256": h.hexdigest()}
+
+
 def inputs(case):
     if case["scene"] == "cube":
         p = scenes.cube_pair(n=case["n"], seed=case["seed"])
@@ -96,7 +125,8 @@ def main():
                     "numbers, which it does not print). Pose T = exp(xi^) with xi = (omega, v).",
            "generator": "python tests/golden/make_golden.py",
            "xi": XI,
-           "cases": [dict(c, expected=compute(c)) for c in CASES]}
+           "cases": [dict(c, expected=compute(c)) for c in CASES],
+           "scenes": {name: scene_digest(name) for name in SCENES}}
     with open(FIXTURE, "w") as f:
         json.dump(out, f, indent=1)
         f.write("\n")

@@ -3,7 +3,8 @@ a regression record of its arithmetic on small seeded inputs, written by
 tests/golden/make_golden.py, which calls only the oracle and the input
 generators.  A change to the oracle's results shows here first; the fixture
 is then rewritten by that script in the same commit, whose message names the
-passage that justifies the change."""
+passage that justifies the change.  The same fixture holds a digest of every
+synthetic workload, so that a measured workload cannot change unnoticed."""
 import importlib.util
 import json
 import os
@@ -23,6 +24,13 @@ with open(make_golden.FIXTURE) as _f:
 
 # rounding-level agreement: the oracle's sums are ordered, so only libm may move the last bits
 RTOL = 1e-11
+
+
+@pytest.mark.parametrize("name", sorted(make_golden.SCENES))
+def test_synthetic_workloads_unchanged(name):
+    """The seeded generators still produce the recorded workloads, array for
+    array (point counts, coordinates, features, true motions, parameters)."""
+    assert make_golden.scene_digest(name) == FIXTURE["scenes"][name]
 
 
 def test_fixture_matches_the_generator_cases():
