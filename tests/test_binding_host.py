@@ -94,3 +94,22 @@ def test_pose_and_params():
         cvo.make_params(blocks=[("se", 1, 0.2, 1.0)] * 5)
     with pytest.raises(KeyError):
         cvo.make_params(blocks=[("cosine", 3, 0.2, 1.0)])
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library, and with no way to build it, every call
+    raises: there is no fallback."""
+    import paper_2012_03683_gb300 as pkg
+
+    def no_build():
+        raise RuntimeError("nvcc failed (stand-in)")
+
+    monkeypatch.setattr(pkg, "_lib", None)
+    monkeypatch.setattr(pkg._build, "LIB", str(tmp_path / "libcvo.so"))
+    monkeypatch.setattr(pkg._build, "build", no_build)
+    with pytest.raises(RuntimeError, match="not built"):
+        pkg.load_library(build_if_missing=False)
+    with pytest.raises(RuntimeError, match="stand-in"):
+        pkg.CVO(ell=0.1)
+    with pytest.raises(RuntimeError, match="stand-in"):
+        pkg.cvo_version()
