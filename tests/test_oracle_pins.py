@@ -205,6 +205,29 @@ def test_band_census_by_brute_force():
     assert oracle.count_band(X, Z, T, 0.0, 100.0) == 300 * 280
 
 
+def test_results_do_not_depend_on_the_thread_count():
+    """The oracle keeps per-point partial sums and adds them in point order,
+    so F, the gradient, F'', the input gradients and a registration are
+    bitwise the same on 1 and on several threads."""
+    r, X, Z, FX, FZ = _cloud_pair(63, 200, 180)
+    T = rand_T(r, 0.2, 0.2)
+    kw = dict(FX=FX, FZ=FZ, blocks=BLOCKS, ell=0.4, cutoff_mult=2.5)
+    default = oracle.num_threads()
+    a = oracle.evaluate(X, Z, T, nthreads=1, direction=np.ones(6), **kw)
+    b = oracle.evaluate(X, Z, T, nthreads=4, direction=np.ones(6), **kw)
+    assert a["F"] == b["F"] and np.array_equal(a["g"], b["g"]) and a["Fpp"] == b["Fpp"]
+    ga = oracle.backward(X, Z, T, nthreads=1, **kw)
+    gb = oracle.backward(X, Z, T, nthreads=4, **kw)
+    for k in ("dX", "dZ", "dFX", "dFZ"):
+        assert np.array_equal(ga[k], gb[k]), k
+    assert ga["dell"] == gb["dell"]
+    Ta, _, tra = oracle.register(X, Z, np.eye(4), nthreads=1, max_iters=5, **kw)
+    Tb, _, trb = oracle.register(X, Z, np.eye(4), nthreads=3, max_iters=5, **kw)
+    assert np.array_equal(Ta, Tb) and np.array_equal(tra, trb)
+    oracle.evaluate(X[:1], Z[:1], T, nthreads=default, **kw)   # the thread count is process-wide: put it back
+    assert oracle.num_threads() == default
+
+
 def test_empty_clouds_give_zero():
     X = np.zeros((0, 3))
     Z = np.ones((5, 3))
