@@ -455,11 +455,18 @@ cvo_status prepare_build(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo
             L.rdesign = rc_hi * 1.0002 / std::pow(std::sqrt(2.0), k);
             double hh = h->cell_factor * L.rdesign;
             for (;;) {
-                L.nx = (int)std::floor(((double)zmax[0] - zmin[0]) / hh) + 1;
-                L.ny = (int)std::floor(((double)zmax[1] - zmin[1]) / hh) + 1;
-                L.nz = (int)std::floor(((double)zmax[2] - zmin[2]) / hh) + 1;
-                L.ncells = (long long)L.nx * L.ny * L.nz;
-                if (L.ncells <= kMaxCells) break;
+                // cell counts in double first: a cloud far wider than the
+                // cutoff would overflow an int before the size check
+                const double cx = std::floor(((double)zmax[0] - zmin[0]) / hh) + 1.0;
+                const double cy = std::floor(((double)zmax[1] - zmin[1]) / hh) + 1.0;
+                const double cz = std::floor(((double)zmax[2] - zmin[2]) / hh) + 1.0;
+                if (cx * cy * cz <= (double)kMaxCells) {
+                    L.nx = (int)cx;
+                    L.ny = (int)cy;
+                    L.nz = (int)cz;
+                    L.ncells = (long long)L.nx * L.ny * L.nz;
+                    break;
+                }
                 hh *= 1.26;
             }
             L.h = hh;
