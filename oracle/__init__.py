@@ -14,9 +14,10 @@ differences on se(3), the SE(3) exponential by the matrix exponential.
 The step rule, its clamps and the left-composed update (a reading: the paper
 names a step size without a rule) by closed-form Newton iterates on problems
 with a one-variable objective along the gradient (tests/test_oracle_step_rule.py).
-The annealing trigger and the stopping rule (readings of Sec. IV, no closed
-form) are checked as the control sequence the reading states along traces;
-the registration's end point by recovery of a known transform.
+The annealing trigger and the stopping rule (readings of Sec. IV) by
+closed-form annealed trajectories of the same one-variable problems
+(tests/test_oracle_anneal_pins.py); the registration's end point by recovery
+of a known transform.
 """
 from __future__ import annotations
 

@@ -43,9 +43,10 @@
  * step size without a rule); it, its clamps, its fixed-step fallback and the
  * left-composed update are pinned by closed-form Newton iterates on problems
  * whose objective along the gradient line has one variable.  The annealing
- * trigger and the convergence test are readings of Sec. IV with no closed
- * form: tests check them as the control sequence the reading states, along
- * registration traces, and the end point by recovery of a known transform.
+ * trigger and the convergence test (readings of Sec. IV) are pinned on the
+ * same problems: there every iteration's indicator, step and decision follow
+ * from a scalar formula, and the tests compare the decay iterations, the
+ * lengthscales and the stop iteration with that closed form.
  */
 #include <math.h>
 #include <stdint.h>

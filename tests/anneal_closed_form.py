@@ -1,0 +1,166 @@
+"""Closed-form registration trajectories with lengthscale annealing.
+
+Two problems whose objective along the gradient line has one variable, so
+that every iteration of the registration loop -- the indicator, the step,
+the annealing decision and the stopping test -- follows from a scalar
+formula, with no call into the oracle or the CUDA library:
+
+- "trans": one pair of points on the x axis, x = (1 + u0, 0, 0) and
+  z = (1, 0, 0).  The gradient is a pure translation along x; with u the
+  offset left, F = sigma^2 exp(-u^2 / 2 l^2), the Newton step along the line
+  is u l^2 / (l^2 - u^2) while u < l (F'' < 0 there), else the fixed 1e-3 m
+  step, clamped to max_step (m) or, when max_step <= 0, to l / 2.
+- "rot": two pairs placed point-symmetrically about the origin at radius r,
+  Z = R_z(-u0) X, with a cutoff that keeps each point with its own partner
+  only.  The translational gradient cancels; with u the angle left and
+  a = r^2 / l^2, F = 2 sigma^2 exp(-a (1 - cos u)) and the Newton step is
+  sin u / (cos u - a sin^2 u) while the denominator is positive, clamped to
+  max_step (rad).
+
+The indicator is Eq. (indicator_actual), i = F / sqrt(N M): sigma^2
+exp(-u^2 / 2 l^2) for "trans" (N = M = 1) and sigma^2 exp(-a (1 - cos u))
+for "rot" (N = M = 2).
+
+The control rule is the reading of Sec. IV that the library and the oracle
+implement (the paper decays the lengthscale by 2 % "when the indicator
+stabilises" and defines neither that test nor a stopping test):
+  - converged: the lengthscale is at its floor (or annealing is off) and the
+    step is below step_tol (both the rotation and the translation step);
+  - otherwise, while l > l_min: the indicator has stabilised when a
+    reference indicator i_ref, taken at the previous iteration at the same
+    lengthscale, exists and |i_k - i_ref| < tol |i_ref|; then
+    l <- max(decay l, l_min) and the reference is dropped; else i_ref = i_k.
+
+`variant` computes plausible misreadings of that rule on the same problem,
+so that a test can show that the case tells them apart: "abs" (absolute
+tolerance), "km2" (comparison with the indicator two iterations back), "keep"
+(reference kept across a decay), "or" (stop when either step is small: here
+the other step is always zero), "nofloor" (stop on a small step whatever the
+lengthscale).
+
+Arithmetic: mpmath at 30 digits when it is importable, else Python floats
+(the cases are chosen with every decision at least 2 % of the tolerance away
+from its threshold, far beyond either precision).
+"""
+from __future__ import annotations
+
+try:
+    import mpmath as _mp
+
+    _mp.mp.dps = 30
+    _num, _exp, _cos, _sin = _mp.mpf, _mp.exp, _mp.cos, _mp.sin
+except Exception:  # pragma: no cover - the GPU image may lack mpmath
+    import math as _m
+
+    _num, _exp, _cos, _sin = float, _m.exp, _m.cos, _m.sin
+
+
+# The cases the tests pin (problem parameters and the registration's own).
+CASES = {
+    # decays interleaved with non-decays while the clamped approach slows,
+    # then every second iteration once the pair is aligned, down to the floor
+    "trans_anneal": dict(kind="trans", u0=0.3037, ell=0.5, ell_min=0.3, sigma=2.0, decay=0.9, tol=2e-3,
+                         max_step=0.01, max_iters=200),
+    # the floor is reached while the clamped steps are still large
+    "trans_floor_early": dict(kind="trans", u0=0.3037, ell=0.5, ell_min=0.45, sigma=2.0, decay=0.9, tol=2e-3,
+                              max_step=0.01, max_iters=200),
+    # rotation about z, annealed
+    "rot_anneal": dict(kind="rot", u0=0.2537, ell=0.5, ell_min=0.35, sigma=1.5, decay=0.9, tol=1e-3,
+                       max_step=0.01, max_iters=200, r=1.0),
+}
+
+STEP_TOL = 1e-5
+
+
+def trajectory(kind, u0, ell, ell_min, sigma, decay, tol, max_step, max_iters, r=1.0, step_tol=STEP_TOL,
+               variant="reading"):
+    """Iterations of the registration loop on the closed-form problem.
+
+    Returns a list of dicts per iteration: ell (the lengthscale the iteration
+    ran at), i (indicator), step (signed step length: m or rad), decayed
+    (0/1), margin (|i - i_ref| / (tol |i_ref|) - 1 where a reference existed,
+    else None), and u (the offset or angle left before the step)."""
+    u, l = _num(u0), _num(ell)
+    lmin = _num(ell_min)
+    have, i_ref = False, _num(0)
+    hist, out = [], []
+    for _ in range(int(max_iters)):
+        if kind == "trans":
+            i = _num(sigma) ** 2 * _exp(-u * u / (2 * l * l))
+            if u == 0:
+                newton = _num(0)
+            elif u * u < l * l:
+                newton = u * l * l / (l * l - u * u)
+            else:
+                newton = _num("1e-3")
+            cap = _num(max_step) if max_step > 0 else l / 2
+        else:
+            a = _num(r) ** 2 / (l * l)
+            i = _num(sigma) ** 2 * _exp(-a * (1 - _cos(u)))
+            den = _cos(u) - a * _sin(u) ** 2
+            newton = _sin(u) / den if den > 0 else (_num("1e-3") if u > 0 else -_num("1e-3"))
+            cap = _num(max_step)
+        step = newton if abs(newton) <= cap else (cap if newton > 0 else -cap)
+        at_floor = l <= lmin
+        if variant == "or":
+            converged = at_floor      # the other step is always zero here
+        elif variant == "nofloor":
+            converged = abs(step) < step_tol
+        else:
+            converged = at_floor and abs(step) < step_tol
+        decayed, margin = 0, None
+        l_run = l
+        if not converged and l > lmin:
+            if have:
+                margin = float((abs(i - i_ref) - tol * abs(i_ref)) / (tol * abs(i_ref)))
+            if variant == "abs":
+                fire = have and abs(i - i_ref) < tol
+            elif variant == "km2":
+                fire = have and len(hist) >= 2 and abs(i - hist[-2]) < tol * abs(hist[-2])
+            else:
+                fire = have and abs(i - i_ref) < tol * abs(i_ref)
+            if fire:
+                l = max(decay * l, lmin)
+                decayed = 1
+                if variant != "keep":
+                    have = False
+            else:
+                i_ref, have = i, True
+        hist.append(i)
+        out.append(dict(ell=float(l_run), i=float(i), step=float(step), decayed=decayed, margin=margin,
+                        u=float(u)))
+        u = u - step
+        if converged:
+            break
+    return out
+
+
+def points(case):
+    """The two clouds of a case (float64 arrays, X then Z) and the
+    registration parameters in the keyword form both libraries take."""
+    import numpy as np
+
+    c = CASES[case]
+    if c["kind"] == "trans":
+        X = np.array([[1.0 + c["u0"], 0.0, 0.0]])
+        Z = np.array([[1.0, 0.0, 0.0]])
+        kw = dict(ell=c["ell"], ell_min=c["ell_min"], sigma=c["sigma"], cutoff_mult=0.0, anneal=True,
+                  decay=c["decay"], indicator_tol=c["tol"], max_iters=c["max_iters"], max_step_trans=c["max_step"],
+                  step_tol_rot=STEP_TOL, step_tol_trans=STEP_TOL)
+    else:
+        r, u0 = c["r"], c["u0"]
+        X = np.array([[r, 0.0, 0.0], [-r, 0.0, 0.0]])
+        cz, sz = np.cos(-u0), np.sin(-u0)
+        Rz = np.array([[cz, -sz, 0.0], [sz, cz, 0.0], [0.0, 0.0, 1.0]])
+        Z = (Rz @ X.T).T
+        # cutoff 3 l keeps each point with its own partner only (the others
+        # are 2 r apart, beyond 3 l for every l of the schedule)
+        kw = dict(ell=c["ell"], ell_min=c["ell_min"], sigma=c["sigma"], cutoff_mult=3.0, anneal=True,
+                  decay=c["decay"], indicator_tol=c["tol"], max_iters=c["max_iters"], max_step_rot=c["max_step"],
+                  step_tol_rot=STEP_TOL, step_tol_trans=STEP_TOL)
+    return X, Z, kw
+
+
+def summary(traj):
+    """(iterations, decay iterations) of a trajectory."""
+    return len(traj), [k for k, it in enumerate(traj) if it["decayed"]]

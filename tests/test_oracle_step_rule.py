@@ -18,8 +18,9 @@ closed form alone, with no call into the oracle's arithmetic:
   step is sin(phi) / (cos(phi) - a sin(phi)^2).
 
 The annealing trigger and stopping test are readings of Sec. IV (the paper
-defines neither); they are checked as the control sequence those readings
-state, along a registration's own trace.
+defines neither).  They are pinned by closed-form annealed trajectories in
+tests/test_oracle_anneal_pins.py; the tests here add checks of the same rule
+along registrations of a cube scene.
 """
 import math
 
