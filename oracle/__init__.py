@@ -11,9 +11,11 @@ by quadrature of the Gaussian convolution identity and by the explicit tensor
 product of Eq. (tensor_product); symmetry, rigid invariance, Cauchy-Schwarz,
 the Remark of Sec. III-C, the gradient and second derivative by central finite
 differences on se(3), the SE(3) exponential by the matrix exponential.
-The step rule, its clamps and the left-composed update (a reading: the paper
-names a step size without a rule) by closed-form Newton iterates on problems
-with a one-variable objective along the gradient (tests/test_oracle_step_rule.py).
+The step rule, its trust region and the left-composed update (a reading: the
+paper names a step size without a rule and cites gradient ascent on the Lie
+group) by closed-form Newton iterates on problems with a one-variable
+objective along the ascent direction, and by the equivariance of the whole
+registration under a common rigid motion (tests/test_oracle_step_rule.py).
 The annealing trigger and the stopping rule (readings of Sec. IV) by
 closed-form annealed trajectories of the same one-variable problems
 (tests/test_oracle_anneal_pins.py); the registration's end point by recovery

@@ -40,9 +40,14 @@
  *
  * The gradient and the second derivative are pinned by central finite
  * differences of F (tests).  The step rule is a reading (the paper names a
- * step size without a rule); it, its clamps, its fixed-step fallback and the
+ * step size without a rule, and cites gradient ascent on the Lie group): a
+ * line-Newton step along the ascent direction of an origin-free metric,
+ * inside a trust region on the motion of Z's points (orc_register).  It, its
+ * trust region, its step to the region's edge where F'' >= 0 and the
  * left-composed update are pinned by closed-form Newton iterates on problems
- * whose objective along the gradient line has one variable.  The annealing
+ * whose objective along the ascent direction has one variable, and by the
+ * equivariance of the whole registration under a common rigid motion of the
+ * inputs.  The annealing
  * trigger and the convergence test (readings of Sec. IV) are pinned on the
  * same problems: there every iteration's indicator, step and decision follow
  * from a scalar formula, and the tests compare the decay iterations, the
@@ -407,20 +412,35 @@ typedef struct {
     long long pairs_total;
 } orc_info;
 
-#define ORC_TRACE_STRIDE 22 /* ell, F, i_theta, |g|, Fpp, t, |t omega|, |t v|, decayed, pairs, rows 0-2 of T_k */
+#define ORC_TRACE_STRIDE 22 /* ell, F, i_theta, sqrt(F'), Fpp, t, |t omega|, |t u|, decayed, pairs, rows 0-2 of T_k */
 
 /*
- * Gradient ascent on SE(3), one line-Newton step along the gradient per
- * iteration, with the lengthscale annealing of Sec. IV.
+ * Gradient ascent on SE(3), one line-Newton step along the ascent direction
+ * per iteration inside a trust region, with the lengthscale annealing of
+ * Sec. IV.
+ *
+ * The ascent direction is the gradient in a metric on se(3) that does not
+ * depend on where the origin of the coordinates lies: perturbations are
+ * written about the moved centroid p = R zbar + t of Z, eta = (omega, u) with
+ * u the velocity of p (xi = (omega, u + p x omega)), and measured by
+ * |eta|^2 = rho^2 |omega|^2 + |u|^2 with rho^2 the mean squared distance of
+ * Z's points from zbar plus l^2 (finite for a cloud of one point).  In these
+ * coordinates the gradient is h = (g_omega + g_v x p, g_v), the ascent
+ * direction d = (h_omega / rho^2, h_u), and F' = h.d.
+ * The trust region bounds how far any point of Z moves in one step,
+ * t (|omega| R + |u|) <= delta, R the largest distance of a point of Z from
+ * zbar, delta = max_step_trans (> 0) or half the lengthscale; and the
+ * rotation, t |omega| <= max_step_rot.
  *
  * Iteration k at pose T_k and lengthscale l_k:
- *   1. F, g, and the second derivative F'' along xi = g (brute force).
+ *   1. F, g, the ascent direction d, and the second derivative F'' along d
+ *      (brute force).
  *   2. i_k = F / sqrt(N M), Eq. (indicator_actual).
- *   3. Step: t = |g|^2 / (-F'') if F'' < 0, else 1e-3 / |g|; then clamp so that
- *      |t omega| <= max_step_rot and |t v| <= max_step_trans.
- *   4. T_{k+1} = exp(t xi^) T_k; Gram-Schmidt on R every 16 iterations.
+ *   3. Step: t = F' / (-F'') if F'' < 0, else the trust region's edge; in
+ *      both cases at most the trust region's edge.
+ *   4. T_{k+1} = exp(t d^) T_k (d as xi); Gram-Schmidt on R every 16 iterations.
  *   5. Stop (converged) if annealing is off or l_k == ell_min, and
- *      |t omega| < step_tol_rot and |t v| < step_tol_trans.
+ *      |t omega| < step_tol_rot and |t u| < step_tol_trans.
  *   6. Annealing: if a reference indicator i_ref at l_k exists and
  *      |i_k - i_ref| < tol |i_ref|, then l_{k+1} = max(decay l_k, ell_min) and
  *      the reference is cleared; otherwise i_ref = i_k.
@@ -441,6 +461,19 @@ int orc_register(const orc_kernel* kin, const orc_reg* r, const orc_cloud* X, co
     int have_ref = 0;
     double i_ref = 0.0;
     const double norm = (X->n > 0 && Z->n > 0) ? 1.0 / sqrt((double)X->n * (double)Z->n) : 0.0;
+    /* centroid of Z, mean squared and largest distance of its points from it */
+    double zbar[3] = {0.0, 0.0, 0.0}, r2 = 0.0, rmax = 0.0;
+    for (int j = 0; j < Z->n; ++j)
+        for (int a = 0; a < 3; ++a) zbar[a] += Z->xyz[3 * (size_t)j + a];
+    for (int a = 0; a < 3; ++a) zbar[a] = Z->n > 0 ? zbar[a] / Z->n : 0.0;
+    for (int j = 0; j < Z->n; ++j) {
+        const double* z = Z->xyz + 3 * (size_t)j;
+        const double e[3] = {z[0] - zbar[0], z[1] - zbar[1], z[2] - zbar[2]};
+        const double q = dot3(e, e);
+        r2 += q;
+        if (sqrt(q) > rmax) rmax = sqrt(q);
+    }
+    if (Z->n > 0) r2 /= Z->n;
     orc_info inf;
     memset(&inf, 0, sizeof(inf));
     inf.status = 1;
@@ -454,28 +487,47 @@ int orc_register(const orc_kernel* kin, const orc_reg* r, const orc_cloud* X, co
         orc_eval(&k, X, Z, T, NULL, out, &np, nthreads);
         double g[6];
         memcpy(g, out + 1, sizeof(g));
-        /* second derivative along the gradient */
-        orc_eval(&k, X, Z, T, g, out, NULL, nthreads);
+        /* the gradient about the moved centroid p, and the ascent direction
+           d in the origin's coordinates xi = (omega, u + p x omega) */
+        double p[3];
+        for (int a = 0; a < 3; ++a) p[a] = T[4 * a] * zbar[0] + T[4 * a + 1] * zbar[1] + T[4 * a + 2] * zbar[2] + T[4 * a + 3];
+        double hw[3], hu[3], gvxp[3];
+        cross3(g + 3, p, gvxp);
+        for (int a = 0; a < 3; ++a) {
+            hw[a] = g[a] + gvxp[a];
+            hu[a] = g[3 + a];
+        }
+        const double rho2 = r2 + ell * ell;
+        double dw[3], pxw[3], d[6];
+        for (int a = 0; a < 3; ++a) dw[a] = hw[a] / rho2;
+        cross3(p, dw, pxw);
+        for (int a = 0; a < 3; ++a) {
+            d[a] = dw[a];
+            d[3 + a] = hu[a] + pxw[a];
+        }
+        const double Fp = dot3(hw, dw) + dot3(hu, hu);   /* F' along d */
+        /* second derivative along d */
+        orc_eval(&k, X, Z, T, d, out, NULL, nthreads);
         const double F = out[0], Fpp = out[7];
         const double ith = F * norm;
-        double gn2 = 0.0;
-        for (int q = 0; q < 6; ++q) gn2 += g[q] * g[q];
+        const double wn = sqrt(dot3(dw, dw)), un = sqrt(dot3(hu, hu));
         double t = 0.0;
-        if (gn2 > 0.0) {
-            t = (Fpp < 0.0) ? gn2 / (-Fpp) : 1e-3 / sqrt(gn2);
-            const double wn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-            const double vn = sqrt(g[3] * g[3] + g[4] * g[4] + g[5] * g[5]);
-            const double max_tr = r->max_step_trans > 0.0 ? r->max_step_trans : 0.5 * ell;
-            if (t * wn > r->max_step_rot) t = r->max_step_rot / wn;
-            if (t * vn > max_tr) t = max_tr / vn;
+        if (Fp > 0.0) {
+            const double delta = r->max_step_trans > 0.0 ? r->max_step_trans : 0.5 * ell;
+            const double m = wn * rmax + un;   /* bound on the speed of Z's points along d */
+            double tmax = m > 0.0 ? delta / m : HUGE_VAL;
+            if (wn > 0.0 && tmax * wn > r->max_step_rot) tmax = r->max_step_rot / wn;
+            t = (Fpp < 0.0) ? Fp / (-Fpp) : tmax;
+            if (t > tmax) t = tmax;
         }
         double xi[6], E[16];
-        for (int q = 0; q < 6; ++q) xi[q] = t * g[q];
+        for (int q = 0; q < 6; ++q) xi[q] = t * d[q];
         orc_se3_exp(xi, E);
         mat4_mul(E, T, T);
         if ((it + 1) % 16 == 0) reorthonormalize(T);
-        const double srot = sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
-        const double strans = sqrt(xi[3] * xi[3] + xi[4] * xi[4] + xi[5] * xi[5]);
+        const double srot = t * wn;
+        const double strans = t * un;
+        const double gn = sqrt(Fp);
         inf.pairs_total += np;
         inf.F = F;
         inf.i_theta = ith;
@@ -501,7 +553,7 @@ int orc_register(const orc_kernel* kin, const orc_reg* r, const orc_cloud* X, co
         }
         if (trace) {
             double* tr = trace + (size_t)ORC_TRACE_STRIDE * it;
-            tr[0] = k.ell; tr[1] = F; tr[2] = ith; tr[3] = sqrt(gn2); tr[4] = Fpp;
+            tr[0] = k.ell; tr[1] = F; tr[2] = ith; tr[3] = gn; tr[4] = Fpp;
             tr[5] = t; tr[6] = srot; tr[7] = strans; tr[8] = decayed; tr[9] = (double)np;
             for (int q = 0; q < 12; ++q) tr[10 + q] = T_k[q];
         }

@@ -6,16 +6,20 @@ the annealing decision and the stopping test -- follows from a scalar
 formula, with no call into the oracle or the CUDA library:
 
 - "trans": one pair of points on the x axis, x = (1 + u0, 0, 0) and
-  z = (1, 0, 0).  The gradient is a pure translation along x; with u the
-  offset left, F = sigma^2 exp(-u^2 / 2 l^2), the Newton step along the line
-  is u l^2 / (l^2 - u^2) while u < l (F'' < 0 there), else the fixed 1e-3 m
-  step, clamped to max_step (m) or, when max_step <= 0, to l / 2.
+  z = (1, 0, 0).  The ascent direction is a pure translation along x; with u
+  the offset left, F = sigma^2 exp(-u^2 / 2 l^2), the Newton step along the
+  line is u l^2 / (l^2 - u^2) while u < l (F'' < 0 there), else the step to
+  the trust region's edge; never beyond that edge, max_step (m) or, when
+  max_step <= 0, l / 2 (one point: it moves by the step itself).
 - "rot": two pairs placed point-symmetrically about the origin at radius r,
   Z = R_z(-u0) X, with a cutoff that keeps each point with its own partner
-  only.  The translational gradient cancels; with u the angle left and
+  only.  The translational gradient cancels and the ascent direction is a
+  rotation about Z's centroid (the origin); with u the angle left and
   a = r^2 / l^2, F = 2 sigma^2 exp(-a (1 - cos u)) and the Newton step is
-  sin u / (cos u - a sin^2 u) while the denominator is positive, clamped to
-  max_step (rad).
+  sin u / (cos u - a sin^2 u) while the denominator is positive, else the
+  step to the trust region's edge; never beyond that edge, the smaller of
+  max_step (rad) and l / (2 r) (a rotation by s moves Z's points, at
+  distance r from the centroid, by r s).
 
 The indicator is Eq. (indicator_actual), i = F / sqrt(N M): sigma^2
 exp(-u^2 / 2 l^2) for "trans" (N = M = 1) and sigma^2 exp(-a (1 - cos u))
@@ -87,19 +91,19 @@ def trajectory(kind, u0, ell, ell_min, sigma, decay, tol, max_step, max_iters, r
     for _ in range(int(max_iters)):
         if kind == "trans":
             i = _num(sigma) ** 2 * _exp(-u * u / (2 * l * l))
+            cap = _num(max_step) if max_step > 0 else l / 2
             if u == 0:
                 newton = _num(0)
             elif u * u < l * l:
                 newton = u * l * l / (l * l - u * u)
             else:
-                newton = _num("1e-3")
-            cap = _num(max_step) if max_step > 0 else l / 2
+                newton = cap if u > 0 else -cap
         else:
             a = _num(r) ** 2 / (l * l)
             i = _num(sigma) ** 2 * _exp(-a * (1 - _cos(u)))
             den = _cos(u) - a * _sin(u) ** 2
-            newton = _sin(u) / den if den > 0 else (_num("1e-3") if u > 0 else -_num("1e-3"))
-            cap = _num(max_step)
+            cap = min(_num(max_step), l / (2 * _num(r)))
+            newton = _sin(u) / den if den > 0 else (cap if u > 0 else -cap)
         step = newton if abs(newton) <= cap else (cap if newton > 0 else -cap)
         at_floor = l <= lmin
         if variant == "or":

@@ -44,6 +44,8 @@ def test_null_handle_rejected_by_every_entry_point(lib):
         "cvo_metric": lambda: lib.cvo_metric(None, None, None, T, ref(d)),
         "cvo_gradient": lambda: lib.cvo_gradient(None, None, None, T, grad, None),
         "cvo_backward": lambda: lib.cvo_backward(None, None, None, T, 1.0, None, None, None, None, ref(d), 0),
+        "cvo_metric_backward": lambda: lib.cvo_metric_backward(None, None, None, T, 1.0, None, None, None, None,
+                                                               ref(d), 0),
         "cvo_cosine": lambda: lib.cvo_cosine(None, None, None, T, None, ref(d), None),
         "cvo_register_pair": lambda: lib.cvo_register_pair(None, None, None, T, T, ref(info)),
         "cvo_register_batch": lambda: lib.cvo_register_batch(None, 1, None, None, T, T, None),
@@ -113,6 +115,15 @@ def test_noalloc_rejects_before_device_work(lib):
     bad = cvo.make_params(cutoff_mult=0.0, blocks=[("se", 3, 0.2, 1.0)])
     bad.blocks[0].scale = 0.0
     expect_invalid(call(bad), "invalid feature block")
+    # the same checks as cvo_create: a finite scale and a finite sigma
+    bad.blocks[0].scale = float("inf")
+    expect_invalid(call(bad), "invalid feature block")
+    bad.blocks[0].scale = 0.2
+    bad.blocks[0].sigma = float("nan")
+    expect_invalid(call(bad), "invalid feature block")
+    with pytest.raises(cvo.CvoError) as e:
+        cvo.cvo_create(bad, stream=0)
+    assert e.value.status == INVALID
 
 
 C_CLIENT = r'''

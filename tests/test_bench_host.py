@@ -15,6 +15,31 @@ CSRC = os.path.join(ROOT, "paper_2012_03683_gb300", "csrc")
 SWEEP_SRC = [os.path.join(CSRC, "cvo_sweep.cu"), os.path.join(CSRC, "cvo_sweep_dev.cuh")]
 
 
+def test_grad_flops_per_pair():
+    # offset 3, distance 5, scale 1, weight 1, accumulators 8; SE block 6d + 1; dot block 4d
+    assert bench.grad_flops_per_pair([]) == 18
+    assert bench.grad_flops_per_pair([("se", 3, 0.2, 1.0)]) == 18 + 19
+    assert bench.grad_flops_per_pair([("se", 3, 0.2, 1.0), ("dot", 19, 1.0, 1.0)]) == 18 + 19 + 76
+
+
+def test_cpu_sample_is_seeded_and_in_range():
+    a = bench.sample_pairs(64)
+    assert a == bench.sample_pairs(64) and len(a) == bench.CPU_SAMPLE_PAIRS == len(set(a))
+    assert all(0 <= k < 64 for k in a)
+
+
+def test_roofline_arithmetic():
+    peaks = {"sm_max_mhz": 2000.0}
+    r = bench.sweep_roofline("k", pairs_evaluated=1e9, sweep_ms_total=100.0, launches=50, fpp=76, peaks=peaks,
+                             peak_src="measured", sms=152)
+    assert r["peak"] == pytest.approx(152 * 128 * 2 * 2e9 / 1e12)
+    assert r["achieved"] == pytest.approx(1e9 * 76 / 0.1 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["sweep_ms_avg"] == pytest.approx(2.0) and r["pairs_per_launch"] == pytest.approx(2e7)
+    assert r["sfu"]["achieved_ex2_per_s"] == pytest.approx(1e10)
+    assert "unit counts" in r["peak_source"]
+
+
 def test_flops_per_pair():
     # offset 3, distance 5, scale 1, moments 19; SE block 3d + 1; dot block 2d
     assert bench.flops_per_pair([]) == 28
@@ -28,8 +53,8 @@ def test_profile_values_follow_the_source_hash(tmp_path):
     text = open(os.path.join(ROOT, "profiles", "sweep_street-20k.md")).read()
     recorded = re.search(r"source_sha256:\s*([0-9a-f]{64})", text).group(1)
     current = hashlib.sha256(b"".join(open(f, "rb").read() for f in SWEEP_SRC)).hexdigest()
-    traffic = bench.profile_value(SWEEP_SRC, "traffic_bytes_per_launch")
-    winst = bench.profile_value(SWEEP_SRC, "warp_instructions_per_launch")
+    traffic = bench.profile_value(SWEEP_SRC, "traffic_bytes_per_launch", "sweep_street-20k.md")
+    winst = bench.profile_value(SWEEP_SRC, "warp_instructions_per_launch", "sweep_street-20k.md")
     if current == recorded:   # the summary was taken on this source: its figures are reported
         assert traffic is not None and 1e6 < traffic < 1e8
         assert winst is not None and 1e6 < winst < 1e9
@@ -38,8 +63,9 @@ def test_profile_values_follow_the_source_hash(tmp_path):
     # any other source (a changed kernel) gets no figure
     other = tmp_path / "changed.cu"
     other.write_text(open(SWEEP_SRC[0]).read() + "\n// changed\n")
-    assert bench.profile_value([str(other), SWEEP_SRC[1]], "traffic_bytes_per_launch") is None
-    assert bench.profile_value(SWEEP_SRC, "no_such_key") is None
+    assert bench.profile_value([str(other), SWEEP_SRC[1]], "traffic_bytes_per_launch", "sweep_street-20k.md") is None
+    assert bench.profile_value(SWEEP_SRC, "no_such_key", "sweep_street-20k.md") is None
+    assert bench.profile_value(SWEEP_SRC, "traffic_bytes_per_launch", "no_such_profile.md") is None
 
 
 class _FakeProc:

@@ -302,6 +302,8 @@ def test_autograd_function(room):
     # the indicator of Eq. (indicator_actual) is F / sqrt(N M)
     Xt.grad = None
     i = cvo.metric_fn(h, Xt, Zt, T, FXt.detach(), FZt.detach())
+    # the value is the library's cvo_metric (no arithmetic in the binding)
+    assert i.item() == h.metric(dev(X), dev(Z), T, dev(FX), dev(FZ))
     i.backward()
     want = d["dX"].double().cpu().numpy() / math.sqrt(len(X) * len(Z))
     assert np.abs(Xt.grad.double().cpu().numpy() - want).max() <= 1e-6 * np.abs(want).max()
@@ -309,3 +311,27 @@ def test_autograd_function(room):
     ref = oracle.backward(X, Z, T, FX=FX, FZ=FZ, blocks=room.blocks, ell=0.1, cutoff_mult=3.0)
     sx, _ = band_masks(X, Z, T, 0.09)
     check_close(Xt.grad.double().cpu().numpy() * math.sqrt(len(X) * len(Z)), ref["dX"], sx, "autograd dX")
+
+
+def test_metric_backward_through_the_c_abi(room):
+    """cvo_metric_backward gives the gradients of di * i_theta: those of
+    cvo_backward scaled by 1 / sqrt(N M) (Eq. indicator_actual), against the
+    oracle's input gradients; empty clouds give zeros."""
+    X, Z, FX, FZ = slice_pair(room, 2000, 14)
+    T = room.T_true
+    h = cvo.CVO(blocks=room.blocks, ell=0.1, cutoff_mult=3.0)
+    di = -1.75
+    got = cvo.cvo_metric_backward(h.h, dev(X), dev(Z), T, dev(FX), dev(FZ), di=di)
+    base = h.backward(dev(X), dev(Z), T, dev(FX), dev(FZ))
+    s = di / math.sqrt(len(X) * len(Z))
+    for k in ("dX", "dZ", "dFX", "dFZ"):
+        g = got[k].double().cpu().numpy()
+        want = s * base[k].double().cpu().numpy()
+        assert np.abs(g - want).max() <= 1e-6 * np.abs(want).max(), k
+    # the scale enters the per-query float32 terms before their sum
+    assert got["dell"] == pytest.approx(s * base["dell"], rel=1e-6)
+    ref = oracle.backward(X, Z, T, FX=FX, FZ=FZ, blocks=room.blocks, ell=0.1, cutoff_mult=3.0)
+    sx, _ = band_masks(X, Z, T, 0.09)
+    check_close(got["dX"].double().cpu().numpy() / s, ref["dX"], sx, "metric dX")
+    e = cvo.cvo_metric_backward(h.h, dev(X[:0]), dev(Z), T, dev(FX[:0]), dev(FZ), di=di)
+    assert float(e["dZ"].abs().max()) == 0.0 and e["dell"] == 0.0

@@ -354,3 +354,60 @@ def test_persistent_loop_deterministic_and_close_to_graph():
     np.testing.assert_allclose(tr1[:k, 2], trg[:k, 2], rtol=1e-5)   # indicator
     np.testing.assert_allclose(tr1[:k, 9], trg[:k, 9], rtol=1e-3)   # pairs (cutoff decisions)
     np.testing.assert_allclose(tr1[:k, 10:22], trg[:k, 10:22], atol=1e-4)   # poses the steps start from
+
+
+def _trace_pose(row):
+    T = np.eye(4)
+    T[:3, :] = row[10:22].reshape(3, 4)
+    return T
+
+
+def test_persistent_loop_one_step_parity_with_oracle():
+    """The persistent kernel's iterations against the oracle: at sampled
+    iterations of its own trajectory the oracle takes one step from the
+    recorded pose and lengthscale, and F, the pair count and the next pose
+    agree (as the graph loop's full-size test checks)."""
+    p = scenes.street_pair()
+    sel = rng(15).permutation(p.n)[:6000]
+    X, Z, FX, FZ = p.X[sel], p.Z[sel], p.FX[sel], p.FZ[sel]
+    kw = dict(ell=0.3, ell_min=0.05, cutoff_mult=3.0, max_iters=40, anneal=True)
+    with cvo.CVO(blocks=p.blocks, **kw) as h:
+        h.set_loop("persistent")
+        T_final, info = h.register(dev(X), dev(Z), np.eye(4), dev(FX), dev(FZ))
+        tr = h.trace()
+    last = tr.shape[0] - 1
+    assert last >= 10
+    for k in sorted({0, 1, 3, 10, last // 2, last}):
+        T_k, ell_k = _trace_pose(tr[k]), tr[k, 0]
+        T_next = _trace_pose(tr[k + 1]) if k < last else T_final
+        T1, _, otr = oracle.register(X, Z, T_k, FX=FX, FZ=FZ, blocks=p.blocks, ell=ell_k, cutoff_mult=3.0,
+                                     max_iters=1)
+        assert tr[k, 1] == pytest.approx(otr[0, 1], rel=F_RTOL), k
+        rc2 = (3.0 * ell_k) ** 2
+        band = oracle.count_band(X, Z, T_k, rc2 * (1 - 1e-5), rc2 * (1 + 1e-5))
+        assert abs(tr[k, 9] - otr[0, 9]) <= band, k
+        xi = oracle.se3_log(np.linalg.inv(T_next) @ T1)
+        assert np.linalg.norm(xi[:3]) <= POSE_TOL and np.linalg.norm(xi[3:]) <= POSE_TOL, k
+
+
+def test_clusters_far_apart_keep_the_grid_within_its_cell_cap():
+    """Two clusters 1e7 m apart with a 15 cm cutoff: the grid of Z would need
+    far more than 2^31 cells at the design cell size; the setup counts cells
+    in double and widens the cells until they fit, and F and the pair count
+    still equal the oracle's."""
+    r = rng(16)
+    a = r.uniform(-0.2, 0.2, size=(24, 3))
+    b = r.uniform(-0.2, 0.2, size=(24, 3))
+    b[:, 0] = 1.0e7                      # exactly representable; y and z carry the detail
+    X = np.concatenate([a, b]).astype(np.float32)
+    Z = (X + r.normal(scale=0.01, size=X.shape)).astype(np.float32)
+    Z[24:, 0] = 1.0e7
+    for T in (np.eye(4), rand_pose(r, ang=0.0, tr=0.02)):
+        with cvo.CVO(ell=0.05, cutoff_mult=3.0) as h:
+            got = h.evaluate(dev(X), dev(Z), T)
+        ref = oracle.evaluate(X.astype(np.float64), Z.astype(np.float64), T, ell=0.05, cutoff_mult=3.0)
+        assert ref["npairs"] > 48
+        assert got["F"] == pytest.approx(ref["F"], rel=F_RTOL)
+        rc2 = 0.15 ** 2
+        band = oracle.count_band(X.astype(np.float64), Z.astype(np.float64), T, rc2 * (1 - 1e-5), rc2 * (1 + 1e-5))
+        assert abs(got["pairs"] - ref["npairs"]) <= band

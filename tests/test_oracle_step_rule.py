@@ -1,23 +1,31 @@
 """Pins of the oracle's registration loop: the step rule, the pose update
-and its composition order, the step clamps, the annealing trigger and the
+and its composition order, the trust region, the annealing trigger and the
 stopping test.
 
-The paper names a step size (Sec. III-B) but prints no rule; the rule taken
-is a Newton step along the gradient line (t = |g|^2 / -F'' where F'' < 0,
-else a fixed 1e-3 step), clamped in rotation and translation.  On problems
-whose objective restricted to that line is a one-variable function with a
-closed form, the Newton step and its iterates are computed here from that
-closed form alone, with no call into the oracle's arithmetic:
+The paper names a step size (Sec. III-B) and cites gradient ascent on the Lie
+group (Sec. I) but prints no rule.  The rule taken: the ascent direction is
+the gradient in a metric on se(3) written about the moved centroid of Z
+(rotations weighted by the cloud's mean squared radius plus l^2), so it does
+not depend on where the coordinate origin lies; the step is a Newton step
+along that direction (t = F' / -F'' where F'' < 0, else the trust region's
+edge), never beyond the trust region: no point of Z moves more than half a
+lengthscale (or max_step_trans), no rotation exceeds max_step_rot.  On
+problems whose objective along the ascent direction has one variable, the
+Newton step and its iterates are computed here from that closed form alone,
+with no call into the oracle's arithmetic:
 
-- one pair of points on the x axis, offset delta: the line is a pure
+- one pair of points on the x axis, offset delta: the direction is a pure
   translation along x and F(s) = exp(-(delta - s)^2 / 2 l^2), so the Newton
   step is s* = delta l^2 / (l^2 - delta^2) while delta < l;
-- two pairs placed point-symmetrically about the origin, Z = R_z(-phi) X:
-  the translational gradient cancels, the line is a rotation about z and
-  F(theta) = 2 exp(-a (1 - cos(phi - theta))), a = r^2 / l^2, so the Newton
-  step is sin(phi) / (cos(phi) - a sin(phi)^2).
+- two pairs placed point-symmetrically about a centre q, Z = R_z(-phi) X
+  about q: the translational gradient cancels, the direction is a rotation
+  about q and F(theta) = 2 exp(-a (1 - cos(phi - theta))), a = r^2 / l^2, so
+  the Newton step is sin(phi) / (cos(phi) - a sin(phi)^2).
 
-The annealing trigger and stopping test are readings of Sec. IV (the paper
+The whole registration is equivariant under a common rigid motion of both
+clouds (the objective is invariant, Sec. III; the rule names no origin),
+which a direction taken about the coordinate origin would break.  The
+annealing trigger and stopping test are readings of Sec. IV (the paper
 defines neither).  They are pinned by closed-form annealed trajectories in
 tests/test_oracle_anneal_pins.py; the tests here add checks of the same rule
 along registrations of a cube scene.
@@ -46,10 +54,11 @@ def rz(t):
     return np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
 
 
-def symmetric_pairs(r, phi):
+def symmetric_pairs(r, phi, q=(0.0, 0.0, 0.0)):
+    q = np.asarray(q, dtype=np.float64)
     X = np.array([[r, 0.0, 0.0], [-r, 0.0, 0.0]])
     Z = (rz(-phi) @ X.T).T
-    return X, Z
+    return X + q, Z + q
 
 
 def newton_translation(delta, ell=ELL):
@@ -120,11 +129,13 @@ def test_translation_clamp_explicit():
     assert T[0, 3] == pytest.approx(0.05, rel=1e-14)
 
 
-def test_fixed_step_where_curvature_is_not_negative():
-    delta = 1.5 * ELL                        # beyond the inflection point: F'' > 0 along g
+def test_step_to_the_trust_edge_where_curvature_is_not_negative():
+    delta = 1.5 * ELL                        # beyond the inflection point: F'' > 0 along the direction
     T, _, tr = oracle.register(*axial_pair(delta), np.eye(4), ell=ELL, max_iters=1)
     assert tr[0, C_FPP] > 0.0
-    assert T[0, 3] == pytest.approx(1e-3, rel=1e-12)
+    assert T[0, 3] == pytest.approx(0.5 * ELL, rel=1e-12)
+    T, _, _ = oracle.register(*axial_pair(delta), np.eye(4), ell=ELL, max_iters=1, max_step_trans=0.03)
+    assert T[0, 3] == pytest.approx(0.03, rel=1e-12)
 
 
 def test_zero_gradient_takes_no_step_and_stops():
@@ -265,3 +276,79 @@ def test_rotation_stays_orthonormal_over_long_runs():
     R = T[:3, :3]
     assert np.abs(R @ R.T - np.eye(3)).max() < 1e-13 and np.linalg.det(R) == pytest.approx(1.0, abs=1e-13)
     assert np.array_equal(T[3], [0.0, 0.0, 0.0, 1.0])
+
+
+Q_FAR = (30.0, -20.0, 50.0)
+
+
+def rotation_about(q, theta):
+    """The pose that rotates by theta about the z axis through q."""
+    R = rz(theta)
+    T = np.eye(4)
+    T[:3, :3] = R
+    T[:3, 3] = np.asarray(q) - R @ np.asarray(q)
+    return T
+
+
+def test_rotation_newton_iterates_about_an_off_origin_centre():
+    """The pairs point-symmetric about a centre q far from the origin: the
+    ascent direction is the rotation about q (not about the origin), and
+    the iterates are the closed-form Newton iterates of the centred problem."""
+    r, phi = 1.0, 0.08
+    a = r * r / ELL ** 2
+    T, _, tr = oracle.register(*symmetric_pairs(r, phi, Q_FAR), np.eye(4), ell=ELL, cutoff_mult=3.0, max_iters=4,
+                               step_tol_rot=0.0, step_tol_trans=0.0)
+    u, total = phi, 0.0
+    for k in range(tr.shape[0]):
+        Tk = np.eye(4)
+        Tk[:3, :] = tr[k, C_T0:C_T0 + 12].reshape(3, 4)
+        assert np.allclose(Tk, rotation_about(Q_FAR, total), atol=1e-12), k
+        assert tr[k, C_STR] < 1e-12                       # the centre does not move
+        s = newton_rotation(u, a)
+        total += s
+        u -= s
+    assert np.allclose(T, rotation_about(Q_FAR, total), atol=1e-12)
+
+
+def test_rotation_trust_region_bounds_the_points_motion():
+    """A rotation by s moves Z's points, at distance r from its centroid, by
+    r s: the step is at most half a lengthscale of motion, 0.5 l / r, below
+    max_step_rot here; where F'' >= 0 the step goes to that edge."""
+    r, ell = 1.0, 0.15
+    a = r * r / ell ** 2
+    edge = 0.5 * ell / r
+    assert edge < 0.1
+    # F'' < 0 and the Newton step beyond the edge
+    phi = 0.08
+    assert math.cos(phi) - a * math.sin(phi) ** 2 > 0 and newton_rotation(phi, a) > edge
+    T, _, tr = oracle.register(*symmetric_pairs(r, phi, Q_FAR), np.eye(4), ell=ell, cutoff_mult=3.0, max_iters=1)
+    assert tr[0, C_FPP] < 0.0 and tr[0, C_SROT] == pytest.approx(edge, rel=1e-12)
+    assert np.allclose(T, rotation_about(Q_FAR, edge), atol=1e-12)
+    # F'' >= 0 along the rotation: the step to the edge
+    phi = 0.3
+    assert math.cos(phi) - a * math.sin(phi) ** 2 < 0
+    T, _, tr = oracle.register(*symmetric_pairs(r, phi, Q_FAR), np.eye(4), ell=ell, cutoff_mult=3.0, max_iters=1)
+    assert tr[0, C_FPP] >= 0.0 and tr[0, C_SROT] == pytest.approx(edge, rel=1e-12)
+
+
+def test_registration_is_equivariant_under_a_common_rigid_motion():
+    """Moving both clouds by one rigid motion G (and the start pose by
+    conjugation) moves the whole trajectory the same way: T' = G T G^-1 at
+    every iteration, with the same indicators, lengthscales and decisions."""
+    p = scenes.cube_pair(n=400, seed=31)
+    G = oracle.se3_exp(np.array([0.4, -0.7, 0.25, 12.0, -30.0, 45.0]))
+    T0 = oracle.se3_exp(np.array([0.01, 0.02, -0.015, 0.03, 0.0, -0.02]))
+    kw = dict(FX=p.FX, FZ=p.FZ, blocks=p.blocks, ell=0.3, ell_min=0.12, cutoff_mult=3.0, max_iters=40, anneal=True,
+              decay=0.9, indicator_tol=2e-3)
+    T, info, tr = oracle.register(p.X, p.Z, T0, **kw)
+    GX = (G[:3, :3] @ p.X.astype(np.float64).T).T + G[:3, 3]
+    GZ = (G[:3, :3] @ p.Z.astype(np.float64).T).T + G[:3, 3]
+    Gi = np.linalg.inv(G)
+    Tg, infog, trg = oracle.register(GX, GZ, G @ T0 @ Gi, **kw)
+    assert infog["iters"] == info["iters"] and info["iters"] >= 10
+    assert np.array_equal(trg[:, C_DEC], tr[:, C_DEC]) and tr[:, C_DEC].sum() >= 2
+    np.testing.assert_allclose(trg[:, C_ELL], tr[:, C_ELL], rtol=1e-12)
+    np.testing.assert_allclose(trg[:, C_ITH], tr[:, C_ITH], rtol=1e-9)
+    np.testing.assert_allclose(trg[:, C_SROT], tr[:, C_SROT], rtol=1e-6, atol=1e-12)
+    np.testing.assert_allclose(trg[:, C_STR], tr[:, C_STR], rtol=1e-6, atol=1e-12)
+    assert np.abs(Tg - G @ T @ Gi).max() < 1e-9

@@ -41,9 +41,12 @@ def _cloud(xyz, feat):
     return c
 
 
-def noalloc_eval(params, X, Z, FX, FZ, T):
+def noalloc_eval(params, X, Z, FX, FZ, T, out=None):
+    """One call through the C ABI; out: a device buffer of sizeof(cvo_eval)
+    bytes for the results (one is made when None)."""
     fn = _fn()
-    out = torch.zeros(ctypes.sizeof(cvo.Eval), dtype=torch.uint8, device="cuda")
+    if out is None:
+        out = torch.zeros(ctypes.sizeof(cvo.Eval), dtype=torch.uint8, device="cuda")
     cx, cz = _cloud(X, FX), _cloud(Z, FZ)
     Tm = np.ascontiguousarray(T, dtype=np.float64)
     stream = torch.cuda.current_stream().cuda_stream
@@ -118,3 +121,57 @@ def test_noalloc_with_feature_cutoff_matches_oracle():
     assert ref["npairs"] < full["npairs"]
     assert got["F"] == pytest.approx(ref["F"], rel=1e-5)
     assert got["pairs"] == ref["npairs"]
+
+
+def test_noalloc_bfloat16_features_match_evaluate():
+    """Features stored in bfloat16 take the same path as in cvo_evaluate."""
+    p = scenes.cube_pair(n=1200, seed=77)
+    kw = dict(blocks=p.blocks, ell=0.1, cutoff_mult=0.0)
+    T = np.eye(4)
+    T[:3, 3] = [0.01, 0.02, -0.015]
+    X, Z = torch.tensor(p.X, device="cuda"), torch.tensor(p.Z, device="cuda")
+    FX = torch.tensor(p.FX, device="cuda").to(torch.bfloat16)
+    FZ = torch.tensor(p.FZ, device="cuda").to(torch.bfloat16)
+    got = noalloc_eval(cvo.make_params(**kw), X, Z, FX, FZ, T)
+    with cvo.CVO(**kw) as h:
+        ref = h.evaluate(X, Z, T, FX, FZ)
+    FXo, FZo = scenes.bf16_round(p.FX), scenes.bf16_round(p.FZ)
+    gterms = oracle.evaluate(p.X, p.Z, T, FX=FXo, FZ=FZo, **kw)["gscale"]
+    _close(got, ref, gterms)
+
+
+def test_noalloc_allocates_nothing_after_the_first_call():
+    """The promise of the entry point: once a first call has run on the
+    device (which, under lazy module loading, may load the library's device
+    code and its fixed array), a further call changes neither PyTorch's
+    allocated bytes nor the device's free memory."""
+    p = scenes.cube_pair(n=900, seed=78)
+    kw = dict(blocks=p.blocks, ell=0.1, cutoff_mult=0.0)
+    X, Z = torch.tensor(p.X, device="cuda"), torch.tensor(p.Z, device="cuda")
+    FX, FZ = torch.tensor(p.FX, device="cuda"), torch.tensor(p.FZ, device="cuda")
+    out = torch.zeros(ctypes.sizeof(cvo.Eval), dtype=torch.uint8, device="cuda")
+    params = cvo.make_params(**kw)
+    first = noalloc_eval(params, X, Z, FX, FZ, np.eye(4), out)
+    torch.cuda.synchronize()
+    alloc0 = torch.cuda.memory_allocated()
+    free0, _ = torch.cuda.mem_get_info()
+    second = noalloc_eval(params, X, Z, FX, FZ, np.eye(4), out)
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert second["F"] == first["F"] and np.array_equal(second["grad"], first["grad"])
+
+
+def test_invalid_feature_block_rejected_by_both_entry_points():
+    """A non-finite sigma or scale of a squared-exponential block is an
+    invalid argument for cvo_create and for the allocation-free entry alike
+    (not NaN results with CVO_OK)."""
+    X = torch.zeros((8, 3), device="cuda")
+    F = torch.zeros((8, 3), device="cuda")
+    for bad in ([("se", 3, 0.2, float("nan"))], [("se", 3, float("inf"), 1.0)]):
+        with pytest.raises(cvo.CvoError) as e:
+            cvo.CVO(blocks=bad, ell=0.1, cutoff_mult=0.0)
+        assert e.value.status == cvo.Status.ERR_INVALID_ARG
+        with pytest.raises(cvo.CvoError) as e:
+            noalloc_eval(cvo.make_params(blocks=bad, ell=0.1, cutoff_mult=0.0), X, X, F, F, np.eye(4))
+        assert e.value.status == cvo.Status.ERR_INVALID_ARG and "feature block" in str(e.value)
