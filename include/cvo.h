@@ -193,6 +193,15 @@ cvo_status cvo_evaluate(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
 cvo_status cvo_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], double dF,
                         float* dX, float* dFX, float* dZ, float* dFZ, double* dell, int outputs_on_device);
 
+/* Gradients of di * i_theta, the indicator of Eq. (indicator_actual)
+ * i_theta = F / sqrt(N M) at lengthscale params.ell, with respect to the
+ * same inputs as cvo_backward (and with its conventions for the outputs,
+ * their layout and the pair set): the paper proposes the indicator as a loss
+ * for learning (Sec. III-C, Sec. VI).  Equivalent to cvo_backward with
+ * dF = di / sqrt(N M); an empty cloud gives zero gradients. */
+cvo_status cvo_metric_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], double di,
+                               float* dX, float* dFX, float* dZ, float* dFZ, double* dell, int outputs_on_device);
+
 /* Registration (Problem 1): gradient ascent on SE(3) from T_init, one
  * line-Newton step along the gradient per iteration (t = |g|^2 / -F'' when
  * F'' < 0, else 1e-3 / |g|, clamped by max_step_rot / max_step_trans),
@@ -220,6 +229,45 @@ cvo_status cvo_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
  * summaries.  Returns the worst status (an error stops the sequence). */
 cvo_status cvo_register_sequence(cvo_handle h, int nframes, const cvo_cloud* frames, double ell_first,
                                  const double T_first[16], double* T_rel, double* T_abs, cvo_info* infos);
+
+/* X-row shards of one registration, for running a single pair on several
+ * GPUs.  The paper uses one GPU; this follows the data-parallel structure of
+ * Eq. (double_sum): F and its derivatives are sums over the rows x_i of X,
+ * so the rows can be split into disjoint shards, each swept against all of Z
+ * on its own GPU, and the per-iteration statistics added before the step.
+ *
+ * One handle per shard (on that shard's GPU), all created with the same
+ * parameters.  Each shard calls
+ *   cvo_shard_begin(h, X_rows, Z, n_total, T_init)   once: its rows of X, all
+ *       of Z, the number of rows of all shards together (n_total, the N of
+ *       the indicator i_theta = F / sqrt(N M), Eq. indicator_actual) and the
+ *       common start pose;
+ * then for each iteration
+ *   cvo_shard_sweep(h, stats)  queues the shard's sweep and writes
+ *       CVO_SHARD_STATS doubles to the DEVICE buffer stats on the handle's
+ *       stream: the 43 linear statistics of the per-point moments (about the
+ *       centre of Z's bounding box, which every shard computes alike), the
+ *       pair count and the candidate count;
+ *   (the caller sums stats over the shards, elementwise, e.g. an all-reduce
+ *       on the handle's stream, so that every shard holds the same sum);
+ *   cvo_shard_step(h, stats, done)  queues the step of cvo_register_pair
+ *       (step rule, SE(3) update, annealing, stopping test) from the summed
+ *       statistics; done (nullable, host): with a non-NULL pointer the call
+ *       waits for the step and sets *done = 1 once the registration has
+ *       stopped (later sweeps and steps then do nothing);
+ * and finally
+ *   cvo_shard_end(h, T_out, info)  the final pose and summary, as
+ *       cvo_register_pair returns them (the trace through cvo_get_trace).
+ * Every shard takes the same steps as long as the summed statistics are the
+ * same bits on every shard.  A shard needs at least one row of X and one
+ * point of Z, and max_iters >= 1.  The handle's stream orders the calls;
+ * stats must stay valid until the step that reads it has run. */
+#define CVO_SHARD_STATS 45
+cvo_status cvo_shard_begin(cvo_handle h, const cvo_cloud* X_rows, const cvo_cloud* Z, long long n_total,
+                           const double T_init[16]);
+cvo_status cvo_shard_sweep(cvo_handle h, double* stats_device);
+cvo_status cvo_shard_step(cvo_handle h, const double* stats_device, int* done);
+cvo_status cvo_shard_end(cvo_handle h, double T_out[16], cvo_info* info);
 
 /* Copies the per-iteration trace of the handle's last registration into out
  * (capacity cap iterations, CVO_TRACE_STRIDE doubles each: l, F, i_theta,
@@ -290,7 +338,8 @@ cvo_status cvo_set_loop(cvo_handle h, int mode);
  * each sweep launch (the loop is then queued from the host), average per
  * launch, and the number of launches; in the persistent mode events around
  * the one kernel, i.e. sweep and step together, per iteration, and the
- * number of iterations. */
+ * number of iterations.  After cvo_backward (or cvo_metric_backward): events
+ * around each gradient sweep (one per cloud whose gradients were asked for). */
 cvo_status cvo_set_timing(cvo_handle h, int on);
 cvo_status cvo_sweep_time(cvo_handle h, double* avg_ms, int* launches);
 
@@ -332,8 +381,12 @@ long long cvo_kernel_launches(void);
  * *out_device is valid once the stream has reached it.  Because the call does
  * not wait for the GPU, non-finite coordinates or features are reported as
  * NaN results, not as an error code.  The first call on each device looks up
- * the array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  Every call reuses the same
+ * the array's device address (cudaGetSymbolAddress) and the SM count with
+ * that device current; make that first call before any stream capture.
+ * Under CUDA's lazy module loading (the default), the library's device code
+ * and with it the array may be loaded on a device only at that first call, so
+ * the 4.5 MiB are committed then: make one call per device at start-up, while
+ * allocating is still allowed, and later calls commit nothing.  Every call reuses the same
  * array, which keeps the previous call's contents (each call rewrites all it
  * reads): calls that overlap on the GPU -- on two streams, or from two host
  * threads on one device -- race and must be serialised by the caller. */

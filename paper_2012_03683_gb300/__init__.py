@@ -26,14 +26,17 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["CVO", "cvo_create", "cvo_destroy", "cvo_set_params", "cvo_inner_product", "cvo_gradient", "cvo_metric",
-           "cvo_evaluate", "cvo_backward", "cvo_cosine", "CVOInnerProduct", "inner_product_fn", "metric_fn",
+           "cvo_evaluate", "cvo_backward", "cvo_metric_backward", "cvo_cosine", "CVOInnerProduct", "CVOMetric",
+           "inner_product_fn", "metric_fn",
            "cvo_register_pair", "cvo_register_batch", "cvo_register_sequence", "cvo_get_trace", "cvo_set_timing",
            "cvo_autotune", "cvo_get_tuning", "cvo_apply_tuning", "cvo_set_loop",
            "cvo_sweep_time", "cvo_last_error", "cvo_version", "cvo_kernel_launches", "load_library", "Status",
-           "CvoError"]
+           "CvoError", "cvo_shard_begin", "cvo_shard_sweep", "cvo_shard_step", "cvo_shard_end", "shard_rows",
+           "register_sharded", "SHARD_STATS"]
 
 MAX_BLOCKS = 4
 TRACE_STRIDE = 22
+SHARD_STATS = 45
 
 
 class Status:
@@ -116,8 +119,9 @@ def load_library(build_if_missing: bool = True):
     lib.cvo_gradient.argtypes = [vp, P(Cloud), P(Cloud), vp, vp, P(ctypes.c_double)]
     lib.cvo_evaluate.argtypes = [vp, P(Cloud), P(Cloud), vp, P(Eval)]
     lib.cvo_cosine.argtypes = [vp, P(Cloud), P(Cloud), vp, vp, P(ctypes.c_double), vp]
-    lib.cvo_backward.argtypes = [vp, P(Cloud), P(Cloud), vp, ctypes.c_double, vp, vp, vp, vp, P(ctypes.c_double),
-                                 ctypes.c_int]
+    for name in ("cvo_backward", "cvo_metric_backward"):
+        getattr(lib, name).argtypes = [vp, P(Cloud), P(Cloud), vp, ctypes.c_double, vp, vp, vp, vp,
+                                       P(ctypes.c_double), ctypes.c_int]
     lib.cvo_register_pair.argtypes = [vp, P(Cloud), P(Cloud), vp, vp, P(Info)]
     lib.cvo_register_batch.argtypes = [vp, ctypes.c_int, P(Cloud), P(Cloud), vp, vp, P(Info)]
     lib.cvo_get_trace.argtypes = [vp, vp, ctypes.c_int]
@@ -128,12 +132,18 @@ def load_library(build_if_missing: bool = True):
     lib.cvo_sweep_time.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int)]
     lib.cvo_autotune.argtypes = [vp, P(Cloud), P(Cloud), vp, P(Tuning)]
     lib.cvo_set_loop.argtypes = [vp, ctypes.c_int]
+    lib.cvo_shard_begin.argtypes = [vp, P(Cloud), P(Cloud), ctypes.c_longlong, vp]
+    lib.cvo_shard_sweep.argtypes = [vp, vp]
+    lib.cvo_shard_step.argtypes = [vp, vp, P(ctypes.c_int)]
+    lib.cvo_shard_end.argtypes = [vp, vp, P(Info)]
     lib.cvo_get_tuning.argtypes = [vp, P(Tuning)]
     lib.cvo_apply_tuning.argtypes = [vp, P(Tuning)]
     for name in ("cvo_create", "cvo_destroy", "cvo_set_params", "cvo_inner_product", "cvo_metric", "cvo_gradient",
-                 "cvo_evaluate", "cvo_backward", "cvo_cosine", "cvo_register_pair", "cvo_register_sequence",
+                 "cvo_evaluate", "cvo_backward", "cvo_metric_backward", "cvo_cosine", "cvo_register_pair",
+                 "cvo_register_sequence",
                  "cvo_register_batch", "cvo_get_trace", "cvo_set_timing", "cvo_sweep_time", "cvo_autotune",
-                 "cvo_get_tuning", "cvo_apply_tuning", "cvo_set_loop"):
+                 "cvo_get_tuning", "cvo_apply_tuning", "cvo_set_loop", "cvo_shard_begin", "cvo_shard_sweep",
+                 "cvo_shard_step", "cvo_shard_end"):
         getattr(lib, name).restype = ctypes.c_int
     lib.cvo_last_error.restype = ctypes.c_char_p
     lib.cvo_last_error.argtypes = []
@@ -302,6 +312,16 @@ def cvo_backward(h, X, Z, T, FX=None, FZ=None, dF=1.0, want=("dX", "dFX", "dZ", 
     lengthscale (see cvo_backward in cvo.h).  Outputs are float32 torch CUDA
     tensors when X is a CUDA tensor, numpy arrays otherwise; names not in
     `want` are neither computed nor returned."""
+    return _backward("cvo_backward", h, X, Z, T, FX, FZ, dF, want)
+
+
+def cvo_metric_backward(h, X, Z, T, FX=None, FZ=None, di=1.0, want=("dX", "dFX", "dZ", "dFZ", "dell")) -> dict:
+    """Gradients of di * i_theta (Eq. indicator_actual) with the outputs of
+    cvo_backward (see cvo_metric_backward in cvo.h)."""
+    return _backward("cvo_metric_backward", h, X, Z, T, FX, FZ, di, want)
+
+
+def _backward(entry, h, X, Z, T, FX, FZ, dF, want) -> dict:
     cx, cz, keep = _clouds(X, Z, FX, FZ)
     Tm = _pose(T)
     D = 0
@@ -326,8 +346,8 @@ def cvo_backward(h, X, Z, T, FX=None, FZ=None, dF=1.0, want=("dX", "dFX", "dZ", 
             out[name] = a
             ptrs.append(a.ctypes.data if a.size else None)
     dell = ctypes.c_double()
-    _check(load_library().cvo_backward(h, ctypes.byref(cx), ctypes.byref(cz), Tm.ctypes.data, float(dF), *ptrs,
-                                       ctypes.byref(dell) if "dell" in want else None, int(on_dev)))
+    _check(getattr(load_library(), entry)(h, ctypes.byref(cx), ctypes.byref(cz), Tm.ctypes.data, float(dF), *ptrs,
+                                          ctypes.byref(dell) if "dell" in want else None, int(on_dev)))
     if "dell" in want:
         out["dell"] = dell.value
     return out
@@ -416,6 +436,80 @@ def cvo_register_sequence(h, frames, ell_first, T_first=None):
     rc = _check(load_library().cvo_register_sequence(h, n, C, float(ell_first), None if T0 is None else T0.ctypes.data,
                                                      T_rel.ctypes.data, T_abs.ctypes.data, infos))
     return T_rel[: max(n - 1, 0)], T_abs[:n], [infos[k].as_dict() for k in range(max(n - 1, 0))], rc
+
+
+def cvo_shard_begin(h, X_rows, Z, n_total, T_init, FX_rows=None, FZ=None):
+    """Starts an X-row shard of one registration (see cvo_shard_begin in cvo.h)."""
+    cx, cz, keep = _clouds(X_rows, Z, FX_rows, FZ)
+    T0 = _pose(T_init)
+    return _check(load_library().cvo_shard_begin(h, ctypes.byref(cx), ctypes.byref(cz), int(n_total), T0.ctypes.data))
+
+
+def cvo_shard_sweep(h, stats):
+    """Queues the shard's sweep; stats: a float64 CUDA tensor of SHARD_STATS entries."""
+    return _check(load_library().cvo_shard_sweep(h, ctypes.c_void_p(_stats_ptr(stats))))
+
+
+def cvo_shard_step(h, stats, wait=False):
+    """Queues the step from the summed statistics; with wait=True returns
+    whether the registration has stopped (else None)."""
+    done = ctypes.c_int(0)
+    _check(load_library().cvo_shard_step(h, ctypes.c_void_p(_stats_ptr(stats)), ctypes.byref(done) if wait else None))
+    return bool(done.value) if wait else None
+
+
+def cvo_shard_end(h):
+    Tout = np.zeros((4, 4))
+    info = Info()
+    rc = _check(load_library().cvo_shard_end(h, Tout.ctypes.data, ctypes.byref(info)))
+    d = info.as_dict()
+    d["rc"] = rc
+    return Tout, d
+
+
+def _stats_ptr(stats):
+    torch = _torch()
+    if torch is None or not isinstance(stats, torch.Tensor) or not stats.is_cuda:
+        raise ValueError("stats must be a CUDA tensor")
+    if stats.dtype != torch.float64 or stats.numel() != SHARD_STATS or not stats.is_contiguous():
+        raise ValueError(f"stats must be a contiguous float64 tensor of {SHARD_STATS} entries")
+    return stats.data_ptr()
+
+
+def shard_rows(n, world, rank):
+    """The rows [lo, hi) of an n-point cloud that shard `rank` of `world`
+    holds: contiguous, disjoint, covering every row once, sizes differing by
+    at most one."""
+    if world < 1 or not 0 <= rank < world or n < 0:
+        raise ValueError("need world >= 1, 0 <= rank < world and n >= 0")
+    base, extra = divmod(n, world)
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
+def register_sharded(h, X_rows, Z, n_total, T_init, FX_rows=None, FZ=None, allreduce=None, *, max_iters,
+                     check_every=8, stats=None):
+    """Registers one pair whose X is split by rows over shards: this
+    process holds the rows X_rows (of n_total) and all of Z.  Every
+    iteration the shard's statistics go through allreduce (a callable that
+    sums a float64 CUDA tensor over the shards in place, on the current
+    stream, e.g. torch.distributed.all_reduce; None: this is the only
+    shard), then the step, for at most max_iters iterations (the handle's
+    params.max_iters).  Whether the registration has stopped is read every
+    check_every iterations.  stats: the float64 CUDA tensor of SHARD_STATS
+    entries to use (None: one is made).  Returns (T_out, info)."""
+    torch = _torch()
+    cvo_shard_begin(h, X_rows, Z, n_total, T_init, FX_rows, FZ)
+    if stats is None:
+        stats = torch.zeros(SHARD_STATS, dtype=torch.float64, device="cuda")
+    for it in range(int(max_iters)):
+        cvo_shard_sweep(h, stats)
+        if allreduce is not None:
+            allreduce(stats)
+        wait = (it + 1) % check_every == 0
+        if cvo_shard_step(h, stats, wait=wait):
+            break
+    return cvo_shard_end(h)
 
 
 def cvo_get_trace(h, cap=100000) -> np.ndarray:
@@ -523,6 +617,10 @@ class CVO:
     def register_sequence(self, frames, ell_first, T_first=None):
         return cvo_register_sequence(self.h, frames, ell_first, T_first)
 
+    def register_sharded(self, X_rows, Z, n_total, T_init=None, FX_rows=None, FZ=None, allreduce=None):
+        return register_sharded(self.h, X_rows, Z, n_total, np.eye(4) if T_init is None else T_init, FX_rows, FZ,
+                                allreduce, max_iters=self.params.max_iters)
+
     def trace(self):
         return cvo_get_trace(self.h)
 
@@ -541,14 +639,17 @@ class CVO:
 
 # ---- differentiable form ---------------------------------------------------------
 
-def _autograd_function():
+def _autograd_function(value_entry, grad_entry):
+    """A torch.autograd.Function of a scalar of the double sum: value_entry
+    computes it (cvo_inner_product or cvo_metric) and grad_entry its input
+    gradients (cvo_backward or cvo_metric_backward), both in the library."""
     torch = _torch()
     if torch is None:  # pragma: no cover
         raise RuntimeError("the differentiable form needs PyTorch")
 
-    class _InnerProduct(torch.autograd.Function):
-        """F(T) of Eq. (double_sum) as a function of X, Z, their features and
-        the lengthscale; the backward pass runs the library's gradient sweeps.
+    class _Fn(torch.autograd.Function):
+        """The scalar as a function of X, Z, their features and the
+        lengthscale; the backward pass runs the library's gradient sweeps.
         T is a constant here: the pose gradient is cvo_gradient's se(3)
         vector."""
 
@@ -560,7 +661,7 @@ def _autograd_function():
             p.ell = ell_v
             cvo_set_params(cvo.h, p)
             try:
-                F = cvo_inner_product(cvo.h, X, Z, T, FX, FZ)
+                v = value_entry(cvo.h, X, Z, T, FX, FZ)
             finally:
                 cvo_set_params(cvo.h, params)
             ctx.cvo = cvo
@@ -569,7 +670,7 @@ def _autograd_function():
             ctx.save_for_backward(X, Z, FX, FZ)
             ctx.ell_meta = (ell.dtype, ell.device) if isinstance(ell, torch.Tensor) else None
             dev = X.device if isinstance(X, torch.Tensor) else "cpu"
-            return torch.tensor(F, dtype=torch.float64, device=dev)
+            return torch.tensor(v, dtype=torch.float64, device=dev)
 
         @staticmethod
         def backward(ctx, gF):
@@ -586,7 +687,7 @@ def _autograd_function():
             p.ell = ctx.ell
             cvo_set_params(cvo.h, p)
             try:
-                out = cvo_backward(cvo.h, X, Z, ctx.T, FX, FZ, dF=float(gF), want=tuple(want))
+                out = grad_entry(cvo.h, X, Z, ctx.T, FX, FZ, float(gF), tuple(want))
             finally:
                 cvo_set_params(cvo.h, params)
 
@@ -604,7 +705,7 @@ def _autograd_function():
             return (as_grad("dX", X), as_grad("dZ", Z), as_grad("dFX", FX) if FX is not None else None,
                     as_grad("dFZ", FZ) if FZ is not None else None, dell, None, None)
 
-    return _InnerProduct
+    return _Fn
 
 
 _fn_cache = {}
@@ -613,9 +714,18 @@ _fn_cache = {}
 def CVOInnerProduct():
     """The torch.autograd.Function class of the differentiable F (built on
     first use so that importing this package does not need PyTorch)."""
-    if "f" not in _fn_cache:
-        _fn_cache["f"] = _autograd_function()
-    return _fn_cache["f"]
+    if "F" not in _fn_cache:
+        _fn_cache["F"] = _autograd_function(cvo_inner_product, cvo_backward)
+    return _fn_cache["F"]
+
+
+def CVOMetric():
+    """The torch.autograd.Function class of the differentiable indicator of
+    Eq. (indicator_actual) (value from cvo_metric, gradients from
+    cvo_metric_backward)."""
+    if "metric" not in _fn_cache:
+        _fn_cache["metric"] = _autograd_function(cvo_metric, cvo_metric_backward)
+    return _fn_cache["metric"]
 
 
 def inner_product_fn(cvo: "CVO", X, Z, T, FX=None, FZ=None, ell=None):
@@ -626,7 +736,6 @@ def inner_product_fn(cvo: "CVO", X, Z, T, FX=None, FZ=None, ell=None):
 
 
 def metric_fn(cvo: "CVO", X, Z, T, FX=None, FZ=None, ell=None):
-    """Differentiable indicator i_theta = F / sqrt(N M) of Eq. (indicator_actual)."""
-    n, m = int(X.shape[0]), int(Z.shape[0])
-    F = inner_product_fn(cvo, X, Z, T, FX, FZ, ell)
-    return F / float(np.sqrt(n * m)) if n and m else F * 0.0
+    """Differentiable indicator i_theta of Eq. (indicator_actual), with the
+    arguments of inner_product_fn."""
+    return CVOMetric().apply(X, Z, FX, FZ, ell, T, cvo)

@@ -20,6 +20,7 @@
 using namespace cvo;
 
 std::atomic<long long> cvo::g_launch_count{0};
+static_assert(CVO_SHARD_STATS == cvo::kShardStats, "shard statistics: header and kernels disagree");
 
 namespace cvo {
 void set_error_message(const char* msg);
@@ -179,6 +180,11 @@ struct cvo_handle_s {
     // of about chunk_len candidates (work items), so up to stream / chunk_len
     // lanes of different warps serve one query
     int chunk_len = kChunkLen;
+    // an X-row shard registration in progress (cvo_shard_begin .. cvo_shard_end)
+    int shard_active = 0;
+    int shard_nb = 0;
+    SweepArgs shard_a{};
+    LevelDesc* shard_levels = nullptr;   // non-NULL: the items are re-planned beside every step
 };
 
 namespace {
@@ -1282,6 +1288,42 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
     return worst;
 }
 
+// X-row shard of one registration (the multi-GPU design of partitioning X
+// by rows; the paper uses one GPU): this handle holds rows of X and all of
+// Z, and its sweeps' statistics are summed with the other shards' before
+// every step, so every shard takes the same step.  The set-up is that of
+// run_register, with the indicator normalised by the whole cloud's size.
+cvo_status run_shard_begin(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, long long n_total, const double* T_init)
+{
+    const cvo_params& p = h->p;
+    h->shard_active = 0;
+    h->last_iters = 0;
+    CVO_TRY(begin_call(h, rec_bf16_of(p, X, Z), 1));
+    PairRes& P = h->pr[0];
+    CVO_TRY(prepare(h, P, X, Z, p.ell, reachable_ell_lo(p)));
+    CVO_TRY(init_state(h, P, 0, T_init, p.ell, 1, h->dense ? kPlanned : kUniform));
+    // i_theta = F / sqrt(N M) with N the rows of every shard (Eq. indicator_actual)
+    IterState* dst = (IterState*)P.state.p;
+    h->h_state->norm = 1.0 / std::sqrt((double)n_total * (double)P.m);
+    CVO_CUDA(cudaMemcpyAsync(&dst->norm, &h->h_state->norm, sizeof(double), cudaMemcpyHostToDevice, h->s));
+    CVO_CUDA(ensure(h->trace, (size_t)std::max(p.max_iters, 1) * CVO_TRACE_STRIDE * sizeof(double)));
+    const bool replan = !h->dense;
+    const int nb = replan ? h->num_sms * kSweepBlocksPerSm : single_pair_blocks(h, P);
+    SweepArgs a{};
+    CVO_TRY(setup_sweep(h, std::vector<PairDesc>{pair_desc(P, 0, nb)}, nb, &a, true));
+    int max_groups = 1;
+    for (int k = 0; k < P.nlevels; ++k) max_groups = std::max(max_groups, P.lv[k].ngroups);
+    CVO_CUDA(ensure(h->gidx, (size_t)std::max(max_groups, P.n) * sizeof(unsigned)));
+    a.nch_next = replan ? (unsigned*)h->gidx.p : nullptr;
+    a.chunk_len = h->chunk_len;
+    h->shard_a = a;
+    h->shard_nb = nb;
+    h->shard_levels = replan ? (LevelDesc*)P.levels_dev.p : nullptr;
+    CVO_CUDA(cudaStreamSynchronize(h->s));
+    h->shard_active = 1;
+    return CVO_OK;
+}
+
 // Gradients of F(T) with respect to both clouds' points and features and to
 // the lengthscale: one gradient sweep per cloud, each with that cloud as the
 // queries over a grid of the other (no atomics, so the result is
@@ -1351,9 +1393,21 @@ cvo_status run_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
         CVO_CUDA(ensure(h->bw_part, (size_t)std::max(nitems, 1) * 32 * (4 + D) * sizeof(float)));
         g.part = (float*)h->bw_part.p;
         const int nb = std::max(1, std::min((nitems + kSweepWarps - 1) / kSweepWarps, h->num_sms * 2 * kSweepBlocksPerSm));
+        const int ev = h->timing ? 2 * h->sweep_n : -1;   // events around each gradient sweep when timing
+        if (ev >= 0) CVO_CUDA(cudaEventRecord(h->evs[ev], h->s));
         CVO_CUDA(launch_grad(g, nb, h->s));
+        if (ev >= 0) {
+            CVO_CUDA(cudaEventRecord(h->evs[ev + 1], h->s));
+            ++h->sweep_n;
+        }
         return CVO_OK;
     };
+    h->sweep_ms = 0.0;
+    h->sweep_n = 0;
+    if (h->timing) {
+        ensure_events(h, 2);
+        if (h->evs.size() < 4) return fail(CVO_ERR_CUDA, "cudaEventCreate failed");
+    }
     if (dev[0] || dev[1] || dell) {
         float* tq = nullptr;
         if (dell) {
@@ -1383,6 +1437,7 @@ cvo_status run_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
         for (int k = 0; k < 4; ++k)
             if (dev[k]) CVO_CUDA(cudaMemcpyAsync(outs[k], dev[k], bytes[k], cudaMemcpyDeviceToHost, h->s));
     CVO_CUDA(cudaStreamSynchronize(h->s));
+    if (h->timing) h->sweep_ms = sum_sweep_events(h, h->sweep_n);
     return CVO_OK;
 }
 
@@ -1608,6 +1663,19 @@ cvo_status cvo_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     return run_backward(h, X, Z, T, dF, dX, dFX, dZ, dFZ, dell, outputs_on_device ? 1 : 0);
 }
 
+cvo_status cvo_metric_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], double di,
+                               float* dX, float* dFX, float* dZ, float* dFZ, double* dell, int outputs_on_device)
+{
+    g_err.clear();
+    if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
+    if (!std::isfinite(di)) return fail(CVO_ERR_INVALID_ARG, "di must be finite");
+    if (!X || !Z) return fail(CVO_ERR_INVALID_ARG, "X or Z is NULL");
+    // i_theta = F / sqrt(N M) (Eq. indicator_actual): the upstream gradient of
+    // F is di / sqrt(N M); an empty cloud has i_theta = 0 and zero gradients
+    const double norm = (X->n > 0 && Z->n > 0) ? 1.0 / std::sqrt((double)X->n * (double)Z->n) : 0.0;
+    return cvo_backward(h, X, Z, T, di * norm, dX, dFX, dZ, dFZ, dell, outputs_on_device);
+}
+
 cvo_status cvo_cosine(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16],
                       const double* norms2_in, double* cos_theta, double* norms2_out)
 {
@@ -1753,6 +1821,72 @@ cvo_status cvo_register_sequence(cvo_handle h, int nframes, const cvo_cloud* fra
         }
     }
     return worst;
+}
+
+cvo_status cvo_shard_begin(cvo_handle h, const cvo_cloud* X_rows, const cvo_cloud* Z, long long n_total,
+                           const double T_init[16])
+{
+    g_err.clear();
+    if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
+    const int D = feat_dim(h->p);
+    CVO_TRY(check_cloud(X_rows, "X_rows", D));
+    CVO_TRY(check_cloud(Z, "Z", D));
+    CVO_TRY(check_pose(T_init, "T_init"));
+    if (X_rows->n < 1 || Z->n < 1) return fail(CVO_ERR_INVALID_ARG, "a shard needs at least one row of X and one point of Z");
+    if (n_total < X_rows->n) return fail(CVO_ERR_INVALID_ARG, "n_total (%lld) < the shard's rows (%d)", n_total, X_rows->n);
+    if (h->p.max_iters < 1) return fail(CVO_ERR_INVALID_ARG, "max_iters must be >= 1 for a shard registration");
+    DeviceGuard g(h->device);
+    return run_shard_begin(h, X_rows, Z, n_total, T_init);
+}
+
+cvo_status cvo_shard_sweep(cvo_handle h, double* stats_device)
+{
+    g_err.clear();
+    if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
+    if (!stats_device) return fail(CVO_ERR_INVALID_ARG, "stats_device is NULL");
+    if (!h->shard_active) return fail(CVO_ERR_INVALID_ARG, "no shard registration in progress (cvo_shard_begin)");
+    DeviceGuard g(h->device);
+    const SweepArgs& a = h->shard_a;
+    CVO_CUDA(launch_sweep(a, h->shard_nb, h->s));
+    if (h->shard_levels) CVO_CUDA(launch_layout(h->shard_levels, a.swept_level, a.nch_next, h->s));
+    CVO_CUDA(launch_stats_out(a.grp_stats, a.grp_cnt, h->shard_nb, stats_device, h->s));
+    return CVO_OK;
+}
+
+cvo_status cvo_shard_step(cvo_handle h, const double* stats_device, int* done)
+{
+    g_err.clear();
+    if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
+    if (!stats_device) return fail(CVO_ERR_INVALID_ARG, "stats_device is NULL");
+    if (!h->shard_active) return fail(CVO_ERR_INVALID_ARG, "no shard registration in progress (cvo_shard_begin)");
+    DeviceGuard g(h->device);
+    IterState* dst = (IterState*)h->pr[0].state.p;
+    CVO_CUDA(launch_finalize_stats(dst, stats_device, (double*)h->trace.p, h->s));
+    if (done) {
+        CVO_CUDA(cudaMemcpyAsync(&h->h_state->done, &dst->done, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+        CVO_CUDA(cudaStreamSynchronize(h->s));
+        *done = h->h_state->done ? 1 : 0;
+    }
+    return CVO_OK;
+}
+
+cvo_status cvo_shard_end(cvo_handle h, double T_out[16], cvo_info* info)
+{
+    g_err.clear();
+    if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
+    if (!T_out) return fail(CVO_ERR_INVALID_ARG, "T_out is NULL");
+    if (!h->shard_active) return fail(CVO_ERR_INVALID_ARG, "no shard registration in progress (cvo_shard_begin)");
+    DeviceGuard g(h->device);
+    h->shard_active = 0;
+    CVO_TRY(fetch_states(h, 1));
+    const IterState* st = h->h_state;
+    std::memcpy(T_out, st->T, 16 * sizeof(double));
+    cvo_info inf;
+    std::memset(&inf, 0, sizeof(inf));
+    fill_info(st, &inf);
+    h->last_iters = st->iter;
+    if (info) *info = inf;
+    return (cvo_status)inf.status;
 }
 
 int cvo_get_trace(cvo_handle h, double* out, int cap)

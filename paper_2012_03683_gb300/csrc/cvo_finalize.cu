@@ -37,22 +37,16 @@ __global__ void k_init_state(IterState* st)
     update_derived(st);
 }
 
-__global__ void __launch_bounds__(kStepThreads)
-k_finalize(IterState* st, const float2* __restrict__ gs, const unsigned long long* __restrict__ gc_, int ngroups,
-           double* trace, cudaGraphConditionalHandle cond, int use_cond)
+// The 43 statistics and the two counts of a sweep from its group sums, by a
+// block of kStepThreads threads: statistic k by warp k % warps, each lane
+// adding every 32nd group sum in group order (all its loads first), then the
+// lanes' sums combined by a butterfly (lane 0's result is kept); fixed
+// order, so deterministic.  S as doubles, Shi / Slo as double-float pairs.
+__device__ void reduce_group_sums(const float2* __restrict__ gs, const unsigned long long* __restrict__ gc_,
+                                  int ngroups, double* S, float* Shi, float* Slo, unsigned long long* cs)
 {
-    static_assert(sizeof(IterState) % 8 == 0, "state is copied in 8-byte words");
-    constexpr int kWords = (int)(sizeof(IterState) / 8);
     constexpr int kWarps = kStepThreads / 32;
-    __shared__ double S[kStatN];
-    __shared__ float Shi[kStatN], Slo[kStatN];
-    __shared__ unsigned long long cs[2];
-    __shared__ unsigned long long sbuf[kWords];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < kWords; i += kStepThreads) sbuf[i] = reinterpret_cast<const unsigned long long*>(st)[i];
-    // statistic k by warp k % kWarps: each lane adds every 32nd group sum in
-    // group order (all its loads first), then the lanes' sums are combined by
-    // a butterfly (lane 0's result is kept); fixed order, so deterministic
     constexpr int kPerLane = kMaxGroups / 32;
     for (int k = warp; k < kStatN; k += kWarps) {
         const float2* row = gs + (size_t)k * kMaxGroups;
@@ -82,7 +76,16 @@ k_finalize(IterState* st, const float2* __restrict__ gs, const unsigned long lon
             if (lane == 0) cs[c] = t;
         }
     }
-    __syncthreads();
+}
+
+// The step on the block's shared copy of the state (sbuf), from the summed
+// statistics, then the state written back.  Called by all kStepThreads
+// threads after the statistics are in shared memory.
+__device__ void finalize_tail(IterState* st, unsigned long long* sbuf, const double* S, const float* Shi,
+                              const float* Slo, const unsigned long long* cs, double* trace,
+                              cudaGraphConditionalHandle cond, int use_cond)
+{
+    constexpr int kWords = (int)(sizeof(IterState) / 8);
     IterState* sst = reinterpret_cast<IterState*>(sbuf);
     if (sst->done) {   // the sweep did nothing; inside a graph's loop: stop it
         if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
@@ -96,6 +99,59 @@ k_finalize(IterState* st, const float2* __restrict__ gs, const unsigned long lon
     __syncthreads();
     for (int i = threadIdx.x; i < kWords; i += kStepThreads) reinterpret_cast<unsigned long long*>(st)[i] = sbuf[i];
     if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, sst->done ? 0u : 1u);
+}
+
+__global__ void __launch_bounds__(kStepThreads)
+k_finalize(IterState* st, const float2* __restrict__ gs, const unsigned long long* __restrict__ gc_, int ngroups,
+           double* trace, cudaGraphConditionalHandle cond, int use_cond)
+{
+    static_assert(sizeof(IterState) % 8 == 0, "state is copied in 8-byte words");
+    constexpr int kWords = (int)(sizeof(IterState) / 8);
+    __shared__ double S[kStatN];
+    __shared__ float Shi[kStatN], Slo[kStatN];
+    __shared__ unsigned long long cs[2];
+    __shared__ unsigned long long sbuf[kWords];
+    for (int i = threadIdx.x; i < kWords; i += kStepThreads) sbuf[i] = reinterpret_cast<const unsigned long long*>(st)[i];
+    reduce_group_sums(gs, gc_, ngroups, S, Shi, Slo, cs);
+    __syncthreads();
+    finalize_tail(st, sbuf, S, Shi, Slo, cs, trace, cond, use_cond);
+}
+
+// A shard's sweep statistics as kShardStats doubles: the 43 statistics, the
+// pair count and the candidate count (the counts are exact in a double up to
+// 2^53).  Summed over the shards of one registration, they are what one
+// sweep over all of X would give, up to rounding.
+__global__ void __launch_bounds__(kStepThreads)
+k_stats_out(const float2* __restrict__ gs, const unsigned long long* __restrict__ gc_, int ngroups, double* out)
+{
+    __shared__ double S[kStatN];
+    __shared__ float Shi[kStatN], Slo[kStatN];
+    __shared__ unsigned long long cs[2];
+    reduce_group_sums(gs, gc_, ngroups, S, Shi, Slo, cs);
+    __syncthreads();
+    if (threadIdx.x < kStatN) out[threadIdx.x] = S[threadIdx.x];
+    else if (threadIdx.x < kStatN + 2) out[threadIdx.x] = (double)cs[threadIdx.x - kStatN];
+}
+
+// The step from statistics summed over the shards of a registration (the
+// output of k_stats_out added over the shards): the same step as k_finalize.
+__global__ void __launch_bounds__(kStepThreads) k_finalize_stats(IterState* st, const double* __restrict__ in, double* trace)
+{
+    constexpr int kWords = (int)(sizeof(IterState) / 8);
+    __shared__ double S[kStatN];
+    __shared__ float Shi[kStatN], Slo[kStatN];
+    __shared__ unsigned long long cs[2];
+    __shared__ unsigned long long sbuf[kWords];
+    for (int i = threadIdx.x; i < kWords; i += kStepThreads) sbuf[i] = reinterpret_cast<const unsigned long long*>(st)[i];
+    if (threadIdx.x < kStatN) {
+        const double v = in[threadIdx.x];
+        S[threadIdx.x] = v;
+        split_df(v, Shi[threadIdx.x], Slo[threadIdx.x]);
+    } else if (threadIdx.x < kStatN + 2) {
+        cs[threadIdx.x - kStatN] = (unsigned long long)in[threadIdx.x];
+    }
+    __syncthreads();
+    finalize_tail(st, sbuf, S, Shi, Slo, cs, trace, cudaGraphConditionalHandle{}, 0);
 }
 
 __global__ void __launch_bounds__(kFinalizeThreads)
@@ -177,6 +233,22 @@ cudaError_t launch_init_state(IterState* st, cudaStream_t s)
 {
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
     k_init_state<<<1, 1, 0, s>>>(st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats_out(const float2* grp_stats, const unsigned long long* grp_cnt, int nblocks, double* out,
+                             cudaStream_t s)
+{
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    const int ngroups = (nblocks + kGroupBlocks - 1) / kGroupBlocks;
+    k_stats_out<<<1, kStepThreads, 0, s>>>(grp_stats, grp_cnt, ngroups, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_stats(IterState* st, const double* stats, double* trace, cudaStream_t s)
+{
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    k_finalize_stats<<<1, kStepThreads, 0, s>>>(st, stats, trace);
     return cudaGetLastError();
 }
 

@@ -190,6 +190,13 @@ cudaError_t launch_init_state(IterState* st, cudaStream_t s);
 // Reduces the ceil(nblocks / kGroupBlocks) group sums of a sweep and takes the step.
 cudaError_t launch_finalize(IterState* st, const float2* grp_stats, const unsigned long long* grp_cnt, int nblocks,
                             double* trace, cudaStream_t s);
+// X-row shards of one registration: the statistics of a sweep as
+// kShardStats doubles (43 statistics, pair count, candidate count), and the
+// step from such statistics summed over the shards.
+constexpr int kShardStats = kStatN + 2;
+cudaError_t launch_stats_out(const float2* grp_stats, const unsigned long long* grp_cnt, int nblocks, double* out,
+                             cudaStream_t s);
+cudaError_t launch_finalize_stats(IterState* st, const double* stats, double* trace, cudaStream_t s);
 // Lays out the swept level's work items for the next sweep from the chunk
 // counts the sweep recorded (registration with a cutoff; one block, run
 // beside the step).  k_layout(LevelDesc* levels, const int* swept_level,

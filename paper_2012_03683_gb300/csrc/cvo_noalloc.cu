@@ -46,7 +46,8 @@ namespace {
 constexpr int kNoAllocMaxPoints = 16384;
 constexpr int kNoAllocMaxRec = 7;                          // float4 per record
 constexpr int kNoAllocMaxFeat = (kNoAllocMaxRec - 1) * 4;  // float32 feature entries
-constexpr int kNoAllocBlocks = 1216;                       // sweep blocks (8 per SM on 152 SMs)
+constexpr int kNoAllocBlocks = 1216;                       // most sweep blocks (partial sums in the array); a
+                                                           // launch takes at most kSweepBlocksPerSm per SM
 constexpr int kMaxDevices = 64;
 constexpr int kNoAllocMaxChunks = 16;                      // work items per query group
 
@@ -79,6 +80,7 @@ namespace {
 
 std::mutex g_addr_mu;
 unsigned char* g_addr[kMaxDevices] = {};
+int g_sms[kMaxDevices] = {};
 
 cvo_status na_fail(cvo_status s, const char* msg)
 {
@@ -87,8 +89,8 @@ cvo_status na_fail(cvo_status s, const char* msg)
 }
 
 // Device address of the scratch array on the current device, looked up once
-// per device with that device current.
-cvo_status scratch_address(unsigned char** out)
+// per device with that device current, and the device's SM count.
+cvo_status scratch_address(unsigned char** out, int* sms)
 {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -104,9 +106,16 @@ cvo_status scratch_address(unsigned char** out)
             cudaGetLastError();
             return na_fail(CVO_ERR_CUDA, "cvo_evaluate_dense_noalloc: cudaGetSymbolAddress of the scratch array failed");
         }
+        int count = 0;
+        if (cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || count <= 0) {
+            cudaGetLastError();
+            return na_fail(CVO_ERR_CUDA, "cvo_evaluate_dense_noalloc: cannot read the device's SM count");
+        }
+        g_sms[dev] = count;
         g_addr[dev] = (unsigned char*)p;
     }
     *out = g_addr[dev];
+    *sms = g_sms[dev];
     return CVO_OK;
 }
 
@@ -235,9 +244,13 @@ extern "C" cvo_status cvo_evaluate_dense_noalloc(const cvo_params* p, void* cuda
     int D = 0;
     for (int b = 0; b < p->n_blocks; ++b) {
         const cvo_feat_block& fb = p->blocks[b];
+        // the checks of cvo_create: a squared-exponential block needs a finite
+        // scale > 0 and a finite sigma
         if (fb.dim < 1 || (fb.kind != CVO_FEAT_SE && fb.kind != CVO_FEAT_DOT) ||
-            (fb.kind == CVO_FEAT_SE && !(fb.scale > 0.0)))
-            return na_fail(CVO_ERR_INVALID_ARG, "cvo_evaluate_dense_noalloc: invalid feature block");
+            (fb.kind == CVO_FEAT_SE && (!(fb.scale > 0.0) || !std::isfinite(fb.scale) || !std::isfinite(fb.sigma))))
+            return na_fail(CVO_ERR_INVALID_ARG,
+                           "cvo_evaluate_dense_noalloc: invalid feature block (dim >= 1, a known kind; "
+                           "squared exponential: scale > 0 and sigma finite)");
         fc.dim[b] = fb.dim;
         fc.kind[b] = fb.kind;
         fc.off[b] = D;
@@ -277,8 +290,9 @@ extern "C" cvo_status cvo_evaluate_dense_noalloc(const cvo_params* p, void* cuda
         if (s != CVO_OK) return s;
     }
     unsigned char* base = nullptr;
+    int sms = 0;
     {
-        const cvo_status s = scratch_address(&base);
+        const cvo_status s = scratch_address(&base, &sms);
         if (s != CVO_OK) return s;
     }
     cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -328,7 +342,8 @@ extern "C" cvo_status cvo_evaluate_dense_noalloc(const cvo_params* p, void* cuda
     ld.items = items;
     ld.nitems = ld.ngroups * nch;
 
-    const int nblocks = std::max(1, std::min((ld.nitems + kSweepWarps - 1) / kSweepWarps, kNoAllocBlocks));
+    const int nblocks = std::max(1, std::min({(ld.nitems + kSweepWarps - 1) / kSweepWarps, kNoAllocBlocks,
+                                              sms * kSweepBlocksPerSm}));
     PairDesc pd;
     pd.levels = lv;
     pd.xrec = xrec;
