@@ -1,23 +1,35 @@
-"""Benchmark: registrations of the stereo-like street pair on GB300.
+"""Benchmark: batched registration of 64 frame pairs against the plain
+single-pair form, on GB300.
 
-One step = one full registration (cvo_register_pair) of the 20,000-point
-street pair: grid and query setup, then up to 100 annealed iterations of the
-fused sweep + on-device step (lengthscale 0.3 -> 0.05 m, cutoff 3
-lengthscales, RGB + 19-class labels).  Inputs are resident in HBM when the
-timed region starts; L2 is flushed (256 MB write) between steps.
+Headline workload (batch-64): 64 cube pairs, 5,000-60,000 points per cloud,
+RGB (squared exponential, scale 0.2) x 19-class labels (inner product), both
+stored in bfloat16 with float32 arithmetic, lengthscale 0.1 m, cutoff 3
+lengthscales, <= 50 iterations, per-pair convergence masks.  One step = one
+batched registration of all 64 pairs (cvo_register_batch: every pair's
+setup, then one CUDA graph whose loop runs the batched sweep and the
+per-pair steps until every pair has stopped).  Inputs are resident in HBM
+when the timed region starts; L2 is flushed (256 MB write) before every
+step; steps are timed with CUDA events on the launching stream.
 
-value  = in-cutoff kernel-pair evaluations per second, summed over ranks
-e2e    = the same metric through the C ABI with pinned host buffers (host to
-         device copies inside the timed region)
-roofline = the sweep kernel's algorithmic FP32 FLOPs per launch over its
-         event-timed duration, against the FP32 peak from the unit counts;
-         with the DRAM traffic and the warp-instruction issue rate of the
-         committed ncu capture when it was taken on the current source
-sections = batch (64 cube pairs batched vs one by one), backward (room pair),
-         large (200,000-point pair), tuning (the autotuner's choice, timed
-         registrations; untimed here)
-cpu_baseline = the FP64 oracle's own registration loop on the same pair,
-         first 20 iterations, on the host cores
+value     = in-cutoff kernel-pair evaluations per second of the batched form,
+            summed over ranks (replicas: each rank registers its own batch)
+registered_pairs_per_s = completed registrations per second, batched
+plain     = the same 64 pairs through cvo_register_pair one after another
+            (CUDA events around each pass over the 64), and the speedup
+e2e       = the batched form through the C ABI with pinned host buffers
+            (host to device copies of every pair inside the timed region)
+roofline  = the batched sweep kernel (k_sweep, bfloat16 label tile on the
+            tensor cores): algorithmic FP32 FLOPs of its in-cutoff pairs over
+            its CUDA-event time per launch (the loop queued from the host),
+            against the FP32 peak from the unit counts; DRAM traffic and warp
+            instructions from the committed ncu summary when it was taken on
+            the current kernel source
+sections  = street (street-20k single pair), cube (the dense 2,000-point
+            pair), backward (room-19k gradients), large (box80-200k), shard
+            (box80-200k with X's rows split over the ranks, one NCCL all-reduce
+            of the sweep statistics per iteration; N > 1)
+cpu_baseline = the FP64 oracle on 8 seeded pairs of the batch (the first
+            iteration of each registration), on the host cores
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cvo|reference]
 """
@@ -38,20 +50,36 @@ sys.path.insert(0, ROOT)
 
 METRIC = "kernel-pair evals/s & registered pairs/s, batched vs plain GPU, at oracle tol"
 UNIT = "pair-evals/s"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 EX2_PER_CLK_SM = 29   # measured ex2.approx.f32 throughput per SM per clock on a GB300
+ISSUE_PER_CLK_SM = 4  # warp instructions per SM per clock (4 schedulers)
+CPU_SAMPLE_PAIRS = 8
+CSRC = os.path.join(ROOT, "paper_2012_03683_gb300", "csrc")
+SWEEP_SRC = [os.path.join(CSRC, "cvo_sweep.cu"), os.path.join(CSRC, "cvo_sweep_dev.cuh")]
 
 
 def flops_per_pair(blocks):
-    """Algorithmic FP32 FLOPs of one in-cutoff pair (FMA = 2): offset 3,
-    squared distance 5, exponent scale 1, moments W/E/Q 19; a squared-
-    exponential block of d entries 3d + 1; an inner-product block of d
+    """Algorithmic FP32 FLOPs of one in-cutoff pair in the sweep (FMA = 2):
+    offset 3, squared distance 5, exponent scale 1, moments W/E/Q 19; a
+    squared-exponential block of d entries 3d + 1; an inner-product block of d
     entries 2d - 1 plus the product with the kernel value 1.  The ex2 runs on
     the XU pipe and is not counted."""
     f = 3 + 5 + 1 + 19
     for kind, dim, _, _ in blocks:
         f += 3 * dim + 1 if kind == "se" else 2 * dim
+    return f
+
+
+def grad_flops_per_pair(blocks):
+    """Algorithmic FP32 FLOPs of one in-cutoff pair in the gradient sweep:
+    offset 3, squared distance 5, exponent scale 1, weight product 1, the
+    accumulators sum w e (3 FMA) and sum w d^2 (1 FMA) 8; a squared-
+    exponential block of d entries 3d + 1 for its exponent and 3d for its
+    accumulator (difference, FMA); an inner-product block 2d for its product
+    and 2d for its accumulator."""
+    f = 3 + 5 + 1 + 1 + 8
+    for kind, dim, _, _ in blocks:
+        f += (3 * dim + 1 + 3 * dim) if kind == "se" else 4 * dim
     return f
 
 
@@ -63,17 +91,17 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def profile_value(kernel_src, key):
-    """A per-launch figure of the sweep (key: traffic_bytes_per_launch,
-    warp_instructions_per_launch) from the committed ncu summary, if it was
-    taken on the current kernel source (the files in kernel_src, hashed in
-    order); else None."""
-    path = os.path.join(ROOT, "profiles", "sweep_street-20k.md")
+def profile_value(kernel_src, key, profile="sweep_batch-64.md"):
+    """A per-launch figure (key: traffic_bytes_per_launch,
+    warp_instructions_per_launch, ...) from a committed ncu summary under
+    profiles/, if it was taken on the current kernel source (the files in
+    kernel_src, hashed in order); else None."""
+    path = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
-    t = re.search(key + r":\s*([0-9.eE+]+)", text)
+    t = re.search(re.escape(key) + r":\s*([0-9.eE+]+)", text)
     if not m or not t:
         return None
     data = b"".join(open(f, "rb").read() for f in kernel_src)
@@ -167,74 +195,187 @@ def sum_over_ranks(dist, world, value, device=None):
     return float(t.item())
 
 
-def workload():
+def spread(ms):
+    """min / median / max of per-rep times (ms)."""
+    a = np.asarray(ms, dtype=np.float64)
+    return {"min": float(a.min()), "median": float(np.median(a)), "max": float(a.max()), "reps": int(a.size)}
+
+
+def batch_workload():
+    import scenes
+    pairs = scenes.batch_pairs()
+    pr = pairs[0].params
+    kw = dict(blocks=pairs[0].blocks, ell=pr["ell"], cutoff_mult=pr["cutoff_mult"], max_iters=pr["max_iters"])
+    config = {"workload": "batch-64", "pairs": len(pairs),
+              "points_per_cloud": "5,000-60,000 (uniform)", "points": int(sum(p.n + p.m for p in pairs)),
+              "scene": "4 m cube faces + N(0, 5 mm), motion <= 8 deg / 0.4 m per pair",
+              "features": "rgb (squared-exponential, scale 0.2) x 19-class labels (inner product), "
+                          "bfloat16 storage, float32 arithmetic",
+              "lengthscale": pr["ell"], "cutoff": "3 lengthscales", "max_iters": pr["max_iters"],
+              "loop": "one CUDA graph for all pairs (batched sweep + per-pair steps, convergence masks)",
+              "l2": "flushed between steps (256 MB write)"}
+    return pairs, kw, config
+
+
+def sample_pairs(n_pairs, k=CPU_SAMPLE_PAIRS, seed=20121203):
+    """The indices of the k seeded pairs of the batch the CPU baseline times."""
+    r = np.random.Generator(np.random.PCG64(seed))
+    return sorted(int(i) for i in r.permutation(n_pairs)[:k])
+
+
+# ---- sections --------------------------------------------------------------
+
+def sweep_roofline(name, pairs_evaluated, sweep_ms_total, launches, fpp, peaks, peak_src, sms, profile=None):
+    """Roofline figures of a sweep kernel from its CUDA-event times."""
+    clk = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    peak = sms * FP32_LANES_PER_SM * 2 * clk / 1e12
+    sec = sweep_ms_total * 1e-3
+    achieved = pairs_evaluated * fpp / sec / 1e12 if sec > 0 else None
+    avg_ms = sweep_ms_total / max(launches, 1)
+    traffic = winst = xu = None
+    if profile:
+        traffic = profile_value(SWEEP_SRC, "traffic_bytes_per_launch", profile)
+        winst = profile_value(SWEEP_SRC, "warp_instructions_per_launch", profile)
+        xu = profile_value(SWEEP_SRC, "xu_pipe_frac", profile)
+    issue_peak = sms * ISSUE_PER_CLK_SM * clk
+    ex2_peak = sms * EX2_PER_CLK_SM * clk
+    return {
+        "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        "frac": achieved / peak if achieved else None, "traffic": traffic, "kernel": name,
+        "flops_per_pair": fpp, "sweep_ms_avg": avg_ms, "sweep_launches": launches,
+        "pairs_per_launch": pairs_evaluated / max(launches, 1),
+        "peak_source": f"unit counts, not a measured FFMA peak: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
+                       f"x {clk / 1e6:.0f} MHz (sm_max_mhz {peak_src})",
+        "sfu": {"achieved_ex2_per_s": pairs_evaluated / sec if sec > 0 else None, "peak_ex2_per_s": ex2_peak,
+                "frac": pairs_evaluated / sec / ex2_peak if sec > 0 else None,
+                "ncu_xu_pipe_frac": xu,
+                "peak_source": f"{sms} SMs x {EX2_PER_CLK_SM} ex2/clk/SM (measured on a GB300 with an "
+                               "independent-chain ex2.approx throughput loop) x sm_max_mhz"},
+        "issue": {"achieved_warp_inst_per_s": winst / (avg_ms * 1e-3) if (winst and avg_ms > 0) else None,
+                  "peak_warp_inst_per_s": issue_peak,
+                  "frac": winst / (avg_ms * 1e-3) / issue_peak if (winst and avg_ms > 0) else None,
+                  "warp_instructions_per_launch": winst,
+                  "source": f"smsp__inst_executed.sum per launch of the committed ncu capture (profiles/{profile}, "
+                            f"same source hash) over the CUDA-event time per launch; peak {sms} SMs x "
+                            f"{ISSUE_PER_CLK_SM} schedulers x sm_max_mhz"},
+    }
+
+
+def plain_section(h, args, torch, flush, reps):
+    """The 64 pairs through cvo_register_pair one after another; CUDA events
+    around each pass over the batch."""
+    stream = torch.cuda.current_stream()
+    for a in args[:2]:
+        h.register(*a)
+    ms, evals = [], 0
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        n = 0
+        for a in args:
+            _, info = h.register(*a)
+            n += info["pairs"]
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        evals += n
+    t = sum(ms) * 1e-3
+    return {"registered_pairs_per_s": reps * len(args) / t, "pair_evals_per_s": evals / t,
+            "ms_per_batch": spread(ms), "timing": "CUDA events around each pass of 64 cvo_register_pair calls"}
+
+
+def street_section(cvo, torch, dev, flush, peaks, peak_src, sms, reps=10):
+    """street-20k: one registration of the 20,000-point street pair (RGB +
+    labels in float32, l 0.3 -> 0.05 m annealed, cutoff 3 l, <= 100
+    iterations), autotuned, graph loop; then the same registrations with the
+    sweep timed per launch."""
     import scenes
     p = scenes.street_pair()
     pr = p.params
     kw = dict(blocks=p.blocks, ell=pr["ell"], ell_min=pr["ell_min"], cutoff_mult=pr["cutoff_mult"],
               max_iters=pr["max_iters"], anneal=pr["anneal"])
-    config = {"workload": "street-20k", "points_per_cloud": p.n,
-              "features": "rgb (squared-exponential, scale 0.2) x 19-class labels (inner product), float32",
-              "lengthscale": "0.3 -> 0.05 m annealed (2 % decays)", "cutoff": "3 lengthscales",
-              "max_iters": pr["max_iters"], "l2": "flushed between steps (256 MB write)"}
-    return p, kw, config
-
-
-def batch_section(cvo, torch, dev, flush, reps=2):
-    """64 cube pairs of 5k-60k points (RGB + labels in bf16): one batched
-    registration (one graph launch for the whole batch) against the same pairs
-    registered one after another through cvo_register_pair."""
-    import scenes
-    pairs = scenes.batch_pairs()
-    pr = pairs[0].params
-    kw = dict(blocks=pairs[0].blocks, ell=pr["ell"], cutoff_mult=pr["cutoff_mult"], max_iters=pr["max_iters"])
-    args = []
-    for p in pairs:
-        args.append((torch.tensor(p.X, device=dev), torch.tensor(p.Z, device=dev), np.eye(4),
-                     torch.tensor(p.FX, device=dev).to(torch.bfloat16),
-                     torch.tensor(p.FZ, device=dev).to(torch.bfloat16)))
-    out = {"workload": "batch-64: cube pairs, 5k-60k points per cloud, rgb + 19 labels in bf16, "
-                       f"l = {pr['ell']}, cutoff 3 l, {pr['max_iters']} iterations",
-           "pairs": len(pairs), "points": int(sum(p.n + p.m for p in pairs))}
+    X, Z = torch.tensor(p.X, device=dev), torch.tensor(p.Z, device=dev)
+    FX, FZ = torch.tensor(p.FX, device=dev), torch.tensor(p.FZ, device=dev)
+    out = {"workload": f"street-20k: {p.n} + {p.m} points, rgb + 19 labels (float32), l 0.3 -> 0.05 m, cutoff 3 l, "
+                       f"<= {pr['max_iters']} iterations"}
+    stream = torch.cuda.current_stream()
     with cvo.CVO(**kw) as h:
-        # cell size and query-group extent tuned on the largest pair (untimed)
-        big = max(range(len(pairs)), key=lambda k: pairs[k].n + pairs[k].m)
-        out["tuning"] = h.autotune(*args[big])
-        h.register_batch(args)
-        torch.cuda.synchronize()
-        t_b, evals_b = 0.0, 0
+        out["tuning"] = h.autotune(X, Z, np.eye(4), FX, FZ)
+        for _ in range(3):
+            h.register(X, Z, np.eye(4), FX, FZ)
+        ms, pairs, iters = [], 0, []
         for _ in range(reps):
             flush.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            _, infos, _ = h.register_batch(args)
-            torch.cuda.synchronize()
-            t_b += time.perf_counter() - t0
-            evals_b += sum(i["pairs"] for i in infos)
-        for a in args[:2]:
-            h.register(*a)
-        t_p, evals_p = 0.0, 0
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            T, info = h.register(X, Z, np.eye(4), FX, FZ)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            pairs += info["pairs"]
+            iters.append(info["iters"])
+        cvo.cvo_set_timing(h.h, True)
+        sw_ms, sw_n, sw_pairs = 0.0, 0, 0
         for _ in range(reps):
             flush.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for a in args:
-                _, info = h.register(*a)
-                evals_p += info["pairs"]
-            torch.cuda.synchronize()
-            t_p += time.perf_counter() - t0
-    out["batched"] = {"registered_pairs_per_s": reps * len(pairs) / t_b, "pair_evals_per_s": evals_b / t_b,
-                      "ms_per_batch": 1e3 * t_b / reps}
-    out["plain"] = {"registered_pairs_per_s": reps * len(pairs) / t_p, "pair_evals_per_s": evals_p / t_p,
-                    "ms_per_batch": 1e3 * t_p / reps}
-    out["speedup"] = t_p / t_b
+            _, inf2 = h.register(X, Z, np.eye(4), FX, FZ)
+            a, n = cvo.cvo_sweep_time(h.h)
+            sw_ms += a * n
+            sw_n += n
+            sw_pairs += inf2["pairs"]
+        cvo.cvo_set_timing(h.h, False)
+    t = sum(ms) * 1e-3
+    D = np.linalg.inv(T) @ p.T_true
+    out.update({"pair_evals_per_s": pairs / t, "registered_pairs_per_s": reps / t, "ms_per_registration": spread(ms),
+                "iterations": iters, "ell_final": info["ell_final"], "status": info["status"],
+                "pose_err_vs_truth": {"rot_rad": float(math.acos(max(-1.0, min(1.0, (np.trace(D[:3, :3]) - 1) / 2)))),
+                                      "trans_m": float(np.linalg.norm(D[:3, 3]))},
+                "roofline": sweep_roofline("k_sweep<FeatFixed<3,19,float32>>", sw_pairs, sw_ms, sw_n,
+                                           flops_per_pair(p.blocks), peaks, peak_src, sms,
+                                           profile="sweep_street-20k.md")})
     return out
 
 
-def backward_section(cvo, torch, dev, flush, reps=5):
+def cube_section(cvo, torch, dev, flush, reps=10):
+    """The dense cube pair (2,000 points per cloud, RGB, l = 0.1, every pair,
+    50 iterations): registration latency between CUDA events."""
+    import scenes
+    p = scenes.cube_pair()
+    pr = p.params
+    kw = dict(blocks=p.blocks, ell=pr["ell"], cutoff_mult=pr["cutoff_mult"], max_iters=pr["max_iters"])
+    X, Z = torch.tensor(p.X, device=dev), torch.tensor(p.Z, device=dev)
+    FX, FZ = torch.tensor(p.FX, device=dev), torch.tensor(p.FZ, device=dev)
+    stream = torch.cuda.current_stream()
+    with cvo.CVO(**kw) as h:
+        for _ in range(3):
+            h.register(X, Z, np.eye(4), FX, FZ)
+        ms, pairs = [], 0
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            T, info = h.register(X, Z, np.eye(4), FX, FZ)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            pairs += info["pairs"]
+    t = sum(ms) * 1e-3
+    D = np.linalg.inv(T) @ p.T_true
+    return {"workload": f"cube-2000: {p.n} + {p.m} points, rgb, l = 0.1, dense, {pr['max_iters']} iterations",
+            "ms_per_registration": spread(ms), "pair_evals_per_s": pairs / t, "iterations": info["iters"],
+            "pose_err_vs_truth": {"rot_rad": float(math.acos(max(-1.0, min(1.0, (np.trace(D[:3, :3]) - 1) / 2)))),
+                                  "trans_m": float(np.linalg.norm(D[:3, 3]))}}
+
+
+def backward_section(cvo, torch, dev, flush, peaks, peak_src, sms, reps=5):
     """Room pair (19,200 points per cloud, rgb, l = 0.1, cutoff 3 l): one
     forward evaluation and one backward pass (gradients for both clouds'
-    points and features and for l, device outputs), CUDA-event timed."""
+    points and features and for l, device outputs), CUDA-event timed; the
+    gradient sweeps also per launch."""
     import scenes
     p = scenes.room_pair()
     pr = p.params
@@ -246,7 +387,7 @@ def backward_section(cvo, torch, dev, flush, reps=5):
         ev = h.evaluate(X, Z, T, FX, FZ)
         h.backward(X, Z, T, FX, FZ)
         stream = torch.cuda.current_stream()
-        t = {"forward": 0.0, "backward": 0.0}
+        t = {"forward": [], "backward": []}
         for _ in range(reps):
             for name in ("forward", "backward"):
                 flush.zero_()
@@ -259,13 +400,24 @@ def backward_section(cvo, torch, dev, flush, reps=5):
                     h.backward(X, Z, T, FX, FZ)
                 e1.record(stream)
                 e1.synchronize()
-                t[name] += e0.elapsed_time(e1)
+                t[name].append(e0.elapsed_time(e1))
+        cvo.cvo_set_timing(h.h, True)
+        g_ms, g_n = 0.0, 0
+        for _ in range(reps):
+            flush.zero_()
+            h.backward(X, Z, T, FX, FZ)
+            a, n = cvo.cvo_sweep_time(h.h)
+            g_ms += a * n
+            g_n += n
+        cvo.cvo_set_timing(h.h, False)
     out["pairs"] = int(ev["pairs"])
-    out["ms_forward"] = t["forward"] / reps
-    out["ms_backward"] = t["backward"] / reps
+    out["ms_forward"] = spread(t["forward"])
+    out["ms_backward"] = spread(t["backward"])
     # the backward sweeps every in-cutoff pair twice (once per cloud)
-    out["backward_pair_evals_per_s"] = 2 * ev["pairs"] / (1e-3 * out["ms_backward"])
+    out["backward_pair_evals_per_s"] = 2 * ev["pairs"] / (1e-3 * float(np.median(t["backward"])))
     out["timing"] = "whole calls (setup, sweeps, copies) between CUDA events, L2 flushed before each"
+    out["roofline"] = sweep_roofline("k_grad + k_grad_reduce (gradient sweep, one per cloud)", ev["pairs"] * g_n,
+                                     g_ms, g_n, grad_flops_per_pair(p.blocks), peaks, peak_src, sms)
     return out
 
 
@@ -297,7 +449,7 @@ def large_section(cvo, torch, dev, flush, reps=2):
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
     D = np.linalg.inv(T) @ p.T_true
-    out.update({"ms_per_registration": float(np.mean(ms)), "iterations": info["iters"],
+    out.update({"ms_per_registration": spread(ms), "iterations": info["iters"], "status": info["status"],
                 "ell_final": info["ell_final"], "i_theta": info["i_theta"], "pairs": info["pairs"],
                 "pair_evals_per_s": info["pairs"] / (1e-3 * float(np.mean(ms))),
                 "pose_err_vs_truth": {"rot_rad": float(math.acos(max(-1.0, min(1.0, (np.trace(D[:3, :3]) - 1) / 2)))),
@@ -305,44 +457,92 @@ def large_section(cvo, torch, dev, flush, reps=2):
     return out
 
 
-def cpu_baseline(p, kw, iters=20):
+def shard_section(cvo, torch, dev, dist, world, rank, flush, reps=2):
+    """box80-200k with X's rows split over the ranks (one GPU each) and Z on
+    every rank: per iteration each rank sweeps its rows, one NCCL all-reduce
+    sums the 45 statistics, and every rank takes the same step.  Latency of
+    the whole registration between a barrier and CUDA events, max over
+    ranks."""
+    import scenes
+    p = scenes.large_pair()
+    pr = p.params
+    kw = dict(blocks=p.blocks, ell=pr["ell"], ell_min=pr["ell_min"], cutoff_mult=pr["cutoff_mult"],
+              max_iters=pr["max_iters"], anneal=pr["anneal"])
+    lo, hi = cvo.shard_rows(p.n, world, rank)
+    Xr, FXr = torch.tensor(p.X[lo:hi], device=dev), torch.tensor(p.FX[lo:hi], device=dev)
+    Z, FZ = torch.tensor(p.Z, device=dev), torch.tensor(p.FZ, device=dev)
+    stream = torch.cuda.current_stream()
+    ms = []
+    with cvo.CVO(**kw) as h:
+        h.register_sharded(Xr, Z, p.n, np.eye(4), FXr, FZ, allreduce=dist.all_reduce)
+        for _ in range(reps):
+            flush.zero_()
+            dist.barrier()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            T, info = h.register_sharded(Xr, Z, p.n, np.eye(4), FXr, FZ, allreduce=dist.all_reduce)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(max_over_ranks(dist, world, e0.elapsed_time(e1), dev))
+    return {"workload": f"box80-200k split by rows of X over {world} GPUs (NCCL all-reduce of 45 statistics per "
+                        "iteration)", "ms_per_registration": spread(ms), "iterations": info["iters"],
+            "ell_final": info["ell_final"], "status": info["status"], "pairs": info["pairs"],
+            "pair_evals_per_s": info["pairs"] / (1e-3 * float(np.median(ms)))}
+
+
+def cpu_baseline(pairs, kw, iters=1):
+    """The FP64 oracle's registration of 8 seeded pairs of the batch, first
+    iteration(s) each, on all host cores."""
     import oracle
     oracle.build()
-    t0 = time.perf_counter()
-    _, info, _ = oracle.register(p.X, p.Z, np.eye(4), FX=p.FX, FZ=p.FZ, **dict(kw, max_iters=iters))
-    dt = time.perf_counter() - t0
-    return {"value": info["pairs_total"] / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"first {info['iters']} of <= {kw['max_iters']} iterations of the FP64 oracle's registration "
-                      f"of the full street-20k pair ({info['pairs_total']} in-cutoff pairs, {dt:.1f} s)",
-            "seconds": dt}
+    idx = sample_pairs(len(pairs))
+    total, evals = 0.0, 0
+    for k in idx:
+        p = pairs[k]
+        t0 = time.perf_counter()
+        _, info, _ = oracle.register(p.X, p.Z, np.eye(4), FX=p.FX, FZ=p.FZ, **dict(kw, max_iters=iters))
+        total += time.perf_counter() - t0
+        evals += info["pairs_total"]
+    return {"value": evals / total, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"the first {iters} iteration(s) of the FP64 oracle's registration of {len(idx)} seeded pairs "
+                      f"of batch-64 (pairs {idx}; {evals} in-cutoff pairs, {total:.1f} s), per pair-eval",
+            "seconds": total}
 
 
 def run_reference(args):
     """The oracle as the reference arm: each step is a bounded sample of the
-    same workload (the first iterations of the oracle's registration)."""
+    same workload (the first iteration of the oracle's registration of one of
+    the 8 seeded pairs of the batch, in turn)."""
     dist, world, rank, _ = dist_setup("gloo")
     if rank != 0:
         return
-    p, kw, config = workload()
-    iters = 4
+    pairs, kw, config = batch_workload()
     import oracle
     oracle.build()
-    for _ in range(args.warmup):
-        oracle.register(p.X, p.Z, np.eye(4), FX=p.FX, FZ=p.FZ, **dict(kw, max_iters=iters))
-    pairs, total = 0, 0.0
-    for _ in range(args.steps):
+    idx = sample_pairs(len(pairs))
+
+    def step(s):
+        p = pairs[idx[s % len(idx)]]
+        _, info, _ = oracle.register(p.X, p.Z, np.eye(4), FX=p.FX, FZ=p.FZ, **dict(kw, max_iters=1))
+        return info["pairs_total"]
+
+    for s in range(args.warmup):
+        step(s)
+    evals, total = 0, 0.0
+    for s in range(args.steps):
         t0 = time.perf_counter()
-        _, info, _ = oracle.register(p.X, p.Z, np.eye(4), FX=p.FX, FZ=p.FZ, **dict(kw, max_iters=iters))
+        evals += step(s)
         total += time.perf_counter() - t0
-        pairs += info["pairs_total"]
-    value = pairs / total
+    value = evals / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config,
             "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(), "value": value, "unit": UNIT,
-                             "sample": f"each step: first {iters} iterations of the FP64 oracle's registration of "
-                                       f"the full street-20k pair"},
+                             "sample": f"each step: the first iteration of the FP64 oracle's registration of one of "
+                                       f"the pairs {idx} of batch-64, in turn"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -353,12 +553,15 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cvo", choices=["cvo", "reference"])
+    ap.add_argument("--reps", type=int, default=10, help="repetitions of the plain pass and of the timed sweeps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain section")
-    ap.add_argument("--no-backward", action="store_true", help="skip the forward/backward section")
-    ap.add_argument("--no-large", action="store_true", help="skip the 200,000-point section")
+    ap.add_argument("--no-sections", action="store_true", help="only the batched headline")
+    ap.add_argument("--no-street", action="store_true")
+    ap.add_argument("--no-cube", action="store_true")
+    ap.add_argument("--no-backward", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--tuning", default=None,
-                    help="cell_factor,super_delta,chunk_len for the street pair instead of autotuning "
+                    help="cell_factor,super_delta,chunk_len for the batch instead of autotuning "
                          "(fixed launch sequence for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -371,165 +574,144 @@ def main():
     dist, world, rank, local = dist_setup("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    p, kw, config = workload()
-    config["parallelism"] = f"replicas x{world}" if world > 1 else "single pair"
-    X = torch.tensor(p.X, device=dev)
-    Z = torch.tensor(p.Z, device=dev)
-    FX = torch.tensor(p.FX, device=dev)
-    FZ = torch.tensor(p.FZ, device=dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    pairs, kw, config = batch_workload()
+    config["parallelism"] = f"replicas x{world}" if world > 1 else "one GPU"
+    args_dev = [(torch.tensor(p.X, device=dev), torch.tensor(p.Z, device=dev), np.eye(4),
+                 torch.tensor(p.FX, device=dev).to(torch.bfloat16), torch.tensor(p.FZ, device=dev).to(torch.bfloat16))
+                for p in pairs]
     h = cvo.CVO(**kw)
-    # sweep tuning for this pair at its start (untimed, before the warm-up)
+    # cell size, query-group extent and item length tuned on the largest pair
+    # (untimed, before the warm-up)
     if args.tuning:
         cf, sd, ip = args.tuning.split(",")
         h.apply_tuning(float(cf), int(sd), int(ip))
         tuning = dict(h.tuning(), source="--tuning")
     else:
-        tuning = h.autotune(X, Z, np.eye(4), FX, FZ)
+        big = max(range(len(pairs)), key=lambda k: pairs[k].n + pairs[k].m)
+        tuning = dict(h.autotune(*args_dev[big]), source=f"autotuned on pair {big}")
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-    T0 = np.eye(4)
 
     for _ in range(max(args.warmup, 3)):
-        h.register(X, Z, T0, FX, FZ)
+        h.register_batch(args_dev)
     torch.cuda.synchronize()
 
-    # ---- timed region: device-resident inputs -------------------------------
+    # ---- timed region: batched registrations, device-resident inputs --------
     sampler = ClockSampler(local)
     sampler.start()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = cvo.cvo_kernel_launches()
-    step_ms, pairs, cands, iters = [], 0, 0, []
-    T_last = None
+    step_ms, evals, conv, iters = [], 0, 0, []
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        T_last, info = h.register(X, Z, T0, FX, FZ)
+        _, infos, _ = h.register_batch(args_dev)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        pairs += info["pairs"]
-        cands += info["candidates"]
-        iters.append(info["iters"])
+        evals += sum(i["pairs"] for i in infos)
+        conv += sum(1 for i in infos if i["status"] == 0)
+        iters = [i["iters"] for i in infos]
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     launches = cvo.cvo_kernel_launches() - launches0
-
-    # ---- sweep kernel duration: the same registrations with CUDA events
-    # around every sweep launch (host-queued iterations instead of the graph)
-    cvo.cvo_set_timing(h.h, True)
-    sweep_ms, sweep_n, sweep_pairs, timed_ms = 0.0, 0, 0, 0.0
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, info = h.register(X, Z, T0, FX, FZ)
-        timed_ms += 1e3 * (time.perf_counter() - t0)
-        ms, n = cvo.cvo_sweep_time(h.h)
-        sweep_ms += ms * n
-        sweep_n += n
-        sweep_pairs += info["pairs"]
-    cvo.cvo_set_timing(h.h, False)
     clocks = sampler.stop()
     total_ms = float(sum(step_ms))
     total_ms_max = max_over_ranks(dist, world, total_ms, dev)
-    pairs_all = sum_over_ranks(dist, world, float(pairs), dev)
-    value = pairs_all / (total_ms_max * 1e-3)
-    regs_per_s = world * args.steps / (total_ms_max * 1e-3)
+    evals_all = sum_over_ranks(dist, world, float(evals), dev)
+    value = evals_all / (total_ms_max * 1e-3)
+    regs_per_s = world * args.steps * len(pairs) / (total_ms_max * 1e-3)
 
-    # ---- end to end: pinned host buffers through the C ABI -----------------
-    Xh, Zh = torch.tensor(p.X).pin_memory(), torch.tensor(p.Z).pin_memory()
-    FXh, FZh = torch.tensor(p.FX).pin_memory(), torch.tensor(p.FZ).pin_memory()
-    h2d = sum(t.numel() * t.element_size() for t in (Xh, Zh, FXh, FZh))
+    # ---- the batched sweep per launch: the same registrations with the loop
+    # queued from the host and CUDA events around every sweep launch
+    cvo.cvo_set_timing(h.h, True)
+    sw_ms, sw_n, sw_evals = 0.0, 0, 0
+    for _ in range(args.reps):
+        flush.zero_()
+        _, infos, _ = h.register_batch(args_dev)
+        a, n = cvo.cvo_sweep_time(h.h)
+        sw_ms += a * n
+        sw_n += n
+        sw_evals += sum(i["pairs"] for i in infos)
+    cvo.cvo_set_timing(h.h, False)
+
+    # ---- the plain form: the same pairs one by one -----------------------------
+    plain = plain_section(h, args_dev, torch, flush, args.reps) if rank == 0 else None
+
+    # ---- end to end: pinned host buffers through the C ABI ------------------
+    args_host = [(torch.tensor(p.X).pin_memory(), torch.tensor(p.Z).pin_memory(), np.eye(4),
+                  torch.tensor(p.FX).to(torch.bfloat16).pin_memory(),
+                  torch.tensor(p.FZ).to(torch.bfloat16).pin_memory()) for p in pairs]
+    h2d = sum(t.numel() * t.element_size() for a in args_host for t in (a[0], a[1], a[3], a[4]))
     import ctypes
-    d2h = 16 * 8 + ctypes.sizeof(cvo.Info)
-    h.register(Xh, Zh, T0, FXh, FZh)
+    d2h = len(pairs) * (16 * 8 + ctypes.sizeof(cvo.Info))
+    h.register_batch(args_host)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    e2e_ms, e2e_pairs = 0.0, 0
-    for _ in range(args.steps):
+    e2e_ms, e2e_evals = 0.0, 0
+    for _ in range(max(1, args.steps // 3)):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, info = h.register(Xh, Zh, T0, FXh, FZh)
+        _, infos, _ = h.register_batch(args_host)
         torch.cuda.synchronize()
         e2e_ms += 1e3 * (time.perf_counter() - t0)
-        e2e_pairs += info["pairs"]
+        e2e_evals += sum(i["pairs"] for i in infos)
     e2e_ms = max_over_ranks(dist, world, e2e_ms, dev)
-    e2e_pairs = sum_over_ranks(dist, world, float(e2e_pairs), dev)
+    e2e_evals = sum_over_ranks(dist, world, float(e2e_evals), dev)
     h.close()
-    batch = batch_section(cvo, torch, dev, flush) if (rank == 0 and not args.no_batch) else None
-    backward = backward_section(cvo, torch, dev, flush) if (rank == 0 and not args.no_backward) else None
-    large = large_section(cvo, torch, dev, flush) if (rank == 0 and not args.no_large) else None
 
+    peaks, peak_src = load_peaks()
+    sections = {}
+    if world > 1 and not args.no_sections and not args.no_large:
+        sections["shard"] = shard_section(cvo, torch, dev, dist, world, rank, flush)
+    if rank == 0 and not args.no_sections:
+        if not args.no_street:
+            sections["street"] = street_section(cvo, torch, dev, flush, peaks, peak_src, sms)
+        if not args.no_cube:
+            sections["cube"] = cube_section(cvo, torch, dev, flush)
+        if not args.no_backward:
+            sections["backward"] = backward_section(cvo, torch, dev, flush, peaks, peak_src, sms)
+        if not args.no_large:
+            sections["large"] = large_section(cvo, torch, dev, flush)
     if rank != 0:
         return
-    peaks, peak_src = load_peaks()
-    fpp = flops_per_pair(kw["blocks"])
-    achieved = sweep_pairs * fpp / (sweep_ms * 1e-3) / 1e12 if sweep_ms > 0 else None
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    csrc = os.path.join(ROOT, "paper_2012_03683_gb300", "csrc")
-    sweep_src = [os.path.join(csrc, "cvo_sweep.cu"), os.path.join(csrc, "cvo_sweep_dev.cuh")]
-    traffic = profile_value(sweep_src, "traffic_bytes_per_launch")
-    winst = profile_value(sweep_src, "warp_instructions_per_launch")
-    sweep_ms_avg = sweep_ms / max(sweep_n, 1)
-    # the same launches against the SM's instruction issue rate (one warp
-    # instruction per scheduler per clock, 4 schedulers per SM): the bound of
-    # a kernel whose FP32 pipes are not the limit
-    issue_peak = SM_COUNT * 4 * peaks.get("sm_max_mhz", 2070.0) * 1e6
-    issue = {"achieved_warp_inst_per_s": winst / (sweep_ms_avg * 1e-3) if (winst and sweep_ms_avg > 0) else None,
-             "peak_warp_inst_per_s": issue_peak,
-             "frac": (winst / (sweep_ms_avg * 1e-3) / issue_peak) if (winst and sweep_ms_avg > 0) else None,
-             "warp_instructions_per_launch": winst,
-             "source": "smsp__inst_executed.sum, mean of the 3 launches of the committed ncu capture "
-                       "(profiles/sweep_street-20k.md, "
-                       "same source hash) over the CUDA-event time per launch; peak: 152 SMs x 4 schedulers "
-                       "x sm_max_mhz"}
-    dT = np.linalg.inv(T_last) @ p.T_true
-    pose_err = {"rot_rad": float(math.acos(max(-1.0, min(1.0, (np.trace(dT[:3, :3]) - 1.0) / 2.0)))),
-                "trans_m": float(np.linalg.norm(dT[:3, 3]))}
+
+    roof = sweep_roofline("k_sweep<FeatMMA<3>> (batched sweep, bfloat16 label tile on the tensor cores)", sw_evals,
+                          sw_ms, sw_n, flops_per_pair(kw["blocks"]), peaks, peak_src, sms,
+                          profile="sweep_batch-64.md")
+    roof["timing"] = ("CUDA events around each batched sweep launch, over the same batched registrations queued "
+                      "from the host (the timed steps run the loop as one CUDA graph)")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": "bf16 features", "data": "synthetic",
+        "config": config,
         "registered_pairs_per_s": regs_per_s,
-        "pairs_per_registration": pairs / args.steps, "candidates_per_registration": cands / args.steps,
+        "ms_per_batch": spread(step_ms),
+        "pair_evals_per_batch": evals / args.steps,
+        "converged_per_batch": conv / args.steps,
         "iterations": iters,
-        "e2e": {"value": e2e_pairs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "plain": plain,
+        "batched_vs_plain": (regs_per_s / world) / plain["registered_pairs_per_s"] if plain else None,
+        "e2e": {"value": e2e_evals / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "tuning": tuning,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None,
-                     "traffic": traffic, "kernel": "k_sweep (fused neighbour sweep)",
-                     "flops_per_pair": fpp, "sweep_ms_avg": sweep_ms_avg, "sweep_launches": sweep_n,
-                     "timing": "CUDA events around each sweep launch, over the same registrations queued "
-                               "from the host (the timed steps run the loop as one CUDA graph)",
-                     "ms_per_registration_event_timed": timed_ms / args.steps,
-                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz "
-                                    f"(sm_max_mhz {peak_src})",
-                     # the one ex2 per in-cutoff pair against the XU pipe's rate
-                     "sfu": {"achieved_ex2_per_s": (sweep_pairs / (sweep_ms * 1e-3)) if sweep_ms > 0 else None,
-                             "peak_ex2_per_s": SM_COUNT * EX2_PER_CLK_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6,
-                             "frac": (sweep_pairs / (sweep_ms * 1e-3)) /
-                                     (SM_COUNT * EX2_PER_CLK_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6)
-                                     if sweep_ms > 0 else None,
-                             "peak_source": f"152 SMs x {EX2_PER_CLK_SM} ex2/clk/SM (measured on a GB300 with an "
-                                            "independent-chain ex2.approx throughput loop) x sm_max_mhz"},
-                     "issue": issue},
+        "roofline": roof,
         "clocks": clocks,
-        "final_pose_err_vs_truth": pose_err,
-        "batch": batch,
-        "backward": backward,
-        "large": large,
+        "sm_count": sms,
     }
+    line.update(sections)
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(p, kw)
+        line["cpu_baseline"] = cpu_baseline(pairs, kw)
     print(json.dumps(line), flush=True)
 
 
