@@ -100,7 +100,9 @@ struct LevelHost {
 };
 
 constexpr long long kMaxCells = 1LL << 26;
-constexpr int kMiscWords = 64;   // bbox (12), bad flag (1), group totals (<= kMaxLevels)
+constexpr int kMiscWords = 64;   // bbox (12), bad flag (1), group totals (<= kMaxLevels), Z's moments (10)
+constexpr int kZStatsWord = 48;  // Z's centroid, mean squared and largest radius: 5 doubles from this word on
+static_assert(kZStatsWord % 2 == 0 && kZStatsWord + 10 <= kMiscWords, "Z's moments must fit the scratch slot");
 
 float decode_orderable(unsigned u)
 {
@@ -118,7 +120,8 @@ struct PairRes {
     int n = 0, m = 0, nlevels = 0;
     LevelHost lv[kMaxLevels];
     LevelDesc ld[kMaxLevels];   // host copy of levels_dev
-    double zc[3] = {0, 0, 0};
+    double zc[3] = {0, 0, 0};   // centroid of Z (the lever centre)
+    double zr2 = 0.0, zrmax = 0.0;
     int max_items = 1;
 
     void free_all()
@@ -154,6 +157,7 @@ struct cvo_handle_s {
     SetupLane lanes[kSetupLanes];
     // sweep / finalize scratch
     DevBuf part_stats, part_cnt, grp_stats, grp_cnt, grp_arrivals, pairs_dev, counters, trace;
+    DevBuf batch_work;   // per pair of a batch: work items left (the batched step re-splits the grid by them)
     // gradients with respect to the inputs: device outputs for host callers,
     // per-query terms of dF/dl and their sum
     DevBuf bw_out[4], bw_tq, bw_dell, bw_part;
@@ -403,6 +407,7 @@ cvo_status prepare_bbox(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_
     int* bad = (int*)(dev + 12);
     CVO_CUDA(launch_bbox(sg->xyz_x, n, dev + 0, bad, h->s));
     CVO_CUDA(launch_bbox(sg->xyz_z, m, dev + 6, bad, h->s));
+    CVO_CUDA(launch_zstats(sg->xyz_z, m, (double*)(dev + kZStatsWord), h->s));
     if (D > 0) {
         CVO_CUDA(launch_check_feat(sg->feat_x, (long long)n * D, X->feat_dtype == CVO_BF16, bad, h->s));
         CVO_CUDA(launch_check_feat(sg->feat_z, (long long)m * D, Z->feat_dtype == CVO_BF16, bad, h->s));
@@ -429,7 +434,13 @@ cvo_status prepare_build(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo
         xmax[a] = decode_orderable(hm[3 + a]);
         zmin[a] = decode_orderable(hm[6 + a]);
         zmax[a] = decode_orderable(hm[9 + a]);
-        P.zc[a] = 0.5 * ((double)zmin[a] + (double)zmax[a]);
+    }
+    {
+        double zs[5];
+        std::memcpy(zs, hm + kZStatsWord, sizeof(zs));
+        for (int a = 0; a < 3; ++a) P.zc[a] = zs[a];
+        P.zr2 = zs[3];
+        P.zrmax = zs[4];
     }
     const int rs = h->rs;
     const int nmax = std::max(n, m);
@@ -605,7 +616,7 @@ cvo_status prepare(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud
     unsigned* dev = (unsigned*)h->misc.p;
     Staged sg;
     CVO_TRY(prepare_bbox(h, P, X, Z, dev, &sg));
-    CVO_CUDA(cudaMemcpyAsync(h->h_misc, dev, 13 * sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
+    CVO_CUDA(cudaMemcpyAsync(h->h_misc, dev, (kZStatsWord + 10) * sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
     CVO_CUDA(cudaStreamSynchronize(h->s));
     CVO_TRY(prepare_build(h, P, X, Z, ell_hi, ell_lo, sg, h->h_misc, dev, true));
     CVO_CUDA(cudaMemcpyAsync(h->h_misc + 16, dev + 16, P.nlevels * sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
@@ -727,6 +738,8 @@ cvo_status init_state(cvo_handle h, PairRes& P, int slot, const double* T, doubl
     st->anneal = p.anneal;
     st->status = 1;
     for (int a = 0; a < 3; ++a) st->c[a] = P.zc[a];
+    st->rho2 = P.zr2;
+    st->rmax = P.zrmax;
     st->nlevels = P.nlevels;
     for (int k = 0; k < P.nlevels; ++k) st->level_h[k] = (float)P.lv[k].rdesign;
     if (mode == 1 && p.max_iters == 0) st->done = 1;
@@ -782,6 +795,7 @@ PairDesc pair_desc(const PairRes& P, int b0, int b1)
     d.m = P.m;
     d.b0 = b0;
     d.b1 = b1;
+    d.bmax = b1 - b0;
     return d;
 }
 
@@ -928,14 +942,15 @@ cvo_status run_graph_loop(cvo_handle h, const SweepArgs& a, bool batch, IterStat
     lpn.kernel.blockDim = dim3(kLayoutThreads);
     lpn.kernel.kernelParams = lp;
     // batch
-    const PairDesc* pairs = a.pairs;
+    PairDesc* pairs = const_cast<PairDesc*>(a.pairs);   // the batched step re-splits the grid in place
     int npairs = a.npairs;
     const float2* ps = a.part_stats;
     const unsigned long long* pc = a.part_cnt;
     int cap = a.part_cap;
     long long tstride = trace_stride;
     unsigned* counters = (unsigned*)h->counters.p;
-    void* fpb[10] = {&pairs, &npairs, &ps, &pc, &cap, &tr, &tstride, &counters, &cond, &use_cond};
+    unsigned* work = (unsigned*)h->batch_work.p;
+    void* fpb[11] = {&pairs, &npairs, &ps, &pc, &cap, &tr, &tstride, &counters, &work, &cond, &use_cond};
     if (batch) {
         fpn.kernel.func = (void*)finalize_batch_kernel();
         fpn.kernel.gridDim = dim3(npairs);
@@ -1232,10 +1247,15 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
     int b = 0;
     for (int i = 0; i < nl; ++i) {
         table.push_back(pair_desc(h->pr[i], b, b + nbs[i]));
+        // as pairs stop, the batched step hands their blocks to the pairs
+        // still running: each up to 8 times its first share, and never more
+        // blocks than it has work items for
+        table.back().bmax = std::max(1, std::min(cap[i], 8 * nbs[i]));
         b += nbs[i];
     }
     SweepArgs a{};
     CVO_TRY(setup_sweep(h, table, b, &a, false));
+    CVO_CUDA(ensure(h->batch_work, (size_t)nl * sizeof(unsigned)));
     const long long tstride = (long long)p.max_iters * CVO_TRACE_STRIDE;
     CVO_CUDA(ensure(h->trace, (size_t)nl * tstride * sizeof(double)));
     double* traces = (double*)h->trace.p;
@@ -1255,8 +1275,9 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
                 if (ev) CVO_CUDA(cudaEventRecord(h->evs[2 * it], h->s));
                 CVO_CUDA(launch_sweep(a, b, h->s));
                 if (ev) CVO_CUDA(cudaEventRecord(h->evs[2 * it + 1], h->s));
-                CVO_CUDA(launch_finalize_batch(a.pairs, nl, a.part_stats, a.part_cnt, a.part_cap, traces, tstride,
-                                               counters, h->s));
+                CVO_CUDA(launch_finalize_batch(const_cast<PairDesc*>(a.pairs), nl, a.part_stats, a.part_cnt,
+                                               a.part_cap, traces, tstride, counters, (unsigned*)h->batch_work.p,
+                                               h->s));
             }
             launched += n;
             if (launched >= p.max_iters) break;
@@ -1598,6 +1619,7 @@ cvo_status cvo_destroy(cvo_handle h)
     DevBuf* bufs[] = {&h->stage_xyz[0], &h->stage_xyz[1], &h->stage_feat[0], &h->stage_feat[1], &h->keys, &h->vals,
                       &h->keys2, &h->vals2, &h->sort_tmp, &h->flags, &h->gidx, &h->misc, &h->part_stats, &h->part_cnt,
                       &h->grp_stats, &h->grp_cnt, &h->grp_arrivals, &h->pairs_dev, &h->counters, &h->trace,
+                      &h->batch_work,
                       &h->bw_out[0], &h->bw_out[1], &h->bw_out[2], &h->bw_out[3], &h->bw_tq, &h->bw_dell, &h->bw_part};
     for (DevBuf* b : bufs) release(*b);
     for (SetupLane& L : h->lanes) {

@@ -12,14 +12,15 @@
 //    the left perturbation exp(xi^) T.  With gc = (gc_w, gc_v) the centred
 //    gradient, R, t the pose:  g_v = R gc_v,  g_w = R (gc_w + c x gc_v) + t x g_v.
 //    The indicator of Eq. (indicator_actual) is F / sqrt(N M).
-// 3. Registration: the step along the gradient (the method is gradient ascent
-//    on SE(3), Sec. I), t = |g|^2 / -F'' with F'' = g^T H g when negative,
-//    else 1e-3 / |g|; the clamps; T <- exp(t g^) T (closed-form SE(3)
-//    exponential, Rodrigues + left Jacobian); Gram-Schmidt on R every 16
-//    iterations; the stopping test; the lengthscale annealing of Sec. IV
-//    (l <- max(decay l, l_min) once the indicator at the current l changes by
-//    less than indicator_tol relative).  F'' is the quadratic form of the
-//    centred Hessian at (w~, v~) = (R^T g_w, -c x w~ + R^T (g_v - t x g_w)).
+// 3. Registration (the method is gradient ascent on SE(3), Sec. I): the
+//    ascent direction in a metric about Z's moved centroid, the Newton step
+//    along it inside a trust region on the motion of Z's points (see
+//    step_warp); T <- exp(t xi^) T (closed-form SE(3) exponential, Rodrigues
+//    + left Jacobian); Gram-Schmidt on R every 16 iterations; the stopping
+//    test; the lengthscale annealing of Sec. IV (l <- max(decay l, l_min)
+//    once the indicator at the current l changes by less than indicator_tol
+//    relative).  F'' is the quadratic form of the centred Hessian at the
+//    direction's centred coordinates (w~, v~).
 // 4. Writes the derived constants of the next sweep (double-float T^-1,
 //    exponent scale, cutoff, grid level).
 // An evaluation (no step) also assembles the full 6x6 Hessian.
@@ -92,7 +93,7 @@ __device__ void finalize_tail(IterState* st, unsigned long long* sbuf, const dou
         return;
     }
     if (sst->mode == 0) {
-        if (threadIdx.x == 0) take_step(sst, S, cs[0], cs[1], trace);
+        if (threadIdx.x == 0) take_step(sst, S, cs[0], cs[1]);
     } else if (threadIdx.x < 32) {
         step_warp(sst, S, Shi, Slo, cs[0], cs[1], trace);
     }
@@ -154,16 +155,91 @@ __global__ void __launch_bounds__(kStepThreads) k_finalize_stats(IterState* st, 
     finalize_tail(st, sbuf, S, Shi, Slo, cs, trace, cudaGraphConditionalHandle{}, 0);
 }
 
+// The last finalize block of a batch re-splits the sweep grid among the
+// pairs still running, for the next sweep: pair k gets blocks [b0, b1) with
+// b0 = a_k + floor((B - A) W_k / W) (a_k running pairs and W_k work before
+// it, A and W in all, B the grid), b1 = b0 + 1 + the proportional share of
+// its own work, then at most bmax.  Blocks between a capped pair's b1 and
+// the next pair's b0 find no work (the sweep returns at once for them).  A
+// fixed-order scan over the pairs in chunks of the block's threads.
+__device__ void resplit_grid(PairDesc* pairs, int npairs, int nblocks, const unsigned* work)
+{
+    __shared__ unsigned long long s_w[kFinalizeThreads];
+    __shared__ unsigned s_a[kFinalizeThreads];
+    __shared__ unsigned long long tot_w;
+    __shared__ unsigned tot_a;
+    const int t = threadIdx.x;
+    // totals
+    unsigned long long w = 0;
+    unsigned a = 0;
+    for (int k = t; k < npairs; k += kFinalizeThreads) {
+        const unsigned v = __ldcg(work + k);
+        w += v;
+        a += v > 0u ? 1u : 0u;
+    }
+    s_w[t] = w;
+    s_a[t] = a;
+    __syncthreads();
+    if (t == 0) {
+        unsigned long long tw = 0;
+        unsigned ta = 0;
+        for (int i = 0; i < kFinalizeThreads; ++i) {
+            tw += s_w[i];
+            ta += s_a[i];
+        }
+        tot_w = tw > 0 ? tw : 1;
+        tot_a = ta;
+    }
+    __syncthreads();
+    const unsigned long long W = tot_w;
+    const long long rem = (long long)nblocks - (long long)tot_a;
+    if (tot_a == 0 || rem < 0) return;   // nothing runs (or more pairs than blocks: keep the split)
+    unsigned long long carry_w = 0;
+    unsigned carry_a = 0;
+    for (int base = 0; base < npairs; base += kFinalizeThreads) {
+        const int k = base + t;
+        const unsigned v = k < npairs ? __ldcg(work + k) : 0u;
+        __syncthreads();
+        s_w[t] = v;
+        s_a[t] = v > 0u ? 1u : 0u;
+        __syncthreads();
+        // inclusive scan of the chunk (Hillis-Steele, fixed order)
+        for (int o = 1; o < kFinalizeThreads; o <<= 1) {
+            const unsigned long long pw = t >= o ? s_w[t - o] : 0ull;
+            const unsigned pa = t >= o ? s_a[t - o] : 0u;
+            __syncthreads();
+            s_w[t] += pw;
+            s_a[t] += pa;
+            __syncthreads();
+        }
+        if (k < npairs) {
+            const unsigned long long wb = carry_w + s_w[t] - v;   // work before pair k
+            const unsigned ab = carry_a + s_a[t] - (v > 0u ? 1u : 0u);
+            const int b0 = (int)(ab + (unsigned long long)rem * wb / W);
+            int b1 = b0;
+            if (v > 0u) {
+                const int b1p = (int)(ab + 1u + (unsigned long long)rem * (wb + v) / W);
+                b1 = min(b1p, b0 + max(pairs[k].bmax, 1));
+            }
+            pairs[k].b0 = b0;
+            pairs[k].b1 = b1;
+        }
+        carry_w += s_w[kFinalizeThreads - 1];
+        carry_a += s_a[kFinalizeThreads - 1];
+    }
+}
+
 __global__ void __launch_bounds__(kFinalizeThreads)
-k_finalize_batch(const PairDesc* __restrict__ pairs, int npairs, const float2* __restrict__ ps,
+k_finalize_batch(PairDesc* __restrict__ pairs, int npairs, const float2* __restrict__ ps,
                  const unsigned long long* __restrict__ pc, int cap, double* traces, long long trace_stride,
-                 unsigned* counters, cudaGraphConditionalHandle cond, int use_cond)
+                 unsigned* counters, unsigned* work, cudaGraphConditionalHandle cond, int use_cond)
 {
     constexpr int kWords = (int)(sizeof(IterState) / 8);
     __shared__ double S[kStatN];
     __shared__ float Shi[kStatN], Slo[kStatN];
     __shared__ unsigned long long cs[2];
     __shared__ unsigned long long sbuf[kWords];
+    __shared__ int is_last;
     const PairDesc P = pairs[blockIdx.x];
     IterState* st = P.st;
     const bool was_done = st->done != 0;
@@ -201,16 +277,23 @@ k_finalize_batch(const PairDesc* __restrict__ pairs, int npairs, const float2* _
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (!was_done && !sst->done) atomicAdd(&counters[1], 1u);
+        const bool running = !was_done && !sst->done;
+        // the work this pair has left: its items at its (next) grid level
+        work[blockIdx.x] = running ? (unsigned)max(P.levels[sst->level].nitems, 1) : 0u;
+        if (running) atomicAdd(&counters[1], 1u);
         __threadfence();
-        if (atomicAdd(&counters[0], 1u) == (unsigned)(npairs - 1)) {
-            __threadfence();
-            const unsigned active = atomicAdd(&counters[1], 0u);
-            counters[2] = active;
-            counters[0] = 0u;
-            counters[1] = 0u;
-            if (use_cond) cudaGraphSetConditional(cond, active > 0u ? 1u : 0u);
-        }
+        is_last = atomicAdd(&counters[0], 1u) == (unsigned)(npairs - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    resplit_grid(pairs, npairs, cap, work);
+    if (threadIdx.x == 0) {
+        const unsigned active = atomicAdd(&counters[1], 0u);
+        counters[2] = active;
+        counters[0] = 0u;
+        counters[1] = 0u;
+        if (use_cond) cudaGraphSetConditional(cond, active > 0u ? 1u : 0u);
     }
 }
 
@@ -219,13 +302,14 @@ k_finalize_batch(const PairDesc* __restrict__ pairs, int npairs, const float2* _
 const void* finalize_kernel() { return (const void*)k_finalize; }
 const void* finalize_batch_kernel() { return (const void*)k_finalize_batch; }
 
-cudaError_t launch_finalize_batch(const PairDesc* pairs, int npairs, const float2* part_stats,
+cudaError_t launch_finalize_batch(PairDesc* pairs, int npairs, const float2* part_stats,
                                   const unsigned long long* part_cnt, int part_cap, double* traces,
-                                  long long trace_stride, unsigned* counters, cudaStream_t s)
+                                  long long trace_stride, unsigned* counters, unsigned* work, cudaStream_t s)
 {
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
     k_finalize_batch<<<npairs, kFinalizeThreads, 0, s>>>(pairs, npairs, part_stats, part_cnt, part_cap, traces,
-                                                         trace_stride, counters, cudaGraphConditionalHandle{}, 0);
+                                                         trace_stride, counters, work,
+                                                         cudaGraphConditionalHandle{}, 0);
     return cudaGetLastError();
 }
 

@@ -120,7 +120,9 @@ struct IterState {
     double norm;             // 1 / sqrt(N M) (0 if empty)
     double cutoff_mult, ell_min, decay, indicator_tol;
     double step_tol_rot, step_tol_trans, max_step_rot, max_step_trans;
-    double c[3];             // lever centre (double)
+    double c[3];             // lever centre (double): the centroid of Z
+    double rho2;             // mean squared distance of Z's points from c (the step's rotation weight, plus l^2)
+    double rmax;             // largest distance of a point of Z from c (the step's trust region)
     int max_iters, anneal;
     int nlevels;
     float level_h[kMaxLevels];
@@ -135,6 +137,7 @@ struct PairDesc {
     IterState* st;
     int n, m;
     int b0, b1;
+    int bmax;                  // most sweep blocks a batch may give this pair when it re-splits the grid
 };
 
 struct SweepArgs {
@@ -165,14 +168,19 @@ extern std::atomic<long long> g_launch_count;
 cudaError_t launch_sweep(const SweepArgs& a, int nblocks, cudaStream_t s);
 
 // Batched step: one block per pair sums that pair's block partials and takes
-// its step; the last block to finish writes the number of pairs still
-// running to *active and, inside a graph, sets the loop's condition.
-// traces: npairs x trace_stride doubles (NULL: no trace).
-cudaError_t launch_finalize_batch(const PairDesc* pairs, int npairs, const float2* part_stats,
+// its step, and records the work the pair has left (its work items at its
+// grid level, 0 once it has stopped) in work[pair]; the last block to finish
+// writes the number of pairs still running to counters[2], re-splits the
+// sweep grid of part_cap blocks among the running pairs in proportion to
+// their work (at least one block each, at most bmax; stopped pairs get none)
+// by rewriting the pairs' b0 / b1 for the next sweep, and, inside a graph,
+// sets the loop's condition.  traces: npairs x trace_stride doubles (NULL: no
+// trace).
+cudaError_t launch_finalize_batch(PairDesc* pairs, int npairs, const float2* part_stats,
                                   const unsigned long long* part_cnt, int part_cap, double* traces,
-                                  long long trace_stride, unsigned* counters, cudaStream_t s);
-// k_finalize_batch(const PairDesc*, int npairs, const float2*, const unsigned long long*, int cap,
-//                  double* traces, long long trace_stride, unsigned* counters,
+                                  long long trace_stride, unsigned* counters, unsigned* work, cudaStream_t s);
+// k_finalize_batch(PairDesc*, int npairs, const float2*, const unsigned long long*, int cap,
+//                  double* traces, long long trace_stride, unsigned* counters, unsigned* work,
 //                  cudaGraphConditionalHandle cond, int use_cond); counters[0] arrivals,
 //                  counters[1] active pairs being counted, counters[2] the last count
 const void* finalize_batch_kernel();
@@ -256,6 +264,8 @@ cudaError_t launch_write_items(const LevelDesc* levels, int level, const unsigne
 // setup (cvo_setup.cu)
 cudaError_t launch_bbox(const float* xyz, int n, unsigned* out6, int* bad, cudaStream_t s);
 cudaError_t launch_check_feat(const void* feat, long long count, int bf16, int* bad, cudaStream_t s);
+// centroid (3), mean squared distance from it and largest distance of a cloud's points: 5 doubles
+cudaError_t launch_zstats(const float* xyz, int n, double* out5, cudaStream_t s);
 cudaError_t launch_cell_keys(const float* xyz, int n, float ox, float oy, float oz, float inv_h, int nx, int ny,
                              int nz, unsigned* keys, unsigned* vals, cudaStream_t s);
 cudaError_t launch_morton_keys(const float* xyz, int n, float ox, float oy, float oz, float inv_cell,

@@ -352,6 +352,7 @@ extern "C" cvo_status cvo_evaluate_dense_noalloc(const cvo_params* p, void* cuda
     pd.m = m;
     pd.b0 = 0;
     pd.b1 = nblocks;
+    pd.bmax = nblocks;
     PairDesc* pair = (PairDesc*)(base + kOffPair);
 
     g_launch_count.fetch_add(2, std::memory_order_relaxed);

@@ -377,9 +377,90 @@ __global__ void k_sum_f32(const float* __restrict__ v, int n, double* out)
     }
 }
 
+// hi + lo += v, error-free in FP32 (a double-float accumulator)
+__device__ __forceinline__ void df_acc(float& hi, float& lo, float v)
+{
+    const float s = __fadd_rn(hi, v);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+    const float t = __fadd_rn(lo, e);
+    hi = __fadd_rn(s, t);
+    lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
+// Fixed-order tree sum of one double per thread over the block (blockDim.x a
+// power of two); the result in red[0].
+__device__ void block_sum(double* red, double v)
+{
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+}
+
+// The centroid of a cloud, the mean squared distance of its points from it
+// and the largest such distance (out: cx, cy, cz, mean r^2, max r), for the
+// metric and the trust region of the registration step.  One block of
+// kZStatsThreads threads; per-thread double-float sums in a fixed stride,
+// then a fixed-order tree, so the result does not vary from run to run.
+constexpr int kZStatsThreads = 1024;
+__global__ void __launch_bounds__(kZStatsThreads) k_zstats(const float* __restrict__ xyz, int n, double* out)
+{
+    __shared__ double red[kZStatsThreads];
+    __shared__ double mean[3];
+    __shared__ float mhi[3], mlo[3];
+    for (int a = 0; a < 3; ++a) {
+        float hi = 0.0f, lo = 0.0f;
+        for (int i = threadIdx.x; i < n; i += kZStatsThreads) df_acc(hi, lo, xyz[3 * (size_t)i + a]);
+        block_sum(red, (double)hi + (double)lo);
+        if (threadIdx.x == 0) {
+            mean[a] = red[0] / (double)n;
+            mhi[a] = (float)mean[a];
+            mlo[a] = (float)(mean[a] - (double)mhi[a]);
+        }
+        __syncthreads();
+    }
+    float hi = 0.0f, lo = 0.0f, mx = 0.0f;
+    for (int i = threadIdx.x; i < n; i += kZStatsThreads) {
+        float q = 0.0f;
+        for (int a = 0; a < 3; ++a) {
+            const float e = __fsub_rn(__fsub_rn(xyz[3 * (size_t)i + a], mhi[a]), mlo[a]);
+            q = fmaf(e, e, q);
+        }
+        df_acc(hi, lo, q);
+        mx = fmaxf(mx, q);
+    }
+    block_sum(red, (double)hi + (double)lo);
+    const double s2 = red[0];
+    __syncthreads();
+    red[threadIdx.x] = (double)mx;
+    __syncthreads();
+    for (int o = kZStatsThreads / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = mean[0];
+        out[1] = mean[1];
+        out[2] = mean[2];
+        out[3] = s2 / (double)n;
+        out[4] = sqrt(red[0]);
+    }
+}
+
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
+
+cudaError_t launch_zstats(const float* xyz, int n, double* out5, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    k_zstats<<<1, kZStatsThreads, 0, s>>>(xyz, n, out5);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_sum_f32(const float* v, int n, double* out, cudaStream_t s)
 {

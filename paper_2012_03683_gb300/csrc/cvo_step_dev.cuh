@@ -232,11 +232,11 @@ __device__ void full_hessian(const double* s, double iL2, double iL4, const doub
         }
 }
 
-// One thread takes the step on a shared-memory copy of the state: global
+// An evaluation (no step): F, the gradient, the full Hessian and the
+// indicator, by one thread on a shared-memory copy of the state (global
 // loads after global stores to the same struct would each wait a full L2
-// round trip.
-__device__ void take_step(IterState* st, const double* S, unsigned long long pairs, unsigned long long cands,
-                          double* trace)
+// round trip).
+__device__ void take_step(IterState* st, const double* S, unsigned long long pairs, unsigned long long cands)
 {
     const double kap = st->kappa;
     const double ell = st->ell, L2 = ell * ell;
@@ -259,93 +259,10 @@ __device__ void take_step(IterState* st, const double* S, unsigned long long pai
     st->cands = (long long)cands;
     for (int q = 0; q < 6; ++q) st->grad[q] = g[q];
 
-    if (st->mode == 0) {
-        double s[kStatN];
-        for (int k = 0; k < kStatN; ++k) s[k] = kap * S[k];
-        full_hessian(s, iL2, iL4, T, st->c, st->hess);
-        st->done = 1;
-        return;
-    }
-
-    // ---- registration step --------------------------------------------------
-    const int it = st->iter;
-    // the gradient direction in the centred coordinates
-    const V3 wt = rtmul(T, gw);
-    const V3 vt = add(scale(cross(c, wt), -1.0), rtmul(T, sub(gv, cross(tt, gw))));
-    // F'' = w~^T Hww w~ + 2 w~^T Hwv v~ + v~^T Hvv v~ (centred Hessian blocks)
-    const double trWpp = S[ST_WPP] + S[ST_WPP + 1] + S[ST_WPP + 2];
-    const double trEp = Ep[0] + Ep[4] + Ep[8];
-    const double ww = dot(wt, wt), vv = dot(vt, vt);
-    const double hww = -symq(S + ST_PQP, wt, wt) * iL4 - (trWpp * ww - symq(S + ST_WPP, wt, wt)) * iL2 +
-                       (fullq(Ep, wt, wt) - trEp * ww) * iL2;
-    const V3 Ev = v3(S[ST_E], S[ST_E + 1], S[ST_E + 2]);
-    const V3 Wpv = v3(S[ST_WP], S[ST_WP + 1], S[ST_WP + 2]);
-    const double hwv = fullq(S + ST_PQ, wt, vt) * iL4 - (dot(wt, cross(Wpv, vt)) + 0.5 * dot(wt, cross(Ev, vt))) * iL2;
-    const double hvv = symq(S + ST_Q, vt, vt) * iL4 - S[ST_W] * vv * iL2;
-    const double Fpp = kap * (hww + 2.0 * hwv + hvv);
-    double gn2 = 0.0;
-    for (int q = 0; q < 6; ++q) gn2 += g[q] * g[q];
-    // Norms and clamp ratios only feed thresholds and the step length: FP32
-    // square roots and divisions (FP64 ones cost ~700 cycles each here).
-    const double wn = (double)sqrtf((float)dot(gw, gw));
-    const double vn = (double)sqrtf((float)dot(gv, gv));
-    double t = 0.0;
-    if (gn2 > 0.0) {
-        t = (Fpp < 0.0) ? gn2 / (-Fpp) : 1e-3 / (double)sqrtf((float)gn2);
-        const double max_tr = st->max_step_trans > 0.0 ? st->max_step_trans : 0.5 * ell;
-        if (t * wn > st->max_step_rot) t = (double)((float)st->max_step_rot / (float)wn);
-        if (t * vn > max_tr) t = (double)((float)max_tr / (float)vn);
-    }
-    double T_k[12];
-    for (int q = 0; q < 12; ++q) T_k[q] = T[q];
-    double xi[6], Ex[16];
-    for (int q = 0; q < 6; ++q) xi[q] = t * g[q];
-    se3_exp_dev(xi, Ex);
-    compose(Ex, T);
-    if ((it + 1) % 16 == 0) orthonormalize(T);
-    const double srot = t * wn;
-    const double strans = t * vn;
-    st->pairs_total += (long long)pairs;
-    st->cands_total += (long long)cands;
-    st->Fpp = Fpp;
-    st->gnorm = (double)sqrtf((float)gn2);
-    st->t = t;
-    st->srot = srot;
-    st->strans = strans;
-    const double ell_used = ell;
-    const int at_floor = !st->anneal || ell <= st->ell_min;
-    const int converged = at_floor && srot < st->step_tol_rot && strans < st->step_tol_trans;
-    int decayed = 0;
-    if (!converged && st->anneal && ell > st->ell_min) {
-        const int fire = st->have_ref && fabs(ith - st->i_ref) < st->indicator_tol * fabs(st->i_ref);
-        if (fire) {
-            double nl = st->decay * ell;
-            if (nl < st->ell_min) nl = st->ell_min;
-            st->ell = nl;
-            st->have_ref = 0;
-            decayed = 1;
-        } else {
-            st->i_ref = ith;
-            st->have_ref = 1;
-        }
-    }
-    st->decayed = decayed;
-    if (trace) {
-        double* tr = trace + (size_t)kTraceStride * it;
-        tr[0] = ell_used; tr[1] = F; tr[2] = ith; tr[3] = st->gnorm; tr[4] = Fpp;
-        tr[5] = t; tr[6] = srot; tr[7] = strans; tr[8] = decayed; tr[9] = (double)pairs;
-        for (int q = 0; q < 12; ++q) tr[10 + q] = T_k[q];
-    }
-    st->ell_last = ell_used;
-    st->iter = it + 1;
-    if (converged) {
-        st->status = 0;
-        st->done = 1;
-    } else if (it + 1 >= st->max_iters) {
-        st->status = 1;
-        st->done = 1;
-    }
-    update_derived(st);
+    double s[kStatN];
+    for (int k = 0; k < kStatN; ++k) s[k] = kap * S[k];
+    full_hessian(s, iL2, iL4, T, st->c, st->hess);
+    st->done = 1;
 }
 
 // Horner coefficients (highest order first) of sin(th)/th, (1 - cos th)/th^2
@@ -359,12 +276,27 @@ __constant__ double c_se3_series[3][9] = {
      1.0 / 39916800.0, 1.0 / 362880.0, 1.0 / 5040.0, 1.0 / 120.0, 1.0 / 6.0}};
 
 // The registration step, run by one warp on the shared-memory state.
+// Gradient ascent on SE(3) (Sec. I) with a step size (Sec. III-B), neither
+// given by the paper as a formula; the rule taken:
+//   direction: the gradient in a metric that names no coordinate origin.
+//     Perturbations are written about the moved centroid p = T c of Z,
+//     eta = (omega, u) with u the velocity of p, and measured by
+//     rho^2 |omega|^2 + |u|^2 (rho^2 = mean squared radius of Z + l^2).  In
+//     the centred coordinates of Z's frame this is (w~, v~) = (gc_w / rho^2,
+//     gc_v), gc the centred gradient the statistics give directly, and
+//     F' = |gc_w|^2 / rho^2 + |gc_v|^2;
+//   length: the Newton step F' / -F'' where F'' < 0, else the trust
+//     region's edge, and never beyond it: no point of Z moves more than
+//     delta = max_step_trans (or l / 2), t (|w~| r_max + |v~|) <= delta, and
+//     t |w~| <= max_step_rot;
+//   update: T <- exp(t xi^) T with xi = (R w~, R v~ + p x R w~);
+//   stop: |t w~| < step_tol_rot and |t v~| < step_tol_trans at the floor.
 // GB300 issues an FP64 warp instruction in about 80 cycles whether one lane
 // or all 32 are active, so the pose arithmetic (FP64) is spread over lanes:
 // the three exponential coefficients on lanes 0-2, the exponential's and the
 // new pose's 12 entries on lanes 0-11, the 12 derived constants on lanes
-// 0-11.  The gradient direction, F'' along it and the step length come from
-// the double-float sums in FP32: they set a direction and a length, while the
+// 0-11.  The direction, F'' along it and the step length come from the
+// double-float sums in FP32: they set a direction and a length, while the
 // pose they update stays in FP64.
 __device__ void step_warp(IterState* st, const double* S, const float* Shi, const float* Slo,
                           unsigned long long pairs, unsigned long long cands, double* trace)
@@ -394,9 +326,6 @@ __device__ void step_warp(IterState* st, const double* S, const float* Shi, cons
     auto rm = [&](const float* a, float* o) {
         for (int r = 0; r < 3; ++r) o[r] = R[3 * r] * a[0] + R[3 * r + 1] * a[1] + R[3 * r + 2] * a[2];
     };
-    auto rtm = [&](const float* a, float* o) {
-        for (int r = 0; r < 3; ++r) o[r] = R[r] * a[0] + R[3 + r] * a[1] + R[6 + r] * a[2];
-    };
     auto cr = [](const float* a, const float* b, float* o) {
         o[0] = a[1] * b[2] - a[2] * b[1];
         o[1] = a[2] * b[0] - a[0] * b[2];
@@ -409,14 +338,13 @@ __device__ void step_warp(IterState* st, const double* S, const float* Shi, cons
     rm(tmp, gw);
     cr(tt, gv, tmp);
     for (int r = 0; r < 3; ++r) gw[r] += tmp[r];
-    // w~ = R^T g_w, v~ = -c x w~ + R^T (g_v - t x g_w)
+    // the ascent direction in the centred coordinates of Z's frame
+    const float rho2 = (float)st->rho2 + ellf * ellf;
     float wt[3], vt[3];
-    rtm(gw, wt);
-    cr(tt, gw, tmp);
-    for (int r = 0; r < 3; ++r) tmp[r] = gv[r] - tmp[r];
-    rtm(tmp, vt);
-    cr(cc, wt, tmp2);
-    for (int r = 0; r < 3; ++r) vt[r] -= tmp2[r];
+    for (int r = 0; r < 3; ++r) {
+        wt[r] = gcw[r] / rho2;
+        vt[r] = gcv[r];
+    }
     auto symqf = [&](int base, const float* a, const float* b) {
         return sf(base) * a[0] * b[0] + sf(base + 1) * a[1] * b[1] + sf(base + 2) * a[2] * b[2] +
                sf(base + 3) * (a[0] * b[1] + a[1] * b[0]) + sf(base + 4) * (a[0] * b[2] + a[2] * b[0]) +
@@ -444,21 +372,30 @@ __device__ void step_warp(IterState* st, const double* S, const float* Shi, cons
     const float hvv = symqf(ST_Q, vt, vt) * il4 - sf(ST_W) * vv * il2;
     const float Fpp = kapf * (hww + 2.0f * hwv + hvv);
     const float g[6] = {gw[0], gw[1], gw[2], gv[0], gv[1], gv[2]};
-    float gn2 = 0.0f;
-    for (int q = 0; q < 6; ++q) gn2 += g[q] * g[q];
-    const float wn = sqrtf(gw[0] * gw[0] + gw[1] * gw[1] + gw[2] * gw[2]);
-    const float vn = sqrtf(gv[0] * gv[0] + gv[1] * gv[1] + gv[2] * gv[2]);
+    const float Fp = (gcw[0] * wt[0] + gcw[1] * wt[1] + gcw[2] * wt[2]) + vv;   // F' along the direction
+    const float wn = sqrtf(ww);
+    const float vn = sqrtf(vv);
     float t = 0.0f;
-    if (gn2 > 0.0f) {
-        t = (Fpp < 0.0f) ? gn2 / (-Fpp) : 1e-3f / sqrtf(gn2);
-        const float max_tr = st->max_step_trans > 0.0 ? (float)st->max_step_trans : 0.5f * ellf;
-        const float max_rot = (float)st->max_step_rot;
-        if (t * wn > max_rot) t = max_rot / wn;
-        if (t * vn > max_tr) t = max_tr / vn;
+    if (Fp > 0.0f) {
+        const float delta = st->max_step_trans > 0.0 ? (float)st->max_step_trans : 0.5f * ellf;
+        const float speed = wn * (float)st->rmax + vn;   // bound on the speed of Z's points
+        float tmax = speed > 0.0f ? delta / speed : 3.0e38f;
+        if (wn > 0.0f && tmax * wn > (float)st->max_step_rot) tmax = (float)st->max_step_rot / wn;
+        t = (Fpp < 0.0f) ? fminf(Fp / (-Fpp), tmax) : tmax;
     }
-    // ---- FP64: exp(t g^) and T <- exp(t g^) T, across lanes ---------------
+    // the step in the origin's coordinates: xi = t (R w~, R v~ + p x R w~), p = R c + t
+    float om[3], uo[3], pc[3], pxo[3];
+    rm(wt, om);
+    rm(vt, uo);
+    rm(cc, pc);
+    for (int r = 0; r < 3; ++r) pc[r] += tt[r];
+    cr(pc, om, pxo);
+    // ---- FP64: exp(xi^) and T <- exp(xi^) T, across lanes ------------------
     double xd[6];
-    for (int q = 0; q < 6; ++q) xd[q] = (double)(t * g[q]);
+    for (int q = 0; q < 3; ++q) {
+        xd[q] = (double)(t * om[q]);
+        xd[3 + q] = (double)(t * (uo[q] + pxo[q]));
+    }
     const double th2 = xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2];
     double coef = 0.0;
     if (th2 < 0.25) {
@@ -511,7 +448,7 @@ __device__ void step_warp(IterState* st, const double* S, const float* Shi, cons
         st->pairs_total += (long long)pairs;
         st->cands_total += (long long)cands;
         st->Fpp = (double)Fpp;
-        st->gnorm = (double)sqrtf(gn2);
+        st->gnorm = (double)sqrtf(fmaxf(Fp, 0.0f));
         st->t = (double)t;
         st->srot = srot;
         st->strans = strans;

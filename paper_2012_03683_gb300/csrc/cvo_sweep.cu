@@ -74,6 +74,10 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
 
     const int nitems = L.nitems;
     const int nblk = P.b1 - P.b0, bloc = (int)blockIdx.x - P.b0;
+    // a batch that re-split its grid may leave blocks past a pair's range
+    // (the pair has fewer items than blocks): they have no work, and no
+    // finalize reads their partials (a single pair's range is the whole grid)
+    if (bloc >= nblk) return;
     for (int item = bloc * kSweepWarps + warp; item < nitems; item += nblk * kSweepWarps) {
         Moments mo;
         float p[3];

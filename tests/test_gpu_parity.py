@@ -243,7 +243,9 @@ def one_step_parity(X, Z, FX, FZ, blocks, cm, tr, T_final, ks, anneal_kw):
 
 
 def test_register_cube_dense_matches_oracle():
-    """The single-pair cube workload (2,000 points, dense, 50 iterations)."""
+    """The single-pair cube workload (2,000 points, dense, <= 50 iterations):
+    the GPU and the oracle stop at the same iteration on the same pose, and,
+    since Z is X moved by the true motion, both end on the true pose."""
     p = scenes.cube_pair()
     kw = dict(ell=0.1, cutoff_mult=0.0, max_iters=50)
     h = cvo.CVO(blocks=p.blocks, **kw)
@@ -255,10 +257,13 @@ def test_register_cube_dense_matches_oracle():
     er, et = pose_err(T_gpu, T_orc)
     assert er <= POSE_TOL and et <= POSE_TOL, (er, et)
     np.testing.assert_allclose(tr_gpu[:, 1], tr_orc[:, 1], rtol=1e-5)
-    one_step_parity(p.X, p.Z, p.FX, p.FZ, p.blocks, 0.0, tr_gpu, T_gpu, [0, 1, 10, 25, 49], {})
-    # ascent: F never decreases, and the pose moves towards the true one
+    last = tr_gpu.shape[0] - 1
+    one_step_parity(p.X, p.Z, p.FX, p.FZ, p.blocks, 0.0, tr_gpu, T_gpu, sorted({0, 1, last // 2, last}), {})
+    # ascent: F never decreases; the registration converged onto the true pose
     assert np.all(np.diff(tr_gpu[:, 1]) > -1e-6 * tr_gpu[1:, 1])
-    assert pose_err(T_gpu, p.T_true)[0] < pose_err(np.eye(4), p.T_true)[0]
+    assert info["status"] == 0
+    er, et = pose_err(T_gpu, p.T_true)
+    assert er <= POSE_TOL and et <= POSE_TOL, (er, et)
 
 
 def test_register_converges_to_known_transform():

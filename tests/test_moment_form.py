@@ -111,3 +111,33 @@ def test_moment_form_matches_direct_form(cm, blocks):
         fpp = oracle.evaluate(X, Z, T, direction=d, **kw)["Fpp"]
         assert float(d @ H @ d) == pytest.approx(fpp, rel=1e-9)
     assert np.allclose(H, H.T, atol=1e-9 * np.abs(H).max())
+
+
+def test_step_direction_from_the_centred_gradient_matches_the_oracles_rule():
+    """The CUDA step takes the ascent direction in Z's centred coordinates,
+    (w~, v~) = (gc_w / rho^2, gc_v) with gc the centred gradient the
+    statistics give, and maps it to the left perturbation as
+    (R w~, R v~ + p x R w~), p = R c + t; the oracle forms it from the
+    origin-based gradient g as (h_w / rho^2, h_u + p x h_w / rho^2) with
+    h = (g_w + g_v x p, g_v).  With c the centroid of Z both are the same
+    vector, and F' = g . d equals |gc_w|^2 / rho^2 + |gc_v|^2."""
+    r = np.random.Generator(np.random.PCG64(33))
+    n, m = 30, 45
+    X = r.uniform(-1, 1, size=(n, 3)) + np.array([20.0, -5.0, 40.0])
+    Z = r.uniform(-1, 1, size=(m, 3)) + np.array([19.5, -5.2, 40.3])
+    T = oracle.se3_exp(np.concatenate([r.normal(size=3) * 0.05, r.normal(size=3) * 0.2]))
+    ell = 0.5
+    c = Z.mean(axis=0)
+    rho2 = np.mean(np.sum((Z - c) ** 2, axis=1)) + ell ** 2
+    S = moment_stats(X, Z, np.zeros((n, 0)), np.zeros((m, 0)), T, ell, 0.0, [], c)
+    g, _ = assemble(S, T, ell, c)
+    ExP = np.array([S["Ep"][1, 2] - S["Ep"][2, 1], S["Ep"][2, 0] - S["Ep"][0, 2], S["Ep"][0, 1] - S["Ep"][1, 0]])
+    gc_w, gc_v = ExP / ell ** 2, -S["E"] / ell ** 2
+    R, t = T[:3, :3], T[:3, 3]
+    p = R @ c + t
+    wt, vt = gc_w / rho2, gc_v
+    d_kernel = np.concatenate([R @ wt, R @ vt + np.cross(p, R @ wt)])
+    hw = g[:3] + np.cross(g[3:], p)
+    d_oracle = np.concatenate([hw / rho2, g[3:] + np.cross(p, hw / rho2)])
+    np.testing.assert_allclose(d_kernel, d_oracle, rtol=0, atol=1e-10 * np.abs(d_oracle).max())
+    assert float(g @ d_oracle) == pytest.approx(gc_w @ gc_w / rho2 + gc_v @ gc_v, rel=1e-10)
