@@ -163,6 +163,19 @@ cvo_status cvo_metric(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, cons
 cvo_status cvo_cosine(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16],
                       const double* norms2_in, double* cos_theta, double* norms2_out);
 
+/* The exact indicator cos_theta of Eq. (indicator) at lengthscale params.ell
+ * (as cvo_cosine computes it, the norms recomputed) and its derivative with
+ * respect to the lengthscale, for callers that treat l as a variable of
+ * their own objective (the paper mentions an adaptive lengthscale, Sec. VI):
+ *   dcos/dl = cos (F'_XZ / F_XZ - (F'_XX / F_XX + F'_ZZ / F_ZZ) / 2),
+ * F' = dF/dl of each of the three double sums (the pair set held fixed, as
+ * in cvo_backward).  Empty clouds, or a zero numerator, give dcos/dl = 0.
+ * The cosine itself rises towards its l -> infinity limit on typical clouds
+ * (every geometric kernel value tends to 1), so it does not fix l on its own.
+ * Cost: three evaluations and three gradient sweeps. */
+cvo_status cvo_cosine_dell(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], double* cos_theta,
+                           double* dcos_dell);
+
 /* F, gradient, Hessian, indicator and pair counts in one sweep. */
 cvo_status cvo_evaluate(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], cvo_eval* out);
 
@@ -332,6 +345,18 @@ cvo_status cvo_apply_tuning(cvo_handle h, const cvo_tuning* t);
  * new handles (CVO_GRAPH=0 means host). */
 enum { CVO_LOOP_HOST = 0, CVO_LOOP_GRAPH = 1, CVO_LOOP_PERSISTENT = 2 };
 cvo_status cvo_set_loop(cvo_handle h, int mode);
+
+/* Failure injection for the persistent loop (CVO_LOOP_PERSISTENT), so that
+ * its error path can be tested without a fault: for the handle's next
+ * registration only, the last block of the persistent kernel leaves at grid
+ * barrier number `barrier` (counted from 0 over the whole loop; three per
+ * iteration) instead of arriving, and every grid barrier gives up after
+ * poll_limit polls (> 0; about 1 us each) instead of the default of
+ * seconds.  The blocks still waiting give up, the kernel returns and the
+ * registration reports CVO_ERR_TIMEOUT; the handle stays usable.  No other
+ * loop mode is affected; barrier < 0 clears a pending injection.  The paper
+ * has no counterpart. */
+cvo_status cvo_inject_barrier_stall(cvo_handle h, int barrier, unsigned poll_limit);
 
 /* Device time (ms) of the handle's last registration's sweeps when timing
  * is on (cvo_set_timing): in the graph and host modes CUDA events around

@@ -284,3 +284,25 @@ def register_sequence(frames, ell_first, T_first=None, *, ell, **kw):
         infos.append(info)
         T_abs.append(T_abs[-1] @ T)
     return T_rel, T_abs, infos
+
+
+def cosine_ell(X, Z, T, FX=None, FZ=None, *, ell, **kw):
+    """The exact indicator of Eq. (indicator) as a function of the
+    lengthscale, and its derivative: cos(l) = F_XZ / sqrt(F_XX F_ZZ), the
+    norms the double sum of each cloud with itself at the identity, and
+        dcos/dl = cos (F'_XZ / F_XZ - (F'_XX / F_XX + F'_ZZ / F_ZZ) / 2)
+    with F' = dF/dl of each sum (orc_backward's dell, the pair set held
+    fixed).  Returns (cos, dcos/dl); an empty cloud gives (0, 0)."""
+    n, m = np.asarray(X).reshape(-1, 3).shape[0], np.asarray(Z).reshape(-1, 3).shape[0]
+    if n == 0 or m == 0:
+        return 0.0, 0.0
+    I = np.eye(4)
+    terms = []
+    for A, B, FA, FB, TT in ((X, Z, FX, FZ, T), (X, X, FX, FX, I), (Z, Z, FZ, FZ, I)):
+        F = evaluate(A, B, TT, FX=FA, FZ=FB, ell=ell, **kw)["F"]
+        dF = backward(A, B, TT, FX=FA, FZ=FB, ell=ell, **kw)["dell"]
+        terms.append((F, dF))
+    (fxz, dxz), (fxx, dxx), (fzz, dzz) = terms
+    c = fxz / np.sqrt(fxx * fzz)
+    return c, c * (dxz / fxz - 0.5 * (dxx / fxx + dzz / fzz))
+

@@ -32,7 +32,7 @@ __all__ = ["CVO", "cvo_create", "cvo_destroy", "cvo_set_params", "cvo_inner_prod
            "cvo_autotune", "cvo_get_tuning", "cvo_apply_tuning", "cvo_set_loop",
            "cvo_sweep_time", "cvo_last_error", "cvo_version", "cvo_kernel_launches", "load_library", "Status",
            "CvoError", "cvo_shard_begin", "cvo_shard_sweep", "cvo_shard_step", "cvo_shard_end", "shard_rows",
-           "register_sharded", "SHARD_STATS"]
+           "register_sharded", "SHARD_STATS", "cvo_cosine_dell", "cosine_fn", "cvo_inject_barrier_stall"]
 
 MAX_BLOCKS = 4
 TRACE_STRIDE = 22
@@ -119,6 +119,7 @@ def load_library(build_if_missing: bool = True):
     lib.cvo_gradient.argtypes = [vp, P(Cloud), P(Cloud), vp, vp, P(ctypes.c_double)]
     lib.cvo_evaluate.argtypes = [vp, P(Cloud), P(Cloud), vp, P(Eval)]
     lib.cvo_cosine.argtypes = [vp, P(Cloud), P(Cloud), vp, vp, P(ctypes.c_double), vp]
+    lib.cvo_cosine_dell.argtypes = [vp, P(Cloud), P(Cloud), vp, P(ctypes.c_double), P(ctypes.c_double)]
     for name in ("cvo_backward", "cvo_metric_backward"):
         getattr(lib, name).argtypes = [vp, P(Cloud), P(Cloud), vp, ctypes.c_double, vp, vp, vp, vp,
                                        P(ctypes.c_double), ctypes.c_int]
@@ -132,6 +133,7 @@ def load_library(build_if_missing: bool = True):
     lib.cvo_sweep_time.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int)]
     lib.cvo_autotune.argtypes = [vp, P(Cloud), P(Cloud), vp, P(Tuning)]
     lib.cvo_set_loop.argtypes = [vp, ctypes.c_int]
+    lib.cvo_inject_barrier_stall.argtypes = [vp, ctypes.c_int, ctypes.c_uint]
     lib.cvo_shard_begin.argtypes = [vp, P(Cloud), P(Cloud), ctypes.c_longlong, vp]
     lib.cvo_shard_sweep.argtypes = [vp, vp]
     lib.cvo_shard_step.argtypes = [vp, vp, P(ctypes.c_int)]
@@ -143,6 +145,7 @@ def load_library(build_if_missing: bool = True):
                  "cvo_register_sequence",
                  "cvo_register_batch", "cvo_get_trace", "cvo_set_timing", "cvo_sweep_time", "cvo_autotune",
                  "cvo_get_tuning", "cvo_apply_tuning", "cvo_set_loop", "cvo_shard_begin", "cvo_shard_sweep",
+                 "cvo_cosine_dell", "cvo_inject_barrier_stall",
                  "cvo_shard_step", "cvo_shard_end"):
         getattr(lib, name).restype = ctypes.c_int
     lib.cvo_last_error.restype = ctypes.c_char_p
@@ -366,6 +369,18 @@ def cvo_cosine(h, X, Z, T, FX=None, FZ=None, norms2=None):
     return c.value, (float(nout[0]), float(nout[1]))
 
 
+def cvo_cosine_dell(h, X, Z, T, FX=None, FZ=None):
+    """The exact indicator of Eq. (indicator) and its derivative with respect
+    to the lengthscale: returns (cos_theta, dcos/dl)."""
+    cx, cz, keep = _clouds(X, Z, FX, FZ)
+    Tm = _pose(T)
+    c = ctypes.c_double()
+    d = ctypes.c_double()
+    _check(load_library().cvo_cosine_dell(h, ctypes.byref(cx), ctypes.byref(cz), Tm.ctypes.data, ctypes.byref(c),
+                                          ctypes.byref(d)))
+    return c.value, d.value
+
+
 def cvo_inner_product(h, X, Z, T, FX=None, FZ=None) -> float:
     cx, cz, keep = _clouds(X, Z, FX, FZ)
     Tm = _pose(T)
@@ -542,6 +557,12 @@ LOOP_MODES = {"host": 0, "graph": 1, "persistent": 2}
 def cvo_set_loop(h, mode):
     """Registration loop of a single pair: "graph" (default), "persistent" or "host"."""
     return _check(load_library().cvo_set_loop(h, LOOP_MODES[mode] if isinstance(mode, str) else int(mode)))
+
+
+def cvo_inject_barrier_stall(h, barrier, poll_limit=4096):
+    """Failure injection for the persistent loop's next registration (see
+    cvo_inject_barrier_stall in cvo.h); barrier < 0 clears it."""
+    return _check(load_library().cvo_inject_barrier_stall(h, int(barrier), int(poll_limit)))
 
 
 def cvo_get_tuning(h) -> dict:
@@ -739,3 +760,44 @@ def metric_fn(cvo: "CVO", X, Z, T, FX=None, FZ=None, ell=None):
     """Differentiable indicator i_theta of Eq. (indicator_actual), with the
     arguments of inner_product_fn."""
     return CVOMetric().apply(X, Z, FX, FZ, ell, T, cvo)
+
+
+def _cosine_function():
+    torch = _torch()
+    if torch is None:  # pragma: no cover
+        raise RuntimeError("the differentiable form needs PyTorch")
+
+    class _Cos(torch.autograd.Function):
+        """The exact indicator of Eq. (indicator) as a function of the
+        lengthscale (the clouds, features and pose are constants here); the
+        value and dcos/dl come from cvo_cosine_dell."""
+
+        @staticmethod
+        def forward(ctx, ell, X, Z, FX, FZ, T, cvo):
+            p = Params.from_buffer_copy(cvo.params)
+            p.ell = float(ell)
+            cvo_set_params(cvo.h, p)
+            try:
+                c, d = cvo_cosine_dell(cvo.h, X, Z, T, FX, FZ)
+            finally:
+                cvo_set_params(cvo.h, cvo.params)
+            ctx.d = d
+            return torch.tensor(c, dtype=ell.dtype, device=ell.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            return g * ctx.d, None, None, None, None, None, None
+
+    return _Cos
+
+
+def cosine_fn(cvo: "CVO", X, Z, T, FX=None, FZ=None, ell=None):
+    """Differentiable exact indicator cos_theta(l) of Eq. (indicator): ell is
+    a scalar tensor (requires_grad for dcos/dl); the clouds, features and
+    pose are held constant."""
+    if "cos" not in _fn_cache:
+        _fn_cache["cos"] = _cosine_function()
+    torch = _torch()
+    if ell is None:
+        ell = torch.tensor(cvo.params.ell, dtype=torch.float64)
+    return _fn_cache["cos"].apply(ell, X, Z, FX, FZ, T, cvo)

@@ -186,6 +186,9 @@ struct cvo_handle_s {
     int chunk_len = kChunkLen;
     // an X-row shard registration in progress (cvo_shard_begin .. cvo_shard_end)
     int shard_active = 0;
+    // failure injection for the next persistent registration (cvo_inject_barrier_stall)
+    int inj_leave_at = -1;
+    unsigned inj_polls = 0;
     int shard_nb = 0;
     SweepArgs shard_a{};
     LevelDesc* shard_levels = nullptr;   // non-NULL: the items are re-planned beside every step
@@ -1063,8 +1066,12 @@ cvo_status run_register(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
             ensure_events(h, 1);
             CVO_CUDA(cudaEventRecord(h->evs[0], h->s));
         }
+        const int leave_at = h->inj_leave_at;
+        const unsigned polls = h->inj_polls;
+        h->inj_leave_at = -1;   // one registration only
+        h->inj_polls = 0;
         CVO_CUDA(launch_register_persistent(a, (unsigned*)h->counters.p, (unsigned*)h->gidx.p, h->chunk_len, trace,
-                                            grid, h->s));
+                                            grid, leave_at, polls, h->s));
         if (h->timing) CVO_CUDA(cudaEventRecord(h->evs[1], h->s));
         CVO_CUDA(cudaMemcpyAsync(h->h_misc + 40, (unsigned*)h->counters.p + 4, sizeof(unsigned), cudaMemcpyDeviceToHost,
                                  h->s));
@@ -1736,6 +1743,43 @@ cvo_status cvo_cosine(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, cons
     return CVO_OK;
 }
 
+cvo_status cvo_cosine_dell(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], double* cos_theta,
+                           double* dcos_dell)
+{
+    g_err.clear();
+    if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
+    if (!cos_theta || !dcos_dell) return fail(CVO_ERR_INVALID_ARG, "cos_theta or dcos_dell is NULL");
+    const int D = feat_dim(h->p);
+    CVO_TRY(check_cloud(X, "X", D));
+    CVO_TRY(check_cloud(Z, "Z", D));
+    CVO_TRY(check_pose(T, "T"));
+    DeviceGuard g(h->device);
+    *cos_theta = 0.0;
+    *dcos_dell = 0.0;
+    if (X->n == 0 || Z->n == 0) return CVO_OK;
+    static const double I[16] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1};
+    // the three double sums of Eq. (indicator) and their l-derivatives (the
+    // gradient sweep of one cloud gives dF/dl = sum w d^2 / l^3)
+    const cvo_cloud* A[3] = {X, X, Z};
+    const cvo_cloud* B[3] = {Z, X, Z};
+    const double* P[3] = {T, I, I};
+    double F[3], dF[3];
+    for (int k = 0; k < 3; ++k) {
+        cvo_eval e;
+        CVO_TRY(run_eval(h, A[k], B[k], P[k], &e));
+        F[k] = e.F;
+        CVO_TRY(run_backward(h, A[k], B[k], P[k], 1.0, nullptr, nullptr, nullptr, nullptr, &dF[k], 0));
+    }
+    if (!(F[1] > 0.0) || !(F[2] > 0.0) || F[0] == 0.0) {
+        *cos_theta = (F[1] > 0.0 && F[2] > 0.0) ? F[0] / std::sqrt(F[1] * F[2]) : 0.0;
+        return CVO_OK;
+    }
+    const double c = F[0] / std::sqrt(F[1] * F[2]);
+    *cos_theta = c;
+    *dcos_dell = c * (dF[0] / F[0] - 0.5 * (dF[1] / F[1] + dF[2] / F[2]));
+    return CVO_OK;
+}
+
 cvo_status cvo_inner_product(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], double* F)
 {
     if (!F) return fail(CVO_ERR_INVALID_ARG, "F is NULL");
@@ -1969,6 +2013,16 @@ cvo_status cvo_set_loop(cvo_handle h, int mode)
     if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
     if (mode < CVO_LOOP_HOST || mode > CVO_LOOP_PERSISTENT) return fail(CVO_ERR_INVALID_ARG, "unknown loop mode %d", mode);
     h->loop_mode = mode;
+    return CVO_OK;
+}
+
+cvo_status cvo_inject_barrier_stall(cvo_handle h, int barrier, unsigned poll_limit)
+{
+    g_err.clear();
+    if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
+    if (barrier >= 0 && poll_limit == 0) return fail(CVO_ERR_INVALID_ARG, "poll_limit must be > 0 with a barrier");
+    h->inj_leave_at = barrier >= 0 ? barrier : -1;
+    h->inj_polls = barrier >= 0 ? poll_limit : 0;
     return CVO_OK;
 }
 

@@ -245,8 +245,11 @@ cudaError_t launch_sum_f32(const float* v, int n, double* out, cudaStream_t s);
 // before the launch (ctl[4] != 0 afterwards: a grid barrier gave up); nch:
 // one unsigned per query group of the largest level.
 cudaError_t persistent_grid(const SweepArgs& sw, int* nblocks);
+// leave_at >= 0: the last block leaves at that grid barrier instead of
+// arriving (failure injection); spin_limit: polls before a barrier gives up
+// (0: the default of seconds).
 cudaError_t launch_register_persistent(const SweepArgs& sw, unsigned* ctl, unsigned* nch, int chunk_len, double* trace,
-                                       int nblocks, cudaStream_t s);
+                                       int nblocks, int leave_at, unsigned spin_limit, cudaStream_t s);
 
 // Work-item planning of one grid level (cvo_sweep.cu): per query group the
 // length of its candidate stream at the state's pose for cutoff radius rc,

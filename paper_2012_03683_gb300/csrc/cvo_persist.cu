@@ -26,7 +26,8 @@
 // block that gives up sets an error flag, every block leaves the loop on that
 // flag, and the host reports CVO_ERR_TIMEOUT.  (The cooperative launch
 // guarantees that all blocks are resident, so the limit is a guard, not a
-// path.)
+// path; cvo_inject_barrier_stall makes one block leave instead of arriving,
+// with a short limit, so that a test can take that path.)
 #include "cvo_step_dev.cuh"
 #include "cvo_sweep_dev.cuh"
 
@@ -42,11 +43,14 @@ struct PersistArgs {
     unsigned* nch;                // chunk count per query group (the largest level's group count)
     int chunk_len;
     double* trace;
+    unsigned spin_limit;          // polls of a barrier before it gives up
+    int leave_at;                 // failure injection: >= 0, the last block leaves the kernel at this
+                                  // grid barrier (counted from 0) instead of arriving; -1: off
 };
 
 // Grid barrier over all blocks of a cooperative launch.  Returns false if
 // the wait gave up or another block has (the error flag is set).
-__device__ bool grid_barrier(unsigned* ctl, unsigned nblocks)
+__device__ bool grid_barrier(unsigned* ctl, unsigned nblocks, unsigned spin_limit)
 {
     __syncthreads();
     __shared__ int ok;
@@ -68,7 +72,7 @@ __device__ bool grid_barrier(unsigned* ctl, unsigned nblocks)
                     good = 0;
                     break;
                 }
-                if (++polls > kSpinLimit) {
+                if (++polls > spin_limit) {
                     atomicExch(ctl + 4, 1u);
                     good = 0;
                     break;
@@ -104,6 +108,11 @@ __global__ void __launch_bounds__(kSweepWarps * 32, 4) k_register(PersistArgs a)
     float4* stage = stage_mem + (size_t)warp * 2 * 32 * rs;
     const unsigned nblocks = gridDim.x;
     const int ngroups = ((int)nblocks + kGroupBlocks - 1) / kGroupBlocks;
+    int barrier = 0;   // grid barriers passed (the failure injection counts them)
+    auto sync_grid = [&]() {
+        if (a.leave_at == barrier++ && blockIdx.x == nblocks - 1) return false;   // leaves without arriving
+        return grid_barrier(a.ctl, nblocks, a.spin_limit);
+    };
 
     for (;;) {
         // the state as block 0 left it (read around the L1: another SM wrote it)
@@ -136,7 +145,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32, 4) k_register(PersistArgs a)
                 atomicMax(a.ctl + 5, (unsigned)c);
             }
         }
-        if (!grid_barrier(a.ctl, nblocks)) return;
+        if (!sync_grid()) return;
 
         // ---- sweep: chunk-major slots round robin over the grid's warps -----
         unsigned npairs = 0, ncand = 0;
@@ -156,7 +165,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32, 4) k_register(PersistArgs a)
             stat_acc_add(acc, mo, p, act, lane);
         }
         sweep_epilogue(acc, npairs, ncand, a.sw, (int)blockIdx.x, (int)nblocks);
-        if (!grid_barrier(a.ctl, nblocks)) return;
+        if (!sync_grid()) return;
 
         // ---- step (block 0) ---------------------------------------------------
         if (blockIdx.x == 0) {
@@ -191,7 +200,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32, 4) k_register(PersistArgs a)
                 reinterpret_cast<unsigned long long*>(st)[i] = sbuf[i];
             __threadfence();
         }
-        if (!grid_barrier(a.ctl, nblocks)) return;
+        if (!sync_grid()) return;
     }
 }
 
@@ -249,7 +258,7 @@ cudaError_t persistent_grid(const SweepArgs& sw, int* nblocks)
 }
 
 cudaError_t launch_register_persistent(const SweepArgs& sw, unsigned* ctl, unsigned* nch, int chunk_len, double* trace,
-                                       int nblocks, cudaStream_t s)
+                                       int nblocks, int leave_at, unsigned spin_limit, cudaStream_t s)
 {
     PersistArgs a{};
     a.sw = sw;
@@ -257,6 +266,8 @@ cudaError_t launch_register_persistent(const SweepArgs& sw, unsigned* ctl, unsig
     a.nch = nch;
     a.chunk_len = chunk_len;
     a.trace = trace;
+    a.leave_at = leave_at;
+    a.spin_limit = spin_limit > 0 ? spin_limit : kSpinLimit;
     size_t smem = 0;
     int nb = nblocks;
     return dispatch(sw.fc, a, &nb, &smem, false, s);

@@ -47,6 +47,7 @@ def test_null_handle_rejected_by_every_entry_point(lib):
         "cvo_metric_backward": lambda: lib.cvo_metric_backward(None, None, None, T, 1.0, None, None, None, None,
                                                                ref(d), 0),
         "cvo_cosine": lambda: lib.cvo_cosine(None, None, None, T, None, ref(d), None),
+        "cvo_cosine_dell": lambda: lib.cvo_cosine_dell(None, None, None, T, ref(d), ref(d)),
         "cvo_register_pair": lambda: lib.cvo_register_pair(None, None, None, T, T, ref(info)),
         "cvo_register_batch": lambda: lib.cvo_register_batch(None, 1, None, None, T, T, None),
         "cvo_register_sequence": lambda: lib.cvo_register_sequence(None, 2, None, 0.3, None, None, None, None),
@@ -56,6 +57,7 @@ def test_null_handle_rejected_by_every_entry_point(lib):
         "cvo_get_tuning": lambda: lib.cvo_get_tuning(None, ref(tun)),
         "cvo_apply_tuning": lambda: lib.cvo_apply_tuning(None, ref(tun)),
         "cvo_set_loop": lambda: lib.cvo_set_loop(None, 1),
+        "cvo_inject_barrier_stall": lambda: lib.cvo_inject_barrier_stall(None, 1, 100),
         "cvo_set_timing": lambda: lib.cvo_set_timing(None, 1),
         "cvo_sweep_time": lambda: lib.cvo_sweep_time(None, ref(d), ref(i)),
     }

@@ -84,3 +84,29 @@ def test_cosine_edge_cases():
     assert c0 == 0.0 and n0[0] == 0.0
     with pytest.raises(cvo.CvoError):
         h.cosine(dev(X), dev(X), np.eye(4), norms2=(-1.0, 1.0))
+
+
+@pytest.mark.parametrize("cm", [0.0, 3.0])
+def test_cosine_lengthscale_derivative_matches_oracle(cm):
+    """cvo_cosine_dell against the oracle's cosine_ell (Eq. indicator and its
+    l-derivative), dense and with a cutoff, and through cosine_fn's autograd."""
+    p = scenes.room_pair()
+    sel = np.random.Generator(np.random.PCG64(41)).permutation(p.n)[:1500]
+    X, Z, FX, FZ = p.X[sel], p.Z[sel], p.FX[sel], p.FZ[sel]
+    T = p.T_true
+    ell = 0.12
+    with cvo.CVO(blocks=p.blocks, ell=ell, cutoff_mult=cm) as h:
+        c, d = cvo.cvo_cosine_dell(h.h, dev(X), dev(Z), T, dev(FX), dev(FZ))
+        lt = torch.tensor(ell, dtype=torch.float64, requires_grad=True)
+        ct = cvo.cosine_fn(h, dev(X), dev(Z), T, dev(FX), dev(FZ), ell=lt)
+        ct.backward()
+    co, do = oracle.cosine_ell(X, Z, T, FX, FZ, ell=ell, blocks=p.blocks, cutoff_mult=cm)
+    assert c == pytest.approx(co, rel=1e-5)
+    # with a cutoff, a pair whose FP32 and FP64 distance tests disagree moves
+    # dF/dl by at most w d^2 / l^3 <= e^-4.5 9 / l: none lie that close here
+    if cm > 0:
+        for A, B, TT in ((X, Z, T), (X, X, np.eye(4)), (Z, Z, np.eye(4))):
+            rc2 = (cm * ell) ** 2
+            assert oracle.count_band(A, B, TT, rc2 * (1 - 1e-5), rc2 * (1 + 1e-5)) == 0
+    assert d == pytest.approx(do, rel=1e-4)
+    assert ct.item() == pytest.approx(c, rel=1e-12) and lt.grad.item() == pytest.approx(d, rel=1e-12)

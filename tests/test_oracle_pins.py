@@ -799,3 +799,63 @@ def test_feature_cutoff_input_gradients_by_central_differences():
     assert g["dFX"][i, 1] == pytest.approx(fd(2, (i, 1)), rel=1e-6, abs=1e-9)   # colour
     assert g["dFX"][i, 4] == pytest.approx(fd(2, (i, 4)), rel=1e-6, abs=1e-9)   # label
     assert g["dFZ"][j, 0] == pytest.approx(fd(3, (j, 0)), rel=1e-6, abs=1e-9)   # colour
+
+
+def test_cosine_and_its_lengthscale_derivative_in_extended_precision():
+    """The exact indicator of Eq. (indicator) as a function of l, written out
+    as its three double sums in 30-digit arithmetic, and its l-derivative by
+    mpmath's differentiation: oracle.cosine_ell gives both (dense sums, both
+    kinds of feature block, a pose that moves Z)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 30
+    r = rng(61)
+    n, m = 5, 6
+    X = r.uniform(-0.5, 0.5, (n, 3))
+    Z = r.uniform(-0.5, 0.5, (m, 3))
+    FX = np.hstack([r.uniform(0, 1, (n, 3)), r.dirichlet(np.ones(4), n)])
+    FZ = np.hstack([r.uniform(0, 1, (m, 3)), r.dirichlet(np.ones(4), m)])
+    blocks = [("se", 3, 0.3, 1.2), ("dot", 4, 1.0, 1.0)]
+    sigma, ell = 1.1, 0.4
+    T = rand_T(r, 0.2, 0.2)
+    mp = mpmath.mpf
+
+    def feat_k(u, v):
+        return mp(1.2) ** 2 * mpmath.exp(-sum((mp(a) - mp(b)) ** 2 for a, b in zip(u[:3], v[:3])) /
+                                         (2 * mp(0.3) ** 2)) * sum(mp(a) * mp(b) for a, b in zip(u[3:], v[3:]))
+
+    def dsum(A, B, FA, FB, l):
+        s = mp(0)
+        for i in range(len(A)):
+            for j in range(len(B)):
+                e2 = sum((mp(A[i][q]) - mp(B[j][q])) ** 2 for q in range(3))
+                s += mp(sigma) ** 2 * mpmath.exp(-e2 / (2 * l ** 2)) * feat_k(FA[i], FB[j])
+        return s
+
+    Y = transform(T, Z)
+
+    def cos(l):
+        return dsum(X, Y, FX, FZ, l) / mpmath.sqrt(dsum(X, X, FX, FX, l) * dsum(Z, Z, FZ, FZ, l))
+
+    c_ref = float(cos(mp(ell)))
+    d_ref = float(mpmath.diff(cos, mp(ell)))
+    c, d = oracle.cosine_ell(X, Z, T, FX, FZ, ell=ell, blocks=blocks, sigma=sigma, cutoff_mult=0.0)
+    assert c == pytest.approx(c_ref, rel=1e-13)
+    assert c == pytest.approx(oracle.cosine(X, Z, T, FX, FZ, ell=ell, blocks=blocks, sigma=sigma), rel=1e-14)
+    assert d == pytest.approx(d_ref, rel=1e-11)
+    assert abs(d) > 1e-3   # the derivative is not trivially zero here
+
+
+def test_cosine_grows_towards_its_large_lengthscale_limit():
+    """Why the library offers dcos/dl for a caller's own objective but no
+    built-in maximisation of the cosine over l: on independently sampled
+    clouds at the true pose the cosine rises monotonically with l towards
+    the limit of constant functions (every geometric kernel value 1), so it
+    has no interior maximum to fix l by."""
+    import scenes
+    q = scenes.batch_pairs(n_pairs=1, n_range=(400, 400))[0]
+    ells = np.geomspace(0.03, 3.0, 9)
+    vals = [oracle.cosine_ell(q.X, q.Z, q.T_true, q.FX, q.FZ, ell=l, blocks=q.blocks, cutoff_mult=0.0)
+            for l in ells]
+    cs = np.array([v[0] for v in vals])
+    ds = np.array([v[1] for v in vals])
+    assert np.all(np.diff(cs) > 0) and np.all(ds > 0)
