@@ -286,7 +286,7 @@ def plain_section(h, args, torch, flush, reps):
             "ms_per_batch": spread(ms), "timing": "CUDA events around each pass of 64 cvo_register_pair calls"}
 
 
-def street_section(cvo, torch, dev, flush, peaks, peak_src, sms, reps=10):
+def street_section(cvo, torch, dev, flush, peaks, peak_src, sms, reps=10, tuning=None):
     """street-20k: one registration of the 20,000-point street pair (RGB +
     labels in float32, l 0.3 -> 0.05 m annealed, cutoff 3 l, <= 100
     iterations), autotuned, graph loop; then the same registrations with the
@@ -302,7 +302,11 @@ def street_section(cvo, torch, dev, flush, peaks, peak_src, sms, reps=10):
                        f"<= {pr['max_iters']} iterations"}
     stream = torch.cuda.current_stream()
     with cvo.CVO(**kw) as h:
-        out["tuning"] = h.autotune(X, Z, np.eye(4), FX, FZ)
+        if tuning:
+            h.apply_tuning(*tuning)
+            out["tuning"] = dict(h.tuning(), source="--tuning")
+        else:
+            out["tuning"] = h.autotune(X, Z, np.eye(4), FX, FZ)
         for _ in range(3):
             h.register(X, Z, np.eye(4), FX, FZ)
         ms, pairs, iters = [], 0, []
@@ -560,9 +564,11 @@ def main():
     ap.add_argument("--no-cube", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--only", default=None, choices=["street", "cube", "backward", "large"],
+                    help="run only this section and print its JSON (a fixed launch sequence for profiling)")
     ap.add_argument("--tuning", default=None,
-                    help="cell_factor,super_delta,chunk_len for the batch instead of autotuning "
-                         "(fixed launch sequence for profiling)")
+                    help="cell_factor,super_delta,chunk_len for the batch (or, with --only street, the street "
+                         "pair) instead of autotuning (fixed launch sequence for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -575,6 +581,20 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if args.only:
+        peaks, peak_src = load_peaks()
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+        tun = None
+        if args.tuning:
+            cf, sd, ip = args.tuning.split(",")
+            tun = (float(cf), int(sd), int(ip))
+        run = {"street": lambda: street_section(cvo, torch, dev, flush, peaks, peak_src, sms, reps=args.reps,
+                                                tuning=tun),
+               "cube": lambda: cube_section(cvo, torch, dev, flush, reps=args.reps),
+               "backward": lambda: backward_section(cvo, torch, dev, flush, peaks, peak_src, sms, reps=args.reps),
+               "large": lambda: large_section(cvo, torch, dev, flush, reps=args.reps)}[args.only]
+        print(json.dumps({args.only: run()}), flush=True)
+        return
     pairs, kw, config = batch_workload()
     config["parallelism"] = f"replicas x{world}" if world > 1 else "one GPU"
     args_dev = [(torch.tensor(p.X, device=dev), torch.tensor(p.Z, device=dev), np.eye(4),

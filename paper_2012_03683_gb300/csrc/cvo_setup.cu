@@ -411,10 +411,11 @@ __global__ void __launch_bounds__(kZStatsThreads) k_zstats(const float* __restri
     __shared__ double red[kZStatsThreads];
     __shared__ double mean[3];
     __shared__ float mhi[3], mlo[3];
+    float hi[3] = {0.0f, 0.0f, 0.0f}, lo[3] = {0.0f, 0.0f, 0.0f};
+    for (int i = threadIdx.x; i < n; i += kZStatsThreads)   // one pass over the points, three sums
+        for (int a = 0; a < 3; ++a) df_acc(hi[a], lo[a], xyz[3 * (size_t)i + a]);
     for (int a = 0; a < 3; ++a) {
-        float hi = 0.0f, lo = 0.0f;
-        for (int i = threadIdx.x; i < n; i += kZStatsThreads) df_acc(hi, lo, xyz[3 * (size_t)i + a]);
-        block_sum(red, (double)hi + (double)lo);
+        block_sum(red, (double)hi[a] + (double)lo[a]);
         if (threadIdx.x == 0) {
             mean[a] = red[0] / (double)n;
             mhi[a] = (float)mean[a];
@@ -422,17 +423,17 @@ __global__ void __launch_bounds__(kZStatsThreads) k_zstats(const float* __restri
         }
         __syncthreads();
     }
-    float hi = 0.0f, lo = 0.0f, mx = 0.0f;
+    float qhi = 0.0f, qlo = 0.0f, mx = 0.0f;
     for (int i = threadIdx.x; i < n; i += kZStatsThreads) {
         float q = 0.0f;
         for (int a = 0; a < 3; ++a) {
             const float e = __fsub_rn(__fsub_rn(xyz[3 * (size_t)i + a], mhi[a]), mlo[a]);
             q = fmaf(e, e, q);
         }
-        df_acc(hi, lo, q);
+        df_acc(qhi, qlo, q);
         mx = fmaxf(mx, q);
     }
-    block_sum(red, (double)hi + (double)lo);
+    block_sum(red, (double)qhi + (double)qlo);
     const double s2 = red[0];
     __syncthreads();
     red[threadIdx.x] = (double)mx;

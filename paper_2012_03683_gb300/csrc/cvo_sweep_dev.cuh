@@ -182,14 +182,17 @@ struct FeatGeneric {
 // float32 accumulation: the products of bfloat16 values are exact, so this
 // matches the scalar float32 sum up to its order).  Per warp scratch: a
 // 32 x 40 bfloat16 tile (the queries' labels once per item, then each
-// batch's candidate labels) and the 32 x 33 float results.
+// batch's candidate labels) and the 32 x 32 float results, candidate-major
+// with a row stride of 36 floats: the accumulator fragments store without
+// bank conflicts (lane (g, t) of a fragment writes bank g + 8 t) and each
+// candidate's row is read by the 32 lanes from 32 consecutive words.
 template <int DSE>
 struct FeatMMA {
     static constexpr int kL = 19;
     static constexpr int D = DSE + kL;
     static constexpr int kRowBytes = 80;                      // 32 labels + pad: conflict-free fragment loads
     static constexpr int kTileBytes = 32 * kRowBytes;
-    static constexpr int kCsStride = 33;
+    static constexpr int kCsStride = 36;
     static constexpr int kScratch = kTileBytes + 32 * kCsStride * 4;
     struct Q {
         float se[DSE > 0 ? DSE : 1];
@@ -293,11 +296,11 @@ struct FeatMMA {
                         : "+f"(c0), "+f"(c1), "+f"(c2), "+f"(c3)
                         : "r"(q.a[mt][ks][0]), "r"(q.a[mt][ks][1]), "r"(q.a[mt][ks][2]), "r"(q.a[mt][ks][3]),
                           "r"(b[ks][0]), "r"(b[ks][1]));
-                const int r0 = g + 16 * mt, col = 2 * t + 8 * nt;
-                q.cs[r0 * kCsStride + col] = c0;
-                q.cs[r0 * kCsStride + col + 1] = c1;
-                q.cs[(r0 + 8) * kCsStride + col] = c2;
-                q.cs[(r0 + 8) * kCsStride + col + 1] = c3;
+                const int r0 = g + 16 * mt, col = 2 * t + 8 * nt;   // query row, candidate column
+                q.cs[col * kCsStride + r0] = c0;
+                q.cs[(col + 1) * kCsStride + r0] = c1;
+                q.cs[col * kCsStride + r0 + 8] = c2;
+                q.cs[(col + 1) * kCsStride + r0 + 8] = c3;
             }
         }
         __syncwarp();
@@ -317,7 +320,7 @@ struct FeatMMA {
             arg = fmaf(du2, fc.s[0], arg);
             if (du2 > fc.fcut2[0]) in = false;
         }
-        return q.cs[q.lane * kCsStride + c];
+        return q.cs[c * kCsStride + q.lane];
     }
 };
 
@@ -329,11 +332,53 @@ __device__ __forceinline__ int floor_cell(float v, float o, float inv_h)
     return (int)fminf(fmaxf(c, -2.0e9f), 2.0e9f);
 }
 
-// A query group's candidate stream: the runs of grid cells (one per (y, z)
-// cell row) that overlap the group's bounding box grown by the cutoff radius.
+// A query group's candidate stream: for each (y, z) row of grid cells that
+// overlaps the group's bounding box grown by the cutoff radius, the run of
+// the row's cells whose x-range can hold a point within the radius of the
+// box.  A row at (y, z) distance d from the box needs only the x-range of
+// the box grown by sqrt(r^2 - d^2) (none when d > r): the stream covers the
+// box grown by a ball, not by a cube, in whole cells.
 struct Stream {
     int cx0, cx1, cy0, cz0, nry, nruns, total;
 };
+
+// The group's box (Z frame: min xyz, max xyz) and the cutoff radius with its
+// rounding margin, per warp in shared memory (read once per run, so they
+// need not hold registers through the candidate loop).  Warps of up to
+// 1024-thread blocks.
+__device__ __forceinline__ float* stream_box()
+{
+    __shared__ float box[32][8];
+    return box[threadIdx.x >> 5];
+}
+
+// The cells [a, b] of run r (row cy0 + r % nry, cz0 + r / nry) of a stream
+// with a cutoff; a > b when the row is out of reach.  The gaps between the
+// row's cell extent and the box are shrunk, and the radius grown, by margins
+// above the FP32 rounding of the coordinates, so no pair within the cutoff is
+// left out.
+__device__ __forceinline__ void run_cells(const LevelDesc& L, const Stream& s, int r, int& a, int& b)
+{
+    const float* bx = stream_box();
+    const float bmn[3] = {bx[0], bx[1], bx[2]}, bmx[3] = {bx[3], bx[4], bx[5]}, rad = bx[6];
+    const int cy = s.cy0 + r % s.nry, cz = s.cz0 + r / s.nry;
+    const float ylo = L.oy + (float)cy * L.h, zlo = L.oz + (float)cz * L.h;
+    // margins: the rounding of the cell bounds (|origin| + |bound| + h) and of the box
+    const float ty = 4.0e-7f * (fabsf(L.oy) + fabsf(ylo) + L.h + fmaxf(fabsf(bmn[1]), fabsf(bmx[1]))) + 1.0e-6f;
+    const float tz = 4.0e-7f * (fabsf(L.oz) + fabsf(zlo) + L.h + fmaxf(fabsf(bmn[2]), fabsf(bmx[2]))) + 1.0e-6f;
+    const float gy = fmaxf(0.0f, fmaxf(ylo - bmx[1], bmn[1] - (ylo + L.h)) - ty);
+    const float gz = fmaxf(0.0f, fmaxf(zlo - bmx[2], bmn[2] - (zlo + L.h)) - tz);
+    const float w2 = rad * rad - (gy * gy + gz * gz);
+    if (w2 < 0.0f) {
+        a = 1;
+        b = 0;
+        return;
+    }
+    const float w = sqrtf(w2) * 1.0001f;
+    const float tx = 4.0e-7f * fmaxf(fabsf(bmn[0]), fabsf(bmx[0])) + 1.0e-6f;
+    a = max(s.cx0, floor_cell(bmn[0] - w - tx, L.ox, L.inv_h));
+    b = min(s.cx1, floor_cell(bmx[0] + w + tx, L.ox, L.inv_h));
+}
 
 // Warp-uniform.  Returns false when the grown box misses the grid.
 __device__ __forceinline__ bool stream_setup(const LevelDesc& L, int m, bool dense, bool act, const float xh[3],
@@ -374,6 +419,17 @@ __device__ __forceinline__ bool stream_setup(const LevelDesc& L, int m, bool den
         s.cx0 = c0[0]; s.cx1 = c1[0]; s.cy0 = c0[1]; s.cz0 = c0[2];
         s.nry = c1[1] - c0[1] + 1;
         s.nruns = s.nry * (c1[2] - c0[2] + 1);
+        float* bx = stream_box();
+        __syncwarp();   // a previous stream of this warp may still be reading the box
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                bx[q] = mn[q];
+                bx[3 + q] = mx[q];
+            }
+            bx[6] = rc * 1.0001f + 1.0e-6f;
+        }
+        __syncwarp();
     }
     int total = 0;
     for (int b0 = 0; b0 < s.nruns; b0 += 32) {
@@ -383,9 +439,13 @@ __device__ __forceinline__ bool stream_setup(const LevelDesc& L, int m, bool den
             if (dense) {
                 len = m;
             } else {
-                const int cy = s.cy0 + r % s.nry, cz = s.cz0 + r / s.nry;
-                const int row = (cz * L.ny + cy) * L.nx;
-                len = __ldg(L.cell_start + row + s.cx1 + 1) - __ldg(L.cell_start + row + s.cx0);
+                int a, b;
+                run_cells(L, s, r, a, b);
+                if (a <= b) {
+                    const int cy = s.cy0 + r % s.nry, cz = s.cz0 + r / s.nry;
+                    const int row = (cz * L.ny + cy) * L.nx;
+                    len = __ldg(L.cell_start + row + b + 1) - __ldg(L.cell_start + row + a);
+                }
             }
         }
 #pragma unroll
@@ -412,10 +472,14 @@ __device__ __forceinline__ void stream_walk(const LevelDesc& L, int m, bool dens
                 rstart = 0;
                 rlen = m;
             } else {
-                const int cy = s.cy0 + r % s.nry, cz = s.cz0 + r / s.nry;
-                const int row = (cz * L.ny + cy) * L.nx;
-                rstart = __ldg(L.cell_start + row + s.cx0);
-                rlen = __ldg(L.cell_start + row + s.cx1 + 1) - rstart;
+                int a, b;
+                run_cells(L, s, r, a, b);
+                if (a <= b) {
+                    const int cy = s.cy0 + r % s.nry, cz = s.cz0 + r / s.nry;
+                    const int row = (cz * L.ny + cy) * L.nx;
+                    rstart = __ldg(L.cell_start + row + a);
+                    rlen = __ldg(L.cell_start + row + b + 1) - rstart;
+                }
             }
         }
         int incl = rlen;
