@@ -62,7 +62,7 @@ struct DevBuf {
 
 // A stream with its own setup scratch: the pairs of a batch are set up on
 // several of these at once (their kernels are small and overlap).
-constexpr int kSetupLanes = 4;
+constexpr int kSetupLanes = 8;
 struct SetupLane {
     cudaStream_t s = nullptr;
     cudaEvent_t ev = nullptr;

@@ -569,14 +569,17 @@ __device__ __forceinline__ void eval_batch(const float4* sb, int cnt, int rs, ty
                                            float rc2, const FeatConst& fc, Moments& mo, unsigned& npairs, int lane)
 {
     Feat::batch(qf, sb, cnt, rs, lane);
+    // one comparison per candidate: an inactive lane takes no pair, the dense
+    // sum every pair
+    const float lim = act ? (dense ? 3.0e38f : rc2) : -1.0f;
     int c = 0;
     for (; c + 1 < cnt; c += 2) {
         const float4* zr0 = sb + c * rs;
         const float4* zr1 = zr0 + rs;
         const Offset o0 = offset_to(zr0[0], xh, xl);
         const Offset o1 = offset_to(zr1[0], xh, xl);
-        bool in0 = act && (dense || o0.d2 <= rc2);
-        bool in1 = act && (dense || o1.d2 <= rc2);
+        bool in0 = o0.d2 <= lim;
+        bool in1 = o1.d2 <= lim;
         if (__any_sync(kFull, in0 || in1)) {
             float a0 = o0.d2 * sg, a1 = o1.d2 * sg;
             const float m0 = Feat::pair(qf, zr0, c, a0, in0, fc);
@@ -591,7 +594,7 @@ __device__ __forceinline__ void eval_batch(const float4* sb, int cnt, int rs, ty
     if (c < cnt) {
         const float4* zr = sb + c * rs;
         const Offset o = offset_to(zr[0], xh, xl);
-        bool in = act && (dense || o.d2 <= rc2);
+        bool in = o.d2 <= lim;
         if (__any_sync(kFull, in)) {
             float arg = o.d2 * sg;
             const float mult = Feat::pair(qf, zr, c, arg, in, fc);
