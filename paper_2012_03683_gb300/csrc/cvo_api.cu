@@ -101,7 +101,7 @@ struct LevelHost {
 
 constexpr long long kMaxCells = 1LL << 26;
 constexpr int kMiscWords = 64;   // bbox (12), bad flag (1), group totals (<= kMaxLevels), Z's moments (10)
-constexpr int kZStatsWord = 48;  // Z's centroid, mean squared and largest radius: 5 doubles from this word on
+constexpr int kZStatsWord = 48;  // Z's centroid, mean squared and largest radius: 5 raw 8-byte words from here
 static_assert(kZStatsWord % 2 == 0 && kZStatsWord + 10 <= kMiscWords, "Z's moments must fit the scratch slot");
 
 float decode_orderable(unsigned u)
@@ -410,7 +410,7 @@ cvo_status prepare_bbox(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_
     int* bad = (int*)(dev + 12);
     CVO_CUDA(launch_bbox(sg->xyz_x, n, dev + 0, bad, h->s));
     CVO_CUDA(launch_bbox(sg->xyz_z, m, dev + 6, bad, h->s));
-    CVO_CUDA(launch_zstats(sg->xyz_z, m, (double*)(dev + kZStatsWord), h->s));
+    CVO_CUDA(launch_zstats(sg->xyz_z, m, (long long*)(dev + kZStatsWord), h->s));
     if (D > 0) {
         CVO_CUDA(launch_check_feat(sg->feat_x, (long long)n * D, X->feat_dtype == CVO_BF16, bad, h->s));
         CVO_CUDA(launch_check_feat(sg->feat_z, (long long)m * D, Z->feat_dtype == CVO_BF16, bad, h->s));
@@ -439,8 +439,10 @@ cvo_status prepare_build(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo
         zmax[a] = decode_orderable(hm[9 + a]);
     }
     {
+        long long raw[5];
+        std::memcpy(raw, hm + kZStatsWord, sizeof(raw));
         double zs[5];
-        std::memcpy(zs, hm + kZStatsWord, sizeof(zs));
+        decode_zstats(raw, m, zs);
         for (int a = 0; a < 3; ++a) P.zc[a] = zs[a];
         P.zr2 = zs[3];
         P.zrmax = zs[4];

@@ -264,9 +264,14 @@ k_finalize_batch(PairDesc* __restrict__ pairs, int npairs, const float2* __restr
             Slo[threadIdx.x] = lo;
         } else if (threadIdx.x == kStatN || threadIdx.x == kStatN + 1) {
             const int c = threadIdx.x - kStatN;
-            unsigned long long t = 0;
-            for (int b = P.b0; b < P.b1; ++b) t += pc[(size_t)c * cap + b];
-            cs[c] = t;
+            const unsigned long long* row = pc + (size_t)c * cap;
+            unsigned long long t[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // eight loads in flight
+            int b = P.b0;
+            for (; b + 8 <= P.b1; b += 8)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) t[k] += row[b + k];
+            for (; b < P.b1; ++b) t[0] += row[b];
+            cs[c] = ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
         }
         __syncthreads();
         if (threadIdx.x < 32)

@@ -267,8 +267,11 @@ cudaError_t launch_write_items(const LevelDesc* levels, int level, const unsigne
 // setup (cvo_setup.cu)
 cudaError_t launch_bbox(const float* xyz, int n, unsigned* out6, int* bad, cudaStream_t s);
 cudaError_t launch_check_feat(const void* feat, long long count, int bf16, int* bad, cudaStream_t s);
-// centroid (3), mean squared distance from it and largest distance of a cloud's points: 5 doubles
-cudaError_t launch_zstats(const float* xyz, int n, double* out5, cudaStream_t s);
+// a cloud's centroid, mean squared distance from it and largest such
+// distance: raw sums into out (5 words of 8 bytes, zeroed before), which
+// decode_zstats turns into (cx, cy, cz, mean r^2, max r) on the host
+cudaError_t launch_zstats(const float* xyz, int n, long long* out, cudaStream_t s);
+void decode_zstats(const long long* raw, int n, double out5[5]);
 cudaError_t launch_cell_keys(const float* xyz, int n, float ox, float oy, float oz, float inv_h, int nx, int ny,
                              int nz, unsigned* keys, unsigned* vals, cudaStream_t s);
 cudaError_t launch_morton_keys(const float* xyz, int n, float ox, float oy, float oz, float inv_cell,

@@ -2,6 +2,9 @@
 // Z (a stable counting sort by cell key), the Morton order of X and its query
 // groups.  The paper notes that the double sum is sparse (Sec. III-B); the
 // grid is how the sweep visits only the pairs near each query.
+#include <cmath>
+#include <cstring>
+
 #include "cvo_internal.cuh"
 
 namespace cvo {
@@ -377,77 +380,86 @@ __global__ void k_sum_f32(const float* __restrict__ v, int n, double* out)
     }
 }
 
-// hi + lo += v, error-free in FP32 (a double-float accumulator)
-__device__ __forceinline__ void df_acc(float& hi, float& lo, float v)
+// Z's centroid, mean squared distance from it and largest such distance,
+// for the metric and the trust region of the registration step, in two
+// passes over many blocks.  Sums are kept in 64-bit fixed point (integer
+// additions do not depend on their order, so the result is the same run to
+// run whatever the blocks' timing): coordinates in units of 2^-32 m,
+// squared distances in units of 2^-24 m^2.  Each block adds its points' sum
+// (a warp butterfly, then the warps in order) into the output with one
+// atomic add per word; the largest squared distance by an atomic max on its
+// (non-negative) FP32 bit pattern.  out (zeroed before the launch): [0..2]
+// coordinate sums, [3] squared-distance sum (long long), then word 8 the
+// largest squared distance's bits.
+constexpr int kZStatsThreads = 256;
+constexpr float kCoordScale = 4294967296.0f;   // 2^32
+constexpr float kSqScale = 16777216.0f;        // 2^24
+
+__device__ __forceinline__ long long warp_sum_ll(long long v)
 {
-    const float s = __fadd_rn(hi, v);
-    const float bb = __fsub_rn(s, hi);
-    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
-    const float t = __fadd_rn(lo, e);
-    hi = __fadd_rn(s, t);
-    lo = __fsub_rn(t, __fsub_rn(hi, s));
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
-// Fixed-order tree sum of one double per thread over the block (blockDim.x a
-// power of two); the result in red[0].
-__device__ void block_sum(double* red, double v)
+__global__ void __launch_bounds__(kZStatsThreads) k_zsum(const float* __restrict__ xyz, int n, long long* out)
 {
-    red[threadIdx.x] = v;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-}
-
-// The centroid of a cloud, the mean squared distance of its points from it
-// and the largest such distance (out: cx, cy, cz, mean r^2, max r), for the
-// metric and the trust region of the registration step.  One block of
-// kZStatsThreads threads; per-thread double-float sums in a fixed stride,
-// then a fixed-order tree, so the result does not vary from run to run.
-constexpr int kZStatsThreads = 1024;
-__global__ void __launch_bounds__(kZStatsThreads) k_zstats(const float* __restrict__ xyz, int n, double* out)
-{
-    __shared__ double red[kZStatsThreads];
-    __shared__ double mean[3];
-    __shared__ float mhi[3], mlo[3];
-    float hi[3] = {0.0f, 0.0f, 0.0f}, lo[3] = {0.0f, 0.0f, 0.0f};
-    for (int i = threadIdx.x; i < n; i += kZStatsThreads)   // one pass over the points, three sums
-        for (int a = 0; a < 3; ++a) df_acc(hi[a], lo[a], xyz[3 * (size_t)i + a]);
+    __shared__ long long part[kZStatsThreads / 32][3];
+    long long s[3] = {0, 0, 0};
+    for (int i = blockIdx.x * kZStatsThreads + threadIdx.x; i < n; i += gridDim.x * kZStatsThreads)
+        for (int a = 0; a < 3; ++a) s[a] += __float2ll_rn(xyz[3 * (size_t)i + a] * kCoordScale);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int a = 0; a < 3; ++a) {
-        block_sum(red, (double)hi[a] + (double)lo[a]);
-        if (threadIdx.x == 0) {
-            mean[a] = red[0] / (double)n;
-            mhi[a] = (float)mean[a];
-            mlo[a] = (float)(mean[a] - (double)mhi[a]);
-        }
-        __syncthreads();
+        const long long w = warp_sum_ll(s[a]);
+        if (lane == 0) part[warp][a] = w;
     }
-    float qhi = 0.0f, qlo = 0.0f, mx = 0.0f;
-    for (int i = threadIdx.x; i < n; i += kZStatsThreads) {
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        long long t = 0;
+        for (int k = 0; k < kZStatsThreads / 32; ++k) t += part[k][threadIdx.x];
+        atomicAdd(reinterpret_cast<unsigned long long*>(out + threadIdx.x), (unsigned long long)t);
+    }
+}
+
+__global__ void __launch_bounds__(kZStatsThreads) k_zspread(const float* __restrict__ xyz, int n, long long* out)
+{
+    __shared__ long long part[kZStatsThreads / 32];
+    __shared__ float mx_part[kZStatsThreads / 32];
+    __shared__ float m_hl[6];
+    if (threadIdx.x < 3) {   // the centroid as a double-float pair
+        const double mean = (double)out[threadIdx.x] / (double)kCoordScale / (double)n;
+        m_hl[threadIdx.x] = (float)mean;
+        m_hl[3 + threadIdx.x] = (float)(mean - (double)m_hl[threadIdx.x]);
+    }
+    __syncthreads();
+    const float mhi[3] = {m_hl[0], m_hl[1], m_hl[2]}, mlo[3] = {m_hl[3], m_hl[4], m_hl[5]};
+    long long s = 0;
+    float mx = 0.0f;
+    for (int i = blockIdx.x * kZStatsThreads + threadIdx.x; i < n; i += gridDim.x * kZStatsThreads) {
         float q = 0.0f;
         for (int a = 0; a < 3; ++a) {
             const float e = __fsub_rn(__fsub_rn(xyz[3 * (size_t)i + a], mhi[a]), mlo[a]);
             q = fmaf(e, e, q);
         }
-        df_acc(qhi, qlo, q);
+        s += __float2ll_rn(q * kSqScale);
         mx = fmaxf(mx, q);
     }
-    block_sum(red, (double)qhi + (double)qlo);
-    const double s2 = red[0];
-    __syncthreads();
-    red[threadIdx.x] = (double)mx;
-    __syncthreads();
-    for (int o = kZStatsThreads / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
-        __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    s = warp_sum_ll(s);
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+        part[warp] = s;
+        mx_part[warp] = mx;
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        out[0] = mean[0];
-        out[1] = mean[1];
-        out[2] = mean[2];
-        out[3] = s2 / (double)n;
-        out[4] = sqrt(red[0]);
+        long long t = 0;
+        float m = 0.0f;
+        for (int k = 0; k < kZStatsThreads / 32; ++k) {
+            t += part[k];
+            m = fmaxf(m, mx_part[k]);
+        }
+        atomicAdd(reinterpret_cast<unsigned long long*>(out + 3), (unsigned long long)t);
+        atomicMax(reinterpret_cast<unsigned*>(out + 4), __float_as_uint(m));
     }
 }
 
@@ -455,12 +467,25 @@ inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
-cudaError_t launch_zstats(const float* xyz, int n, double* out5, cudaStream_t s)
+cudaError_t launch_zstats(const float* xyz, int n, long long* out, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    g_launch_count.fetch_add(1, std::memory_order_relaxed);
-    k_zstats<<<1, kZStatsThreads, 0, s>>>(xyz, n, out5);
+    const int nb = min(blocks_for(n, 4 * kZStatsThreads), 64);
+    g_launch_count.fetch_add(2, std::memory_order_relaxed);
+    k_zsum<<<nb, kZStatsThreads, 0, s>>>(xyz, n, out);
+    k_zspread<<<nb, kZStatsThreads, 0, s>>>(xyz, n, out);
     return cudaGetLastError();
+}
+
+void decode_zstats(const long long* raw, int n, double out5[5])
+{
+    for (int a = 0; a < 3; ++a) out5[a] = n > 0 ? (double)raw[a] / (double)kCoordScale / (double)n : 0.0;
+    out5[3] = n > 0 ? (double)raw[3] / (double)kSqScale / (double)n : 0.0;
+    unsigned bits;
+    std::memcpy(&bits, raw + 4, sizeof(bits));
+    float mx;
+    std::memcpy(&mx, &bits, sizeof(mx));
+    out5[4] = std::sqrt((double)mx);
 }
 
 cudaError_t launch_sum_f32(const float* v, int n, double* out, cudaStream_t s)

@@ -86,3 +86,25 @@ def test_batch_full_size_final_poses_match_oracle(batch_run):
         rc2 = (kw["cutoff_mult"] * kw["ell"]) ** 2
         band = oracle.count_band(p.X, p.Z, T_batch[k], rc2 * (1 - 1e-5), rc2 * (1 + 1e-5))
         assert abs(got["pairs"] - ref["npairs"]) <= band, k
+
+
+def test_batch_full_size_converges_where_the_oracle_does(batch_run):
+    """End to end against the FP64 oracle: the smallest pair of the batch and
+    the two pairs next to it in size, registered by the oracle from the same
+    start with the same schedule, end on the batch's poses (1e-4 rad and
+    1e-4 m) after the same number of iterations (give or take one, the
+    stopping test sees 1e-5 steps); every pair of the batch converged, and
+    near the sampled clouds' true motion (independent samples: within their
+    sampling noise, 2e-3 rad / 2e-2 m)."""
+    pairs, kw, T_batch, infos, _, _, _ = batch_run
+    assert all(i["status"] == cvo.Status.OK for i in infos)
+    order = sorted(range(len(pairs)), key=lambda k: pairs[k].n * pairs[k].m)
+    for k in order[:3]:
+        p = pairs[k]
+        To, oinfo, _ = oracle.register(p.X, p.Z, np.eye(4), FX=p.FX, FZ=p.FZ, **kw)
+        assert oinfo["status"] == 0, k
+        er, et = pose_err(T_batch[k], To)
+        assert er <= POSE_TOL and et <= POSE_TOL, (k, er, et)
+        assert abs(infos[k]["iters"] - oinfo["iters"]) <= 1, k
+        er, et = pose_err(T_batch[k], p.T_true)
+        assert er <= 2e-3 and et <= 2e-2, (k, er, et)
