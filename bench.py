@@ -232,16 +232,20 @@ def sweep_roofline(name, pairs_evaluated, sweep_ms_total, launches, fpp, peaks, 
     sec = sweep_ms_total * 1e-3
     achieved = pairs_evaluated * fpp / sec / 1e12 if sec > 0 else None
     avg_ms = sweep_ms_total / max(launches, 1)
-    traffic = winst = xu = None
+    traffic = winst = xu = issue_active = None
     if profile:
         traffic = profile_value(SWEEP_SRC, "traffic_bytes_per_launch", profile)
         winst = profile_value(SWEEP_SRC, "warp_instructions_per_launch", profile)
         xu = profile_value(SWEEP_SRC, "xu_pipe_frac", profile)
+        issue_active = profile_value(SWEEP_SRC, "issue_active_frac", profile)
     issue_peak = sms * ISSUE_PER_CLK_SM * clk
     ex2_peak = sms * EX2_PER_CLK_SM * clk
     return {
         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
         "frac": achieved / peak if achieved else None, "traffic": traffic, "kernel": name,
+        "traffic_source": (f"dram__bytes_read.sum + dram__bytes_write.sum per launch of the committed ncu capture "
+                           f"(profiles/{profile}), a launch with every pair running; null when the kernel source "
+                           f"changed since") if profile else None,
         "flops_per_pair": fpp, "sweep_ms_avg": avg_ms, "sweep_launches": launches,
         "pairs_per_launch": pairs_evaluated / max(launches, 1),
         "peak_source": f"unit counts, not a measured FFMA peak: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
@@ -251,13 +255,11 @@ def sweep_roofline(name, pairs_evaluated, sweep_ms_total, launches, fpp, peaks, 
                 "ncu_xu_pipe_frac": xu,
                 "peak_source": f"{sms} SMs x {EX2_PER_CLK_SM} ex2/clk/SM (measured on a GB300 with an "
                                "independent-chain ex2.approx throughput loop) x sm_max_mhz"},
-        "issue": {"achieved_warp_inst_per_s": winst / (avg_ms * 1e-3) if (winst and avg_ms > 0) else None,
-                  "peak_warp_inst_per_s": issue_peak,
-                  "frac": winst / (avg_ms * 1e-3) / issue_peak if (winst and avg_ms > 0) else None,
+        "issue": {"frac": issue_active, "peak_warp_inst_per_s": issue_peak,
                   "warp_instructions_per_launch": winst,
-                  "source": f"smsp__inst_executed.sum per launch of the committed ncu capture (profiles/{profile}, "
-                            f"same source hash) over the CUDA-event time per launch; peak {sms} SMs x "
-                            f"{ISSUE_PER_CLK_SM} schedulers x sm_max_mhz"},
+                  "source": f"smsp__issue_active (share of scheduler cycles issuing) and smsp__inst_executed.sum of "
+                            f"the launches of the committed ncu capture (profiles/{profile}, same source hash); "
+                            f"peak {sms} SMs x {ISSUE_PER_CLK_SM} schedulers x sm_max_mhz"},
     }
 
 

@@ -236,14 +236,18 @@ cudaError_t persist_t(const PersistArgs& a, int* nblocks, size_t* smem_out, bool
 template <class... T>
 cudaError_t dispatch(const FeatConst& f, T&&... args)
 {
+    // the feature-space cutoff's test is compiled in (the persistent loop is
+    // an option, so one instance per block list serves both settings)
     if (f.n_blocks == 0) return persist_t<FeatNone>(args...);
     const bool se3 = f.n_blocks >= 1 && f.kind[0] == 0 && f.dim[0] == 3;
     if (f.n_blocks == 1 && se3)
-        return f.bf16 ? persist_t<FeatFixed<3, 0, true>>(args...) : persist_t<FeatFixed<3, 0, false>>(args...);
+        return f.bf16 ? persist_t<FeatFixed<3, 0, true, true>>(args...) : persist_t<FeatFixed<3, 0, false, true>>(args...);
     if (f.n_blocks == 2 && se3 && f.kind[1] == 1 && f.dim[1] == 19)
-        return f.bf16 ? persist_t<FeatFixed<3, 19, true>>(args...) : persist_t<FeatFixed<3, 19, false>>(args...);
+        return f.bf16 ? persist_t<FeatFixed<3, 19, true, true>>(args...)
+                      : persist_t<FeatFixed<3, 19, false, true>>(args...);
     if (f.n_blocks == 1 && f.kind[0] == 1 && f.dim[0] == 19)
-        return f.bf16 ? persist_t<FeatFixed<0, 19, true>>(args...) : persist_t<FeatFixed<0, 19, false>>(args...);
+        return f.bf16 ? persist_t<FeatFixed<0, 19, true, false>>(args...)
+                      : persist_t<FeatFixed<0, 19, false, false>>(args...);
     return persist_t<FeatGeneric>(args...);
 }
 

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
 
 template <int DSE, int DDOT, bool BF16>
 struct GradFixed {
-    using F = FeatFixed<DSE, DDOT, BF16>;
+    using F = FeatFixed<DSE, DDOT, BF16, true>;
     static constexpr int D = F::D;
     static constexpr bool kSharedAcc = false;
     using Q = typename F::Q;
@@ -532,17 +532,26 @@ cudaError_t info_t(int rs, SweepLaunch* out)
 }  // namespace
 
 // The sweep specialisation for a block list: kernel and dynamic shared memory.
+template <bool Cut>
+cudaError_t sweep_info_se3(const FeatConst& f, int rs, SweepLaunch* out)
+{
+    if (f.n_blocks == 1)
+        return f.bf16 ? info_t<FeatFixed<3, 0, true, Cut>>(rs, out) : info_t<FeatFixed<3, 0, false, Cut>>(rs, out);
+    // bfloat16 labels: the label inner products on the tensor cores
+    return f.bf16 ? info_t<FeatMMA<3, Cut>>(rs, out) : info_t<FeatFixed<3, 19, false, Cut>>(rs, out);
+}
+
 cudaError_t sweep_launch_info(const FeatConst& f, int rs, SweepLaunch* out)
 {
     if (f.n_blocks == 0) return info_t<FeatNone>(rs, out);
     const bool se3 = f.n_blocks >= 1 && f.kind[0] == 0 && f.dim[0] == 3;
-    if (f.n_blocks == 1 && se3)
-        return f.bf16 ? info_t<FeatFixed<3, 0, true>>(rs, out) : info_t<FeatFixed<3, 0, false>>(rs, out);
-    // bfloat16 labels: the label inner products on the tensor cores
-    if (f.n_blocks == 2 && se3 && f.kind[1] == 1 && f.dim[1] == 19)
-        return f.bf16 ? info_t<FeatMMA<3>>(rs, out) : info_t<FeatFixed<3, 19, false>>(rs, out);
+    const bool labels = f.n_blocks == 2 && f.kind[1] == 1 && f.dim[1] == 19;
+    if (se3 && (f.n_blocks == 1 || labels)) {
+        // the feature-space cutoff's test only where it is on (the colour block's limit is finite)
+        return f.fcut2[0] < 1.0e38f ? sweep_info_se3<true>(f, rs, out) : sweep_info_se3<false>(f, rs, out);
+    }
     if (f.n_blocks == 1 && f.kind[0] == 1 && f.dim[0] == 19)
-        return f.bf16 ? info_t<FeatMMA<0>>(rs, out) : info_t<FeatFixed<0, 19, false>>(rs, out);
+        return f.bf16 ? info_t<FeatMMA<0, false>>(rs, out) : info_t<FeatFixed<0, 19, false, false>>(rs, out);
     return info_t<FeatGeneric>(rs, out);
 }
 

@@ -76,7 +76,8 @@ struct FeatNone {
 
 // One squared-exponential block (Eq. newscalar) of DSE entries followed by
 // one inner-product block (Eq. scalar) of DDOT entries; either may be empty.
-template <int DSE, int DDOT, bool BF16>
+// Cut: the feature-space cutoff is on (else its test is compiled out).
+template <int DSE, int DDOT, bool BF16, bool Cut>
 struct FeatFixed {
     static constexpr int kScratch = 0;
     static constexpr int D = DSE + DDOT;
@@ -124,7 +125,9 @@ struct FeatFixed {
                 du2 = fmaf(d, d, du2);
             }
             arg = fmaf(du2, fc.s[0], arg);
-            if (du2 > fc.fcut2[0]) in = false;
+            if constexpr (Cut) {
+                if (du2 > fc.fcut2[0]) in = false;
+            }
         }
         if constexpr (DDOT > 0) {
             float d4[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // four independent chains
@@ -186,7 +189,7 @@ struct FeatGeneric {
 // with a row stride of 36 floats: the accumulator fragments store without
 // bank conflicts (lane (g, t) of a fragment writes bank g + 8 t) and each
 // candidate's row is read by the 32 lanes from 32 consecutive words.
-template <int DSE>
+template <int DSE, bool Cut>
 struct FeatMMA {
     static constexpr int kL = 19;
     static constexpr int D = DSE + kL;
@@ -318,7 +321,9 @@ struct FeatMMA {
                 du2 = fmaf(d, d, du2);
             }
             arg = fmaf(du2, fc.s[0], arg);
-            if (du2 > fc.fcut2[0]) in = false;
+            if constexpr (Cut) {
+                if (du2 > fc.fcut2[0]) in = false;
+            }
         }
         return q.cs[c * kCsStride + q.lane];
     }
