@@ -603,15 +603,18 @@ def main():
                  torch.tensor(p.FX, device=dev).to(torch.bfloat16), torch.tensor(p.FZ, device=dev).to(torch.bfloat16))
                 for p in pairs]
     h = cvo.CVO(**kw)
-    # cell size, query-group extent and item length tuned on the largest pair
-    # (untimed, before the warm-up)
+    # cell size, query-group extent and item length (untimed, before the
+    # warm-up): the plain form's tuned on the largest pair registered alone,
+    # the batch's on the batch itself (its grid holds every pair's items, so
+    # it prefers longer ones)
     if args.tuning:
         cf, sd, ip = args.tuning.split(",")
         h.apply_tuning(float(cf), int(sd), int(ip))
-        tuning = dict(h.tuning(), source="--tuning")
+        tuning = tuning_plain = dict(h.tuning(), source="--tuning")
     else:
         big = max(range(len(pairs)), key=lambda k: pairs[k].n + pairs[k].m)
-        tuning = dict(h.autotune(*args_dev[big]), source=f"autotuned on pair {big}")
+        tuning_plain = dict(h.autotune(*args_dev[big]), source=f"autotuned on pair {big}")
+        tuning = dict(h.autotune_batch(args_dev), source="autotuned on the batch (cvo_autotune_batch)")
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
@@ -664,7 +667,13 @@ def main():
     cvo.cvo_set_timing(h.h, False)
 
     # ---- the plain form: the same pairs one by one -----------------------------
-    plain = plain_section(h, args_dev, torch, flush, args.reps) if rank == 0 else None
+    if rank == 0:
+        h.apply_tuning(tuning_plain["cell_factor"], tuning_plain["super_delta"], tuning_plain["chunk_len"])
+        plain = plain_section(h, args_dev, torch, flush, args.reps)
+        plain["tuning"] = tuning_plain
+        h.apply_tuning(tuning["cell_factor"], tuning["super_delta"], tuning["chunk_len"])
+    else:
+        plain = None
 
     # ---- end to end: pinned host buffers through the C ABI ------------------
     args_host = [(torch.tensor(p.X).pin_memory(), torch.tensor(p.Z).pin_memory(), np.eye(4),

@@ -316,13 +316,23 @@ typedef struct {
  * under each tuning of a small grid (cell_factor 0.35 / 0.5 / 0.7 / 1.0 and
  * super_delta 1 / 2 / 3 at the current chunk_len; with cutoff_mult <= 0 there
  * is no grid and these stay as they are), then, for the fastest, chunk_len
- * 64 / 96 / 128 / 192; each timed on the host clock as a caller sees it
- * (setup, iterations, result copies; best of two runs).  Keeps the fastest
- * tuning on the handle and returns it in *out (measured_ms: its time).
- * Results do not depend on the tuning beyond rounding; every tuning's F at
- * the start pose is checked against the first (CVO_ERR_CUDA if they differ
- * by more than 1e-4 relative).  Costs up to 30 registrations. */
+ * 64 / 96 / 128 / 192 / 384 / 768 / 1536; each timed on the host clock as a
+ * caller sees it (setup, iterations, result copies; best of two runs).
+ * Keeps the fastest tuning on the handle and returns it in *out
+ * (measured_ms: its time).  Results do not depend on the tuning beyond
+ * rounding; every tuning's F at the start pose is checked against the first
+ * (CVO_ERR_CUDA if they differ by more than 1e-4 relative).  Costs up to 36
+ * registrations. */
 cvo_status cvo_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], cvo_tuning* out);
+
+/* The same search timed on a batched registration (cvo_register_batch) of
+ * the npairs pairs (arguments as there; the results are not returned): a
+ * batch fills the device with many pairs' work items, so its best tuning
+ * (typically longer items) differs from one pair's.  The check value is the
+ * sum over the pairs of F at their start poses.  Costs up to 36 batched
+ * registrations. */
+cvo_status cvo_autotune_batch(cvo_handle h, int npairs, const cvo_cloud* X, const cvo_cloud* Z, const double* T_init,
+                              cvo_tuning* out);
 
 /* The handle's current tuning (measured_ms = 0), and setting it (validated as
  * cvo_set_tuning, chunk_len in [16, 4096]). */

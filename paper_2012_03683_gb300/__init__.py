@@ -29,7 +29,7 @@ __all__ = ["CVO", "cvo_create", "cvo_destroy", "cvo_set_params", "cvo_inner_prod
            "cvo_evaluate", "cvo_backward", "cvo_metric_backward", "cvo_cosine", "CVOInnerProduct", "CVOMetric",
            "inner_product_fn", "metric_fn",
            "cvo_register_pair", "cvo_register_batch", "cvo_register_sequence", "cvo_get_trace", "cvo_set_timing",
-           "cvo_autotune", "cvo_get_tuning", "cvo_apply_tuning", "cvo_set_loop",
+           "cvo_autotune", "cvo_autotune_batch", "cvo_get_tuning", "cvo_apply_tuning", "cvo_set_loop",
            "cvo_sweep_time", "cvo_last_error", "cvo_version", "cvo_kernel_launches", "load_library", "Status",
            "CvoError", "cvo_shard_begin", "cvo_shard_sweep", "cvo_shard_step", "cvo_shard_end", "shard_rows",
            "register_sharded", "SHARD_STATS", "cvo_cosine_dell", "cosine_fn", "cvo_inject_barrier_stall"]
@@ -132,6 +132,7 @@ def load_library(build_if_missing: bool = True):
     lib.cvo_set_tuning.restype = ctypes.c_int
     lib.cvo_sweep_time.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int)]
     lib.cvo_autotune.argtypes = [vp, P(Cloud), P(Cloud), vp, P(Tuning)]
+    lib.cvo_autotune_batch.argtypes = [vp, ctypes.c_int, P(Cloud), P(Cloud), vp, P(Tuning)]
     lib.cvo_set_loop.argtypes = [vp, ctypes.c_int]
     lib.cvo_inject_barrier_stall.argtypes = [vp, ctypes.c_int, ctypes.c_uint]
     lib.cvo_shard_begin.argtypes = [vp, P(Cloud), P(Cloud), ctypes.c_longlong, vp]
@@ -144,6 +145,7 @@ def load_library(build_if_missing: bool = True):
                  "cvo_evaluate", "cvo_backward", "cvo_metric_backward", "cvo_cosine", "cvo_register_pair",
                  "cvo_register_sequence",
                  "cvo_register_batch", "cvo_get_trace", "cvo_set_timing", "cvo_sweep_time", "cvo_autotune",
+                 "cvo_autotune_batch",
                  "cvo_get_tuning", "cvo_apply_tuning", "cvo_set_loop", "cvo_shard_begin", "cvo_shard_sweep",
                  "cvo_cosine_dell", "cvo_inject_barrier_stall",
                  "cvo_shard_step", "cvo_shard_end"):
@@ -419,9 +421,7 @@ def cvo_register_pair(h, X, Z, T_init, FX=None, FZ=None):
     return Tout, d
 
 
-def cvo_register_batch(h, pairs):
-    """pairs: sequence of (X, Z, T_init, FX, FZ)."""
-    keep = []
+def _batch_clouds(pairs, keep):
     n = len(pairs)
     CX = (Cloud * max(n, 1))()
     CZ = (Cloud * max(n, 1))()
@@ -430,6 +430,13 @@ def cvo_register_batch(h, pairs):
         CX[k] = _as_cloud(X, FX, keep)
         CZ[k] = _as_cloud(Z, FZ, keep)
         T0[k] = _pose(T)
+    return n, CX, CZ, T0
+
+
+def cvo_register_batch(h, pairs):
+    """pairs: sequence of (X, Z, T_init, FX, FZ)."""
+    keep = []
+    n, CX, CZ, T0 = _batch_clouds(pairs, keep)
     Tout = np.zeros_like(T0)
     infos = (Info * max(n, 1))()
     rc = _check(load_library().cvo_register_batch(h, n, CX, CZ, T0.ctypes.data, Tout.ctypes.data, infos))
@@ -551,6 +558,17 @@ def cvo_autotune(h, X, Z, T, FX=None, FZ=None) -> dict:
     return out.as_dict()
 
 
+def cvo_autotune_batch(h, pairs) -> dict:
+    """Times a batched registration of pairs ((X, Z, T_init, FX, FZ) each)
+    under a grid of tunings and keeps the fastest on the handle (see
+    cvo_autotune_batch in cvo.h)."""
+    keep = []
+    n, CX, CZ, T0 = _batch_clouds(pairs, keep)
+    out = Tuning()
+    _check(load_library().cvo_autotune_batch(h, n, CX, CZ, T0.ctypes.data, ctypes.byref(out)))
+    return out.as_dict()
+
+
 LOOP_MODES = {"host": 0, "graph": 1, "persistent": 2}
 
 
@@ -647,6 +665,9 @@ class CVO:
 
     def autotune(self, X, Z, T=None, FX=None, FZ=None):
         return cvo_autotune(self.h, X, Z, np.eye(4) if T is None else T, FX, FZ)
+
+    def autotune_batch(self, pairs):
+        return cvo_autotune_batch(self.h, pairs)
 
     def tuning(self):
         return cvo_get_tuning(self.h)

@@ -1471,54 +1471,43 @@ cvo_status run_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     return CVO_OK;
 }
 
-// Autotuner: one registration of (X, Z) from T with the handle's parameters
+// Autotuner: a workload (one registration, or one batched registration) run
 // under every tuning of a small grid, timed on the host clock as a caller
 // sees it (setup, iterations, result copies; best of two runs); the fastest
-// is kept.  First the grid cell and query-group extent (with a cutoff),
-// then, for the best of those, the work-item length.  The results must not
-// depend on the tuning beyond rounding: F at the start pose (the first
-// iteration's) of every tuning is checked against the first one's.
-cvo_status run_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double* T, cvo_tuning* out)
+// is kept.  First the grid cell and query-group extent (with a cutoff), then,
+// for the best of those, the work-item length.  The results must not depend
+// on the tuning beyond rounding: run() returns a value (F) that every tuning
+// must give to 1e-4 relative of the first one's.
+template <class Run>
+cvo_status tune_grid(cvo_handle h, Run&& run, cvo_tuning* out)
 {
     static const double kCell[] = {0.35, 0.5, 0.7, 1.0};
     static const int kSuper[] = {1, 2, 3};
-    static const int kItemLens[] = {64, 96, 128, 192};
+    static const int kItemLens[] = {64, 96, 128, 192, 384, 768, 1536};
     const double cf0 = h->cell_factor;
     const int sd0 = h->super_delta, ip0 = h->chunk_len;
     cvo_tuning best{cf0, sd0, ip0, 1e30};
-    std::memset(out, 0, sizeof(*out));
-    if (X->n == 0 || Z->n == 0 || h->p.max_iters == 0) {
-        *out = cvo_tuning{cf0, sd0, ip0, 0.0};
-        return CVO_OK;
-    }
     double F_ref = 0.0;
     bool have_ref = false;
     cvo_status st = CVO_OK;
-    double T_out[16];
-    cvo_info inf;
     auto try_one = [&](double cf, int sd, int ip) {
         h->cell_factor = cf;
         h->super_delta = sd;
         h->chunk_len = ip;
-        double ms = 1e30;
+        double ms = 1e30, F = 0.0;
         for (int rep = 0; rep < 2; ++rep) {
             const auto t0 = std::chrono::steady_clock::now();
-            st = run_register(h, X, Z, T, T_out, &inf);
+            st = run(&F);
             if (st < 0) return;
             const auto t1 = std::chrono::steady_clock::now();
             ms = std::min(ms, std::chrono::duration<double, std::milli>(t1 - t0).count());
         }
         st = CVO_OK;
-        double row[2] = {0.0, 0.0};   // l and F of the first iteration
-        if (cudaMemcpy(row, h->trace.p, sizeof(row), cudaMemcpyDeviceToHost) != cudaSuccess) {
-            st = fail(CVO_ERR_CUDA, "autotune: trace copy failed");
-            return;
-        }
         if (!have_ref) {
-            F_ref = row[1];
+            F_ref = F;
             have_ref = true;
-        } else if (std::fabs(row[1] - F_ref) > 1e-4 * std::fabs(F_ref) + 1e-300) {
-            st = fail(CVO_ERR_CUDA, "autotune: F differs between tunings (%g vs %g)", row[1], F_ref);
+        } else if (std::fabs(F - F_ref) > 1e-4 * std::fabs(F_ref) + 1e-300) {
+            st = fail(CVO_ERR_CUDA, "autotune: F differs between tunings (%g vs %g)", F, F_ref);
             return;
         }
         if (ms < best.measured_ms) best = cvo_tuning{cf, sd, ip, ms};
@@ -1555,6 +1544,61 @@ cvo_status run_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     h->chunk_len = best.chunk_len;
     *out = best;
     return CVO_OK;
+}
+
+// One registration of (X, Z) from T; the check value is F at the start pose
+// (the first iteration's).
+cvo_status run_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double* T, cvo_tuning* out)
+{
+    std::memset(out, 0, sizeof(*out));
+    if (X->n == 0 || Z->n == 0 || h->p.max_iters == 0) {
+        *out = cvo_tuning{h->cell_factor, h->super_delta, h->chunk_len, 0.0};
+        return CVO_OK;
+    }
+    double T_out[16];
+    cvo_info inf;
+    return tune_grid(
+        h,
+        [&](double* F) -> cvo_status {
+            CVO_TRY(run_register(h, X, Z, T, T_out, &inf));
+            double row[2] = {0.0, 0.0};   // l and F of the first iteration
+            if (cudaMemcpy(row, h->trace.p, sizeof(row), cudaMemcpyDeviceToHost) != cudaSuccess)
+                return fail(CVO_ERR_CUDA, "autotune: trace copy failed");
+            *F = row[1];
+            return CVO_OK;
+        },
+        out);
+}
+
+// One batched registration of the npairs pairs; the check value is the sum of
+// the pairs' F at their start poses (the first row of each running pair's
+// trace).
+cvo_status run_autotune_batch(cvo_handle h, int npairs, const cvo_cloud* X, const cvo_cloud* Z, const double* T_init,
+                              cvo_tuning* out)
+{
+    std::memset(out, 0, sizeof(*out));
+    int nl = 0;   // pairs that run (both clouds non-empty)
+    for (int k = 0; k < npairs; ++k) nl += (X[k].n > 0 && Z[k].n > 0) ? 1 : 0;
+    if (nl == 0 || h->p.max_iters == 0) {
+        *out = cvo_tuning{h->cell_factor, h->super_delta, h->chunk_len, 0.0};
+        return CVO_OK;
+    }
+    std::vector<double> T_out((size_t)16 * npairs), rows((size_t)2 * nl);
+    const size_t tstride = (size_t)h->p.max_iters * CVO_TRACE_STRIDE * sizeof(double);
+    return tune_grid(
+        h,
+        [&](double* F) -> cvo_status {
+            CVO_TRY(run_register_batch(h, npairs, X, Z, T_init, T_out.data(), nullptr));
+            // (l, F) of each running pair's first iteration
+            if (cudaMemcpy2D(rows.data(), 2 * sizeof(double), h->trace.p, tstride, 2 * sizeof(double), (size_t)nl,
+                             cudaMemcpyDeviceToHost) != cudaSuccess)
+                return fail(CVO_ERR_CUDA, "autotune: trace copy failed");
+            double sum = 0.0;
+            for (int i = 0; i < nl; ++i) sum += rows[(size_t)2 * i + 1];
+            *F = sum;
+            return CVO_OK;
+        },
+        out);
 }
 
 struct DeviceGuard {
@@ -1992,6 +2036,24 @@ cvo_status cvo_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
     CVO_TRY(check_pose(T, "T"));
     DeviceGuard g(h->device);
     return run_autotune(h, X, Z, T, out);
+}
+
+cvo_status cvo_autotune_batch(cvo_handle h, int npairs, const cvo_cloud* X, const cvo_cloud* Z, const double* T_init,
+                              cvo_tuning* out)
+{
+    g_err.clear();
+    if (!h) return fail(CVO_ERR_INVALID_ARG, "handle is NULL");
+    if (!out) return fail(CVO_ERR_INVALID_ARG, "out is NULL");
+    if (npairs < 0) return fail(CVO_ERR_INVALID_ARG, "npairs < 0");
+    if (npairs > 0 && (!X || !Z || !T_init)) return fail(CVO_ERR_INVALID_ARG, "NULL array");
+    const int D = feat_dim(h->p);
+    for (int k = 0; k < npairs; ++k) {
+        CVO_TRY(check_cloud(X + k, "X[k]", D));
+        CVO_TRY(check_cloud(Z + k, "Z[k]", D));
+        CVO_TRY(check_pose(T_init + 16 * k, "T_init[k]"));
+    }
+    DeviceGuard g(h->device);
+    return run_autotune_batch(h, npairs, X, Z, T_init, out);
 }
 
 cvo_status cvo_get_tuning(cvo_handle h, cvo_tuning* out)

@@ -54,6 +54,7 @@ def test_null_handle_rejected_by_every_entry_point(lib):
         "cvo_get_trace": lambda: lib.cvo_get_trace(None, None, 0),
         "cvo_set_tuning": lambda: lib.cvo_set_tuning(None, 0.5, 2),
         "cvo_autotune": lambda: lib.cvo_autotune(None, None, None, T, ref(tun)),
+        "cvo_autotune_batch": lambda: lib.cvo_autotune_batch(None, 1, None, None, T, ref(tun)),
         "cvo_get_tuning": lambda: lib.cvo_get_tuning(None, ref(tun)),
         "cvo_apply_tuning": lambda: lib.cvo_apply_tuning(None, ref(tun)),
         "cvo_set_loop": lambda: lib.cvo_set_loop(None, 1),

@@ -1,6 +1,7 @@
-"""The sweep autotuner (cvo_autotune): it picks a tuning from its grid, the
-tuning sticks to the handle, and results under the chosen tuning keep the
-oracle parity of the default one (F relative 1e-5, gradient 1e-4 of |g|)."""
+"""The sweep autotuners (cvo_autotune, cvo_autotune_batch): each picks a
+tuning from its grid, the tuning sticks to the handle, and results under the
+chosen tuning keep the oracle parity of the default one (F relative 1e-5,
+gradient 1e-4 of |g|; a batch's poses within 1e-4 of the default tuning's)."""
 import numpy as np
 import pytest
 
@@ -11,6 +12,10 @@ torch = pytest.importorskip("torch")
 import paper_2012_03683_gb300 as cvo  # noqa: E402
 
 pytestmark = pytest.mark.gpu
+
+CELLS = (0.35, 0.5, 0.7, 1.0)
+SUPERS = (1, 2, 3)
+ITEM_LENS = (64, 96, 128, 192, 384, 768, 1536)
 
 
 def dev(a):
@@ -35,8 +40,8 @@ def test_autotune_street_slice():
     h = cvo.CVO(**kw)
     assert h.tuning()["cell_factor"] == 0.5 and h.tuning()["super_delta"] == 2
     t = h.autotune(dev(X), dev(Z), p.T_true, dev(FX), dev(FZ))
-    assert t["cell_factor"] in (0.35, 0.5, 0.7, 1.0) and t["super_delta"] in (1, 2, 3)
-    assert t["chunk_len"] in (64, 96, 128, 192) and t["measured_ms"] > 0.0
+    assert t["cell_factor"] in CELLS and t["super_delta"] in SUPERS
+    assert t["chunk_len"] in ITEM_LENS and t["measured_ms"] > 0.0
     # the timed sweep did the work: no faster than the pairs it evaluates allow
     # (6,000 x 6,000 points at l = 0.2 take tens of microseconds)
     ev = h.evaluate(dev(X), dev(Z), p.T_true, dev(FX), dev(FZ))
@@ -57,7 +62,7 @@ def test_autotune_dense_and_invalid():
     h = cvo.CVO(**kw)
     t = h.autotune(dev(p.X), dev(p.Z), p.T_true, dev(p.FX), dev(p.FZ))
     # dense: no grid, so only the work split is tuned
-    assert t["cell_factor"] == 0.5 and t["super_delta"] == 2 and t["chunk_len"] in (64, 96, 128, 192)
+    assert t["cell_factor"] == 0.5 and t["super_delta"] == 2 and t["chunk_len"] in ITEM_LENS
     check_parity(h, p.X, p.Z, p.FX, p.FZ, p.T_true, kw)
     with pytest.raises(cvo.CvoError):
         h.apply_tuning(0.1, 2, 8)
@@ -99,3 +104,29 @@ def test_item_length_changes_only_the_work_split():
         np.testing.assert_allclose(tr[:, 1], tr0[:, 1], rtol=1e-5)
         # later poses differ by rounding: a few pairs on the cutoff sphere may differ
         np.testing.assert_allclose(tr[:, 9], tr0[:, 9], rtol=1e-4)
+
+
+def test_autotune_batch():
+    """The batch tuner times cvo_register_batch on the pairs themselves; the
+    kept tuning gives the default tuning's poses (within 1e-4 rad and m) and
+    iteration counts (give or take one)."""
+    pairs = scenes.batch_pairs(n_pairs=6, n_range=(3000, 9000))
+    pr = pairs[0].params
+    kw = dict(blocks=pairs[0].blocks, ell=pr["ell"], cutoff_mult=pr["cutoff_mult"], max_iters=pr["max_iters"])
+    args = [(dev(q.X), dev(q.Z), np.eye(4), dev(q.FX).to(torch.bfloat16), dev(q.FZ).to(torch.bfloat16))
+            for q in pairs]
+    with cvo.CVO(**kw) as h:
+        T0, inf0, _ = h.register_batch(args)
+        t = h.autotune_batch(args)
+        assert t["cell_factor"] in CELLS and t["super_delta"] in SUPERS and t["chunk_len"] in ITEM_LENS
+        assert t["measured_ms"] > 0.0
+        cur = h.tuning()
+        assert (cur["cell_factor"], cur["super_delta"], cur["chunk_len"]) == \
+            (t["cell_factor"], t["super_delta"], t["chunk_len"])
+        T1, inf1, _ = h.register_batch(args)
+        # nothing to time: the tuning is kept as it is
+        assert h.autotune_batch([])["measured_ms"] == 0.0 and h.tuning() == cur
+    for k in range(len(pairs)):
+        xi = oracle.se3_log(np.linalg.inv(T0[k]) @ T1[k])
+        assert np.linalg.norm(xi[:3]) <= 1e-4 and np.linalg.norm(xi[3:]) <= 1e-4, (k, xi)
+        assert abs(inf0[k]["iters"] - inf1[k]["iters"]) <= 1, k

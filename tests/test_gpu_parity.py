@@ -46,8 +46,10 @@ def rand_pose(r, ang=0.2, tr=0.3):
     return oracle.se3_exp(np.concatenate([r.normal(size=3) * ang / math.sqrt(3), r.normal(size=3) * tr / math.sqrt(3)]))
 
 
-def compare_eval(X, Z, FX, FZ, blocks, ell, cm, T, bf16=False, sigma=1.0, ndir=3, seed=0):
+def compare_eval(X, Z, FX, FZ, blocks, ell, cm, T, bf16=False, sigma=1.0, ndir=3, seed=0, tuning=None):
     h = cvo.CVO(blocks=blocks, ell=ell, cutoff_mult=cm, sigma=sigma)
+    if tuning is not None:
+        cvo.cvo_set_tuning(h.h, *tuning)
     if FX is not None and bf16:
         fx_d, fz_d = bf16_dev(FX), bf16_dev(FZ)
         FXo, FZo = scenes.bf16_round(FX), scenes.bf16_round(FZ)
@@ -110,6 +112,54 @@ def test_cutoff_semantic_bf16():
     FZ = np.hstack([r.uniform(0, 1, (m, 3)), r.dirichlet(np.ones(19), m)]).astype(np.float32)
     blocks = [("se", 3, 0.2, 1.0), ("dot", 19, 1.0, 1.0)]
     compare_eval(X, Z, FX, FZ, blocks, 0.1, 3.0, rand_pose(r, 0.05, 0.05), bf16=True)
+
+
+SEM_BLOCKS = [("se", 3, 0.2, 1.0), ("dot", 19, 1.0, 1.0)]
+
+
+def semantic_features(r, n):
+    return np.hstack([r.uniform(0, 1, (n, 3)), r.dirichlet(np.ones(19), n)]).astype(np.float32)
+
+
+def test_tile_far_from_origin_bf16():
+    """bfloat16 RGB + labels with a cutoff (every pair of a staged batch on a
+    dense tile, moments about the query group's centre on the tensor cores)
+    80 m from the origin with l = 5 cm."""
+    r = rng(16)
+    n = 3000
+    base = np.array([60.0, -20.0, 80.0])
+    X = (base + r.uniform(-1, 1, size=(n, 3))).astype(np.float32)
+    Z = (X + r.normal(0, 0.01, size=X.shape)).astype(np.float32)
+    FX = semantic_features(r, n)
+    FZ = FX.copy()
+    FZ[:, :3] = np.clip(FX[:, :3] + r.normal(0, 0.05, (n, 3)), 0, 1)
+    compare_eval(X, Z, FX, FZ, SEM_BLOCKS, 0.05, 3.0, rand_pose(r, 0.002, 0.02), bf16=True)
+
+
+@pytest.mark.parametrize("super_delta", [2, 4, 6])
+def test_tile_sparse_queries_wide_groups_bf16(super_delta):
+    """Sparse queries over a dense cloud with Morton super-cells of 2^k
+    cutoff radii: a query group spans several radii, so its moments about
+    the group's centre are far larger than about each query (the most
+    cancellation when they are moved to each query's origin)."""
+    r = rng(17 + super_delta)
+    n, m = 700, 9000
+    X = r.uniform(-3, 3, size=(n, 3)).astype(np.float32)
+    Z = r.uniform(-3, 3, size=(m, 3)).astype(np.float32)
+    compare_eval(X, Z, semantic_features(r, n), semantic_features(r, m), SEM_BLOCKS, 0.15, 3.0,
+                 rand_pose(r, 0.05, 0.05), bf16=True, tuning=(0.5, super_delta))
+
+
+@pytest.mark.parametrize("n", [1, 5, 31, 33, 100])
+def test_tile_ragged_groups_and_batches_bf16(n):
+    """Groups of fewer than 32 queries and staged batches of fewer than 32
+    candidates on the dense tile."""
+    r = rng(30 + n)
+    m = 3 * n + 7
+    X = r.uniform(-0.3, 0.3, (n, 3)).astype(np.float32)
+    Z = r.uniform(-0.3, 0.3, (m, 3)).astype(np.float32)
+    compare_eval(X, Z, semantic_features(r, n), semantic_features(r, m), SEM_BLOCKS, 0.1, 3.0,
+                 rand_pose(r, 0.05, 0.05), bf16=True, ndir=2)
 
 
 def test_generic_blocks():
