@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -116,6 +117,7 @@ float decode_orderable(unsigned u)
 // queries of X and their groups, the iteration state.
 struct PairRes {
     DevBuf xrec, morton, levels_dev, state;
+    DevBuf in_xyz[2], in_feat[2];   // a batch's device copies of host-resident inputs (X, Z)
     DevBuf zrec[kMaxLevels], cell_start[kMaxLevels], groups[kMaxLevels], items[kMaxLevels];
     int n = 0, m = 0, nlevels = 0;
     LevelHost lv[kMaxLevels];
@@ -126,7 +128,7 @@ struct PairRes {
 
     void free_all()
     {
-        DevBuf* bufs[] = {&xrec, &morton, &levels_dev, &state};
+        DevBuf* bufs[] = {&xrec, &morton, &levels_dev, &state, &in_xyz[0], &in_xyz[1], &in_feat[0], &in_feat[1]};
         for (DevBuf* b : bufs) release(*b);
         for (int k = 0; k < kMaxLevels; ++k) {
             release(zrec[k]);
@@ -158,6 +160,7 @@ struct cvo_handle_s {
     // sweep / finalize scratch
     DevBuf part_stats, part_cnt, grp_stats, grp_cnt, grp_arrivals, pairs_dev, counters, trace;
     DevBuf batch_work;   // per pair of a batch: work items left (the batched step re-splits the grid by them)
+    DevBuf batch_scratch;   // a batch's set-up: every pair's segment of the sort and scan scratch
     // gradients with respect to the inputs: device outputs for host callers,
     // per-query terms of dF/dl and their sum
     DevBuf bw_out[4], bw_tq, bw_dell, bw_part;
@@ -391,74 +394,33 @@ struct Staged {
     const void* feat_z = nullptr;
 };
 
-// prepare() in three phases, each ending where the host needs a device
-// result, so that a batch can run every pair's phase before one wait:
-// dev / hm are the pair's kMiscWords slot of scratch on the device and its
-// host copy.
-// Phase 1: inputs staged; bounding boxes and the finiteness flag into dev.
-cvo_status prepare_bbox(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud* Z, unsigned* dev, Staged* sg)
+// A pair's phase-1 results (its scratch slot hm): the boxes of X and Z and
+// Z's moments (into P); an error if a coordinate or feature was not finite.
+cvo_status decode_slot(PairRes& P, const unsigned* hm, float xmin[3], float xmax[3], float zmin[3], float zmax[3])
 {
-    const int D = h->D;
-    const int n = X->n, m = Z->n;
-    P.n = n;
-    P.m = m;
-    CVO_TRY(stage(h, X, 0, D, &sg->xyz_x, &sg->feat_x));
-    CVO_TRY(stage(h, Z, 1, D, &sg->xyz_z, &sg->feat_z));
-    CVO_CUDA(cudaMemsetAsync(dev, 0, kMiscWords * sizeof(unsigned), h->s));
-    CVO_CUDA(cudaMemsetAsync(dev + 0, 0xff, 3 * sizeof(unsigned), h->s));
-    CVO_CUDA(cudaMemsetAsync(dev + 6, 0xff, 3 * sizeof(unsigned), h->s));
-    int* bad = (int*)(dev + 12);
-    CVO_CUDA(launch_bbox(sg->xyz_x, n, dev + 0, bad, h->s));
-    CVO_CUDA(launch_bbox(sg->xyz_z, m, dev + 6, bad, h->s));
-    CVO_CUDA(launch_zstats(sg->xyz_z, m, (long long*)(dev + kZStatsWord), h->s));
-    if (D > 0) {
-        CVO_CUDA(launch_check_feat(sg->feat_x, (long long)n * D, X->feat_dtype == CVO_BF16, bad, h->s));
-        CVO_CUDA(launch_check_feat(sg->feat_z, (long long)m * D, Z->feat_dtype == CVO_BF16, bad, h->s));
-    }
-    return CVO_OK;
-}
-
-// Phase 2: from the boxes (hm), the grid levels of Z, the Morton-ordered
-// queries of X and their groups (group counts into dev + 16 + level).
-cvo_status prepare_build(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud* Z, double ell_hi,
-                         double ell_lo, const Staged& sg, const unsigned* hm, unsigned* dev, bool fan_out)
-{
-    const cvo_params& p = h->p;
-    const int D = h->D;
-    const int n = X->n, m = Z->n;
-    const float* xyz_x = sg.xyz_x;
-    const float* xyz_z = sg.xyz_z;
-    const void* feat_x = sg.feat_x;
-    const void* feat_z = sg.feat_z;
     if (hm[12]) return fail(CVO_ERR_INVALID_ARG, "non-finite coordinate or feature");
-    float xmin[3], xmax[3], zmin[3], zmax[3];
     for (int a = 0; a < 3; ++a) {
         xmin[a] = decode_orderable(hm[a]);
         xmax[a] = decode_orderable(hm[3 + a]);
         zmin[a] = decode_orderable(hm[6 + a]);
         zmax[a] = decode_orderable(hm[9 + a]);
     }
-    {
-        long long raw[5];
-        std::memcpy(raw, hm + kZStatsWord, sizeof(raw));
-        double zs[5];
-        decode_zstats(raw, m, zs);
-        for (int a = 0; a < 3; ++a) P.zc[a] = zs[a];
-        P.zr2 = zs[3];
-        P.zrmax = zs[4];
-    }
-    const int rs = h->rs;
-    const int nmax = std::max(n, m);
-    // the handle's own setup scratch, which the work plan uses after this
-    // (with fan_out the builds below run on the lanes' copies)
-    CVO_CUDA(ensure(h->keys, (size_t)nmax * 4));
-    CVO_CUDA(ensure(h->vals, (size_t)nmax * 4));
-    CVO_CUDA(ensure(h->keys2, (size_t)nmax * 4));
-    CVO_CUDA(ensure(h->vals2, (size_t)nmax * 4));
-    CVO_CUDA(ensure(h->flags, (size_t)std::max(n, 1) * 4));
-    CVO_CUDA(ensure(h->gidx, (size_t)std::max(n, 1) * 4));
+    long long raw[5];
+    std::memcpy(raw, hm + kZStatsWord, sizeof(raw));
+    double zs[5];
+    decode_zstats(raw, P.m, zs);
+    for (int a = 0; a < 3; ++a) P.zc[a] = zs[a];
+    P.zr2 = zs[3];
+    P.zrmax = zs[4];
+    return CVO_OK;
+}
 
-    // grid levels of Z
+// The grid levels of Z for lengthscales in [ell_lo, ell_hi] from Z's box:
+// one per factor sqrt(2) of the cutoff radius, cell edge cell_factor times
+// the level's radius (grown until the grid has at most kMaxCells cells).
+void set_levels(cvo_handle h, PairRes& P, const float zmin[3], const float zmax[3], double ell_hi, double ell_lo)
+{
+    const cvo_params& p = h->p;
     if (h->dense) {
         P.nlevels = 1;
         LevelHost& L = P.lv[0];
@@ -495,6 +457,69 @@ cvo_status prepare_build(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo
             L.ox = zmin[0]; L.oy = zmin[1]; L.oz = zmin[2];
         }
     }
+}
+
+// Morton super-cells of edge about 2^super_delta times the level's cutoff
+// radius hold the query groups (the dense sum: one super-cell)
+int group_shift(cvo_handle h, const LevelHost& L, double cell0)
+{
+    if (h->dense) return 30;
+    const int e = (int)std::floor(std::log2(L.rdesign / cell0)) + h->super_delta;
+    return 3 * std::max(0, std::min(10, e));
+}
+
+// prepare() in three phases, each ending where the host needs a device
+// result, so that a batch can run every pair's phase before one wait:
+// dev / hm are the pair's kMiscWords slot of scratch on the device and its
+// host copy.
+// Phase 1: inputs staged; bounding boxes and the finiteness flag into dev.
+cvo_status prepare_bbox(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud* Z, unsigned* dev, Staged* sg)
+{
+    const int D = h->D;
+    const int n = X->n, m = Z->n;
+    P.n = n;
+    P.m = m;
+    CVO_TRY(stage(h, X, 0, D, &sg->xyz_x, &sg->feat_x));
+    CVO_TRY(stage(h, Z, 1, D, &sg->xyz_z, &sg->feat_z));
+    CVO_CUDA(cudaMemsetAsync(dev, 0, kMiscWords * sizeof(unsigned), h->s));
+    CVO_CUDA(cudaMemsetAsync(dev + 0, 0xff, 3 * sizeof(unsigned), h->s));
+    CVO_CUDA(cudaMemsetAsync(dev + 6, 0xff, 3 * sizeof(unsigned), h->s));
+    int* bad = (int*)(dev + 12);
+    CVO_CUDA(launch_bbox(sg->xyz_x, n, dev + 0, bad, h->s));
+    CVO_CUDA(launch_bbox(sg->xyz_z, m, dev + 6, bad, h->s));
+    CVO_CUDA(launch_zstats(sg->xyz_z, m, (long long*)(dev + kZStatsWord), h->s));
+    if (D > 0) {
+        CVO_CUDA(launch_check_feat(sg->feat_x, (long long)n * D, X->feat_dtype == CVO_BF16, bad, h->s));
+        CVO_CUDA(launch_check_feat(sg->feat_z, (long long)m * D, Z->feat_dtype == CVO_BF16, bad, h->s));
+    }
+    return CVO_OK;
+}
+
+// Phase 2: from the boxes (hm), the grid levels of Z, the Morton-ordered
+// queries of X and their groups (group counts into dev + 16 + level).
+cvo_status prepare_build(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud* Z, double ell_hi,
+                         double ell_lo, const Staged& sg, const unsigned* hm, unsigned* dev, bool fan_out)
+{
+    const int D = h->D;
+    const int n = X->n, m = Z->n;
+    const float* xyz_x = sg.xyz_x;
+    const float* xyz_z = sg.xyz_z;
+    const void* feat_x = sg.feat_x;
+    const void* feat_z = sg.feat_z;
+    float xmin[3], xmax[3], zmin[3], zmax[3];
+    CVO_TRY(decode_slot(P, hm, xmin, xmax, zmin, zmax));
+    const int rs = h->rs;
+    const int nmax = std::max(n, m);
+    // the handle's own setup scratch, which the work plan uses after this
+    // (with fan_out the builds below run on the lanes' copies)
+    CVO_CUDA(ensure(h->keys, (size_t)nmax * 4));
+    CVO_CUDA(ensure(h->vals, (size_t)nmax * 4));
+    CVO_CUDA(ensure(h->keys2, (size_t)nmax * 4));
+    CVO_CUDA(ensure(h->vals2, (size_t)nmax * 4));
+    CVO_CUDA(ensure(h->flags, (size_t)std::max(n, 1) * 4));
+    CVO_CUDA(ensure(h->gidx, (size_t)std::max(n, 1) * 4));
+
+    set_levels(h, P, zmin, zmax, ell_hi, ell_lo);
     // with fan_out, the grid levels and the queries are built on the setup
     // lanes at once (each lane its own scratch), joined at the end
     if (fan_out) {
@@ -567,13 +592,7 @@ cvo_status prepare_build(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo
     CVO_CUDA(ensure(h->gidx, (size_t)std::max(n, 1) * 4));
     for (int k = 0; k < P.nlevels; ++k) {
         LevelHost& L = P.lv[k];
-        int sh = 30;
-        if (!h->dense) {
-            // Morton super-cells of edge about 2^super_delta times the
-            // level's cutoff radius hold the query groups
-            const int e = (int)std::floor(std::log2(L.rdesign / cell0)) + h->super_delta;
-            sh = 3 * std::max(0, std::min(10, e));
-        }
+        const int sh = group_shift(h, L, cell0);
         L.shift = sh;
         CVO_CUDA(ensure(P.groups[k], (size_t)std::max(n, 1) * sizeof(int2)));
         CVO_CUDA(launch_group_flags((const unsigned*)P.morton.p, n, sh, (unsigned*)h->flags.p, h->s));
@@ -720,7 +739,9 @@ cvo_status ensure_host_states(cvo_handle h, int n)
 // Initial state of one pair; host copy in h->h_state[slot].
 enum PlanMode { kNoPlan = 0, kUniform = 1, kPlanned = 2 };
 
-cvo_status init_state(cvo_handle h, PairRes& P, int slot, const double* T, double ell, int mode, int plan)
+// The state filled on the host (h->h_state[slot]) and copied to the device;
+// its derived constants are k_init_state's.
+cvo_status fill_state(cvo_handle h, PairRes& P, int slot, const double* T, double ell, int mode)
 {
     IterState* st = h->h_state + slot;
     std::memset(st, 0, sizeof(IterState));
@@ -750,10 +771,272 @@ cvo_status init_state(cvo_handle h, PairRes& P, int slot, const double* T, doubl
     if (mode == 1 && p.max_iters == 0) st->done = 1;
     CVO_CUDA(ensure(P.state, sizeof(IterState)));
     CVO_CUDA(cudaMemcpyAsync(P.state.p, st, sizeof(IterState), cudaMemcpyHostToDevice, h->s));
+    return CVO_OK;
+}
+
+cvo_status init_state(cvo_handle h, PairRes& P, int slot, const double* T, double ell, int mode, int plan)
+{
+    CVO_TRY(fill_state(h, P, slot, T, ell, mode));
     CVO_CUDA(launch_init_state((IterState*)P.state.p, h->s));
     if (plan != kNoPlan) CVO_TRY(plan_items(h, P, plan == kPlanned));
     return CVO_OK;
 }
+
+// The set-up of a batch whose inputs are on the device: prepare, init_state
+// and plan_items (planned) for every pair, each stage one launch for all
+// pairs (the batched launchers) rather than a few dozen launches per pair,
+// with one wait after each of the three phases.  The results are those of
+// the pair-by-pair set-up: the same kernel bodies on the same data, and
+// stable sorts (a pair whose keys need fewer digits than another's takes
+// extra passes on zero digits, which keep its order).
+double reachable_ell_lo(const cvo_params& p);
+
+struct BatchSeg {   // a pair's segment of the batch scratch
+    unsigned *keys, *vals, *keys2, *vals2, *flags, *gidx, *temp;
+};
+
+cvo_status prepare_batch(cvo_handle h, const std::vector<int>& live, const cvo_cloud* X, const cvo_cloud* Z,
+                         const double* T_init, long long* work)
+{
+    const cvo_params& p = h->p;
+    const int nl = (int)live.size();
+    const int D = h->D, rs = h->rs;
+    const double ell_lo = reachable_ell_lo(p);
+    CVO_CUDA(ensure(h->misc, (size_t)nl * kMiscWords * sizeof(unsigned)));
+    CVO_TRY(ensure_host_misc(h, nl * kMiscWords));
+    unsigned* dev = (unsigned*)h->misc.p;
+    unsigned* hm = h->h_misc;
+    auto slot = [&](int i) { return dev + (size_t)i * kMiscWords; };
+    auto hslot = [&](int i) { return hm + (size_t)i * kMiscWords; };
+    auto fetch = [&]() -> cvo_status {
+        CVO_CUDA(cudaMemcpyAsync(hm, dev, (size_t)nl * kMiscWords * sizeof(unsigned), cudaMemcpyDeviceToHost, h->s));
+        CVO_CUDA(cudaStreamSynchronize(h->s));
+        return CVO_OK;
+    };
+
+    // phase 1: boxes, finiteness, Z's moments
+    std::vector<BoxJob> box(nl);
+    for (int i = 0; i < nl; ++i) {
+        const cvo_cloud& x = X[live[i]];
+        const cvo_cloud& z = Z[live[i]];
+        PairRes& P = h->pr[i];
+        P.n = x.n;
+        P.m = z.n;
+        BoxJob& b = box[i];
+        b.xyz_x = x.xyz;
+        b.xyz_z = z.xyz;
+        b.feat_x = x.feat;
+        b.feat_z = z.feat;
+        b.nfx = D > 0 ? (long long)x.n * D : 0;
+        b.nfz = D > 0 ? (long long)z.n * D : 0;
+        b.n = x.n;
+        b.m = z.n;
+        b.fx_bf16 = x.feat_dtype == CVO_BF16;
+        b.fz_bf16 = z.feat_dtype == CVO_BF16;
+        b.box_x = slot(i);
+        b.box_z = slot(i) + 6;
+        b.bad = (int*)(slot(i) + 12);
+        b.zstats = (long long*)(slot(i) + kZStatsWord);
+    }
+    CVO_CUDA(launch_boxes_batch(box.data(), nl, h->s));
+    CVO_TRY(fetch());
+
+    // the scratch: per pair max(n, m) words in each of six arrays, and the
+    // sorts' temporary words
+    std::vector<size_t> cap(nl), tw(nl);
+    size_t sum_cap = 0, sum_tw = 0;
+    for (int i = 0; i < nl; ++i) {
+        cap[i] = (size_t)std::max(1, std::max(h->pr[i].n, h->pr[i].m));
+        tw[i] = sort_batch_temp_words((int)cap[i]);
+        sum_cap += cap[i];
+        sum_tw += tw[i];
+    }
+    CVO_CUDA(ensure(h->batch_scratch, (6 * sum_cap + sum_tw) * sizeof(unsigned)));
+    std::vector<BatchSeg> seg(nl);
+    {
+        unsigned* base = (unsigned*)h->batch_scratch.p;
+        size_t off = 0, toff = 6 * sum_cap;
+        for (int i = 0; i < nl; ++i) {
+            unsigned** arrays[6] = {&seg[i].keys, &seg[i].vals, &seg[i].keys2, &seg[i].vals2, &seg[i].flags,
+                                    &seg[i].gidx};
+            for (int a = 0; a < 6; ++a) *arrays[a] = base + (size_t)a * sum_cap + off;
+            seg[i].temp = base + toff;
+            off += cap[i];
+            toff += tw[i];
+        }
+    }
+
+    // phase 2: grid levels of Z, the Morton order of X, query groups
+    std::vector<double> cell0(nl);
+    std::vector<std::array<float, 3>> xlo(nl);
+    int nlev = 0;
+    for (int i = 0; i < nl; ++i) {
+        PairRes& P = h->pr[i];
+        float xmin[3], xmax[3], zmin[3], zmax[3];
+        CVO_TRY(decode_slot(P, hslot(i), xmin, xmax, zmin, zmax));
+        set_levels(h, P, zmin, zmax, p.ell, ell_lo);
+        nlev = std::max(nlev, P.nlevels);
+        double ext = 0.0;
+        for (int a = 0; a < 3; ++a) ext = std::max(ext, (double)xmax[a] - xmin[a]);
+        cell0[i] = std::max(ext / 1024.0, 1e-6);
+        xlo[i] = {xmin[0], xmin[1], xmin[2]};
+        CVO_CUDA(ensure(P.xrec, (size_t)std::max(P.n, 1) * rs * sizeof(float4)));
+        CVO_CUDA(ensure(P.morton, (size_t)std::max(P.n, 1) * 4));
+        for (int k = 0; k < P.nlevels; ++k) {
+            LevelHost& L = P.lv[k];
+            L.shift = group_shift(h, L, cell0[i]);
+            CVO_CUDA(ensure(P.zrec[k], (size_t)std::max(P.m, 1) * rs * sizeof(float4)));
+            CVO_CUDA(ensure(P.cell_start[k], (size_t)(L.ncells + 1) * sizeof(int)));
+            CVO_CUDA(ensure(P.groups[k], (size_t)std::max(P.n, 1) * sizeof(int2)));
+        }
+    }
+    // pairs i of a job list: idx[j]
+    std::vector<int> idx;
+    auto pairs_with_level = [&](int k) {
+        idx.clear();
+        for (int i = 0; i < nl; ++i)
+            if (h->pr[i].nlevels > k) idx.push_back(i);
+    };
+    // sorted (keys, vals) of pair i after a batched sort: in place or in the alternates
+    auto sorted_keys = [&](int i, int alt) { return alt ? seg[i].keys2 : seg[i].keys; };
+    auto sorted_vals = [&](int i, int alt) { return alt ? seg[i].vals2 : seg[i].vals; };
+    auto sort_jobs = [&](const std::vector<int>& ids, auto&& count_of) {
+        std::vector<SortJob> sj(ids.size());
+        for (size_t j = 0; j < ids.size(); ++j) {
+            const BatchSeg& g = seg[ids[j]];
+            sj[j] = SortJob{g.keys, g.vals, g.keys2, g.vals2, g.temp, count_of(ids[j])};
+        }
+        return sj;
+    };
+    for (int k = 0; k < nlev; ++k) {
+        pairs_with_level(k);
+        const int cnt = (int)idx.size();
+        std::vector<PackJob> pj(cnt);
+        if (h->dense) {
+            for (int j = 0; j < cnt; ++j) {
+                PairRes& P = h->pr[idx[j]];
+                const cvo_cloud& z = Z[live[idx[j]]];
+                const int cs[2] = {0, P.m};
+                CVO_CUDA(cudaMemcpyAsync(P.cell_start[k].p, cs, sizeof(cs), cudaMemcpyHostToDevice, h->s));
+                pj[j] = PackJob{z.xyz, z.feat, nullptr, nullptr, nullptr, (float4*)P.zrec[k].p, P.m,
+                                z.feat_dtype == CVO_BF16};
+            }
+        } else {
+            std::vector<KeyJob> kj(cnt);
+            int nbits = 1;
+            for (int j = 0; j < cnt; ++j) {
+                const PairRes& P = h->pr[idx[j]];
+                const LevelHost& L = P.lv[k];
+                kj[j] = KeyJob{Z[live[idx[j]]].xyz, seg[idx[j]].keys, seg[idx[j]].vals, L.ox, L.oy, L.oz,
+                               (float)(1.0 / L.h), P.m, L.nx, L.ny, L.nz};
+                nbits = std::max(nbits, bits_for(L.ncells));
+            }
+            CVO_CUDA(launch_cell_keys_batch(kj.data(), cnt, h->s));
+            const std::vector<SortJob> sj = sort_jobs(idx, [&](int i) { return h->pr[i].m; });
+            int alt = 0;
+            CVO_CUDA(radix_sort_batch(sj.data(), cnt, nbits, &alt, h->s));
+            std::vector<CellStartJob> cj(cnt);
+            for (int j = 0; j < cnt; ++j) {
+                PairRes& P = h->pr[idx[j]];
+                const cvo_cloud& z = Z[live[idx[j]]];
+                cj[j] = CellStartJob{sorted_keys(idx[j], alt), (int*)P.cell_start[k].p, P.m, (int)P.lv[k].ncells};
+                pj[j] = PackJob{z.xyz, z.feat, sorted_vals(idx[j], alt), nullptr, nullptr, (float4*)P.zrec[k].p, P.m,
+                                z.feat_dtype == CVO_BF16};
+            }
+            CVO_CUDA(launch_cell_start_batch(cj.data(), cnt, h->s));
+        }
+        CVO_CUDA(launch_pack_batch(pj.data(), cnt, D, rs, h->rec_bf16, h->s));
+    }
+    {   // queries: Morton order of X in its own frame
+        std::vector<int> all(nl);
+        for (int i = 0; i < nl; ++i) all[i] = i;
+        std::vector<KeyJob> kj(nl);
+        for (int i = 0; i < nl; ++i)
+            kj[i] = KeyJob{X[live[i]].xyz, seg[i].keys, seg[i].vals, xlo[i][0], xlo[i][1], xlo[i][2],
+                           (float)(1.0 / cell0[i]), h->pr[i].n, 0, 0, 0};
+        CVO_CUDA(launch_morton_keys_batch(kj.data(), nl, h->s));
+        const std::vector<SortJob> sj = sort_jobs(all, [&](int i) { return h->pr[i].n; });
+        int alt = 0;
+        CVO_CUDA(radix_sort_batch(sj.data(), nl, 30, &alt, h->s));
+        std::vector<PackJob> pj(nl);
+        for (int i = 0; i < nl; ++i) {
+            PairRes& P = h->pr[i];
+            const cvo_cloud& x = X[live[i]];
+            pj[i] = PackJob{x.xyz, x.feat, sorted_vals(i, alt), sorted_keys(i, alt), (unsigned*)P.morton.p,
+                            (float4*)P.xrec.p, P.n, x.feat_dtype == CVO_BF16};
+        }
+        CVO_CUDA(launch_pack_batch(pj.data(), nl, D, rs, h->rec_bf16, h->s));
+    }
+    for (int k = 0; k < nlev; ++k) {   // query groups per level; their counts into the slots
+        pairs_with_level(k);
+        const int cnt = (int)idx.size();
+        std::vector<GroupJob> gj(cnt);
+        std::vector<ScanJob> sc(cnt);
+        for (int j = 0; j < cnt; ++j) {
+            const int i = idx[j];
+            PairRes& P = h->pr[i];
+            gj[j] = GroupJob{(const unsigned*)P.morton.p, seg[i].flags, seg[i].gidx, (int2*)P.groups[k].p, P.n,
+                             P.lv[k].shift};
+            sc[j] = ScanJob{seg[i].flags, seg[i].gidx, slot(i) + 16 + k, P.n};
+        }
+        CVO_CUDA(launch_group_flags_batch(gj.data(), cnt, h->s));
+        CVO_CUDA(launch_scan_batch(sc.data(), cnt, h->s));
+        CVO_CUDA(launch_group_write_batch(gj.data(), cnt, h->s));
+    }
+    CVO_TRY(fetch());
+
+    // phase 3: level descriptors, start states, the planned work items
+    std::vector<StateJob> stj(nl);
+    for (int i = 0; i < nl; ++i) {
+        PairRes& P = h->pr[i];
+        CVO_TRY(prepare_finish(h, P, hslot(i)));
+        CVO_TRY(fill_state(h, P, i, T_init + 16 * live[i], p.ell, 1));
+        stj[i] = StateJob{(IterState*)P.state.p};
+    }
+    CVO_CUDA(launch_init_state_batch(stj.data(), nl, h->s));
+    for (int k = 0; k < nlev; ++k) {
+        pairs_with_level(k);
+        const int cnt = (int)idx.size();
+        std::vector<CostJob> cj(cnt);
+        for (int j = 0; j < cnt; ++j) {
+            const int i = idx[j];
+            PairRes& P = h->pr[i];
+            const LevelHost& L = P.lv[k];
+            CVO_CUDA(ensure(P.items[k], (size_t)std::max(L.ngroups, 1) * kMaxChunks * sizeof(int4)));
+            cj[j] = CostJob{(const LevelDesc*)P.levels_dev.p, (const float4*)P.xrec.p, (const IterState*)P.state.p,
+                            seg[i].keys, seg[i].vals, seg[i].flags, k, L.ngroups, P.m,
+                            h->dense ? -1.0f : (float)L.rdesign};
+        }
+        CVO_CUDA(launch_group_cost_batch(cj.data(), cnt, rs, h->dense, h->chunk_len, h->s));
+        const std::vector<SortJob> sj = sort_jobs(idx, [&](int i) { return h->pr[i].lv[k].ngroups; });
+        int alt = 0;
+        CVO_CUDA(radix_sort_batch(sj.data(), cnt, 32, &alt, h->s));
+        std::vector<GatherJob> gj(cnt);
+        std::vector<ScanJob> sc(cnt);
+        std::vector<ItemsJob> it(cnt);
+        for (int j = 0; j < cnt; ++j) {
+            const int i = idx[j];
+            PairRes& P = h->pr[i];
+            const int ng = P.lv[k].ngroups;
+            // chunk counts in sorted order, their scan (into the sorted keys'
+            // place, no longer needed) and the items
+            gj[j] = GatherJob{seg[i].flags, sorted_vals(i, alt), seg[i].gidx, ng};
+            sc[j] = ScanJob{seg[i].gidx, sorted_keys(i, alt), slot(i) + 16 + k, ng};
+            it[j] = ItemsJob{(const LevelDesc*)P.levels_dev.p, sorted_vals(i, alt), seg[i].flags, sorted_keys(i, alt),
+                             (int4*)P.items[k].p, k, ng};
+        }
+        CVO_CUDA(launch_gather_batch(gj.data(), cnt, h->s));
+        CVO_CUDA(launch_scan_batch(sc.data(), cnt, h->s));
+        CVO_CUDA(launch_write_items_batch(it.data(), cnt, h->s));
+    }
+    CVO_TRY(fetch());
+    for (int i = 0; i < nl; ++i) {
+        CVO_TRY(plan_finish(h, h->pr[i], true, hslot(i)));
+        *work += h->pr[i].max_items;
+    }
+    return CVO_OK;
+}
+
 
 // Sweep scratch sized for nblocks blocks; the pair table uploaded.
 cvo_status setup_sweep(cvo_handle h, const std::vector<PairDesc>& table, int nblocks, SweepArgs* a, bool groups)
@@ -1157,64 +1440,38 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
     CVO_TRY(begin_call(h, bf, nl));
     const double ell_lo = reachable_ell_lo(p);
     long long work = 0;
-    bool on_device = true;
-    for (int k : live) on_device = on_device && X[k].on_device && Z[k].on_device;
-    if (on_device && nl > 1) {
-        // every pair's setup phase before one wait per phase (a wait per pair
-        // and phase left the device idle between small kernels), the pairs
-        // spread over kSetupLanes streams, each with its own scratch, so
-        // that their small kernels overlap; each pair has its own slot of
-        // results
-        CVO_CUDA(ensure(h->misc, (size_t)nl * kMiscWords * sizeof(unsigned)));
-        CVO_TRY(ensure_host_misc(h, nl * kMiscWords));
-        CVO_TRY(ensure_lanes(h));
-        unsigned* dev = (unsigned*)h->misc.p;
-        unsigned* hm = h->h_misc;
-        const size_t slots = (size_t)nl * kMiscWords * sizeof(unsigned);
-        int nmax = 1;
-        for (int k : live) nmax = std::max(nmax, std::max(X[k].n, Z[k].n));
-        for (SetupLane& L : h->lanes) {   // sized once, before any pair queues work on them
-            for (DevBuf* b : {&L.keys, &L.vals, &L.keys2, &L.vals2, &L.flags, &L.gidx})
-                CVO_CUDA(ensure(*b, (size_t)nmax * 4));
-            CVO_CUDA(ensure(L.sort_tmp, radix_sort_temp_bytes(nmax)));
-            CVO_CUDA(cudaEventRecord(L.ev, h->s));   // the lanes start after the handle's stream
-            CVO_CUDA(cudaStreamWaitEvent(L.s, L.ev, 0));
-        }
-        // runs f(i) for every pair on its lane, then joins the lanes
-        auto on_lanes = [&](auto&& f) -> cvo_status {
-            cvo_status st = CVO_OK;
-            for (int i = 0; i < nl && st == CVO_OK; ++i) {
-                SetupLane& L = h->lanes[i % kSetupLanes];
-                swap_lane(h, L);
-                st = f(i);
-                swap_lane(h, L);
-            }
-            if (st != CVO_OK) return st;
-            return join_lanes(h);
-        };
-        std::vector<Staged> sg(nl);
-        CVO_TRY(on_lanes([&](int i) {
-            return prepare_bbox(h, h->pr[i], X + live[i], Z + live[i], dev + (size_t)i * kMiscWords, &sg[i]);
-        }));
-        CVO_CUDA(cudaMemcpyAsync(hm, dev, slots, cudaMemcpyDeviceToHost, h->s));
-        CVO_CUDA(cudaStreamSynchronize(h->s));
-        CVO_TRY(on_lanes([&](int i) {
-            return prepare_build(h, h->pr[i], X + live[i], Z + live[i], p.ell, ell_lo, sg[i],
-                                 hm + (size_t)i * kMiscWords, dev + (size_t)i * kMiscWords, false);
-        }));
-        CVO_CUDA(cudaMemcpyAsync(hm, dev, slots, cudaMemcpyDeviceToHost, h->s));
-        CVO_CUDA(cudaStreamSynchronize(h->s));
-        CVO_TRY(on_lanes([&](int i) {
-            CVO_TRY(prepare_finish(h, h->pr[i], hm + (size_t)i * kMiscWords));
-            CVO_TRY(init_state(h, h->pr[i], i, T_init + 16 * live[i], p.ell, 1, kNoPlan));
-            return plan_launch(h, h->pr[i], true, dev + (size_t)i * kMiscWords);
-        }));
-        CVO_CUDA(cudaMemcpyAsync(hm, dev, slots, cudaMemcpyDeviceToHost, h->s));
-        CVO_CUDA(cudaStreamSynchronize(h->s));
+    // host-resident inputs first copied to the pairs' own device buffers, so
+    // that every batch takes the batched set-up (unless CVO_BATCH_SETUP=pairs
+    // in the environment selects the pair-by-pair one, for comparison)
+    const char* mode = std::getenv("CVO_BATCH_SETUP");
+    const bool batched = nl > 1 && !(mode && std::strcmp(mode, "pairs") == 0);
+    std::vector<cvo_cloud> Xd, Zd;
+    if (batched) {
+        Xd.assign(X, X + npairs);
+        Zd.assign(Z, Z + npairs);
+        const int D = h->D;
         for (int i = 0; i < nl; ++i) {
-            CVO_TRY(plan_finish(h, h->pr[i], true, hm + (size_t)i * kMiscWords));
-            work += h->pr[i].max_items;
+            const int k = live[i];
+            cvo_cloud* c[2] = {&Xd[k], &Zd[k]};
+            for (int side = 0; side < 2; ++side) {
+                cvo_cloud& cl = *c[side];
+                if (cl.on_device) continue;
+                PairRes& P = h->pr[i];
+                const size_t bx = (size_t)cl.n * 3 * sizeof(float);
+                CVO_CUDA(ensure(P.in_xyz[side], bx));
+                CVO_CUDA(cudaMemcpyAsync(P.in_xyz[side].p, cl.xyz, bx, cudaMemcpyHostToDevice, h->s));
+                cl.xyz = (const float*)P.in_xyz[side].p;
+                if (D > 0) {
+                    const size_t bf = (size_t)cl.n * D * (cl.feat_dtype == CVO_BF16 ? 2 : 4);
+                    CVO_CUDA(ensure(P.in_feat[side], bf));
+                    CVO_CUDA(cudaMemcpyAsync(P.in_feat[side].p, cl.feat, bf, cudaMemcpyHostToDevice, h->s));
+                    cl.feat = P.in_feat[side].p;
+                }
+                cl.on_device = 1;
+            }
         }
+        // every pair's set-up stage in one launch for all pairs
+        CVO_TRY(prepare_batch(h, live, Xd.data(), Zd.data(), T_init, &work));
     } else {
         for (int i = 0; i < nl; ++i) {
             CVO_TRY(prepare(h, h->pr[i], X + live[i], Z + live[i], p.ell, ell_lo));
@@ -1672,7 +1929,7 @@ cvo_status cvo_destroy(cvo_handle h)
     DevBuf* bufs[] = {&h->stage_xyz[0], &h->stage_xyz[1], &h->stage_feat[0], &h->stage_feat[1], &h->keys, &h->vals,
                       &h->keys2, &h->vals2, &h->sort_tmp, &h->flags, &h->gidx, &h->misc, &h->part_stats, &h->part_cnt,
                       &h->grp_stats, &h->grp_cnt, &h->grp_arrivals, &h->pairs_dev, &h->counters, &h->trace,
-                      &h->batch_work,
+                      &h->batch_work, &h->batch_scratch,
                       &h->bw_out[0], &h->bw_out[1], &h->bw_out[2], &h->bw_out[3], &h->bw_tq, &h->bw_dell, &h->bw_part};
     for (DevBuf* b : bufs) release(*b);
     for (SetupLane& L : h->lanes) {

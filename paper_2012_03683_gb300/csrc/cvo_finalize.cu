@@ -38,6 +38,16 @@ __global__ void k_init_state(IterState* st)
     update_derived(st);
 }
 
+// the same for many pairs: thread i of the job list's states
+__global__ void k_init_state_b(JobList<StateJob> J)
+{
+    const int i = threadIdx.x;
+    if (i >= J.count) return;
+    IterState* st = J.j[i].st;
+    for (int r = 0; r < 3; ++r) split_df(st->c[r], st->chi[r], st->clo[r]);
+    update_derived(st);
+}
+
 // The 43 statistics and the two counts of a sweep from its group sums, by a
 // block of kStepThreads threads: statistic k by warp k % warps, each lane
 // adding every 32nd group sum in group order (all its loads first), then the
@@ -323,6 +333,20 @@ cudaError_t launch_init_state(IterState* st, cudaStream_t s)
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
     k_init_state<<<1, 1, 0, s>>>(st);
     return cudaGetLastError();
+}
+
+cudaError_t launch_init_state_batch(const StateJob* jobs, int count, cudaStream_t s)
+{
+    for (int c0 = 0; c0 < count; c0 += kJobsPerLaunch) {
+        JobList<StateJob> L;
+        L.count = count - c0 < kJobsPerLaunch ? count - c0 : kJobsPerLaunch;
+        for (int i = 0; i < L.count; ++i) L.j[i] = jobs[c0 + i];
+        g_launch_count.fetch_add(1, std::memory_order_relaxed);
+        k_init_state_b<<<1, kJobsPerLaunch, 0, s>>>(L);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_stats_out(const float2* grp_stats, const unsigned long long* grp_cnt, int nblocks, double* out,

@@ -264,6 +264,143 @@ cudaError_t launch_gather_u32(const unsigned* src, const unsigned* idx, int n, u
 cudaError_t launch_write_items(const LevelDesc* levels, int level, const unsigned* sorted_groups, const unsigned* nch,
                                const unsigned* offsets, int ngroups, int4* items, cudaStream_t s);
 
+// ---- batched setup: one launch for the pairs of a batch ---------------------
+// The per-pair stages of the set-up (boxes, grids, Morton order, groups,
+// work items) for many pairs at once: each launch takes up to
+// kJobsPerLaunch pairs' jobs by value as a kernel parameter, blockIdx.y
+// selects the job, and the kernels run the single-pair kernels' bodies, so
+// the results are the same.  The launchers take a host array of any length
+// and launch once per kJobsPerLaunch jobs.  Every pointer is the pair's own
+// buffer (or its segment of a shared scratch buffer) with room for the
+// counts given.
+constexpr int kJobsPerLaunch = 64;
+
+template <class J>
+struct JobList {
+    int count;
+    J j[kJobsPerLaunch];
+};
+
+// boxes of X and Z (6 words each: min bits x3, max bits x3), the
+// non-finite flag, Z's moments (5 words of 8 bytes) and the features' check
+struct BoxJob {
+    const float* xyz_x;
+    const float* xyz_z;
+    const void* feat_x;
+    const void* feat_z;
+    long long nfx, nfz;   // feature values to check (n D, m D)
+    int n, m, fx_bf16, fz_bf16;
+    unsigned* box_x;
+    unsigned* box_z;
+    int* bad;
+    long long* zstats;
+};
+
+// grid-cell keys (nx, ny, nz, inv = 1 / cell edge) or Morton keys (inv = 1 /
+// Morton cell) of one cloud, with the point indices as values
+struct KeyJob {
+    const float* xyz;
+    unsigned* keys;
+    unsigned* vals;
+    float ox, oy, oz, inv;
+    int n, nx, ny, nz;
+};
+
+// a stable sort of n (key, value) pairs; temp holds 2 * 256 * ceil(n /
+// 1024) words; the result is in (keys, vals) after an even number of
+// passes, else in (keys2, vals2)
+struct SortJob {
+    unsigned* keys;
+    unsigned* vals;
+    unsigned* keys2;
+    unsigned* vals2;
+    unsigned* temp;
+    int n;
+};
+
+struct CellStartJob {
+    const unsigned* keys;   // sorted cell keys
+    int* cell_start;        // ncells + 1
+    int n, ncells;
+};
+
+// records of one cloud in the order given (order NULL: as stored); keys_out
+// (optional) receives the sorted keys
+struct PackJob {
+    const float* xyz;
+    const void* feat;
+    const unsigned* order;
+    const unsigned* keys;
+    unsigned* keys_out;
+    float4* rec;
+    int n, feat_bf16;
+};
+
+// exclusive scan of n words; total (optional) receives the sum
+struct ScanJob {
+    const unsigned* in;
+    unsigned* out;
+    unsigned* total;
+    int n;
+};
+
+// query groups of one level from the Morton-sorted keys: flags (first query
+// of each group), then (with gidx, the flags' scan) the group table
+struct GroupJob {
+    const unsigned* morton;
+    unsigned* flags;
+    const unsigned* gidx;
+    int2* groups;
+    int n, shift;
+};
+
+size_t sort_batch_temp_words(int n);
+cudaError_t launch_boxes_batch(const BoxJob* jobs, int count, cudaStream_t s);   // zeroes its outputs first
+cudaError_t launch_cell_keys_batch(const KeyJob* jobs, int count, cudaStream_t s);
+cudaError_t launch_morton_keys_batch(const KeyJob* jobs, int count, cudaStream_t s);
+cudaError_t radix_sort_batch(const SortJob* jobs, int count, int nbits, int* result_in_alt, cudaStream_t s);
+cudaError_t launch_cell_start_batch(const CellStartJob* jobs, int count, cudaStream_t s);
+cudaError_t launch_pack_batch(const PackJob* jobs, int count, int D, int rs, int rec_bf16, cudaStream_t s);
+cudaError_t launch_scan_batch(const ScanJob* jobs, int count, cudaStream_t s);
+cudaError_t launch_group_flags_batch(const GroupJob* jobs, int count, cudaStream_t s);
+cudaError_t launch_group_write_batch(const GroupJob* jobs, int count, cudaStream_t s);
+
+// work items of one level of many pairs (cvo_sweep.cu), as launch_group_cost,
+// launch_gather_u32 and launch_write_items
+struct CostJob {
+    const LevelDesc* levels;
+    const float4* xrec;
+    const IterState* st;
+    unsigned* keys;
+    unsigned* vals;
+    unsigned* nch;
+    int level, ngroups, m;
+    float rc;
+};
+struct GatherJob {
+    const unsigned* src;
+    const unsigned* idx;
+    unsigned* dst;
+    int n;
+};
+struct ItemsJob {
+    const LevelDesc* levels;
+    const unsigned* sorted_groups;
+    const unsigned* nch;
+    const unsigned* offsets;
+    int4* items;
+    int level, ngroups;
+};
+cudaError_t launch_group_cost_batch(const CostJob* jobs, int count, int rs, int dense, int chunk_len, cudaStream_t s);
+cudaError_t launch_gather_batch(const GatherJob* jobs, int count, cudaStream_t s);
+cudaError_t launch_write_items_batch(const ItemsJob* jobs, int count, cudaStream_t s);
+
+// k_init_state of many pairs (cvo_finalize.cu)
+struct StateJob {
+    IterState* st;
+};
+cudaError_t launch_init_state_batch(const StateJob* jobs, int count, cudaStream_t s);
+
 // setup (cvo_setup.cu)
 cudaError_t launch_bbox(const float* xyz, int n, unsigned* out6, int* bad, cudaStream_t s);
 cudaError_t launch_check_feat(const void* feat, long long count, int bf16, int* bad, cudaStream_t s);

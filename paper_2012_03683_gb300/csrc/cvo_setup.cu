@@ -17,11 +17,16 @@ __device__ __forceinline__ unsigned orderable(float f)
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-__global__ void k_bbox(const float* __restrict__ xyz, int n, unsigned* out6, int* bad)
+// Kernel bodies take their block index and block count (bx, nbx) or their
+// element index, so that the single-pair kernels and the batched ones (one
+// launch for many pairs, blockIdx.y the pair) run the same code.
+
+__device__ __forceinline__ void bbox_body(const float* __restrict__ xyz, int n, unsigned* out6, int* bad, int bx,
+                                          int nbx)
 {
     float mn[3] = {3.0e38f, 3.0e38f, 3.0e38f}, mx[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
     int nonfinite = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int i = bx * blockDim.x + threadIdx.x; i < n; i += nbx * blockDim.x) {
         for (int a = 0; a < 3; ++a) {
             const float v = xyz[3 * (size_t)i + a];
             if (!isfinite(v)) {
@@ -48,11 +53,16 @@ __global__ void k_bbox(const float* __restrict__ xyz, int n, unsigned* out6, int
     }
 }
 
-__global__ void k_check_feat(const void* __restrict__ feat, long long count, int bf16, int* bad)
+__global__ void k_bbox(const float* __restrict__ xyz, int n, unsigned* out6, int* bad)
+{
+    bbox_body(xyz, n, out6, bad, blockIdx.x, gridDim.x);
+}
+
+__device__ __forceinline__ void check_feat_body(const void* __restrict__ feat, long long count, int bf16, int* bad,
+                                                int bx, int nbx)
 {
     int nonfinite = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
-         i += (long long)gridDim.x * blockDim.x) {
+    for (long long i = bx * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)nbx * blockDim.x) {
         float v;
         if (bf16) v = __uint_as_float(((unsigned)((const unsigned short*)feat)[i]) << 16);
         else v = ((const float*)feat)[i];
@@ -61,22 +71,32 @@ __global__ void k_check_feat(const void* __restrict__ feat, long long count, int
     if (__any_sync(0xffffffffu, nonfinite) && (threadIdx.x & 31) == 0) atomicOr(bad, 1);
 }
 
+__global__ void k_check_feat(const void* __restrict__ feat, long long count, int bf16, int* bad)
+{
+    check_feat_body(feat, count, bf16, bad, blockIdx.x, gridDim.x);
+}
+
 __device__ __forceinline__ int cell_of(float v, float o, float inv_h, int n)
 {
     int c = (int)floorf((v - o) * inv_h);
     return min(max(c, 0), n - 1);
 }
 
-__global__ void k_cell_keys(const float* __restrict__ xyz, int n, float ox, float oy, float oz, float inv_h, int nx,
-                            int ny, int nz, unsigned* keys, unsigned* vals)
+__device__ __forceinline__ void cell_keys_body(const float* __restrict__ xyz, int n, float ox, float oy, float oz,
+                                               float inv_h, int nx, int ny, int nz, unsigned* keys, unsigned* vals, int j)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const int cx = cell_of(xyz[3 * (size_t)j + 0], ox, inv_h, nx);
     const int cy = cell_of(xyz[3 * (size_t)j + 1], oy, inv_h, ny);
     const int cz = cell_of(xyz[3 * (size_t)j + 2], oz, inv_h, nz);
     keys[j] = (unsigned)((cz * ny + cy) * nx + cx);
     vals[j] = (unsigned)j;
+}
+
+__global__ void k_cell_keys(const float* __restrict__ xyz, int n, float ox, float oy, float oz, float inv_h, int nx,
+                            int ny, int nz, unsigned* keys, unsigned* vals)
+{
+    cell_keys_body(xyz, n, ox, oy, oz, inv_h, nx, ny, nz, keys, vals, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 __device__ __forceinline__ unsigned spread10(unsigned v)
@@ -89,10 +109,9 @@ __device__ __forceinline__ unsigned spread10(unsigned v)
     return v;
 }
 
-__global__ void k_morton_keys(const float* __restrict__ xyz, int n, float ox, float oy, float oz, float inv_cell,
-                              unsigned* keys, unsigned* vals)
+__device__ __forceinline__ void morton_keys_body(const float* __restrict__ xyz, int n, float ox, float oy, float oz,
+                                                 float inv_cell, unsigned* keys, unsigned* vals, int j)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     unsigned q[3];
     const float o[3] = {ox, oy, oz};
@@ -104,6 +123,12 @@ __global__ void k_morton_keys(const float* __restrict__ xyz, int n, float ox, fl
     vals[j] = (unsigned)j;
 }
 
+__global__ void k_morton_keys(const float* __restrict__ xyz, int n, float ox, float oy, float oz, float inv_cell,
+                              unsigned* keys, unsigned* vals)
+{
+    morton_keys_body(xyz, n, ox, oy, oz, inv_cell, keys, vals, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // ---- stable LSD radix sort, 8-bit digits ------------------------------------
 
 constexpr int kSortThreads = 256;
@@ -111,29 +136,38 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortTile = 1024;                  // keys per block (small tiles: the sorts here are short and latency bound)
 constexpr int kSortSub = kSortTile / kSortWarps; // keys per warp
 
-__global__ void k_radix_hist(const unsigned* __restrict__ keys, int n, int shift, unsigned* hist, int nb)
+// tile bx of nb: its digit counts into hist[digit * nb + bx]
+__device__ __forceinline__ void radix_hist_body(const unsigned* __restrict__ keys, int n, int shift, unsigned* hist,
+                                                int nb, int bx)
 {
     __shared__ unsigned cnt[256];
     cnt[threadIdx.x] = 0;
     __syncthreads();
-    const int base = blockIdx.x * kSortTile;
+    const int base = bx * kSortTile;
     for (int k = threadIdx.x; k < kSortTile; k += kSortThreads) {
         const int i = base + k;
         if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1u);
     }
     __syncthreads();
-    hist[threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
+    hist[threadIdx.x * nb + bx] = cnt[threadIdx.x];
 }
 
-__global__ void k_radix_scatter(const unsigned* __restrict__ keys, const unsigned* __restrict__ vals, int n,
-                                int shift, const unsigned* __restrict__ offs, int nb, unsigned* keys_out,
-                                unsigned* vals_out)
+__global__ void k_radix_hist(const unsigned* __restrict__ keys, int n, int shift, unsigned* hist, int nb)
+{
+    radix_hist_body(keys, n, shift, hist, nb, blockIdx.x);
+}
+
+// tile bx of nb: its keys scattered stably to their offsets (offs: the
+// exclusive scan of hist)
+__device__ __forceinline__ void radix_scatter_body(const unsigned* __restrict__ keys, const unsigned* __restrict__ vals,
+                                                   int n, int shift, const unsigned* __restrict__ offs, int nb,
+                                                   unsigned* keys_out, unsigned* vals_out, int bx)
 {
     __shared__ unsigned wcnt[kSortWarps][256];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int d = threadIdx.x; d < kSortWarps * 256; d += kSortThreads) (&wcnt[0][0])[d] = 0;
     __syncthreads();
-    const int base = blockIdx.x * kSortTile + warp * kSortSub;
+    const int base = bx * kSortTile + warp * kSortSub;
     for (int r = 0; r < kSortSub; r += 32) {
         const int i = base + r + lane;
         if (i < n) atomicAdd(&wcnt[warp][(keys[i] >> shift) & 255u], 1u);
@@ -141,7 +175,7 @@ __global__ void k_radix_scatter(const unsigned* __restrict__ keys, const unsigne
     __syncthreads();
     {   // per digit: block offset plus the counts of the earlier warps
         const int d = threadIdx.x;
-        unsigned run = offs[d * nb + blockIdx.x];
+        unsigned run = offs[d * nb + bx];
         for (int w = 0; w < kSortWarps; ++w) {
             const unsigned c = wcnt[w][d];
             wcnt[w][d] = run;
@@ -166,6 +200,13 @@ __global__ void k_radix_scatter(const unsigned* __restrict__ keys, const unsigne
         }
         __syncwarp();
     }
+}
+
+__global__ void k_radix_scatter(const unsigned* __restrict__ keys, const unsigned* __restrict__ vals, int n,
+                                int shift, const unsigned* __restrict__ offs, int nb, unsigned* keys_out,
+                                unsigned* vals_out)
+{
+    radix_scatter_body(keys, vals, n, shift, offs, nb, keys_out, vals_out, blockIdx.x);
 }
 
 // Short arrays (n <= kSmallSort): the whole LSD radix sort in one block, in
@@ -250,8 +291,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_sort_small(unsigned* keys, un
     }
 }
 
-// single-block exclusive scan; total (optional) receives the sum
-__global__ void k_scan_single(const unsigned* __restrict__ in, unsigned* out, int n, unsigned* total)
+// single-block (1024 threads) exclusive scan; total (optional) receives the sum
+__device__ __forceinline__ void scan_body(const unsigned* __restrict__ in, unsigned* out, int n, unsigned* total)
 {
     __shared__ unsigned sums[1024];
     const int t = threadIdx.x;
@@ -276,9 +317,14 @@ __global__ void k_scan_single(const unsigned* __restrict__ in, unsigned* out, in
     if (t == 1023 && total) *total = sums[1023];
 }
 
-__global__ void k_cell_start(const unsigned* __restrict__ keys, int n, int ncells, int* cell_start)
+__global__ void k_scan_single(const unsigned* __restrict__ in, unsigned* out, int n, unsigned* total)
 {
-    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    scan_body(in, out, n, total);
+}
+
+__device__ __forceinline__ void cell_start_body(const unsigned* __restrict__ keys, int n, int ncells, int* cell_start,
+                                                long long c)
+{
     if (c > ncells) return;
     int lo = 0, hi = n;   // first index with key >= c
     while (lo < hi) {
@@ -289,16 +335,21 @@ __global__ void k_cell_start(const unsigned* __restrict__ keys, int n, int ncell
     cell_start[c] = lo;
 }
 
+__global__ void k_cell_start(const unsigned* __restrict__ keys, int n, int ncells, int* cell_start)
+{
+    cell_start_body(keys, n, ncells, cell_start, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
+
 __device__ __forceinline__ unsigned short f32_to_bf16_bits(float f)
 {
     const unsigned u = __float_as_uint(f);
     return (unsigned short)((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
 }
 
-__global__ void k_pack(const float* __restrict__ xyz, const void* __restrict__ feat, int feat_bf16, int D,
-                       const unsigned* __restrict__ order, int n, float4* rec, int rs, int rec_bf16)
+__device__ __forceinline__ void pack_body(const float* __restrict__ xyz, const void* __restrict__ feat, int feat_bf16,
+                                          int D, const unsigned* __restrict__ order, int n, float4* rec, int rs,
+                                          int rec_bf16, int s)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int j = order ? (int)order[s] : s;
     float4* r = rec + (size_t)s * rs;
@@ -326,6 +377,12 @@ __global__ void k_pack(const float* __restrict__ xyz, const void* __restrict__ f
     }
 }
 
+__global__ void k_pack(const float* __restrict__ xyz, const void* __restrict__ feat, int feat_bf16, int D,
+                       const unsigned* __restrict__ order, int n, float4* rec, int rs, int rec_bf16)
+{
+    pack_body(xyz, feat, feat_bf16, D, order, n, rec, rs, rec_bf16, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 __device__ __forceinline__ int lower_bound_u32(const unsigned* a, int n, unsigned long long v)
 {
     int lo = 0, hi = n;
@@ -337,23 +394,35 @@ __device__ __forceinline__ int lower_bound_u32(const unsigned* a, int n, unsigne
     return lo;
 }
 
-__global__ void k_group_flags(const unsigned* __restrict__ morton, int n, int shift, unsigned* flags)
+__device__ __forceinline__ void group_flags_body(const unsigned* __restrict__ morton, int n, int shift, unsigned* flags,
+                                                 int i)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const unsigned long long seg = (unsigned long long)(morton[i] >> shift);
     const int start = lower_bound_u32(morton, n, seg << shift);
     flags[i] = ((i - start) % 32 == 0) ? 1u : 0u;
 }
 
-__global__ void k_group_write(const unsigned* __restrict__ morton, const unsigned* __restrict__ flags,
-                              const unsigned* __restrict__ gidx, int n, int shift, int2* groups)
+__global__ void k_group_flags(const unsigned* __restrict__ morton, int n, int shift, unsigned* flags)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    group_flags_body(morton, n, shift, flags, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__device__ __forceinline__ void group_write_body(const unsigned* __restrict__ morton,
+                                                 const unsigned* __restrict__ flags,
+                                                 const unsigned* __restrict__ gidx, int n, int shift, int2* groups,
+                                                 int i)
+{
     if (i >= n || !flags[i]) return;
     const unsigned long long seg = (unsigned long long)(morton[i] >> shift);
     const int end = lower_bound_u32(morton, n, (seg + 1ull) << shift);
     groups[gidx[i]] = make_int2(i, min(32, end - i));
+}
+
+__global__ void k_group_write(const unsigned* __restrict__ morton, const unsigned* __restrict__ flags,
+                              const unsigned* __restrict__ gidx, int n, int shift, int2* groups)
+{
+    group_write_body(morton, flags, gidx, n, shift, groups, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Deterministic sum of n floats: per-thread double-float partials in a fixed
@@ -401,11 +470,11 @@ __device__ __forceinline__ long long warp_sum_ll(long long v)
     return v;
 }
 
-__global__ void __launch_bounds__(kZStatsThreads) k_zsum(const float* __restrict__ xyz, int n, long long* out)
+__device__ __forceinline__ void zsum_body(const float* __restrict__ xyz, int n, long long* out, int bx, int nbx)
 {
     __shared__ long long part[kZStatsThreads / 32][3];
     long long s[3] = {0, 0, 0};
-    for (int i = blockIdx.x * kZStatsThreads + threadIdx.x; i < n; i += gridDim.x * kZStatsThreads)
+    for (int i = bx * kZStatsThreads + threadIdx.x; i < n; i += nbx * kZStatsThreads)
         for (int a = 0; a < 3; ++a) s[a] += __float2ll_rn(xyz[3 * (size_t)i + a] * kCoordScale);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int a = 0; a < 3; ++a) {
@@ -420,7 +489,12 @@ __global__ void __launch_bounds__(kZStatsThreads) k_zsum(const float* __restrict
     }
 }
 
-__global__ void __launch_bounds__(kZStatsThreads) k_zspread(const float* __restrict__ xyz, int n, long long* out)
+__global__ void __launch_bounds__(kZStatsThreads) k_zsum(const float* __restrict__ xyz, int n, long long* out)
+{
+    zsum_body(xyz, n, out, blockIdx.x, gridDim.x);
+}
+
+__device__ __forceinline__ void zspread_body(const float* __restrict__ xyz, int n, long long* out, int bx, int nbx)
 {
     __shared__ long long part[kZStatsThreads / 32];
     __shared__ float mx_part[kZStatsThreads / 32];
@@ -434,7 +508,7 @@ __global__ void __launch_bounds__(kZStatsThreads) k_zspread(const float* __restr
     const float mhi[3] = {m_hl[0], m_hl[1], m_hl[2]}, mlo[3] = {m_hl[3], m_hl[4], m_hl[5]};
     long long s = 0;
     float mx = 0.0f;
-    for (int i = blockIdx.x * kZStatsThreads + threadIdx.x; i < n; i += gridDim.x * kZStatsThreads) {
+    for (int i = bx * kZStatsThreads + threadIdx.x; i < n; i += nbx * kZStatsThreads) {
         float q = 0.0f;
         for (int a = 0; a < 3; ++a) {
             const float e = __fsub_rn(__fsub_rn(xyz[3 * (size_t)i + a], mhi[a]), mlo[a]);
@@ -461,6 +535,128 @@ __global__ void __launch_bounds__(kZStatsThreads) k_zspread(const float* __restr
         atomicAdd(reinterpret_cast<unsigned long long*>(out + 3), (unsigned long long)t);
         atomicMax(reinterpret_cast<unsigned*>(out + 4), __float_as_uint(m));
     }
+}
+
+__global__ void __launch_bounds__(kZStatsThreads) k_zspread(const float* __restrict__ xyz, int n, long long* out)
+{
+    zspread_body(xyz, n, out, blockIdx.x, gridDim.x);
+}
+
+// ---- batched kernels: blockIdx.y is the job ---------------------------------
+
+__global__ void k_boxes_init_b(JobList<BoxJob> J)
+{
+    const BoxJob& b = J.j[blockIdx.y];
+    const int t = threadIdx.x;
+    if (t < 6) {   // minima start at the largest orderable value, maxima at 0
+        b.box_x[t] = t < 3 ? 0xffffffffu : 0u;
+        b.box_z[t] = t < 3 ? 0xffffffffu : 0u;
+    }
+    if (t == 6) *b.bad = 0;
+    if (t >= 8 && t < 13) b.zstats[t - 8] = 0;
+}
+
+__global__ void k_bbox_b(JobList<BoxJob> J)
+{
+    const BoxJob& b = J.j[blockIdx.y];
+    if (blockIdx.z == 0) bbox_body(b.xyz_x, b.n, b.box_x, b.bad, blockIdx.x, gridDim.x);
+    else bbox_body(b.xyz_z, b.m, b.box_z, b.bad, blockIdx.x, gridDim.x);
+}
+
+__global__ void k_check_feat_b(JobList<BoxJob> J)
+{
+    const BoxJob& b = J.j[blockIdx.y];
+    if (blockIdx.z == 0) {
+        if (b.nfx > 0) check_feat_body(b.feat_x, b.nfx, b.fx_bf16, b.bad, blockIdx.x, gridDim.x);
+    } else if (b.nfz > 0) {
+        check_feat_body(b.feat_z, b.nfz, b.fz_bf16, b.bad, blockIdx.x, gridDim.x);
+    }
+}
+
+__global__ void __launch_bounds__(kZStatsThreads) k_zsum_b(JobList<BoxJob> J)
+{
+    const BoxJob& b = J.j[blockIdx.y];
+    if (b.m > 0) zsum_body(b.xyz_z, b.m, b.zstats, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kZStatsThreads) k_zspread_b(JobList<BoxJob> J)
+{
+    const BoxJob& b = J.j[blockIdx.y];
+    if (b.m > 0) zspread_body(b.xyz_z, b.m, b.zstats, blockIdx.x, gridDim.x);
+}
+
+__global__ void k_cell_keys_b(JobList<KeyJob> J)
+{
+    const KeyJob& k = J.j[blockIdx.y];
+    cell_keys_body(k.xyz, k.n, k.ox, k.oy, k.oz, k.inv, k.nx, k.ny, k.nz, k.keys, k.vals,
+                   blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void k_morton_keys_b(JobList<KeyJob> J)
+{
+    const KeyJob& k = J.j[blockIdx.y];
+    morton_keys_body(k.xyz, k.n, k.ox, k.oy, k.oz, k.inv, k.keys, k.vals, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__device__ __forceinline__ int sort_tiles(int n) { return (n + kSortTile - 1) / kSortTile; }
+
+// parity 0: (keys, vals) -> (keys2, vals2); 1: the other way
+__global__ void k_radix_hist_b(JobList<SortJob> J, int shift, int parity)
+{
+    const SortJob& q = J.j[blockIdx.y];
+    const int nb = sort_tiles(q.n);
+    if ((int)blockIdx.x >= nb) return;
+    radix_hist_body(parity ? q.keys2 : q.keys, q.n, shift, q.temp, nb, blockIdx.x);
+}
+
+__global__ void k_radix_scan_b(JobList<SortJob> J)
+{
+    const SortJob& q = J.j[blockIdx.y];
+    const int nb = sort_tiles(q.n);
+    scan_body(q.temp, q.temp + 256 * nb, 256 * nb, nullptr);
+}
+
+__global__ void k_radix_scatter_b(JobList<SortJob> J, int shift, int parity)
+{
+    const SortJob& q = J.j[blockIdx.y];
+    const int nb = sort_tiles(q.n);
+    if ((int)blockIdx.x >= nb) return;
+    if (parity)
+        radix_scatter_body(q.keys2, q.vals2, q.n, shift, q.temp + 256 * nb, nb, q.keys, q.vals, blockIdx.x);
+    else
+        radix_scatter_body(q.keys, q.vals, q.n, shift, q.temp + 256 * nb, nb, q.keys2, q.vals2, blockIdx.x);
+}
+
+__global__ void k_cell_start_b(JobList<CellStartJob> J)
+{
+    const CellStartJob& c = J.j[blockIdx.y];
+    cell_start_body(c.keys, c.n, c.ncells, c.cell_start, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
+
+__global__ void k_pack_b(JobList<PackJob> J, int D, int rs, int rec_bf16)
+{
+    const PackJob& q = J.j[blockIdx.y];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    pack_body(q.xyz, q.feat, q.feat_bf16, D, q.order, q.n, q.rec, rs, rec_bf16, i);
+    if (q.keys_out != nullptr && i < q.n) q.keys_out[i] = q.keys[i];
+}
+
+__global__ void k_scan_b(JobList<ScanJob> J)
+{
+    const ScanJob& q = J.j[blockIdx.y];
+    scan_body(q.in, q.out, q.n, q.total);
+}
+
+__global__ void k_group_flags_b(JobList<GroupJob> J)
+{
+    const GroupJob& q = J.j[blockIdx.y];
+    group_flags_body(q.morton, q.n, q.shift, q.flags, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void k_group_write_b(JobList<GroupJob> J)
+{
+    const GroupJob& q = J.j[blockIdx.y];
+    group_write_body(q.morton, q.flags, q.gidx, q.n, q.shift, q.groups, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
@@ -612,6 +808,148 @@ cudaError_t launch_group_write(const unsigned* sorted_morton, const unsigned* fl
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
     k_group_write<<<blocks_for(n, 256), 256, 0, s>>>(sorted_morton, flags, gidx, n, shift, groups);
     return cudaGetLastError();
+}
+
+// ---- batched launchers ----------------------------------------------------------
+
+namespace {
+
+// f(list) for each run of up to kJobsPerLaunch jobs
+template <class J, class F>
+cudaError_t each_chunk(const J* jobs, int count, F&& f)
+{
+    for (int c0 = 0; c0 < count; c0 += kJobsPerLaunch) {
+        JobList<J> L;
+        L.count = min(kJobsPerLaunch, count - c0);
+        for (int i = 0; i < L.count; ++i) L.j[i] = jobs[c0 + i];
+        const cudaError_t e = f(L);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+size_t sort_batch_temp_words(int n)
+{
+    const int nb = (n + kSortTile - 1) / kSortTile;
+    return (size_t)2 * 256 * (nb > 0 ? nb : 1);
+}
+
+cudaError_t launch_boxes_batch(const BoxJob* jobs, int count, cudaStream_t s)
+{
+    return each_chunk(jobs, count, [&](const JobList<BoxJob>& L) {
+        int nmax = 1, mmax = 1;
+        long long fmax = 1;
+        for (int i = 0; i < L.count; ++i) {
+            nmax = max(nmax, max(L.j[i].n, L.j[i].m));
+            mmax = max(mmax, L.j[i].m);
+            fmax = max(fmax, max(L.j[i].nfx, L.j[i].nfz));
+        }
+        g_launch_count.fetch_add(5, std::memory_order_relaxed);
+        k_boxes_init_b<<<dim3(1, L.count), 32, 0, s>>>(L);
+        k_bbox_b<<<dim3(min(blocks_for(nmax, 256), 64), L.count, 2), 256, 0, s>>>(L);
+        const int nz = min(blocks_for(mmax, 4 * kZStatsThreads), 64);
+        k_zsum_b<<<dim3(nz, L.count), kZStatsThreads, 0, s>>>(L);
+        k_zspread_b<<<dim3(nz, L.count), kZStatsThreads, 0, s>>>(L);
+        k_check_feat_b<<<dim3((int)min((long long)blocks_for(fmax, 256), 256LL), L.count, 2), 256, 0, s>>>(L);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_cell_keys_batch(const KeyJob* jobs, int count, cudaStream_t s)
+{
+    return each_chunk(jobs, count, [&](const JobList<KeyJob>& L) {
+        int nmax = 1;
+        for (int i = 0; i < L.count; ++i) nmax = max(nmax, L.j[i].n);
+        g_launch_count.fetch_add(1, std::memory_order_relaxed);
+        k_cell_keys_b<<<dim3(blocks_for(nmax, 256), L.count), 256, 0, s>>>(L);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_morton_keys_batch(const KeyJob* jobs, int count, cudaStream_t s)
+{
+    return each_chunk(jobs, count, [&](const JobList<KeyJob>& L) {
+        int nmax = 1;
+        for (int i = 0; i < L.count; ++i) nmax = max(nmax, L.j[i].n);
+        g_launch_count.fetch_add(1, std::memory_order_relaxed);
+        k_morton_keys_b<<<dim3(blocks_for(nmax, 256), L.count), 256, 0, s>>>(L);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t radix_sort_batch(const SortJob* jobs, int count, int nbits, int* result_in_alt, cudaStream_t s)
+{
+    int passes = 0;
+    for (int shift = 0; shift < nbits; shift += 8) ++passes;
+    *result_in_alt = passes & 1;
+    return each_chunk(jobs, count, [&](const JobList<SortJob>& L) {
+        int nbmax = 1;
+        for (int i = 0; i < L.count; ++i) nbmax = max(nbmax, (L.j[i].n + kSortTile - 1) / kSortTile);
+        int parity = 0;
+        for (int shift = 0; shift < nbits; shift += 8) {
+            g_launch_count.fetch_add(3, std::memory_order_relaxed);
+            k_radix_hist_b<<<dim3(nbmax, L.count), kSortThreads, 0, s>>>(L, shift, parity);
+            k_radix_scan_b<<<dim3(1, L.count), 1024, 0, s>>>(L);
+            k_radix_scatter_b<<<dim3(nbmax, L.count), kSortThreads, 0, s>>>(L, shift, parity);
+            parity ^= 1;
+        }
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_cell_start_batch(const CellStartJob* jobs, int count, cudaStream_t s)
+{
+    return each_chunk(jobs, count, [&](const JobList<CellStartJob>& L) {
+        long long cmax = 1;
+        for (int i = 0; i < L.count; ++i) cmax = max(cmax, (long long)L.j[i].ncells + 1);
+        g_launch_count.fetch_add(1, std::memory_order_relaxed);
+        k_cell_start_b<<<dim3(blocks_for(cmax, 256), L.count), 256, 0, s>>>(L);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_pack_batch(const PackJob* jobs, int count, int D, int rs, int rec_bf16, cudaStream_t s)
+{
+    return each_chunk(jobs, count, [&](const JobList<PackJob>& L) {
+        int nmax = 1;
+        for (int i = 0; i < L.count; ++i) nmax = max(nmax, L.j[i].n);
+        g_launch_count.fetch_add(1, std::memory_order_relaxed);
+        k_pack_b<<<dim3(blocks_for(nmax, 128), L.count), 128, 0, s>>>(L, D, rs, rec_bf16);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_scan_batch(const ScanJob* jobs, int count, cudaStream_t s)
+{
+    return each_chunk(jobs, count, [&](const JobList<ScanJob>& L) {
+        g_launch_count.fetch_add(1, std::memory_order_relaxed);
+        k_scan_b<<<dim3(1, L.count), 1024, 0, s>>>(L);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_group_flags_batch(const GroupJob* jobs, int count, cudaStream_t s)
+{
+    return each_chunk(jobs, count, [&](const JobList<GroupJob>& L) {
+        int nmax = 1;
+        for (int i = 0; i < L.count; ++i) nmax = max(nmax, L.j[i].n);
+        g_launch_count.fetch_add(1, std::memory_order_relaxed);
+        k_group_flags_b<<<dim3(blocks_for(nmax, 256), L.count), 256, 0, s>>>(L);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_group_write_batch(const GroupJob* jobs, int count, cudaStream_t s)
+{
+    return each_chunk(jobs, count, [&](const JobList<GroupJob>& L) {
+        int nmax = 1;
+        for (int i = 0; i < L.count; ++i) nmax = max(nmax, L.j[i].n);
+        g_launch_count.fetch_add(1, std::memory_order_relaxed);
+        k_group_write_b<<<dim3(blocks_for(nmax, 256), L.count), 256, 0, s>>>(L);
+        return cudaGetLastError();
+    });
 }
 
 }  // namespace cvo

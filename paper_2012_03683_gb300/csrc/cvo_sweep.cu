@@ -388,13 +388,11 @@ cudaError_t grad_t(const GradArgs& g, int nblocks, cudaStream_t s)
 
 // One warp per query group: the length of the group's candidate stream at the
 // state's pose and cutoff radius rc, and the group's chunk count.
-__global__ void __launch_bounds__(128) k_group_cost(const LevelDesc* __restrict__ levels, int level, int ngroups,
-                                                    const float4* __restrict__ xrec, int m, int rs, int dense,
-                                                    const IterState* __restrict__ st, float rc, int chunk_len,
-                                                    unsigned* keys, unsigned* vals, unsigned* nch)
+__device__ __forceinline__ void group_cost_body(const LevelDesc* __restrict__ levels, int level, int ngroups,
+                                                const float4* __restrict__ xrec, int m, int rs, int dense,
+                                                const IterState* __restrict__ st, float rc, int chunk_len,
+                                                unsigned* keys, unsigned* vals, unsigned* nch, int g, int lane)
 {
-    const int lane = threadIdx.x & 31;
-    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (g >= ngroups) return;   // warp-uniform
     if (chunk_len <= 0) {       // uniform items: Morton order, kChunks each
         if (lane == 0) {
@@ -419,6 +417,23 @@ __global__ void __launch_bounds__(128) k_group_cost(const LevelDesc* __restrict_
         vals[g] = (unsigned)g;
         nch[g] = (unsigned)max(1, min(kMaxChunks, c));
     }
+}
+
+__global__ void __launch_bounds__(128) k_group_cost(const LevelDesc* __restrict__ levels, int level, int ngroups,
+                                                    const float4* __restrict__ xrec, int m, int rs, int dense,
+                                                    const IterState* __restrict__ st, float rc, int chunk_len,
+                                                    unsigned* keys, unsigned* vals, unsigned* nch)
+{
+    group_cost_body(levels, level, ngroups, xrec, m, rs, dense, st, rc, chunk_len, keys, vals, nch,
+                    (blockIdx.x * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31);
+}
+
+// the same for many pairs (blockIdx.y: the job)
+__global__ void __launch_bounds__(128) k_group_cost_b(JobList<CostJob> J, int rs, int dense, int chunk_len)
+{
+    const CostJob& q = J.j[blockIdx.y];
+    group_cost_body(q.levels, q.level, q.ngroups, q.xrec, q.m, rs, dense, q.st, q.rc, chunk_len, q.keys, q.vals, q.nch,
+                    (blockIdx.x * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31);
 }
 
 // Work items of level Ld for the next sweep, group after group in group
@@ -515,6 +530,38 @@ __global__ void k_write_items(const LevelDesc* __restrict__ levels, int level, c
     for (int k = 0; k < n; ++k) items[off + k] = make_int4(grp.x, grp.y, k | (n << 16), g);
 }
 
+__global__ void k_gather_b(JobList<GatherJob> J)
+{
+    const GatherJob& q = J.j[blockIdx.y];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < q.n) q.dst[i] = q.src[q.idx[i]];
+}
+
+__global__ void k_write_items_b(JobList<ItemsJob> J)
+{
+    const ItemsJob& q = J.j[blockIdx.y];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= q.ngroups) return;
+    const int g = (int)q.sorted_groups[i];
+    const int2 grp = q.levels[q.level].groups[g];
+    const int n = (int)q.nch[g];
+    const unsigned off = q.offsets[i];
+    for (int k = 0; k < n; ++k) q.items[off + k] = make_int4(grp.x, grp.y, k | (n << 16), g);
+}
+
+template <class J, class F>
+cudaError_t each_chunk(const J* jobs, int count, F&& f)
+{
+    for (int c0 = 0; c0 < count; c0 += kJobsPerLaunch) {
+        JobList<J> L;
+        L.count = min(kJobsPerLaunch, count - c0);
+        for (int i = 0; i < L.count; ++i) L.j[i] = jobs[c0 + i];
+        const cudaError_t e = f(L);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 template <class Feat>
 cudaError_t info_t(int rs, SweepLaunch* out)
 {
@@ -599,6 +646,39 @@ cudaError_t launch_gather_u32(const unsigned* src, const unsigned* idx, int n, u
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
     k_gather_u32<<<(n + 255) / 256, 256, 0, s>>>(src, idx, n, dst);
     return cudaGetLastError();
+}
+
+cudaError_t launch_group_cost_batch(const CostJob* jobs, int count, int rs, int dense, int chunk_len, cudaStream_t s)
+{
+    return each_chunk(jobs, count, [&](const JobList<CostJob>& L) {
+        int gmax = 1;
+        for (int i = 0; i < L.count; ++i) gmax = max(gmax, L.j[i].ngroups);
+        g_launch_count.fetch_add(1, std::memory_order_relaxed);
+        k_group_cost_b<<<dim3((gmax + 3) / 4, L.count), 128, 0, s>>>(L, rs, dense, chunk_len);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_gather_batch(const GatherJob* jobs, int count, cudaStream_t s)
+{
+    return each_chunk(jobs, count, [&](const JobList<GatherJob>& L) {
+        int nmax = 1;
+        for (int i = 0; i < L.count; ++i) nmax = max(nmax, L.j[i].n);
+        g_launch_count.fetch_add(1, std::memory_order_relaxed);
+        k_gather_b<<<dim3((nmax + 255) / 256, L.count), 256, 0, s>>>(L);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_write_items_batch(const ItemsJob* jobs, int count, cudaStream_t s)
+{
+    return each_chunk(jobs, count, [&](const JobList<ItemsJob>& L) {
+        int gmax = 1;
+        for (int i = 0; i < L.count; ++i) gmax = max(gmax, L.j[i].ngroups);
+        g_launch_count.fetch_add(1, std::memory_order_relaxed);
+        k_write_items_b<<<dim3((gmax + 127) / 128, L.count), 128, 0, s>>>(L);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_write_items(const LevelDesc* levels, int level, const unsigned* sorted_groups, const unsigned* nch,

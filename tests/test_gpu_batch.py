@@ -85,17 +85,62 @@ def test_batch_with_empty_pair_and_host_buffers():
     assert er <= POSE_TOL and et <= POSE_TOL
 
 
-def test_phased_setup_of_device_batches_equals_per_pair_setup():
-    """A batch of device-resident pairs runs each setup phase for all pairs
-    before one wait; a batch with a host-resident pair sets the pairs up one
-    after another.  The kernels and their order per pair are the same, so the
-    results are bitwise equal."""
+def host_last(pairs, args):
+    """The same batch with its last pair in host memory."""
+    q = pairs[-1]
+    return args[:-1] + [(q.X, q.Z, np.eye(4), scenes.bf16_bits(q.FX), scenes.bf16_bits(q.FZ))]
+
+
+def assert_bitwise_equal(a, b):
+    (Ta, ia, _), (Tb, ib, _) = a, b
+    for k in range(len(ia)):
+        assert np.array_equal(Ta[k], Tb[k]), k
+        assert ia[k]["F"] == ib[k]["F"] and ia[k]["pairs"] == ib[k]["pairs"] and ia[k]["iters"] == ib[k]["iters"], k
+
+
+def batched_and_pairwise(h, args, monkeypatch):
+    """A batch set up by the batched stages (one launch per stage for all
+    pairs), and set up pair by pair (CVO_BATCH_SETUP=pairs)."""
+    got = h.register_batch(args)
+    with monkeypatch.context() as m:
+        m.setenv("CVO_BATCH_SETUP", "pairs")
+        ref = h.register_batch(args)
+    return got, ref
+
+
+def test_batched_setup_equals_per_pair_setup(monkeypatch):
+    """The batched set-up runs the per-pair kernels' bodies on the same data
+    with stable sorts, so the registrations are bitwise those of the
+    pair-by-pair set-up -- here with clouds above and below the one-block
+    sort's size; a batch with a host-resident pair (copied to the device
+    first) gives the same bits."""
     pairs, args = small_batch(n_pairs=4, seed=31)
-    host_last = args[:3] + [(pairs[3].X, pairs[3].Z, np.eye(4), scenes.bf16_bits(pairs[3].FX),
-                             scenes.bf16_bits(pairs[3].FZ))]
+    pairs2 = scenes.batch_pairs(n_pairs=2, seed=32, n_range=(9000, 12000))
+    for q in pairs2:
+        args.append((torch.tensor(q.X, device="cuda"), torch.tensor(q.Z, device="cuda"), np.eye(4),
+                     torch.tensor(q.FX, device="cuda").to(torch.bfloat16),
+                     torch.tensor(q.FZ, device="cuda").to(torch.bfloat16)))
+    pairs = pairs + pairs2
     with cvo.CVO(blocks=pairs[0].blocks, **KW) as h:
-        T_dev, infos_dev, _ = h.register_batch(args)
-        T_mix, infos_mix, _ = h.register_batch(host_last)
-    for k in range(4):
-        assert np.array_equal(T_dev[k], T_mix[k]), k
-        assert infos_dev[k]["F"] == infos_mix[k]["F"] and infos_dev[k]["pairs"] == infos_mix[k]["pairs"]
+        got, ref = batched_and_pairwise(h, args, monkeypatch)
+        assert_bitwise_equal(got, ref)
+        assert_bitwise_equal(got, h.register_batch(host_last(pairs, args)))
+
+
+def test_batched_setup_over_several_launches_and_levels(monkeypatch):
+    """More pairs than one batched launch takes (64), annealed over several
+    grid levels: still bitwise the pair-by-pair set-up's results."""
+    pairs = scenes.batch_pairs(n_pairs=70, seed=33, n_range=(200, 900))
+    args = [(torch.tensor(q.X, device="cuda"), torch.tensor(q.Z, device="cuda"), np.eye(4),
+             torch.tensor(q.FX, device="cuda").to(torch.bfloat16), torch.tensor(q.FZ, device="cuda").to(torch.bfloat16))
+            for q in pairs]
+    kw = dict(ell=0.4, ell_min=0.1, anneal=True, cutoff_mult=3.0, max_iters=30)
+    with cvo.CVO(blocks=pairs[0].blocks, **kw) as h:
+        assert_bitwise_equal(*batched_and_pairwise(h, args, monkeypatch))
+
+
+def test_batched_setup_dense(monkeypatch):
+    pairs, args = small_batch(n_pairs=3, seed=34)
+    args = [(X[:600], Z[:500], T, FX[:600], FZ[:500]) for X, Z, T, FX, FZ in args]
+    with cvo.CVO(blocks=pairs[0].blocks, ell=0.2, cutoff_mult=0.0, max_iters=10) as h:
+        assert_bitwise_equal(*batched_and_pairwise(h, args, monkeypatch))
