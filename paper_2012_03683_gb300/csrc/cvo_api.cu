@@ -161,6 +161,11 @@ struct cvo_handle_s {
     DevBuf part_stats, part_cnt, grp_stats, grp_cnt, grp_arrivals, pairs_dev, counters, trace;
     DevBuf batch_work;   // per pair of a batch: work items left (the batched step re-splits the grid by them)
     DevBuf batch_scratch;   // a batch's set-up: every pair's segment of the sort and scan scratch
+    // many small host <-> device copies through one staging copy (upload_blocks, fetch_states)
+    DevBuf d_stage;
+    unsigned char* h_stage = nullptr;   // pinned, h_stage_cap bytes
+    size_t h_stage_cap = 0;
+    cudaEvent_t stage_ev = nullptr;     // after the last copy out of h_stage
     // gradients with respect to the inputs: device outputs for host callers,
     // per-query terms of dF/dl and their sum
     DevBuf bw_out[4], bw_tq, bw_dell, bw_part;
@@ -606,7 +611,9 @@ cvo_status prepare_build(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo
 }
 
 // Phase 3: the level descriptors, with the group counts (hm).
-cvo_status prepare_finish(cvo_handle h, PairRes& P, const unsigned* hm)
+// The level descriptors on the host (P.ld), with the group counts (hm); the
+// device copy's buffer ensured.
+cvo_status level_descs(PairRes& P, const unsigned* hm)
 {
     const int n = P.n;
     for (int k = 0; k < P.nlevels; ++k) {
@@ -627,6 +634,12 @@ cvo_status prepare_finish(cvo_handle h, PairRes& P, const unsigned* hm)
     }
     P.max_items = 1;
     CVO_CUDA(ensure(P.levels_dev, sizeof(P.ld)));
+    return CVO_OK;
+}
+
+cvo_status prepare_finish(cvo_handle h, PairRes& P, const unsigned* hm)
+{
+    CVO_TRY(level_descs(P, hm));
     CVO_CUDA(cudaMemcpyAsync(P.levels_dev.p, P.ld, P.nlevels * sizeof(LevelDesc), cudaMemcpyHostToDevice, h->s));
     return CVO_OK;
 }
@@ -681,9 +694,10 @@ cvo_status plan_launch(cvo_handle h, PairRes& P, bool planned, unsigned* dev)
     return CVO_OK;
 }
 
-cvo_status plan_finish(cvo_handle h, PairRes& P, bool planned, const unsigned* hm)
+// The planned items into the level descriptors on the host (P.ld), with the
+// item counts (hm).
+void plan_descs(PairRes& P, bool planned, const unsigned* hm)
 {
-    if (P.n == 0) return CVO_OK;
     int max_items = 1;
     for (int k = 0; k < P.nlevels; ++k) {
         P.lv[k].nitems = (int)hm[16 + k];
@@ -693,6 +707,12 @@ cvo_status plan_finish(cvo_handle h, PairRes& P, bool planned, const unsigned* h
         max_items = std::max(max_items, P.lv[k].nitems);
     }
     P.max_items = max_items;
+}
+
+cvo_status plan_finish(cvo_handle h, PairRes& P, bool planned, const unsigned* hm)
+{
+    if (P.n == 0) return CVO_OK;
+    plan_descs(P, planned, hm);
     CVO_CUDA(cudaMemcpyAsync(P.levels_dev.p, P.ld, P.nlevels * sizeof(LevelDesc), cudaMemcpyHostToDevice, h->s));
     return CVO_OK;
 }
@@ -739,9 +759,10 @@ cvo_status ensure_host_states(cvo_handle h, int n)
 // Initial state of one pair; host copy in h->h_state[slot].
 enum PlanMode { kNoPlan = 0, kUniform = 1, kPlanned = 2 };
 
-// The state filled on the host (h->h_state[slot]) and copied to the device;
-// its derived constants are k_init_state's.
-cvo_status fill_state(cvo_handle h, PairRes& P, int slot, const double* T, double ell, int mode)
+// The state filled on the host (h->h_state[slot]), its device buffer
+// ensured; fill_state also copies it to the device.  Its derived constants
+// are k_init_state's.
+cvo_status state_host(cvo_handle h, PairRes& P, int slot, const double* T, double ell, int mode)
 {
     IterState* st = h->h_state + slot;
     std::memset(st, 0, sizeof(IterState));
@@ -770,7 +791,13 @@ cvo_status fill_state(cvo_handle h, PairRes& P, int slot, const double* T, doubl
     for (int k = 0; k < P.nlevels; ++k) st->level_h[k] = (float)P.lv[k].rdesign;
     if (mode == 1 && p.max_iters == 0) st->done = 1;
     CVO_CUDA(ensure(P.state, sizeof(IterState)));
-    CVO_CUDA(cudaMemcpyAsync(P.state.p, st, sizeof(IterState), cudaMemcpyHostToDevice, h->s));
+    return CVO_OK;
+}
+
+cvo_status fill_state(cvo_handle h, PairRes& P, int slot, const double* T, double ell, int mode)
+{
+    CVO_TRY(state_host(h, P, slot, T, ell, mode));
+    CVO_CUDA(cudaMemcpyAsync(P.state.p, h->h_state + slot, sizeof(IterState), cudaMemcpyHostToDevice, h->s));
     return CVO_OK;
 }
 
@@ -790,6 +817,47 @@ cvo_status init_state(cvo_handle h, PairRes& P, int slot, const double* T, doubl
 // stable sorts (a pair whose keys need fewer digits than another's takes
 // extra passes on zero digits, which keep its order).
 double reachable_ell_lo(const cvo_params& p);
+
+// Host blocks to device destinations in one host-to-device copy (through the
+// pinned staging buffer) and one copy kernel, instead of a copy per block.
+// Sizes are multiples of 4 bytes.  The staging buffer is rewritten only
+// after the previous copy out of it has completed.
+struct HostBlock {
+    const void* src;
+    void* dst;
+    size_t bytes;
+};
+
+cvo_status upload_blocks(cvo_handle h, const std::vector<HostBlock>& blocks)
+{
+    size_t total = 0;
+    for (const HostBlock& b : blocks) total += (b.bytes + 15) & ~(size_t)15;
+    if (total == 0) return CVO_OK;
+    if (h->stage_ev) CVO_CUDA(cudaEventSynchronize(h->stage_ev));
+    else CVO_CUDA(cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming));
+    if (total > h->h_stage_cap) {
+        unsigned char* q = nullptr;
+        if (cudaMallocHost((void**)&q, total) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CVO_ERR_OOM, "cudaMallocHost failed");
+        }
+        if (h->h_stage) cudaFreeHost(h->h_stage);
+        h->h_stage = q;
+        h->h_stage_cap = total;
+    }
+    CVO_CUDA(ensure(h->d_stage, total));
+    std::vector<CopyJob> jobs;
+    size_t off = 0;
+    for (const HostBlock& b : blocks) {
+        std::memcpy(h->h_stage + off, b.src, b.bytes);
+        jobs.push_back(CopyJob{(const unsigned char*)h->d_stage.p + off, b.dst, (int)b.bytes});
+        off += (b.bytes + 15) & ~(size_t)15;
+    }
+    CVO_CUDA(cudaMemcpyAsync(h->d_stage.p, h->h_stage, total, cudaMemcpyHostToDevice, h->s));
+    CVO_CUDA(cudaEventRecord(h->stage_ev, h->s));
+    CVO_CUDA(launch_copy_batch(jobs.data(), (int)jobs.size(), h->s));
+    return CVO_OK;
+}
 
 struct BatchSeg {   // a pair's segment of the batch scratch
     unsigned *keys, *vals, *keys2, *vals2, *flags, *gidx, *temp;
@@ -987,12 +1055,16 @@ cvo_status prepare_batch(cvo_handle h, const std::vector<int>& live, const cvo_c
 
     // phase 3: level descriptors, start states, the planned work items
     std::vector<StateJob> stj(nl);
+    std::vector<HostBlock> up;
     for (int i = 0; i < nl; ++i) {
         PairRes& P = h->pr[i];
-        CVO_TRY(prepare_finish(h, P, hslot(i)));
-        CVO_TRY(fill_state(h, P, i, T_init + 16 * live[i], p.ell, 1));
+        CVO_TRY(level_descs(P, hslot(i)));
+        CVO_TRY(state_host(h, P, i, T_init + 16 * live[i], p.ell, 1));
+        up.push_back(HostBlock{P.ld, P.levels_dev.p, P.nlevels * sizeof(LevelDesc)});
+        up.push_back(HostBlock{h->h_state + i, P.state.p, sizeof(IterState)});
         stj[i] = StateJob{(IterState*)P.state.p};
     }
+    CVO_TRY(upload_blocks(h, up));
     CVO_CUDA(launch_init_state_batch(stj.data(), nl, h->s));
     for (int k = 0; k < nlev; ++k) {
         pairs_with_level(k);
@@ -1030,11 +1102,14 @@ cvo_status prepare_batch(cvo_handle h, const std::vector<int>& live, const cvo_c
         CVO_CUDA(launch_write_items_batch(it.data(), cnt, h->s));
     }
     CVO_TRY(fetch());
+    up.clear();
     for (int i = 0; i < nl; ++i) {
-        CVO_TRY(plan_finish(h, h->pr[i], true, hslot(i)));
-        *work += h->pr[i].max_items;
+        PairRes& P = h->pr[i];
+        plan_descs(P, true, hslot(i));
+        up.push_back(HostBlock{P.ld, P.levels_dev.p, P.nlevels * sizeof(LevelDesc)});
+        *work += P.max_items;
     }
-    return CVO_OK;
+    return upload_blocks(h, up);
 }
 
 
@@ -1103,10 +1178,24 @@ int single_pair_blocks(cvo_handle h, const PairRes& P)
     return std::max(1, std::min((P.max_items + kSweepWarps - 1) / kSweepWarps, h->num_sms * kSweepBlocksPerSm));
 }
 
+// The pairs' states into h->h_state: gathered on the device and copied back
+// at once (one pair: copied directly).
 cvo_status fetch_states(cvo_handle h, int npairs)
 {
-    for (int k = 0; k < npairs; ++k)
-        CVO_CUDA(cudaMemcpyAsync(h->h_state + k, h->pr[k].state.p, sizeof(IterState), cudaMemcpyDeviceToHost, h->s));
+    if (npairs > 1) {
+        CVO_CUDA(ensure(h->d_stage, (size_t)npairs * sizeof(IterState)));
+        std::vector<CopyJob> jobs(npairs);
+        for (int k = 0; k < npairs; ++k)
+            jobs[k] = CopyJob{h->pr[k].state.p, (unsigned char*)h->d_stage.p + (size_t)k * sizeof(IterState),
+                              (int)sizeof(IterState)};
+        CVO_CUDA(launch_copy_batch(jobs.data(), npairs, h->s));
+        CVO_CUDA(cudaMemcpyAsync(h->h_state, h->d_stage.p, (size_t)npairs * sizeof(IterState), cudaMemcpyDeviceToHost,
+                                 h->s));
+    } else {
+        for (int k = 0; k < npairs; ++k)
+            CVO_CUDA(cudaMemcpyAsync(h->h_state + k, h->pr[k].state.p, sizeof(IterState), cudaMemcpyDeviceToHost,
+                                     h->s));
+    }
     CVO_CUDA(cudaStreamSynchronize(h->s));
     return CVO_OK;
 }
@@ -1929,7 +2018,7 @@ cvo_status cvo_destroy(cvo_handle h)
     DevBuf* bufs[] = {&h->stage_xyz[0], &h->stage_xyz[1], &h->stage_feat[0], &h->stage_feat[1], &h->keys, &h->vals,
                       &h->keys2, &h->vals2, &h->sort_tmp, &h->flags, &h->gidx, &h->misc, &h->part_stats, &h->part_cnt,
                       &h->grp_stats, &h->grp_cnt, &h->grp_arrivals, &h->pairs_dev, &h->counters, &h->trace,
-                      &h->batch_work, &h->batch_scratch,
+                      &h->batch_work, &h->batch_scratch, &h->d_stage,
                       &h->bw_out[0], &h->bw_out[1], &h->bw_out[2], &h->bw_out[3], &h->bw_tq, &h->bw_dell, &h->bw_part};
     for (DevBuf* b : bufs) release(*b);
     for (SetupLane& L : h->lanes) {
@@ -1942,6 +2031,8 @@ cvo_status cvo_destroy(cvo_handle h)
     for (cudaEvent_t e : h->evs) cudaEventDestroy(e);
     if (h->h_state) cudaFreeHost(h->h_state);
     if (h->h_misc) cudaFreeHost(h->h_misc);
+    if (h->h_stage) cudaFreeHost(h->h_stage);
+    if (h->stage_ev) cudaEventDestroy(h->stage_ev);
     delete h;
     return CVO_OK;
 }

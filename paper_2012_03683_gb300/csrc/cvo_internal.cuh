@@ -395,6 +395,15 @@ cudaError_t launch_group_cost_batch(const CostJob* jobs, int count, int rs, int 
 cudaError_t launch_gather_batch(const GatherJob* jobs, int count, cudaStream_t s);
 cudaError_t launch_write_items_batch(const ItemsJob* jobs, int count, cudaStream_t s);
 
+// blocks of bytes (multiples of 4) copied between device buffers, one block
+// per job (cvo_setup.cu)
+struct CopyJob {
+    const void* src;
+    void* dst;
+    int bytes;
+};
+cudaError_t launch_copy_batch(const CopyJob* jobs, int count, cudaStream_t s);
+
 // k_init_state of many pairs (cvo_finalize.cu)
 struct StateJob {
     IterState* st;

@@ -3,6 +3,7 @@
 // groups.  The paper notes that the double sum is sparse (Sec. III-B); the
 // grid is how the sweep visits only the pairs near each query.
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 
 #include "cvo_internal.cuh"
@@ -58,11 +59,31 @@ __global__ void k_bbox(const float* __restrict__ xyz, int n, unsigned* out6, int
     bbox_body(xyz, n, out6, bad, blockIdx.x, gridDim.x);
 }
 
+// a word of two bfloat16 values, or one FP32 value: some exponent all ones
+__device__ __forceinline__ bool word_nonfinite(unsigned w, int bf16)
+{
+    return (w & 0x7f800000u) == 0x7f800000u || (bf16 && (w & 0x7f80u) == 0x7f80u);
+}
+
 __device__ __forceinline__ void check_feat_body(const void* __restrict__ feat, long long count, int bf16, int* bad,
                                                 int bx, int nbx)
 {
     int nonfinite = 0;
-    for (long long i = bx * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)nbx * blockDim.x) {
+    const long long t0 = bx * (long long)blockDim.x + threadIdx.x, stride = (long long)nbx * blockDim.x;
+    long long done = 0;   // values checked 16 bytes at a time
+    if ((reinterpret_cast<uintptr_t>(feat) & 15) == 0) {
+        const int per = bf16 ? 8 : 4;
+        const long long nv = count / per;
+        const uint4* v4 = reinterpret_cast<const uint4*>(feat);
+        for (long long i = t0; i < nv; i += stride) {
+            const uint4 u = v4[i];
+            if (word_nonfinite(u.x, bf16) || word_nonfinite(u.y, bf16) || word_nonfinite(u.z, bf16) ||
+                word_nonfinite(u.w, bf16))
+                nonfinite = 1;
+        }
+        done = nv * per;
+    }
+    for (long long i = done + t0; i < count; i += stride) {
         float v;
         if (bf16) v = __uint_as_float(((unsigned)((const unsigned short*)feat)[i]) << 16);
         else v = ((const float*)feat)[i];
@@ -356,24 +377,34 @@ __device__ __forceinline__ void pack_body(const float* __restrict__ xyz, const v
     // w carries the point's index in the caller's order (for per-point outputs)
     r[0] = make_float4(xyz[3 * (size_t)j], xyz[3 * (size_t)j + 1], xyz[3 * (size_t)j + 2], __int_as_float(j));
     if (rs <= 1) return;
+    // the feature part of the record, 16 bytes at a time (zero past D)
+    uint4* dst = reinterpret_cast<uint4*>(r + 1);
+    const unsigned short* f16 = (const unsigned short*)feat + (size_t)j * D;
+    const float* f32 = (const float*)feat + (size_t)j * D;
     if (rec_bf16) {
-        unsigned short* dst = (unsigned short*)(r + 1);
-        const int cap = (rs - 1) * 8;
-        for (int k = 0; k < cap; ++k) {
-            unsigned short b = 0;
-            if (k < D) b = feat_bf16 ? ((const unsigned short*)feat)[(size_t)j * D + k]
-                                     : f32_to_bf16_bits(((const float*)feat)[(size_t)j * D + k]);
-            dst[k] = b;
+        auto half = [&](int k) -> unsigned {
+            if (k >= D) return 0u;
+            return feat_bf16 ? (unsigned)f16[k] : (unsigned)f32_to_bf16_bits(f32[k]);
+        };
+        // an even D (and a 4-byte aligned array) keeps every row's bfloat16
+        // pairs 4-byte aligned
+        const bool words = feat_bf16 && (D & 1) == 0 && (reinterpret_cast<uintptr_t>(feat) & 3) == 0;
+        for (int q = 0; q < rs - 1; ++q) {
+            unsigned v[4];
+            for (int t = 0; t < 4; ++t) {
+                const int k = 8 * q + 2 * t;
+                v[t] = (words && k + 1 < D) ? reinterpret_cast<const unsigned*>(f16)[k >> 1]
+                                            : (half(k) | (half(k + 1) << 16));
+            }
+            dst[q] = make_uint4(v[0], v[1], v[2], v[3]);
         }
     } else {
-        float* dst = (float*)(r + 1);
-        const int cap = (rs - 1) * 4;
-        for (int k = 0; k < cap; ++k) {
-            float v = 0.0f;
-            if (k < D) v = feat_bf16 ? __uint_as_float(((unsigned)((const unsigned short*)feat)[(size_t)j * D + k]) << 16)
-                                     : ((const float*)feat)[(size_t)j * D + k];
-            dst[k] = v;
-        }
+        auto val = [&](int k) -> float {
+            if (k >= D) return 0.0f;
+            return feat_bf16 ? __uint_as_float(((unsigned)f16[k]) << 16) : f32[k];
+        };
+        for (int q = 0; q < rs - 1; ++q)
+            reinterpret_cast<float4*>(dst)[q] = make_float4(val(4 * q), val(4 * q + 1), val(4 * q + 2), val(4 * q + 3));
     }
 }
 
@@ -651,6 +682,14 @@ __global__ void k_group_flags_b(JobList<GroupJob> J)
 {
     const GroupJob& q = J.j[blockIdx.y];
     group_flags_body(q.morton, q.n, q.shift, q.flags, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void k_copy_b(JobList<CopyJob> J)
+{
+    const CopyJob& c = J.j[blockIdx.y];
+    const unsigned* src = static_cast<const unsigned*>(c.src);
+    unsigned* dst = static_cast<unsigned*>(c.dst);
+    for (int i = threadIdx.x; i < c.bytes / 4; i += blockDim.x) dst[i] = src[i];
 }
 
 __global__ void k_group_write_b(JobList<GroupJob> J)
@@ -948,6 +987,15 @@ cudaError_t launch_group_write_batch(const GroupJob* jobs, int count, cudaStream
         for (int i = 0; i < L.count; ++i) nmax = max(nmax, L.j[i].n);
         g_launch_count.fetch_add(1, std::memory_order_relaxed);
         k_group_write_b<<<dim3(blocks_for(nmax, 256), L.count), 256, 0, s>>>(L);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_copy_batch(const CopyJob* jobs, int count, cudaStream_t s)
+{
+    return each_chunk(jobs, count, [&](const JobList<CopyJob>& L) {
+        g_launch_count.fetch_add(1, std::memory_order_relaxed);
+        k_copy_b<<<dim3(1, L.count), 256, 0, s>>>(L);
         return cudaGetLastError();
     });
 }
