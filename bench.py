@@ -263,6 +263,16 @@ def sweep_roofline(name, pairs_evaluated, sweep_ms_total, launches, fpp, peaks, 
     }
 
 
+def parse_tuning(text):
+    """--tuning "cell_factor,super_delta,chunk_len[,query_lanes]" as apply_tuning's arguments."""
+    parts = text.split(",")
+    return (float(parts[0]), int(parts[1]), int(parts[2]), int(parts[3]) if len(parts) > 3 else 1)
+
+
+def tuning_args(t):
+    return (t["cell_factor"], t["super_delta"], t["chunk_len"], t.get("query_lanes", 1))
+
+
 def plain_section(h, args, torch, flush, reps):
     """The 64 pairs through cvo_register_pair one after another; CUDA events
     around each pass over the batch."""
@@ -569,8 +579,8 @@ def main():
     ap.add_argument("--only", default=None, choices=["street", "cube", "backward", "large"],
                     help="run only this section and print its JSON (a fixed launch sequence for profiling)")
     ap.add_argument("--tuning", default=None,
-                    help="cell_factor,super_delta,chunk_len for the batch (or, with --only street, the street "
-                         "pair) instead of autotuning (fixed launch sequence for profiling)")
+                    help="cell_factor,super_delta,chunk_len[,query_lanes] for the batch (or, with --only street, the "
+                         "street pair) instead of autotuning (fixed launch sequence for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -588,8 +598,7 @@ def main():
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
         tun = None
         if args.tuning:
-            cf, sd, ip = args.tuning.split(",")
-            tun = (float(cf), int(sd), int(ip))
+            tun = parse_tuning(args.tuning)
         run = {"street": lambda: street_section(cvo, torch, dev, flush, peaks, peak_src, sms, reps=args.reps,
                                                 tuning=tun),
                "cube": lambda: cube_section(cvo, torch, dev, flush, reps=args.reps),
@@ -608,8 +617,7 @@ def main():
     # the batch's on the batch itself (its grid holds every pair's items, so
     # it prefers longer ones)
     if args.tuning:
-        cf, sd, ip = args.tuning.split(",")
-        h.apply_tuning(float(cf), int(sd), int(ip))
+        h.apply_tuning(*parse_tuning(args.tuning))
         tuning = tuning_plain = dict(h.tuning(), source="--tuning")
     else:
         big = max(range(len(pairs)), key=lambda k: pairs[k].n + pairs[k].m)
@@ -668,10 +676,10 @@ def main():
 
     # ---- the plain form: the same pairs one by one -----------------------------
     if rank == 0:
-        h.apply_tuning(tuning_plain["cell_factor"], tuning_plain["super_delta"], tuning_plain["chunk_len"])
+        h.apply_tuning(*tuning_args(tuning_plain))
         plain = plain_section(h, args_dev, torch, flush, args.reps)
         plain["tuning"] = tuning_plain
-        h.apply_tuning(tuning["cell_factor"], tuning["super_delta"], tuning["chunk_len"])
+        h.apply_tuning(*tuning_args(tuning))
     else:
         plain = None
 

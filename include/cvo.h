@@ -303,25 +303,31 @@ cvo_status cvo_set_tuning(cvo_handle h, double cell_factor, int super_delta);
  * dense registrations measure the streams at the call's pose, longest
  * first; a single registration with a cutoff measures them again in every
  * sweep and lays out the next sweep's items from them, since its streams
- * follow the moving pose).  measured_ms: the time cvo_autotune measured for
- * the tuning it kept, else 0. */
+ * follow the moving pose), and the lanes per query of the sweep (1, 2 or 4,
+ * default 1: query groups of 32 / query_lanes queries, each query's
+ * candidates shared among that many lanes; a block list other than RGB + 19
+ * labels, or the feature-space cutoff, keeps one lane per query and leaves
+ * the group's other lanes idle).  measured_ms: the time cvo_autotune
+ * measured for the tuning it kept, else 0. */
 typedef struct {
     double cell_factor;
     int super_delta;
     int chunk_len;
     double measured_ms;
+    int query_lanes;   /* 0 is read as 1 */
 } cvo_tuning;
 
 /* Autotuner: registers (X, Z) from pose T with the handle's parameters
  * under each tuning of a small grid (cell_factor 0.35 / 0.5 / 0.7 / 1.0 and
  * super_delta 1 / 2 / 3 at the current chunk_len; with cutoff_mult <= 0 there
- * is no grid and these stay as they are), then, for the fastest, chunk_len
- * 64 / 96 / 128 / 192 / 384 / 768 / 1536; each timed on the host clock as a
+ * is no grid and these stay as they are), then, for the fastest, query_lanes
+ * 1 / 2 / 4, then chunk_len 64 / 96 / 128 / 192 / 384 / 768 / 1536; each
+ * timed on the host clock as a
  * caller sees it (setup, iterations, result copies; best of two runs).
  * Keeps the fastest tuning on the handle and returns it in *out
  * (measured_ms: its time).  Results do not depend on the tuning beyond
  * rounding; every tuning's F at the start pose is checked against the first
- * (CVO_ERR_CUDA if they differ by more than 1e-4 relative).  Costs up to 36
+ * (CVO_ERR_CUDA if they differ by more than 1e-4 relative).  Costs up to 38
  * registrations. */
 cvo_status cvo_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], cvo_tuning* out);
 
@@ -329,13 +335,13 @@ cvo_status cvo_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
  * the npairs pairs (arguments as there; the results are not returned): a
  * batch fills the device with many pairs' work items, so its best tuning
  * (typically longer items) differs from one pair's.  The check value is the
- * sum over the pairs of F at their start poses.  Costs up to 36 batched
+ * sum over the pairs of F at their start poses.  Costs up to 38 batched
  * registrations. */
 cvo_status cvo_autotune_batch(cvo_handle h, int npairs, const cvo_cloud* X, const cvo_cloud* Z, const double* T_init,
                               cvo_tuning* out);
 
 /* The handle's current tuning (measured_ms = 0), and setting it (validated as
- * cvo_set_tuning, chunk_len in [16, 4096]). */
+ * cvo_set_tuning, chunk_len in [16, 4096], query_lanes 1, 2 or 4). */
 cvo_status cvo_get_tuning(cvo_handle h, cvo_tuning* out);
 cvo_status cvo_apply_tuning(cvo_handle h, const cvo_tuning* t);
 

@@ -84,7 +84,7 @@ class Info(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("cell_factor", ctypes.c_double), ("super_delta", ctypes.c_int), ("chunk_len", ctypes.c_int),
-                ("measured_ms", ctypes.c_double)]
+                ("measured_ms", ctypes.c_double), ("query_lanes", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -589,8 +589,8 @@ def cvo_get_tuning(h) -> dict:
     return out.as_dict()
 
 
-def cvo_apply_tuning(h, cell_factor, super_delta, chunk_len):
-    t = Tuning(float(cell_factor), int(super_delta), int(chunk_len), 0.0)
+def cvo_apply_tuning(h, cell_factor, super_delta, chunk_len, query_lanes=1):
+    t = Tuning(float(cell_factor), int(super_delta), int(chunk_len), 0.0, int(query_lanes))
     return _check(load_library().cvo_apply_tuning(h, ctypes.byref(t)))
 
 
@@ -675,8 +675,8 @@ class CVO:
     def set_loop(self, mode):
         return cvo_set_loop(self.h, mode)
 
-    def apply_tuning(self, cell_factor, super_delta, chunk_len):
-        return cvo_apply_tuning(self.h, cell_factor, super_delta, chunk_len)
+    def apply_tuning(self, cell_factor, super_delta, chunk_len, query_lanes=1):
+        return cvo_apply_tuning(self.h, cell_factor, super_delta, chunk_len, query_lanes)
 
 
 # ---- differentiable form ---------------------------------------------------------

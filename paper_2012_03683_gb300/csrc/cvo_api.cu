@@ -192,6 +192,9 @@ struct cvo_handle_s {
     // of about chunk_len candidates (work items), so up to stream / chunk_len
     // lanes of different warps serve one query
     int chunk_len = kChunkLen;
+    // lanes per query in the sweep (1, 2 or 4): query groups of 32 / query_lanes
+    // queries, each query's candidates shared among its lanes
+    int query_lanes = 1;
     // an X-row shard registration in progress (cvo_shard_begin .. cvo_shard_end)
     int shard_active = 0;
     // failure injection for the next persistent registration (cvo_inject_barrier_stall)
@@ -600,10 +603,12 @@ cvo_status prepare_build(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo
         const int sh = group_shift(h, L, cell0);
         L.shift = sh;
         CVO_CUDA(ensure(P.groups[k], (size_t)std::max(n, 1) * sizeof(int2)));
-        CVO_CUDA(launch_group_flags((const unsigned*)P.morton.p, n, sh, (unsigned*)h->flags.p, h->s));
+        CVO_CUDA(launch_group_flags((const unsigned*)P.morton.p, n, sh, 32 / h->query_lanes, (unsigned*)h->flags.p,
+                                    h->s));
         CVO_CUDA(exclusive_scan_u32((const unsigned*)h->flags.p, (unsigned*)h->gidx.p, n, dev + 16 + k, h->s));
         CVO_CUDA(launch_group_write((const unsigned*)P.morton.p, (const unsigned*)h->flags.p,
-                                    (const unsigned*)h->gidx.p, n, sh, (int2*)P.groups[k].p, h->s));
+                                    (const unsigned*)h->gidx.p, n, sh, 32 / h->query_lanes, (int2*)P.groups[k].p,
+                                    h->s));
     }
     held.drop();
     if (fan_out) CVO_TRY(join_lanes(h));
@@ -1044,7 +1049,7 @@ cvo_status prepare_batch(cvo_handle h, const std::vector<int>& live, const cvo_c
             const int i = idx[j];
             PairRes& P = h->pr[i];
             gj[j] = GroupJob{(const unsigned*)P.morton.p, seg[i].flags, seg[i].gidx, (int2*)P.groups[k].p, P.n,
-                             P.lv[k].shift};
+                             P.lv[k].shift, 32 / h->query_lanes};
             sc[j] = ScanJob{seg[i].flags, seg[i].gidx, slot(i) + 16 + k, P.n};
         }
         CVO_CUDA(launch_group_flags_batch(gj.data(), cnt, h->s));
@@ -1145,6 +1150,7 @@ cvo_status setup_sweep(cvo_handle h, const std::vector<PairDesc>& table, int nbl
     a->nch_next = nullptr;
     a->swept_level = (int*)h->counters.p + 10;
     a->chunk_len = h->chunk_len;
+    a->lanes = h->query_lanes;
     return CVO_OK;
 }
 
@@ -1166,7 +1172,7 @@ PairDesc pair_desc(const PairRes& P, int b0, int b1)
 cvo_status resident_sweep_blocks(cvo_handle h, int* out)
 {
     SweepLaunch sl;
-    CVO_CUDA(sweep_launch_info(h->fc, h->rs, &sl));
+    CVO_CUDA(sweep_launch_info(h->fc, h->rs, h->query_lanes, &sl));
     int per_sm = 0;
     CVO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sl.func, kSweepWarps * 32, sl.smem));
     *out = std::max(per_sm, 1) * h->num_sms;
@@ -1258,7 +1264,7 @@ cvo_status run_graph_loop(cvo_handle h, const SweepArgs& a, bool batch, IterStat
                           long long trace_stride, LevelDesc* levels)
 {
     SweepLaunch sl;
-    CVO_CUDA(sweep_launch_info(a.fc, a.rs, &sl));
+    CVO_CUDA(sweep_launch_info(a.fc, a.rs, a.lanes, &sl));
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
     cvo_status status = CVO_OK;
@@ -1829,17 +1835,19 @@ cvo_status tune_grid(cvo_handle h, Run&& run, cvo_tuning* out)
 {
     static const double kCell[] = {0.35, 0.5, 0.7, 1.0};
     static const int kSuper[] = {1, 2, 3};
+    static const int kLanes[] = {1, 2, 4};
     static const int kItemLens[] = {64, 96, 128, 192, 384, 768, 1536};
     const double cf0 = h->cell_factor;
-    const int sd0 = h->super_delta, ip0 = h->chunk_len;
-    cvo_tuning best{cf0, sd0, ip0, 1e30};
+    const int sd0 = h->super_delta, ip0 = h->chunk_len, ql0 = h->query_lanes;
+    cvo_tuning best{cf0, sd0, ip0, 1e30, ql0};
     double F_ref = 0.0;
     bool have_ref = false;
     cvo_status st = CVO_OK;
-    auto try_one = [&](double cf, int sd, int ip) {
+    auto try_one = [&](double cf, int sd, int ip, int ql) {
         h->cell_factor = cf;
         h->super_delta = sd;
         h->chunk_len = ip;
+        h->query_lanes = ql;
         double ms = 1e30, F = 0.0;
         for (int rep = 0; rep < 2; ++rep) {
             const auto t0 = std::chrono::steady_clock::now();
@@ -1856,38 +1864,40 @@ cvo_status tune_grid(cvo_handle h, Run&& run, cvo_tuning* out)
             st = fail(CVO_ERR_CUDA, "autotune: F differs between tunings (%g vs %g)", F, F_ref);
             return;
         }
-        if (ms < best.measured_ms) best = cvo_tuning{cf, sd, ip, ms};
+        if (ms < best.measured_ms) best = cvo_tuning{cf, sd, ip, ms, ql};
     };
     // the dense sum has no grid and no super-cells: only the work split is tuned
     if (!(h->p.cutoff_mult > 0.0)) {
-        try_one(cf0, sd0, ip0);
+        try_one(cf0, sd0, ip0, ql0);
     } else {
         for (double cf : kCell) {
             for (int sd : kSuper) {
-                try_one(cf, sd, ip0);
+                try_one(cf, sd, ip0, ql0);
                 if (st < 0) break;
             }
             if (st < 0) break;
         }
     }
-    if (st >= 0) {
-        const double cfb = best.cell_factor;
-        const int sdb = best.super_delta;
-        for (int ip : kItemLens) {
-            if (ip == ip0) continue;
-            try_one(cfb, sdb, ip);
-            if (st < 0) break;
-        }
+    // then the lanes per query, then the work-item length, for the best so far
+    for (int ql : kLanes) {
+        if (st < 0 || ql == ql0) continue;
+        try_one(best.cell_factor, best.super_delta, ip0, ql);
+    }
+    for (int ip : kItemLens) {
+        if (st < 0 || ip == ip0) continue;
+        try_one(best.cell_factor, best.super_delta, ip, best.query_lanes);
     }
     if (st < 0) {
         h->cell_factor = cf0;
         h->super_delta = sd0;
         h->chunk_len = ip0;
+        h->query_lanes = ql0;
         return st;
     }
     h->cell_factor = best.cell_factor;
     h->super_delta = best.super_delta;
     h->chunk_len = best.chunk_len;
+    h->query_lanes = best.query_lanes;
     *out = best;
     return CVO_OK;
 }
@@ -1898,7 +1908,7 @@ cvo_status run_autotune(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
 {
     std::memset(out, 0, sizeof(*out));
     if (X->n == 0 || Z->n == 0 || h->p.max_iters == 0) {
-        *out = cvo_tuning{h->cell_factor, h->super_delta, h->chunk_len, 0.0};
+        *out = cvo_tuning{h->cell_factor, h->super_delta, h->chunk_len, 0.0, h->query_lanes};
         return CVO_OK;
     }
     double T_out[16];
@@ -1926,7 +1936,7 @@ cvo_status run_autotune_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
     int nl = 0;   // pairs that run (both clouds non-empty)
     for (int k = 0; k < npairs; ++k) nl += (X[k].n > 0 && Z[k].n > 0) ? 1 : 0;
     if (nl == 0 || h->p.max_iters == 0) {
-        *out = cvo_tuning{h->cell_factor, h->super_delta, h->chunk_len, 0.0};
+        *out = cvo_tuning{h->cell_factor, h->super_delta, h->chunk_len, 0.0, h->query_lanes};
         return CVO_OK;
     }
     std::vector<double> T_out((size_t)16 * npairs), rows((size_t)2 * nl);
@@ -2407,7 +2417,7 @@ cvo_status cvo_autotune_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
 cvo_status cvo_get_tuning(cvo_handle h, cvo_tuning* out)
 {
     if (!h || !out) return fail(CVO_ERR_INVALID_ARG, "NULL argument");
-    *out = cvo_tuning{h->cell_factor, h->super_delta, h->chunk_len, 0.0};
+    *out = cvo_tuning{h->cell_factor, h->super_delta, h->chunk_len, 0.0, h->query_lanes};
     return CVO_OK;
 }
 
@@ -2415,8 +2425,11 @@ cvo_status cvo_apply_tuning(cvo_handle h, const cvo_tuning* t)
 {
     if (!h || !t) return fail(CVO_ERR_INVALID_ARG, "NULL argument");
     if (t->chunk_len < 16 || t->chunk_len > 4096) return fail(CVO_ERR_INVALID_ARG, "chunk_len must be in [16, 4096]");
+    const int ql = t->query_lanes == 0 ? 1 : t->query_lanes;   // 0: a tuning from before the field (one lane)
+    if (ql != 1 && ql != 2 && ql != 4) return fail(CVO_ERR_INVALID_ARG, "query_lanes must be 1, 2 or 4");
     CVO_TRY(cvo_set_tuning(h, t->cell_factor, t->super_delta));
     h->chunk_len = t->chunk_len;
+    h->query_lanes = ql;
     return CVO_OK;
 }
 

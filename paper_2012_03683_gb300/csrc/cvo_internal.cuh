@@ -157,6 +157,7 @@ struct SweepArgs {
                                // ceil(stream length / chunk_len), written by the group's item with chunk 0
                                // (NULL: not recorded)
     int chunk_len;
+    int lanes;                 // lanes per query (query groups of 32 / lanes queries)
     int* swept_level;          // with nch_next: the level the sweep covered (written by block 0)
 };
 
@@ -190,7 +191,8 @@ struct SweepLaunch {
     const void* func;   // k_sweep specialisation
     size_t smem;        // dynamic shared memory
 };
-cudaError_t sweep_launch_info(const FeatConst& fc, int rs, SweepLaunch* out);
+// lanes: lanes per query of the sweep (1, 2, 4; the query groups hold 32 / lanes queries)
+cudaError_t sweep_launch_info(const FeatConst& fc, int rs, int lanes, SweepLaunch* out);
 // k_finalize(IterState*, const float2* grp_stats, const unsigned long long* grp_cnt, int ngroups,
 //            double* trace, cudaGraphConditionalHandle cond, int use_cond), kStepThreads threads
 const void* finalize_kernel();
@@ -351,7 +353,7 @@ struct GroupJob {
     unsigned* flags;
     const unsigned* gidx;
     int2* groups;
-    int n, shift;
+    int n, shift, gsize;
 };
 
 size_t sort_batch_temp_words(int n);
@@ -428,9 +430,12 @@ cudaError_t radix_sort_pairs(unsigned* keys, unsigned* vals, unsigned* keys_alt,
 cudaError_t launch_cell_start(const unsigned* sorted_keys, int n, int ncells, int* cell_start, cudaStream_t s);
 cudaError_t launch_pack(const float* xyz, const void* feat, int feat_bf16, int D, const unsigned* order, int n,
                         float4* rec, int rs, int rec_bf16, cudaStream_t s);
-cudaError_t launch_group_flags(const unsigned* sorted_morton, int n, int shift, unsigned* flags, cudaStream_t s);
+// query groups: up to gsize consecutive Morton-sorted queries of one super-cell
+// (2^shift Morton units) each
+cudaError_t launch_group_flags(const unsigned* sorted_morton, int n, int shift, int gsize, unsigned* flags,
+                               cudaStream_t s);
 cudaError_t exclusive_scan_u32(const unsigned* in, unsigned* out, int n, unsigned* total, cudaStream_t s);
 cudaError_t launch_group_write(const unsigned* sorted_morton, const unsigned* flags, const unsigned* gidx, int n,
-                               int shift, int2* groups, cudaStream_t s);
+                               int shift, int gsize, int2* groups, cudaStream_t s);
 
 }  // namespace cvo

@@ -425,35 +425,36 @@ __device__ __forceinline__ int lower_bound_u32(const unsigned* a, int n, unsigne
     return lo;
 }
 
-__device__ __forceinline__ void group_flags_body(const unsigned* __restrict__ morton, int n, int shift, unsigned* flags,
-                                                 int i)
+// groups of up to gsize consecutive queries of one Morton super-cell
+__device__ __forceinline__ void group_flags_body(const unsigned* __restrict__ morton, int n, int shift, int gsize,
+                                                 unsigned* flags, int i)
 {
     if (i >= n) return;
     const unsigned long long seg = (unsigned long long)(morton[i] >> shift);
     const int start = lower_bound_u32(morton, n, seg << shift);
-    flags[i] = ((i - start) % 32 == 0) ? 1u : 0u;
+    flags[i] = ((i - start) % gsize == 0) ? 1u : 0u;
 }
 
-__global__ void k_group_flags(const unsigned* __restrict__ morton, int n, int shift, unsigned* flags)
+__global__ void k_group_flags(const unsigned* __restrict__ morton, int n, int shift, int gsize, unsigned* flags)
 {
-    group_flags_body(morton, n, shift, flags, blockIdx.x * blockDim.x + threadIdx.x);
+    group_flags_body(morton, n, shift, gsize, flags, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 __device__ __forceinline__ void group_write_body(const unsigned* __restrict__ morton,
                                                  const unsigned* __restrict__ flags,
-                                                 const unsigned* __restrict__ gidx, int n, int shift, int2* groups,
-                                                 int i)
+                                                 const unsigned* __restrict__ gidx, int n, int shift, int gsize,
+                                                 int2* groups, int i)
 {
     if (i >= n || !flags[i]) return;
     const unsigned long long seg = (unsigned long long)(morton[i] >> shift);
     const int end = lower_bound_u32(morton, n, (seg + 1ull) << shift);
-    groups[gidx[i]] = make_int2(i, min(32, end - i));
+    groups[gidx[i]] = make_int2(i, min(gsize, end - i));
 }
 
 __global__ void k_group_write(const unsigned* __restrict__ morton, const unsigned* __restrict__ flags,
-                              const unsigned* __restrict__ gidx, int n, int shift, int2* groups)
+                              const unsigned* __restrict__ gidx, int n, int shift, int gsize, int2* groups)
 {
-    group_write_body(morton, flags, gidx, n, shift, groups, blockIdx.x * blockDim.x + threadIdx.x);
+    group_write_body(morton, flags, gidx, n, shift, gsize, groups, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Deterministic sum of n floats: per-thread double-float partials in a fixed
@@ -681,7 +682,7 @@ __global__ void k_scan_b(JobList<ScanJob> J)
 __global__ void k_group_flags_b(JobList<GroupJob> J)
 {
     const GroupJob& q = J.j[blockIdx.y];
-    group_flags_body(q.morton, q.n, q.shift, q.flags, blockIdx.x * blockDim.x + threadIdx.x);
+    group_flags_body(q.morton, q.n, q.shift, q.gsize, q.flags, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 __global__ void k_copy_b(JobList<CopyJob> J)
@@ -695,7 +696,8 @@ __global__ void k_copy_b(JobList<CopyJob> J)
 __global__ void k_group_write_b(JobList<GroupJob> J)
 {
     const GroupJob& q = J.j[blockIdx.y];
-    group_write_body(q.morton, q.flags, q.gidx, q.n, q.shift, q.groups, blockIdx.x * blockDim.x + threadIdx.x);
+    group_write_body(q.morton, q.flags, q.gidx, q.n, q.shift, q.gsize, q.groups,
+                     blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
@@ -825,11 +827,12 @@ cudaError_t launch_pack(const float* xyz, const void* feat, int feat_bf16, int D
     return cudaGetLastError();
 }
 
-cudaError_t launch_group_flags(const unsigned* sorted_morton, int n, int shift, unsigned* flags, cudaStream_t s)
+cudaError_t launch_group_flags(const unsigned* sorted_morton, int n, int shift, int gsize, unsigned* flags,
+                               cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
-    k_group_flags<<<blocks_for(n, 256), 256, 0, s>>>(sorted_morton, n, shift, flags);
+    k_group_flags<<<blocks_for(n, 256), 256, 0, s>>>(sorted_morton, n, shift, gsize, flags);
     return cudaGetLastError();
 }
 
@@ -841,11 +844,11 @@ cudaError_t exclusive_scan_u32(const unsigned* in, unsigned* out, int n, unsigne
 }
 
 cudaError_t launch_group_write(const unsigned* sorted_morton, const unsigned* flags, const unsigned* gidx, int n,
-                               int shift, int2* groups, cudaStream_t s)
+                               int shift, int gsize, int2* groups, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
-    k_group_write<<<blocks_for(n, 256), 256, 0, s>>>(sorted_morton, flags, gidx, n, shift, groups);
+    k_group_write<<<blocks_for(n, 256), 256, 0, s>>>(sorted_morton, flags, gidx, n, shift, gsize, groups);
     return cudaGetLastError();
 }
 

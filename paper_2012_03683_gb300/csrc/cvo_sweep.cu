@@ -37,7 +37,7 @@
 namespace cvo {
 namespace {
 
-template <class Feat>
+template <class Feat, int S>
 __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
 {
     extern __shared__ float4 stage_mem[];   // [kSweepWarps][2][32][rs]
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
         Moments mo;
         float p[3];
         bool act;
-        if (!sweep_item<Feat>(P, L, item, cst, rs, dense, sg, rc, rc2, fc, stage, scratch, lane, mo, p, act, npairs,
+        if (!sweep_item<Feat, S>(P, L, item, cst, rs, dense, sg, rc, rc2, fc, stage, scratch, lane, mo, p, act, npairs,
                               ncand, a.nch_next, a.chunk_len))
             continue;
         stat_acc_add(acc, mo, p, act, lane);
@@ -562,16 +562,16 @@ cudaError_t each_chunk(const J* jobs, int count, F&& f)
     return cudaSuccess;
 }
 
-template <class Feat>
+template <class Feat, int S = 1>
 cudaError_t info_t(int rs, SweepLaunch* out)
 {
     static bool attr_set = false;   // one-time opt-in above the 48 KB default
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep<Feat>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(k_sweep<Feat, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    out->func = (const void*)k_sweep<Feat>;
+    out->func = (const void*)k_sweep<Feat, S>;
     out->smem = (size_t)kSweepWarps * 2 * 32 * rs * sizeof(float4) + (size_t)kSweepWarps * Feat::kScratch;
     return cudaSuccess;
 }
@@ -588,11 +588,26 @@ cudaError_t sweep_info_se3(const FeatConst& f, int rs, SweepLaunch* out)
     return f.bf16 ? info_t<FeatMMA<3, Cut>>(rs, out) : info_t<FeatFixed<3, 19, false, Cut>>(rs, out);
 }
 
-cudaError_t sweep_launch_info(const FeatConst& f, int rs, SweepLaunch* out)
+// RGB + 19 labels with S lanes per query (the feature-space cutoff off)
+template <int S>
+cudaError_t sweep_info_lanes(const FeatConst& f, int rs, SweepLaunch* out)
+{
+    return f.bf16 ? info_t<FeatMMA<3, false, S>, S>(rs, out) : info_t<FeatFixed<3, 19, false, false>, S>(rs, out);
+}
+
+cudaError_t sweep_launch_info(const FeatConst& f, int rs, int lanes, SweepLaunch* out)
 {
     if (f.n_blocks == 0) return info_t<FeatNone>(rs, out);
     const bool se3 = f.n_blocks >= 1 && f.kind[0] == 0 && f.dim[0] == 3;
     const bool labels = f.n_blocks == 2 && f.kind[1] == 1 && f.dim[1] == 19;
+    // query groups of 32 / lanes queries: RGB + labels take each query's
+    // candidates on that many lanes; any other block list (or the
+    // feature-space cutoff) takes them on one lane, the group's other lanes
+    // idle, which is correct but slower
+    if (se3 && labels && f.fcut2[0] >= 1.0e38f) {
+        if (lanes == 2) return sweep_info_lanes<2>(f, rs, out);
+        if (lanes == 4) return sweep_info_lanes<4>(f, rs, out);
+    }
     if (se3 && (f.n_blocks == 1 || labels)) {
         // the feature-space cutoff's test only where it is on (the colour block's limit is finite)
         return f.fcut2[0] < 1.0e38f ? sweep_info_se3<true>(f, rs, out) : sweep_info_se3<false>(f, rs, out);
@@ -693,7 +708,7 @@ cudaError_t launch_write_items(const LevelDesc* levels, int level, const unsigne
 cudaError_t launch_sweep(const SweepArgs& a, int nblocks, cudaStream_t s)
 {
     SweepLaunch li;
-    cudaError_t e = sweep_launch_info(a.fc, a.rs, &li);
+    cudaError_t e = sweep_launch_info(a.fc, a.rs, a.lanes, &li);
     if (e != cudaSuccess) return e;
     void* args[1] = {(void*)&a};
     g_launch_count.fetch_add(1, std::memory_order_relaxed);

@@ -189,21 +189,36 @@ struct FeatGeneric {
 // with a row stride of 36 floats: the accumulator fragments store without
 // bank conflicts (lane (g, t) of a fragment writes bank g + 8 t) and each
 // candidate's row is read by the 32 lanes from 32 consecutive words.
-template <int DSE, bool Cut>
+// With S lanes per query (S = 2, 4: groups of 32 / S queries, one row tile
+// of 16) the results are stored in rows of S candidates x 32 / S queries,
+// row stride 40 floats: the fragment stores stay conflict free (lane (g, t)
+// writes bank 8 t + g plus a constant) and the S lanes of a query, which
+// take S consecutive candidates at once, read one row's disjoint parts.
+template <int DSE, bool Cut, int S = 1>
 struct FeatMMA {
     static constexpr int kL = 19;
     static constexpr int D = DSE + kL;
+    static constexpr int kQ = 32 / S;                         // queries per group
+    static constexpr int kMt = S == 1 ? 2 : 1;                // row tiles of 16 queries
     static constexpr int kRowBytes = 80;                      // 32 labels + pad: conflict-free fragment loads
     static constexpr int kTileBytes = 32 * kRowBytes;
     static constexpr int kCsStride = 36;
+    static constexpr int kCsRow = 40;
     static constexpr int kScratch = kTileBytes + 32 * kCsStride * 4;
+    static_assert(S == 1 || (32 / S) * kCsRow <= 32 * kCsStride, "the grouped result rows fit the tile");
     struct Q {
         float se[DSE > 0 ? DSE : 1];
-        unsigned a[2][2][4];        // A fragments [m tile][k step][register]
+        unsigned a[kMt][2][4];      // A fragments [m tile][k step][register]
         unsigned char* tile;
         float* cs;
-        int lane;
+        int col;                    // this lane's query (its column of the results)
     };
+    // where the label product of candidate c and query r is kept
+    __device__ static int cs_index(int c, int r)
+    {
+        if constexpr (S == 1) return c * kCsStride + r;
+        else return (c / S) * kCsRow + (c % S) * kQ + r;
+    }
     // label pairs (l, l + 1), l = 0, 2, ..., 30 (zero past the 19th) of a
     // record's bfloat16 feature row
     __device__ static void label_pairs(const float4* feat, unsigned (&out)[16])
@@ -242,7 +257,7 @@ struct FeatMMA {
     {
         q.tile = scratch;
         q.cs = reinterpret_cast<float*>(scratch + kTileBytes);
-        q.lane = lane;
+        q.col = lane & (kQ - 1);
         if constexpr (DSE > 0) {
             const uint4 u = reinterpret_cast<const uint4*>(rec + 1)[0];
             const unsigned w[2] = {u.x, u.y};
@@ -257,7 +272,7 @@ struct FeatMMA {
         __syncwarp();
         const int g = lane >> 2, t = lane & 3;
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
+        for (int mt = 0; mt < kMt; ++mt)
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
                 q.a[mt][ks][0] = word(q.tile, g + 16 * mt, t + 8 * ks);
@@ -289,7 +304,7 @@ struct FeatMMA {
                 b[ks][1] = word(q.tile, g + 8 * nt, t + 4 + 8 * ks);
             }
 #pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
+            for (int mt = 0; mt < kMt; ++mt) {
                 float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, c3 = 0.0f;
 #pragma unroll
                 for (int ks = 0; ks < 2; ++ks)
@@ -300,10 +315,12 @@ struct FeatMMA {
                         : "r"(q.a[mt][ks][0]), "r"(q.a[mt][ks][1]), "r"(q.a[mt][ks][2]), "r"(q.a[mt][ks][3]),
                           "r"(b[ks][0]), "r"(b[ks][1]));
                 const int r0 = g + 16 * mt, col = 2 * t + 8 * nt;   // query row, candidate column
-                q.cs[col * kCsStride + r0] = c0;
-                q.cs[(col + 1) * kCsStride + r0] = c1;
-                q.cs[col * kCsStride + r0 + 8] = c2;
-                q.cs[(col + 1) * kCsStride + r0 + 8] = c3;
+                q.cs[cs_index(col, r0)] = c0;
+                q.cs[cs_index(col + 1, r0)] = c1;
+                if (r0 + 8 < kQ) {   // rows past the group's queries are not kept
+                    q.cs[cs_index(col, r0 + 8)] = c2;
+                    q.cs[cs_index(col + 1, r0 + 8)] = c3;
+                }
             }
         }
         __syncwarp();
@@ -325,7 +342,7 @@ struct FeatMMA {
                 if (du2 > fc.fcut2[0]) in = false;
             }
         }
-        return q.cs[c * kCsStride + q.lane];
+        return q.cs[cs_index(c, q.col)];
     }
 };
 
@@ -568,7 +585,9 @@ __device__ __forceinline__ void add_moments(Moments& mo, float w, const Offset& 
 // Candidates go two at a time under one warp vote: the two evaluations are
 // independent chains (staged loads, feature products, ex2), which hides
 // latency at this kernel's occupancy; a pair with no lane in range is skipped.
-template <class Feat>
+// With S lanes per query (S > 1), lane s of a query takes candidates s, s + S,
+// s + 2 S, ... of the batch, two at a time.
+template <class Feat, int S = 1>
 __device__ __forceinline__ void eval_batch(const float4* sb, int cnt, int rs, typename Feat::Q& qf,
                                            const float xh[3], const float xl[3], bool act, bool dense, float sg,
                                            float rc2, const FeatConst& fc, Moments& mo, unsigned& npairs, int lane)
@@ -577,6 +596,31 @@ __device__ __forceinline__ void eval_batch(const float4* sb, int cnt, int rs, ty
     // one comparison per candidate: an inactive lane takes no pair, the dense
     // sum every pair
     const float lim = act ? (dense ? 3.0e38f : rc2) : -1.0f;
+    if constexpr (S > 1) {
+        const int s = lane / (32 / S);
+        for (int base = 0; base < cnt; base += 2 * S) {
+            const int c0 = base + s, c1 = base + S + s;
+            const bool v0 = c0 < cnt, v1 = c1 < cnt;
+            const int r0 = v0 ? c0 : 0, r1 = v1 ? c1 : 0;   // past the batch: read record 0, take no pair
+            const float4* zr0 = sb + r0 * rs;
+            const float4* zr1 = sb + r1 * rs;
+            const Offset o0 = offset_to(zr0[0], xh, xl);
+            const Offset o1 = offset_to(zr1[0], xh, xl);
+            bool in0 = v0 && o0.d2 <= lim;
+            bool in1 = v1 && o1.d2 <= lim;
+            if (__any_sync(kFull, in0 || in1)) {
+                float a0 = o0.d2 * sg, a1 = o1.d2 * sg;
+                const float m0 = Feat::pair(qf, zr0, r0, a0, in0, fc);
+                const float m1 = Feat::pair(qf, zr1, r1, a1, in1, fc);
+                const float w0 = in0 ? ex2(a0) * m0 : 0.0f;
+                const float w1 = in1 ? ex2(a1) * m1 : 0.0f;
+                npairs += (in0 ? 1u : 0u) + (in1 ? 1u : 0u);
+                add_moments(mo, w0, o0);
+                add_moments(mo, w1, o1);
+            }
+        }
+        return;
+    }
     int c = 0;
     for (; c + 1 < cnt; c += 2) {
         const float4* zr0 = sb + c * rs;
@@ -614,7 +658,7 @@ __device__ __forceinline__ void eval_batch(const float4* sb, int cnt, int rs, ty
 // count): the moments of this lane's query over the chunk, and its lever
 // arm p = x' - c.  cst: the state's derived constants Ahi, Alo, bhi, blo,
 // chi, clo (30 floats).  Returns false when the group's stream is empty.
-template <class Feat>
+template <class Feat, int S = 1>
 __device__ __forceinline__ bool sweep_chunk(const PairDesc& P, const LevelDesc& L, int2 grp, int k, int nch,
                                             const float* cst, int rs, bool dense, float sg, float rc, float rc2,
                                             const FeatConst& fc, float4* stage, unsigned char* scratch, int lane,
@@ -628,8 +672,10 @@ __device__ __forceinline__ bool sweep_chunk(const PairDesc& P, const LevelDesc& 
     const float* blo = cst + 21;
     const float* chi = cst + 24;
     const float* clo = cst + 27;
-    act = lane < grp.y;
-    const int qi = grp.x + (act ? lane : 0);
+    // this lane's query: lane % (32 / S) of the group (its S lanes share its candidates)
+    const int ql = lane & (32 / S - 1);
+    act = ql < grp.y;
+    const int qi = grp.x + (act ? ql : 0);
     const float4* qrec = P.xrec + (size_t)qi * rs;
     const float4 xq4 = qrec[0];
     const float xq[3] = {xq4.x, xq4.y, xq4.z};
@@ -652,8 +698,8 @@ __device__ __forceinline__ bool sweep_chunk(const PairDesc& P, const LevelDesc& 
     Feat::load_query(qf, qrec, fc, scratch, lane);
     mo = Moments{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     stream_walk(L, P.m, dense, sm, clo_, chi_, rs, stage, lane, [&](const float4* sb, int cnt) {
-        eval_batch<Feat>(sb, cnt, rs, qf, xh, xl, act, dense, sg, rc2, fc, mo, npairs, lane);
-        ncand += act ? (unsigned)cnt : 0u;
+        eval_batch<Feat, S>(sb, cnt, rs, qf, xh, xl, act, dense, sg, rc2, fc, mo, npairs, lane);
+        ncand += (act && lane < 32 / S) ? (unsigned)cnt : 0u;   // (query, candidate) tests
     });
     p[0] = (xh[0] - chi[0]) + (xl[0] - clo[0]);
     p[1] = (xh[1] - chi[1]) + (xl[1] - clo[1]);
@@ -662,7 +708,7 @@ __device__ __forceinline__ bool sweep_chunk(const PairDesc& P, const LevelDesc& 
 }
 
 // One work item of a sweep from the level's item table.
-template <class Feat>
+template <class Feat, int S = 1>
 __device__ __forceinline__ bool sweep_item(const PairDesc& P, const LevelDesc& L, int item, const float* cst, int rs,
                                            bool dense, float sg, float rc, float rc2, const FeatConst& fc,
                                            float4* stage, unsigned char* scratch, int lane, Moments& mo, float p[3],
@@ -670,8 +716,9 @@ __device__ __forceinline__ bool sweep_item(const PairDesc& P, const LevelDesc& L
                                            int chunk_len = 0)
 {
     const int4 w = L.items[item];
-    return sweep_chunk<Feat>(P, L, make_int2(w.x, w.y), w.z & 0xffff, w.z >> 16, cst, rs, dense, sg, rc, rc2, fc, stage,
-                             scratch, lane, mo, p, act, npairs, ncand, L.chunk_min, nch_next, chunk_len, w.w);
+    return sweep_chunk<Feat, S>(P, L, make_int2(w.x, w.y), w.z & 0xffff, w.z >> 16, cst, rs, dense, sg, rc, rc2, fc,
+                                stage, scratch, lane, mo, p, act, npairs, ncand, L.chunk_min, nch_next, chunk_len,
+                                w.w);
 }
 
 // The 43 linear statistics of one query's moments about the lever centre

@@ -16,6 +16,7 @@ pytestmark = pytest.mark.gpu
 CELLS = (0.35, 0.5, 0.7, 1.0)
 SUPERS = (1, 2, 3)
 ITEM_LENS = (64, 96, 128, 192, 384, 768, 1536)
+LANES = (1, 2, 4)
 
 
 def dev(a):
@@ -41,14 +42,14 @@ def test_autotune_street_slice():
     assert h.tuning()["cell_factor"] == 0.5 and h.tuning()["super_delta"] == 2
     t = h.autotune(dev(X), dev(Z), p.T_true, dev(FX), dev(FZ))
     assert t["cell_factor"] in CELLS and t["super_delta"] in SUPERS
-    assert t["chunk_len"] in ITEM_LENS and t["measured_ms"] > 0.0
+    assert t["chunk_len"] in ITEM_LENS and t["query_lanes"] in LANES and t["measured_ms"] > 0.0
     # the timed sweep did the work: no faster than the pairs it evaluates allow
     # (6,000 x 6,000 points at l = 0.2 take tens of microseconds)
     ev = h.evaluate(dev(X), dev(Z), p.T_true, dev(FX), dev(FZ))
     assert ev["pairs"] > 1e5 and t["measured_ms"] > 0.01
     cur = h.tuning()
-    assert (cur["cell_factor"], cur["super_delta"], cur["chunk_len"]) == \
-        (t["cell_factor"], t["super_delta"], t["chunk_len"])
+    assert (cur["cell_factor"], cur["super_delta"], cur["chunk_len"], cur["query_lanes"]) == \
+        (t["cell_factor"], t["super_delta"], t["chunk_len"], t["query_lanes"])
     check_parity(h, X, Z, FX, FZ, p.T_true, kw)
     # every tuning of the grid keeps parity (spot-check the extremes)
     for cf, sd, ip in [(0.35, 1, 48), (1.0, 3, 128)]:
@@ -68,6 +69,8 @@ def test_autotune_dense_and_invalid():
         h.apply_tuning(0.1, 2, 8)
     with pytest.raises(cvo.CvoError):
         h.apply_tuning(0.5, 2, 8)
+    with pytest.raises(cvo.CvoError):
+        h.apply_tuning(0.5, 2, 128, 3)
     # empty clouds: nothing to time, the tuning is unchanged
     before = h.tuning()
     t = h.autotune(dev(p.X[:0]), dev(p.Z), p.T_true, dev(p.FX[:0]), dev(p.FZ))
@@ -119,10 +122,11 @@ def test_autotune_batch():
         T0, inf0, _ = h.register_batch(args)
         t = h.autotune_batch(args)
         assert t["cell_factor"] in CELLS and t["super_delta"] in SUPERS and t["chunk_len"] in ITEM_LENS
+        assert t["query_lanes"] in LANES
         assert t["measured_ms"] > 0.0
         cur = h.tuning()
-        assert (cur["cell_factor"], cur["super_delta"], cur["chunk_len"]) == \
-            (t["cell_factor"], t["super_delta"], t["chunk_len"])
+        assert (cur["cell_factor"], cur["super_delta"], cur["chunk_len"], cur["query_lanes"]) == \
+            (t["cell_factor"], t["super_delta"], t["chunk_len"], t["query_lanes"])
         T1, inf1, _ = h.register_batch(args)
         # nothing to time: the tuning is kept as it is
         assert h.autotune_batch([])["measured_ms"] == 0.0 and h.tuning() == cur

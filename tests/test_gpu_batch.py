@@ -144,3 +144,19 @@ def test_batched_setup_dense(monkeypatch):
     args = [(X[:600], Z[:500], T, FX[:600], FZ[:500]) for X, Z, T, FX, FZ in args]
     with cvo.CVO(blocks=pairs[0].blocks, ell=0.2, cutoff_mult=0.0, max_iters=10) as h:
         assert_bitwise_equal(*batched_and_pairwise(h, args, monkeypatch))
+
+
+def test_batch_lanes_per_query():
+    """The batch with 2 and 4 lanes per query (query groups of 16 and 8)
+    reaches the one-lane batch's poses to rounding."""
+    pairs, args = small_batch(n_pairs=4, seed=35)
+    with cvo.CVO(blocks=pairs[0].blocks, **KW) as h:
+        t = h.tuning()
+        T1, i1, _ = h.register_batch(args)
+        for lanes in (2, 4):
+            h.apply_tuning(t["cell_factor"], t["super_delta"], t["chunk_len"], lanes)
+            Tl, il, _ = h.register_batch(args)
+            for k in range(len(pairs)):
+                er, et = pose_err(T1[k], Tl[k])
+                assert er <= POSE_TOL and et <= POSE_TOL, (lanes, k, er, et)
+                assert il[k]["F"] == pytest.approx(i1[k]["F"], rel=1e-4), (lanes, k)

@@ -46,10 +46,13 @@ def rand_pose(r, ang=0.2, tr=0.3):
     return oracle.se3_exp(np.concatenate([r.normal(size=3) * ang / math.sqrt(3), r.normal(size=3) * tr / math.sqrt(3)]))
 
 
-def compare_eval(X, Z, FX, FZ, blocks, ell, cm, T, bf16=False, sigma=1.0, ndir=3, seed=0, tuning=None):
+def compare_eval(X, Z, FX, FZ, blocks, ell, cm, T, bf16=False, sigma=1.0, ndir=3, seed=0, tuning=None, lanes=1):
     h = cvo.CVO(blocks=blocks, ell=ell, cutoff_mult=cm, sigma=sigma)
     if tuning is not None:
         cvo.cvo_set_tuning(h.h, *tuning)
+    if lanes != 1:
+        t = h.tuning()
+        h.apply_tuning(t["cell_factor"], t["super_delta"], t["chunk_len"], lanes)
     if FX is not None and bf16:
         fx_d, fz_d = bf16_dev(FX), bf16_dev(FZ)
         FXo, FZo = scenes.bf16_round(FX), scenes.bf16_round(FZ)
@@ -160,6 +163,47 @@ def test_tile_ragged_groups_and_batches_bf16(n):
     Z = r.uniform(-0.3, 0.3, (m, 3)).astype(np.float32)
     compare_eval(X, Z, semantic_features(r, n), semantic_features(r, m), SEM_BLOCKS, 0.1, 3.0,
                  rand_pose(r, 0.05, 0.05), bf16=True, ndir=2)
+
+
+@pytest.mark.parametrize("lanes", [2, 4])
+def test_lanes_per_query_semantic_bf16(lanes):
+    """Query groups of 32 / lanes queries, each query's candidates shared by
+    that many lanes (bfloat16 labels on the tensor-core tile)."""
+    r = rng(40 + lanes)
+    n, m = 2100, 1900
+    X = r.uniform(-1, 1, size=(n, 3)).astype(np.float32)
+    Z = r.uniform(-1, 1, size=(m, 3)).astype(np.float32)
+    compare_eval(X, Z, semantic_features(r, n), semantic_features(r, m), SEM_BLOCKS, 0.1, 3.0,
+                 rand_pose(r, 0.05, 0.05), bf16=True, lanes=lanes)
+
+
+@pytest.mark.parametrize("lanes", [2, 4])
+def test_lanes_per_query_street_f32(lanes):
+    p = scenes.street_pair()
+    sel = rng(7).permutation(p.n)[:5000]
+    compare_eval(p.X[sel], p.Z[sel], p.FX[sel], p.FZ[sel], p.blocks, 0.3, 3.0, p.T_true, lanes=lanes)
+
+
+@pytest.mark.parametrize("n", [1, 5, 17, 33])
+def test_lanes_per_query_ragged(n):
+    """Groups smaller than 32 / lanes and batches shorter than 2 lanes x
+    candidates."""
+    r = rng(60 + n)
+    m = 3 * n + 7
+    X = r.uniform(-0.3, 0.3, (n, 3)).astype(np.float32)
+    Z = r.uniform(-0.3, 0.3, (m, 3)).astype(np.float32)
+    for lanes in (2, 4):
+        compare_eval(X, Z, semantic_features(r, n), semantic_features(r, m), SEM_BLOCKS, 0.1, 3.0,
+                     rand_pose(r, 0.05, 0.05), bf16=True, ndir=1, lanes=lanes)
+
+
+def test_lanes_per_query_other_blocks():
+    """A block list without a multi-lane sweep keeps one lane per query in
+    the smaller groups: still the oracle's sums."""
+    r = rng(70)
+    X = r.uniform(-2, 2, size=(3001, 3)).astype(np.float32)
+    Z = r.uniform(-2, 2, size=(2999, 3)).astype(np.float32)
+    compare_eval(X, Z, None, None, [], 0.15, 3.0, rand_pose(r, 0.1, 0.2), lanes=4)
 
 
 def test_generic_blocks():
