@@ -90,7 +90,8 @@ void release(DevBuf& b)
 }
 
 struct LevelHost {
-    double h;         // cell edge
+    double h;         // cell edge (y and z)
+    double hx;        // cell edge along x (h / cell_xdiv)
     double rdesign;   // cutoff radius the level is built for (cell edge = cell_factor * rdesign)
     int nx, ny, nz;
     float ox, oy, oz;
@@ -195,6 +196,10 @@ struct cvo_handle_s {
     // lanes per query in the sweep (1, 2 or 4): query groups of 32 / query_lanes
     // queries, each query's candidates shared among its lanes
     int query_lanes = 1;
+    // grid cells along x (the rows whose runs the sweep streams) up to
+    // cell_xdiv times shorter than across: the runs' ends trim closer to the
+    // query group's ball-grown box, and the number of runs stays the same
+    int cell_xdiv = 4;
     // an X-row shard registration in progress (cvo_shard_begin .. cvo_shard_end)
     int shard_active = 0;
     // failure injection for the next persistent registration (cvo_inject_barrier_stall)
@@ -433,6 +438,7 @@ void set_levels(cvo_handle h, PairRes& P, const float zmin[3], const float zmax[
         P.nlevels = 1;
         LevelHost& L = P.lv[0];
         L.h = 1.0;
+        L.hx = 1.0;
         L.rdesign = 1.0;
         L.nx = L.ny = L.nz = 1;
         L.ox = zmin[0]; L.oy = zmin[1]; L.oz = zmin[2];
@@ -446,10 +452,13 @@ void set_levels(cvo_handle h, PairRes& P, const float zmin[3], const float zmax[
             LevelHost& L = P.lv[k];
             L.rdesign = rc_hi * 1.0002 / std::pow(std::sqrt(2.0), k);
             double hh = h->cell_factor * L.rdesign;
+            // the x division first falls back to fewer parts, then the cells
+            // grow, until the grid has at most kMaxCells cells
+            int xdiv = h->cell_xdiv;
             for (;;) {
                 // cell counts in double first: a cloud far wider than the
                 // cutoff would overflow an int before the size check
-                const double cx = std::floor(((double)zmax[0] - zmin[0]) / hh) + 1.0;
+                const double cx = std::floor(((double)zmax[0] - zmin[0]) / (hh / xdiv)) + 1.0;
                 const double cy = std::floor(((double)zmax[1] - zmin[1]) / hh) + 1.0;
                 const double cz = std::floor(((double)zmax[2] - zmin[2]) / hh) + 1.0;
                 if (cx * cy * cz <= (double)kMaxCells) {
@@ -459,9 +468,11 @@ void set_levels(cvo_handle h, PairRes& P, const float zmin[3], const float zmax[
                     L.ncells = (long long)L.nx * L.ny * L.nz;
                     break;
                 }
-                hh *= 1.26;
+                if (xdiv > 1) xdiv /= 2;
+                else hh *= 1.26;
             }
             L.h = hh;
+            L.hx = hh / xdiv;
             L.ox = zmin[0]; L.oy = zmin[1]; L.oz = zmin[2];
         }
     }
@@ -569,8 +580,8 @@ cvo_status prepare_build(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo
             CVO_CUDA(launch_pack(xyz_z, feat_z, Z->feat_dtype == CVO_BF16, D, nullptr, m, (float4*)P.zrec[k].p, rs,
                                  h->rec_bf16, h->s));
         } else {
-            CVO_CUDA(launch_cell_keys(xyz_z, m, L.ox, L.oy, L.oz, (float)(1.0 / L.h), L.nx, L.ny, L.nz,
-                                      (unsigned*)h->keys.p, (unsigned*)h->vals.p, h->s));
+            CVO_CUDA(launch_cell_keys(xyz_z, m, L.ox, L.oy, L.oz, (float)(1.0 / L.h), (float)(1.0 / L.hx), L.nx, L.ny,
+                                      L.nz, (unsigned*)h->keys.p, (unsigned*)h->vals.p, h->s));
             unsigned *ks, *vs;
             CVO_TRY(sort_pairs(h, m, bits_for(L.ncells), &ks, &vs));
             CVO_CUDA(launch_cell_start(ks, m, (int)L.ncells, (int*)P.cell_start[k].p, h->s));
@@ -628,6 +639,7 @@ cvo_status level_descs(PairRes& P, const unsigned* hm)
         LevelDesc& d = P.ld[k];
         d.h = (float)L.h;
         d.inv_h = (float)(1.0 / L.h);
+        d.inv_hx = (float)(1.0 / L.hx);
         d.ox = L.ox; d.oy = L.oy; d.oz = L.oz;
         d.nx = L.nx; d.ny = L.ny; d.nz = L.nz;
         d.cell_start = (const int*)P.cell_start[k].p;
@@ -1001,7 +1013,7 @@ cvo_status prepare_batch(cvo_handle h, const std::vector<int>& live, const cvo_c
                 const PairRes& P = h->pr[idx[j]];
                 const LevelHost& L = P.lv[k];
                 kj[j] = KeyJob{Z[live[idx[j]]].xyz, seg[idx[j]].keys, seg[idx[j]].vals, L.ox, L.oy, L.oz,
-                               (float)(1.0 / L.h), P.m, L.nx, L.ny, L.nz};
+                               (float)(1.0 / L.h), (float)(1.0 / L.hx), P.m, L.nx, L.ny, L.nz};
                 nbits = std::max(nbits, bits_for(L.ncells));
             }
             CVO_CUDA(launch_cell_keys_batch(kj.data(), cnt, h->s));
@@ -1026,7 +1038,7 @@ cvo_status prepare_batch(cvo_handle h, const std::vector<int>& live, const cvo_c
         std::vector<KeyJob> kj(nl);
         for (int i = 0; i < nl; ++i)
             kj[i] = KeyJob{X[live[i]].xyz, seg[i].keys, seg[i].vals, xlo[i][0], xlo[i][1], xlo[i][2],
-                           (float)(1.0 / cell0[i]), h->pr[i].n, 0, 0, 0};
+                           (float)(1.0 / cell0[i]), (float)(1.0 / cell0[i]), h->pr[i].n, 0, 0, 0};
         CVO_CUDA(launch_morton_keys_batch(kj.data(), nl, h->s));
         const std::vector<SortJob> sj = sort_jobs(all, [&](int i) { return h->pr[i].n; });
         int alt = 0;

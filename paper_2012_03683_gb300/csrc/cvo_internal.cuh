@@ -66,7 +66,8 @@ enum StatIndex {
 };
 
 struct LevelDesc {
-    float h, inv_h;          // cell edge and its inverse
+    float h, inv_h;          // cell edge and its inverse (y and z)
+    float inv_hx;            // inverse cell edge along x (the cells' rows; a fraction of h trims the rows' runs)
     float ox, oy, oz;        // grid origin (minimum corner), Z frame
     int nx, ny, nz;          // cells per axis
     const int* cell_start;   // nx*ny*nz + 1
@@ -304,7 +305,7 @@ struct KeyJob {
     const float* xyz;
     unsigned* keys;
     unsigned* vals;
-    float ox, oy, oz, inv;
+    float ox, oy, oz, inv, invx;   // invx: along x (grid cells)
     int n, nx, ny, nz;
 };
 
@@ -420,8 +421,8 @@ cudaError_t launch_check_feat(const void* feat, long long count, int bf16, int* 
 // decode_zstats turns into (cx, cy, cz, mean r^2, max r) on the host
 cudaError_t launch_zstats(const float* xyz, int n, long long* out, cudaStream_t s);
 void decode_zstats(const long long* raw, int n, double out5[5]);
-cudaError_t launch_cell_keys(const float* xyz, int n, float ox, float oy, float oz, float inv_h, int nx, int ny,
-                             int nz, unsigned* keys, unsigned* vals, cudaStream_t s);
+cudaError_t launch_cell_keys(const float* xyz, int n, float ox, float oy, float oz, float inv_h, float inv_hx, int nx,
+                             int ny, int nz, unsigned* keys, unsigned* vals, cudaStream_t s);
 cudaError_t launch_morton_keys(const float* xyz, int n, float ox, float oy, float oz, float inv_cell,
                                unsigned* keys, unsigned* vals, cudaStream_t s);
 size_t radix_sort_temp_bytes(int n);

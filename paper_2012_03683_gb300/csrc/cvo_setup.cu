@@ -104,20 +104,21 @@ __device__ __forceinline__ int cell_of(float v, float o, float inv_h, int n)
 }
 
 __device__ __forceinline__ void cell_keys_body(const float* __restrict__ xyz, int n, float ox, float oy, float oz,
-                                               float inv_h, int nx, int ny, int nz, unsigned* keys, unsigned* vals, int j)
+                                               float inv_h, float inv_hx, int nx, int ny, int nz, unsigned* keys,
+                                               unsigned* vals, int j)
 {
     if (j >= n) return;
-    const int cx = cell_of(xyz[3 * (size_t)j + 0], ox, inv_h, nx);
+    const int cx = cell_of(xyz[3 * (size_t)j + 0], ox, inv_hx, nx);
     const int cy = cell_of(xyz[3 * (size_t)j + 1], oy, inv_h, ny);
     const int cz = cell_of(xyz[3 * (size_t)j + 2], oz, inv_h, nz);
     keys[j] = (unsigned)((cz * ny + cy) * nx + cx);
     vals[j] = (unsigned)j;
 }
 
-__global__ void k_cell_keys(const float* __restrict__ xyz, int n, float ox, float oy, float oz, float inv_h, int nx,
-                            int ny, int nz, unsigned* keys, unsigned* vals)
+__global__ void k_cell_keys(const float* __restrict__ xyz, int n, float ox, float oy, float oz, float inv_h,
+                            float inv_hx, int nx, int ny, int nz, unsigned* keys, unsigned* vals)
 {
-    cell_keys_body(xyz, n, ox, oy, oz, inv_h, nx, ny, nz, keys, vals, blockIdx.x * blockDim.x + threadIdx.x);
+    cell_keys_body(xyz, n, ox, oy, oz, inv_h, inv_hx, nx, ny, nz, keys, vals, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 __device__ __forceinline__ unsigned spread10(unsigned v)
@@ -620,7 +621,7 @@ __global__ void __launch_bounds__(kZStatsThreads) k_zspread_b(JobList<BoxJob> J)
 __global__ void k_cell_keys_b(JobList<KeyJob> J)
 {
     const KeyJob& k = J.j[blockIdx.y];
-    cell_keys_body(k.xyz, k.n, k.ox, k.oy, k.oz, k.inv, k.nx, k.ny, k.nz, k.keys, k.vals,
+    cell_keys_body(k.xyz, k.n, k.ox, k.oy, k.oz, k.inv, k.invx, k.nx, k.ny, k.nz, k.keys, k.vals,
                    blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -750,12 +751,12 @@ cudaError_t launch_check_feat(const void* feat, long long count, int bf16, int* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_cell_keys(const float* xyz, int n, float ox, float oy, float oz, float inv_h, int nx, int ny,
-                             int nz, unsigned* keys, unsigned* vals, cudaStream_t s)
+cudaError_t launch_cell_keys(const float* xyz, int n, float ox, float oy, float oz, float inv_h, float inv_hx, int nx,
+                             int ny, int nz, unsigned* keys, unsigned* vals, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
-    k_cell_keys<<<blocks_for(n, 256), 256, 0, s>>>(xyz, n, ox, oy, oz, inv_h, nx, ny, nz, keys, vals);
+    k_cell_keys<<<blocks_for(n, 256), 256, 0, s>>>(xyz, n, ox, oy, oz, inv_h, inv_hx, nx, ny, nz, keys, vals);
     return cudaGetLastError();
 }
 

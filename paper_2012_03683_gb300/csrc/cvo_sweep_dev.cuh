@@ -398,8 +398,8 @@ __device__ __forceinline__ void run_cells(const LevelDesc& L, const Stream& s, i
     }
     const float w = sqrtf(w2) * 1.0001f;
     const float tx = 4.0e-7f * fmaxf(fabsf(bmn[0]), fabsf(bmx[0])) + 1.0e-6f;
-    a = max(s.cx0, floor_cell(bmn[0] - w - tx, L.ox, L.inv_h));
-    b = min(s.cx1, floor_cell(bmx[0] + w + tx, L.ox, L.inv_h));
+    a = max(s.cx0, floor_cell(bmn[0] - w - tx, L.ox, L.inv_hx));
+    b = min(s.cx1, floor_cell(bmx[0] + w + tx, L.ox, L.inv_hx));
 }
 
 // Warp-uniform.  Returns false when the grown box misses the grid.
@@ -431,8 +431,9 @@ __device__ __forceinline__ bool stream_setup(const LevelDesc& L, int m, bool den
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             const float pad = rc * 1.0001f + 4.0e-7f * fmaxf(fabsf(mn[r]), fabsf(mx[r])) + 1.0e-6f;
-            c0[r] = floor_cell(mn[r] - pad, o3[r], L.inv_h);
-            c1[r] = floor_cell(mx[r] + pad, o3[r], L.inv_h);
+            const float inv = r == 0 ? L.inv_hx : L.inv_h;
+            c0[r] = floor_cell(mn[r] - pad, o3[r], inv);
+            c1[r] = floor_cell(mx[r] + pad, o3[r], inv);
             if (c1[r] < 0 || c0[r] > n3[r] - 1) empty = true;
             c0[r] = max(c0[r], 0);
             c1[r] = min(c1[r], n3[r] - 1);
