@@ -124,10 +124,10 @@ def semantic_features(r, n):
     return np.hstack([r.uniform(0, 1, (n, 3)), r.dirichlet(np.ones(19), n)]).astype(np.float32)
 
 
-def test_tile_far_from_origin_bf16():
-    """bfloat16 RGB + labels with a cutoff (every pair of a staged batch on a
-    dense tile, moments about the query group's centre on the tensor cores)
-    80 m from the origin with l = 5 cm."""
+def test_semantic_bf16_far_from_origin():
+    """bfloat16 RGB + labels with a cutoff (the label products on the
+    tensor-core tile) 80 m from the origin with l = 5 cm: the offsets keep
+    their precision (double-float queries) there too."""
     r = rng(16)
     n = 3000
     base = np.array([60.0, -20.0, 80.0])
@@ -140,11 +140,10 @@ def test_tile_far_from_origin_bf16():
 
 
 @pytest.mark.parametrize("super_delta", [2, 4, 6])
-def test_tile_sparse_queries_wide_groups_bf16(super_delta):
+def test_semantic_bf16_sparse_queries_wide_groups(super_delta):
     """Sparse queries over a dense cloud with Morton super-cells of 2^k
-    cutoff radii: a query group spans several radii, so its moments about
-    the group's centre are far larger than about each query (the most
-    cancellation when they are moved to each query's origin)."""
+    cutoff radii: a query group spans several radii, so its candidate
+    stream is long and each candidate is in range of few of its queries."""
     r = rng(17 + super_delta)
     n, m = 700, 9000
     X = r.uniform(-3, 3, size=(n, 3)).astype(np.float32)
@@ -154,9 +153,9 @@ def test_tile_sparse_queries_wide_groups_bf16(super_delta):
 
 
 @pytest.mark.parametrize("n", [1, 5, 31, 33, 100])
-def test_tile_ragged_groups_and_batches_bf16(n):
+def test_semantic_bf16_ragged_groups_and_batches(n):
     """Groups of fewer than 32 queries and staged batches of fewer than 32
-    candidates on the dense tile."""
+    candidates on the tensor-core label tile."""
     r = rng(30 + n)
     m = 3 * n + 7
     X = r.uniform(-0.3, 0.3, (n, 3)).astype(np.float32)
