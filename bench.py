@@ -637,7 +637,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = cvo.cvo_kernel_launches()
-    step_ms, evals, conv, iters = [], 0, 0, []
+    step_ms, evals, conv, iters, tests = [], 0, 0, [], 0
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -648,6 +648,7 @@ def main():
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         evals += sum(i["pairs"] for i in infos)
+        tests += sum(i["candidates"] for i in infos)
         conv += sum(1 for i in infos if i["status"] == 0)
         iters = [i["iters"] for i in infos]
     torch.cuda.synchronize()
@@ -736,6 +737,9 @@ def main():
         "registered_pairs_per_s": regs_per_s,
         "ms_per_batch": spread(step_ms),
         "pair_evals_per_batch": evals / args.steps,
+        # the sweep's (query, candidate) distance tests per in-cutoff pair: the
+        # candidates its streams examine beyond the pairs the method counts
+        "sweep_tests_per_pair": tests / max(evals, 1),
         "converged_per_batch": conv / args.steps,
         "iterations": iters,
         "plain": plain,
