@@ -629,7 +629,7 @@ cvo_status prepare_build(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo
 // Phase 3: the level descriptors, with the group counts (hm).
 // The level descriptors on the host (P.ld), with the group counts (hm); the
 // device copy's buffer ensured.
-cvo_status level_descs(PairRes& P, const unsigned* hm)
+cvo_status level_descs(cvo_handle h, PairRes& P, const unsigned* hm)
 {
     const int n = P.n;
     for (int k = 0; k < P.nlevels; ++k) {
@@ -648,6 +648,10 @@ cvo_status level_descs(PairRes& P, const unsigned* hm)
         d.items = nullptr;
         d.ngroups = L.ngroups;
         d.nitems = 0;
+        d.chunk_min = 0;
+        // trimming the rows by each query pays only where a work item is long
+        // enough to carry it (the trim is per item, the saving per candidate)
+        d.trim = h->chunk_len >= kTrimChunkLen ? 1 : 0;
     }
     P.max_items = 1;
     CVO_CUDA(ensure(P.levels_dev, sizeof(P.ld)));
@@ -656,7 +660,7 @@ cvo_status level_descs(PairRes& P, const unsigned* hm)
 
 cvo_status prepare_finish(cvo_handle h, PairRes& P, const unsigned* hm)
 {
-    CVO_TRY(level_descs(P, hm));
+    CVO_TRY(level_descs(h, P, hm));
     CVO_CUDA(cudaMemcpyAsync(P.levels_dev.p, P.ld, P.nlevels * sizeof(LevelDesc), cudaMemcpyHostToDevice, h->s));
     return CVO_OK;
 }
@@ -1075,7 +1079,7 @@ cvo_status prepare_batch(cvo_handle h, const std::vector<int>& live, const cvo_c
     std::vector<HostBlock> up;
     for (int i = 0; i < nl; ++i) {
         PairRes& P = h->pr[i];
-        CVO_TRY(level_descs(P, hslot(i)));
+        CVO_TRY(level_descs(h, P, hslot(i)));
         CVO_TRY(state_host(h, P, i, T_init + 16 * live[i], p.ell, 1));
         up.push_back(HostBlock{P.ld, P.levels_dev.p, P.nlevels * sizeof(LevelDesc)});
         up.push_back(HostBlock{h->h_state + i, P.state.p, sizeof(IterState)});

@@ -47,6 +47,7 @@ constexpr int kMaxChunks = 64;   // most work items (chunks) one query group's s
 constexpr int kChunkLen = 128;   // default candidates per planned work item
 constexpr int kChunks = 8;       // chunks per group of the uniform items
 constexpr int kChunkMin = 64;    // shortest run-time chunk of the uniform items
+constexpr int kTrimChunkLen = 768;   // planned items at least this long trim the stream rows by each query
 constexpr int kFinalizeThreads = 64;   // threads of a batched step block
 constexpr int kStepThreads = 384;      // threads of the single-pair step block (its registers allow 12 warps)
 constexpr int kGroupBlocks = 8;    // sweep blocks per reduction group (the group's last block sums them)
@@ -78,7 +79,7 @@ struct LevelDesc {
     int nitems;
     int chunk_min;           // > 0: a group's stream is cut into min(chunks, length / chunk_min) chunks at
                              // run time (the rest of its items are empty); 0: into the planned chunks
-    int pad_;
+    int trim;                // 1: the stream rows' runs cover the queries' balls; 0: the group's box grown by a ball
 };
 
 // Feature-kernel constants (exponent in log2 units).

@@ -334,6 +334,7 @@ extern "C" cvo_status cvo_evaluate_dense_noalloc(const cvo_params* p, void* cuda
     ld.h = 1.0f;
     ld.inv_h = 1.0f;
     ld.inv_hx = 1.0f;
+    ld.trim = 0;
     ld.nx = ld.ny = ld.nz = 1;
     ld.cell_start = nullptr;   // the dense sweep reads every record in order
     ld.zrec = zrec;

@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32, 4) k_register(PersistArgs a)
     const PairDesc P = a.sw.pairs[0];
     IterState* st = P.st;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int rs = a.sw.rs;
+    const int rs = rec_stride<Feat>(a.sw.rs);
     const bool dense = a.sw.dense != 0;
     const FeatConst fc = a.sw.fc;
     float4* stage = stage_mem + (size_t)warp * 2 * 32 * rs;
@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32, 4) k_register(PersistArgs a)
 template <class Feat>
 cudaError_t persist_t(const PersistArgs& a, int* nblocks, size_t* smem_out, bool query, cudaStream_t s)
 {
+    if (Feat::kRs > 0 && Feat::kRs != a.sw.rs) return cudaErrorInvalidValue;   // the policy's record layout
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_register<Feat>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);

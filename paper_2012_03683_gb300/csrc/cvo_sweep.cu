@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
     StatAcc acc;
     stat_acc_init(acc, lane);
     const LevelDesc L = P.levels[st->level];
-    const int rs = a.rs;
+    const int rs = rec_stride<Feat>(a.rs);
     const bool dense = a.dense != 0;
     const float sg = st->sg, rc = st->rc, rc2 = st->rc2;
     const FeatConst fc = a.fc;
@@ -565,6 +565,7 @@ cudaError_t each_chunk(const J* jobs, int count, F&& f)
 template <class Feat, int S = 1>
 cudaError_t info_t(int rs, SweepLaunch* out)
 {
+    if (Feat::kRs > 0 && Feat::kRs != rs) return cudaErrorInvalidValue;   // the policy's record layout
     static bool attr_set = false;   // one-time opt-in above the 48 KB default
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_sweep<Feat, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);

@@ -62,12 +62,16 @@ __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wai
 
 // Eq. (geometric_only): no features, c_ij = 1.
 // Interface of a feature policy: kScratch bytes of shared memory per warp;
-// load_query once per work item; batch once per staged batch of candidates
+// kRs, the record stride in float4 that its layout fixes (0 where only the
+// launch knows it: the host checks the two agree, and a fixed stride lets
+// the compiler fold the staged records' addresses); load_query once per work
+// item; batch once per staged batch of candidates
 // (warp-uniform); pair per candidate c of the batch, adding the feature
 // exponent to arg, clearing in when the feature-space cutoff excludes the
 // pair, and returning the product of the inner-product factors.
 struct FeatNone {
     static constexpr int kScratch = 0;
+    static constexpr int kRs = 1;
     struct Q {};
     __device__ static void load_query(Q&, const float4*, const FeatConst&, unsigned char*, int) {}
     __device__ static void batch(Q&, const float4*, int, int, int) {}
@@ -82,6 +86,7 @@ struct FeatFixed {
     static constexpr int kScratch = 0;
     static constexpr int D = DSE + DDOT;
     static constexpr int kVec = BF16 ? (2 * D + 15) / 16 : (4 * D + 15) / 16;
+    static constexpr int kRs = 1 + kVec;
     struct Q {
         float v[D];
     };
@@ -142,6 +147,7 @@ struct FeatFixed {
 // Any block list (up to 4 blocks, 64 entries): features read per pair.
 struct FeatGeneric {
     static constexpr int kScratch = 0;
+    static constexpr int kRs = 0;
     struct Q {
         const float4* rec;
     };
@@ -205,6 +211,7 @@ struct FeatMMA {
     static constexpr int kCsStride = 36;
     static constexpr int kCsRow = 40;
     static constexpr int kScratch = kTileBytes + 32 * kCsStride * 4;
+    static constexpr int kRs = 1 + (2 * D + 15) / 16;   // xyz, then D bfloat16 features
     static_assert(S == 1 || (32 / S) * kCsRow <= 32 * kCsStride, "the grouped result rows fit the tile");
     struct Q {
         float se[DSE > 0 ? DSE : 1];
@@ -348,6 +355,15 @@ struct FeatMMA {
 
 // ---- the sweep --------------------------------------------------------------
 
+
+// The record stride a kernel of policy Feat works with: the policy's own
+// where it fixes one (a compile-time constant), else the launch's.
+template <class Feat>
+__device__ __forceinline__ int rec_stride(int rs)
+{
+    return Feat::kRs > 0 ? Feat::kRs : rs;
+}
+
 __device__ __forceinline__ int floor_cell(float v, float o, float inv_h)
 {
     const float c = floorf((v - o) * inv_h);
@@ -357,11 +373,17 @@ __device__ __forceinline__ int floor_cell(float v, float o, float inv_h)
 // A query group's candidate stream: for each (y, z) row of grid cells that
 // overlaps the group's bounding box grown by the cutoff radius, the run of
 // the row's cells whose x-range can hold a point within the radius of the
-// box.  A row at (y, z) distance d from the box needs only the x-range of
-// the box grown by sqrt(r^2 - d^2) (none when d > r): the stream covers the
-// box grown by a ball, not by a cube, in whole cells.
+// group.  A point at (y, z) distance d from the row needs only the x-range
+// within sqrt(r^2 - d^2) of it (none when d > r).  Taken for the group's
+// box, the run covers the box grown by a ball, not by a cube, in whole
+// cells; with the level's trim flag, runs 0-31 take it for each query and
+// cover the union of the queries' ranges, the queries' balls (on the cube
+// scenes 12 % fewer candidates, for a loop over the queries per row; a
+// stream has rarely more runs).  r0start / r0len: this lane's run's first
+// cell record and record count for runs 0-31 (the walk's first pass reads
+// them instead of bounding the rows again).
 struct Stream {
-    int cx0, cx1, cy0, cz0, nry, nruns, total;
+    int cx0, cx1, cy0, cz0, nry, nruns, total, nq, r0start, r0len;
 };
 
 // The group's box (Z frame: min xyz, max xyz) and the cutoff radius with its
@@ -374,32 +396,72 @@ __device__ __forceinline__ float* stream_box()
     return box[threadIdx.x >> 5];
 }
 
+// The group's query positions (Z frame, the high parts of x'), per warp in
+// shared memory: entry q is lane q's query; an inactive lane's entry lies
+// out of every row's reach.  Warps of blocks of up to kSweepWarps warps
+// (every kernel that forms streams is launched with at most that many).
+__device__ __forceinline__ float4* stream_queries()
+{
+    __shared__ float4 qp[kSweepWarps][32];
+    return qp[threadIdx.x >> 5];
+}
+
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // The cells [a, b] of run r (row cy0 + r % nry, cz0 + r / nry) of a stream
 // with a cutoff; a > b when the row is out of reach.  The gaps between the
-// row's cell extent and the box are shrunk, and the radius grown, by margins
-// above the FP32 rounding of the coordinates, so no pair within the cutoff is
-// left out.
-__device__ __forceinline__ void run_cells(const LevelDesc& L, const Stream& s, int r, int& a, int& b)
+// row's cell extent and the box (or the queries) are shrunk, and the radius
+// grown, by margins above the FP32 rounding of the coordinates (and of the
+// square root), so no pair within the cutoff is left out.  per_query: the
+// run takes the union of the queries' ranges (else the box's range).
+__device__ __forceinline__ void run_cells(const LevelDesc& L, const Stream& s, int r, bool per_query, int& a, int& b)
 {
     const float* bx = stream_box();
     const float bmn[3] = {bx[0], bx[1], bx[2]}, bmx[3] = {bx[3], bx[4], bx[5]}, rad = bx[6];
     const int cy = s.cy0 + r % s.nry, cz = s.cz0 + r / s.nry;
     const float ylo = L.oy + (float)cy * L.h, zlo = L.oz + (float)cz * L.h;
+    const float yhi = ylo + L.h, zhi = zlo + L.h;
     // margins: the rounding of the cell bounds (|origin| + |bound| + h) and of the box
     const float ty = 4.0e-7f * (fabsf(L.oy) + fabsf(ylo) + L.h + fmaxf(fabsf(bmn[1]), fabsf(bmx[1]))) + 1.0e-6f;
     const float tz = 4.0e-7f * (fabsf(L.oz) + fabsf(zlo) + L.h + fmaxf(fabsf(bmn[2]), fabsf(bmx[2]))) + 1.0e-6f;
-    const float gy = fmaxf(0.0f, fmaxf(ylo - bmx[1], bmn[1] - (ylo + L.h)) - ty);
-    const float gz = fmaxf(0.0f, fmaxf(zlo - bmx[2], bmn[2] - (zlo + L.h)) - tz);
-    const float w2 = rad * rad - (gy * gy + gz * gz);
-    if (w2 < 0.0f) {
+    float lo = 3.0e38f, hi = -3.0e38f;
+    if (per_query) {
+        const float4* qp = stream_queries();
+        const float rad2 = rad * rad;
+        for (int q = 0; q < s.nq; ++q) {
+            const float4 x = qp[q];
+            const float gy = fmaxf(0.0f, fmaxf(ylo - x.y, x.y - yhi) - ty);
+            const float gz = fmaxf(0.0f, fmaxf(zlo - x.z, x.z - zhi) - tz);
+            const float w2 = rad2 - fmaf(gy, gy, gz * gz);
+            if (w2 >= 0.0f) {
+                const float w = sqrt_approx(w2) * 1.0001f;
+                lo = fminf(lo, x.x - w);
+                hi = fmaxf(hi, x.x + w);
+            }
+        }
+    } else {
+        const float gy = fmaxf(0.0f, fmaxf(ylo - bmx[1], bmn[1] - yhi) - ty);
+        const float gz = fmaxf(0.0f, fmaxf(zlo - bmx[2], bmn[2] - zhi) - tz);
+        const float w2 = rad * rad - (gy * gy + gz * gz);
+        if (w2 >= 0.0f) {
+            const float w = sqrtf(w2) * 1.0001f;
+            lo = bmn[0] - w;
+            hi = bmx[0] + w;
+        }
+    }
+    if (lo > hi) {
         a = 1;
         b = 0;
         return;
     }
-    const float w = sqrtf(w2) * 1.0001f;
     const float tx = 4.0e-7f * fmaxf(fabsf(bmn[0]), fabsf(bmx[0])) + 1.0e-6f;
-    a = max(s.cx0, floor_cell(bmn[0] - w - tx, L.ox, L.inv_hx));
-    b = min(s.cx1, floor_cell(bmx[0] + w + tx, L.ox, L.inv_hx));
+    a = max(s.cx0, floor_cell(lo - tx, L.ox, L.inv_hx));
+    b = min(s.cx1, floor_cell(hi + tx, L.ox, L.inv_hx));
 }
 
 // Warp-uniform.  Returns false when the grown box misses the grid.
@@ -409,6 +471,7 @@ __device__ __forceinline__ bool stream_setup(const LevelDesc& L, int m, bool den
     s.cx0 = s.cx1 = s.cy0 = s.cz0 = 0;
     s.nry = 1;
     s.nruns = 1;
+    s.nq = 0;
     if (!dense) {
         float mn[3], mx[3];
 #pragma unroll
@@ -443,7 +506,8 @@ __device__ __forceinline__ bool stream_setup(const LevelDesc& L, int m, bool den
         s.nry = c1[1] - c0[1] + 1;
         s.nruns = s.nry * (c1[2] - c0[2] + 1);
         float* bx = stream_box();
-        __syncwarp();   // a previous stream of this warp may still be reading the box
+        float4* qp = stream_queries();
+        __syncwarp();   // a previous stream of this warp may still be reading the box and queries
         if (lane == 0) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
@@ -452,24 +516,35 @@ __device__ __forceinline__ bool stream_setup(const LevelDesc& L, int m, bool den
             }
             bx[6] = rc * 1.0001f + 1.0e-6f;
         }
+        if (L.trim) {
+            qp[lane] = act ? make_float4(xh[0], xh[1], xh[2], 0.0f) : make_float4(0.0f, 3.0e38f, 3.0e38f, 0.0f);
+            s.nq = 32 - __clz(__ballot_sync(kFull, act));   // entries past the last active lane are not read
+        }
         __syncwarp();
     }
     int total = 0;
+    s.r0start = 0;
+    s.r0len = 0;
     for (int b0 = 0; b0 < s.nruns; b0 += 32) {
-        int len = 0;
+        int start = 0, len = 0;
         const int r = b0 + lane;
         if (r < s.nruns) {
             if (dense) {
                 len = m;
             } else {
                 int a, b;
-                run_cells(L, s, r, a, b);
+                run_cells(L, s, r, L.trim && b0 == 0, a, b);
                 if (a <= b) {
                     const int cy = s.cy0 + r % s.nry, cz = s.cz0 + r / s.nry;
                     const int row = (cz * L.ny + cy) * L.nx;
-                    len = __ldg(L.cell_start + row + b + 1) - __ldg(L.cell_start + row + a);
+                    start = __ldg(L.cell_start + row + a);
+                    len = __ldg(L.cell_start + row + b + 1) - start;
                 }
             }
+        }
+        if (b0 == 0) {
+            s.r0start = start;
+            s.r0len = len;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) len += __shfl_xor_sync(kFull, len, o);
@@ -490,13 +565,16 @@ __device__ __forceinline__ void stream_walk(const LevelDesc& L, int m, bool dens
     for (int b0 = 0; b0 < s.nruns && base < chi; b0 += 32) {
         int rstart = 0, rlen = 0;
         const int r = b0 + lane;
-        if (r < s.nruns) {
+        if (b0 == 0) {   // the runs the setup trimmed
+            rstart = s.r0start;
+            rlen = s.r0len;
+        } else if (r < s.nruns) {
             if (dense) {
                 rstart = 0;
                 rlen = m;
             } else {
                 int a, b;
-                run_cells(L, s, r, a, b);
+                run_cells(L, s, r, false, a, b);   // runs past the first 32 take the box's range
                 if (a <= b) {
                     const int cy = s.cy0 + r % s.nry, cz = s.cz0 + r / s.nry;
                     const int row = (cz * L.ny + cy) * L.nx;
@@ -622,8 +700,7 @@ __device__ __forceinline__ void eval_batch(const float4* sb, int cnt, int rs, ty
         }
         return;
     }
-    int c = 0;
-    for (; c + 1 < cnt; c += 2) {
+    auto two = [&](int c) {
         const float4* zr0 = sb + c * rs;
         const float4* zr1 = zr0 + rs;
         const Offset o0 = offset_to(zr0[0], xh, xl);
@@ -640,7 +717,16 @@ __device__ __forceinline__ void eval_batch(const float4* sb, int cnt, int rs, ty
             add_moments(mo, w0, o0);
             add_moments(mo, w1, o1);
         }
+    };
+    // a full batch: a loop of fixed trip count, not unrolled (unrolled 4 or
+    // 16 times it measured slower: the loop body is long already)
+    if (cnt == 32) {
+#pragma unroll 1
+        for (int c = 0; c < 32; c += 2) two(c);
+        return;
     }
+    int c = 0;
+    for (; c + 1 < cnt; c += 2) two(c);
     if (c < cnt) {
         const float4* zr = sb + c * rs;
         const Offset o = offset_to(zr[0], xh, xl);
