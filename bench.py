@@ -257,9 +257,10 @@ def sweep_roofline(name, pairs_evaluated, sweep_ms_total, launches, fpp, peaks, 
                                "independent-chain ex2.approx throughput loop) x sm_max_mhz"},
         "issue": {"frac": issue_active, "peak_warp_inst_per_s": issue_peak,
                   "warp_instructions_per_launch": winst,
-                  "source": f"smsp__issue_active (share of scheduler cycles issuing) and smsp__inst_executed.sum of "
-                            f"the launches of the committed ncu capture (profiles/{profile}, same source hash); "
-                            f"peak {sms} SMs x {ISSUE_PER_CLK_SM} schedulers x sm_max_mhz"},
+                  "source": (f"smsp__issue_active (share of scheduler cycles issuing) and smsp__inst_executed.sum of "
+                             f"the launches of the committed ncu capture (profiles/{profile}, same source hash); "
+                             if profile else "no committed capture read for this kernel; ")
+                            + f"peak {sms} SMs x {ISSUE_PER_CLK_SM} schedulers x sm_max_mhz"},
     }
 
 
