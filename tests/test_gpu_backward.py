@@ -77,8 +77,11 @@ def check_close(got, ref, skip=None, name=""):
     assert err <= tol, f"{name}: max error {err:.3e} > {tol:.3e} (scale {scale:.3e})"
 
 
-def run_pair(X, Z, FX, FZ, blocks, ell, cm, T, bf16=False, sigma=1.0, dF=1.0):
+def run_pair(X, Z, FX, FZ, blocks, ell, cm, T, bf16=False, sigma=1.0, dF=1.0, chunk_len=None):
     h = cvo.CVO(blocks=blocks, ell=ell, cutoff_mult=cm, sigma=sigma)
+    if chunk_len is not None:
+        t = h.tuning()
+        h.apply_tuning(t["cell_factor"], t["super_delta"], chunk_len)
     if FX is not None and bf16:
         fx, fz = bf16_dev(FX), bf16_dev(FZ)
         FXo, FZo = scenes.bf16_round(FX), scenes.bf16_round(FZ)
@@ -93,8 +96,8 @@ def run_pair(X, Z, FX, FZ, blocks, ell, cm, T, bf16=False, sigma=1.0, dF=1.0):
     return got, ref, h
 
 
-def compare(X, Z, FX, FZ, blocks, ell, cm, T, bf16=False, sigma=1.0, dF=1.0):
-    got, ref, _ = run_pair(X, Z, FX, FZ, blocks, ell, cm, T, bf16, sigma, dF)
+def compare(X, Z, FX, FZ, blocks, ell, cm, T, bf16=False, sigma=1.0, dF=1.0, chunk_len=None):
+    got, ref, _ = run_pair(X, Z, FX, FZ, blocks, ell, cm, T, bf16, sigma, dF, chunk_len)
     for k in ("dX", "dZ", "dFX", "dFZ"):
         if k in ref:
             ref[k] = ref[k] * dF
@@ -145,6 +148,15 @@ def test_backward_room_slice(room, bf16):
     X, Z, FX, FZ = slice_pair(room, 4000, 1)
     T = room.T_true @ rand_pose(rng(2))
     compare(X, Z, FX, FZ, room.blocks, 0.1, 3.0, T, bf16=bf16)
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_backward_room_slice_trimmed_streams(room, bf16):
+    """768-candidate items: the gradient sweep's streams trimmed by each
+    query's ball."""
+    X, Z, FX, FZ = slice_pair(room, 4000, 1)
+    T = room.T_true @ rand_pose(rng(2))
+    compare(X, Z, FX, FZ, room.blocks, 0.1, 3.0, T, bf16=bf16, chunk_len=768)
 
 
 @pytest.mark.parametrize("bf16", [False, True])

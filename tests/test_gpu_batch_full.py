@@ -1,7 +1,9 @@
 """The batch-64 workload at full size (64 cube pairs of 5,000-60,000 points
 per cloud, RGB + 19 labels stored in bfloat16, l = 0.1, cutoff 3 l, <= 50
 iterations) in the launch configuration the benchmark times: tuned on the
-largest pair, all pairs registered by one batched graph launch.
+whole batch by the batch tuner, all pairs registered by one batched graph
+launch (the tuner's choice so far, 768-candidate items, also trims the
+streams by each query's ball).
 
 Checks: sampled pairs (the smallest, the median and the largest) registered
 alone give the batch's result (the single-pair path is held to the oracle by
@@ -46,7 +48,7 @@ def batch_run():
     order = sorted(range(len(pairs)), key=lambda k: pairs[k].n + pairs[k].m)
     picks = [order[0], order[len(order) // 2], order[-1]]
     with cvo.CVO(**kw) as h:
-        h.autotune(*args[order[-1]])
+        h.autotune_batch(args)
         T_batch, infos, rc = h.register_batch(args)
         singles = {k: h.register(*args[k]) for k in picks}
         evals = {k: h.evaluate(args[k][0], args[k][1], T_batch[k], args[k][3], args[k][4]) for k in picks}

@@ -46,13 +46,14 @@ def rand_pose(r, ang=0.2, tr=0.3):
     return oracle.se3_exp(np.concatenate([r.normal(size=3) * ang / math.sqrt(3), r.normal(size=3) * tr / math.sqrt(3)]))
 
 
-def compare_eval(X, Z, FX, FZ, blocks, ell, cm, T, bf16=False, sigma=1.0, ndir=3, seed=0, tuning=None, lanes=1):
+def compare_eval(X, Z, FX, FZ, blocks, ell, cm, T, bf16=False, sigma=1.0, ndir=3, seed=0, tuning=None, lanes=1,
+                 chunk_len=None):
     h = cvo.CVO(blocks=blocks, ell=ell, cutoff_mult=cm, sigma=sigma)
     if tuning is not None:
         cvo.cvo_set_tuning(h.h, *tuning)
-    if lanes != 1:
+    if lanes != 1 or chunk_len is not None:
         t = h.tuning()
-        h.apply_tuning(t["cell_factor"], t["super_delta"], t["chunk_len"], lanes)
+        h.apply_tuning(t["cell_factor"], t["super_delta"], t["chunk_len"] if chunk_len is None else chunk_len, lanes)
     if FX is not None and bf16:
         fx_d, fz_d = bf16_dev(FX), bf16_dev(FZ)
         FXo, FZo = scenes.bf16_round(FX), scenes.bf16_round(FZ)
@@ -203,6 +204,107 @@ def test_lanes_per_query_other_blocks():
     X = r.uniform(-2, 2, size=(3001, 3)).astype(np.float32)
     Z = r.uniform(-2, 2, size=(2999, 3)).astype(np.float32)
     compare_eval(X, Z, None, None, [], 0.15, 3.0, rand_pose(r, 0.1, 0.2), lanes=4)
+
+
+# Planned work items of 768 candidates or more trim the first 32 rows of a
+# query group's stream by each query's ball (the set-up loops over the
+# group's queries per row); shorter items, and rows past the first 32, take
+# the group's box grown by a ball.  The tests above run the default
+# 128-candidate items; these run the trimmed streams.
+TRIM_LENS = [768, 1536]
+
+
+@pytest.mark.parametrize("chunk_len", TRIM_LENS)
+def test_trimmed_streams_semantic_bf16(chunk_len):
+    """Rows trimmed by each query on a dense random cloud, bfloat16 labels on
+    the tensor-core tile."""
+    r = rng(3)
+    n, m = 2100, 1900
+    X = r.uniform(-1, 1, size=(n, 3)).astype(np.float32)
+    Z = r.uniform(-1, 1, size=(m, 3)).astype(np.float32)
+    compare_eval(X, Z, semantic_features(r, n), semantic_features(r, m), SEM_BLOCKS, 0.1, 3.0,
+                 rand_pose(r, 0.05, 0.05), bf16=True, chunk_len=chunk_len)
+
+
+def test_trimmed_streams_far_from_origin():
+    """The per-query trim's rounding margins 80 m from the origin with
+    l = 5 cm."""
+    r = rng(16)
+    n = 3000
+    base = np.array([60.0, -20.0, 80.0])
+    X = (base + r.uniform(-1, 1, size=(n, 3))).astype(np.float32)
+    Z = (X + r.normal(0, 0.01, size=X.shape)).astype(np.float32)
+    FX = semantic_features(r, n)
+    FZ = FX.copy()
+    FZ[:, :3] = np.clip(FX[:, :3] + r.normal(0, 0.05, (n, 3)), 0, 1)
+    compare_eval(X, Z, FX, FZ, SEM_BLOCKS, 0.05, 3.0, rand_pose(r, 0.002, 0.02), bf16=True, chunk_len=768)
+
+
+@pytest.mark.parametrize("super_delta", [2, 4, 6])
+def test_trimmed_streams_wide_groups(super_delta):
+    """Query groups over 2^k cutoff radii: streams of more than 32 rows, the
+    first 32 trimmed by each query and the rest by the box."""
+    r = rng(17 + super_delta)
+    n, m = 700, 9000
+    X = r.uniform(-3, 3, size=(n, 3)).astype(np.float32)
+    Z = r.uniform(-3, 3, size=(m, 3)).astype(np.float32)
+    compare_eval(X, Z, semantic_features(r, n), semantic_features(r, m), SEM_BLOCKS, 0.15, 3.0,
+                 rand_pose(r, 0.05, 0.05), bf16=True, tuning=(0.5, super_delta), chunk_len=768)
+
+
+@pytest.mark.parametrize("n", [1, 5, 31, 33, 100])
+def test_trimmed_streams_ragged_groups(n):
+    """Groups of fewer than 32 queries: the lanes past the group's last query
+    take no part in the trim."""
+    r = rng(30 + n)
+    m = 3 * n + 7
+    X = r.uniform(-0.3, 0.3, (n, 3)).astype(np.float32)
+    Z = r.uniform(-0.3, 0.3, (m, 3)).astype(np.float32)
+    compare_eval(X, Z, semantic_features(r, n), semantic_features(r, m), SEM_BLOCKS, 0.1, 3.0,
+                 rand_pose(r, 0.05, 0.05), bf16=True, ndir=2, chunk_len=768)
+
+
+@pytest.mark.parametrize("lanes", [2, 4])
+def test_trimmed_streams_lanes_per_query(lanes):
+    """The trim with 2 or 4 lanes per query (each query's position held by
+    all of its lanes)."""
+    r = rng(50 + lanes)
+    n, m = 1500, 2500
+    X = r.uniform(-1, 1, size=(n, 3)).astype(np.float32)
+    Z = r.uniform(-1, 1, size=(m, 3)).astype(np.float32)
+    compare_eval(X, Z, semantic_features(r, n), semantic_features(r, m), SEM_BLOCKS, 0.1, 3.0,
+                 rand_pose(r, 0.05, 0.05), bf16=True, lanes=lanes, chunk_len=768)
+
+
+def test_trimmed_streams_street_f32():
+    """The trim on the float32 feature path (street subsample, RGB + 19
+    labels)."""
+    p = scenes.street_pair()
+    sel = rng(7).permutation(p.n)[:5000]
+    compare_eval(p.X[sel], p.Z[sel], p.FX[sel], p.FZ[sel], p.blocks, 0.3, 3.0, p.T_true, chunk_len=768)
+
+
+def test_trim_keeps_every_pair():
+    """The same pair with the box's streams (384-candidate items) and the
+    queries' streams (768): the same in-cutoff pair count exactly, fewer
+    distance tests, the same double sum up to float32 summation order."""
+    r = rng(40)
+    n, m = 4000, 4000
+    X = r.uniform(-1, 1, size=(n, 3)).astype(np.float32)
+    Z = (X + r.normal(0, 0.02, size=X.shape)).astype(np.float32)
+    FX, FZ = semantic_features(r, n), semantic_features(r, m)
+    T = rand_pose(r, 0.05, 0.05)
+    out = {}
+    for chunk_len in (384, 768):
+        with cvo.CVO(blocks=SEM_BLOCKS, ell=0.1, cutoff_mult=3.0) as h:
+            t = h.tuning()
+            h.apply_tuning(t["cell_factor"], t["super_delta"], chunk_len)
+            out[chunk_len] = h.evaluate(dev(X), dev(Z), T, bf16_dev(FX), bf16_dev(FZ))
+    box, trim = out[384], out[768]
+    assert trim["pairs"] == box["pairs"]
+    assert box["pairs"] <= trim["candidates"] < box["candidates"]
+    assert trim["F"] == pytest.approx(box["F"], rel=1e-6)
+    assert np.abs(trim["grad"] - box["grad"]).max() <= 1e-5 * np.abs(box["grad"]).max()
 
 
 def test_generic_blocks():
