@@ -230,30 +230,32 @@ def make_params(blocks=(), ell=0.1, ell_min=None, sigma=1.0, cutoff_mult=3.0, ma
 def _as_cloud(xyz, feat, keep):
     """Builds a Cloud from numpy arrays or torch tensors; keep holds references."""
     torch = _torch()
-    c = Cloud()
     if torch is not None and isinstance(xyz, torch.Tensor):
-        t = xyz.detach()
+        # (a batch marshals 2 clouds per pair: no tensor is copied or
+        # detached unless it has to be)
+        t = xyz.detach() if xyz.requires_grad else xyz
         if t.dtype != torch.float32 or t.dim() != 2 or t.shape[1] != 3:
             raise ValueError("xyz must be an (N, 3) float32 tensor")
-        t = t.contiguous()
+        if not t.is_contiguous():
+            t = t.contiguous()
         keep.append(t)
-        c.xyz = t.data_ptr() if t.numel() else None
-        c.n = t.shape[0]
-        c.on_device = 1 if t.is_cuda else 0
+        n = t.shape[0]
+        cuda = t.is_cuda
+        fptr, fdt = None, 0
         if feat is not None:
-            f = feat.detach()
-            if f.is_cuda != t.is_cuda:
+            f = feat.detach() if feat.requires_grad else feat
+            if f.is_cuda != cuda:
                 raise ValueError("xyz and features must live on the same device")
             if f.dtype == torch.bfloat16:
-                c.feat_dtype = 1
-            elif f.dtype == torch.float32:
-                c.feat_dtype = 0
-            else:
+                fdt = 1
+            elif f.dtype != torch.float32:
                 raise ValueError("features must be float32 or bfloat16")
-            f = f.contiguous()
+            if not f.is_contiguous():
+                f = f.contiguous()
             keep.append(f)
-            c.feat = f.data_ptr() if f.numel() else None
-        return c
+            fptr = f.data_ptr() if f.numel() else None
+        return Cloud(t.data_ptr() if n else None, n, fptr, fdt, 1 if cuda else 0)
+    c = Cloud()
     a = np.ascontiguousarray(np.asarray(xyz, dtype=np.float32).reshape(-1, 3))
     keep.append(a)
     c.xyz = a.ctypes.data if a.size else None

@@ -407,6 +407,14 @@ struct CopyJob {
     int bytes;
 };
 cudaError_t launch_copy_batch(const CopyJob* jobs, int count, cudaStream_t s);
+// a host-resident input pulled into device memory by the SMs (src: the
+// device-side address of page-locked, mapped host memory)
+struct PullJob {
+    const void* src;
+    void* dst;
+    long long bytes;
+};
+cudaError_t launch_pull_batch(const PullJob* jobs, int count, cudaStream_t s);
 
 // k_init_state of many pairs (cvo_finalize.cu)
 struct StateJob {

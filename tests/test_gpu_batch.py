@@ -98,6 +98,36 @@ def assert_bitwise_equal(a, b):
         assert ia[k]["F"] == ib[k]["F"] and ia[k]["pairs"] == ib[k]["pairs"] and ia[k]["iters"] == ib[k]["iters"], k
 
 
+def test_batch_from_page_locked_host_memory(monkeypatch):
+    """Host-resident inputs of a batch: page-locked ones (pulled into device
+    memory by the library's own kernel), some at offsets that are not 16-byte
+    aligned, and pageable ones (copied by the driver) give the bits of the
+    same batch from device memory."""
+    pairs, args = small_batch(n_pairs=5, seed=41)
+
+    def shifted(t):
+        # a view one row into a larger page-locked buffer
+        big = torch.empty((t.shape[0] + 1,) + tuple(t.shape[1:]), dtype=t.dtype).pin_memory()
+        big[1:] = t.cpu()
+        return big[1:]
+
+    host = []
+    for k, (X, Z, T, FX, FZ) in enumerate(args):
+        if k in (0, 2):
+            host.append((X.cpu().pin_memory(), Z.cpu().pin_memory(), T, FX.cpu().pin_memory(), FZ.cpu().pin_memory()))
+        elif k in (1, 4):
+            host.append((shifted(X), shifted(Z), T, shifted(FX), shifted(FZ)))
+        else:
+            host.append((X.cpu(), Z.cpu(), T, FX.cpu(), FZ.cpu()))
+    assert host[1][0].data_ptr() % 16 != 0 and host[1][3].data_ptr() % 16 != 0
+    with cvo.CVO(blocks=pairs[0].blocks, **KW) as h:
+        got = h.register_batch(host)
+        assert_bitwise_equal(got, h.register_batch(args))
+        with monkeypatch.context() as m:
+            m.setenv("CVO_BATCH_SETUP", "pairs")
+            assert_bitwise_equal(got, h.register_batch(host))
+
+
 def batched_and_pairwise(h, args, monkeypatch):
     """A batch set up by the batched stages (one launch per stage for all
     pairs), and set up pair by pair (CVO_BATCH_SETUP=pairs)."""
