@@ -190,15 +190,22 @@ __device__ void resplit_grid(PairDesc* pairs, int npairs, int nblocks, const uns
     s_w[t] = w;
     s_a[t] = a;
     __syncthreads();
-    if (t == 0) {
+    if (t < 32) {   // integer sums: any order gives the same totals
         unsigned long long tw = 0;
         unsigned ta = 0;
-        for (int i = 0; i < kFinalizeThreads; ++i) {
+        for (int i = t; i < kFinalizeThreads; i += 32) {
             tw += s_w[i];
             ta += s_a[i];
         }
-        tot_w = tw > 0 ? tw : 1;
-        tot_a = ta;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tw += __shfl_xor_sync(0xffffffffu, tw, o);
+            ta += __shfl_xor_sync(0xffffffffu, ta, o);
+        }
+        if (t == 0) {
+            tot_w = tw > 0 ? tw : 1;
+            tot_a = ta;
+        }
     }
     __syncthreads();
     const unsigned long long W = tot_w;
@@ -257,31 +264,43 @@ k_finalize_batch(PairDesc* __restrict__ pairs, int npairs, const float2* __restr
     if (!was_done) {
         for (int i = threadIdx.x; i < kWords; i += kFinalizeThreads)
             sbuf[i] = reinterpret_cast<const unsigned long long*>(st)[i];
-        if (threadIdx.x < kStatN) {
-            const float2* row = ps + (size_t)threadIdx.x * cap;
+        // statistic k by warp k % warps: lane l adds the pair's block
+        // partials l, l + 32, ... (coalesced, all of a lane's loads issued
+        // before its adds), then a butterfly over the lanes; a fixed order
+        constexpr int kWarps = kFinalizeThreads / 32;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int k = warp; k < kStatN; k += kWarps) {
+            const float2* row = ps + (size_t)k * cap;
             float hi = 0.0f, lo = 0.0f;
-            int b = P.b0;
-            for (; b + 8 <= P.b1; b += 8) {
-                float2 v[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) v[k] = row[b + k];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) df_add(hi, lo, v[k].x, v[k].y);
+            int b = P.b0 + lane;
+            for (; b + 96 < P.b1; b += 128) {
+                const float2 v0 = row[b], v1 = row[b + 32], v2 = row[b + 64], v3 = row[b + 96];
+                df_add(hi, lo, v0.x, v0.y);
+                df_add(hi, lo, v1.x, v1.y);
+                df_add(hi, lo, v2.x, v2.y);
+                df_add(hi, lo, v3.x, v3.y);
             }
-            for (; b < P.b1; ++b) df_add(hi, lo, row[b].x, row[b].y);
-            S[threadIdx.x] = (double)hi + (double)lo;
-            Shi[threadIdx.x] = hi;
-            Slo[threadIdx.x] = lo;
-        } else if (threadIdx.x == kStatN || threadIdx.x == kStatN + 1) {
-            const int c = threadIdx.x - kStatN;
-            const unsigned long long* row = pc + (size_t)c * cap;
-            unsigned long long t[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // eight loads in flight
-            int b = P.b0;
-            for (; b + 8 <= P.b1; b += 8)
+            for (; b < P.b1; b += 32) df_add(hi, lo, row[b].x, row[b].y);
 #pragma unroll
-                for (int k = 0; k < 8; ++k) t[k] += row[b + k];
-            for (; b < P.b1; ++b) t[0] += row[b];
-            cs[c] = ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
+            for (int o = 16; o > 0; o >>= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+                df_add(hi, lo, oh, ol);
+            }
+            if (lane == 0) {
+                S[k] = (double)hi + (double)lo;
+                Shi[k] = hi;
+                Slo[k] = lo;
+            }
+        }
+        if (warp == kWarps - 1) {   // pair and candidate counts (integer sums: any order)
+            for (int c = 0; c < 2; ++c) {
+                const unsigned long long* row = pc + (size_t)c * cap;
+                unsigned long long t = 0;
+                for (int b = P.b0 + lane; b < P.b1; b += 32) t += row[b];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                if (lane == 0) cs[c] = t;
+            }
         }
         __syncthreads();
         if (threadIdx.x < 32)

@@ -48,7 +48,7 @@ constexpr int kChunkLen = 128;   // default candidates per planned work item
 constexpr int kChunks = 8;       // chunks per group of the uniform items
 constexpr int kChunkMin = 64;    // shortest run-time chunk of the uniform items
 constexpr int kTrimChunkLen = 768;   // planned items at least this long trim the stream rows by each query
-constexpr int kFinalizeThreads = 64;   // threads of a batched step block
+constexpr int kFinalizeThreads = 256;  // threads of a batched step block
 constexpr int kStepThreads = 384;      // threads of the single-pair step block (its registers allow 12 warps)
 constexpr int kGroupBlocks = 8;    // sweep blocks per reduction group (the group's last block sums them)
 constexpr int kMaxGroups = 256;    // reduction groups per sweep launch (so at most kGroupBlocks * kMaxGroups sweep blocks)
