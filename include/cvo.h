@@ -291,12 +291,12 @@ int cvo_get_trace(cvo_handle h, double* out, int cap);
 
 /* Tuning of the neighbour sweep (performance only; results do not depend on
  * it beyond rounding): grid cell edge = cell_factor * cutoff radius
- * (0.25..4), query groups drawn from Morton super-cells about
+ * (0.25..4), query groups drawn from octree super-cells about
  * 2^super_delta cutoff radii wide (-2..6).  Defaults 0.5 and 2. */
 cvo_status cvo_set_tuning(cvo_handle h, double cell_factor, int super_delta);
 
 /* Tuning of the neighbour sweep: grid cell edge (cell_factor x cutoff
- * radius), query-group extent (Morton super-cells about 2^super_delta
+ * radius), query-group extent (octree super-cells about 2^super_delta
  * cutoff radii wide) and the work split (each query group's candidate
  * stream is cut into work items of about chunk_len candidates, so up to
  * length / chunk_len warps serve one query group: evaluations, batches and

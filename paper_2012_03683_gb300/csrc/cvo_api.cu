@@ -114,10 +114,10 @@ float decode_orderable(unsigned u)
     return f;
 }
 
-// Device resources of one prepared pair: grid levels of Z, Morton-ordered
+// Device resources of one prepared pair: grid levels of Z, Hilbert-ordered
 // queries of X and their groups, the iteration state.
 struct PairRes {
-    DevBuf xrec, morton, levels_dev, state;
+    DevBuf xrec, hkeys, levels_dev, state;
     DevBuf in_xyz[2], in_feat[2];   // a batch's device copies of host-resident inputs (X, Z)
     DevBuf zrec[kMaxLevels], cell_start[kMaxLevels], groups[kMaxLevels], items[kMaxLevels];
     int n = 0, m = 0, nlevels = 0;
@@ -129,7 +129,7 @@ struct PairRes {
 
     void free_all()
     {
-        DevBuf* bufs[] = {&xrec, &morton, &levels_dev, &state, &in_xyz[0], &in_xyz[1], &in_feat[0], &in_feat[1]};
+        DevBuf* bufs[] = {&xrec, &hkeys, &levels_dev, &state, &in_xyz[0], &in_xyz[1], &in_feat[0], &in_feat[1]};
         for (DevBuf* b : bufs) release(*b);
         for (int k = 0; k < kMaxLevels; ++k) {
             release(zrec[k]);
@@ -186,7 +186,7 @@ struct cvo_handle_s {
     double kappa = 1.0;
     int sweep_blocks = 1;
     // tuning: grid cell edge = cell_factor * cutoff radius; query groups live in
-    // Morton super-cells about 2^super_delta cutoff radii wide
+    // octree super-cells about 2^super_delta cutoff radii wide
     double cell_factor = 0.5;
     int super_delta = 2;
     // work split: each query group's candidate stream is split into chunks
@@ -478,7 +478,7 @@ void set_levels(cvo_handle h, PairRes& P, const float zmin[3], const float zmax[
     }
 }
 
-// Morton super-cells of edge about 2^super_delta times the level's cutoff
+// octree super-cells of edge about 2^super_delta times the level's cutoff
 // radius hold the query groups (the dense sum: one super-cell)
 int group_shift(cvo_handle h, const LevelHost& L, double cell0)
 {
@@ -514,7 +514,7 @@ cvo_status prepare_bbox(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_
     return CVO_OK;
 }
 
-// Phase 2: from the boxes (hm), the grid levels of Z, the Morton-ordered
+// Phase 2: from the boxes (hm), the grid levels of Z, the Hilbert-ordered
 // queries of X and their groups (group counts into dev + 16 + level).
 cvo_status prepare_build(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud* Z, double ell_hi,
                          double ell_lo, const Staged& sg, const unsigned* hm, unsigned* dev, bool fan_out)
@@ -590,21 +590,21 @@ cvo_status prepare_build(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo
         }
     }
 
-    // queries: Morton order of X in its own frame
+    // queries: Hilbert order of X in its own frame
     use_lane(0);
     double ext = 0.0;
     for (int a = 0; a < 3; ++a) ext = std::max(ext, (double)xmax[a] - xmin[a]);
     const double cell0 = std::max(ext / 1024.0, 1e-6);
     CVO_CUDA(ensure(P.xrec, (size_t)std::max(n, 1) * rs * sizeof(float4)));
-    CVO_CUDA(ensure(P.morton, (size_t)std::max(n, 1) * 4));
-    CVO_CUDA(launch_morton_keys(xyz_x, n, xmin[0], xmin[1], xmin[2], (float)(1.0 / cell0), (unsigned*)h->keys.p,
+    CVO_CUDA(ensure(P.hkeys, (size_t)std::max(n, 1) * 4));
+    CVO_CUDA(launch_hilbert_keys(xyz_x, n, xmin[0], xmin[1], xmin[2], (float)(1.0 / cell0), (unsigned*)h->keys.p,
                                 (unsigned*)h->vals.p, h->s));
     {
         unsigned *ks, *vs;
         CVO_TRY(sort_pairs(h, n, 30, &ks, &vs));
         CVO_CUDA(launch_pack(xyz_x, feat_x, X->feat_dtype == CVO_BF16, D, vs, n, (float4*)P.xrec.p, rs, h->rec_bf16,
                              h->s));
-        CVO_CUDA(cudaMemcpyAsync(P.morton.p, ks, (size_t)n * 4, cudaMemcpyDeviceToDevice, h->s));
+        CVO_CUDA(cudaMemcpyAsync(P.hkeys.p, ks, (size_t)n * 4, cudaMemcpyDeviceToDevice, h->s));
     }
     // query groups per level
     CVO_CUDA(ensure(h->flags, (size_t)std::max(n, 1) * 4));
@@ -614,10 +614,10 @@ cvo_status prepare_build(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo
         const int sh = group_shift(h, L, cell0);
         L.shift = sh;
         CVO_CUDA(ensure(P.groups[k], (size_t)std::max(n, 1) * sizeof(int2)));
-        CVO_CUDA(launch_group_flags((const unsigned*)P.morton.p, n, sh, 32 / h->query_lanes, (unsigned*)h->flags.p,
+        CVO_CUDA(launch_group_flags((const unsigned*)P.hkeys.p, n, sh, 32 / h->query_lanes, (unsigned*)h->flags.p,
                                     h->s));
         CVO_CUDA(exclusive_scan_u32((const unsigned*)h->flags.p, (unsigned*)h->gidx.p, n, dev + 16 + k, h->s));
-        CVO_CUDA(launch_group_write((const unsigned*)P.morton.p, (const unsigned*)h->flags.p,
+        CVO_CUDA(launch_group_write((const unsigned*)P.hkeys.p, (const unsigned*)h->flags.p,
                                     (const unsigned*)h->gidx.p, n, sh, 32 / h->query_lanes, (int2*)P.groups[k].p,
                                     h->s));
     }
@@ -665,7 +665,7 @@ cvo_status prepare_finish(cvo_handle h, PairRes& P, const unsigned* hm)
     return CVO_OK;
 }
 
-// Builds the grid levels of Z, the Morton-ordered queries of X and their groups
+// Builds the grid levels of Z, the Hilbert-ordered queries of X and their groups
 // for lengthscales in [ell_lo, ell_hi].  Uses the handle's shared scratch.
 // The work items are planned by init_state, once the start pose is known.
 cvo_status prepare(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud* Z, double ell_hi, double ell_lo)
@@ -687,7 +687,7 @@ cvo_status prepare(cvo_handle h, PairRes& P, const cvo_cloud* X, const cvo_cloud
 // length at the level's design cutoff radius, groups sorted longest first,
 // each split into ceil(length / chunk_len) chunks (at most kMaxChunks) --
 // exact for an evaluation, and good for a batch of pairs whose poses stay
-// near their starts.  Otherwise uniform: kChunks per group in Morton order,
+// near their starts.  Otherwise uniform: kChunks per group in Hilbert order,
 // cut at run time: the first sweep of each grid level of a registration
 // with a cutoff, whose later sweeps take the items k_layout lays out from
 // the stream lengths the previous sweep recorded.
@@ -955,7 +955,7 @@ cvo_status prepare_batch(cvo_handle h, const std::vector<int>& live, const cvo_c
         }
     }
 
-    // phase 2: grid levels of Z, the Morton order of X, query groups
+    // phase 2: grid levels of Z, the Hilbert order of X, query groups
     std::vector<double> cell0(nl);
     std::vector<std::array<float, 3>> xlo(nl);
     int nlev = 0;
@@ -970,7 +970,7 @@ cvo_status prepare_batch(cvo_handle h, const std::vector<int>& live, const cvo_c
         cell0[i] = std::max(ext / 1024.0, 1e-6);
         xlo[i] = {xmin[0], xmin[1], xmin[2]};
         CVO_CUDA(ensure(P.xrec, (size_t)std::max(P.n, 1) * rs * sizeof(float4)));
-        CVO_CUDA(ensure(P.morton, (size_t)std::max(P.n, 1) * 4));
+        CVO_CUDA(ensure(P.hkeys, (size_t)std::max(P.n, 1) * 4));
         for (int k = 0; k < P.nlevels; ++k) {
             LevelHost& L = P.lv[k];
             L.shift = group_shift(h, L, cell0[i]);
@@ -1036,14 +1036,14 @@ cvo_status prepare_batch(cvo_handle h, const std::vector<int>& live, const cvo_c
         }
         CVO_CUDA(launch_pack_batch(pj.data(), cnt, D, rs, h->rec_bf16, h->s));
     }
-    {   // queries: Morton order of X in its own frame
+    {   // queries: Hilbert order of X in its own frame
         std::vector<int> all(nl);
         for (int i = 0; i < nl; ++i) all[i] = i;
         std::vector<KeyJob> kj(nl);
         for (int i = 0; i < nl; ++i)
             kj[i] = KeyJob{X[live[i]].xyz, seg[i].keys, seg[i].vals, xlo[i][0], xlo[i][1], xlo[i][2],
                            (float)(1.0 / cell0[i]), (float)(1.0 / cell0[i]), h->pr[i].n, 0, 0, 0};
-        CVO_CUDA(launch_morton_keys_batch(kj.data(), nl, h->s));
+        CVO_CUDA(launch_hilbert_keys_batch(kj.data(), nl, h->s));
         const std::vector<SortJob> sj = sort_jobs(all, [&](int i) { return h->pr[i].n; });
         int alt = 0;
         CVO_CUDA(radix_sort_batch(sj.data(), nl, 30, &alt, h->s));
@@ -1051,7 +1051,7 @@ cvo_status prepare_batch(cvo_handle h, const std::vector<int>& live, const cvo_c
         for (int i = 0; i < nl; ++i) {
             PairRes& P = h->pr[i];
             const cvo_cloud& x = X[live[i]];
-            pj[i] = PackJob{x.xyz, x.feat, sorted_vals(i, alt), sorted_keys(i, alt), (unsigned*)P.morton.p,
+            pj[i] = PackJob{x.xyz, x.feat, sorted_vals(i, alt), sorted_keys(i, alt), (unsigned*)P.hkeys.p,
                             (float4*)P.xrec.p, P.n, x.feat_dtype == CVO_BF16};
         }
         CVO_CUDA(launch_pack_batch(pj.data(), nl, D, rs, h->rec_bf16, h->s));
@@ -1064,7 +1064,7 @@ cvo_status prepare_batch(cvo_handle h, const std::vector<int>& live, const cvo_c
         for (int j = 0; j < cnt; ++j) {
             const int i = idx[j];
             PairRes& P = h->pr[i];
-            gj[j] = GroupJob{(const unsigned*)P.morton.p, seg[i].flags, seg[i].gidx, (int2*)P.groups[k].p, P.n,
+            gj[j] = GroupJob{(const unsigned*)P.hkeys.p, seg[i].flags, seg[i].gidx, (int2*)P.groups[k].p, P.n,
                              P.lv[k].shift, 32 / h->query_lanes};
             sc[j] = ScanJob{seg[i].flags, seg[i].gidx, slot(i) + 16 + k, P.n};
         }

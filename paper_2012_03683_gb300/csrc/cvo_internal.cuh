@@ -8,10 +8,10 @@
 //                 zero padded to 16 bytes)
 //   cell_start    per level, ncells + 1 ints: records of cell c are
 //                 [cell_start[c], cell_start[c+1])
-//   xrec          N query records in the same layout, in Morton order of X's
+//   xrec          N query records in the same layout, in Hilbert order of X's
 //                 own frame (spatially compact runs)
 //   groups        per level, (first query, count <= 32) of each query group:
-//                 consecutive queries inside one Morton super-cell whose edge
+//                 consecutive queries inside one octree super-cell whose edge
 //                 does not exceed that level's cell edge
 //   items         per level, the work items of a sweep: (first query, count,
 //                 chunk k | chunks n << 16, group index) -- chunk k of n of one
@@ -20,7 +20,7 @@
 //                 pose of the call (about chunk_len candidates per item),
 //                 groups with the longest streams first.  A registration with
 //                 a cutoff, whose pose moves: the first sweep of a level takes
-//                 uniform items (8 chunks per group in Morton order, cut at
+//                 uniform items (8 chunks per group in Hilbert order, cut at
 //                 run time to min(8, length / 64)); every sweep records each
 //                 group's stream length and k_layout lays out the next sweep's
 //                 items from them (n = ceil(length / chunk_len), group order)
@@ -269,7 +269,7 @@ cudaError_t launch_write_items(const LevelDesc* levels, int level, const unsigne
                                const unsigned* offsets, int ngroups, int4* items, cudaStream_t s);
 
 // ---- batched setup: one launch for the pairs of a batch ---------------------
-// The per-pair stages of the set-up (boxes, grids, Morton order, groups,
+// The per-pair stages of the set-up (boxes, grids, Hilbert order, groups,
 // work items) for many pairs at once: each launch takes up to
 // kJobsPerLaunch pairs' jobs by value as a kernel parameter, blockIdx.y
 // selects the job, and the kernels run the single-pair kernels' bodies, so
@@ -300,8 +300,8 @@ struct BoxJob {
     long long* zstats;
 };
 
-// grid-cell keys (nx, ny, nz, inv = 1 / cell edge) or Morton keys (inv = 1 /
-// Morton cell) of one cloud, with the point indices as values
+// grid-cell keys (nx, ny, nz, inv = 1 / cell edge) or Hilbert keys (inv = 1 /
+// the edge of the curve's cells) of one cloud, with the point indices as values
 struct KeyJob {
     const float* xyz;
     unsigned* keys;
@@ -348,10 +348,10 @@ struct ScanJob {
     int n;
 };
 
-// query groups of one level from the Morton-sorted keys: flags (first query
+// query groups of one level from the Hilbert-sorted keys: flags (first query
 // of each group), then (with gidx, the flags' scan) the group table
 struct GroupJob {
-    const unsigned* morton;
+    const unsigned* hkeys;
     unsigned* flags;
     const unsigned* gidx;
     int2* groups;
@@ -361,7 +361,7 @@ struct GroupJob {
 size_t sort_batch_temp_words(int n);
 cudaError_t launch_boxes_batch(const BoxJob* jobs, int count, cudaStream_t s);   // zeroes its outputs first
 cudaError_t launch_cell_keys_batch(const KeyJob* jobs, int count, cudaStream_t s);
-cudaError_t launch_morton_keys_batch(const KeyJob* jobs, int count, cudaStream_t s);
+cudaError_t launch_hilbert_keys_batch(const KeyJob* jobs, int count, cudaStream_t s);
 cudaError_t radix_sort_batch(const SortJob* jobs, int count, int nbits, int* result_in_alt, cudaStream_t s);
 cudaError_t launch_cell_start_batch(const CellStartJob* jobs, int count, cudaStream_t s);
 cudaError_t launch_pack_batch(const PackJob* jobs, int count, int D, int rs, int rec_bf16, cudaStream_t s);
@@ -432,7 +432,7 @@ cudaError_t launch_zstats(const float* xyz, int n, long long* out, cudaStream_t 
 void decode_zstats(const long long* raw, int n, double out5[5]);
 cudaError_t launch_cell_keys(const float* xyz, int n, float ox, float oy, float oz, float inv_h, float inv_hx, int nx,
                              int ny, int nz, unsigned* keys, unsigned* vals, cudaStream_t s);
-cudaError_t launch_morton_keys(const float* xyz, int n, float ox, float oy, float oz, float inv_cell,
+cudaError_t launch_hilbert_keys(const float* xyz, int n, float ox, float oy, float oz, float inv_cell,
                                unsigned* keys, unsigned* vals, cudaStream_t s);
 size_t radix_sort_temp_bytes(int n);
 cudaError_t radix_sort_pairs(unsigned* keys, unsigned* vals, unsigned* keys_alt, unsigned* vals_alt, int n,
@@ -440,12 +440,12 @@ cudaError_t radix_sort_pairs(unsigned* keys, unsigned* vals, unsigned* keys_alt,
 cudaError_t launch_cell_start(const unsigned* sorted_keys, int n, int ncells, int* cell_start, cudaStream_t s);
 cudaError_t launch_pack(const float* xyz, const void* feat, int feat_bf16, int D, const unsigned* order, int n,
                         float4* rec, int rs, int rec_bf16, cudaStream_t s);
-// query groups: up to gsize consecutive Morton-sorted queries of one super-cell
-// (2^shift Morton units) each
-cudaError_t launch_group_flags(const unsigned* sorted_morton, int n, int shift, int gsize, unsigned* flags,
+// query groups: up to gsize consecutive Hilbert-sorted queries of one super-cell
+// (2^shift key units: an octree cell) each
+cudaError_t launch_group_flags(const unsigned* sorted_keys, int n, int shift, int gsize, unsigned* flags,
                                cudaStream_t s);
 cudaError_t exclusive_scan_u32(const unsigned* in, unsigned* out, int n, unsigned* total, cudaStream_t s);
-cudaError_t launch_group_write(const unsigned* sorted_morton, const unsigned* flags, const unsigned* gidx, int n,
+cudaError_t launch_group_write(const unsigned* sorted_keys, const unsigned* flags, const unsigned* gidx, int n,
                                int shift, int gsize, int2* groups, cudaStream_t s);
 
 }  // namespace cvo

@@ -1,5 +1,5 @@
 // Setup kernels, run once per cloud pair: bounding boxes, the uniform grid of
-// Z (a stable counting sort by cell key), the Morton order of X and its query
+// Z (a stable counting sort by cell key), the Hilbert order of X and its query
 // groups.  The paper notes that the double sum is sparse (Sec. III-B); the
 // grid is how the sweep visits only the pairs near each query.
 #include <cmath>
@@ -131,8 +131,47 @@ __device__ __forceinline__ unsigned spread10(unsigned v)
     return v;
 }
 
-__device__ __forceinline__ void morton_keys_body(const float* __restrict__ xyz, int n, float ox, float oy, float oz,
-                                                 float inv_cell, unsigned* keys, unsigned* vals, int j)
+// The 30-bit index along the 3-D Hilbert curve of the cell (x, y, z) of a
+// 1024^3 grid, by Skilling's transform of the coordinates to the curve's
+// "transposed" index (J. Skilling, Programming the Hilbert curve, AIP Conf.
+// Proc. 707, 2004): for each bit from the top, invert or exchange the lower
+// bits, then Gray-encode; the index interleaves the transposed words' bits,
+// x's bit b at 3b + 2.  Consecutive indices are neighbouring cells, and the
+// cells of an octree cell of edge 2^k are 2^3k consecutive indices (the
+// key's top bits name the octree cell, as with Morton keys).
+__device__ __forceinline__ unsigned hilbert_index10(unsigned x, unsigned y, unsigned z)
+{
+    unsigned X[3] = {x, y, z};
+    for (unsigned Q = 1u << 9; Q > 1u; Q >>= 1) {
+        const unsigned P = Q - 1u;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (X[i] & Q) {
+                X[0] ^= P;   // invert
+            } else {         // exchange
+                const unsigned t = (X[0] ^ X[i]) & P;
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    X[1] ^= X[0];   // Gray encode
+    X[2] ^= X[1];
+    unsigned t = 0u;
+    for (unsigned Q = 1u << 9; Q > 1u; Q >>= 1)
+        if (X[2] & Q) t ^= Q - 1u;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) X[i] ^= t;
+    return (spread10(X[0]) << 2) | (spread10(X[1]) << 1) | spread10(X[2]);
+}
+
+// The queries' order: the Hilbert index of each point's cell (edge 1 /
+// inv_cell from the origin o, 1024 cells a side), with the point indices as
+// values.  Chunks of 32 consecutive queries in Hilbert order are more compact
+// than in Hilbert order, which has jumps across octree cells (on the cube
+// scenes about 5 % fewer candidates streamed and evaluated).
+__device__ __forceinline__ void hilbert_keys_body(const float* __restrict__ xyz, int n, float ox, float oy, float oz,
+                                                  float inv_cell, unsigned* keys, unsigned* vals, int j)
 {
     if (j >= n) return;
     unsigned q[3];
@@ -141,14 +180,14 @@ __device__ __forceinline__ void morton_keys_body(const float* __restrict__ xyz, 
         int c = (int)floorf((xyz[3 * (size_t)j + a] - o[a]) * inv_cell);
         q[a] = (unsigned)min(max(c, 0), 1023);
     }
-    keys[j] = spread10(q[0]) | (spread10(q[1]) << 1) | (spread10(q[2]) << 2);
+    keys[j] = hilbert_index10(q[0], q[1], q[2]);
     vals[j] = (unsigned)j;
 }
 
-__global__ void k_morton_keys(const float* __restrict__ xyz, int n, float ox, float oy, float oz, float inv_cell,
+__global__ void k_hilbert_keys(const float* __restrict__ xyz, int n, float ox, float oy, float oz, float inv_cell,
                               unsigned* keys, unsigned* vals)
 {
-    morton_keys_body(xyz, n, ox, oy, oz, inv_cell, keys, vals, blockIdx.x * blockDim.x + threadIdx.x);
+    hilbert_keys_body(xyz, n, ox, oy, oz, inv_cell, keys, vals, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---- stable LSD radix sort, 8-bit digits ------------------------------------
@@ -426,36 +465,36 @@ __device__ __forceinline__ int lower_bound_u32(const unsigned* a, int n, unsigne
     return lo;
 }
 
-// groups of up to gsize consecutive queries of one Morton super-cell
-__device__ __forceinline__ void group_flags_body(const unsigned* __restrict__ morton, int n, int shift, int gsize,
+// groups of up to gsize consecutive queries of one octree super-cell
+__device__ __forceinline__ void group_flags_body(const unsigned* __restrict__ hkeys, int n, int shift, int gsize,
                                                  unsigned* flags, int i)
 {
     if (i >= n) return;
-    const unsigned long long seg = (unsigned long long)(morton[i] >> shift);
-    const int start = lower_bound_u32(morton, n, seg << shift);
+    const unsigned long long seg = (unsigned long long)(hkeys[i] >> shift);
+    const int start = lower_bound_u32(hkeys, n, seg << shift);
     flags[i] = ((i - start) % gsize == 0) ? 1u : 0u;
 }
 
-__global__ void k_group_flags(const unsigned* __restrict__ morton, int n, int shift, int gsize, unsigned* flags)
+__global__ void k_group_flags(const unsigned* __restrict__ hkeys, int n, int shift, int gsize, unsigned* flags)
 {
-    group_flags_body(morton, n, shift, gsize, flags, blockIdx.x * blockDim.x + threadIdx.x);
+    group_flags_body(hkeys, n, shift, gsize, flags, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-__device__ __forceinline__ void group_write_body(const unsigned* __restrict__ morton,
+__device__ __forceinline__ void group_write_body(const unsigned* __restrict__ hkeys,
                                                  const unsigned* __restrict__ flags,
                                                  const unsigned* __restrict__ gidx, int n, int shift, int gsize,
                                                  int2* groups, int i)
 {
     if (i >= n || !flags[i]) return;
-    const unsigned long long seg = (unsigned long long)(morton[i] >> shift);
-    const int end = lower_bound_u32(morton, n, (seg + 1ull) << shift);
+    const unsigned long long seg = (unsigned long long)(hkeys[i] >> shift);
+    const int end = lower_bound_u32(hkeys, n, (seg + 1ull) << shift);
     groups[gidx[i]] = make_int2(i, min(gsize, end - i));
 }
 
-__global__ void k_group_write(const unsigned* __restrict__ morton, const unsigned* __restrict__ flags,
+__global__ void k_group_write(const unsigned* __restrict__ hkeys, const unsigned* __restrict__ flags,
                               const unsigned* __restrict__ gidx, int n, int shift, int gsize, int2* groups)
 {
-    group_write_body(morton, flags, gidx, n, shift, gsize, groups, blockIdx.x * blockDim.x + threadIdx.x);
+    group_write_body(hkeys, flags, gidx, n, shift, gsize, groups, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Deterministic sum of n floats: per-thread double-float partials in a fixed
@@ -625,10 +664,10 @@ __global__ void k_cell_keys_b(JobList<KeyJob> J)
                    blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-__global__ void k_morton_keys_b(JobList<KeyJob> J)
+__global__ void k_hilbert_keys_b(JobList<KeyJob> J)
 {
     const KeyJob& k = J.j[blockIdx.y];
-    morton_keys_body(k.xyz, k.n, k.ox, k.oy, k.oz, k.inv, k.keys, k.vals, blockIdx.x * blockDim.x + threadIdx.x);
+    hilbert_keys_body(k.xyz, k.n, k.ox, k.oy, k.oz, k.inv, k.keys, k.vals, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 __device__ __forceinline__ int sort_tiles(int n) { return (n + kSortTile - 1) / kSortTile; }
@@ -683,7 +722,7 @@ __global__ void k_scan_b(JobList<ScanJob> J)
 __global__ void k_group_flags_b(JobList<GroupJob> J)
 {
     const GroupJob& q = J.j[blockIdx.y];
-    group_flags_body(q.morton, q.n, q.shift, q.gsize, q.flags, blockIdx.x * blockDim.x + threadIdx.x);
+    group_flags_body(q.hkeys, q.n, q.shift, q.gsize, q.flags, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 __global__ void k_copy_b(JobList<CopyJob> J)
@@ -721,7 +760,7 @@ __global__ void k_pull_b(JobList<PullJob> J)
 __global__ void k_group_write_b(JobList<GroupJob> J)
 {
     const GroupJob& q = J.j[blockIdx.y];
-    group_write_body(q.morton, q.flags, q.gidx, q.n, q.shift, q.gsize, q.groups,
+    group_write_body(q.hkeys, q.flags, q.gidx, q.n, q.shift, q.gsize, q.groups,
                      blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -784,12 +823,12 @@ cudaError_t launch_cell_keys(const float* xyz, int n, float ox, float oy, float 
     return cudaGetLastError();
 }
 
-cudaError_t launch_morton_keys(const float* xyz, int n, float ox, float oy, float oz, float inv_cell,
+cudaError_t launch_hilbert_keys(const float* xyz, int n, float ox, float oy, float oz, float inv_cell,
                                unsigned* keys, unsigned* vals, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
-    k_morton_keys<<<blocks_for(n, 256), 256, 0, s>>>(xyz, n, ox, oy, oz, inv_cell, keys, vals);
+    k_hilbert_keys<<<blocks_for(n, 256), 256, 0, s>>>(xyz, n, ox, oy, oz, inv_cell, keys, vals);
     return cudaGetLastError();
 }
 
@@ -852,12 +891,12 @@ cudaError_t launch_pack(const float* xyz, const void* feat, int feat_bf16, int D
     return cudaGetLastError();
 }
 
-cudaError_t launch_group_flags(const unsigned* sorted_morton, int n, int shift, int gsize, unsigned* flags,
+cudaError_t launch_group_flags(const unsigned* sorted_keys, int n, int shift, int gsize, unsigned* flags,
                                cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
-    k_group_flags<<<blocks_for(n, 256), 256, 0, s>>>(sorted_morton, n, shift, gsize, flags);
+    k_group_flags<<<blocks_for(n, 256), 256, 0, s>>>(sorted_keys, n, shift, gsize, flags);
     return cudaGetLastError();
 }
 
@@ -868,12 +907,12 @@ cudaError_t exclusive_scan_u32(const unsigned* in, unsigned* out, int n, unsigne
     return cudaGetLastError();
 }
 
-cudaError_t launch_group_write(const unsigned* sorted_morton, const unsigned* flags, const unsigned* gidx, int n,
+cudaError_t launch_group_write(const unsigned* sorted_keys, const unsigned* flags, const unsigned* gidx, int n,
                                int shift, int gsize, int2* groups, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
-    k_group_write<<<blocks_for(n, 256), 256, 0, s>>>(sorted_morton, flags, gidx, n, shift, gsize, groups);
+    k_group_write<<<blocks_for(n, 256), 256, 0, s>>>(sorted_keys, flags, gidx, n, shift, gsize, groups);
     return cudaGetLastError();
 }
 
@@ -935,13 +974,13 @@ cudaError_t launch_cell_keys_batch(const KeyJob* jobs, int count, cudaStream_t s
     });
 }
 
-cudaError_t launch_morton_keys_batch(const KeyJob* jobs, int count, cudaStream_t s)
+cudaError_t launch_hilbert_keys_batch(const KeyJob* jobs, int count, cudaStream_t s)
 {
     return each_chunk(jobs, count, [&](const JobList<KeyJob>& L) {
         int nmax = 1;
         for (int i = 0; i < L.count; ++i) nmax = max(nmax, L.j[i].n);
         g_launch_count.fetch_add(1, std::memory_order_relaxed);
-        k_morton_keys_b<<<dim3(blocks_for(nmax, 256), L.count), 256, 0, s>>>(L);
+        k_hilbert_keys_b<<<dim3(blocks_for(nmax, 256), L.count), 256, 0, s>>>(L);
         return cudaGetLastError();
     });
 }

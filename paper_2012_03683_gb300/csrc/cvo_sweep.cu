@@ -4,12 +4,13 @@
 //
 // evaluated in Z's frame, |x_i - T z_j| = |x'_i - z_j| with x'_i = T^-1 x_i.
 //
-// Work decomposition.  A warp owns one query group: up to 32 queries that lie
-// in one Morton super-cell of X (so they stay spatially compact under any
-// rigid motion), one query per lane.  The group's candidate stream is every Z
-// point in the grid cells that overlap the group's bounding box in Z's frame,
-// grown by the cutoff radius; since the grid sorts Z by cell with x fastest,
-// the stream is a short list of contiguous runs (one per (y, z) cell row).
+// Work decomposition.  A warp owns one query group: up to 32 queries,
+// consecutive in Hilbert order, that lie in one octree super-cell of X (so
+// they stay spatially compact under any rigid motion), one query per lane.
+// The group's candidate stream is every Z point in the grid cells that
+// overlap the group's bounding box in Z's frame, grown by the cutoff radius;
+// since the grid sorts Z by cell with x fastest, the stream is a short list
+// of contiguous runs (one per (y, z) cell row).
 // A group's stream is split into chunks, each its own work item (see the
 // item layouts in cvo_internal.cuh).
 //
@@ -394,7 +395,7 @@ __device__ __forceinline__ void group_cost_body(const LevelDesc* __restrict__ le
                                                 unsigned* keys, unsigned* vals, unsigned* nch, int g, int lane)
 {
     if (g >= ngroups) return;   // warp-uniform
-    if (chunk_len <= 0) {       // uniform items: Morton order, kChunks each
+    if (chunk_len <= 0) {       // uniform items: Hilbert order, kChunks each
         if (lane == 0) {
             keys[g] = (unsigned)g;
             vals[g] = (unsigned)g;

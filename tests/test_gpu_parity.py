@@ -142,7 +142,7 @@ def test_semantic_bf16_far_from_origin():
 
 @pytest.mark.parametrize("super_delta", [2, 4, 6])
 def test_semantic_bf16_sparse_queries_wide_groups(super_delta):
-    """Sparse queries over a dense cloud with Morton super-cells of 2^k
+    """Sparse queries over a dense cloud with octree super-cells of 2^k
     cutoff radii: a query group spans several radii, so its candidate
     stream is long and each candidate is in range of few of its queries."""
     r = rng(17 + super_delta)
