@@ -128,6 +128,27 @@ def test_batch_from_page_locked_host_memory(monkeypatch):
             assert_bitwise_equal(got, h.register_batch(host))
 
 
+def test_batch_page_locked_nonfinite_feature_rejected():
+    """Page-locked inputs, pulled into device memory by the library's own
+    kernel, are checked like device inputs: a NaN in one pair's features (X's,
+    then Z's) returns CVO_ERR_INVALID_ARG, and the handle then registers the
+    clean batch with the bits it gave before."""
+    pairs, args = small_batch(n_pairs=4, seed=43)
+    host = [(X.cpu().pin_memory(), Z.cpu().pin_memory(), T, FX.cpu().pin_memory(), FZ.cpu().pin_memory())
+            for (X, Z, T, FX, FZ) in args]
+    with cvo.CVO(blocks=pairs[0].blocks, **KW) as h:
+        ref = h.register_batch(host)
+        for side in (3, 4):   # X's features, then Z's
+            bad = [list(a) for a in host]
+            f = bad[2][side].clone().pin_memory()
+            f[f.shape[0] // 2, 5] = float("nan")
+            bad[2][side] = f
+            with pytest.raises(cvo.CvoError) as e:
+                h.register_batch([tuple(a) for a in bad])
+            assert e.value.status == cvo.Status.ERR_INVALID_ARG
+        assert_bitwise_equal(ref, h.register_batch(host))
+
+
 def batched_and_pairwise(h, args, monkeypatch):
     """A batch set up by the batched stages (one launch per stage for all
     pairs), and set up pair by pair (CVO_BATCH_SETUP=pairs)."""
