@@ -83,6 +83,16 @@ def grad_flops_per_pair(blocks):
     return f
 
 
+def with_measured_throughput(cvo, peaks):
+    """The peaks with the FP32 FMA and ex2 rates measured on this GPU now
+    (cvo_measure_throughput, about 20 ms, outside every timed region)."""
+    out = dict(peaks)
+    t = cvo.cvo_measure_throughput()
+    out["ffma_flops"] = t["ffma_flops"]
+    out["ex2_per_s"] = t["ex2_per_s"]
+    return out
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -228,7 +238,9 @@ def sample_pairs(n_pairs, k=CPU_SAMPLE_PAIRS, seed=20121203):
 def sweep_roofline(name, pairs_evaluated, sweep_ms_total, launches, fpp, peaks, peak_src, sms, profile=None):
     """Roofline figures of a sweep kernel from its CUDA-event times."""
     clk = peaks.get("sm_max_mhz", 2070.0) * 1e6
-    peak = sms * FP32_LANES_PER_SM * 2 * clk / 1e12
+    unit_peak = sms * FP32_LANES_PER_SM * 2 * clk / 1e12
+    measured = peaks.get("ffma_flops")
+    peak = measured / 1e12 if measured else unit_peak
     sec = sweep_ms_total * 1e-3
     achieved = pairs_evaluated * fpp / sec / 1e12 if sec > 0 else None
     avg_ms = sweep_ms_total / max(launches, 1)
@@ -239,7 +251,9 @@ def sweep_roofline(name, pairs_evaluated, sweep_ms_total, launches, fpp, peaks, 
         xu = profile_value(SWEEP_SRC, "xu_pipe_frac", profile)
         issue_active = profile_value(SWEEP_SRC, "issue_active_frac", profile)
     issue_peak = sms * ISSUE_PER_CLK_SM * clk
-    ex2_peak = sms * EX2_PER_CLK_SM * clk
+    ex2_measured = peaks.get("ex2_per_s")
+    ex2_peak = ex2_measured if ex2_measured else sms * EX2_PER_CLK_SM * clk
+    unit_text = f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clk / 1e6:.0f} MHz (sm_max_mhz {peak_src})"
     return {
         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
         "frac": achieved / peak if achieved else None, "traffic": traffic, "kernel": name,
@@ -248,13 +262,18 @@ def sweep_roofline(name, pairs_evaluated, sweep_ms_total, launches, fpp, peaks, 
                            f"changed since") if profile else None,
         "flops_per_pair": fpp, "sweep_ms_avg": avg_ms, "sweep_launches": launches,
         "pairs_per_launch": pairs_evaluated / max(launches, 1),
-        "peak_source": f"unit counts, not a measured FFMA peak: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
-                       f"x {clk / 1e6:.0f} MHz (sm_max_mhz {peak_src})",
+        "peak_source": (f"of measured: FP32 FMA rate measured in this run on this GPU (cvo_measure_throughput: "
+                        f"independent fma.rn.f32 chains, 8 blocks of 256 threads per SM, best of 5 launches); "
+                        f"unit count {unit_text} = {unit_peak:.1f} TFLOP/s") if measured
+                       else f"unit counts, not a measured FFMA peak: {unit_text}",
+        "peak_unit_count": unit_peak,
         "sfu": {"achieved_ex2_per_s": pairs_evaluated / sec if sec > 0 else None, "peak_ex2_per_s": ex2_peak,
                 "frac": pairs_evaluated / sec / ex2_peak if sec > 0 else None,
                 "ncu_xu_pipe_frac": xu,
-                "peak_source": f"{sms} SMs x {EX2_PER_CLK_SM} ex2/clk/SM (measured on a GB300 with an "
-                               "independent-chain ex2.approx throughput loop) x sm_max_mhz"},
+                "peak_source": ("of measured: ex2.approx.ftz.f32 rate measured in this run on this GPU "
+                                "(cvo_measure_throughput: independent chains, best of 5 launches)") if ex2_measured
+                               else (f"{sms} SMs x {EX2_PER_CLK_SM} ex2/clk/SM (measured on a GB300 with an "
+                                     "independent-chain ex2.approx throughput loop) x sm_max_mhz")},
         "issue": {"frac": issue_active, "peak_warp_inst_per_s": issue_peak,
                   "warp_instructions_per_launch": winst,
                   "source": (f"smsp__issue_active (share of scheduler cycles issuing) and smsp__inst_executed.sum of "
@@ -434,7 +453,8 @@ def backward_section(cvo, torch, dev, flush, peaks, peak_src, sms, reps=5):
     out["backward_pair_evals_per_s"] = 2 * ev["pairs"] / (1e-3 * float(np.median(t["backward"])))
     out["timing"] = "whole calls (setup, sweeps, copies) between CUDA events, L2 flushed before each"
     out["roofline"] = sweep_roofline("k_grad + k_grad_reduce (gradient sweep, one per cloud)", ev["pairs"] * g_n,
-                                     g_ms, g_n, grad_flops_per_pair(p.blocks), peaks, peak_src, sms)
+                                     g_ms, g_n, grad_flops_per_pair(p.blocks), peaks, peak_src, sms,
+                                     profile="grad_room-19k.md")
     return out
 
 
@@ -596,6 +616,7 @@ def main():
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     if args.only:
         peaks, peak_src = load_peaks()
+        peaks = with_measured_throughput(cvo, peaks)
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
         tun = None
         if args.tuning:
@@ -710,6 +731,7 @@ def main():
     h.close()
 
     peaks, peak_src = load_peaks()
+    peaks = with_measured_throughput(cvo, peaks)
     sections = {}
     if world > 1 and not args.no_sections and not args.no_large:
         sections["shard"] = shard_section(cvo, torch, dev, dist, world, rank, flush)

@@ -394,6 +394,27 @@ const char* cvo_version(void);
  * handles, all threads), for launch accounting by benchmarks. */
 long long cvo_kernel_launches(void);
 
+/* Measured throughput of the units the sweep runs on, for roofline
+ * denominators.  An addition of this library: the paper has no counterpart.
+ * The sweep is bound by FP32 arithmetic and by one ex2 per pair; counting
+ * units (SMs x 128 FP32 lanes x 2 x clock) gives a ceiling the hardware may
+ * not reach, so this call measures the rates the current device reaches:
+ * kernels of independent fma.rn.f32 chains and of ex2.approx.ftz.f32 chains
+ * on 8 blocks of 256 threads per SM, each timed with CUDA events on
+ * cuda_stream (NULL: legacy default stream), best of 5 launches after one
+ * untimed launch; about 20 ms in all.  Synchronous.  out receives the FP32
+ * rate in FLOP/s (an FMA counts 2), the ex2 rate in evaluations per second,
+ * the best launch times and the SM count.  CVO_ERR_INVALID_ARG for a NULL
+ * out, CVO_ERR_CUDA when a launch fails.  Allocates nothing; the figures
+ * hold for the clocks the GPU ran at while measured. */
+typedef struct {
+    double ffma_flops;   /* FP32 FLOP/s of fused multiply-adds */
+    double ex2_per_s;    /* ex2.approx.ftz.f32 evaluations per second */
+    double ms_ffma, ms_ex2;   /* best launch times */
+    int sms;
+} cvo_throughput;
+cvo_status cvo_measure_throughput(void* cuda_stream, cvo_throughput* out);
+
 /* Dense evaluation that allocates nothing.  This entry point is an addition
  * of this library: the paper has no counterpart.
  *

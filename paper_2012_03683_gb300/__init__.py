@@ -95,6 +95,11 @@ class Eval(ctypes.Structure):
                 ("i_theta", ctypes.c_double), ("pairs", ctypes.c_longlong), ("candidates", ctypes.c_longlong)]
 
 
+class Throughput(ctypes.Structure):
+    _fields_ = [("ffma_flops", ctypes.c_double), ("ex2_per_s", ctypes.c_double), ("ms_ffma", ctypes.c_double),
+                ("ms_ex2", ctypes.c_double), ("sms", ctypes.c_int)]
+
+
 _lib = None
 
 
@@ -154,10 +159,23 @@ def load_library(build_if_missing: bool = True):
     lib.cvo_last_error.argtypes = []
     lib.cvo_version.restype = ctypes.c_char_p
     lib.cvo_version.argtypes = []
+    lib.cvo_measure_throughput.restype = ctypes.c_int
+    lib.cvo_measure_throughput.argtypes = [vp, P(Throughput)]
     lib.cvo_kernel_launches.restype = ctypes.c_longlong
     lib.cvo_kernel_launches.argtypes = []
     _lib = lib
     return lib
+
+
+def cvo_measure_throughput(stream=None) -> dict:
+    """Measured FP32 FMA and ex2 rates of the current device
+    (cvo_measure_throughput): ffma_flops (FLOP/s), ex2_per_s, the best
+    launch times (ms) and the SM count."""
+    t = Throughput()
+    s = _current_stream() if stream is None else ctypes.c_void_p(int(stream))
+    _check(load_library().cvo_measure_throughput(s, ctypes.byref(t)))
+    return {"ffma_flops": t.ffma_flops, "ex2_per_s": t.ex2_per_s, "ms_ffma": t.ms_ffma, "ms_ex2": t.ms_ex2,
+            "sms": t.sms}
 
 
 def cvo_kernel_launches() -> int:
