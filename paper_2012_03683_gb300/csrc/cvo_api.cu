@@ -161,6 +161,8 @@ struct cvo_handle_s {
     // sweep / finalize scratch
     DevBuf part_stats, part_cnt, grp_stats, grp_cnt, grp_arrivals, pairs_dev, counters, trace;
     DevBuf batch_work;   // per pair of a batch: work items left (the batched step re-splits the grid by them)
+    DevBuf item_rows;    // a batch's work queue: one statistics row per work item
+    DevBuf queue_buf;    // a batch's work queue: [0] next item, [1] items, then ibase (pairs + 1 ints)
     DevBuf batch_scratch;   // a batch's set-up: every pair's segment of the sort and scan scratch
     // many small host <-> device copies through one staging copy (upload_blocks, fetch_states)
     DevBuf d_stage;
@@ -1185,12 +1187,14 @@ PairDesc pair_desc(const PairRes& P, int b0, int b1)
 }
 
 // Sweep blocks resident at once on the device for the handle's feature policy.
-cvo_status resident_sweep_blocks(cvo_handle h, int* out)
+// queue_pairs > 0: the work-queue sweep of a batch of that many pairs.
+cvo_status resident_sweep_blocks(cvo_handle h, int* out, int queue_pairs = 0)
 {
     SweepLaunch sl;
-    CVO_CUDA(sweep_launch_info(h->fc, h->rs, h->query_lanes, &sl));
+    CVO_CUDA(sweep_launch_info(h->fc, h->rs, h->query_lanes, &sl, queue_pairs > 0));
+    const size_t smem = sl.smem + (queue_pairs > 0 ? queue_smem(queue_pairs) : 0);
     int per_sm = 0;
-    CVO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sl.func, kSweepWarps * 32, sl.smem));
+    CVO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sl.func, sl.threads, smem));
     *out = std::max(per_sm, 1) * h->num_sms;
     return CVO_OK;
 }
@@ -1280,7 +1284,7 @@ cvo_status run_graph_loop(cvo_handle h, const SweepArgs& a, bool batch, IterStat
                           long long trace_stride, LevelDesc* levels)
 {
     SweepLaunch sl;
-    CVO_CUDA(sweep_launch_info(a.fc, a.rs, a.lanes, &sl));
+    CVO_CUDA(sweep_launch_info(a.fc, a.rs, a.lanes, &sl, a.item_rows != nullptr));
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
     cvo_status status = CVO_OK;
@@ -1311,8 +1315,8 @@ cvo_status run_graph_loop(cvo_handle h, const SweepArgs& a, bool batch, IterStat
     kp.type = cudaGraphNodeTypeKernel;
     kp.kernel.func = (void*)sl.func;
     kp.kernel.gridDim = dim3(h->sweep_blocks);
-    kp.kernel.blockDim = dim3(kSweepWarps * 32);
-    kp.kernel.sharedMemBytes = (unsigned)sl.smem;
+    kp.kernel.blockDim = dim3(sl.threads);
+    kp.kernel.sharedMemBytes = (unsigned)(sl.smem + (a.item_rows != nullptr ? queue_smem(a.npairs) : 0));
     kp.kernel.kernelParams = sp;
     cudaGraphNode_t sn;
     if (!check(cudaGraphAddNode(&sn, body, nullptr, nullptr, 0, &kp), "sweep node")) return cleanup(), status;
@@ -1349,7 +1353,8 @@ cvo_status run_graph_loop(cvo_handle h, const SweepArgs& a, bool batch, IterStat
     long long tstride = trace_stride;
     unsigned* counters = (unsigned*)h->counters.p;
     unsigned* work = (unsigned*)h->batch_work.p;
-    void* fpb[11] = {&pairs, &npairs, &ps, &pc, &cap, &tr, &tstride, &counters, &work, &cond, &use_cond};
+    BatchQueue bq{a.item_rows, const_cast<int*>(a.ibase), a.queue};
+    void* fpb[12] = {&pairs, &npairs, &ps, &pc, &cap, &tr, &tstride, &counters, &work, &bq, &cond, &use_cond};
     if (batch) {
         fpn.kernel.func = (void*)finalize_batch_kernel();
         fpn.kernel.gridDim = dim3(npairs);
@@ -1614,9 +1619,14 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
     // pairs (608 resident blocks): 878 blocks (two waves, the second partly
     // filled) 131 ms per batch; one wave 143 ms (no balancing within it);
     // 2, 4, 8, 16, 32 waves 131, 117, 113, 113, 116 ms
+    // the work queue (unless CVO_BATCH_QUEUE=0 in the environment selects the
+    // block split below, for comparison): one resident wave whose warps take
+    // the items of all running pairs from a counter
+    const char* qmode = std::getenv("CVO_BATCH_QUEUE");
+    const bool queue = !(qmode && std::strcmp(qmode, "0") == 0) && queue_smem(nl) <= 16384;   // ibase in shared memory
     int resident = 0;
-    CVO_TRY(resident_sweep_blocks(h, &resident));
-    const int budget = std::max(nl, 8 * resident);
+    CVO_TRY(resident_sweep_blocks(h, &resident, queue ? nl : 0));
+    const int budget = queue ? std::max(nl, resident) : std::max(nl, 8 * resident);
     std::vector<int> nbs(nl), cap(nl);
     std::vector<std::pair<double, int>> rem;
     int used = 0;
@@ -1648,9 +1658,21 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
         table.back().bmax = std::max(1, std::min(cap[i], 8 * nbs[i]));
         b += nbs[i];
     }
+    if (queue) b = budget;   // the block ranges are not used
     SweepArgs a{};
     CVO_TRY(setup_sweep(h, table, b, &a, false));
     CVO_CUDA(ensure(h->batch_work, (size_t)nl * sizeof(unsigned)));
+    if (queue) {
+        // a row per work item of each pair's largest grid level
+        size_t rows = 0;
+        for (int i = 0; i < nl; ++i) rows += (size_t)std::max(h->pr[i].max_items, 1);
+        CVO_CUDA(ensure(h->item_rows, rows * kRowFloats * sizeof(float)));
+        CVO_CUDA(ensure(h->queue_buf, (size_t)(4 + nl + 1) * sizeof(unsigned)));
+        a.item_rows = (float*)h->item_rows.p;
+        a.queue = (unsigned*)h->queue_buf.p;
+        a.ibase = (const int*)((unsigned*)h->queue_buf.p + 4);
+        CVO_CUDA(launch_queue_init(a.pairs, nl, (unsigned*)h->batch_work.p, const_cast<int*>(a.ibase), a.queue, h->s));
+    }
     const long long tstride = (long long)p.max_iters * CVO_TRACE_STRIDE;
     CVO_CUDA(ensure(h->trace, (size_t)nl * tstride * sizeof(double)));
     double* traces = (double*)h->trace.p;
@@ -1672,7 +1694,7 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
                 if (ev) CVO_CUDA(cudaEventRecord(h->evs[2 * it + 1], h->s));
                 CVO_CUDA(launch_finalize_batch(const_cast<PairDesc*>(a.pairs), nl, a.part_stats, a.part_cnt,
                                                a.part_cap, traces, tstride, counters, (unsigned*)h->batch_work.p,
-                                               h->s));
+                                               BatchQueue{a.item_rows, const_cast<int*>(a.ibase), a.queue}, h->s));
             }
             launched += n;
             if (launched >= p.max_iters) break;
@@ -2062,7 +2084,7 @@ cvo_status cvo_destroy(cvo_handle h)
     DevBuf* bufs[] = {&h->stage_xyz[0], &h->stage_xyz[1], &h->stage_feat[0], &h->stage_feat[1], &h->keys, &h->vals,
                       &h->keys2, &h->vals2, &h->sort_tmp, &h->flags, &h->gidx, &h->misc, &h->part_stats, &h->part_cnt,
                       &h->grp_stats, &h->grp_cnt, &h->grp_arrivals, &h->pairs_dev, &h->counters, &h->trace,
-                      &h->batch_work, &h->batch_scratch, &h->d_stage,
+                      &h->batch_work, &h->item_rows, &h->queue_buf, &h->batch_scratch, &h->d_stage,
                       &h->bw_out[0], &h->bw_out[1], &h->bw_out[2], &h->bw_out[3], &h->bw_tq, &h->bw_dell, &h->bw_part};
     for (DevBuf* b : bufs) release(*b);
     for (SetupLane& L : h->lanes) {

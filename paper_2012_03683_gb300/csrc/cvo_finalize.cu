@@ -246,10 +246,107 @@ __device__ void resplit_grid(PairDesc* pairs, int npairs, int nblocks, const uns
     }
 }
 
+// A pair's statistics from its work items' rows [i0, i1) of a batch's work
+// queue, in a fixed order: the block reads the rows as float4 columns,
+// thread (r, c) of kRowGroups x kCols adding column c (statistics 4 c ..
+// 4 c + 3; the counts at 43 and 44 as integers) of rows i0 + r, i0 + r +
+// kRowGroups, ... in double-float, several rows' loads in flight; the
+// kRowGroups partial sums of each statistic are then added in row-group
+// order.  The order depends on the item numbers only, not on which warp
+// swept an item.
+__device__ void reduce_item_rows(const float* __restrict__ rows, int i0, int i1, double* S, float* Shi, float* Slo,
+                                 unsigned long long* cs)
+{
+    constexpr int kCols = kRowFloats / 4;                  // 12 float4 per row
+    constexpr int kRowGroups = kFinalizeThreads / kCols;   // 21
+    constexpr int kUnroll = 12;
+    __shared__ float ph[kRowGroups][kRowFloats], pl[kRowGroups][kRowFloats];
+    __shared__ unsigned long long pc2[kRowGroups][2];
+    const int t = threadIdx.x;
+    if (t < kRowGroups * kCols) {
+        const int c = t % kCols, r = t / kCols;
+        float h[4] = {0.0f, 0.0f, 0.0f, 0.0f}, l[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        unsigned long long cnt0 = 0ull, cnt1 = 0ull;
+        auto add = [&](const float4 v) {
+            const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int k = 4 * c + e;
+                if (k < kStatN) df_add(h[e], l[e], x[e], 0.0f);
+                else if (k == kStatN) cnt0 += __float_as_uint(x[e]);
+                else if (k == kStatN + 1) cnt1 += __float_as_uint(x[e]);
+            }
+        };
+        const float4* base = reinterpret_cast<const float4*>(rows) + c;
+        int i = i0 + r;
+        for (; i + (kUnroll - 1) * kRowGroups < i1; i += kUnroll * kRowGroups) {
+            float4 v[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) v[u] = __ldcg(base + (size_t)(i + u * kRowGroups) * kCols);
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) add(v[u]);
+        }
+        for (; i < i1; i += kRowGroups) add(__ldcg(base + (size_t)i * kCols));
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            ph[r][4 * c + e] = h[e];
+            pl[r][4 * c + e] = l[e];
+        }
+        if (4 * c <= kStatN && kStatN < 4 * c + 4) pc2[r][0] = cnt0;
+        if (4 * c <= kStatN + 1 && kStatN + 1 < 4 * c + 4) pc2[r][1] = cnt1;
+    }
+    __syncthreads();
+    if (t < kStatN) {
+        float hi = 0.0f, lo = 0.0f;
+        for (int r = 0; r < kRowGroups; ++r) df_add(hi, lo, ph[r][t], pl[r][t]);
+        S[t] = (double)hi + (double)lo;
+        Shi[t] = hi;
+        Slo[t] = lo;
+    } else if (t < kStatN + 2) {
+        unsigned long long v = 0;
+        for (int r = 0; r < kRowGroups; ++r) v += pc2[r][t - kStatN];
+        cs[t - kStatN] = v;
+    }
+}
+
+// The next sweep's first item of each pair: the exclusive prefix sum of the
+// pairs' work (work[p] items, 0 for a stopped pair), by one block.
+__device__ void queue_bases(const unsigned* work, int npairs, int* ibase, unsigned* queue)
+{
+    __shared__ unsigned wsum[kFinalizeThreads / 32];
+    __shared__ unsigned carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0u;
+    __syncthreads();
+    for (int k0 = 0; k0 < npairs; k0 += kFinalizeThreads) {
+        const int k = k0 + (int)threadIdx.x;
+        const unsigned v = k < npairs ? __ldcg(work + k) : 0u;
+        unsigned incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        unsigned before = carry;
+        for (int w = 0; w < warp; ++w) before += wsum[w];
+        if (k < npairs) ibase[k] = (int)(before + incl - v);
+        __syncthreads();
+        if (threadIdx.x == kFinalizeThreads - 1) carry = before + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        ibase[npairs] = (int)carry;
+        queue[0] = 0u;
+        queue[1] = carry;
+    }
+}
+
 __global__ void __launch_bounds__(kFinalizeThreads)
 k_finalize_batch(PairDesc* __restrict__ pairs, int npairs, const float2* __restrict__ ps,
                  const unsigned long long* __restrict__ pc, int cap, double* traces, long long trace_stride,
-                 unsigned* counters, unsigned* work, cudaGraphConditionalHandle cond, int use_cond)
+                 unsigned* counters, unsigned* work, BatchQueue bq, cudaGraphConditionalHandle cond, int use_cond)
 {
     constexpr int kWords = (int)(sizeof(IterState) / 8);
     __shared__ double S[kStatN];
@@ -261,7 +358,17 @@ k_finalize_batch(PairDesc* __restrict__ pairs, int npairs, const float2* __restr
     IterState* st = P.st;
     const bool was_done = st->done != 0;
     IterState* sst = reinterpret_cast<IterState*>(sbuf);
-    if (!was_done) {
+    if (!was_done && bq.rows != nullptr) {
+        for (int i = threadIdx.x; i < kWords; i += kFinalizeThreads)
+            sbuf[i] = reinterpret_cast<const unsigned long long*>(st)[i];
+        reduce_item_rows(bq.rows, bq.ibase[blockIdx.x], bq.ibase[blockIdx.x + 1], S, Shi, Slo, cs);
+        __syncthreads();
+        if (threadIdx.x < 32)
+            step_warp(sst, S, Shi, Slo, cs[0], cs[1], traces ? traces + (size_t)blockIdx.x * trace_stride : nullptr);
+        __syncthreads();
+        for (int i = threadIdx.x; i < kWords; i += kFinalizeThreads)
+            reinterpret_cast<unsigned long long*>(st)[i] = sbuf[i];
+    } else if (!was_done) {
         for (int i = threadIdx.x; i < kWords; i += kFinalizeThreads)
             sbuf[i] = reinterpret_cast<const unsigned long long*>(st)[i];
         // statistic k by warp k % warps: lane l adds the pair's block
@@ -313,7 +420,9 @@ k_finalize_batch(PairDesc* __restrict__ pairs, int npairs, const float2* __restr
     if (threadIdx.x == 0) {
         const bool running = !was_done && !sst->done;
         // the work this pair has left: its items at its (next) grid level
-        work[blockIdx.x] = running ? (unsigned)max(P.levels[sst->level].nitems, 1) : 0u;
+        // (a queue takes them exactly; the block split at least one block)
+        const int left = running ? P.levels[sst->level].nitems : 0;
+        work[blockIdx.x] = bq.rows != nullptr ? (unsigned)left : (running ? (unsigned)max(left, 1) : 0u);
         if (running) atomicAdd(&counters[1], 1u);
         __threadfence();
         is_last = atomicAdd(&counters[0], 1u) == (unsigned)(npairs - 1);
@@ -321,7 +430,8 @@ k_finalize_batch(PairDesc* __restrict__ pairs, int npairs, const float2* __restr
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    resplit_grid(pairs, npairs, cap, work);
+    if (bq.rows != nullptr) queue_bases(work, npairs, bq.ibase, bq.queue);
+    else resplit_grid(pairs, npairs, cap, work);
     if (threadIdx.x == 0) {
         const unsigned active = atomicAdd(&counters[1], 0u);
         counters[2] = active;
@@ -331,18 +441,41 @@ k_finalize_batch(PairDesc* __restrict__ pairs, int npairs, const float2* __restr
     }
 }
 
+// The first sweep's work queue of a batch: each pair's items at the grid
+// level its state starts on (none once stopped), their first-item numbers
+// and the queue's counter.  One block.
+__global__ void __launch_bounds__(kFinalizeThreads)
+k_queue_init(const PairDesc* __restrict__ pairs, int npairs, unsigned* work, int* ibase, unsigned* queue)
+{
+    for (int k = threadIdx.x; k < npairs; k += kFinalizeThreads) {
+        const IterState* st = pairs[k].st;
+        work[k] = st->done ? 0u : (unsigned)pairs[k].levels[st->level].nitems;
+    }
+    __syncthreads();
+    queue_bases(work, npairs, ibase, queue);
+}
+
 }  // namespace
+
+cudaError_t launch_queue_init(const PairDesc* pairs, int npairs, unsigned* work, int* ibase, unsigned* queue,
+                              cudaStream_t s)
+{
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    k_queue_init<<<1, kFinalizeThreads, 0, s>>>(pairs, npairs, work, ibase, queue);
+    return cudaGetLastError();
+}
 
 const void* finalize_kernel() { return (const void*)k_finalize; }
 const void* finalize_batch_kernel() { return (const void*)k_finalize_batch; }
 
 cudaError_t launch_finalize_batch(PairDesc* pairs, int npairs, const float2* part_stats,
                                   const unsigned long long* part_cnt, int part_cap, double* traces,
-                                  long long trace_stride, unsigned* counters, unsigned* work, cudaStream_t s)
+                                  long long trace_stride, unsigned* counters, unsigned* work, BatchQueue bq,
+                                  cudaStream_t s)
 {
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
     k_finalize_batch<<<npairs, kFinalizeThreads, 0, s>>>(pairs, npairs, part_stats, part_cnt, part_cap, traces,
-                                                         trace_stride, counters, work,
+                                                         trace_stride, counters, work, bq,
                                                          cudaGraphConditionalHandle{}, 0);
     return cudaGetLastError();
 }

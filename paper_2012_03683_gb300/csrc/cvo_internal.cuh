@@ -161,6 +161,24 @@ struct SweepArgs {
     int chunk_len;
     int lanes;                 // lanes per query (query groups of 32 / lanes queries)
     int* swept_level;          // with nch_next: the level the sweep covered (written by block 0)
+    // a batch's work queue (item_rows non-NULL): one resident wave of blocks
+    // whose warps take the batch's work items from a counter, largest pair
+    // first; item i (pair p's item i - ibase[p]) leaves its statistics in
+    // row i, and the batched step sums each pair's rows in item order
+    float* item_rows;          // [items][kRowFloats]: the 43 statistics, then the pair and test counts (as bits)
+    unsigned* queue;           // [0] the next item to take, [1] the items of this sweep
+    const int* ibase;          // [npairs + 1] first item of each pair (a stopped pair has none)
+};
+
+constexpr int kRowFloats = 48;   // floats per work item's statistics row (43 + 2 counts, padded)
+constexpr int kQueueWarps = 4;        // warps per work-queue sweep block (six, three blocks per SM, measured slower)
+constexpr int kStreamWarps = kQueueWarps > kSweepWarps ? kQueueWarps : kSweepWarps;   // most warps per block that form streams
+
+// The batched step's view of the work queue (rows NULL: the per-block partials).
+struct BatchQueue {
+    const float* rows;
+    int* ibase;                // rewritten for the next sweep by the last block
+    unsigned* queue;
 };
 
 // ---- launchers (host) ------------------------------------------------------
@@ -179,22 +197,36 @@ cudaError_t launch_sweep(const SweepArgs& a, int nblocks, cudaStream_t s);
 // by rewriting the pairs' b0 / b1 for the next sweep, and, inside a graph,
 // sets the loop's condition.  traces: npairs x trace_stride doubles (NULL: no
 // trace).
+// With a work queue (bq.rows non-NULL) each pair's statistics are the sum
+// of its items' rows, in item order, and the last block writes the next
+// sweep's ibase (the running pairs' work items, in pair order) and resets
+// the queue instead of re-splitting the grid.
 cudaError_t launch_finalize_batch(PairDesc* pairs, int npairs, const float2* part_stats,
                                   const unsigned long long* part_cnt, int part_cap, double* traces,
-                                  long long trace_stride, unsigned* counters, unsigned* work, cudaStream_t s);
+                                  long long trace_stride, unsigned* counters, unsigned* work, BatchQueue bq,
+                                  cudaStream_t s);
 // k_finalize_batch(PairDesc*, int npairs, const float2*, const unsigned long long*, int cap,
 //                  double* traces, long long trace_stride, unsigned* counters, unsigned* work,
-//                  cudaGraphConditionalHandle cond, int use_cond); counters[0] arrivals,
+//                  BatchQueue bq, cudaGraphConditionalHandle cond, int use_cond); counters[0] arrivals,
 //                  counters[1] active pairs being counted, counters[2] the last count
 const void* finalize_batch_kernel();
+// The first sweep's work queue of a batch (work: npairs scratch words; ibase
+// npairs + 1 ints; queue 2 words), from the pairs' initial states.
+cudaError_t launch_queue_init(const PairDesc* pairs, int npairs, unsigned* work, int* ibase, unsigned* queue,
+                              cudaStream_t s);
 
 // Kernel handles for CUDA-graph kernel nodes.
 struct SweepLaunch {
-    const void* func;   // k_sweep specialisation
+    const void* func;   // k_sweep (or k_sweep_q) specialisation
     size_t smem;        // dynamic shared memory
+    int threads;        // threads per block
 };
-// lanes: lanes per query of the sweep (1, 2, 4; the query groups hold 32 / lanes queries)
-cudaError_t sweep_launch_info(const FeatConst& fc, int rs, int lanes, SweepLaunch* out);
+// lanes: lanes per query of the sweep (1, 2, 4; the query groups hold 32 / lanes queries);
+// queue: the work-queue form of a batch (k_sweep_q)
+cudaError_t sweep_launch_info(const FeatConst& fc, int rs, int lanes, SweepLaunch* out, bool queue = false);
+// Dynamic shared memory a work-queue sweep adds to SweepLaunch::smem: its
+// copy of ibase (npairs + 1 ints).
+inline size_t queue_smem(int npairs) { return ((size_t)(npairs + 1) * sizeof(int) + 15) & ~(size_t)15; }
 // k_finalize(IterState*, const float2* grp_stats, const unsigned long long* grp_cnt, int ngroups,
 //            double* trace, cudaGraphConditionalHandle cond, int use_cond), kStepThreads threads
 const void* finalize_kernel();

@@ -92,6 +92,80 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep(SweepArgs a)
     sweep_epilogue(acc, npairs, ncand, a, (int)blockIdx.x, (int)gridDim.x);
 }
 
+// The batched sweep as a work queue.  One resident wave of blocks of
+// kQueueWarps warps; each warp takes the batch's next work item from a
+// counter (a.queue[0]) until the ibase[npairs] items of this sweep are
+// gone, so no warp waits for the others of its block and no slot waits for
+// a block to be launched (the block split of k_sweep kept about 84 % of the
+// warp slots busy on a 64-pair batch).  Item i belongs to the pair p with
+// ibase[p] <= i < ibase[p + 1] (the running pairs' items in pair order,
+// each pair's longest first); the warp keeps that pair's descriptor, grid
+// level, state constants and transform in shared memory while its items
+// follow one another.  Each item's 43 statistics and two counts go to its
+// own row of a.item_rows, which the batched step sums in item order: the
+// result does not depend on which warp took which item, so it is the same
+// bits run after run.
+template <class Feat, int S>
+__global__ void __launch_bounds__(kQueueWarps * 32) k_sweep_q(SweepArgs a)
+{
+    extern __shared__ float4 stage_mem[];   // [kQueueWarps][2][32][rs], the warps' scratch, ibase
+    __shared__ float cstw[kQueueWarps][32];         // per warp: Ahi, Alo, bhi, blo, chi, clo of its pair
+    __shared__ PairDesc pairw[kQueueWarps];
+    __shared__ LevelDesc levelw[kQueueWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int np = a.npairs;
+    const int rs = rec_stride<Feat>(a.rs);
+    int* sib = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(stage_mem + (size_t)kQueueWarps * 2 * 32 * rs) +
+                                      (size_t)kQueueWarps * Feat::kScratch);
+    for (int k = threadIdx.x; k <= np; k += blockDim.x) sib[k] = __ldg(a.ibase + k);
+    __syncthreads();
+    const int total = sib[np];
+    const bool dense = a.dense != 0;
+    const FeatConst fc = a.fc;
+    float4* stage = stage_mem + (size_t)warp * 2 * 32 * rs;
+    unsigned char* scratch =
+        reinterpret_cast<unsigned char*>(stage_mem + (size_t)kQueueWarps * 2 * 32 * rs) + (size_t)warp * Feat::kScratch;
+    float* cst = cstw[warp];
+    StatAcc idx;
+    stat_acc_init(idx, lane);
+    int pi = -1;
+    float sg = 0.0f, rc = 0.0f, rc2 = 0.0f;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = (int)atomicAdd(a.queue, 1u);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= total) break;
+        int lo = 0, hi = np - 1;   // the last pair whose first item is at or before this one
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sib[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        if (lo != pi) {
+            pi = lo;
+            __syncwarp();
+            const PairDesc P = a.pairs[pi];
+            const IterState* st = P.st;
+            if (lane == 0) {
+                pairw[warp] = P;
+                levelw[warp] = P.levels[__ldg(&st->level)];
+            }
+            if (lane < 30) cst[lane] = __ldg(&st->Ahi[0] + lane);
+            sg = __ldg(&st->sg);
+            rc = __ldg(&st->rc);
+            rc2 = __ldg(&st->rc2);
+            __syncwarp();
+        }
+        Moments mo;
+        float p[3];
+        bool act = false;
+        unsigned npairs = 0, ncand = 0;
+        const bool ok = sweep_item<Feat, S>(pairw[warp], levelw[warp], item - sib[pi], cst, rs, dense, sg, rc, rc2, fc,
+                                            stage, scratch, lane, mo, p, act, npairs, ncand);
+        stat_row_write(a.item_rows + (size_t)item * kRowFloats, idx, mo, p, ok && act, npairs, ncand, lane);
+    }
+}
+
 // ---- gradients with respect to the inputs -----------------------------------
 //
 // For the pairs inside the cutoff (the pair set held fixed) and the weight
@@ -564,17 +638,21 @@ cudaError_t each_chunk(const J* jobs, int count, F&& f)
 }
 
 template <class Feat, int S = 1>
-cudaError_t info_t(int rs, SweepLaunch* out)
+cudaError_t info_t(int rs, SweepLaunch* out, bool queue = false)
 {
     if (Feat::kRs > 0 && Feat::kRs != rs) return cudaErrorInvalidValue;   // the policy's record layout
     static bool attr_set = false;   // one-time opt-in above the 48 KB default
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_sweep<Feat, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_sweep_q<Feat, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    out->func = (const void*)k_sweep<Feat, S>;
-    out->smem = (size_t)kSweepWarps * 2 * 32 * rs * sizeof(float4) + (size_t)kSweepWarps * Feat::kScratch;
+    out->func = queue ? (const void*)k_sweep_q<Feat, S> : (const void*)k_sweep<Feat, S>;
+    const int warps = queue ? kQueueWarps : kSweepWarps;
+    out->smem = (size_t)warps * 2 * 32 * rs * sizeof(float4) + (size_t)warps * Feat::kScratch;
+    out->threads = warps * 32;
     return cudaSuccess;
 }
 
@@ -582,24 +660,26 @@ cudaError_t info_t(int rs, SweepLaunch* out)
 
 // The sweep specialisation for a block list: kernel and dynamic shared memory.
 template <bool Cut>
-cudaError_t sweep_info_se3(const FeatConst& f, int rs, SweepLaunch* out)
+cudaError_t sweep_info_se3(const FeatConst& f, int rs, SweepLaunch* out, bool queue)
 {
     if (f.n_blocks == 1)
-        return f.bf16 ? info_t<FeatFixed<3, 0, true, Cut>>(rs, out) : info_t<FeatFixed<3, 0, false, Cut>>(rs, out);
+        return f.bf16 ? info_t<FeatFixed<3, 0, true, Cut>>(rs, out, queue)
+                      : info_t<FeatFixed<3, 0, false, Cut>>(rs, out, queue);
     // bfloat16 labels: the label inner products on the tensor cores
-    return f.bf16 ? info_t<FeatMMA<3, Cut>>(rs, out) : info_t<FeatFixed<3, 19, false, Cut>>(rs, out);
+    return f.bf16 ? info_t<FeatMMA<3, Cut>>(rs, out, queue) : info_t<FeatFixed<3, 19, false, Cut>>(rs, out, queue);
 }
 
 // RGB + 19 labels with S lanes per query (the feature-space cutoff off)
 template <int S>
-cudaError_t sweep_info_lanes(const FeatConst& f, int rs, SweepLaunch* out)
+cudaError_t sweep_info_lanes(const FeatConst& f, int rs, SweepLaunch* out, bool queue)
 {
-    return f.bf16 ? info_t<FeatMMA<3, false, S>, S>(rs, out) : info_t<FeatFixed<3, 19, false, false>, S>(rs, out);
+    return f.bf16 ? info_t<FeatMMA<3, false, S>, S>(rs, out, queue)
+                  : info_t<FeatFixed<3, 19, false, false>, S>(rs, out, queue);
 }
 
-cudaError_t sweep_launch_info(const FeatConst& f, int rs, int lanes, SweepLaunch* out)
+cudaError_t sweep_launch_info(const FeatConst& f, int rs, int lanes, SweepLaunch* out, bool queue)
 {
-    if (f.n_blocks == 0) return info_t<FeatNone>(rs, out);
+    if (f.n_blocks == 0) return info_t<FeatNone>(rs, out, queue);
     const bool se3 = f.n_blocks >= 1 && f.kind[0] == 0 && f.dim[0] == 3;
     const bool labels = f.n_blocks == 2 && f.kind[1] == 1 && f.dim[1] == 19;
     // query groups of 32 / lanes queries: RGB + labels take each query's
@@ -607,16 +687,17 @@ cudaError_t sweep_launch_info(const FeatConst& f, int rs, int lanes, SweepLaunch
     // feature-space cutoff) takes them on one lane, the group's other lanes
     // idle, which is correct but slower
     if (se3 && labels && f.fcut2[0] >= 1.0e38f) {
-        if (lanes == 2) return sweep_info_lanes<2>(f, rs, out);
-        if (lanes == 4) return sweep_info_lanes<4>(f, rs, out);
+        if (lanes == 2) return sweep_info_lanes<2>(f, rs, out, queue);
+        if (lanes == 4) return sweep_info_lanes<4>(f, rs, out, queue);
     }
     if (se3 && (f.n_blocks == 1 || labels)) {
         // the feature-space cutoff's test only where it is on (the colour block's limit is finite)
-        return f.fcut2[0] < 1.0e38f ? sweep_info_se3<true>(f, rs, out) : sweep_info_se3<false>(f, rs, out);
+        return f.fcut2[0] < 1.0e38f ? sweep_info_se3<true>(f, rs, out, queue) : sweep_info_se3<false>(f, rs, out, queue);
     }
     if (f.n_blocks == 1 && f.kind[0] == 1 && f.dim[0] == 19)
-        return f.bf16 ? info_t<FeatMMA<0, false>>(rs, out) : info_t<FeatFixed<0, 19, false, false>>(rs, out);
-    return info_t<FeatGeneric>(rs, out);
+        return f.bf16 ? info_t<FeatMMA<0, false>>(rs, out, queue)
+                      : info_t<FeatFixed<0, 19, false, false>>(rs, out, queue);
+    return info_t<FeatGeneric>(rs, out, queue);
 }
 
 // Gradient sweep specialisation for the block list (the same families as the
@@ -710,11 +791,12 @@ cudaError_t launch_write_items(const LevelDesc* levels, int level, const unsigne
 cudaError_t launch_sweep(const SweepArgs& a, int nblocks, cudaStream_t s)
 {
     SweepLaunch li;
-    cudaError_t e = sweep_launch_info(a.fc, a.rs, a.lanes, &li);
+    cudaError_t e = sweep_launch_info(a.fc, a.rs, a.lanes, &li, a.item_rows != nullptr);
     if (e != cudaSuccess) return e;
     void* args[1] = {(void*)&a};
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
-    return cudaLaunchKernel(li.func, dim3(nblocks), dim3(kSweepWarps * 32), args, li.smem, s);
+    const size_t smem = li.smem + (a.item_rows != nullptr ? queue_smem(a.npairs) : 0);
+    return cudaLaunchKernel(li.func, dim3(nblocks), dim3(li.threads), args, smem, s);
 }
 
 }  // namespace cvo

@@ -398,11 +398,11 @@ __device__ __forceinline__ float* stream_box()
 
 // The group's query positions (Z frame, the high parts of x'), per warp in
 // shared memory: entry q is lane q's query; an inactive lane's entry lies
-// out of every row's reach.  Warps of blocks of up to kSweepWarps warps
+// out of every row's reach.  Warps of blocks of up to kStreamWarps warps
 // (every kernel that forms streams is launched with at most that many).
 __device__ __forceinline__ float4* stream_queries()
 {
-    __shared__ float4 qp[kSweepWarps][32];
+    __shared__ float4 qp[kStreamWarps][32];
     return qp[threadIdx.x >> 5];
 }
 
@@ -887,8 +887,11 @@ __device__ __forceinline__ void stat_acc_init(StatAcc& a, int lane)
     a.s1 = 0.0f;
 }
 
-// Adds one work item's statistics (zero for an inactive lane).  Warp-uniform.
-__device__ __forceinline__ void stat_acc_add(StatAcc& a, const Moments& mo, const float p[3], bool act, int lane)
+// One work item's statistics summed over the warp (zero for an inactive
+// lane): lane l gets the sums of the two statistics (i0, i1) that
+// stat_acc_init gives it.  Warp-uniform.
+__device__ __forceinline__ void stat_item_sums(const Moments& mo, const float p[3], bool act, int lane, float& s0,
+                                               float& s1)
 {
     float v[kStatPad];
 #pragma unroll
@@ -903,8 +906,40 @@ __device__ __forceinline__ void stat_acc_add(StatAcc& a, const Moments& mo, cons
     const float a1 = up ? 0.0f : v[1];
     const float b0 = up ? v[0] : v[2];
     const float b1 = up ? v[1] : 0.0f;
-    a.s0 += a0 + __shfl_xor_sync(kFull, b0, 1);
-    a.s1 += a1 + __shfl_xor_sync(kFull, b1, 1);
+    s0 = a0 + __shfl_xor_sync(kFull, b0, 1);
+    s1 = a1 + __shfl_xor_sync(kFull, b1, 1);
+}
+
+// Adds one work item's statistics to the lane's running sums.  Warp-uniform.
+__device__ __forceinline__ void stat_acc_add(StatAcc& a, const Moments& mo, const float p[3], bool act, int lane)
+{
+    float s0, s1;
+    stat_item_sums(mo, p, act, lane, s0, s1);
+    a.s0 += s0;
+    a.s1 += s1;
+}
+
+// One work item's statistics into its row of a batch's work-queue table
+// (kRowFloats floats: the 43 statistics, then the item's pair and test
+// counts as 32-bit integers).  Every statistic of the row is written (zero
+// for an empty item), so rows left by an earlier sweep are never read.
+// idx: the lane's statistic indices (stat_acc_init).  Warp-uniform.
+__device__ __forceinline__ void stat_row_write(float* row, const StatAcc& idx, const Moments& mo, const float p[3],
+                                               bool act, unsigned np, unsigned nc, int lane)
+{
+    float s0, s1;
+    stat_item_sums(mo, p, act, lane, s0, s1);
+    if (idx.i0 >= 0) row[idx.i0] = s0;
+    if (idx.i1 >= 0) row[idx.i1] = s1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        np += __shfl_xor_sync(kFull, np, o);
+        nc += __shfl_xor_sync(kFull, nc, o);
+    }
+    if (lane == 0) {
+        row[kStatN] = __uint_as_float(np);
+        row[kStatN + 1] = __uint_as_float(nc);
+    }
 }
 
 // End of a sweep block's work: the warps' running sums added over the block's

@@ -211,3 +211,26 @@ def test_batch_lanes_per_query():
                 er, et = pose_err(T1[k], Tl[k])
                 assert er <= POSE_TOL and et <= POSE_TOL, (lanes, k, er, et)
                 assert il[k]["F"] == pytest.approx(i1[k]["F"], rel=1e-4), (lanes, k)
+
+
+def test_work_queue_matches_block_split_and_repeats(monkeypatch):
+    """The batched sweep's work queue (warps take items from a counter, each
+    item's statistics in its own row, summed per pair in item order) against
+    the block split of the same batch (CVO_BATCH_QUEUE=0): the same poses,
+    F and pair counts up to the summation order, and bitwise the same
+    results on a second run whatever warp took which item."""
+    pairs, args = small_batch(n_pairs=6, seed=47)
+    with cvo.CVO(blocks=pairs[0].blocks, **KW) as h:
+        q1 = h.register_batch(args)
+        q2 = h.register_batch(args)
+        with monkeypatch.context() as m:
+            m.setenv("CVO_BATCH_QUEUE", "0")
+            blk = h.register_batch(args)
+    assert_bitwise_equal(q1, q2)
+    (Tq, iq, _), (Tb, ib, _) = q1, blk
+    for k in range(len(iq)):
+        er, et = pose_err(Tq[k], Tb[k])
+        assert er <= 1e-6 and et <= 1e-6, (k, er, et)
+        assert iq[k]["F"] == pytest.approx(ib[k]["F"], rel=1e-6)
+        assert abs(iq[k]["pairs"] - ib[k]["pairs"]) <= 2
+        assert iq[k]["iters"] == ib[k]["iters"]
