@@ -1353,9 +1353,14 @@ cvo_status run_graph_loop(cvo_handle h, const SweepArgs& a, bool batch, IterStat
     long long tstride = trace_stride;
     unsigned* counters = (unsigned*)h->counters.p;
     unsigned* work = (unsigned*)h->batch_work.p;
+    void* fpb[11] = {&pairs, &npairs, &ps, &pc, &cap, &tr, &tstride, &counters, &work, &cond, &use_cond};
     BatchQueue bq{a.item_rows, const_cast<int*>(a.ibase), a.queue};
-    void* fpb[12] = {&pairs, &npairs, &ps, &pc, &cap, &tr, &tstride, &counters, &work, &bq, &cond, &use_cond};
-    if (batch) {
+    void* fpq[9] = {&pairs, &npairs, &tr, &tstride, &counters, &work, &bq, &cond, &use_cond};
+    if (batch && a.item_rows != nullptr) {
+        fpn.kernel.func = (void*)finalize_batch_queue_kernel();
+        fpn.kernel.gridDim = dim3(npairs * kStepCluster);
+        fpn.kernel.kernelParams = fpq;
+    } else if (batch) {
         fpn.kernel.func = (void*)finalize_batch_kernel();
         fpn.kernel.gridDim = dim3(npairs);
         fpn.kernel.kernelParams = fpb;

@@ -27,6 +27,8 @@
 //
 // GB300 runs FP64 at 1/72 of the FP32 rate, so this serial code is kept to
 // closed forms (no 6x6 products on the registration path).
+#include <cooperative_groups.h>
+
 #include "cvo_step_dev.cuh"
 
 namespace cvo {
@@ -246,16 +248,16 @@ __device__ void resplit_grid(PairDesc* pairs, int npairs, int nblocks, const uns
     }
 }
 
-// A pair's statistics from its work items' rows [i0, i1) of a batch's work
-// queue, in a fixed order: the block reads the rows as float4 columns,
+// The sum of a batch's work-queue rows [i0, i1) (statistics in
+// double-float bh + bl, counts in bc), in a fixed order: the block reads the rows as float4 columns,
 // thread (r, c) of kRowGroups x kCols adding column c (statistics 4 c ..
 // 4 c + 3; the counts at 43 and 44 as integers) of rows i0 + r, i0 + r +
 // kRowGroups, ... in double-float, several rows' loads in flight; the
 // kRowGroups partial sums of each statistic are then added in row-group
 // order.  The order depends on the item numbers only, not on which warp
 // swept an item.
-__device__ void reduce_item_rows(const float* __restrict__ rows, int i0, int i1, double* S, float* Shi, float* Slo,
-                                 unsigned long long* cs)
+__device__ void reduce_item_rows(const float* __restrict__ rows, int i0, int i1, float* bh, float* bl,
+                                 unsigned long long* bc)
 {
     constexpr int kCols = kRowFloats / 4;                  // 12 float4 per row
     constexpr int kRowGroups = kFinalizeThreads / kCols;   // 21
@@ -299,13 +301,12 @@ __device__ void reduce_item_rows(const float* __restrict__ rows, int i0, int i1,
     if (t < kStatN) {
         float hi = 0.0f, lo = 0.0f;
         for (int r = 0; r < kRowGroups; ++r) df_add(hi, lo, ph[r][t], pl[r][t]);
-        S[t] = (double)hi + (double)lo;
-        Shi[t] = hi;
-        Slo[t] = lo;
+        bh[t] = hi;
+        bl[t] = lo;
     } else if (t < kStatN + 2) {
         unsigned long long v = 0;
         for (int r = 0; r < kRowGroups; ++r) v += pc2[r][t - kStatN];
-        cs[t - kStatN] = v;
+        bc[t - kStatN] = v;
     }
 }
 
@@ -346,7 +347,7 @@ __device__ void queue_bases(const unsigned* work, int npairs, int* ibase, unsign
 __global__ void __launch_bounds__(kFinalizeThreads)
 k_finalize_batch(PairDesc* __restrict__ pairs, int npairs, const float2* __restrict__ ps,
                  const unsigned long long* __restrict__ pc, int cap, double* traces, long long trace_stride,
-                 unsigned* counters, unsigned* work, BatchQueue bq, cudaGraphConditionalHandle cond, int use_cond)
+                 unsigned* counters, unsigned* work, cudaGraphConditionalHandle cond, int use_cond)
 {
     constexpr int kWords = (int)(sizeof(IterState) / 8);
     __shared__ double S[kStatN];
@@ -358,17 +359,7 @@ k_finalize_batch(PairDesc* __restrict__ pairs, int npairs, const float2* __restr
     IterState* st = P.st;
     const bool was_done = st->done != 0;
     IterState* sst = reinterpret_cast<IterState*>(sbuf);
-    if (!was_done && bq.rows != nullptr) {
-        for (int i = threadIdx.x; i < kWords; i += kFinalizeThreads)
-            sbuf[i] = reinterpret_cast<const unsigned long long*>(st)[i];
-        reduce_item_rows(bq.rows, bq.ibase[blockIdx.x], bq.ibase[blockIdx.x + 1], S, Shi, Slo, cs);
-        __syncthreads();
-        if (threadIdx.x < 32)
-            step_warp(sst, S, Shi, Slo, cs[0], cs[1], traces ? traces + (size_t)blockIdx.x * trace_stride : nullptr);
-        __syncthreads();
-        for (int i = threadIdx.x; i < kWords; i += kFinalizeThreads)
-            reinterpret_cast<unsigned long long*>(st)[i] = sbuf[i];
-    } else if (!was_done) {
+    if (!was_done) {
         for (int i = threadIdx.x; i < kWords; i += kFinalizeThreads)
             sbuf[i] = reinterpret_cast<const unsigned long long*>(st)[i];
         // statistic k by warp k % warps: lane l adds the pair's block
@@ -420,9 +411,7 @@ k_finalize_batch(PairDesc* __restrict__ pairs, int npairs, const float2* __restr
     if (threadIdx.x == 0) {
         const bool running = !was_done && !sst->done;
         // the work this pair has left: its items at its (next) grid level
-        // (a queue takes them exactly; the block split at least one block)
-        const int left = running ? P.levels[sst->level].nitems : 0;
-        work[blockIdx.x] = bq.rows != nullptr ? (unsigned)left : (running ? (unsigned)max(left, 1) : 0u);
+        work[blockIdx.x] = running ? (unsigned)max(P.levels[sst->level].nitems, 1) : 0u;
         if (running) atomicAdd(&counters[1], 1u);
         __threadfence();
         is_last = atomicAdd(&counters[0], 1u) == (unsigned)(npairs - 1);
@@ -430,8 +419,92 @@ k_finalize_batch(PairDesc* __restrict__ pairs, int npairs, const float2* __restr
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    if (bq.rows != nullptr) queue_bases(work, npairs, bq.ibase, bq.queue);
-    else resplit_grid(pairs, npairs, cap, work);
+    resplit_grid(pairs, npairs, cap, work);
+    if (threadIdx.x == 0) {
+        const unsigned active = atomicAdd(&counters[1], 0u);
+        counters[2] = active;
+        counters[0] = 0u;
+        counters[1] = 0u;
+        if (use_cond) cudaGraphSetConditional(cond, active > 0u ? 1u : 0u);
+    }
+}
+
+// The batched step with a work queue: a cluster of kStepCluster blocks per
+// pair.  Block r of the cluster sums the r-th of kStepCluster equal slices
+// of the pair's item rows (reduce_item_rows), block 0 adds the slices' sums
+// in rank order through distributed shared memory and takes the step, so
+// the order is fixed by the item numbers and the pair's rows are read by
+// kStepCluster SMs at once.  Block 0 then records the pair's work at its
+// next grid level (0 once stopped); the last pair to finish lays out the
+// next sweep's queue (queue_bases) and, inside a graph, sets the loop's
+// condition.
+__global__ void __cluster_dims__(kStepCluster, 1, 1) __launch_bounds__(kFinalizeThreads)
+k_finalize_batch_q(PairDesc* __restrict__ pairs, int npairs, double* traces, long long trace_stride,
+                   unsigned* counters, unsigned* work, BatchQueue bq, cudaGraphConditionalHandle cond, int use_cond)
+{
+    namespace cg = cooperative_groups;
+    constexpr int kWords = (int)(sizeof(IterState) / 8);
+    __shared__ double S[kStatN];
+    __shared__ float Shi[kStatN], Slo[kStatN];
+    __shared__ unsigned long long cs[2];
+    __shared__ unsigned long long sbuf[kWords];
+    __shared__ float bh[kStatN], bl[kStatN];          // this block's slice sums
+    __shared__ unsigned long long bc[2];
+    __shared__ int is_last;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int pi = (int)blockIdx.x / kStepCluster;
+    const PairDesc P = pairs[pi];
+    IterState* st = P.st;
+    const bool was_done = st->done != 0;   // the same for every block of the cluster
+    if (!was_done) {
+        const int i0 = bq.ibase[pi], n = bq.ibase[pi + 1] - i0;
+        const int a = i0 + (int)(((long long)n * rank) / kStepCluster);
+        const int b = i0 + (int)(((long long)n * (rank + 1)) / kStepCluster);
+        reduce_item_rows(bq.rows, a, b, bh, bl, bc);
+    }
+    cluster.sync();
+    IterState* sst = reinterpret_cast<IterState*>(sbuf);
+    if (rank == 0 && !was_done) {
+        const int t = threadIdx.x;
+        if (t < kStatN) {
+            float hi = 0.0f, lo = 0.0f;
+            for (int r = 0; r < kStepCluster; ++r) {
+                const float* rh = cluster.map_shared_rank(bh, r);
+                const float* rl = cluster.map_shared_rank(bl, r);
+                df_add(hi, lo, rh[t], rl[t]);
+            }
+            S[t] = (double)hi + (double)lo;
+            Shi[t] = hi;
+            Slo[t] = lo;
+        } else if (t < kStatN + 2) {
+            unsigned long long v = 0;
+            for (int r = 0; r < kStepCluster; ++r) v += cluster.map_shared_rank(bc, r)[t - kStatN];
+            cs[t - kStatN] = v;
+        }
+        for (int i = t; i < kWords; i += kFinalizeThreads) sbuf[i] = reinterpret_cast<const unsigned long long*>(st)[i];
+    }
+    cluster.sync();   // the other blocks' slice sums stay readable until block 0 has them
+    if (rank != 0) return;
+    if (!was_done) {
+        if (threadIdx.x < 32)
+            step_warp(sst, S, Shi, Slo, cs[0], cs[1], traces ? traces + (size_t)pi * trace_stride : nullptr);
+        __syncthreads();
+        for (int i = threadIdx.x; i < kWords; i += kFinalizeThreads)
+            reinterpret_cast<unsigned long long*>(st)[i] = sbuf[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool running = !was_done && !sst->done;
+        work[pi] = running ? (unsigned)P.levels[sst->level].nitems : 0u;
+        if (running) atomicAdd(&counters[1], 1u);
+        __threadfence();
+        is_last = atomicAdd(&counters[0], 1u) == (unsigned)(npairs - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    queue_bases(work, npairs, bq.ibase, bq.queue);
     if (threadIdx.x == 0) {
         const unsigned active = atomicAdd(&counters[1], 0u);
         counters[2] = active;
@@ -467,6 +540,7 @@ cudaError_t launch_queue_init(const PairDesc* pairs, int npairs, unsigned* work,
 
 const void* finalize_kernel() { return (const void*)k_finalize; }
 const void* finalize_batch_kernel() { return (const void*)k_finalize_batch; }
+const void* finalize_batch_queue_kernel() { return (const void*)k_finalize_batch_q; }
 
 cudaError_t launch_finalize_batch(PairDesc* pairs, int npairs, const float2* part_stats,
                                   const unsigned long long* part_cnt, int part_cap, double* traces,
@@ -474,8 +548,14 @@ cudaError_t launch_finalize_batch(PairDesc* pairs, int npairs, const float2* par
                                   cudaStream_t s)
 {
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    if (bq.rows != nullptr) {
+        k_finalize_batch_q<<<npairs * kStepCluster, kFinalizeThreads, 0, s>>>(pairs, npairs, traces, trace_stride,
+                                                                              counters, work, bq,
+                                                                              cudaGraphConditionalHandle{}, 0);
+        return cudaGetLastError();
+    }
     k_finalize_batch<<<npairs, kFinalizeThreads, 0, s>>>(pairs, npairs, part_stats, part_cnt, part_cap, traces,
-                                                         trace_stride, counters, work, bq,
+                                                         trace_stride, counters, work,
                                                          cudaGraphConditionalHandle{}, 0);
     return cudaGetLastError();
 }

@@ -49,6 +49,7 @@ constexpr int kChunks = 8;       // chunks per group of the uniform items
 constexpr int kChunkMin = 64;    // shortest run-time chunk of the uniform items
 constexpr int kTrimChunkLen = 768;   // planned items at least this long trim the stream rows by each query
 constexpr int kFinalizeThreads = 256;  // threads of a batched step block
+constexpr int kStepCluster = 4;        // blocks per pair of the batched step with a work queue (a cluster)
 constexpr int kStepThreads = 384;      // threads of the single-pair step block (its registers allow 12 warps)
 constexpr int kGroupBlocks = 8;    // sweep blocks per reduction group (the group's last block sums them)
 constexpr int kMaxGroups = 256;    // reduction groups per sweep launch (so at most kGroupBlocks * kMaxGroups sweep blocks)
@@ -210,6 +211,11 @@ cudaError_t launch_finalize_batch(PairDesc* pairs, int npairs, const float2* par
 //                  BatchQueue bq, cudaGraphConditionalHandle cond, int use_cond); counters[0] arrivals,
 //                  counters[1] active pairs being counted, counters[2] the last count
 const void* finalize_batch_kernel();
+// The same step with a work queue: a cluster of kStepCluster blocks per pair
+// (grid npairs * kStepCluster), k_finalize_batch_q(PairDesc*, int npairs,
+// double* traces, long long trace_stride, unsigned* counters, unsigned* work,
+// BatchQueue bq, cudaGraphConditionalHandle cond, int use_cond).
+const void* finalize_batch_queue_kernel();
 // The first sweep's work queue of a batch (work: npairs scratch words; ibase
 // npairs + 1 ints; queue 2 words), from the pairs' initial states.
 cudaError_t launch_queue_init(const PairDesc* pairs, int npairs, unsigned* work, int* ibase, unsigned* queue,
