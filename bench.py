@@ -85,9 +85,15 @@ def grad_flops_per_pair(blocks):
 
 def with_measured_throughput(cvo, peaks):
     """The peaks with the FP32 FMA and ex2 rates measured on this GPU now
-    (cvo_measure_throughput, about 20 ms, outside every timed region)."""
+    (cvo_measure_throughput, about 20 ms, outside every timed region); if
+    the measurement fails, the unit counts stand in (the roofline's
+    peak_source then says so)."""
     out = dict(peaks)
-    t = cvo.cvo_measure_throughput()
+    try:
+        t = cvo.cvo_measure_throughput()
+    except Exception as e:  # noqa: BLE001 - the bench line must still be printed
+        print(f"cvo_measure_throughput failed ({e}); unit-count peaks", file=sys.stderr)
+        return out
     out["ffma_flops"] = t["ffma_flops"]
     out["ex2_per_s"] = t["ex2_per_s"]
     return out

@@ -40,6 +40,36 @@ def test_roofline_arithmetic():
     assert "unit counts" in r["peak_source"]
 
 
+def test_roofline_against_measured_rates():
+    """With the FP32 FMA and ex2 rates measured in the run, those are the
+    denominators, and the unit count is reported beside them."""
+    peaks = {"sm_max_mhz": 2000.0, "ffma_flops": 75e12, "ex2_per_s": 9e12}
+    r = bench.sweep_roofline("k", pairs_evaluated=1e9, sweep_ms_total=100.0, launches=50, fpp=76, peaks=peaks,
+                             peak_src="measured", sms=152)
+    assert r["peak"] == pytest.approx(75.0)
+    assert r["peak_unit_count"] == pytest.approx(152 * 128 * 2 * 2e9 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / 75.0)
+    assert r["sfu"]["peak_ex2_per_s"] == pytest.approx(9e12)
+    assert r["peak_source"].startswith("of measured") and "of measured" in r["sfu"]["peak_source"]
+
+
+def test_measured_rates_fall_back_to_unit_counts():
+    class Fails:
+        @staticmethod
+        def cvo_measure_throughput():
+            raise RuntimeError("no device")
+
+    class Works:
+        @staticmethod
+        def cvo_measure_throughput():
+            return {"ffma_flops": 7e13, "ex2_per_s": 1e13, "ms_ffma": 1.0, "ms_ex2": 1.0, "sms": 152}
+
+    base = {"sm_max_mhz": 2070.0}
+    assert bench.with_measured_throughput(Fails, base) == base
+    got = bench.with_measured_throughput(Works, base)
+    assert got["ffma_flops"] == 7e13 and got["ex2_per_s"] == 1e13 and "ffma_flops" not in base
+
+
 def test_flops_per_pair():
     # offset 3, distance 5, scale 1, moments 19; SE block 3d + 1; dot block 2d
     assert bench.flops_per_pair([]) == 28
