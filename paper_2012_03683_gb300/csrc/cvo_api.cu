@@ -1556,6 +1556,12 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
     }
     const int nl = (int)live.size();
     if (nl == 0) return p.max_iters == 0 && npairs > 0 ? CVO_NOT_CONVERGED : CVO_OK;
+    // the pairs in order of Z's size, largest first: the work queue takes
+    // their items in this order, so every sweep ends on small pairs' short
+    // items instead of waiting for a large pair's long ones taken last
+    // (batch-64: 27.9 -> 27.3 ms); a pair's result does not depend on where
+    // its items stand in the queue
+    std::stable_sort(live.begin(), live.end(), [&](int x, int y) { return Z[x].n > Z[y].n; });
     int bf = 1;
     for (int k : live) bf &= rec_bf16_of(p, X + k, Z + k);
     CVO_TRY(begin_call(h, bf, nl));
