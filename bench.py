@@ -753,8 +753,7 @@ def main():
     if rank != 0:
         return
 
-    roof = sweep_roofline("k_sweep_q<FeatMMA<3>> (batched sweep as a work queue, bfloat16 label tile on the tensor "
-                          "cores)", sw_evals,
+    roof = sweep_roofline("k_sweep<FeatMMA<3>> (batched sweep, bfloat16 label tile on the tensor cores)", sw_evals,
                           sw_ms, sw_n, flops_per_pair(kw["blocks"]), peaks, peak_src, sms,
                           profile="sweep_batch-64.md")
     roof["timing"] = ("CUDA events around each batched sweep launch, over the same batched registrations queued "

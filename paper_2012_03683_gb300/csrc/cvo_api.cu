@@ -1556,11 +1556,11 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
     }
     const int nl = (int)live.size();
     if (nl == 0) return p.max_iters == 0 && npairs > 0 ? CVO_NOT_CONVERGED : CVO_OK;
-    // the pairs in order of Z's size, largest first: the work queue takes
-    // their items in this order, so every sweep ends on small pairs' short
-    // items instead of waiting for a large pair's long ones taken last
-    // (batch-64: 27.9 -> 27.3 ms); a pair's result does not depend on where
-    // its items stand in the queue
+    // the pairs in order of Z's size, largest first: the sweep's blocks (and
+    // the work queue's items) go to them in this order, so every sweep ends on
+    // small pairs' short items instead of waiting for a large pair's long
+    // ones started last (batch-64: block split 28.7 -> 26.9 ms, work queue
+    // 27.9 -> 27.2 ms); a pair's result does not depend on its place
     std::stable_sort(live.begin(), live.end(), [&](int x, int y) { return Z[x].n > Z[y].n; });
     int bf = 1;
     for (int k : live) bf &= rec_bf16_of(p, X + k, Z + k);
@@ -1630,11 +1630,12 @@ cvo_status run_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, cons
     // pairs (608 resident blocks): 878 blocks (two waves, the second partly
     // filled) 131 ms per batch; one wave 143 ms (no balancing within it);
     // 2, 4, 8, 16, 32 waves 131, 117, 113, 113, 116 ms
-    // the work queue (unless CVO_BATCH_QUEUE=0 in the environment selects the
-    // block split below, for comparison): one resident wave whose warps take
-    // the items of all running pairs from a counter
+    // the block split below, or with CVO_BATCH_QUEUE=1 in the environment the
+    // work queue: one resident wave whose warps take the items of all running
+    // pairs from a counter (its results do not depend on the grid; with the
+    // pairs largest first the block split measured 0.8 % faster)
     const char* qmode = std::getenv("CVO_BATCH_QUEUE");
-    const bool queue = !(qmode && std::strcmp(qmode, "0") == 0) && queue_smem(nl) <= 16384;   // ibase in shared memory
+    const bool queue = qmode && std::strcmp(qmode, "1") == 0 && queue_smem(nl) <= 16384;   // ibase in shared memory
     int resident = 0;
     CVO_TRY(resident_sweep_blocks(h, &resident, queue ? nl : 0));
     const int budget = queue ? std::max(nl, resident) : std::max(nl, 8 * resident);

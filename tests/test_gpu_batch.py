@@ -214,18 +214,18 @@ def test_batch_lanes_per_query():
 
 
 def test_work_queue_matches_block_split_and_repeats(monkeypatch):
-    """The batched sweep's work queue (warps take items from a counter, each
-    item's statistics in its own row, summed per pair in item order) against
-    the block split of the same batch (CVO_BATCH_QUEUE=0): the same poses,
-    F and pair counts up to the summation order, and bitwise the same
+    """The batched sweep's work queue (CVO_BATCH_QUEUE=1: warps take items
+    from a counter, each item's statistics in its own row, summed per pair in
+    item order) against the default block split of the same batch: the same
+    poses, F and pair counts up to the summation order, and bitwise the same
     results on a second run whatever warp took which item."""
     pairs, args = small_batch(n_pairs=6, seed=47)
     with cvo.CVO(blocks=pairs[0].blocks, **KW) as h:
-        q1 = h.register_batch(args)
-        q2 = h.register_batch(args)
+        blk = h.register_batch(args)
         with monkeypatch.context() as m:
-            m.setenv("CVO_BATCH_QUEUE", "0")
-            blk = h.register_batch(args)
+            m.setenv("CVO_BATCH_QUEUE", "1")
+            q1 = h.register_batch(args)
+            q2 = h.register_batch(args)
     assert_bitwise_equal(q1, q2)
     (Tq, iq, _), (Tb, ib, _) = q1, blk
     for k in range(len(iq)):
