@@ -215,18 +215,29 @@ cvo_status cvo_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, co
 cvo_status cvo_metric_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T[16], double di,
                                float* dX, float* dFX, float* dZ, float* dFZ, double* dell, int outputs_on_device);
 
-/* Registration (Problem 1): gradient ascent on SE(3) from T_init, one
- * line-Newton step along the gradient per iteration (t = |g|^2 / -F'' when
- * F'' < 0, else 1e-3 / |g|, clamped by max_step_rot / max_step_trans),
- * T <- exp(t g^) T, with the lengthscale annealing of Sec. IV when
- * params.anneal = 1.  T_out receives the final pose; info (nullable) the
- * summary.  Returns CVO_OK when converged, CVO_NOT_CONVERGED at max_iters. */
+/* Registration (Problem 1): gradient ascent on SE(3) from T_init (Sec. I).
+ * Each iteration takes the ascent direction in a metric that names no
+ * coordinate origin (rotation and translation about Z's moved centroid,
+ * the rotation weighted by Z's mean squared radius plus l^2), a
+ * line-Newton step along it (F' / -F'' when F'' < 0, else the edge of the
+ * trust region) inside a trust region on the motion of Z's points (none
+ * moves more than max_step_trans, or half a lengthscale when that is 0,
+ * and the rotation is at most max_step_rot), and T <- exp(t xi^) T; the
+ * lengthscale anneals as in Sec. IV when params.anneal = 1.  T_out
+ * receives the final pose; info (nullable) the summary.  Returns CVO_OK
+ * when converged, CVO_NOT_CONVERGED at max_iters. */
 cvo_status cvo_register_pair(cvo_handle h, const cvo_cloud* X, const cvo_cloud* Z, const double T_init[16],
                              double T_out[16], cvo_info* info);
 
 /* Registers npairs independent pairs (X[k], Z[k]) from T_init[16k..16k+15];
  * T_out and infos (nullable) are indexed the same way.  Returns the worst
- * status (an error, else CVO_NOT_CONVERGED if any pair hit max_iters). */
+ * status (an error, else CVO_NOT_CONVERGED if any pair hit max_iters).
+ * All pairs share one sweep per iteration (one CUDA graph for the loop),
+ * whose blocks go to the pairs in order of Z's size, largest first; a pair
+ * stops on its own (a per-pair mask) and its blocks pass to the pairs
+ * still running.  CVO_BATCH_QUEUE=1 in the environment selects a work-queue
+ * sweep instead (warps take the pairs' work items from a counter; results
+ * independent of the device's SM count, about 1 % slower on 64 pairs). */
 cvo_status cvo_register_batch(cvo_handle h, int npairs, const cvo_cloud* X, const cvo_cloud* Z,
                               const double* T_init, double* T_out, cvo_info* infos);
 
