@@ -92,10 +92,10 @@ typedef struct {
     int anneal;            /* 1: lengthscale annealing of Sec. IV */
     double decay;          /* l <- max(decay * l, ell_min) when the indicator stabilises (0.98: 2 %) */
     double indicator_tol;  /* "stabilised": |i_k - i_ref| < indicator_tol * |i_ref| at the same l */
-    double step_tol_rot;   /* converged when |t omega| < step_tol_rot ... */
-    double step_tol_trans; /* ... and |t v| < step_tol_trans, with l at its floor */
-    double max_step_rot;   /* clamp of |t omega| per iteration (rad) */
-    double max_step_trans; /* clamp of |t v| per iteration (m); <= 0: 0.5 * current l */
+    double step_tol_rot;   /* converged when the step's rotation |t omega| < step_tol_rot ... */
+    double step_tol_trans; /* ... and the motion of Z's centroid < step_tol_trans, with l at its floor */
+    double max_step_rot;   /* bound on the step's rotation |t omega| per iteration (rad) */
+    double max_step_trans; /* bound on any point of Z's motion per iteration (m); <= 0: 0.5 * current l */
     double feat_cutoff_mult; /* > 0: a pair also needs |u_b - v_b| <= feat_cutoff_mult * scale_b for every
                                 CVO_FEAT_SE block b (the feature-space sparsity of Sec. III-B; changes F);
                                 <= 0: off (default) */
@@ -221,7 +221,7 @@ cvo_status cvo_metric_backward(cvo_handle h, const cvo_cloud* X, const cvo_cloud
  * the rotation weighted by Z's mean squared radius plus l^2), a
  * line-Newton step along it (F' / -F'' when F'' < 0, else the edge of the
  * trust region) inside a trust region on the motion of Z's points (none
- * moves more than max_step_trans, or half a lengthscale when that is 0,
+ * moves more than max_step_trans, or half a lengthscale when that is <= 0,
  * and the rotation is at most max_step_rot), and T <- exp(t xi^) T; the
  * lengthscale anneals as in Sec. IV when params.anneal = 1.  T_out
  * receives the final pose; info (nullable) the summary.  Returns CVO_OK
