@@ -234,3 +234,27 @@ def test_work_queue_matches_block_split_and_repeats(monkeypatch):
         assert iq[k]["F"] == pytest.approx(ib[k]["F"], rel=1e-6)
         assert abs(iq[k]["pairs"] - ib[k]["pairs"]) <= 2
         assert iq[k]["iters"] == ib[k]["iters"]
+
+
+def test_pair_order_does_not_change_results(monkeypatch):
+    """The batch's pairs enter the sweep largest first whatever their order
+    in the call: permuting them gives each pair its pose, F and pair count
+    again (to rounding with the block split; bitwise with the work queue,
+    whose per-pair sums depend on the items alone)."""
+    pairs, args = small_batch(n_pairs=6, seed=53)
+    perm = [4, 1, 5, 0, 3, 2]
+    with cvo.CVO(blocks=pairs[0].blocks, **KW) as h:
+        T0, i0, _ = h.register_batch(args)
+        T1, i1, _ = h.register_batch([args[k] for k in perm])
+        for j, k in enumerate(perm):
+            er, et = pose_err(T0[k], T1[j])
+            assert er <= 1e-6 and et <= 1e-6, (k, er, et)
+            assert i1[j]["F"] == pytest.approx(i0[k]["F"], rel=1e-6)
+            assert i1[j]["iters"] == i0[k]["iters"]
+        with monkeypatch.context() as m:
+            m.setenv("CVO_BATCH_QUEUE", "1")
+            Tq0, iq0, _ = h.register_batch(args)
+            Tq1, iq1, _ = h.register_batch([args[k] for k in perm])
+    for j, k in enumerate(perm):
+        assert np.array_equal(Tq0[k], Tq1[j]), k
+        assert iq0[k]["F"] == iq1[j]["F"] and iq0[k]["pairs"] == iq1[j]["pairs"], k
